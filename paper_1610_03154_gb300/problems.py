@@ -1,0 +1,268 @@
+"""Seeded synthetic inputs: sparse operators, candidate vectors and right-hand sides.
+
+This module builds the linear systems ``A x = b`` (with near-nullspace candidates
+``B``) that both the CUDA path and the CPU checker consume. It holds only the
+discretisations and random draws, none of the root-node AMG arithmetic, so it
+can be shared by both sides without coupling them.
+
+Workloads (the paper's own meshes are not available; these stand in for them):
+
+* ``poisson5``       - 5-point ``[4,-1]`` Laplacian on an ``m x m`` interior grid
+                       (Dirichlet nodes eliminated); Sec. 2 two-grid model problem.
+* ``q1_aniso``       - bilinear (Q1) finite elements for ``-div(Q^T D Q grad u)``
+                       with ``Q`` a rotation by ``psi`` and ``D = diag(1, eps)``,
+                       the rotated anisotropic diffusion of Sec. 5.2 on a structured
+                       mesh of the unit square.  ``dirichlet=False`` keeps every node
+                       (natural boundary), which is the 50x50 Q1 Laplacian of Sec. 2.3.
+* ``convdiff_upwind``- first-order upwind finite differences for
+                       ``-nu Lap u + w . grad u`` on ``[-1,1]^2`` with the
+                       recirculating wind ``w = (2y(1-x^2), -2x(1-y^2))``, the
+                       double-glazing problem of Sec. 5.3 (upwind FD instead of GFEM).
+* ``varcoef_fv``     - cell-centred finite volumes for ``-div(exp(theta) grad u)``
+                       with harmonic-mean face coefficients.
+
+Every matrix is returned as CSR with int32 ``rowptr``/``col`` (sorted, unique
+columns, explicit diagonal) and float64 values.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclass
+class CSR:
+    n_rows: int
+    n_cols: int
+    rowptr: np.ndarray  # int32 [n_rows+1]
+    col: np.ndarray     # int32 [nnz]
+    val: np.ndarray     # float64 [nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_scipy(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.val, self.col, self.rowptr), shape=(self.n_rows, self.n_cols))
+
+    @staticmethod
+    def from_scipy(m) -> "CSR":
+        m = sp.csr_matrix(m)
+        m.sum_duplicates()
+        m.sort_indices()
+        return CSR(m.shape[0], m.shape[1], m.indptr.astype(np.int32), m.indices.astype(np.int32),
+                   m.data.astype(np.float64))
+
+
+def _finish(m) -> CSR:
+    m = sp.csr_matrix(m)
+    m.sum_duplicates()
+    m.sort_indices()
+    return CSR.from_scipy(m)
+
+
+def poisson5(m: int) -> CSR:
+    """Unscaled 5-point Laplacian ``[4,-1]`` on the ``m x m`` interior nodes (row-major, x fastest)."""
+    n = m * m
+    idx = np.arange(n).reshape(m, m)  # [y, x]
+    rows = [idx.ravel()]
+    cols = [idx.ravel()]
+    vals = [np.full(n, 4.0)]
+    for dy, dx in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+        ys, xs = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+        yn, xn = ys + dy, xs + dx
+        ok = (yn >= 0) & (yn < m) & (xn >= 0) & (xn < m)
+        rows.append(idx[ys[ok], xs[ok]])
+        cols.append(idx[yn[ok], xn[ok]])
+        vals.append(np.full(int(ok.sum()), -1.0))
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    return _finish(A)
+
+
+def q1_element_stiffness(eps: float, psi: float) -> np.ndarray:
+    """4x4 bilinear element stiffness for ``K = Q^T D Q`` on a square element.
+
+    Local node order: (0,0), (1,0), (1,1), (0,1).  In 2-D the Q1 stiffness of a
+    square element does not depend on its side.  The integrand is a polynomial
+    of degree <= 2 per direction, so 2x2 Gauss quadrature is exact.
+    """
+    c, s = math.cos(psi), math.sin(psi)
+    Q = np.array([[c, -s], [s, c]])
+    D = np.diag([1.0, eps])
+    K = Q.T @ D @ Q
+    g = np.array([-1.0, 1.0]) / math.sqrt(3.0)
+    pts = (g + 1.0) / 2.0
+    Ke = np.zeros((4, 4))
+    for x in pts:
+        for y in pts:
+            # gradients of (1-x)(1-y), x(1-y), xy, (1-x)y
+            grad = np.array([[-(1 - y), -(1 - x)],
+                             [(1 - y), -x],
+                             [y, x],
+                             [-y, (1 - x)]])
+            Ke += 0.25 * grad @ K @ grad.T
+    return Ke
+
+
+def q1_aniso(ne: int, eps: float = 1.0, psi: float = 0.0, dirichlet: bool = True) -> CSR:
+    """Q1 FEM stiffness for rotated anisotropic diffusion on ``ne x ne`` square elements.
+
+    ``dirichlet=True`` eliminates the boundary nodes (homogeneous Dirichlet),
+    leaving ``(ne-1)^2`` unknowns; ``False`` keeps all ``(ne+1)^2`` nodes.
+    """
+    Ke = q1_element_stiffness(eps, psi)
+    nn = ne + 1
+    ey, ex = np.meshgrid(np.arange(ne), np.arange(ne), indexing="ij")
+    ey, ex = ey.ravel(), ex.ravel()
+    loc = np.stack([ey * nn + ex, ey * nn + ex + 1, (ey + 1) * nn + ex + 1, (ey + 1) * nn + ex], axis=1)
+    if dirichlet:
+        m = ne - 1
+        gy, gx = np.divmod(np.arange(nn * nn), nn)
+        interior = (gx > 0) & (gx < ne) & (gy > 0) & (gy < ne)
+        newid = np.full(nn * nn, -1, dtype=np.int64)
+        newid[interior] = (gy[interior] - 1) * m + (gx[interior] - 1)
+        loc = newid[loc]
+        n = m * m
+    else:
+        n = nn * nn
+    r = np.repeat(loc, 4, axis=1).ravel()
+    cidx = np.tile(loc, (1, 4)).ravel()
+    v = np.tile(Ke.ravel(), ne * ne)
+    ok = (r >= 0) & (cidx >= 0)
+    A = sp.coo_matrix((v[ok], (r[ok], cidx[ok])), shape=(n, n))
+    return _finish(A)
+
+
+def convdiff_upwind(m: int, nu: float = 1e-3) -> CSR:
+    """First-order upwind FD for ``-nu Lap u + w.grad u`` on ``[-1,1]^2``, ``m x m`` interior points.
+
+    ``h = 2/(m+1)``, wind ``w = (2y(1-x^2), -2x(1-y^2))``, homogeneous Dirichlet
+    boundary eliminated.  Rows are ordered row-major with x fastest.
+    """
+    h = 2.0 / (m + 1)
+    n = m * m
+    j, i = np.divmod(np.arange(n), m)
+    x = -1.0 + (i + 1) * h
+    y = -1.0 + (j + 1) * h
+    wx = 2.0 * y * (1.0 - x * x)
+    wy = -2.0 * x * (1.0 - y * y)
+    dif = nu / (h * h)
+    diag = 4.0 * dif + (np.abs(wx) + np.abs(wy)) / h
+    west = -dif - np.where(wx > 0, wx, 0.0) / h
+    east = -dif + np.where(wx < 0, wx, 0.0) / h
+    south = -dif - np.where(wy > 0, wy, 0.0) / h
+    north = -dif + np.where(wy < 0, wy, 0.0) / h
+    rows, cols, vals = [np.arange(n)], [np.arange(n)], [diag]
+    for coef, di, dj in ((west, -1, 0), (east, 1, 0), (south, 0, -1), (north, 0, 1)):
+        ii, jj = i + di, j + dj
+        ok = (ii >= 0) & (ii < m) & (jj >= 0) & (jj < m)
+        rows.append(np.arange(n)[ok])
+        cols.append((jj * m + ii)[ok])
+        vals.append(coef[ok])
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    return _finish(A)
+
+
+def gaussian_field(m: int, seed: int, smooth_steps: int = 5) -> np.ndarray:
+    """White noise N(0,1) on ``m x m`` cells, smoothed by Jacobi heat steps, rescaled to std 1."""
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((m, m))
+    for _ in range(smooth_steps):
+        p = np.pad(f, 1, mode="edge")
+        f = 0.5 * f + 0.125 * (p[:-2, 1:-1] + p[2:, 1:-1] + p[1:-1, :-2] + p[1:-1, 2:])
+    f = (f - f.mean()) / f.std()
+    return f.ravel()
+
+
+def varcoef_fv(m: int, theta: np.ndarray) -> tuple[CSR, np.ndarray]:
+    """Cell-centred FV for ``-div(exp(theta) grad u) = f`` on the unit square, Dirichlet u=0.
+
+    Face coefficient = harmonic mean of ``exp(theta)`` of the two cells; a
+    boundary face uses the cell's own coefficient at half distance (factor 2).
+    Returns the matrix and, for each stored entry, the index of the cell pair
+    it depends on is left to the caller (see ``varcoef_face_list``).
+    """
+    k = np.exp(theta).reshape(m, m)
+    h = 1.0 / m
+    n = m * m
+    idx = np.arange(n).reshape(m, m)
+    diag = np.zeros((m, m))
+    rows, cols, vals = [], [], []
+    # x-faces between (y, x) and (y, x+1)
+    kx = 2.0 * k[:, :-1] * k[:, 1:] / (k[:, :-1] + k[:, 1:])
+    diag[:, :-1] += kx
+    diag[:, 1:] += kx
+    rows += [idx[:, :-1].ravel(), idx[:, 1:].ravel()]
+    cols += [idx[:, 1:].ravel(), idx[:, :-1].ravel()]
+    vals += [-kx.ravel(), -kx.ravel()]
+    ky = 2.0 * k[:-1, :] * k[1:, :] / (k[:-1, :] + k[1:, :])
+    diag[:-1, :] += ky
+    diag[1:, :] += ky
+    rows += [idx[:-1, :].ravel(), idx[1:, :].ravel()]
+    cols += [idx[1:, :].ravel(), idx[:-1, :].ravel()]
+    vals += [-ky.ravel(), -ky.ravel()]
+    # Dirichlet boundary faces
+    diag[:, 0] += 2.0 * k[:, 0]
+    diag[:, -1] += 2.0 * k[:, -1]
+    diag[0, :] += 2.0 * k[0, :]
+    diag[-1, :] += 2.0 * k[-1, :]
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    f = np.full(n, h * h)
+    return _finish(A), f
+
+
+def rhs_uniform(n: int, seed: int) -> np.ndarray:
+    """Right-hand side with entries uniform in [-1, 1] from ``numpy.random.default_rng(seed)``."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, n)
+
+
+@dataclass
+class Problem:
+    name: str
+    A: CSR
+    B: np.ndarray          # n x k candidates (k = 1 here), row-major
+    b: np.ndarray          # right-hand side
+    params: dict = field(default_factory=dict)
+    Bhat: np.ndarray | None = None
+    description: str = ""
+
+
+# Solver settings per workload.  Keys mirror the C-ABI ``rn_params`` fields.
+PARAMS_POISSON = dict(soc_theta=0.25, soc_theta_coarse=0.1, degree=2, n_sweeps=4, method=0, prefilter=0.0, postfilter=0.0,
+                      max_coarse=64, max_levels=25, b_sweeps=4, omega=2.0 / 3.0, seed=12345,
+                      symmetric=1, nu_pre=1, nu_post=1, outer=0)
+PARAMS_ANISO = dict(soc_theta=0.25, soc_theta_coarse=-1.0, degree=4, n_sweeps=6, method=0, prefilter=0.1, postfilter=0.1,
+                    max_coarse=64, max_levels=25, b_sweeps=4, omega=2.0 / 3.0, seed=12345,
+                    symmetric=1, nu_pre=1, nu_post=1, outer=1)
+PARAMS_CONVDIFF = dict(soc_theta=0.25, soc_theta_coarse=-1.0, degree=1, n_sweeps=2, method=1, prefilter=0.0, postfilter=0.0,
+                       max_coarse=64, max_levels=25, b_sweeps=4, omega=2.0 / 3.0, seed=12345,
+                       symmetric=0, nu_pre=1, nu_post=1, outer=2, restart=30)
+
+
+def poisson_problem(m: int = 64, seed: int = 1) -> Problem:
+    A = poisson5(m)
+    n = A.n_rows
+    return Problem(f"poisson5_{m}x{m}", A, np.ones((n, 1)), rhs_uniform(n, seed), dict(PARAMS_POISSON),
+                   description=f"2D Poisson, 5-point FD on {m}x{m} interior grid (n={n})")
+
+
+def aniso_problem(ne: int = 1024, eps: float = 1e-3, psi: float = math.pi / 8, seed: int = 2) -> Problem:
+    A = q1_aniso(ne, eps, psi, dirichlet=True)
+    n = A.n_rows
+    return Problem(f"q1_aniso_{ne}x{ne}", A, np.ones((n, 1)), rhs_uniform(n, seed), dict(PARAMS_ANISO),
+                   description=f"2D rotated anisotropic diffusion, Q1 FEM on {ne}x{ne} elements "
+                               f"(n={n}), eps={eps}, psi={psi:.6f}")
+
+
+def convdiff_problem(m: int = 2048, nu: float = 1e-3, seed: int = 3) -> Problem:
+    A = convdiff_upwind(m, nu)
+    n = A.n_rows
+    return Problem(f"convdiff_{m}x{m}", A, np.ones((n, 1)), rhs_uniform(n, seed), dict(PARAMS_CONVDIFF),
+                   Bhat=np.ones((n, 1)),
+                   description=f"2D convection-diffusion, upwind FD on {m}x{m} grid (n={n}), nu={nu}")
