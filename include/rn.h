@@ -1,0 +1,181 @@
+/*
+ * rn.h - C ABI of the GB300 (sm_103a) root-node algebraic multigrid library.
+ *
+ * Method: Manteuffel, Olson, Schroder, Southworth, "A Root-Node Based
+ * Algebraic Multigrid Method" (arXiv:1610.03154).  The library solves the
+ * linear system A x = b of eq. linear-system (Sec. 1) with near-nullspace
+ * candidates B (and B-hat for A^T when A is nonsymmetric, Sec. 3.1):
+ *   rn_setup  builds the hierarchy of Alg. 3 (root_node_setup) on the GPU:
+ *             strength (Sec. 3.2, eq. soc), seeded root-node aggregation
+ *             (Sec. 3.3), pattern N = S^d C with pre-filter (Sec. 3.4-3.5,
+ *             Alg. 4), tentative T (Sec. 3.6, eq. root-nodeform), constrained
+ *             energy minimisation of P by CG or GMRES sweeps with the row-wise
+ *             constraint projection (Sec. 3.6, eq. Tproj, Sec. 4 Lemma th:cg),
+ *             post-filter + enforce + one re-sweep (Sec. 3.7), R = P^T or the
+ *             same construction on A^T (Sec. 3.8), Galerkin A_c = R A P.
+ *   rn_solve  runs V(nu_pre, nu_post) cycles with weighted Jacobi (Sec. 2,
+ *             eq. twogrid) and a dense LU on the coarsest level, accelerated
+ *             by CG or flexible GMRES, to a relative residual tolerance.
+ *
+ * Conventions (all entry points):
+ *   - Status codes, never abort/exit.  rn_last_error() gives a thread-local
+ *     message for the last failing call on the calling thread.
+ *   - Matrices are CSR with int32 row pointers and column indices, columns
+ *     sorted ascending and unique within each row, explicit nonzero diagonal,
+ *     float64 values.  nnz must be < 2^31.
+ *   - Location: pointers are device pointers when `location == RN_DEVICE`
+ *     and ordinary host memory when `location == RN_HOST` (the library then
+ *     copies the data in and the result out, inside the call).
+ *   - Inputs are borrowed for the duration of the call only; rn_setup copies
+ *     what it keeps.  The hierarchy is owned by the library until rn_free.
+ *   - Device work runs on params.stream (a cudaStream_t; NULL means the
+ *     legacy default stream).  Device memory comes from the stream-ordered
+ *     allocator (cudaMallocAsync) on that stream.  rn_setup and rn_solve
+ *     return after their last host read-back; outputs are complete when they
+ *     return.
+ *   - k (the number of candidates) must be 1.
+ *   - One hierarchy must not be used by two threads at once.
+ */
+#ifndef RN_H
+#define RN_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RN_OK = 0,
+    RN_EINVAL = 1,      /* bad argument or malformed CSR (unsorted, no diagonal, zero root candidate) */
+    RN_ENOMEM = 2,      /* device allocation failed */
+    RN_ESINGULAR = 3,   /* coarsest-level LU met a pivot below 1e-14 max|A| */
+    RN_ESTALL = 4,      /* coarsening stopped with more than 4096 rows left for the dense LU */
+    RN_ENOTCONV = 5,    /* solve hit maxit before the tolerance (x holds the last iterate) */
+    RN_ETIMEOUT = 6,    /* a bounded device loop (aggregation rounds) did not finish */
+    RN_ECUDA = 7,       /* a CUDA runtime call failed */
+    RN_EINTERNAL = 8    /* internal limit exceeded (e.g. a product row over 16384 distinct columns) */
+} rn_status;
+
+enum { RN_DEVICE = 0, RN_HOST = 1 };
+enum { RN_ENERGY_CG = 0, RN_ENERGY_GMRES = 1 };
+enum { RN_FP64 = 0, RN_MIXED = 1 };
+enum { RN_OUTER_STATIONARY = 0, RN_OUTER_CG = 1, RN_OUTER_FGMRES = 2 };
+
+typedef struct {
+    int32_t n_rows, n_cols;
+    int64_t nnz;
+    const int32_t *rowptr; /* n_rows + 1 */
+    const int32_t *col;    /* nnz */
+    const double *val;     /* nnz */
+} rn_csr;
+
+typedef struct {
+    double soc_theta;        /* strength drop tolerance on the finest level (Sec. 3.2) */
+    double soc_theta_coarse; /* on levels >= 1; < 0 means same as soc_theta */
+    int degree;              /* d in N = S^d C (Sec. 3.4) */
+    int n_sweeps;            /* energy-minimisation iterations (Sec. 3.6; paper: ceil(1.5 d)) */
+    int energy_method;       /* RN_ENERGY_CG (SPD) or RN_ENERGY_GMRES */
+    int energy_precond;      /* 1: Jacobi row scaling in CG energy minimisation */
+    double prefilter;        /* theta_pre of Alg. 4 on N (<= 0: off) */
+    double postfilter;       /* theta_post of Alg. 4 on P (<= 0: off) */
+    int max_coarse;          /* coarsen while n > max_coarse */
+    int max_levels;          /* <= 32 */
+    int b_sweeps;            /* candidate relaxation sweeps (Sec. 3.1; paper: 4) */
+    double omega;            /* weighted-Jacobi weight (cycle and candidate sweeps) */
+    uint64_t seed;           /* aggregation priority seed (level l uses seed + l) */
+    int symmetric;           /* 1: R = P^T;  0: R built from A^T and B-hat */
+    int nu_pre, nu_post;     /* V-cycle relaxation counts */
+    int precision;           /* RN_FP64, or RN_MIXED: FP32 cycle inside the FP64 outer iteration */
+    int outer;               /* RN_OUTER_STATIONARY / RN_OUTER_CG / RN_OUTER_FGMRES */
+    int restart;             /* FGMRES restart length */
+    int use_graphs;          /* 1: capture the preconditioner cycle in a CUDA graph */
+    int keep_aux;            /* 1: keep S, N, T, agg, roots per level for rn_export_* */
+    void *stream;            /* cudaStream_t */
+} rn_params;
+
+typedef struct {
+    int iters;
+    double rel_res;  /* ||b - A x|| / ||b|| in FP64 at exit */
+    double rho;      /* average convergence factor (r_K / r_0)^(1/K) */
+    double solve_ms; /* wall time of the call */
+    int status;
+} rn_solve_info;
+
+#define RN_MAX_LEVELS 32
+typedef struct {
+    int levels;
+    int32_t n[RN_MAX_LEVELS];
+    int64_t nnz_A[RN_MAX_LEVELS], nnz_P[RN_MAX_LEVELS], nnz_R[RN_MAX_LEVELS];
+    double oc;        /* operator complexity, eq. oc */
+    double cc;        /* cycle complexity, eq. cc */
+    double setup_ms;  /* wall time of rn_setup */
+    int agg_rounds;   /* aggregation rounds summed over levels */
+} rn_stats;
+
+typedef struct rn_hierarchy rn_hierarchy;
+
+/* Fill *p with the defaults (theta 0.25, d 2, 4 CG sweeps, no filtering,
+ * max_coarse 64, 4 candidate sweeps, omega 2/3, symmetric, V(1,1), FP64,
+ * CG outer, graphs on).  Returns RN_EINVAL for p == NULL. */
+rn_status rn_default_params(rn_params *p);
+
+/* Build the hierarchy (Alg. 3) for A with candidates B (n x k, row-major,
+ * k == 1) and, when p->symmetric == 0, Bhat (candidates for A^T).
+ * `location` applies to A's arrays, B and Bhat.  On success *out owns the
+ * hierarchy; on any error *out is NULL and nothing is leaked. */
+rn_status rn_setup(const rn_csr *A, const double *B, const double *Bhat, int k, int location,
+                   const rn_params *p, rn_hierarchy **out);
+
+/* Solve A x = b to ||b - A x|| <= rtol ||b||: x holds x0 on entry and the
+ * solution on exit (n entries each, `location` as in rn_setup).  info may be
+ * NULL.  Returns RN_ENOTCONV when maxit outer iterations did not converge. */
+rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int location, double rtol, int maxit,
+                   rn_solve_info *info);
+
+/* Apply one V-cycle to b with zero initial guess: x = M^{-1} b (device
+ * pointers, FP64, level-0 size).  Used to check the cycle itself. */
+rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x);
+
+/* Release everything the hierarchy owns.  NULL is a no-op. */
+void rn_free(rn_hierarchy *h);
+
+/* Level sizes and the complexities of Sec. 2.4 (eq. oc, eq. cc). */
+rn_status rn_hierarchy_stats(const rn_hierarchy *h, rn_stats *s);
+
+/* Copy one matrix of level `lvl` to host buffers.
+ * which: 0 A, 1 S, 2 N (pattern after pre-filter and root pattern, values of
+ * S^d C), 3 T, 4 P, 5 R.  S, N and T need keep_aux.  Call once with NULL
+ * arrays to get n_rows, n_cols and nnz, then with buffers of rowptr[n_rows+1],
+ * col[nnz], val[nnz].  Returns RN_EINVAL when the matrix does not exist. */
+rn_status rn_export_csr(const rn_hierarchy *h, int lvl, int which, int32_t *n_rows, int32_t *n_cols, int64_t *nnz,
+                        int32_t *rowptr, int32_t *col, double *val);
+
+/* Copy one vector of level `lvl` to host.  which: 0 agg (int32, n), 1 roots
+ * (int32, n_c), 2 row types (int32, n: 0 free, 1 root, 2 unaggregated),
+ * 3 smoothed B (double, n), 4 Bc (double, n_c), 5 smoothed B-hat, 6 B-hat_c.
+ * out == NULL only returns *len. */
+rn_status rn_export_vec(const rn_hierarchy *h, int lvl, int which, int64_t *len, void *out);
+
+/* Per-kernel device timing.  While enabled, every library kernel launch is
+ * bracketed by CUDA events on its stream; rn_profile_read returns, per kernel
+ * name, the launch count, summed device milliseconds and the algorithmic
+ * bytes the launches moved (the traffic model of each kernel: every input
+ * and output array touched once).  Process-wide, not thread-safe. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double ms;
+    double bytes;
+} rn_kernel_stat;
+rn_status rn_profile_enable(int on);
+rn_status rn_profile_reset(void);
+rn_status rn_profile_read(rn_kernel_stat *out, int max, int *count);
+
+const char *rn_last_error(void);
+const char *rn_status_string(rn_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,268 @@
+// rn_api.cu - the extern "C" entry points declared in include/rn.h.
+// Each entry point converts internal errors (rn::Error) into status codes and
+// records a thread-local message; nothing aborts.
+#include <cstring>
+
+#include "rn_hier.cuh"
+
+namespace rn {
+const std::string &last_error_ref();
+}
+
+rn_hierarchy::~rn_hierarchy() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+}
+
+#define RN_API_BEGIN try {
+#define RN_API_END                                                          \
+    }                                                                       \
+    catch (const rn::Error &e) {                                            \
+        rn::set_last_error(e.msg);                                          \
+        return e.status;                                                    \
+    }                                                                       \
+    catch (const std::bad_alloc &) {                                        \
+        rn::set_last_error("host allocation failed");                       \
+        return RN_ENOMEM;                                                   \
+    }                                                                       \
+    catch (...) {                                                           \
+        rn::set_last_error("unexpected internal exception");                \
+        return RN_EINTERNAL;                                                \
+    }
+
+extern "C" rn_status rn_default_params(rn_params *p) {
+    if (!p) return RN_EINVAL;
+    std::memset(p, 0, sizeof *p);
+    p->soc_theta = 0.25;
+    p->soc_theta_coarse = -1.0;
+    p->degree = 2;
+    p->n_sweeps = 4;
+    p->energy_method = RN_ENERGY_CG;
+    p->energy_precond = 1;
+    p->prefilter = 0.0;
+    p->postfilter = 0.0;
+    p->max_coarse = 64;
+    p->max_levels = 25;
+    p->b_sweeps = 4;
+    p->omega = 2.0 / 3.0;
+    p->seed = 12345;
+    p->symmetric = 1;
+    p->nu_pre = 1;
+    p->nu_post = 1;
+    p->precision = RN_FP64;
+    p->outer = RN_OUTER_CG;
+    p->restart = 30;
+    p->use_graphs = 1;
+    p->keep_aux = 0;
+    p->stream = nullptr;
+    return RN_OK;
+}
+
+static void check_params(const rn_params *p) {
+    using rn::fail;
+    if (p->degree < 0 || p->degree > 16) fail(RN_EINVAL, "degree must be in [0, 16]");
+    if (p->n_sweeps < 0 || p->n_sweeps > 1000) fail(RN_EINVAL, "n_sweeps must be in [0, 1000]");
+    if (p->energy_method != RN_ENERGY_CG && p->energy_method != RN_ENERGY_GMRES) fail(RN_EINVAL, "energy_method");
+    if (p->max_levels < 1) fail(RN_EINVAL, "max_levels must be >= 1");
+    if (p->max_coarse < 1) fail(RN_EINVAL, "max_coarse must be >= 1");
+    if (p->b_sweeps < 0) fail(RN_EINVAL, "b_sweeps must be >= 0");
+    if (p->nu_pre < 0 || p->nu_post < 0) fail(RN_EINVAL, "nu_pre/nu_post must be >= 0");
+    if (p->precision != RN_FP64 && p->precision != RN_MIXED) fail(RN_EINVAL, "precision");
+    if (p->outer < RN_OUTER_STATIONARY || p->outer > RN_OUTER_FGMRES) fail(RN_EINVAL, "outer");
+    if (p->outer == RN_OUTER_FGMRES && (p->restart < 1 || p->restart > 1000)) fail(RN_EINVAL, "restart");
+    if (!(p->omega > 0.0)) fail(RN_EINVAL, "omega must be > 0");
+}
+
+extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bhat, int k, int location,
+                              const rn_params *p, rn_hierarchy **out) {
+    if (out) *out = nullptr;
+    RN_API_BEGIN
+    using rn::fail;
+    if (!A || !B || !p || !out) fail(RN_EINVAL, "null argument");
+    if (k != 1) fail(RN_EINVAL, "only k = 1 candidate is supported");
+    if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
+    if (A->n_rows <= 0 || A->n_rows != A->n_cols) fail(RN_EINVAL, "A must be square and non-empty");
+    if (A->nnz <= 0 || A->nnz > INT32_MAX - 1) fail(RN_EINVAL, "nnz out of range");
+    if (!A->rowptr || !A->col || !A->val) fail(RN_EINVAL, "null CSR array");
+    check_params(p);
+    if (!p->symmetric && !Bhat) fail(RN_EINVAL, "nonsymmetric setup needs Bhat");
+    std::unique_ptr<rn_hierarchy> h(new rn_hierarchy());
+    h->p = *p;
+    h->s = static_cast<cudaStream_t>(p->stream);
+    cudaStream_t s = h->s;
+    const double t0 = rn::now_ms();
+    const int32_t n = A->n_rows;
+    rn::DVec<int32_t> rp, ci;
+    rn::DVec<double> va, Bd, Bhd;
+    rn::CsrView Av{n, n, A->nnz, A->rowptr, A->col, A->val};
+    const double *Bp = B, *Bhp = Bhat;
+    if (location == RN_HOST) {
+        rp.alloc(n + 1, s);
+        ci.alloc(A->nnz, s);
+        va.alloc(A->nnz, s);
+        Bd.alloc(n, s);
+        rn::h2d(rp.p, A->rowptr, n + 1, s);
+        rn::h2d(ci.p, A->col, A->nnz, s);
+        rn::h2d(va.p, A->val, A->nnz, s);
+        rn::h2d(Bd.p, B, n, s);
+        Av.rowptr = rp.p;
+        Av.col = ci.p;
+        Av.val = va.p;
+        Bp = Bd.p;
+        if (!p->symmetric) {
+            Bhd.alloc(n, s);
+            rn::h2d(Bhd.p, Bhat, n, s);
+            Bhp = Bhd.p;
+        }
+    }
+    rn::build_hierarchy(*h, Av, Bp, Bhp);
+    rn::prepare_solve(*h);
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    h->setup_ms = rn::now_ms() - t0;
+    *out = h.release();
+    return RN_OK;
+    RN_API_END
+}
+
+extern "C" rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int location, double rtol, int maxit,
+                              rn_solve_info *info) {
+    RN_API_BEGIN
+    using rn::fail;
+    if (!h || !b || !x) fail(RN_EINVAL, "null argument");
+    if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
+    if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
+    cudaStream_t s = h->s;
+    const int64_t n = h->lev[0]->A.n;
+    const double t0 = rn::now_ms();
+    rn_status st;
+    if (location == RN_HOST) {
+        rn::DVec<double> bd(n, s), xd(n, s);
+        rn::h2d(bd.p, b, n, s);
+        rn::h2d(xd.p, x, n, s);
+        st = rn::solve(*h, bd.p, xd.p, rtol, maxit, info);
+        rn::d2h(x, xd.p, n, s);
+        RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    } else {
+        st = rn::solve(*h, b, x, rtol, maxit, info);
+    }
+    if (info) info->solve_ms = rn::now_ms() - t0;
+    if (st == RN_ENOTCONV) rn::set_last_error("solve did not reach the tolerance within maxit");
+    return st;
+    RN_API_END
+}
+
+extern "C" rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x) {
+    RN_API_BEGIN
+    if (!h || !b || !x) rn::fail(RN_EINVAL, "null argument");
+    rn::apply_cycle(*h, b, x);
+    RN_CUDA_CHECK(cudaStreamSynchronize(h->s));
+    return RN_OK;
+    RN_API_END
+}
+
+extern "C" void rn_free(rn_hierarchy *h) {
+    if (!h) return;
+    cudaStream_t s = h->s;
+    try {
+        delete h;
+    } catch (...) {
+    }
+    cudaStreamSynchronize(s);
+}
+
+extern "C" rn_status rn_hierarchy_stats(const rn_hierarchy *h, rn_stats *st) {
+    if (!h || !st) return RN_EINVAL;
+    std::memset(st, 0, sizeof *st);
+    st->levels = (int)h->lev.size();
+    const double nnz0 = (double)h->lev[0]->A.nnz;
+    double oc = 0.0, cc = 0.0;
+    const int nu = h->p.nu_pre + h->p.nu_post;
+    for (size_t l = 0; l < h->lev.size() && l < RN_MAX_LEVELS; l++) {
+        const rn_level &L = *h->lev[l];
+        st->n[l] = L.A.n;
+        st->nnz_A[l] = L.A.nnz;
+        st->nnz_P[l] = L.P.nnz;
+        st->nnz_R[l] = L.R.nnz;
+        oc += L.A.nnz / nnz0;
+        if (l + 1 < h->lev.size()) cc += ((nu + 1) * (double)L.A.nnz + L.P.nnz + L.R.nnz) / nnz0;
+    }
+    st->oc = oc;
+    st->cc = cc;
+    st->setup_ms = h->setup_ms;
+    st->agg_rounds = h->agg_rounds;
+    return RN_OK;
+}
+
+extern "C" rn_status rn_export_csr(const rn_hierarchy *h, int lvl, int which, int32_t *n_rows, int32_t *n_cols,
+                                   int64_t *nnz, int32_t *rowptr, int32_t *col, double *val) {
+    RN_API_BEGIN
+    using rn::fail;
+    if (!h || lvl < 0 || lvl >= (int)h->lev.size()) fail(RN_EINVAL, "level out of range");
+    const rn_level &L = *h->lev[lvl];
+    const rn::DCsr *M = nullptr;
+    switch (which) {
+        case 0: M = &L.A; break;
+        case 1: M = &L.S; break;
+        case 2: M = &L.N; break;
+        case 3: M = &L.T; break;
+        case 4: M = &L.P; break;
+        case 5: M = &L.R; break;
+        default: fail(RN_EINVAL, "which");
+    }
+    if (!M->rowptr.p) fail(RN_EINVAL, "matrix not present on this level (keep_aux off or coarsest level)");
+    if (n_rows) *n_rows = M->n;
+    if (n_cols) *n_cols = M->m;
+    if (nnz) *nnz = M->nnz;
+    cudaStream_t s = h->s;
+    if (rowptr) rn::d2h(rowptr, M->rowptr.p, M->n + 1, s);
+    if (col) rn::d2h(col, M->col.p, M->nnz, s);
+    if (val && M->val.p) rn::d2h(val, M->val.p, M->nnz, s);
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    return RN_OK;
+    RN_API_END
+}
+
+extern "C" rn_status rn_export_vec(const rn_hierarchy *h, int lvl, int which, int64_t *len, void *out) {
+    RN_API_BEGIN
+    using rn::fail;
+    if (!h || !len || lvl < 0 || lvl >= (int)h->lev.size()) fail(RN_EINVAL, "bad argument");
+    const rn_level &L = *h->lev[lvl];
+    const void *src = nullptr;
+    size_t elt = 4;
+    int64_t n = 0;
+    switch (which) {
+        case 0: src = L.agg.p; n = L.agg.n; break;
+        case 1: src = L.roots.p; n = L.roots.n; break;
+        case 2: src = L.rowtype.p; n = L.rowtype.n; break;
+        case 3: src = L.B.p; n = L.B.n; elt = 8; break;
+        case 4: src = L.Bc.p; n = L.Bc.n; elt = 8; break;
+        case 5: src = L.Bhat.p; n = L.Bhat.n; elt = 8; break;
+        case 6: src = L.Bhatc.p; n = L.Bhatc.n; elt = 8; break;
+        default: fail(RN_EINVAL, "which");
+    }
+    if (!src) fail(RN_EINVAL, "vector not present on this level");
+    *len = n;
+    if (out) {
+        RN_CUDA_CHECK(cudaMemcpyAsync(out, src, (size_t)n * elt, cudaMemcpyDeviceToHost, h->s));
+        RN_CUDA_CHECK(cudaStreamSynchronize(h->s));
+    }
+    return RN_OK;
+    RN_API_END
+}
+
+extern "C" const char *rn_last_error(void) { return rn::last_error_ref().c_str(); }
+
+extern "C" const char *rn_status_string(rn_status s) {
+    switch (s) {
+        case RN_OK: return "RN_OK";
+        case RN_EINVAL: return "RN_EINVAL";
+        case RN_ENOMEM: return "RN_ENOMEM";
+        case RN_ESINGULAR: return "RN_ESINGULAR";
+        case RN_ESTALL: return "RN_ESTALL";
+        case RN_ENOTCONV: return "RN_ENOTCONV";
+        case RN_ETIMEOUT: return "RN_ETIMEOUT";
+        case RN_ECUDA: return "RN_ECUDA";
+        case RN_EINTERNAL: return "RN_EINTERNAL";
+    }
+    return "unknown";
+}

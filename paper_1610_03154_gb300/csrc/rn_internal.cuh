@@ -1,0 +1,229 @@
+// rn_internal.cuh - shared internals of the root-node AMG CUDA library.
+//
+// Error model: internal code throws rn::Error (status + message); every C-ABI
+// entry point catches it and returns the status.  Device buffers are RAII
+// objects freed with cudaFreeAsync on the stream they were allocated on, so an
+// exception anywhere in setup releases everything.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/rn.h"
+
+namespace rn {
+
+struct Error {
+    rn_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(rn_status s, const std::string &msg);
+void set_last_error(const std::string &msg);
+
+#define RN_CUDA_CHECK(call)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            if (e_ == cudaErrorMemoryAllocation)                                              \
+                ::rn::fail(RN_ENOMEM, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+            ::rn::fail(RN_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+        }                                                                                     \
+    } while (0)
+
+// --------------------------------------------------------------- device memory
+void *dmalloc(size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+
+template <typename T>
+struct DVec {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DVec() = default;
+    DVec(size_t n_, cudaStream_t s_) { alloc(n_, s_); }
+    void alloc(size_t n_, cudaStream_t s_) {
+        release();
+        s = s_;
+        n = n_;
+        p = n ? static_cast<T *>(dmalloc(n * sizeof(T), s)) : nullptr;
+    }
+    void release() {
+        if (p) dfree(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    ~DVec() { release(); }
+    DVec(const DVec &) = delete;
+    DVec &operator=(const DVec &) = delete;
+    DVec(DVec &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DVec &operator=(DVec &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; s = o.s;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    T *get() const { return p; }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// Device CSR owned by the library.  val32 is the FP32 shadow used by the
+// mixed-precision cycle.
+struct DCsr {
+    int32_t n = 0, m = 0;
+    int64_t nnz = 0;
+    DVec<int32_t> rowptr, col;
+    DVec<double> val;
+    DVec<float> val32;
+};
+
+// Borrowed view of a CSR (device pointers).
+struct CsrView {
+    int32_t n, m;
+    int64_t nnz;
+    const int32_t *rowptr, *col;
+    const double *val;
+};
+inline CsrView view(const DCsr &a) { return CsrView{a.n, a.m, a.nnz, a.rowptr.p, a.col.p, a.val.p}; }
+
+// --------------------------------------------------------------- launches
+int num_sms();
+int grid_for(int64_t work_items, int items_per_block, int blocks_per_sm = 8);
+
+// Profiled launch: records CUDA events around the kernel when profiling is on
+// and attributes `bytes` of algorithmic traffic to `name`.
+struct ProfScope {
+    const char *name;
+    double bytes;
+    cudaStream_t s;
+    int slot = -1;
+    ProfScope(const char *name_, double bytes_, cudaStream_t s_);
+    ~ProfScope() noexcept(false);
+};
+void check_launch(const char *name);
+bool profiling_enabled();
+
+#define RN_LAUNCH(name, bytes, stream, kernel, grid, block, smem, ...)     \
+    do {                                                                   \
+        ::rn::ProfScope ps_((name), (double)(bytes), (stream));            \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);        \
+        ::rn::check_launch(name);                                          \
+    } while (0)
+
+template <typename T>
+void h2d(T *dst, const T *src, size_t n, cudaStream_t s) {
+    if (n) RN_CUDA_CHECK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+template <typename T>
+void d2h(T *dst, const T *src, size_t n, cudaStream_t s) {
+    if (n) RN_CUDA_CHECK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+}
+template <typename T>
+void d2d(T *dst, const T *src, size_t n, cudaStream_t s) {
+    if (n) RN_CUDA_CHECK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+}
+template <typename T>
+T read_scalar(const T *dptr, cudaStream_t s) {
+    T v;
+    RN_CUDA_CHECK(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    return v;
+}
+
+// --------------------------------------------------------------- primitives (rn_prims.cu)
+// Exclusive scan of n int32 counts into out[0..n] (out[n] = total); returns
+// the total (one device->host read).  Fails with RN_EINTERNAL if the total
+// does not fit in int32.
+int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t s);
+// Deterministic two-stage dot products: partial sums per block in fixed order.
+constexpr int kReduceBlocks = 1216;   // partial-sum slots (8 x 152 SMs)
+void dot(const double *x, const double *y, int64_t n, double *result, cudaStream_t s, double *partial);
+// *result = sum of partial[0..nb) in a fixed order (one block).
+void reduce_partials(const double *partial, int nb, double *result, cudaStream_t s);
+void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
+void fill_f64(double *p, double v, int64_t n, cudaStream_t s);
+// diag[i] = a_ii (fails RN_EINVAL through *bad when a diagonal is missing or zero)
+void extract_diag(const CsrView &A, double *diag, int32_t *bad, cudaStream_t s);
+// Transpose with sorted rows (values optional).
+void transpose(const CsrView &A, bool with_val, DCsr &At, cudaStream_t s);
+void to_float(const double *x, float *y, int64_t n, cudaStream_t s);
+
+// --------------------------------------------------------------- products (rn_spgemm.cu)
+// Symbolic product pattern of A*B (explicit zeros kept), rows sorted.
+void spgemm_symbolic(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s);
+// Values of C = A*B on C's pattern (which must contain every product).
+// exact = true: products and sums in ascending k order with no fused
+// multiply-add (matches a plain sequential CPU evaluation bit for bit).
+void spgemm_numeric(const CsrView &A, const CsrView &B, DCsr &C, bool exact, cudaStream_t s);
+
+// Energy-minimisation operator on the fixed pattern N shared by X and W:
+//   W = Proj(Mask_N(A X)) (scale = -1 negates), plus, when dot_out != nullptr,
+//   the Frobenius product <Y, W> reduced deterministically into *dot_out.
+struct ProjArgs {
+    const int32_t *rowtype;  // 0 free, 1 root, 2 unaggregated
+    const double *Bc;        // coarse candidates
+};
+void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, int32_t nc,
+                         const double *X, double *W, const ProjArgs &pa, double scale, const double *Y,
+                         double *dot_out, double *partial, cudaStream_t s);
+
+// --------------------------------------------------------------- misc
+std::string fmt(const char *f, ...);
+double now_ms();
+
+}  // namespace rn
+
+// --------------------------------------------------------------- device helpers
+namespace rn {
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ double group_sum(double v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ float group_sumf(float v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if (G == 32) return 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    return ((1u << (G & 31)) - 1u) << (lane & ~(G - 1));
+}
+// SplitMix64 (Steele, Lea, Flood 2014), from its published definition.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+// Block-level sum of one double per thread; result valid in thread 0.
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v, double *smem32) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) smem32[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < BLOCK / 32) ? smem32[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+}  // namespace rn

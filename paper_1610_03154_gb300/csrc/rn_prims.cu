@@ -1,0 +1,422 @@
+// rn_prims.cu - allocator, profiling, scan, deterministic reductions,
+// transpose and small elementwise kernels.
+#include <cstdarg>
+#include <chrono>
+#include <map>
+#include <mutex>
+
+#include "rn_internal.cuh"
+
+namespace rn {
+
+// --------------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+const std::string &last_error_ref() { return g_last_error; }
+
+[[noreturn]] void fail(rn_status s, const std::string &msg) { throw Error{s, msg}; }
+
+std::string fmt(const char *f, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, f);
+    vsnprintf(buf, sizeof buf, f, ap);
+    va_end(ap);
+    return std::string(buf);
+}
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// --------------------------------------------------------------------- memory
+static bool g_pool_configured = false;
+
+void *dmalloc(size_t bytes, cudaStream_t s) {
+    if (!g_pool_configured) {
+        // keep freed blocks cached in the device's default pool: setup makes
+        // many short-lived allocations
+        int dev = 0;
+        RN_CUDA_CHECK(cudaGetDevice(&dev));
+        cudaMemPool_t pool;
+        RN_CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, dev));
+        uint64_t thr = UINT64_MAX;
+        RN_CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pool_configured = true;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(e == cudaErrorMemoryAllocation ? RN_ENOMEM : RN_ECUDA,
+             fmt("cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e)));
+    }
+    return p;
+}
+
+void dfree(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// --------------------------------------------------------------------- launch helpers
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        RN_CUDA_CHECK(cudaGetDevice(&dev));
+        RN_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
+int grid_for(int64_t work_items, int items_per_block, int blocks_per_sm) {
+    int64_t need = (work_items + items_per_block - 1) / items_per_block;
+    int64_t cap = (int64_t)num_sms() * blocks_per_sm;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+void check_launch(const char *name) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) fail(RN_ECUDA, fmt("launch of %s: %s", name, cudaGetErrorString(e)));
+}
+
+// --------------------------------------------------------------------- profiling
+struct Pending {
+    std::string name;
+    double bytes;
+    cudaEvent_t a, b;
+};
+struct KStat {
+    int64_t launches = 0;
+    double ms = 0.0, bytes = 0.0;
+};
+static bool g_prof_on = false;
+static std::vector<Pending> g_pending;
+static std::vector<cudaEvent_t> g_event_pool;
+static std::map<std::string, KStat> g_stats;
+static std::mutex g_prof_mu;
+
+bool profiling_enabled() { return g_prof_on; }
+
+static cudaEvent_t get_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    RN_CUDA_CHECK(cudaEventCreate(&e));
+    return e;
+}
+
+static void drain_pending() {
+    for (auto &p : g_pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        KStat &k = g_stats[p.name];
+        k.launches++;
+        k.ms += ms;
+        k.bytes += p.bytes;
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
+}
+
+ProfScope::ProfScope(const char *name_, double bytes_, cudaStream_t s_) : name(name_), bytes(bytes_), s(s_) {
+    if (!g_prof_on) return;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    Pending p{name, bytes, get_event(), get_event()};
+    cudaEventRecord(p.a, s);
+    g_pending.push_back(p);
+    slot = (int)g_pending.size() - 1;
+    if (g_pending.size() > 4096) {
+        // keep the pending list bounded (this synchronises the recorded events)
+        cudaEventRecord(g_pending.back().b, s);
+        Pending last = g_pending.back();
+        g_pending.pop_back();
+        drain_pending();
+        g_pending.push_back(last);
+        slot = 0;
+    }
+}
+
+ProfScope::~ProfScope() noexcept(false) {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (slot < (int)g_pending.size()) cudaEventRecord(g_pending[slot].b, s);
+}
+
+}  // namespace rn
+
+extern "C" rn_status rn_profile_enable(int on) {
+    rn::g_prof_on = (on != 0);
+    return RN_OK;
+}
+
+extern "C" rn_status rn_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(rn::g_prof_mu);
+    rn::drain_pending();
+    rn::g_stats.clear();
+    return RN_OK;
+}
+
+extern "C" rn_status rn_profile_read(rn_kernel_stat *out, int max, int *count) {
+    std::lock_guard<std::mutex> lk(rn::g_prof_mu);
+    rn::drain_pending();
+    int c = 0;
+    for (auto &kv : rn::g_stats) {
+        if (out && c < max) {
+            snprintf(out[c].name, sizeof out[c].name, "%s", kv.first.c_str());
+            out[c].launches = kv.second.launches;
+            out[c].ms = kv.second.ms;
+            out[c].bytes = kv.second.bytes;
+        }
+        c++;
+    }
+    if (count) *count = c;
+    return RN_OK;
+}
+
+namespace rn {
+
+// --------------------------------------------------------------------- scan
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+// exclusive block scan of one int64 per thread; returns the block total
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t *out_excl, int64_t *smem) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = (lane < (int)(blockDim.x >> 5)) ? smem[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        smem[lane] = t;  // inclusive warp totals
+    }
+    __syncthreads();
+    int64_t warp_off = (w > 0) ? smem[w - 1] : 0;
+    int64_t total = smem[(blockDim.x >> 5) - 1];
+    *out_excl = warp_off + x - v;
+    __syncthreads();
+    return total;
+}
+
+__global__ void scan_block_sums(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ sums) {
+    __shared__ int64_t smem[32];
+    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int64_t v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++)
+        if (base + k < n) v += in[base + k];
+    int64_t ex;
+    int64_t tot = block_exclusive_scan(v, &ex, smem);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void scan_sums(int64_t *__restrict__ sums, int64_t nb, int64_t *__restrict__ total) {
+    __shared__ int64_t smem[32];
+    // each thread takes a contiguous slice of the block sums
+    int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+    int64_t lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
+    int64_t v = 0;
+    for (int64_t i = lo; i < hi; i++) v += sums[i];
+    int64_t ex;
+    int64_t tot = block_exclusive_scan(v, &ex, smem);
+    int64_t run = ex;
+    for (int64_t i = lo; i < hi; i++) {
+        int64_t t = sums[i];
+        sums[i] = run;
+        run += t;
+    }
+    if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void scan_apply(const int32_t *__restrict__ in, int64_t n, const int64_t *__restrict__ offs,
+                           const int64_t *__restrict__ total, int32_t *__restrict__ out) {
+    __shared__ int64_t smem[32];
+    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int32_t vals[kScanItems];
+    int64_t v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        vals[k] = (base + k < n) ? in[base + k] : 0;
+        v += vals[k];
+    }
+    int64_t ex;
+    block_exclusive_scan(v, &ex, smem);
+    int64_t run = offs[blockIdx.x] + ex;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        if (base + k < n) out[base + k] = (int32_t)run;
+        run += vals[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (int32_t)(*total);
+}
+
+int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t s) {
+    int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb < 1) nb = 1;
+    DVec<int64_t> sums(nb + 1, s);
+    int64_t *total = sums.p + nb;
+    RN_LAUNCH("scan", 4.0 * n, s, scan_block_sums, (int)nb, kScanThreads, 0, counts, n, sums.p);
+    RN_LAUNCH("scan", 8.0 * nb, s, scan_sums, 1, kScanThreads, 0, sums.p, nb, total);
+    RN_LAUNCH("scan", 8.0 * n, s, scan_apply, (int)nb, kScanThreads, 0, counts, n, sums.p, total, out);
+    int64_t t = read_scalar(total, s);
+    if (t > INT32_MAX) fail(RN_EINTERNAL, fmt("scan total %lld exceeds int32", (long long)t));
+    return t;
+}
+
+// --------------------------------------------------------------------- reductions
+constexpr int kRedThreads = 256;
+
+__global__ void dot_partial(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+                            double *__restrict__ partial) {
+    __shared__ double sm[32];
+    double v = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v += x[i] * y[i];
+    double t = block_sum<kRedThreads>(v, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void reduce_final(const double *__restrict__ partial, int nb, double *__restrict__ result) {
+    __shared__ double sm[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += partial[i];
+    double t = block_sum<1024>(v, sm);
+    if (threadIdx.x == 0) *result = t;
+}
+
+void reduce_partials(const double *partial, int nb, double *result, cudaStream_t s) {
+    RN_LAUNCH("reduce_final", 8.0 * nb, s, reduce_final, 1, 1024, 0, partial, nb, result);
+}
+
+void dot(const double *x, const double *y, int64_t n, double *result, cudaStream_t s, double *partial) {
+    int nb = grid_for(n, kRedThreads * 4, 8);
+    if (nb > kReduceBlocks) nb = kReduceBlocks;
+    RN_LAUNCH("dot", 16.0 * n, s, dot_partial, nb, kRedThreads, 0, x, y, n, partial);
+    RN_LAUNCH("reduce_final", 8.0 * nb, s, reduce_final, 1, 1024, 0, partial, nb, result);
+}
+
+// --------------------------------------------------------------------- elementwise
+__global__ void fill_i32_kernel(int32_t *p, int32_t v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+__global__ void fill_f64_kernel(double *p, double v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+__global__ void to_float_kernel(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
+void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    RN_LAUNCH("fill", 4.0 * n, s, fill_i32_kernel, grid_for(n, 1024), 256, 0, p, v, n);
+}
+void fill_f64(double *p, double v, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    RN_LAUNCH("fill", 8.0 * n, s, fill_f64_kernel, grid_for(n, 1024), 256, 0, p, v, n);
+}
+void to_float(const double *x, float *y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    RN_LAUNCH("to_float", 12.0 * n, s, to_float_kernel, grid_for(n, 1024), 256, 0, x, y, n);
+}
+
+__global__ void extract_diag_kernel(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                    const double *__restrict__ val, double *__restrict__ diag, int32_t *bad) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double d = 0.0;
+        int found = 0;
+        for (int32_t e = rowptr[i]; e < rowptr[i + 1]; e++)
+            if (col[e] == i) { d = val[e]; found = 1; }
+        diag[i] = d;
+        if (!found || d == 0.0) atomicMax(bad, i + 1);
+    }
+}
+
+void extract_diag(const CsrView &A, double *diag, int32_t *bad, cudaStream_t s) {
+    RN_LAUNCH("extract_diag", 12.0 * A.nnz + 12.0 * A.n, s, extract_diag_kernel, grid_for(A.n, 256), 256, 0, A.n,
+              A.rowptr, A.col, A.val, diag, bad);
+}
+
+// --------------------------------------------------------------------- transpose
+__global__ void count_cols_kernel(int64_t nnz, const int32_t *__restrict__ col, int32_t *__restrict__ cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[col[e]], 1);
+}
+
+__global__ void transpose_scatter_kernel(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                         const double *__restrict__ val, int32_t *__restrict__ next,
+                                         int32_t *__restrict__ tcol, double *__restrict__ tval) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int32_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+            int32_t pos = atomicAdd(&next[col[e]], 1);
+            tcol[pos] = i;
+            if (val) tval[pos] = val[e];
+        }
+    }
+}
+
+// warp per output row: rank sort of the (unique) row indices of the segment
+__global__ void segment_rank_sort_kernel(int32_t m, const int32_t *__restrict__ rowptr,
+                                         const int32_t *__restrict__ kin, const double *__restrict__ vin,
+                                         int32_t *__restrict__ kout, double *__restrict__ vout) {
+    const int lane = threadIdx.x & 31;
+    for (int32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < m; r += (gridDim.x * blockDim.x) >> 5) {
+        int32_t s = rowptr[r], t = rowptr[r + 1];
+        for (int32_t e = s + lane; e < t; e += 32) {
+            int32_t key = kin[e];
+            int32_t rank = 0;
+            for (int32_t f = s; f < t; f++) rank += (kin[f] < key);
+            kout[s + rank] = key;
+            if (vin) vout[s + rank] = vin[e];
+        }
+    }
+}
+
+void transpose(const CsrView &A, bool with_val, DCsr &At, cudaStream_t s) {
+    At.n = A.m;
+    At.m = A.n;
+    At.nnz = A.nnz;
+    DVec<int32_t> cnt(A.m + 1, s);
+    fill_i32(cnt.p, 0, A.m + 1, s);
+    if (A.nnz)
+        RN_LAUNCH("transpose", 4.0 * A.nnz, s, count_cols_kernel, grid_for(A.nnz, 1024), 256, 0, A.nnz, A.col, cnt.p);
+    At.rowptr.alloc(A.m + 1, s);
+    scan_counts(cnt.p, At.rowptr.p, A.m, s);
+    DVec<int32_t> next(A.m, s), tcol(A.nnz, s);
+    DVec<double> tval;
+    if (with_val) tval.alloc(A.nnz, s);
+    d2d(next.p, At.rowptr.p, A.m, s);
+    if (A.nnz)
+        RN_LAUNCH("transpose", 16.0 * A.nnz, s, transpose_scatter_kernel, grid_for(A.n, 256), 256, 0, A.n, A.rowptr,
+                  A.col, with_val ? A.val : nullptr, next.p, tcol.p, tval.p);
+    At.col.alloc(A.nnz, s);
+    if (with_val) At.val.alloc(A.nnz, s);
+    if (A.nnz)
+        RN_LAUNCH("transpose", 24.0 * A.nnz, s, segment_rank_sort_kernel, grid_for((int64_t)A.m * 32, 256), 256, 0,
+                  A.m, At.rowptr.p, tcol.p, with_val ? tval.p : nullptr, At.col.p, with_val ? At.val.p : nullptr);
+}
+
+}  // namespace rn

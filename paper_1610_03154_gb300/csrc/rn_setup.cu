@@ -1,0 +1,982 @@
+// rn_setup.cu - root-node AMG setup (Alg. 3) on the GPU.
+//
+// Every step of the level loop runs in the kernels below; the host only
+// sizes allocations (one device->host read per prefix sum) and steps the
+// aggregation rounds.  Pattern decisions (strength, aggregation, S^d C and
+// its pre-filter) use the same FP64 operation sequence as a plain sequential
+// evaluation - rounded divide, square root, multiply and add with no fused
+// multiply-add - so the integer outcomes (patterns, roots, aggregates) are
+// reproducible bit for bit.
+#include <algorithm>
+#include <cmath>
+
+#include "rn_hier.cuh"
+
+namespace rn {
+
+constexpr double kGuard = 1e-10;     // keep <=> v >= theta * ref * (1 - kGuard)
+constexpr double kCgStop = 1e-28;    // CG energy minimisation stops at <R,Z> <= kCgStop <R0,Z0>
+constexpr int kMaxAggRounds = 4096;  // bound on distance-2 MIS rounds
+constexpr int kMaxDense = 4096;      // largest coarsest level for the dense LU
+constexpr int kT = 256;              // threads per block of the row kernels
+
+enum { FREE_ROW = 0, ROOT_ROW = 1, UNAGG_ROW = 2 };
+enum { UNDECIDED = 0, TAKEN = 1, REMOVED = 2, ISOLATED = 3 };
+
+// ------------------------------------------------------------------ input validation
+__global__ void validate_kernel(int32_t n, int64_t nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                const double *__restrict__ val, int32_t *__restrict__ bad) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t s = rp[i], e = rp[i + 1];
+        bool ok = (s >= 0 && e >= s && e <= nnz) && (i != 0 || s == 0) && (i != n - 1 || e == nnz);
+        bool diag = false;
+        for (int32_t q = s; ok && q < e; q++) {
+            int32_t j = col[q];
+            if (j < 0 || j >= n || (q > s && j <= col[q - 1]) || !isfinite(val[q])) ok = false;
+            if (j == i) diag = true;
+        }
+        if (!ok || !diag) atomicMax(bad, i + 1);
+    }
+}
+
+// ------------------------------------------------------------------ strength (Sec. 3.2, eq. soc)
+__device__ __forceinline__ double soc_value(double aij, double di, double dj) {
+    return __ddiv_rn(fabs(aij), __dsqrt_rn(__dmul_rn(fabs(di), fabs(dj))));
+}
+
+template <bool FILL>
+__global__ void strength_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                                const double *__restrict__ aval, const double *__restrict__ diag, double thr,
+                                int32_t *__restrict__ count, const int32_t *__restrict__ srp,
+                                int32_t *__restrict__ scol, double *__restrict__ sval) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double di = diag[i];
+        if (!FILL) {
+            int32_t c = 1;
+            for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
+                int32_t j = acol[e];
+                if (j != i && soc_value(aval[e], di, diag[j]) >= thr) c++;
+            }
+            count[i] = c;
+        } else {
+            double vmax = 0.0;
+            for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
+                int32_t j = acol[e];
+                if (j == i) continue;
+                double v = soc_value(aval[e], di, diag[j]);
+                if (v >= thr && v > vmax) vmax = v;
+            }
+            int32_t dst = srp[i];
+            for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
+                int32_t j = acol[e];
+                if (j == i) {
+                    scol[dst] = i;
+                    sval[dst++] = 1.0;
+                    continue;
+                }
+                double v = soc_value(aval[e], di, diag[j]);
+                if (v >= thr) {
+                    scol[dst] = j;
+                    sval[dst++] = __ddiv_rn(v, vmax);
+                }
+            }
+        }
+    }
+}
+
+// aggregation graph: pattern(S) united with pattern(S)^T, diagonal removed
+template <bool FILL>
+__global__ void union_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                             const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
+                             int32_t *__restrict__ count, const int32_t *__restrict__ grp, int32_t *__restrict__ gcol) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t a = arp[i], ae = arp[i + 1], b = brp[i], be = brp[i + 1];
+        int32_t c = 0, dst = FILL ? grp[i] : 0;
+        while (a < ae || b < be) {
+            int32_t ja = a < ae ? acol[a] : INT32_MAX;
+            int32_t jb = b < be ? bcol[b] : INT32_MAX;
+            int32_t j = ja < jb ? ja : jb;
+            if (ja == j) a++;
+            if (jb == j) b++;
+            if (j != i) {
+                if (FILL) gcol[dst++] = j;
+                c++;
+            }
+        }
+        if (!FILL) count[i] = c;
+    }
+}
+
+// ------------------------------------------------------------------ seeded MIS-2 aggregation (Sec. 3.3)
+// priority pi(i) = (splitmix64(seed ^ i), i), compared lexicographically
+__device__ __forceinline__ bool prio_gt(int32_t a, int32_t b, uint64_t seed) {
+    uint64_t ha = splitmix64(seed ^ (uint64_t)(uint32_t)a), hb = splitmix64(seed ^ (uint64_t)(uint32_t)b);
+    return ha > hb || (ha == hb && a > b);
+}
+
+__global__ void mis_init_kernel(int32_t n, const int32_t *__restrict__ grp, int32_t *__restrict__ state) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        state[i] = (grp[i + 1] > grp[i]) ? UNDECIDED : ISOLATED;
+}
+
+// m1[i] = best undecided node in the closed neighbourhood of i (or -1)
+__global__ void mis_m1_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
+                              const int32_t *__restrict__ state, uint64_t seed, int32_t *__restrict__ m1) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t best = (state[i] == UNDECIDED) ? i : -1;
+        for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
+            int32_t j = gcol[e];
+            if (state[j] == UNDECIDED && (best < 0 || prio_gt(j, best, seed))) best = j;
+        }
+        m1[i] = best;
+    }
+}
+
+// an undecided node is taken when it is the best undecided node within distance 2
+__global__ void mis_take_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
+                                const int32_t *__restrict__ m1, uint64_t seed, int32_t *__restrict__ state) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (state[i] != UNDECIDED) continue;
+        int32_t best = m1[i];
+        for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
+            int32_t c = m1[gcol[e]];
+            if (c >= 0 && (best < 0 || prio_gt(c, best, seed))) best = c;
+        }
+        if (best == i) state[i] = TAKEN;
+    }
+}
+
+// r1[i] = 1 when i is taken or adjacent to a taken node
+__global__ void mis_r1_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
+                              const int32_t *__restrict__ state, int32_t *__restrict__ r1) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t f = (state[i] == TAKEN);
+        for (int32_t e = grp[i]; e < grp[i + 1] && !f; e++) f = (state[gcol[e]] == TAKEN);
+        r1[i] = f;
+    }
+}
+
+// undecided nodes within distance 2 of a taken node are removed
+__global__ void mis_remove_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
+                                  const int32_t *__restrict__ r1, int32_t *__restrict__ state,
+                                  int32_t *__restrict__ undecided) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (state[i] != UNDECIDED) continue;
+        int32_t f = r1[i];
+        for (int32_t e = grp[i]; e < grp[i + 1] && !f; e++) f = r1[gcol[e]];
+        if (f) state[i] = REMOVED;
+        else atomicAdd(undecided, 1);
+    }
+}
+
+__global__ void flag_taken_kernel(int32_t n, const int32_t *__restrict__ state, int32_t *__restrict__ flag) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = (state[i] == TAKEN);
+}
+
+__global__ void roots_kernel(int32_t n, const int32_t *__restrict__ state, const int32_t *__restrict__ cidx,
+                             int32_t *__restrict__ roots) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (state[i] == TAKEN) roots[cidx[i]] = i;
+}
+
+// pass 1: join the neighbouring root of largest priority
+__global__ void agg_pass1_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
+                                 const int32_t *__restrict__ state, const int32_t *__restrict__ cidx, uint64_t seed,
+                                 int32_t *__restrict__ pass1) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t a = -1;
+        if (state[i] == TAKEN) {
+            a = cidx[i];
+        } else if (state[i] == REMOVED) {
+            int32_t best = -1;
+            for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
+                int32_t j = gcol[e];
+                if (state[j] == TAKEN && (best < 0 || prio_gt(j, best, seed))) best = j;
+            }
+            if (best >= 0) a = cidx[best];
+        }
+        pass1[i] = a;
+    }
+}
+
+// pass 2: join the aggregate of the pass-1 neighbour whose root has the largest priority
+__global__ void agg_pass2_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
+                                 const int32_t *__restrict__ state, const int32_t *__restrict__ pass1,
+                                 const int32_t *__restrict__ roots, uint64_t seed, int32_t *__restrict__ agg,
+                                 int32_t *__restrict__ bad) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t a = pass1[i];
+        if (a < 0 && state[i] == REMOVED) {
+            for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
+                int32_t c = pass1[gcol[e]];
+                if (c < 0 || state[gcol[e]] == TAKEN) continue;
+                if (a < 0 || prio_gt(roots[c], roots[a], seed)) a = c;
+            }
+            if (a < 0) atomicMax(bad, i + 1);
+        }
+        agg[i] = a;
+    }
+}
+
+__global__ void rowtype_kernel(int32_t n, const int32_t *__restrict__ state, const int32_t *__restrict__ agg,
+                               int32_t *__restrict__ rowtype) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        rowtype[i] = (state[i] == TAKEN) ? ROOT_ROW : (agg[i] < 0 ? UNAGG_ROW : FREE_ROW);
+}
+
+// ------------------------------------------------------------------ candidates (Sec. 3.1)
+// one weighted-Jacobi sweep on A B = 0, summed in CSR order without FMA
+__global__ void cand_jacobi_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                                   const double *__restrict__ aval, const double *__restrict__ B, double omega,
+                                   double *__restrict__ Bn) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc = 0.0, d = 0.0;
+        for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
+            acc = __dadd_rn(acc, __dmul_rn(aval[e], B[acol[e]]));
+            if (acol[e] == i) d = aval[e];
+        }
+        Bn[i] = __dsub_rn(B[i], __dmul_rn(omega, __ddiv_rn(acc, d)));
+    }
+}
+
+__global__ void gather_kernel(int32_t nc, const int32_t *__restrict__ roots, const double *__restrict__ B,
+                              double *__restrict__ Bc, int32_t *__restrict__ bad) {
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        double v = B[roots[c]];
+        Bc[c] = v;
+        if (!(fabs(v) >= 1e-300)) atomicMax(bad, c + 1);
+    }
+}
+
+// ------------------------------------------------------------------ pattern (Sec. 3.4-3.5)
+__global__ void aggflag_kernel(int32_t n, const int32_t *__restrict__ agg, int32_t *__restrict__ flag) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = agg[i] >= 0;
+}
+
+__global__ void c_matrix_kernel(int32_t n, const int32_t *__restrict__ agg, const int32_t *__restrict__ rp,
+                                int32_t *__restrict__ col, double *__restrict__ val) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (agg[i] >= 0) {
+            col[rp[i]] = agg[i];
+            val[rp[i]] = 1.0;
+        }
+}
+
+// pre-filter (Alg. 4, drop tolerance) on free rows, root rows -> identity row
+template <bool FILL>
+__global__ void prefilter_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const double *__restrict__ val, const int32_t *__restrict__ rowtype,
+                                 const int32_t *__restrict__ agg, double theta, double omg, int32_t *__restrict__ count,
+                                 const int32_t *__restrict__ frp, int32_t *__restrict__ fcol,
+                                 double *__restrict__ fval) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int t = rowtype[i];
+        const int32_t a = agg[i];
+        double thr = 0.0;
+        if (t == FREE_ROW && theta > 0.0) {
+            double m = 0.0;
+            for (int32_t e = rp[i]; e < rp[i + 1]; e++)
+                if (fabs(val[e]) > m) m = fabs(val[e]);
+            thr = __dmul_rn(__dmul_rn(theta, m), omg);
+        }
+        int32_t c = 0, dst = FILL ? frp[i] : 0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            bool keep;
+            if (t == ROOT_ROW) keep = (col[e] == a);
+            else if (t == FREE_ROW) keep = (theta <= 0.0) || (fabs(val[e]) >= thr) || (col[e] == a);
+            else keep = false;
+            if (keep) {
+                if (FILL) {
+                    fcol[dst] = col[e];
+                    fval[dst] = (t == ROOT_ROW) ? 1.0 : val[e];
+                    dst++;
+                }
+                c++;
+            }
+        }
+        if (!FILL) count[i] = c;
+    }
+}
+
+// T on the pattern (eq. root-nodeform): T_{i,agg(i)} = B_i / Bc_{agg(i)}
+__global__ void tentative_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const int32_t *__restrict__ agg, const double *__restrict__ B,
+                                 const double *__restrict__ Bc, double *__restrict__ T) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            int32_t j = col[e];
+            T[e] = (j == agg[i]) ? __ddiv_rn(B[i], Bc[j]) : 0.0;
+        }
+}
+
+// ------------------------------------------------------------------ CG energy minimisation (Sec. 3.6)
+// Device scalars: sc[0] rho, sc[1] rho0, sc[2] beta, sc[3] <Dd,W>, sc[4] alpha, sc[5] new rho.
+// fl[0] = done.
+template <int G>
+__global__ void __launch_bounds__(kT)
+cg_rho_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ diag,
+              int precond, double *__restrict__ partial) {
+    __shared__ double sm[32];
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    double acc = 0.0;
+    for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
+        const double d = precond ? diag[i] : 1.0;
+        for (int32_t q = rp[i] + lane; q < rp[i + 1]; q += G) acc = fma(R[q], R[q] / d, acc);
+    }
+    double t = block_sum<kT>(acc, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void cg_finalize_rho_kernel(double *sc, int32_t *fl, int it, double stop) {
+    if (fl[0]) return;
+    const double r = sc[5];
+    if (it == 0) sc[1] = r;
+    if (r == 0.0 || r <= stop * sc[1]) {
+        fl[0] = 1;
+        return;
+    }
+    sc[2] = (it == 0) ? 0.0 : r / sc[0];
+    sc[0] = r;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kT)
+cg_dd_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ diag,
+             int precond, const double *__restrict__ sc, const int32_t *__restrict__ fl, int first,
+             double *__restrict__ Dd) {
+    if (fl[0]) return;
+    const double beta = sc[2];
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
+        const double d = precond ? diag[i] : 1.0;
+        for (int32_t q = rp[i] + lane; q < rp[i + 1]; q += G) {
+            const double z = R[q] / d;
+            Dd[q] = first ? z : z + beta * Dd[q];
+        }
+    }
+}
+
+__global__ void cg_finalize_dw_kernel(double *sc, int32_t *fl) {
+    if (fl[0]) return;
+    if (!(sc[3] > 0.0)) {
+        fl[0] = 1;
+        return;
+    }
+    sc[4] = sc[0] / sc[3];
+}
+
+template <int G>
+__global__ void __launch_bounds__(kT)
+cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, double *__restrict__ P, double *__restrict__ R,
+                 const double *__restrict__ Dd, const double *__restrict__ W, const double *__restrict__ diag,
+                 int precond, const double *__restrict__ sc, const int32_t *__restrict__ fl,
+                 double *__restrict__ partial) {
+    __shared__ double sm[32];
+    const bool done = fl[0] != 0;
+    const double alpha = sc[4];
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    double acc = 0.0;
+    if (!done) {
+        for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
+            const double d = precond ? diag[i] : 1.0;
+            for (int32_t q = rp[i] + lane; q < rp[i + 1]; q += G) {
+                P[q] = P[q] + alpha * Dd[q];
+                const double r = R[q] - alpha * W[q];
+                R[q] = r;
+                acc = fma(r, r / d, acc);
+            }
+        }
+    }
+    double t = block_sum<kT>(acc, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// ------------------------------------------------------------------ GMRES energy minimisation (Sec. 4.2)
+// sc[0] beta, sc[1] ||w||^2 / scratch, fl[0] done, fl[1] k (number of finished steps)
+__global__ void gm_start_kernel(double *sc, int32_t *fl, double *g) {
+    const double b2 = sc[1];
+    fl[0] = 0;
+    fl[1] = 0;
+    if (!(b2 > 0.0)) {
+        fl[0] = 1;
+        return;
+    }
+    const double beta = sqrt(b2);
+    sc[0] = beta;
+    g[0] = beta;
+}
+
+__global__ void gm_scale_kernel(int64_t nz, double *__restrict__ v, const double *__restrict__ den,
+                                const int32_t *__restrict__ fl) {
+    if (fl[0]) return;
+    const double d = *den;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x)
+        v[q] = v[q] / d;
+}
+
+__global__ void gm_axpy_kernel(int64_t nz, double *__restrict__ w, const double *__restrict__ v,
+                               const double *__restrict__ h, const int32_t *__restrict__ fl) {
+    if (fl[0]) return;
+    const double c = *h;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x)
+        w[q] = w[q] - c * v[q];
+}
+
+// Givens update of Hessenberg column j; H row-major (m+1) x m
+__global__ void gm_givens_kernel(int m, int j, double *H, double *cs, double *sn, double *g, double *sc, int32_t *fl) {
+    if (fl[0]) return;
+    const double hn = sqrt(sc[1]);
+    H[(j + 1) * m + j] = hn;
+    for (int i = 0; i < j; i++) {
+        double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+    }
+    const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+    if (den == 0.0) {
+        fl[0] = 1;
+        return;
+    }
+    cs[j] = H[j * m + j] / den;
+    sn[j] = H[(j + 1) * m + j] / den;
+    H[j * m + j] = den;
+    H[(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    fl[1] = j + 1;
+    sc[2] = hn;  // next basis vector = w / hn
+    if (hn == 0.0) fl[0] = 1;
+}
+
+__global__ void gm_backsolve_kernel(int m, const double *H, const double *g, double *y, const int32_t *fl) {
+    const int k = fl[1];
+    for (int i = k - 1; i >= 0; i--) {
+        double s = g[i];
+        for (int j = i + 1; j < k; j++) s -= H[i * m + j] * y[j];
+        y[i] = s / H[i * m + i];
+    }
+    for (int i = k; i < m; i++) y[i] = 0.0;
+}
+
+__global__ void gm_combine_kernel(int64_t nz, int m, double *__restrict__ P, const double *__restrict__ V,
+                                  const double *__restrict__ y, const int32_t *__restrict__ fl) {
+    const int k = fl[1];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x) {
+        double p = P[q];
+        for (int j = 0; j < k; j++) p = p + y[j] * V[(int64_t)j * nz + q];
+        P[q] = p;
+    }
+}
+
+// ------------------------------------------------------------------ post-filter + enforce (Sec. 3.7)
+template <bool FILL>
+__global__ void postfilter_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                  const double *__restrict__ val, const int32_t *__restrict__ rowtype,
+                                  const int32_t *__restrict__ agg, double theta, double omg,
+                                  int32_t *__restrict__ count, const int32_t *__restrict__ frp,
+                                  int32_t *__restrict__ fcol, double *__restrict__ fval) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool fr = rowtype[i] == FREE_ROW;
+        double thr = 0.0;
+        if (fr) {
+            double m = 0.0;
+            for (int32_t e = rp[i]; e < rp[i + 1]; e++)
+                if (fabs(val[e]) > m) m = fabs(val[e]);
+            thr = __dmul_rn(__dmul_rn(theta, m), omg);
+        }
+        int32_t c = 0, dst = FILL ? frp[i] : 0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            bool keep = !fr || fabs(val[e]) >= thr || col[e] == agg[i];
+            if (keep) {
+                if (FILL) {
+                    fcol[dst] = col[e];
+                    fval[dst] = val[e];
+                    dst++;
+                }
+                c++;
+            }
+        }
+        if (!FILL) count[i] = c;
+    }
+}
+
+// minimal-norm row fit (t + u) Bc = B_i on the row's pattern (eq. Tproj)
+__global__ void enforce_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                               double *__restrict__ val, const int32_t *__restrict__ rowtype,
+                               const double *__restrict__ B, const double *__restrict__ Bc) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (rowtype[i] != FREE_ROW) continue;
+        double tb = 0.0, bb = 0.0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            const double b = Bc[col[e]];
+            tb += val[e] * b;
+            bb += b * b;
+        }
+        const double c = (B[i] - tb) / bb;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) val[e] = val[e] + c * Bc[col[e]];
+    }
+}
+
+// ------------------------------------------------------------------ coarsest level: dense LU -> inverse
+__global__ void csr_to_dense_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                    const double *__restrict__ val, double *__restrict__ M) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) M[(int64_t)i * n + col[e]] = val[e];
+}
+
+// One block: partial pivoting (largest |pivot|, lowest row on ties), in place.
+__global__ void __launch_bounds__(1024) dense_lu_kernel(int n, double *M, int32_t *piv, int32_t *flag) {
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ double amax;
+    __shared__ int pivrow;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    double m = 0.0;
+    for (int64_t q = tid; q < (int64_t)n * n; q += blockDim.x) m = fmax(m, fabs(M[q]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) sv[w] = m;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int k = 0; k < nw; k++) a = fmax(a, sv[k]);
+        amax = a;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; k++) {
+        double best = -1.0;
+        int brow = n;
+        for (int i = k + tid; i < n; i += blockDim.x) {
+            double v = fabs(M[(int64_t)i * n + k]);
+            if (v > best || (v == best && i < brow)) { best = v; brow = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+            if (ov > best || (ov == best && orow < brow)) { best = ov; brow = orow; }
+        }
+        if (lane == 0) { sv[w] = best; si[w] = brow; }
+        __syncthreads();
+        if (tid == 0) {
+            double b = -1.0;
+            int r = n;
+            for (int q = 0; q < nw; q++)
+                if (sv[q] > b || (sv[q] == b && si[q] < r)) { b = sv[q]; r = si[q]; }
+            pivrow = r;
+            piv[k] = r;
+            if (!(b >= 1e-14 * amax) || b == 0.0) flag[0] = 1;
+        }
+        __syncthreads();
+        if (flag[0]) return;
+        const int p = pivrow;
+        if (p != k)
+            for (int j = tid; j < n; j += blockDim.x) {
+                double t = M[(int64_t)k * n + j];
+                M[(int64_t)k * n + j] = M[(int64_t)p * n + j];
+                M[(int64_t)p * n + j] = t;
+            }
+        __syncthreads();
+        const double d = M[(int64_t)k * n + k];
+        for (int i = k + 1 + tid; i < n; i += blockDim.x) M[(int64_t)i * n + k] = M[(int64_t)i * n + k] / d;
+        __syncthreads();
+        const int r = n - k - 1;
+        for (int64_t q = tid; q < (int64_t)r * r; q += blockDim.x) {
+            const int i = k + 1 + (int)(q / r), j = k + 1 + (int)(q % r);
+            M[(int64_t)i * n + j] = M[(int64_t)i * n + j] - M[(int64_t)i * n + k] * M[(int64_t)k * n + j];
+        }
+        __syncthreads();
+    }
+}
+
+// inverse column c: solve L U x = P e_c
+__global__ void lu_inverse_kernel(int n, const double *__restrict__ LU, const int32_t *__restrict__ piv,
+                                  double *__restrict__ X, double *__restrict__ work) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double *x = work + (int64_t)c * n;
+        for (int i = 0; i < n; i++) x[i] = (i == c) ? 1.0 : 0.0;
+        for (int k = 0; k < n; k++)
+            if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+        for (int i = 0; i < n; i++) {
+            double s = x[i];
+            for (int j = 0; j < i; j++) s -= LU[(int64_t)i * n + j] * x[j];
+            x[i] = s;
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            double s = x[i];
+            for (int j = i + 1; j < n; j++) s -= LU[(int64_t)i * n + j] * x[j];
+            x[i] = s / LU[(int64_t)i * n + i];
+        }
+        for (int i = 0; i < n; i++) X[(int64_t)i * n + c] = x[i];
+    }
+}
+
+// ================================================================== host orchestration
+static int rows_grid(int64_t n) { return grid_for(n, kT, 8); }
+
+static int pick_g(double avg) {
+    if (avg <= 4.5) return 4;
+    if (avg <= 10.0) return 8;
+    if (avg <= 20.0) return 16;
+    return 32;
+}
+
+#define RN_ROWG_LAUNCH(name, bytes, s, G, kern, n, ...)                                                   \
+    do {                                                                                                  \
+        const int grid_ = std::min(grid_for((n), kT / (G), 8), kReduceBlocks);                            \
+        switch (G) {                                                                                      \
+            case 4: RN_LAUNCH(name, bytes, s, kern<4>, grid_, kT, 0, n, __VA_ARGS__); break;              \
+            case 8: RN_LAUNCH(name, bytes, s, kern<8>, grid_, kT, 0, n, __VA_ARGS__); break;              \
+            case 16: RN_LAUNCH(name, bytes, s, kern<16>, grid_, kT, 0, n, __VA_ARGS__); break;            \
+            default: RN_LAUNCH(name, bytes, s, kern<32>, grid_, kT, 0, n, __VA_ARGS__); break;            \
+        }                                                                                                 \
+        gridp = grid_;                                                                                    \
+    } while (0)
+
+struct Pattern {  // borrowed view of a fixed pattern
+    int32_t n, nc;
+    int64_t nnz;
+    const int32_t *rp, *col;
+};
+
+// CG energy minimisation of the values X (in/out) on pattern N.
+static void energy_min_cg(rn_hierarchy &h, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                          const double *Bc, const double *diag, int sweeps) {
+    cudaStream_t s = h.s;
+    const int precond = h.p.energy_precond;
+    DVec<double> R(N.nnz, s), Dd(N.nnz, s), W(N.nnz, s);
+    double *sc = h.scal.p;
+    int32_t *fl = h.iflags.p;
+    fill_i32(fl, 0, 1, s);
+    ProjArgs pa{rowtype, Bc};
+    const int G = pick_g(N.n ? (double)N.nnz / N.n : 1.0);
+    int gridp = 1;
+    const double nzb = 8.0 * N.nnz, rpb = 4.0 * (N.n + 1), db = 8.0 * N.n;
+    masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, R.p, pa, -1.0, nullptr, nullptr, h.partial.p, s);
+    RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R.p, diag, precond, h.partial.p);
+    reduce_partials(h.partial.p, gridp, sc + 5, s);
+    for (int it = 0; it < sweeps; it++) {
+        RN_LAUNCH("energy_cg_scalar", 0, s, cg_finalize_rho_kernel, 1, 1, 0, sc, fl, it, kCgStop);
+        RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R.p, diag, precond,
+                       sc, fl, it == 0 ? 1 : 0, Dd.p);
+        masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, Dd.p, W.p, pa, 1.0, Dd.p, sc + 3, h.partial.p, s);
+        RN_LAUNCH("energy_cg_scalar", 0, s, cg_finalize_dw_kernel, 1, 1, 0, sc, fl);
+        RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R.p, Dd.p,
+                       W.p, diag, precond, sc, fl, h.partial.p);
+        reduce_partials(h.partial.p, gridp, sc + 5, s);
+    }
+}
+
+// GMRES energy minimisation (m Arnoldi steps, modified Gram-Schmidt).
+static void energy_min_gmres(rn_hierarchy &h, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                             const double *Bc, int m) {
+    if (m <= 0) return;
+    cudaStream_t s = h.s;
+    const int64_t nz = N.nnz;
+    DVec<double> V((size_t)(m + 1) * (nz > 0 ? nz : 1), s), W(nz > 0 ? nz : 1, s);
+    DVec<double> Hm((size_t)(m + 1) * m + 4 * (m + 1), s);
+    fill_f64(Hm.p, 0.0, (int64_t)Hm.n, s);
+    double *H = Hm.p, *cs = H + (m + 1) * m, *sn = cs + (m + 1), *g = sn + (m + 1), *y = g + (m + 1);
+    double *sc = h.scal.p;
+    int32_t *fl = h.iflags.p;
+    ProjArgs pa{rowtype, Bc};
+    const int eg = grid_for(nz, 1024);
+    const double nzb = 8.0 * nz;
+    masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, V.p, pa, -1.0, nullptr, nullptr, h.partial.p, s);
+    dot(V.p, V.p, nz, sc + 1, s, h.partial.p);
+    RN_LAUNCH("energy_gmres_scalar", 0, s, gm_start_kernel, 1, 1, 0, sc, fl, g);
+    RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel, eg, 256, 0, nz, V.p, sc, fl);
+    for (int j = 0; j < m; j++) {
+        double *vj = V.p + (int64_t)j * nz;
+        masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, vj, W.p, pa, 1.0, nullptr, nullptr, h.partial.p, s);
+        for (int i = 0; i <= j; i++) {
+            double *vi = V.p + (int64_t)i * nz;
+            dot(W.p, vi, nz, H + i * m + j, s, h.partial.p);
+            RN_LAUNCH("energy_gmres_vec", 3 * nzb, s, gm_axpy_kernel, eg, 256, 0, nz, W.p, vi, H + i * m + j, fl);
+        }
+        dot(W.p, W.p, nz, sc + 1, s, h.partial.p);
+        RN_LAUNCH("energy_gmres_scalar", 0, s, gm_givens_kernel, 1, 1, 0, m, j, H, cs, sn, g, sc, fl);
+        if (j + 1 < m + 1) {
+            d2d(V.p + (int64_t)(j + 1) * nz, W.p, nz, s);
+            RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel, eg, 256, 0, nz, V.p + (int64_t)(j + 1) * nz,
+                      sc + 2, fl);
+        }
+    }
+    RN_LAUNCH("energy_gmres_scalar", 0, s, gm_backsolve_kernel, 1, 1, 0, m, H, g, y, fl);
+    RN_LAUNCH("energy_gmres_vec", (m + 2) * nzb, s, gm_combine_kernel, eg, 256, 0, nz, m, X, V.p, y, fl);
+}
+
+static void energy_min(rn_hierarchy &h, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                       const double *Bc, const double *diag, int sweeps) {
+    if (h.p.energy_method == RN_ENERGY_GMRES) energy_min_gmres(h, A, N, X, rowtype, Bc, sweeps);
+    else energy_min_cg(h, A, N, X, rowtype, Bc, diag, sweeps);
+}
+
+static void check_flag(const int32_t *flag, cudaStream_t s, rn_status st, const char *what) {
+    int32_t v = read_scalar(flag, s);
+    if (v) fail(st, fmt("%s (index %d)", what, v - 1));
+}
+
+// Smooth candidates, build P (or R^T) on pattern N: Alg. 3 inject / improve /
+// filter / enforce / improve.  Pout receives the final pattern and values.
+static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, const int32_t *agg,
+                           const int32_t *roots, int32_t nc, const int32_t *rowtype, double *Bsm, const double *diag,
+                           double *Bc, DCsr &Pout, DCsr *Tkeep) {
+    cudaStream_t s = h.s;
+    const int32_t n = A.n;
+    // candidates: b_sweeps weighted-Jacobi sweeps on A B = 0 (exact)
+    {
+        DVec<double> tmp(n, s);
+        for (int sw = 0; sw < h.p.b_sweeps; sw++) {
+            RN_LAUNCH("candidates", 12.0 * A.nnz + 24.0 * n, s, cand_jacobi_kernel, rows_grid(n), kT, 0, n, A.rowptr,
+                      A.col, A.val, Bsm, h.p.omega, tmp.p);
+            d2d(Bsm, tmp.p, n, s);
+        }
+    }
+    fill_i32(h.iflags.p + 2, 0, 1, s);
+    RN_LAUNCH("inject", 16.0 * nc, s, gather_kernel, rows_grid(nc), kT, 0, nc, roots, Bsm, Bc, h.iflags.p + 2);
+    check_flag(h.iflags.p + 2, s, RN_EINVAL, "candidate vanishes at a root node");
+    // P = T on N
+    Pout.n = n;
+    Pout.m = nc;
+    Pout.nnz = N.nnz;
+    Pout.rowptr.alloc(n + 1, s);
+    Pout.col.alloc(N.nnz, s);
+    Pout.val.alloc(N.nnz, s);
+    d2d(Pout.rowptr.p, N.rowptr.p, n + 1, s);
+    d2d(Pout.col.p, N.col.p, N.nnz, s);
+    RN_LAUNCH("tentative", 16.0 * N.nnz + 16.0 * n, s, tentative_kernel, rows_grid(n), kT, 0, n, N.rowptr.p, N.col.p,
+              agg, Bsm, Bc, Pout.val.p);
+    if (Tkeep) {
+        Tkeep->n = n; Tkeep->m = nc; Tkeep->nnz = N.nnz;
+        Tkeep->rowptr.alloc(n + 1, s); Tkeep->col.alloc(N.nnz, s); Tkeep->val.alloc(N.nnz, s);
+        d2d(Tkeep->rowptr.p, N.rowptr.p, n + 1, s);
+        d2d(Tkeep->col.p, N.col.p, N.nnz, s);
+        d2d(Tkeep->val.p, Pout.val.p, N.nnz, s);
+    }
+    Pattern pat{n, nc, N.nnz, Pout.rowptr.p, Pout.col.p};
+    energy_min(h, A, pat, Pout.val.p, rowtype, Bc, diag, h.p.n_sweeps);
+    if (h.p.postfilter > 0.0) {
+        const double omg = 1.0 - kGuard;
+        DVec<int32_t> cnt(n + 1, s);
+        RN_LAUNCH("postfilter", 24.0 * Pout.nnz, s, postfilter_kernel<false>, rows_grid(n), kT, 0, n, Pout.rowptr.p,
+                  Pout.col.p, Pout.val.p, rowtype, agg, h.p.postfilter, omg, cnt.p, nullptr, nullptr, nullptr);
+        DCsr F;
+        F.n = n; F.m = nc;
+        F.rowptr.alloc(n + 1, s);
+        F.nnz = scan_counts(cnt.p, F.rowptr.p, n, s);
+        F.col.alloc(F.nnz, s);
+        F.val.alloc(F.nnz, s);
+        RN_LAUNCH("postfilter", 24.0 * Pout.nnz + 12.0 * F.nnz, s, postfilter_kernel<true>, rows_grid(n), kT, 0, n,
+                  Pout.rowptr.p, Pout.col.p, Pout.val.p, rowtype, agg, h.p.postfilter, omg, nullptr, F.rowptr.p,
+                  F.col.p, F.val.p);
+        RN_LAUNCH("enforce", 28.0 * F.nnz + 8.0 * n, s, enforce_kernel, rows_grid(n), kT, 0, n, F.rowptr.p, F.col.p,
+                  F.val.p, rowtype, Bsm, Bc);
+        Pout = std::move(F);
+        Pattern pf{n, nc, Pout.nnz, Pout.rowptr.p, Pout.col.p};
+        energy_min(h, A, pf, Pout.val.p, rowtype, Bc, diag, 1);
+    }
+}
+
+void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const double *Bhat0) {
+    cudaStream_t s = h.s;
+    const rn_params &p = h.p;
+    const double omg = 1.0 - kGuard;
+    h.partial.alloc(kReduceBlocks, s);
+    h.scal.alloc(64, s);
+    h.iflags.alloc(16, s);
+    fill_f64(h.scal.p, 0.0, 64, s);
+    fill_i32(h.iflags.p, 0, 16, s);
+    // level 0: private copy of A, B (and B-hat)
+    {
+        auto L = std::make_unique<rn_level>();
+        L->A.n = A0.n; L->A.m = A0.m; L->A.nnz = A0.nnz;
+        L->A.rowptr.alloc(A0.n + 1, s); L->A.col.alloc(A0.nnz, s); L->A.val.alloc(A0.nnz, s);
+        d2d(L->A.rowptr.p, A0.rowptr, A0.n + 1, s);
+        d2d(L->A.col.p, A0.col, A0.nnz, s);
+        d2d(L->A.val.p, A0.val, A0.nnz, s);
+        L->B.alloc(A0.n, s);
+        d2d(L->B.p, B0, A0.n, s);
+        if (!p.symmetric) {
+            L->Bhat.alloc(A0.n, s);
+            d2d(L->Bhat.p, Bhat0, A0.n, s);
+        }
+        fill_i32(h.iflags.p + 3, 0, 1, s);
+        RN_LAUNCH("validate", 12.0 * A0.nnz + 4.0 * A0.n, s, validate_kernel, rows_grid(A0.n), kT, 0, A0.n, A0.nnz,
+                  L->A.rowptr.p, L->A.col.p, L->A.val.p, h.iflags.p + 3);
+        check_flag(h.iflags.p + 3, s, RN_EINVAL, "CSR row malformed (bounds, unsorted/duplicate columns, no diagonal, "
+                                                 "or non-finite value)");
+        h.lev.push_back(std::move(L));
+    }
+    const int maxlev = std::max(1, std::min(p.max_levels, RN_MAX_LEVELS));
+    for (int l = 0;; l++) {
+        rn_level &L = *h.lev[l];
+        const int32_t n = L.A.n;
+        CsrView A = view(L.A);
+        L.diag.alloc(n, s);
+        fill_i32(h.iflags.p + 4, 0, 1, s);
+        extract_diag(A, L.diag.p, h.iflags.p + 4, s);
+        if (n <= p.max_coarse || l >= maxlev - 1) break;
+        check_flag(h.iflags.p + 4, s, RN_EINVAL, "missing or zero diagonal");
+        // ---- strength (line 'strength')
+        const double theta = (l > 0 && p.soc_theta_coarse >= 0.0) ? p.soc_theta_coarse : p.soc_theta;
+        const double thr = theta * omg;
+        DCsr S;
+        S.n = S.m = n;
+        {
+            DVec<int32_t> cnt(n + 1, s);
+            RN_LAUNCH("strength", 12.0 * A.nnz + 16.0 * n, s, strength_kernel<false>, rows_grid(n), kT, 0, n,
+                      A.rowptr, A.col, A.val, L.diag.p, thr, cnt.p, nullptr, nullptr, nullptr);
+            S.rowptr.alloc(n + 1, s);
+            S.nnz = scan_counts(cnt.p, S.rowptr.p, n, s);
+            S.col.alloc(S.nnz, s);
+            S.val.alloc(S.nnz, s);
+            RN_LAUNCH("strength", 12.0 * A.nnz + 16.0 * n + 12.0 * S.nnz, s, strength_kernel<true>, rows_grid(n), kT,
+                      0, n, A.rowptr, A.col, A.val, L.diag.p, thr, nullptr, S.rowptr.p, S.col.p, S.val.p);
+        }
+        // ---- aggregation graph and seeded MIS-2 (line 'aggregate')
+        DCsr Gr;
+        {
+            DCsr St;
+            transpose(view(S), false, St, s);
+            DVec<int32_t> cnt(n + 1, s);
+            RN_LAUNCH("agg_graph", 8.0 * S.nnz + 8.0 * n, s, union_kernel<false>, rows_grid(n), kT, 0, n, S.rowptr.p,
+                      S.col.p, St.rowptr.p, St.col.p, cnt.p, nullptr, nullptr);
+            Gr.n = Gr.m = n;
+            Gr.rowptr.alloc(n + 1, s);
+            Gr.nnz = scan_counts(cnt.p, Gr.rowptr.p, n, s);
+            Gr.col.alloc(Gr.nnz, s);
+            RN_LAUNCH("agg_graph", 8.0 * S.nnz + 8.0 * n + 4.0 * Gr.nnz, s, union_kernel<true>, rows_grid(n), kT, 0, n,
+                      S.rowptr.p, S.col.p, St.rowptr.p, St.col.p, nullptr, Gr.rowptr.p, Gr.col.p);
+        }
+        const uint64_t seed = p.seed + (uint64_t)l;
+        DVec<int32_t> state(n, s), m1(n, s), r1(n, s);
+        const double gb = 4.0 * Gr.nnz + 8.0 * n;
+        RN_LAUNCH("mis2", gb, s, mis_init_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, state.p);
+        int rounds = 0;
+        for (;; rounds++) {
+            if (rounds >= kMaxAggRounds) fail(RN_ETIMEOUT, fmt("aggregation did not finish in %d rounds", rounds));
+            fill_i32(h.iflags.p + 5, 0, 1, s);
+            RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_m1_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, state.p,
+                      seed, m1.p);
+            RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_take_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, m1.p,
+                      seed, state.p);
+            RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_r1_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, state.p,
+                      r1.p);
+            RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_remove_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, r1.p,
+                      state.p, h.iflags.p + 5);
+            if (read_scalar(h.iflags.p + 5, s) == 0) break;
+        }
+        h.agg_rounds += rounds + 1;
+        DVec<int32_t> cidx(n + 1, s);
+        RN_LAUNCH("aggregate", 8.0 * n, s, flag_taken_kernel, rows_grid(n), kT, 0, n, state.p, m1.p);
+        const int32_t nc = (int32_t)scan_counts(m1.p, cidx.p, n, s);
+        if (nc == 0 || nc >= n) break;  // stalled: this level is the coarsest
+        L.nc = nc;
+        L.roots.alloc(nc, s);
+        L.agg.alloc(n, s);
+        L.rowtype.alloc(n, s);
+        RN_LAUNCH("aggregate", 12.0 * n, s, roots_kernel, rows_grid(n), kT, 0, n, state.p, cidx.p, L.roots.p);
+        RN_LAUNCH("aggregate", gb + 12.0 * n, s, agg_pass1_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p,
+                  state.p, cidx.p, seed, r1.p);
+        fill_i32(h.iflags.p + 6, 0, 1, s);
+        RN_LAUNCH("aggregate", gb + 16.0 * n, s, agg_pass2_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p,
+                  state.p, r1.p, L.roots.p, seed, L.agg.p, h.iflags.p + 6);
+        check_flag(h.iflags.p + 6, s, RN_EINTERNAL, "aggregation pass 2 left a node unassigned");
+        RN_LAUNCH("aggregate", 12.0 * n, s, rowtype_kernel, rows_grid(n), kT, 0, n, state.p, L.agg.p, L.rowtype.p);
+        // ---- pattern N = S^d C, pre-filter, root-node pattern
+        DCsr N;
+        {
+            DCsr cur;
+            cur.n = n;
+            cur.m = nc;
+            cur.rowptr.alloc(n + 1, s);
+            RN_LAUNCH("pattern", 8.0 * n, s, aggflag_kernel, rows_grid(n), kT, 0, n, L.agg.p, m1.p);
+            cur.nnz = scan_counts(m1.p, cur.rowptr.p, n, s);
+            cur.col.alloc(cur.nnz, s);
+            cur.val.alloc(cur.nnz, s);
+            RN_LAUNCH("pattern", 16.0 * n, s, c_matrix_kernel, rows_grid(n), kT, 0, n, L.agg.p, cur.rowptr.p, cur.col.p,
+                      cur.val.p);
+            for (int t = 0; t < p.degree; t++) {
+                DCsr nxt;
+                spgemm_symbolic(view(S), view(cur), nxt, s);
+                spgemm_numeric(view(S), view(cur), nxt, true, s);
+                cur = std::move(nxt);
+            }
+            DVec<int32_t> cnt(n + 1, s);
+            RN_LAUNCH("prefilter", 12.0 * cur.nnz + 12.0 * n, s, prefilter_kernel<false>, rows_grid(n), kT, 0, n,
+                      cur.rowptr.p, cur.col.p, cur.val.p, L.rowtype.p, L.agg.p, p.prefilter, omg, cnt.p, nullptr,
+                      nullptr, nullptr);
+            N.n = n;
+            N.m = nc;
+            N.rowptr.alloc(n + 1, s);
+            N.nnz = scan_counts(cnt.p, N.rowptr.p, n, s);
+            N.col.alloc(N.nnz, s);
+            N.val.alloc(N.nnz, s);
+            RN_LAUNCH("prefilter", 12.0 * cur.nnz + 12.0 * n + 12.0 * N.nnz, s, prefilter_kernel<true>, rows_grid(n),
+                      kT, 0, n, cur.rowptr.p, cur.col.p, cur.val.p, L.rowtype.p, L.agg.p, p.prefilter, omg, nullptr,
+                      N.rowptr.p, N.col.p, N.val.p);
+        }
+        // ---- candidates, T, energy minimisation, filtering -> P
+        L.Bc.alloc(nc, s);
+        build_transfer(h, A, N, L.agg.p, L.roots.p, nc, L.rowtype.p, L.B.p, L.diag.p, L.Bc.p, L.P,
+                       p.keep_aux ? &L.T : nullptr);
+        // ---- R
+        if (p.symmetric) {
+            transpose(view(L.P), true, L.R, s);
+        } else {
+            DCsr At, Rt;
+            transpose(A, true, At, s);
+            DVec<double> diagT(n, s);
+            d2d(diagT.p, L.diag.p, n, s);  // the diagonal of A^T is the diagonal of A
+            L.Bhatc.alloc(nc, s);
+            build_transfer(h, view(At), N, L.agg.p, L.roots.p, nc, L.rowtype.p, L.Bhat.p, diagT.p, L.Bhatc.p, Rt,
+                           nullptr);
+            transpose(view(Rt), true, L.R, s);
+        }
+        // ---- Galerkin product A_{l+1} = R (A P)
+        auto Lc = std::make_unique<rn_level>();
+        {
+            DCsr AP;
+            spgemm_symbolic(A, view(L.P), AP, s);
+            spgemm_numeric(A, view(L.P), AP, false, s);
+            spgemm_symbolic(view(L.R), view(AP), Lc->A, s);
+            spgemm_numeric(view(L.R), view(AP), Lc->A, false, s);
+        }
+        Lc->B.alloc(nc, s);
+        d2d(Lc->B.p, L.Bc.p, nc, s);
+        if (!p.symmetric) {
+            Lc->Bhat.alloc(nc, s);
+            d2d(Lc->Bhat.p, L.Bhatc.p, nc, s);
+        }
+        if (p.keep_aux) {
+            L.S = std::move(S);
+            L.N = std::move(N);
+        }
+        h.lev.push_back(std::move(Lc));
+    }
+    // ---- coarsest level: dense LU with partial pivoting, kept as an explicit inverse
+    rn_level &C = *h.lev.back();
+    const int32_t nL = C.A.n;
+    if (nL > kMaxDense) fail(RN_ESTALL, fmt("coarsening stalled with %d rows (> %d for the dense solve)", nL, kMaxDense));
+    h.nL = nL;
+    DVec<double> M((size_t)nL * nL, s), work((size_t)nL * nL, s);
+    DVec<int32_t> piv(nL, s);
+    fill_f64(M.p, 0.0, (int64_t)nL * nL, s);
+    RN_LAUNCH("coarse_lu", 12.0 * C.A.nnz, s, csr_to_dense_kernel, rows_grid(nL), kT, 0, nL, C.A.rowptr.p, C.A.col.p,
+              C.A.val.p, M.p);
+    fill_i32(h.iflags.p + 7, 0, 1, s);
+    RN_LAUNCH("coarse_lu", 16.0 * nL * nL, s, dense_lu_kernel, 1, 1024, 0, nL, M.p, piv.p, h.iflags.p + 7);
+    check_flag(h.iflags.p + 7, s, RN_ESINGULAR, "coarsest-level LU pivot below 1e-14 max|A|");
+    h.Ainv.alloc((size_t)nL * nL, s);
+    RN_LAUNCH("coarse_lu", 24.0 * nL * nL, s, lu_inverse_kernel, grid_for(nL, 64, 4), 64, 0, nL, M.p, piv.p, h.Ainv.p,
+              work.p);
+    if (!p.keep_aux) {
+        for (auto &Lp : h.lev) {
+            Lp->agg.release();
+            Lp->roots.release();
+        }
+    }
+}
+
+}  // namespace rn

@@ -1,0 +1,240 @@
+"""Python binding of the C ABI in include/rn.h (argument marshalling only).
+
+Every step of setup and solve runs in ``librn.so``'s CUDA kernels.  The
+functions ``rn_setup``, ``rn_solve``, ``rn_free``, ... carry the C names; the
+``Hierarchy`` class is a thin owner around them that accepts torch tensors
+(device) or numpy arrays (host).  Importing this module fails loudly when the
+library has not been built or cannot be loaded: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librn.so")
+
+RN_OK, RN_EINVAL, RN_ENOMEM, RN_ESINGULAR, RN_ESTALL, RN_ENOTCONV, RN_ETIMEOUT, RN_ECUDA, RN_EINTERNAL = range(9)
+RN_DEVICE, RN_HOST = 0, 1
+RN_ENERGY_CG, RN_ENERGY_GMRES = 0, 1
+RN_FP64, RN_MIXED = 0, 1
+RN_OUTER_STATIONARY, RN_OUTER_CG, RN_OUTER_FGMRES = 0, 1, 2
+RN_MAX_LEVELS = 32
+STATUS_NAMES = ["RN_OK", "RN_EINVAL", "RN_ENOMEM", "RN_ESINGULAR", "RN_ESTALL", "RN_ENOTCONV", "RN_ETIMEOUT",
+                "RN_ECUDA", "RN_EINTERNAL"]
+
+
+class rn_csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class rn_params(C.Structure):
+    _fields_ = [("soc_theta", C.c_double), ("soc_theta_coarse", C.c_double), ("degree", C.c_int),
+                ("n_sweeps", C.c_int), ("energy_method", C.c_int), ("energy_precond", C.c_int),
+                ("prefilter", C.c_double), ("postfilter", C.c_double), ("max_coarse", C.c_int),
+                ("max_levels", C.c_int), ("b_sweeps", C.c_int), ("omega", C.c_double), ("seed", C.c_uint64),
+                ("symmetric", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int), ("precision", C.c_int),
+                ("outer", C.c_int), ("restart", C.c_int), ("use_graphs", C.c_int), ("keep_aux", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class rn_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rel_res", C.c_double), ("rho", C.c_double), ("solve_ms", C.c_double),
+                ("status", C.c_int)]
+
+
+class rn_stats(C.Structure):
+    _fields_ = [("levels", C.c_int), ("n", C.c_int32 * RN_MAX_LEVELS), ("nnz_A", C.c_int64 * RN_MAX_LEVELS),
+                ("nnz_P", C.c_int64 * RN_MAX_LEVELS), ("nnz_R", C.c_int64 * RN_MAX_LEVELS), ("oc", C.c_double),
+                ("cc", C.c_double), ("setup_ms", C.c_double), ("agg_rounds", C.c_int)]
+
+
+class rn_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    L.rn_default_params.argtypes = [P(rn_params)]
+    L.rn_setup.argtypes = [P(rn_csr), C.c_void_p, C.c_void_p, C.c_int, C.c_int, P(rn_params), P(C.c_void_p)]
+    L.rn_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, P(rn_solve_info)]
+    L.rn_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.rn_free.argtypes = [C.c_void_p]
+    L.rn_free.restype = None
+    L.rn_hierarchy_stats.argtypes = [C.c_void_p, P(rn_stats)]
+    L.rn_export_csr.argtypes = [C.c_void_p, C.c_int, C.c_int, P(C.c_int32), P(C.c_int32), P(C.c_int64),
+                                C.c_void_p, C.c_void_p, C.c_void_p]
+    L.rn_export_vec.argtypes = [C.c_void_p, C.c_int, C.c_int, P(C.c_int64), C.c_void_p]
+    L.rn_profile_enable.argtypes = [C.c_int]
+    L.rn_profile_reset.argtypes = []
+    L.rn_profile_read.argtypes = [P(rn_kernel_stat), C.c_int, P(C.c_int)]
+    L.rn_last_error.restype = C.c_char_p
+    L.rn_status_string.argtypes = [C.c_int]
+    L.rn_status_string.restype = C.c_char_p
+    return L
+
+
+lib = _load()
+
+# ----------------------------------------------------------------- C names
+rn_default_params = lib.rn_default_params
+rn_setup = lib.rn_setup
+rn_solve = lib.rn_solve
+rn_vcycle = lib.rn_vcycle
+rn_free = lib.rn_free
+rn_hierarchy_stats = lib.rn_hierarchy_stats
+rn_export_csr = lib.rn_export_csr
+rn_export_vec = lib.rn_export_vec
+rn_profile_enable = lib.rn_profile_enable
+rn_profile_reset = lib.rn_profile_reset
+rn_profile_read = lib.rn_profile_read
+rn_last_error = lib.rn_last_error
+rn_status_string = lib.rn_status_string
+
+
+class RNError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.rn_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 9 else status}: {msg}")
+
+
+def _check(st: int, where: str):
+    if st != RN_OK:
+        raise RNError(st, where)
+
+
+def default_params(**overrides) -> rn_params:
+    p = rn_params()
+    _check(rn_default_params(C.byref(p)), "rn_default_params")
+    for k, v in overrides.items():
+        if k in ("outer_name",):
+            continue
+        if not hasattr(p, k):
+            continue
+        setattr(p, k, v)
+    return p
+
+
+def params_from_config(cfg: dict, **overrides) -> rn_params:
+    """Map a workload parameter dict (see problems.PARAMS_*) to rn_params."""
+    m = dict(cfg)
+    m.update(overrides)
+    kw = dict(soc_theta=m.get("soc_theta", 0.25), soc_theta_coarse=m.get("soc_theta_coarse", -1.0),
+              degree=m.get("degree", 2), n_sweeps=m.get("n_sweeps", 4), energy_method=m.get("method", 0),
+              energy_precond=m.get("precond", 1), prefilter=m.get("prefilter", 0.0),
+              postfilter=m.get("postfilter", 0.0), max_coarse=m.get("max_coarse", 64),
+              max_levels=m.get("max_levels", 25), b_sweeps=m.get("b_sweeps", 4), omega=m.get("omega", 2.0 / 3.0),
+              seed=m.get("seed", 12345), symmetric=m.get("symmetric", 1), nu_pre=m.get("nu_pre", 1),
+              nu_post=m.get("nu_post", 1), precision=m.get("precision", RN_FP64), outer=m.get("outer", RN_OUTER_CG),
+              restart=m.get("restart", 30), use_graphs=m.get("use_graphs", 1), keep_aux=m.get("keep_aux", 0))
+    return default_params(**kw)
+
+
+def _ptr(a) -> int:
+    """Device pointer of a contiguous torch tensor, or host pointer of a numpy array."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _is_host(a) -> bool:
+    return isinstance(a, np.ndarray) or (hasattr(a, "is_cuda") and not a.is_cuda)
+
+
+class Hierarchy:
+    """Owns an rn_hierarchy.  A, B, Bhat: torch CUDA tensors or numpy arrays."""
+
+    def __init__(self, rowptr, col, val, B, Bhat=None, params: rn_params | None = None, stream=None):
+        host = _is_host(val)
+        if host:
+            rowptr = np.ascontiguousarray(rowptr, np.int32)
+            col = np.ascontiguousarray(col, np.int32)
+            val = np.ascontiguousarray(val, np.float64)
+            B = np.ascontiguousarray(B, np.float64).reshape(-1)
+            Bhat = None if Bhat is None else np.ascontiguousarray(Bhat, np.float64).reshape(-1)
+        n = int(rowptr.shape[0]) - 1
+        self.n = n
+        self.params = params if params is not None else default_params()
+        if stream is not None:
+            self.params.stream = C.c_void_p(stream)
+        A = rn_csr(n, n, int(col.shape[0]), _ptr(rowptr), _ptr(col), _ptr(val))
+        h = C.c_void_p()
+        self._keep = (rowptr, col, val, B, Bhat)
+        st = rn_setup(C.byref(A), _ptr(B), _ptr(Bhat) if Bhat is not None else None, 1,
+                      RN_HOST if host else RN_DEVICE, C.byref(self.params), C.byref(h))
+        self._keep = None
+        _check(st, "rn_setup")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            rn_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def solve(self, b, x, rtol=1e-8, maxit=500, raise_on_notconv=True):
+        host = _is_host(b)
+        info = rn_solve_info()
+        st = rn_solve(self._h, _ptr(b), _ptr(x), RN_HOST if host else RN_DEVICE, rtol, maxit, C.byref(info))
+        if st != RN_OK and (st != RN_ENOTCONV or raise_on_notconv):
+            raise RNError(st, "rn_solve")
+        return dict(iters=info.iters, rel_res=info.rel_res, rho=info.rho, solve_ms=info.solve_ms, status=st)
+
+    def vcycle(self, b, x):
+        _check(rn_vcycle(self._h, _ptr(b), _ptr(x)), "rn_vcycle")
+
+    def stats(self) -> dict:
+        s = rn_stats()
+        _check(rn_hierarchy_stats(self._h, C.byref(s)), "rn_hierarchy_stats")
+        L = s.levels
+        return dict(levels=L, n=list(s.n[:L]), nnz_A=list(s.nnz_A[:L]), nnz_P=list(s.nnz_P[:L]),
+                    nnz_R=list(s.nnz_R[:L]), oc=s.oc, cc=s.cc, setup_ms=s.setup_ms, agg_rounds=s.agg_rounds)
+
+    def export_csr(self, lvl: int, which: int):
+        """(rowptr, col, val, shape) numpy copies of matrix `which` (0 A, 1 S, 2 N, 3 T, 4 P, 5 R) on level lvl."""
+        nr, nc, nz = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(rn_export_csr(self._h, lvl, which, C.byref(nr), C.byref(nc), C.byref(nz), None, None, None),
+               "rn_export_csr")
+        rp = np.zeros(nr.value + 1, np.int32)
+        ci = np.zeros(max(nz.value, 1), np.int32)
+        va = np.zeros(max(nz.value, 1), np.float64)
+        _check(rn_export_csr(self._h, lvl, which, C.byref(nr), C.byref(nc), C.byref(nz), rp.ctypes.data,
+                             ci.ctypes.data, va.ctypes.data), "rn_export_csr")
+        return rp, ci[: nz.value], va[: nz.value], (nr.value, nc.value)
+
+    def export_vec(self, lvl: int, which: int):
+        """0 agg, 1 roots, 2 row types (int32); 3 B, 4 Bc, 5 Bhat, 6 Bhat_c (float64)."""
+        ln = C.c_int64()
+        _check(rn_export_vec(self._h, lvl, which, C.byref(ln), None), "rn_export_vec")
+        out = np.zeros(max(ln.value, 1), np.int32 if which <= 2 else np.float64)
+        _check(rn_export_vec(self._h, lvl, which, C.byref(ln), out.ctypes.data), "rn_export_vec")
+        return out[: ln.value]
+
+
+def profile_enable(on: bool = True):
+    _check(rn_profile_enable(1 if on else 0), "rn_profile_enable")
+
+
+def profile_reset():
+    _check(rn_profile_reset(), "rn_profile_reset")
+
+
+def profile_read() -> dict:
+    cnt = C.c_int()
+    _check(rn_profile_read(None, 0, C.byref(cnt)), "rn_profile_read")
+    arr = (rn_kernel_stat * max(cnt.value, 1))()
+    _check(rn_profile_read(arr, cnt.value, C.byref(cnt)), "rn_profile_read")
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes)
+            for i in range(cnt.value)}

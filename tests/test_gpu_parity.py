@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Bars (stated per check):
+  * bit-exact: strength pattern, aggregates, roots, row types, the patterns of
+    N, T, P, R and every coarse A; on the finest level also the values of S,
+    N = S^d C, T and the smoothed candidates (same operation sequence, no FMA);
+  * values of P, R, coarse A (and S, N, T below the finest level):
+    max|gpu - oracle| <= 1e-12 * max|oracle| per matrix;
+  * solutions: true relative residual < 1e-8 and, for the same outer method,
+    iteration counts within 2 of the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_1610_03154_gb300 import problems as PR
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch, torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def rn():
+    from paper_1610_03154_gb300 import rn as mod
+
+    return mod
+
+
+def dev(torch_dev, a):
+    torch, d = torch_dev
+    return torch.from_numpy(np.ascontiguousarray(a)).to(d)
+
+
+def gpu_hierarchy(rn, torch_dev, pr, **over):
+    A = pr.A
+    params = rn.params_from_config(pr.params, keep_aux=1, **over)
+    Bh = None if pr.Bhat is None else dev(torch_dev, pr.Bhat.reshape(-1))
+    return rn.Hierarchy(dev(torch_dev, A.rowptr), dev(torch_dev, A.col), dev(torch_dev, A.val),
+                        dev(torch_dev, pr.B.reshape(-1)), Bh, params=params)
+
+
+def as_csr(t):
+    rp, ci, va, shape = t
+    return sp.csr_matrix((va, ci, rp), shape=shape)
+
+
+def same_pattern(g, o, what):
+    assert g.shape == o.shape, (what, g.shape, o.shape)
+    assert np.array_equal(g.indptr, o.indptr), f"{what}: row pointers differ"
+    assert np.array_equal(g.indices, o.indices), f"{what}: column indices differ"
+
+
+def close_values(g, o, what, exact=False):
+    if exact:
+        assert np.array_equal(g.data, o.data), f"{what}: values not bit-identical " \
+            f"(max diff {np.max(np.abs(g.data - o.data)) if g.nnz else 0})"
+        return
+    scale = np.max(np.abs(o.data)) if o.nnz else 1.0
+    err = np.max(np.abs(g.data - o.data)) if o.nnz else 0.0
+    assert err <= TOL * scale, f"{what}: max diff {err:.3e} > {TOL} * {scale:.3e}"
+
+
+def compare_hierarchies(h, oh, nonsym=False):
+    st = h.stats()
+    assert st["levels"] == len(oh.levels), (st["n"], [L.A.shape[0] for L in oh.levels])
+    for l, L in enumerate(oh.levels):
+        Ag = as_csr(h.export_csr(l, 0))
+        same_pattern(Ag, L.A, f"A[{l}]")
+        close_values(Ag, L.A, f"A[{l}]", exact=(l == 0))
+        if l == len(oh.levels) - 1:
+            break
+        exact0 = (l == 0)
+        Sg = as_csr(h.export_csr(l, 1))
+        same_pattern(Sg, L.S, f"S[{l}]")
+        close_values(Sg, L.S, f"S[{l}]", exact=exact0)
+        assert np.array_equal(h.export_vec(l, 0), L.agg), f"agg[{l}]"
+        assert np.array_equal(h.export_vec(l, 1), L.roots), f"roots[{l}]"
+        assert np.array_equal(h.export_vec(l, 2), L.rowtype), f"rowtype[{l}]"
+        Ng = as_csr(h.export_csr(l, 2))
+        same_pattern(Ng, L.N, f"N[{l}]")
+        close_values(Ng, L.N, f"N[{l}]", exact=exact0)
+        Bg = h.export_vec(l, 3)
+        if exact0:
+            assert np.array_equal(Bg, L.B), "smoothed B[0]"
+        else:
+            assert np.max(np.abs(Bg - L.B)) <= TOL * np.max(np.abs(L.B))
+        Tg = as_csr(h.export_csr(l, 3))
+        same_pattern(Tg, L.T, f"T[{l}]")
+        close_values(Tg, L.T, f"T[{l}]", exact=exact0)
+        Pg = as_csr(h.export_csr(l, 4))
+        same_pattern(Pg, L.P, f"P[{l}]")
+        close_values(Pg, L.P, f"P[{l}]")
+        Rg = as_csr(h.export_csr(l, 5))
+        same_pattern(Rg, L.R, f"R[{l}]")
+        close_values(Rg, L.R, f"R[{l}]")
+        if nonsym:
+            assert np.max(np.abs(h.export_vec(l, 6) - L.Bhatc)) <= TOL * np.max(np.abs(L.Bhatc))
+    # complexities of eq. oc / eq. cc agree with the oracle's counts
+    ost = oh.stats()
+    assert abs(st["oc"] - ost["oc"]) < 1e-12 and abs(st["cc"] - ost["cc"]) < 1e-12
+
+
+def gpu_solve(rn, torch_dev, h, pr, rtol=1e-8, maxit=1000):
+    torch, d = torch_dev
+    b = dev(torch_dev, pr.b)
+    x = torch.zeros_like(b)
+    info = h.solve(b, x, rtol=rtol, maxit=maxit)
+    xs = x.cpu().numpy()
+    res = np.linalg.norm(pr.b - pr.A.to_scipy() @ xs) / np.linalg.norm(pr.b)
+    return xs, info, res
+
+
+CASES = {
+    "poisson64": lambda: PR.poisson_problem(64),                 # the 4096-dof Poisson workload
+    "poisson37": lambda: PR.poisson_problem(37),                 # ragged sizes
+    "aniso96": lambda: PR.aniso_problem(96),                     # rotated anisotropy, d=4, pre/post filter
+    "aniso255": lambda: PR.aniso_problem(255),                   # 64k rows: many tiles, ragged tail
+    "convdiff80": lambda: PR.convdiff_problem(80),               # nonsymmetric, GMRES energy-min
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_hierarchy_parity(rn, torch_dev, oracle, case):
+    pr = CASES[case]()
+    h = gpu_hierarchy(rn, torch_dev, pr)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, Bhat=pr.Bhat, **pr.params)
+    compare_hierarchies(h, oh, nonsym=pr.Bhat is not None)
+    h.close()
+
+
+@pytest.mark.parametrize("case", ["poisson64", "aniso96", "convdiff80"])
+def test_solve_parity_fp64(rn, torch_dev, oracle, case):
+    pr = CASES[case]()
+    h = gpu_hierarchy(rn, torch_dev, pr)
+    xs, info, res = gpu_solve(rn, torch_dev, h, pr)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, Bhat=pr.Bhat, **pr.params)
+    xo, oinfo = oh.solve(pr.b, tol=1e-8, maxit=1000, outer=pr.params["outer"], restart=pr.params.get("restart", 30))
+    assert info["status"] == 0 and oinfo["status"] == 0
+    assert res < 1e-8
+    assert abs(info["iters"] - oinfo["iters"]) <= 2, (info["iters"], oinfo["iters"])
+    assert np.linalg.norm(xs - xo) / np.linalg.norm(xo) < 1e-5
+    h.close()
+
+
+@pytest.mark.parametrize("outer", [0, 1, 2])
+def test_outer_methods_converge(rn, torch_dev, oracle, outer):
+    pr = CASES["poisson64"]()
+    h = gpu_hierarchy(rn, torch_dev, pr, outer=outer)
+    xs, info, res = gpu_solve(rn, torch_dev, h, pr)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    xo, oinfo = oh.solve(pr.b, tol=1e-8, maxit=1000, outer=outer)
+    assert res < 1e-8
+    assert abs(info["iters"] - oinfo["iters"]) <= 2, (info["iters"], oinfo["iters"])
+    h.close()
+
+
+@pytest.mark.parametrize("case", ["poisson64", "aniso96", "convdiff80"])
+def test_mixed_precision_reaches_fp64_tolerance(rn, torch_dev, case):
+    pr = CASES[case]()
+    h = gpu_hierarchy(rn, torch_dev, pr, precision=rn.RN_MIXED)
+    xs, info, res = gpu_solve(rn, torch_dev, h, pr)
+    assert info["status"] == 0
+    assert res < 1e-8
+    h.close()
+
+
+def test_vcycle_matches_oracle_cycle(rn, torch_dev, oracle):
+    torch, d = torch_dev
+    pr = CASES["aniso96"]()
+    h = gpu_hierarchy(rn, torch_dev, pr, use_graphs=0)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    b = dev(torch_dev, pr.b)
+    x = torch.zeros_like(b)
+    h.vcycle(b, x)
+    xo = oh.vcycle(pr.b)
+    xg = x.cpu().numpy()
+    assert np.max(np.abs(xg - xo)) <= 1e-10 * np.max(np.abs(xo))
+    # the graph-captured cycle gives the same result as direct launches
+    h2 = gpu_hierarchy(rn, torch_dev, pr, use_graphs=1)
+    x2 = torch.zeros_like(b)
+    h2.vcycle(b, x2)
+    h2.vcycle(b, x2)
+    assert np.array_equal(x2.cpu().numpy(), xg)
+    h.close()
+    h2.close()
+
+
+def test_host_location_matches_device(rn, torch_dev):
+    pr = CASES["poisson37"]()
+    A = pr.A
+    params = rn.params_from_config(pr.params)
+    hh = rn.Hierarchy(A.rowptr, A.col, A.val, pr.B.reshape(-1), params=params)
+    x = np.zeros(A.n_rows)
+    info = hh.solve(pr.b.copy(), x, rtol=1e-8)
+    hd = gpu_hierarchy(rn, torch_dev, pr)
+    xd, infod, res = gpu_solve(rn, torch_dev, hd, pr)
+    assert info["iters"] == infod["iters"]
+    assert np.array_equal(x, xd)
+    hh.close()
+    hd.close()
+
+
+def test_deterministic_repeat(rn, torch_dev):
+    pr = CASES["aniso96"]()
+    outs = []
+    for _ in range(2):
+        h = gpu_hierarchy(rn, torch_dev, pr)
+        P = h.export_csr(0, 4)
+        xs, info, res = gpu_solve(rn, torch_dev, h, pr)
+        outs.append((P[2].copy(), xs, info["iters"]))
+        h.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
+
+
+# ------------------------------------------------------------------ edge cases
+def _mk(rn, torch_dev, rowptr, col, val, **over):
+    params = rn.default_params(**over)
+    n = len(rowptr) - 1
+    return rn.Hierarchy(dev(torch_dev, np.array(rowptr, np.int32)), dev(torch_dev, np.array(col, np.int32)),
+                        dev(torch_dev, np.array(val, np.float64)), dev(torch_dev, np.ones(n)), params=params)
+
+
+def test_one_by_one_and_tiny_systems(rn, torch_dev):
+    torch, d = torch_dev
+    h = _mk(rn, torch_dev, [0, 1], [0], [2.0])
+    b = dev(torch_dev, np.array([3.0]))
+    x = torch.zeros_like(b)
+    info = h.solve(b, x)
+    assert abs(x.item() - 1.5) < 1e-15 and info["status"] == 0
+    h.close()
+    pr = PR.poisson_problem(6)  # 36 rows <= max_coarse: a one-level hierarchy, exact solve
+    h = gpu_hierarchy(rn, torch_dev, pr)
+    assert h.stats()["levels"] == 1
+    xs, info, res = gpu_solve(rn, torch_dev, h, pr, rtol=1e-13)
+    assert res < 1e-13 and info["iters"] <= 1
+    h.close()
+
+
+def test_no_coarsening_diagonal_matrix(rn, torch_dev):
+    torch, d = torch_dev
+    n = 300  # every node isolated: setup stops on the first level; dense solve
+    h = _mk(rn, torch_dev, list(range(n + 1)), list(range(n)), list(np.linspace(1, 2, n)), max_coarse=10)
+    assert h.stats()["levels"] == 1
+    b = dev(torch_dev, np.ones(n))
+    x = torch.zeros_like(b)
+    h.solve(b, x)
+    assert np.allclose(x.cpu().numpy(), 1.0 / np.linspace(1, 2, n), rtol=1e-14)
+    h.close()
+
+
+def test_rejects_malformed_csr(rn, torch_dev):
+    with pytest.raises(rn.RNError) as e:
+        _mk(rn, torch_dev, [0, 2, 4], [1, 0, 0, 1], [-1.0, 2.0, 2.0, -1.0])  # unsorted row 0
+    assert e.value.status == rn.RN_EINVAL
+    with pytest.raises(rn.RNError) as e:
+        _mk(rn, torch_dev, [0, 1, 2], [1, 0], [1.0, 1.0])  # no diagonal
+    assert e.value.status == rn.RN_EINVAL
+    with pytest.raises(rn.RNError) as e:
+        _mk(rn, torch_dev, [0, 1, 2], [0, 1], [1.0, float("nan")])
+    assert e.value.status == rn.RN_EINVAL
+
+
+def test_singular_coarsest_level(rn, torch_dev):
+    A = PR.q1_aniso(5, 1.0, 0.0, dirichlet=False)  # Neumann Laplacian: singular
+    with pytest.raises(rn.RNError) as e:
+        _mk(rn, torch_dev, A.rowptr, A.col, A.val, max_coarse=100)
+    assert e.value.status == rn.RN_ESINGULAR
+
+
+def test_not_converged_status(rn, torch_dev):
+    torch, d = torch_dev
+    pr = CASES["aniso96"]()
+    h = gpu_hierarchy(rn, torch_dev, pr)
+    b = dev(torch_dev, pr.b)
+    x = torch.zeros_like(b)
+    info = h.solve(b, x, rtol=1e-8, maxit=2, raise_on_notconv=False)
+    assert info["status"] == rn.RN_ENOTCONV and info["iters"] == 2
+    h.close()
+
+
+# ------------------------------------------------------------------ full-size workloads
+@pytest.mark.slow
+def test_full_size_aniso_hierarchy_parity_and_solve(rn, torch_dev, oracle):
+    """The 1024x1024-element rotated anisotropic workload (n = 1,046,529) in the
+    benchmark's launch configuration: every level of the hierarchy against the
+    oracle, and the solution against the FP64 residual bar."""
+    pr = PR.aniso_problem(1024)
+    h = gpu_hierarchy(rn, torch_dev, pr)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    compare_hierarchies(h, oh)
+    h.close()
+    for prec in (rn.RN_FP64, rn.RN_MIXED):
+        h = gpu_hierarchy(rn, torch_dev, pr, keep_aux=0, precision=prec)
+        xs, info, res = gpu_solve(rn, torch_dev, h, pr, maxit=2000)
+        assert info["status"] == 0 and res < 1e-8, (prec, info, res)
+        h.close()
