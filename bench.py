@@ -1,0 +1,341 @@
+"""Benchmark: setup + solve time to a 1e-8 relative residual for root-node AMG.
+
+Workload (one step): the rotated anisotropic diffusion system, Q1 bilinear
+elements on a 1024 x 1024 element mesh of the unit square (n = 1,046,529,
+nnz = 9,406,489), eps = 1e-3, psi = pi/8, homogeneous Dirichlet, B = 1,
+right-hand side uniform in [-1, 1] (seed 2).  A step is the whole hot path:
+rn_setup (strength, aggregation, pattern, energy-minimised P with pre- and
+post-filter, R, Galerkin RAP, coarsest LU) followed by rn_solve (CG with
+the V(1,1) weighted-Jacobi cycle) from x0 = 0 to ||b - A x|| < 1e-8 ||b||.
+
+  value      seconds per step with A, B, b resident in HBM (CUDA events);
+             the default form is the mixed-precision one (FP32 cycle inside
+             FP64 flexible CG); the plain FP64 form is reported beside it.
+  e2e        the same through the C ABI with host buffers (pinned), the
+             host->device copies of A, B, b, x0 and the device->host copy
+             of x inside the timed region.
+  roofline   the dominant kernel of the step (by device time), achieved
+             algorithmic bytes / measured duration against the measured HBM
+             copy bandwidth.
+  cpu_baseline  the FP64 CPU oracle on this machine's host (1 thread): its
+             full setup plus a bounded number of CG iterations, the solve
+             scaled to the iteration count the GPU FP64 form needed.
+
+--impl reference times the oracle alone on the same workload (bounded sample
+per step, as above).  With --gpus N under torchrun every rank solves its own
+replica (no data-path collective; "replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1610_03154_gb300 import problems as PR  # noqa: E402
+
+METRIC = "setup+solve s to 1e-8 rel. residual (FP64 vs mixed/batched); HBM GB/s % roofline"
+WORKLOAD_NE = 1024
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_oracle_sample(pr, iters_target: int | None, cg_sample_iters: int = 25):
+    """Oracle setup (full) + a bounded CG solve; returns seconds and the sample description."""
+    from oracle import oracle as O
+
+    t0 = time.perf_counter()
+    h = O.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, info = h.solve(pr.b, tol=1e-8, maxit=cg_sample_iters, outer=1)
+    t_solve = time.perf_counter() - t0
+    done = max(info["iters"], 1)
+    per_it = t_solve / done
+    need = iters_target if iters_target else done
+    value = t_setup + per_it * need
+    sample = (f"oracle setup in full ({t_setup:.2f} s) + {done} FP64 CG iterations ({t_solve:.2f} s), "
+              f"solve scaled to {need} iterations")
+    return value, sample, t_setup, per_it
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    pr = PR.aniso_problem(WORKLOAD_NE)
+    # iteration count of the oracle on this workload: one full FP64 CG solve up front (not timed)
+    from oracle import oracle as O
+
+    h = O.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    _, info = h.solve(pr.b, tol=1e-8, maxit=2000, outer=1)
+    iters = info["iters"]
+    del h
+    for _ in range(max(0, args.warmup - 1)):
+        run_oracle_sample(pr, iters)
+    vals, sample = [], ""
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, sample, _, _ = run_oracle_sample(pr, iters)
+        vals.append(v)
+    wall = time.perf_counter() - t_all
+    value = float(np.mean(vals))
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": pr.description, "solver": "oracle FP64 CG + V(1,1) Jacobi", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "oracle_iters_to_1e-8": iters, "sample_wall_s": wall},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--ne", type=int, default=WORKLOAD_NE, help="elements per side (default: the 1024^2 workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1610_03154_gb300 import rn
+
+    pr = PR.aniso_problem(args.ne)
+    A = pr.A
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rp, ci, va, Bd, bd = t(A.rowptr), t(A.col), t(A.val), t(pr.B.reshape(-1)), t(pr.b)
+    xd = torch.zeros_like(bd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def params(prec):
+        return rn.params_from_config(pr.params, precision=rn.RN_MIXED if prec == "mixed" else rn.RN_FP64,
+                                     outer=rn.RN_OUTER_CG, use_graphs=1)
+
+    def step(prec):
+        xd.zero_()
+        h = rn.Hierarchy(rp, ci, va, Bd, params=params(prec), stream=sptr)
+        info = h.solve(bd, xd, rtol=1e-8, maxit=5000)
+        h.close()
+        return info
+
+    def timed(prec, k):
+        times, infos = [], []
+        for _ in range(k):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step(prec))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        return times, infos
+
+    prec = args.precision
+    other = "fp64" if prec == "mixed" else "mixed"
+    for _ in range(max(3, args.warmup)):
+        step(prec)
+        step(other)
+    # check the solution once against the FP64 residual bar (host, scipy)
+    xs = xd.cpu().numpy()
+    res_check = float(np.linalg.norm(pr.b - A.to_scipy() @ xs) / np.linalg.norm(pr.b))
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = int(rn.rn_kernel_launches())
+    with ClockSampler(local) as clk:
+        times, infos = timed(prec, args.steps)
+    launches = int(rn.rn_kernel_launches()) - l0
+    torch.cuda.synchronize()
+    step_s = float(np.mean(times))
+    if ws > 1:
+        tt = torch.tensor([step_s], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        step_s = float(tt.item())
+    times_other, infos_other = timed(other, args.steps)
+
+    # per-kernel device times of one step (events around every launch)
+    rn.profile_reset()
+    rn.profile_enable(True)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    step(prec)
+    torch.cuda.synchronize()
+    prof = rn.profile_read()
+    rn.profile_enable(False)
+    total_ms = sum(v["ms"] for v in prof.values())
+    top = sorted(prof.items(), key=lambda kv: -kv[1]["ms"])
+    name, st = top[0]
+    peak, peak_kind = load_peaks()
+    achieved = st["bytes"] / (st["ms"] / 1e3) / 1e9 if st["ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "launches": st["launches"], "avg_launch_us": st["ms"] * 1e3 / max(st["launches"], 1),
+                "share_of_step_device_time": st["ms"] / total_ms if total_ms else None}
+    kernels = {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
+                   "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] > 0 else None}
+               for k, v in top[:12]}
+
+    # end to end through the C ABI with host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hrp, hci, hva, hB, hb = pin(A.rowptr), pin(A.col), pin(A.val), pin(pr.B.reshape(-1)), pin(pr.b)
+    hx = pin(np.zeros(A.n_rows))
+    e2e_times = []
+    for _ in range(args.steps):
+        hx[:] = 0.0
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = rn.Hierarchy(hrp, hci, hva, hB, params=params(prec), stream=sptr)
+        h.solve(hb, hx, rtol=1e-8, maxit=5000)
+        h.close()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = hrp.nbytes + hci.nbytes + hva.nbytes + hB.nbytes + hb.nbytes + hx.nbytes
+    d2h = hx.nbytes
+
+    stats_h = rn.Hierarchy(rp, ci, va, Bd, params=params(prec), stream=sptr)
+    hs = stats_h.stats()
+    stats_h.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        fp64_iters = (infos_other if other == "fp64" else infos)[0]["iters"]
+        v, sample, _, _ = run_oracle_sample(pr, fp64_iters)
+        cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": step_s * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": pr.description, "precision": prec, "outer": "flexible CG" if prec == "mixed"
+                       else "CG", "cycle": "V(1,1) weighted Jacobi omega=2/3, dense coarsest solve",
+                       "setup": "theta=0.25 symmetric strength, seeded MIS-2 aggregation, d=4, 6 CG energy-min "
+                                "sweeps, pre/post filter 0.1", "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{ws}"},
+            "iters": infos[0]["iters"], "rel_res": infos[0]["rel_res"], "rel_res_host_check": res_check,
+            "step_s_all": times,
+            f"{other}": {"value": float(np.mean(times_other)), "iters": infos_other[0]["iters"],
+                         "rel_res": infos_other[0]["rel_res"]},
+            "hierarchy": {"levels": hs["levels"], "n": hs["n"], "nnz_A": hs["nnz_A"], "nnz_P": hs["nnz_P"],
+                          "oc": hs["oc"], "cc": hs["cc"], "setup_ms_last": hs["setup_ms"]},
+            "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "roofline": roofline,
+            "kernels_top": kernels,
+            "gpu_launches": launches // max(args.steps, 1),
+            "gpu_launches_timed_region": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

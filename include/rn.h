@@ -172,6 +172,10 @@ rn_status rn_profile_enable(int on);
 rn_status rn_profile_reset(void);
 rn_status rn_profile_read(rn_kernel_stat *out, int max, int *count);
 
+/* Number of library kernels launched by this process so far (kernels inside
+ * a replayed CUDA graph are counted one by one). */
+int64_t rn_kernel_launches(void);
+
 const char *rn_last_error(void);
 const char *rn_status_string(rn_status s);
 

@@ -20,8 +20,13 @@ static inline void *orc_xcalloc(size_t n, size_t s) {
 
 /* Guard constant for floating threshold tests: keep <=> v >= theta*ref*(1-g). */
 #define ORC_GUARD 1e-10
-/* CG energy minimisation stops once <R,Z> <= ORC_CG_STOP * <R0,Z0>. */
-#define ORC_CG_STOP 1e-28
+/* CG energy minimisation stops once <R,Z> <= ORC_CG_STOP * <R0,Z0> (the
+ * residual is ~1e-11 of its start: the Krylov space is exhausted and further
+ * steps would only amplify rounding noise). */
+#define ORC_CG_STOP 1e-22
+/* GMRES energy minimisation treats h_{j+1,j} <= ORC_GMRES_BREAK * beta as a
+ * (happy) breakdown. */
+#define ORC_GMRES_BREAK 1e-14
 
 void orc_csr_alloc(orc_csr *a, int32_t nrows, int32_t ncols, int64_t nnz, int with_val);
 void orc_csr_copy(const orc_csr *a, orc_csr *b);

@@ -360,12 +360,15 @@ int orc_tentative(orc_csr *N, const int32_t *agg, const int32_t *roots, const do
  * Row-wise projection onto the constraint space {U : U Bc = 0} (eq. Tproj with
  * a zero right-hand side), restricted to each row's pattern J:
  *   free rows:  u <- u - (u.b / b.b) b,  b = Bc[J];
+ *   free rows with a single pattern entry: u <- 0 (the exact projection);
  *   root and unaggregated rows are fixed: u <- 0.
  */
 void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc) {
     for (int32_t i = 0; i < W->nrows; i++) {
         int32_t s = W->rowptr[i], e = W->rowptr[i + 1];
-        if (rowtype[i] != ORC_FREE) {
+        /* fixed rows, and one-entry rows whose constraint space is exactly {0}
+         * (the formula below would leave rounding noise there) */
+        if (rowtype[i] != ORC_FREE || e - s == 1) {
             for (int32_t q = s; q < e; q++) W->val[q] = 0.0;
             continue;
         }
@@ -527,7 +530,7 @@ int orc_energy_min_gmres(const orc_csr *A, orc_csr *P, const int32_t *rowtype, c
             g[j] = cs[j] * g[j];
             k = j + 1;
             if (res_trace) for (int jj = j + 1; jj <= m; jj++) res_trace[jj] = fabs(g[j + 1]);
-            if (hn == 0.0) break;
+            if (hn <= ORC_GMRES_BREAK * beta) break;
             V[j + 1] = (double *)orc_xmalloc((size_t)nz * sizeof(double));
             for (int64_t q = 0; q < nz; q++) V[j + 1][q] = W.val[q] / hn;
         }

@@ -86,10 +86,27 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
     if (!A->rowptr || !A->col || !A->val) fail(RN_EINVAL, "null CSR array");
     check_params(p);
     if (!p->symmetric && !Bhat) fail(RN_EINVAL, "nonsymmetric setup needs Bhat");
+    // With no stream given, work goes to a stream the hierarchy creates: a
+    // blocking stream, so it stays ordered with the legacy default stream,
+    // and unlike that stream it can be captured into a CUDA graph.
+    struct StreamGuard {
+        cudaStream_t s = nullptr;
+        ~StreamGuard() {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        }
+    } own;
+    cudaStream_t s = static_cast<cudaStream_t>(p->stream);
+    if (!s) {
+        RN_CUDA_CHECK(cudaStreamCreate(&own.s));
+        s = own.s;
+    }
     std::unique_ptr<rn_hierarchy> h(new rn_hierarchy());
     h->p = *p;
-    h->s = static_cast<cudaStream_t>(p->stream);
-    cudaStream_t s = h->s;
+    h->s = s;
+    h->own_stream = (own.s != nullptr);
     const double t0 = rn::now_ms();
     const int32_t n = A->n_rows;
     rn::DVec<int32_t> rp, ci;
@@ -119,7 +136,9 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
     rn::prepare_solve(*h);
     RN_CUDA_CHECK(cudaStreamSynchronize(s));
     h->setup_ms = rn::now_ms() - t0;
+    rp.release(); ci.release(); va.release(); Bd.release(); Bhd.release();
     *out = h.release();
+    own.s = nullptr;  // the hierarchy owns it now; rn_free destroys it
     return RN_OK;
     RN_API_END
 }
@@ -163,11 +182,13 @@ extern "C" rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x) {
 extern "C" void rn_free(rn_hierarchy *h) {
     if (!h) return;
     cudaStream_t s = h->s;
+    const bool own = h->own_stream;
     try {
         delete h;
     } catch (...) {
     }
     cudaStreamSynchronize(s);
+    if (own) cudaStreamDestroy(s);
 }
 
 extern "C" rn_status rn_hierarchy_stats(const rn_hierarchy *h, rn_stats *st) {

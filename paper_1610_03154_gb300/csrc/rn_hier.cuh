@@ -25,7 +25,8 @@ struct rn_level {
 
 struct rn_hierarchy {
     rn_params p{};
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr;  // params.stream, or a stream the hierarchy created (own_stream)
+    bool own_stream = false;
     std::vector<std::unique_ptr<rn_level>> lev;  // lev.back() is the coarsest
     int32_t nL = 0;
     rn::DVec<double> Ainv;                        // coarsest inverse, row-major nL x nL
@@ -40,6 +41,7 @@ struct rn_hierarchy {
     cudaGraphExec_t graph_exec = nullptr;
     const double *graph_in = nullptr;
     double *graph_out = nullptr;
+    int64_t graph_kernels = 0;                    // kernel nodes in the captured cycle
     // statistics
     double setup_ms = 0.0;
     int agg_rounds = 0;

@@ -108,6 +108,8 @@ struct ProfScope {
 };
 void check_launch(const char *name);
 bool profiling_enabled();
+void add_launches(int64_t k);      // kernels replayed inside a CUDA graph
+int64_t launches_so_far();
 
 #define RN_LAUNCH(name, bytes, stream, kernel, grid, block, smem, ...)     \
     do {                                                                   \

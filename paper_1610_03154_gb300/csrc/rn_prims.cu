@@ -1,5 +1,6 @@
 // rn_prims.cu - allocator, profiling, scan, deterministic reductions,
 // transpose and small elementwise kernels.
+#include <atomic>
 #include <cstdarg>
 #include <chrono>
 #include <map>
@@ -127,7 +128,12 @@ static void drain_pending() {
     g_pending.clear();
 }
 
+static std::atomic<int64_t> g_launches{0};
+void add_launches(int64_t k) { g_launches += k; }
+int64_t launches_so_far() { return g_launches.load(); }
+
 ProfScope::ProfScope(const char *name_, double bytes_, cudaStream_t s_) : name(name_), bytes(bytes_), s(s_) {
+    g_launches++;
     if (!g_prof_on) return;
     cudaStreamCaptureStatus cs;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
@@ -154,6 +160,8 @@ ProfScope::~ProfScope() noexcept(false) {
 }
 
 }  // namespace rn
+
+extern "C" int64_t rn_kernel_launches(void) { return rn::launches_so_far(); }
 
 extern "C" rn_status rn_profile_enable(int on) {
     rn::g_prof_on = (on != 0);

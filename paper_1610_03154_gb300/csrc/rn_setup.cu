@@ -15,7 +15,8 @@
 namespace rn {
 
 constexpr double kGuard = 1e-10;     // keep <=> v >= theta * ref * (1 - kGuard)
-constexpr double kCgStop = 1e-28;    // CG energy minimisation stops at <R,Z> <= kCgStop <R0,Z0>
+constexpr double kCgStop = 1e-22;    // CG energy minimisation stops at <R,Z> <= kCgStop <R0,Z0>
+constexpr double kGmresBreak = 1e-14; // GMRES energy minimisation: h_{j+1,j} <= kGmresBreak * beta ends it
 constexpr int kMaxAggRounds = 4096;  // bound on distance-2 MIS rounds
 constexpr int kMaxDense = 4096;      // largest coarsest level for the dense LU
 constexpr int kT = 256;              // threads per block of the row kernels
@@ -425,7 +426,8 @@ __global__ void gm_axpy_kernel(int64_t nz, double *__restrict__ w, const double 
 }
 
 // Givens update of Hessenberg column j; H row-major (m+1) x m
-__global__ void gm_givens_kernel(int m, int j, double *H, double *cs, double *sn, double *g, double *sc, int32_t *fl) {
+__global__ void gm_givens_kernel(int m, int j, double *H, double *cs, double *sn, double *g, double *sc, int32_t *fl,
+                                 double brk) {
     if (fl[0]) return;
     const double hn = sqrt(sc[1]);
     H[(j + 1) * m + j] = hn;
@@ -447,7 +449,7 @@ __global__ void gm_givens_kernel(int m, int j, double *H, double *cs, double *sn
     g[j] = cs[j] * g[j];
     fl[1] = j + 1;
     sc[2] = hn;  // next basis vector = w / hn
-    if (hn == 0.0) fl[0] = 1;
+    if (hn <= brk * sc[0]) fl[0] = 1;
 }
 
 __global__ void gm_backsolve_kernel(int m, const double *H, const double *g, double *y, const int32_t *fl) {
@@ -695,7 +697,7 @@ static void energy_min_gmres(rn_hierarchy &h, const CsrView &A, const Pattern &N
             RN_LAUNCH("energy_gmres_vec", 3 * nzb, s, gm_axpy_kernel, eg, 256, 0, nz, W.p, vi, H + i * m + j, fl);
         }
         dot(W.p, W.p, nz, sc + 1, s, h.partial.p);
-        RN_LAUNCH("energy_gmres_scalar", 0, s, gm_givens_kernel, 1, 1, 0, m, j, H, cs, sn, g, sc, fl);
+        RN_LAUNCH("energy_gmres_scalar", 0, s, gm_givens_kernel, 1, 1, 0, m, j, H, cs, sn, g, sc, fl, kGmresBreak);
         if (j + 1 < m + 1) {
             d2d(V.p + (int64_t)(j + 1) * nz, W.p, nz, s);
             RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel, eg, 256, 0, nz, V.p + (int64_t)(j + 1) * nz,

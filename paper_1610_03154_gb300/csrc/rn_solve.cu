@@ -355,20 +355,24 @@ void apply_cycle(rn_hierarchy &h, const double *rhs, double *out) {
     rn_level &L0 = *h.lev[0];
     const int64_t n = L0.A.n;
     if (!h.graph_exec) {
+        const int64_t before = launches_so_far();
         RN_CUDA_CHECK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         try {
             cycle_direct(h, h.graph_in, h.graph_out);
         } catch (...) {
-            cudaGraph_t g;
+            cudaGraph_t g = nullptr;
             cudaStreamEndCapture(s, &g);
             if (g) cudaGraphDestroy(g);
             throw;
         }
         RN_CUDA_CHECK(cudaStreamEndCapture(s, &h.graph));
         RN_CUDA_CHECK(cudaGraphInstantiate(&h.graph_exec, h.graph, 0));
+        h.graph_kernels = launches_so_far() - before;
+        add_launches(-h.graph_kernels);  // captured, not launched
     }
     if (rhs != h.graph_in) d2d(const_cast<double *>(h.graph_in), rhs, n, s);
     RN_CUDA_CHECK(cudaGraphLaunch(h.graph_exec, s));
+    add_launches(h.graph_kernels);
     if (out != h.graph_out) d2d(out, h.graph_out, n, s);
 }
 

@@ -211,7 +211,8 @@ masked_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t 
     double dot_acc = 0.0;
     for (int32_t i = blockIdx.x * GPB + g; i < n; i += gridDim.x * GPB) {
         const int32_t cs = crp[i], ce = crp[i + 1];
-        if (PROJ && rowtype[i] != 0) {
+        // fixed rows, and one-entry rows whose constraint space is exactly {0}
+        if (PROJ && (rowtype[i] != 0 || ce - cs == 1)) {
             for (int32_t q = cs + lane; q < ce; q += G) cval[q] = 0.0;
             continue;
         }

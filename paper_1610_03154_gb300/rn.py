@@ -75,6 +75,8 @@ def _load():
     L.rn_profile_enable.argtypes = [C.c_int]
     L.rn_profile_reset.argtypes = []
     L.rn_profile_read.argtypes = [P(rn_kernel_stat), C.c_int, P(C.c_int)]
+    L.rn_kernel_launches.argtypes = []
+    L.rn_kernel_launches.restype = C.c_int64
     L.rn_last_error.restype = C.c_char_p
     L.rn_status_string.argtypes = [C.c_int]
     L.rn_status_string.restype = C.c_char_p
@@ -97,6 +99,7 @@ rn_profile_reset = lib.rn_profile_reset
 rn_profile_read = lib.rn_profile_read
 rn_last_error = lib.rn_last_error
 rn_status_string = lib.rn_status_string
+rn_kernel_launches = lib.rn_kernel_launches
 
 
 class RNError(RuntimeError):

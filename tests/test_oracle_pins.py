@@ -590,3 +590,23 @@ def test_operator_and_cycle_complexity_formulas(oracle):
     assert st["oc"] == sum(nnz) / nnz[0]  # eq. oc
     cc = sum(3 * L.A.nnz + L.P.nnz + L.R.nnz for L in h.levels[:-1]) / nnz[0]  # eq. cc, V(1,1)
     assert st["cc"] == cc
+
+
+def test_single_entry_rows_have_empty_constraint_space(oracle):
+    # a free row whose pattern is only its own aggregate cannot move: U Bc = 0
+    # on one entry forces U = 0, so energy minimisation returns T unchanged
+    A = PR.poisson5(9).to_scipy()
+    lev = _setup_level(oracle, A, 0)  # d = 0: N = C, one entry per aggregated row
+    assert np.all(np.diff(lev["N"].indptr)[lev["agg"] >= 0] == 1)
+    P, trace = oracle.energy_min_cg(A, lev["T"], lev["rt"], lev["Bc"], 6)
+    assert np.array_equal(P.toarray(), lev["T"].toarray())
+    Pg, res = oracle.energy_min_gmres(A, lev["T"], lev["rt"], lev["Bc"], 3)
+    assert np.array_equal(Pg.toarray(), lev["T"].toarray())
+
+
+def test_energy_monotone_on_every_level(oracle):
+    pr = PR.aniso_problem(96)
+    h = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    for L in h.levels[:-1]:
+        P, tr = oracle.energy_min_cg(L.A, L.T, L.rowtype, L.Bc, 6)
+        assert np.all(np.diff(tr) <= 1e-12 * abs(tr[0])), tr
