@@ -172,6 +172,29 @@ def reference_arm(args):
     return 0
 
 
+def profile_step(args):
+    """A bounded run of the same workload for profilers: setup, then a fixed
+    number of outer iterations (the solve stops at --profile-iters)."""
+    import torch
+
+    from paper_1610_03154_gb300 import rn
+
+    dev = torch.device("cuda", 0)
+    pr = PR.aniso_problem(args.ne)
+    A = pr.A
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rp, ci, va, Bd, bd = t(A.rowptr), t(A.col), t(A.val), t(pr.B.reshape(-1)), t(pr.b)
+    p = rn.params_from_config(pr.params, precision=rn.RN_MIXED if args.precision == "mixed" else rn.RN_FP64,
+                              outer=rn.RN_OUTER_CG, use_graphs=0)
+    h = rn.Hierarchy(rp, ci, va, Bd, params=p)
+    x = torch.zeros_like(bd)
+    info = h.solve(bd, x, rtol=1e-8, maxit=args.profile_iters, raise_on_notconv=False)
+    h.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_step": True, "iters": info["iters"], "rel_res": info["rel_res"]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,9 +204,14 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--ne", type=int, default=WORKLOAD_NE, help="elements per side (default: the 1024^2 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="one setup + --profile-iters outer iterations and nothing else (for ncu captures)")
+    ap.add_argument("--profile-iters", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_step:
+        return profile_step(args)
 
     import torch
 

@@ -140,6 +140,23 @@ rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x);
 /* Release everything the hierarchy owns.  NULL is a no-op. */
 void rn_free(rn_hierarchy *h);
 
+/* Constrained energy minimisation of one transfer operator on a fixed pattern
+ * (Alg. 3 'improve'; Sec. 3.6 with the row projection of eq. Tproj; Sec. 4,
+ * Lemma th:cg): starting from the values P (in/out, nnz(N) entries on the
+ * pattern of N), run `sweeps` iterations of CG (method RN_ENERGY_CG; Jacobi
+ * row scaling when precond != 0) or GMRES (RN_ENERGY_GMRES) on the operator
+ * X -> Proj(Mask_N(A X)), which keeps P on N, keeps root rows fixed and keeps
+ * P Bc unchanged.
+ *   A        n x n CSR (device), sorted columns, nonzero diagonal;
+ *   N        n x n_c pattern (device CSR; N->val is ignored), sorted columns;
+ *   rowtype  n entries (device): 0 free, 1 root (fixed), 2 unaggregated (fixed);
+ *   Bc       n_c coarse candidates (device).
+ * Work runs on `stream` (NULL: a stream the call creates); scratch comes from
+ * the stream-ordered allocator.  Returns RN_EINVAL for bad sizes or a zero
+ * diagonal; P is unchanged on error. */
+rn_status rn_energy_min(const rn_csr *A, const rn_csr *N, const int32_t *rowtype, const double *Bc, double *P,
+                        int sweeps, int method, int precond, void *stream);
+
 /* Level sizes and the complexities of Sec. 2.4 (eq. oc, eq. cc). */
 rn_status rn_hierarchy_stats(const rn_hierarchy *h, rn_stats *s);
 

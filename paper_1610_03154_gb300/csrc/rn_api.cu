@@ -173,8 +173,69 @@ extern "C" rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int l
 extern "C" rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x) {
     RN_API_BEGIN
     if (!h || !b || !x) rn::fail(RN_EINVAL, "null argument");
-    rn::apply_cycle(*h, b, x);
+    rn::cycle_checked(*h, b, x);
     RN_CUDA_CHECK(cudaStreamSynchronize(h->s));
+    return RN_OK;
+    RN_API_END
+}
+
+namespace {
+// A stream the call owns when the caller passes none (blocking, so it stays
+// ordered with the legacy default stream).
+struct CallStream {
+    cudaStream_t s = nullptr;
+    bool own = false;
+    explicit CallStream(void *given) {
+        s = static_cast<cudaStream_t>(given);
+        if (!s) {
+            RN_CUDA_CHECK(cudaStreamCreate(&s));
+            own = true;
+        }
+    }
+    ~CallStream() {
+        if (own) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+};
+}  // namespace
+
+extern "C" rn_status rn_energy_min(const rn_csr *A, const rn_csr *N, const int32_t *rowtype, const double *Bc,
+                                   double *P, int sweeps, int method, int precond, void *stream) {
+    RN_API_BEGIN
+    using rn::fail;
+    if (!A || !N || !rowtype || !Bc || !P) fail(RN_EINVAL, "null argument");
+    if (A->n_rows <= 0 || A->n_rows != A->n_cols || !A->rowptr || !A->col || !A->val) fail(RN_EINVAL, "A");
+    if (A->nnz <= 0 || A->nnz > INT32_MAX - 1) fail(RN_EINVAL, "nnz(A) out of range");
+    if (N->n_rows != A->n_rows || N->n_cols < 1 || N->nnz < 0 || N->nnz > INT32_MAX - 1 || !N->rowptr ||
+        (N->nnz > 0 && !N->col))
+        fail(RN_EINVAL, "pattern N does not match A");
+    if (sweeps < 0 || sweeps > 1000) fail(RN_EINVAL, "sweeps must be in [0, 1000]");
+    if (method != RN_ENERGY_CG && method != RN_ENERGY_GMRES) fail(RN_EINVAL, "method");
+    CallStream cs(stream);
+    cudaStream_t s = cs.s;
+    const int32_t n = A->n_rows;
+    rn::DVec<double> diag(n, s), partial(2 * rn::kReduceBlocks, s), sc(64, s);
+    rn::DVec<unsigned> counter(4, s);
+    rn::DVec<int32_t> fl(16, s);
+    RN_CUDA_CHECK(cudaMemsetAsync(counter.p, 0, 4 * sizeof(unsigned), s));
+    RN_CUDA_CHECK(cudaMemsetAsync(fl.p, 0, 16 * sizeof(int32_t), s));
+    RN_CUDA_CHECK(cudaMemsetAsync(sc.p, 0, 64 * sizeof(double), s));
+    rn::CsrView Av{n, n, A->nnz, A->rowptr, A->col, A->val};
+    rn::extract_diag(Av, diag.p, fl.p + 4, s);
+    if (rn::read_scalar(fl.p + 4, s)) fail(RN_EINVAL, "missing or zero diagonal");
+    rn::EmCtx c;
+    c.s = s;
+    c.partial = partial.p;
+    c.counter = counter.p;
+    c.sc = sc.p;
+    c.fl = fl.p;
+    c.precond = precond ? 1 : 0;
+    c.method = method;
+    rn::Pattern pat{n, N->n_cols, N->nnz, N->rowptr, N->col};
+    rn::energy_min(c, Av, pat, P, rowtype, Bc, diag.p, sweeps);
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
     return RN_OK;
     RN_API_END
 }

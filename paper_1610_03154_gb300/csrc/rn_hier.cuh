@@ -30,7 +30,8 @@ struct rn_hierarchy {
     std::vector<std::unique_ptr<rn_level>> lev;  // lev.back() is the coarsest
     int32_t nL = 0;
     rn::DVec<double> Ainv;                        // coarsest inverse, row-major nL x nL
-    rn::DVec<double> partial;                     // block partial sums
+    rn::DVec<double> partial;                     // block partial sums (2 x kReduceBlocks)
+    rn::DVec<unsigned> counters;                  // arrival counter of the grid reductions (kept at 0)
     rn::DVec<double> scal;                        // device scalars
     rn::DVec<int32_t> iflags;                     // device int flags
     // outer-iteration vectors (level-0 size)
@@ -51,8 +52,30 @@ struct rn_hierarchy {
 namespace rn {
 // setup (rn_setup.cu)
 void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const double *Bhat0);
+
+struct Pattern {  // borrowed view of a fixed interpolation pattern
+    int32_t n, nc;
+    int64_t nnz;
+    const int32_t *rp, *col;
+};
+// Context of one energy minimisation: stream, reduction scratch, scalar block
+// (>= 8 doubles), flags (>= 2 ints), settings, and optional CG workspaces
+// (nnz(N) doubles each; allocated internally when null).
+struct EmCtx {
+    cudaStream_t s = nullptr;
+    double *partial = nullptr;
+    unsigned *counter = nullptr;
+    double *sc = nullptr;
+    int32_t *fl = nullptr;
+    int precond = 1;
+    int method = RN_ENERGY_CG;
+    double *R = nullptr, *Dd = nullptr, *W = nullptr;
+};
+void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                const double *Bc, const double *diag, int sweeps);
 // solve (rn_solve.cu)
 void prepare_solve(rn_hierarchy &h);
 rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int maxit, rn_solve_info *info);
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out);
+void cycle_checked(rn_hierarchy &h, const double *rhs, double *out);  // + staging-error check
 }  // namespace rn

@@ -81,6 +81,8 @@ struct DCsr {
     DVec<int32_t> rowptr, col;
     DVec<double> val;
     DVec<float> val32;
+    int32_t maxlen = 0;     // longest row (set before solving)
+    int tile_group = 0;     // lanes per row of the staged SpMV (0: rows too long, unstaged kernel)
 };
 
 // Borrowed view of a CSR (device pointers).
@@ -143,11 +145,14 @@ T read_scalar(const T *dptr, cudaStream_t s) {
 // the total (one device->host read).  Fails with RN_EINTERNAL if the total
 // does not fit in int32.
 int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t s);
-// Deterministic two-stage dot products: partial sums per block in fixed order.
-constexpr int kReduceBlocks = 1216;   // partial-sum slots (8 x 152 SMs)
-void dot(const double *x, const double *y, int64_t n, double *result, cudaStream_t s, double *partial);
-// *result = sum of partial[0..nb) in a fixed order (one block).
-void reduce_partials(const double *partial, int nb, double *result, cudaStream_t s);
+// Deterministic grid reductions: per-block partial sums, summed in block order
+// by the last block (see grid_finish).  Grids of reducing kernels never exceed
+// kReduceBlocks blocks.
+constexpr int kReduceBlocks = 1216;   // partial-sum slots per value (8 x 152 SMs)
+struct Fin;
+// *result = <x, y>
+void dot(const double *x, const double *y, int64_t n, double *result, cudaStream_t s, double *partial,
+         unsigned *counter);
 void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
 void fill_f64(double *p, double v, int64_t n, cudaStream_t s);
 // diag[i] = a_ii (fails RN_EINVAL through *bad when a diagonal is missing or zero)
@@ -173,7 +178,7 @@ struct ProjArgs {
 };
 void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, int32_t nc,
                          const double *X, double *W, const ProjArgs &pa, double scale, const double *Y,
-                         double *dot_out, double *partial, cudaStream_t s);
+                         const Fin &fin, cudaStream_t s);
 
 // --------------------------------------------------------------- misc
 std::string fmt(const char *f, ...);
@@ -227,5 +232,91 @@ __device__ __forceinline__ double block_sum(double v, double *smem32) {
     }
     __syncthreads();
     return r;
+}
+
+// What the last block does with the finished sums of a grid reduction.
+enum FinMode { FIN_NONE = 0, FIN_STORE = 1, FIN_CG_RHO = 2, FIN_CG_DW = 3, FIN_RZ = 4 };
+struct Fin {
+    int mode = FIN_NONE;
+    double *partial = nullptr;   // >= 2 * kReduceBlocks slots
+    unsigned *counter = nullptr; // zero between launches (the last block resets it)
+    double *out = nullptr;       // FIN_STORE: out[0] = s0 (and out[1] = s1 when two sums)
+    double *sc = nullptr;        // scalar block of the CG recurrences
+    int32_t *fl = nullptr;       // fl[0]: energy-minimisation "done"
+    int it = 0;
+    double stop = 0.0;
+};
+
+__device__ __forceinline__ void apply_fin(const Fin &f, const double *s, int nv) {
+    switch (f.mode) {
+        case FIN_STORE:
+            f.out[0] = s[0];
+            if (nv > 1) f.out[1] = s[1];
+            break;
+        case FIN_CG_RHO: {  // energy CG: rho = <R, D^-1 R>; stop test; beta
+            if (f.fl[0]) return;
+            const double r = s[0];
+            if (f.it == 0) f.sc[1] = r;
+            if (r == 0.0 || r <= f.stop * f.sc[1]) {
+                f.fl[0] = 1;
+                return;
+            }
+            f.sc[2] = (f.it == 0) ? 0.0 : r / f.sc[0];
+            f.sc[0] = r;
+            break;
+        }
+        case FIN_CG_DW: {  // energy CG: <D, W>; breakdown test; alpha
+            if (f.fl[0]) return;
+            f.sc[3] = s[0];
+            if (!(s[0] > 0.0)) {
+                f.fl[0] = 1;
+                return;
+            }
+            f.sc[4] = f.sc[0] / s[0];
+            break;
+        }
+        case FIN_RZ:  // outer CG: keep the previous <r,z>, store <r,z> and <z, r_old>
+            f.sc[14] = f.sc[9];
+            f.sc[9] = s[0];
+            if (nv > 1) f.sc[11] = s[1];
+            break;
+        default: break;
+    }
+}
+
+// Deterministic grid reduction of NV per-thread values.  Every block writes
+// its totals to f.partial[k * kReduceBlocks + block]; the block that arrives
+// last sums them in block order (a fixed order, whichever block is last) and
+// applies the finisher in thread 0.  All threads of every block must call it.
+template <int BLOCK, int NV>
+__device__ __forceinline__ void grid_finish(const double (&v)[NV], const Fin &f, double *smem32) {
+    if (f.mode == FIN_NONE) return;
+    __shared__ int am_last;
+    double t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) t[k] = block_sum<BLOCK>(v[k], smem32);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) f.partial[k * kReduceBlocks + blockIdx.x] = t[k];
+        __threadfence();
+        const unsigned prev = atomicAdd(f.counter, 1u);
+        am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        double s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double a = 0.0;
+            for (int i = threadIdx.x; i < (int)gridDim.x; i += BLOCK) a += __ldcg(&f.partial[k * kReduceBlocks + i]);
+            s[k] = block_sum<BLOCK>(a, smem32);
+        }
+        if (threadIdx.x == 0) {
+            apply_fin(f, s, NV);
+            *f.counter = 0u;
+            __threadfence();
+        }
+    }
 }
 }  // namespace rn

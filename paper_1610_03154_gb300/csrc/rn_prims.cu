@@ -48,6 +48,10 @@ void *dmalloc(size_t bytes, cudaStream_t s) {
         g_pool_configured = true;
     }
     void *p = nullptr;
+    // every buffer gets >= 256 bytes of tail slack: the tile kernels copy CSR
+    // segments with 16-byte-granular bulk copies that may end up to 15 bytes
+    // past the last element (the slack is never interpreted)
+    bytes = ((bytes + 255) / 256) * 256 + 256;
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -295,33 +299,24 @@ int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t
 // --------------------------------------------------------------------- reductions
 constexpr int kRedThreads = 256;
 
-__global__ void dot_partial(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
-                            double *__restrict__ partial) {
+__global__ void dot_kernel(const double *__restrict__ x, const double *__restrict__ y, int64_t n, Fin fin) {
     __shared__ double sm[32];
-    double v = 0.0;
+    double v[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v += x[i] * y[i];
-    double t = block_sum<kRedThreads>(v, sm);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+        v[0] = fma(x[i], y[i], v[0]);
+    grid_finish<kRedThreads, 1>(v, fin, sm);
 }
 
-__global__ void reduce_final(const double *__restrict__ partial, int nb, double *__restrict__ result) {
-    __shared__ double sm[32];
-    double v = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += partial[i];
-    double t = block_sum<1024>(v, sm);
-    if (threadIdx.x == 0) *result = t;
-}
-
-void reduce_partials(const double *partial, int nb, double *result, cudaStream_t s) {
-    RN_LAUNCH("reduce_final", 8.0 * nb, s, reduce_final, 1, 1024, 0, partial, nb, result);
-}
-
-void dot(const double *x, const double *y, int64_t n, double *result, cudaStream_t s, double *partial) {
+void dot(const double *x, const double *y, int64_t n, double *result, cudaStream_t s, double *partial,
+         unsigned *counter) {
     int nb = grid_for(n, kRedThreads * 4, 8);
     if (nb > kReduceBlocks) nb = kReduceBlocks;
-    RN_LAUNCH("dot", 16.0 * n, s, dot_partial, nb, kRedThreads, 0, x, y, n, partial);
-    RN_LAUNCH("reduce_final", 8.0 * nb, s, reduce_final, 1, 1024, 0, partial, nb, result);
+    Fin f;
+    f.mode = FIN_STORE;
+    f.partial = partial;
+    f.counter = counter;
+    f.out = result;
+    RN_LAUNCH("dot", 16.0 * n, s, dot_kernel, nb, kRedThreads, 0, x, y, n, f);
 }
 
 // --------------------------------------------------------------------- elementwise

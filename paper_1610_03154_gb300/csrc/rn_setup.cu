@@ -313,33 +313,20 @@ __global__ void tentative_kernel(int32_t n, const int32_t *__restrict__ rp, cons
 }
 
 // ------------------------------------------------------------------ CG energy minimisation (Sec. 3.6)
-// Device scalars: sc[0] rho, sc[1] rho0, sc[2] beta, sc[3] <Dd,W>, sc[4] alpha, sc[5] new rho.
-// fl[0] = done.
+// Device scalars: sc[0] rho, sc[1] rho0, sc[2] beta, sc[3] <Dd,W>, sc[4] alpha; fl[0] = done.
+// The scalar recurrences run in the finishing block of each reduction (Fin).
 template <int G>
 __global__ void __launch_bounds__(kT)
 cg_rho_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ diag,
-              int precond, double *__restrict__ partial) {
+              int precond, Fin fin) {
     __shared__ double sm[32];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    double acc = 0.0;
+    double acc[1] = {0.0};
     for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
         const double d = precond ? diag[i] : 1.0;
-        for (int32_t q = rp[i] + lane; q < rp[i + 1]; q += G) acc = fma(R[q], R[q] / d, acc);
+        for (int32_t q = rp[i] + lane; q < rp[i + 1]; q += G) acc[0] = fma(R[q], R[q] / d, acc[0]);
     }
-    double t = block_sum<kT>(acc, sm);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
-}
-
-__global__ void cg_finalize_rho_kernel(double *sc, int32_t *fl, int it, double stop) {
-    if (fl[0]) return;
-    const double r = sc[5];
-    if (it == 0) sc[1] = r;
-    if (r == 0.0 || r <= stop * sc[1]) {
-        fl[0] = 1;
-        return;
-    }
-    sc[2] = (it == 0) ? 0.0 : r / sc[0];
-    sc[0] = r;
+    grid_finish<kT, 1>(acc, fin, sm);
 }
 
 template <int G>
@@ -359,26 +346,16 @@ cg_dd_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict
     }
 }
 
-__global__ void cg_finalize_dw_kernel(double *sc, int32_t *fl) {
-    if (fl[0]) return;
-    if (!(sc[3] > 0.0)) {
-        fl[0] = 1;
-        return;
-    }
-    sc[4] = sc[0] / sc[3];
-}
-
 template <int G>
 __global__ void __launch_bounds__(kT)
 cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, double *__restrict__ P, double *__restrict__ R,
                  const double *__restrict__ Dd, const double *__restrict__ W, const double *__restrict__ diag,
-                 int precond, const double *__restrict__ sc, const int32_t *__restrict__ fl,
-                 double *__restrict__ partial) {
+                 int precond, const double *__restrict__ sc, const int32_t *__restrict__ fl, Fin fin) {
     __shared__ double sm[32];
     const bool done = fl[0] != 0;
     const double alpha = sc[4];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    double acc = 0.0;
+    double acc[1] = {0.0};
     if (!done) {
         for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
             const double d = precond ? diag[i] : 1.0;
@@ -386,12 +363,11 @@ cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, double *__restrict__
                 P[q] = P[q] + alpha * Dd[q];
                 const double r = R[q] - alpha * W[q];
                 R[q] = r;
-                acc = fma(r, r / d, acc);
+                acc[0] = fma(r, r / d, acc[0]);
             }
         }
     }
-    double t = block_sum<kT>(acc, sm);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    grid_finish<kT, 1>(acc, fin, sm);  // the finisher ignores the sum once done is set
 }
 
 // ------------------------------------------------------------------ GMRES energy minimisation (Sec. 4.2)
@@ -635,68 +611,75 @@ static int pick_g(double avg) {
         gridp = grid_;                                                                                    \
     } while (0)
 
-struct Pattern {  // borrowed view of a fixed pattern
-    int32_t n, nc;
-    int64_t nnz;
-    const int32_t *rp, *col;
-};
-
 // CG energy minimisation of the values X (in/out) on pattern N.
-static void energy_min_cg(rn_hierarchy &h, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
-                          const double *Bc, const double *diag, int sweeps) {
-    cudaStream_t s = h.s;
-    const int precond = h.p.energy_precond;
-    DVec<double> R(N.nnz, s), Dd(N.nnz, s), W(N.nnz, s);
-    double *sc = h.scal.p;
-    int32_t *fl = h.iflags.p;
+void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                   const double *Bc, const double *diag, int sweeps) {
+    cudaStream_t s = c.s;
+    const int precond = c.precond;
+    DVec<double> Rv, Dv, Wv;
+    double *R = c.R, *Dd = c.Dd, *W = c.W;
+    if (!R) { Rv.alloc(N.nnz, s); R = Rv.p; }
+    if (!Dd) { Dv.alloc(N.nnz, s); Dd = Dv.p; }
+    if (!W) { Wv.alloc(N.nnz, s); W = Wv.p; }
+    double *sc = c.sc;
+    int32_t *fl = c.fl;
     fill_i32(fl, 0, 1, s);
     ProjArgs pa{rowtype, Bc};
     const int G = pick_g(N.n ? (double)N.nnz / N.n : 1.0);
     int gridp = 1;
+    (void)gridp;
     const double nzb = 8.0 * N.nnz, rpb = 4.0 * (N.n + 1), db = 8.0 * N.n;
-    masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, R.p, pa, -1.0, nullptr, nullptr, h.partial.p, s);
-    RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R.p, diag, precond, h.partial.p);
-    reduce_partials(h.partial.p, gridp, sc + 5, s);
+    Fin fin;
+    fin.partial = c.partial;
+    fin.counter = c.counter;
+    fin.sc = sc;
+    fin.fl = fl;
+    fin.stop = kCgStop;
+    const Fin none;
+    masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, R, pa, -1.0, nullptr, none, s);
+    fin.mode = FIN_CG_RHO;
+    fin.it = 0;
+    RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R, diag, precond, fin);
     for (int it = 0; it < sweeps; it++) {
-        RN_LAUNCH("energy_cg_scalar", 0, s, cg_finalize_rho_kernel, 1, 1, 0, sc, fl, it, kCgStop);
-        RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R.p, diag, precond,
-                       sc, fl, it == 0 ? 1 : 0, Dd.p);
-        masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, Dd.p, W.p, pa, 1.0, Dd.p, sc + 3, h.partial.p, s);
-        RN_LAUNCH("energy_cg_scalar", 0, s, cg_finalize_dw_kernel, 1, 1, 0, sc, fl);
-        RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R.p, Dd.p,
-                       W.p, diag, precond, sc, fl, h.partial.p);
-        reduce_partials(h.partial.p, gridp, sc + 5, s);
+        RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R, diag, precond,
+                       sc, fl, it == 0 ? 1 : 0, Dd);
+        fin.mode = FIN_CG_DW;
+        masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, Dd, W, pa, 1.0, Dd, fin, s);
+        fin.mode = FIN_CG_RHO;
+        fin.it = it + 1;
+        RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R, Dd, W, diag,
+                       precond, sc, fl, fin);
     }
 }
 
 // GMRES energy minimisation (m Arnoldi steps, modified Gram-Schmidt).
-static void energy_min_gmres(rn_hierarchy &h, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
-                             const double *Bc, int m) {
+void energy_min_gmres(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                      const double *Bc, int m) {
     if (m <= 0) return;
-    cudaStream_t s = h.s;
+    cudaStream_t s = c.s;
     const int64_t nz = N.nnz;
     DVec<double> V((size_t)(m + 1) * (nz > 0 ? nz : 1), s), W(nz > 0 ? nz : 1, s);
     DVec<double> Hm((size_t)(m + 1) * m + 4 * (m + 1), s);
     fill_f64(Hm.p, 0.0, (int64_t)Hm.n, s);
     double *H = Hm.p, *cs = H + (m + 1) * m, *sn = cs + (m + 1), *g = sn + (m + 1), *y = g + (m + 1);
-    double *sc = h.scal.p;
-    int32_t *fl = h.iflags.p;
+    double *sc = c.sc;
+    int32_t *fl = c.fl;
     ProjArgs pa{rowtype, Bc};
     const int eg = grid_for(nz, 1024);
     const double nzb = 8.0 * nz;
-    masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, V.p, pa, -1.0, nullptr, nullptr, h.partial.p, s);
-    dot(V.p, V.p, nz, sc + 1, s, h.partial.p);
+    masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, V.p, pa, -1.0, nullptr, Fin(), s);
+    dot(V.p, V.p, nz, sc + 1, s, c.partial, c.counter);
     RN_LAUNCH("energy_gmres_scalar", 0, s, gm_start_kernel, 1, 1, 0, sc, fl, g);
     RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel, eg, 256, 0, nz, V.p, sc, fl);
     for (int j = 0; j < m; j++) {
         double *vj = V.p + (int64_t)j * nz;
-        masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, vj, W.p, pa, 1.0, nullptr, nullptr, h.partial.p, s);
+        masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, vj, W.p, pa, 1.0, nullptr, Fin(), s);
         for (int i = 0; i <= j; i++) {
             double *vi = V.p + (int64_t)i * nz;
-            dot(W.p, vi, nz, H + i * m + j, s, h.partial.p);
+            dot(W.p, vi, nz, H + i * m + j, s, c.partial, c.counter);
             RN_LAUNCH("energy_gmres_vec", 3 * nzb, s, gm_axpy_kernel, eg, 256, 0, nz, W.p, vi, H + i * m + j, fl);
         }
-        dot(W.p, W.p, nz, sc + 1, s, h.partial.p);
+        dot(W.p, W.p, nz, sc + 1, s, c.partial, c.counter);
         RN_LAUNCH("energy_gmres_scalar", 0, s, gm_givens_kernel, 1, 1, 0, m, j, H, cs, sn, g, sc, fl, kGmresBreak);
         if (j + 1 < m + 1) {
             d2d(V.p + (int64_t)(j + 1) * nz, W.p, nz, s);
@@ -708,10 +691,22 @@ static void energy_min_gmres(rn_hierarchy &h, const CsrView &A, const Pattern &N
     RN_LAUNCH("energy_gmres_vec", (m + 2) * nzb, s, gm_combine_kernel, eg, 256, 0, nz, m, X, V.p, y, fl);
 }
 
-static void energy_min(rn_hierarchy &h, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
-                       const double *Bc, const double *diag, int sweeps) {
-    if (h.p.energy_method == RN_ENERGY_GMRES) energy_min_gmres(h, A, N, X, rowtype, Bc, sweeps);
-    else energy_min_cg(h, A, N, X, rowtype, Bc, diag, sweeps);
+void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                const double *Bc, const double *diag, int sweeps) {
+    if (c.method == RN_ENERGY_GMRES) energy_min_gmres(c, A, N, X, rowtype, Bc, sweeps);
+    else energy_min_cg(c, A, N, X, rowtype, Bc, diag, sweeps);
+}
+
+static EmCtx ctx_of(rn_hierarchy &h) {
+    EmCtx c;
+    c.s = h.s;
+    c.partial = h.partial.p;
+    c.counter = h.counters.p;
+    c.sc = h.scal.p;
+    c.fl = h.iflags.p;
+    c.precond = h.p.energy_precond;
+    c.method = h.p.energy_method;
+    return c;
 }
 
 static void check_flag(const int32_t *flag, cudaStream_t s, rn_status st, const char *what) {
@@ -757,7 +752,7 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
         d2d(Tkeep->val.p, Pout.val.p, N.nnz, s);
     }
     Pattern pat{n, nc, N.nnz, Pout.rowptr.p, Pout.col.p};
-    energy_min(h, A, pat, Pout.val.p, rowtype, Bc, diag, h.p.n_sweeps);
+    energy_min(ctx_of(h), A, pat, Pout.val.p, rowtype, Bc, diag, h.p.n_sweeps);
     if (h.p.postfilter > 0.0) {
         const double omg = 1.0 - kGuard;
         DVec<int32_t> cnt(n + 1, s);
@@ -776,7 +771,7 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
                   F.val.p, rowtype, Bsm, Bc);
         Pout = std::move(F);
         Pattern pf{n, nc, Pout.nnz, Pout.rowptr.p, Pout.col.p};
-        energy_min(h, A, pf, Pout.val.p, rowtype, Bc, diag, 1);
+        energy_min(ctx_of(h), A, pf, Pout.val.p, rowtype, Bc, diag, 1);
     }
 }
 
@@ -784,7 +779,9 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
     cudaStream_t s = h.s;
     const rn_params &p = h.p;
     const double omg = 1.0 - kGuard;
-    h.partial.alloc(kReduceBlocks, s);
+    h.partial.alloc(2 * kReduceBlocks, s);
+    h.counters.alloc(4, s);
+    RN_CUDA_CHECK(cudaMemsetAsync(h.counters.p, 0, 4 * sizeof(unsigned), s));
     h.scal.alloc(64, s);
     h.iflags.alloc(16, s);
     fill_f64(h.scal.p, 0.0, 64, s);

@@ -7,7 +7,15 @@
 // sizes are fixed after setup, so one application of the cycle is captured
 // in a CUDA graph and replayed.  In mixed precision the cycle runs on FP32
 // shadows of A, P, R and the diagonal; the outer iteration (residual, Krylov
-// vectors, dot products) and the coarsest solve stay FP64.
+// vectors, dot products) and the coarsest solve stay FP64, and the level-0
+// kernels read the FP64 right-hand side and write the FP64 result directly.
+//
+// SpMV-family kernels stream the CSR arrays through shared memory: each
+// persistent CTA walks tiles of 256/G rows; thread 0 issues TMA bulk copies
+// (cp.async.bulk, completion counted on an mbarrier) of the tile's column and
+// value segments into a double buffer, so the next tile's matrix data is in
+// flight while the current one is computed.  Only x is gathered from global
+// memory (it is small enough to stay in L2).
 #include <algorithm>
 #include <cmath>
 
@@ -15,139 +23,308 @@
 
 namespace rn {
 
-constexpr int kS = 256;  // threads per block, SpMV family
+constexpr int kS = 256;           // threads per block, SpMV family
+constexpr int kTileNnz = 3072;    // matrix entries per shared-memory stage
+constexpr int kTileSlack = 8;     // room for 16-byte alignment of the bulk copies
+constexpr uint32_t kMaxSpin = 1u << 24;  // bound on mbarrier polls before giving up
 
-enum SpOp { OP_SPMV = 0, OP_SPMV_ADD = 1, OP_RESID = 2, OP_JACOBI = 3 };
+enum SpOp { OP_SPMV = 0, OP_SPMV_ADD = 1, OP_RESID = 2, OP_JACOBI = 3, OP_SPMV_DOT = 4 };
 
-// Row-group SpMV family: G lanes per row, rows contiguous per block.
-//   OP_SPMV      y = A x
-//   OP_SPMV_ADD  y += A x            (prolongation: A = P)
-//   OP_RESID     y = b - A x         (+ sum y^2 into partial)
-//   OP_JACOBI    y = x + omega (b - A x) / diag
-template <typename T, int G, int OP>
+// ------------------------------------------------------------------ mbarrier / bulk-copy helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t k = 0; k < kMaxSpin; k++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <typename T, typename TB, typename TO, int OP>
+__device__ __forceinline__ void spmv_epilogue(int32_t i, T acc, const T *__restrict__ x, const TB *__restrict__ b,
+                                              const T *__restrict__ diag, T omega, TO *__restrict__ y, double &red) {
+    if (OP == OP_SPMV) {
+        y[i] = (TO)acc;
+    } else if (OP == OP_SPMV_ADD) {
+        y[i] = (TO)((T)y[i] + acc);
+    } else if (OP == OP_RESID) {
+        const T r = (T)b[i] - acc;
+        y[i] = (TO)r;
+        red += (double)r * (double)r;
+    } else if (OP == OP_JACOBI) {
+        y[i] = (TO)(x[i] + omega * ((T)b[i] - acc) / diag[i]);
+    } else {  // OP_SPMV_DOT
+        y[i] = (TO)acc;
+        red += (double)x[i] * (double)acc;
+    }
+}
+
+// Tile kernel: G lanes per row, RPT = 256/G rows per tile.  The tile's row
+// pointers and its matrix segment (<= kTileNnz entries; guaranteed by the
+// host's choice of G) are staged by bulk copies into a two-stage buffer.
+// Thread 0 keeps the next tile's copies in flight and prefetches the bounds
+// of the tile after that.  err[0] is set if an mbarrier wait gives up.
+template <typename T, typename TB, typename TO, int G, int OP>
 __global__ void __launch_bounds__(kS)
-spmv_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const T *__restrict__ val,
-            const T *__restrict__ x, const T *__restrict__ b, const T *__restrict__ diag, T omega, T *__restrict__ y,
-            double *__restrict__ partial) {
+spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                 const T *__restrict__ val, const T *__restrict__ x, const TB *__restrict__ b,
+                 const T *__restrict__ diag, T omega, TO *__restrict__ y, Fin fin, int32_t *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int SL = kTileNnz + kTileSlack;
+    constexpr int RPT = kS / G;
+    constexpr int RL = RPT + 8;  // staged row pointers per stage (RPT + 1, rounded to 16 bytes)
+    constexpr int VA = 16 / (int)sizeof(T);
+    int32_t *scol = reinterpret_cast<int32_t *>(smem_raw);
+    int32_t *srp = scol + 2 * SL;
+    T *sval = reinterpret_cast<T *>(smem_raw + (2 * SL + 2 * RL) * sizeof(int32_t));
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sm[32];
-    const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    const unsigned mask = group_mask<G>();
-    double nrm = 0.0;
-    for (int32_t i = blockIdx.x * (kS / G) + g; i < n; i += gridDim.x * (kS / G)) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t pend = 0u;             // thread 0: bit s = copies into stage s issued, not yet waited for
+    int32_t be0 = 0, be1 = 0;       // thread 0: nnz bounds of the next tile to issue
+    auto load_bounds = [&](int t) {
+        if (t < ntiles) {
+            be0 = rp[t * RPT];
+            be1 = rp[min(n, t * RPT + RPT)];
+        }
+    };
+    auto issue = [&](int stage, int t) {
+        const int32_t r0 = t * RPT;
+        const int32_t r1 = min(n, r0 + RPT);
+        const int32_t c0 = be0 & ~3, c1 = (be1 + 3) & ~3;
+        const int32_t v0 = be0 & ~(VA - 1), v1 = (be1 + VA - 1) & ~(VA - 1);
+        const uint32_t cb = (uint32_t)(c1 - c0) * 4u, vb = (uint32_t)(v1 - v0) * (uint32_t)sizeof(T);
+        const uint32_t rb = (uint32_t)(((r1 - r0 + 1) + 3) & ~3) * 4u;  // r0 is a multiple of 8: aligned
+        mbar_expect_tx(&bar[stage], cb + vb + rb);
+        bulk_g2s(srp + stage * RL, rp + r0, rb, &bar[stage]);
+        if (cb) bulk_g2s(scol + stage * SL, col + c0, cb, &bar[stage]);
+        if (vb) bulk_g2s(sval + stage * SL, val + v0, vb, &bar[stage]);
+        pend |= 1u << stage;
+    };
+    double red[1] = {0.0};
+    uint32_t parity = 0u;  // bit s = phase parity to wait for on stage s
+    bool failed = false;
+    int st = 0;
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) {
+        load_bounds(tile);
+        issue(0, tile);
+        load_bounds(tile + gridDim.x);
+    }
+    for (; tile < ntiles; tile += gridDim.x, st ^= 1) {
+        const int nxt = tile + gridDim.x;
+        if (tid == 0 && nxt < ntiles) {
+            fence_proxy_async();  // earlier generic reads of that stage come before the async writes
+            issue(st ^ 1, nxt);
+            load_bounds(nxt + gridDim.x);  // lands while this tile is computed
+        }
+        const int32_t r0 = tile * RPT;
+        const int32_t row = r0 + tid / G;
+        const int lane = tid % G;
+        const bool live = row < min(n, r0 + RPT);
+        // epilogue operands: issue their loads before waiting on the stage
+        T xi = T(0), di = T(1);
+        TB bi = TB(0);
+        TO yi = TO(0);
+        if (live && lane == 0) {
+            if (OP == OP_JACOBI || OP == OP_SPMV_DOT) xi = x[row];
+            if (OP == OP_RESID || OP == OP_JACOBI) bi = b[row];
+            if (OP == OP_JACOBI) di = diag[row];
+            if (OP == OP_SPMV_ADD) yi = y[row];
+        }
+        const bool ok = mbar_wait_bounded(&bar[st], (parity >> st) & 1u);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        parity ^= 1u << st;
+        if (tid == 0) pend &= ~(1u << st);
+        const int32_t *srow = srp + st * RL;
+        const int32_t e0 = srow[0];
+        const int32_t c0 = e0 & ~3, v0 = e0 & ~(VA - 1);
+        const int32_t *sc = scol + st * SL;
+        const T *sv = sval + st * SL;
         T acc = T(0);
-        const int32_t e1 = rp[i + 1];
-        for (int32_t e = rp[i] + lane; e < e1; e += G) acc = fma(val[e], x[col[e]], acc);
+        if (live) {
+            // staged entry k of the matrix sits at sc[k - c0] / sv[k - v0]
+            const int32_t s = srow[tid / G], e = srow[tid / G + 1];
+            int32_t k = s + lane;
+            for (; k + 3 * G < e; k += 4 * G) {  // four independent gathers in flight
+                const int32_t j0 = sc[k - c0], j1 = sc[k + G - c0], j2 = sc[k + 2 * G - c0], j3 = sc[k + 3 * G - c0];
+                const T a0 = sv[k - v0], a1 = sv[k + G - v0], a2 = sv[k + 2 * G - v0], a3 = sv[k + 3 * G - v0];
+                const T x0 = x[j0], x1 = x[j1], x2 = x[j2], x3 = x[j3];
+                acc = fma(a0, x0, acc);
+                acc = fma(a1, x1, acc);
+                acc = fma(a2, x2, acc);
+                acc = fma(a3, x3, acc);
+            }
+            for (; k < e; k += G) acc = fma(sv[k - v0], x[sc[k - c0]], acc);
+        }
         if (G > 1) {
+            const unsigned mask = group_mask<G>();
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
         }
-        if (lane == 0) {
-            if (OP == OP_SPMV) y[i] = acc;
-            else if (OP == OP_SPMV_ADD) y[i] += acc;
-            else if (OP == OP_RESID) {
-                const T r = b[i] - acc;
-                y[i] = r;
-                nrm += (double)r * (double)r;
+        if (live && lane == 0) {
+            if (OP == OP_SPMV) {
+                y[row] = (TO)acc;
+            } else if (OP == OP_SPMV_ADD) {
+                y[row] = (TO)((T)yi + acc);
+            } else if (OP == OP_RESID) {
+                const T r = (T)bi - acc;
+                y[row] = (TO)r;
+                red[0] += (double)r * (double)r;
+            } else if (OP == OP_JACOBI) {
+                y[row] = (TO)(xi + omega * ((T)bi - acc) / di);
             } else {
-                y[i] = x[i] + omega * (b[i] - acc) / diag[i];
+                y[row] = (TO)acc;
+                red[0] += (double)xi * (double)acc;
             }
         }
+        __syncthreads();  // this stage is fully read before it is refilled
     }
-    if (OP == OP_RESID && partial) {
-        const double t = block_sum<kS>(nrm, sm);
-        if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    if (failed) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int q = 0; q < 2; q++)
+                if ((pend >> q) & 1u) mbar_wait_bounded(&bar[q], (parity >> q) & 1u);  // let our own copies land
+        }
+        __syncthreads();
     }
+    if (OP == OP_RESID || OP == OP_SPMV_DOT) grid_finish<kS, 1>(red, fin, sm);
 }
 
-template <typename T>
-__global__ void jacobi_zero_kernel(int32_t n, const T *__restrict__ b, const T *__restrict__ diag, T omega,
+// Fallback for matrices with rows too long for a stage: G lanes per row
+// straight from global memory.
+template <typename T, typename TB, typename TO, int G, int OP>
+__global__ void __launch_bounds__(kS)
+spmv_group_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                  const T *__restrict__ val, const T *__restrict__ x, const TB *__restrict__ b,
+                  const T *__restrict__ diag, T omega, TO *__restrict__ y, Fin fin) {
+    __shared__ double sm[32];
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    double red[1] = {0.0};
+    for (int32_t i0 = blockIdx.x * (kS / G); i0 < n; i0 += gridDim.x * (kS / G)) {
+        const int32_t i = i0 + g;
+        T acc = T(0);
+        if (i < n)
+            for (int32_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(val[e], x[col[e]], acc);
+        if (G > 1) {
+            const unsigned mask = group_mask<G>();
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
+        }
+        if (lane == 0 && i < n) spmv_epilogue<T, TB, TO, OP>(i, acc, x, b, diag, omega, y, red[0]);
+    }
+    if (OP == OP_RESID || OP == OP_SPMV_DOT) grid_finish<kS, 1>(red, fin, sm);
+}
+
+template <typename T, typename TB>
+__global__ void jacobi_zero_kernel(int32_t n, const TB *__restrict__ b, const T *__restrict__ diag, T omega,
                                    T *__restrict__ y) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        y[i] = omega * b[i] / diag[i];
+        y[i] = omega * (T)b[i] / diag[i];
 }
 
-// x = A_L^{-1} b on the coarsest level (FP64 arithmetic, T in/out), warp per row
-template <typename T>
-__global__ void coarse_solve_kernel(int32_t n, const double *__restrict__ Ainv, const T *__restrict__ b,
-                                    T *__restrict__ x) {
+// x = A_L^{-1} b on the coarsest level (FP64 arithmetic), warp per row
+template <typename TB, typename TO>
+__global__ void coarse_solve_kernel(int32_t n, const double *__restrict__ Ainv, const TB *__restrict__ b,
+                                    TO *__restrict__ x) {
     const int lane = threadIdx.x & 31;
     for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
         double acc = 0.0;
         for (int32_t j = lane; j < n; j += 32) acc = fma(Ainv[(int64_t)i * n + j], (double)b[j], acc);
         acc = warp_sum(acc);
-        if (lane == 0) x[i] = (T)acc;
+        if (lane == 0) x[i] = (TO)acc;
     }
 }
 
-__global__ void d2f_kernel(int64_t n, const double *__restrict__ x, float *__restrict__ y) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (float)x[i];
-}
 __global__ void f2d_kernel(int64_t n, const float *__restrict__ x, double *__restrict__ y) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (double)x[i];
 }
 
+__global__ void row_maxlen_kernel(int32_t n, const int32_t *__restrict__ rp, int32_t *__restrict__ out) {
+    int32_t m = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, rp[i + 1] - rp[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 // ------------------------------------------------------------------ outer-iteration vector kernels
-// sc: device scalars.  Layout used by the outer solvers:
-//   sc[8] ||r||^2, sc[9] <r,z>, sc[10] <p,q>, sc[11] <z, r_old>, sc[12] alpha, sc[13] beta, sc[14] rz_prev
+// Device scalars: sc[8] ||r||^2, sc[9] <r,z>, sc[10] <p,Ap>, sc[11] <z,r_old>, sc[14] previous <r,z>,
+// sc[15] |g_{j+1}| (FGMRES), sc[16] h_{j+1,j}, sc[17] ||b||^2.
 __global__ void axpy_kernel(int64_t n, double *__restrict__ x, const double *__restrict__ z) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] += z[i];
 }
 
-__global__ void cg_alpha_kernel(double *sc) { sc[12] = sc[9] / sc[10]; }
-
-// x += alpha p; r_old = r (optional); r -= alpha q; partial ||r||^2
+// alpha = <r,z>/<p,Ap>; x += alpha p; r_old = r (flexible); r -= alpha q; ||r||^2
 __global__ void __launch_bounds__(kS)
 cg_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-             const double *__restrict__ q, double *__restrict__ rold, const double *__restrict__ sc,
-             double *__restrict__ partial) {
+             const double *__restrict__ q, double *__restrict__ rold, const double *__restrict__ sc, Fin fin) {
     __shared__ double sm[32];
-    const double a = sc[12];
-    double acc = 0.0;
+    const double a = sc[9] / sc[10];
+    double acc[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         x[i] = x[i] + a * p[i];
         const double ri = r[i];
         if (rold) rold[i] = ri;
         const double rn = ri - a * q[i];
         r[i] = rn;
-        acc = fma(rn, rn, acc);
+        acc[0] = fma(rn, rn, acc[0]);
     }
-    const double t = block_sum<kS>(acc, sm);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    grid_finish<kS, 1>(acc, fin, sm);
 }
 
-// <r,z> and (flexible) <z, r_old>
+// <r,z> and (flexible) <z, r_old>; the finisher keeps the previous <r,z>
 __global__ void __launch_bounds__(kS)
 cg_rz_kernel(int64_t n, const double *__restrict__ r, const double *__restrict__ z, const double *__restrict__ rold,
-             double *__restrict__ partial) {
+             Fin fin) {
     __shared__ double sm[32];
-    double a = 0.0, b = 0.0;
+    double acc[2] = {0.0, 0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        a = fma(r[i], z[i], a);
-        if (rold) b = fma(z[i], rold[i], b);
+        acc[0] = fma(r[i], z[i], acc[0]);
+        if (rold) acc[1] = fma(z[i], rold[i], acc[1]);
     }
-    const double ta = block_sum<kS>(a, sm);
-    const double tb = block_sum<kS>(b, sm);
-    if (threadIdx.x == 0) {
-        partial[blockIdx.x] = ta;
-        partial[kReduceBlocks + blockIdx.x] = tb;
-    }
+    grid_finish<kS, 2>(acc, fin, sm);
 }
 
-// beta = <z,r> / rz_prev  (standard)  or  (<z,r> - <z,r_old>) / rz_prev  (flexible)
-__global__ void cg_beta_kernel(double *sc, int flexible) {
-    const double rz = sc[9];
-    sc[13] = (flexible ? (rz - sc[11]) : rz) / sc[14];
-    sc[14] = rz;
-}
-
+// p = z + beta p, beta = <z,r>/<z,r>_prev (standard) or (<z,r> - <z,r_old>)/<z,r>_prev (flexible)
 __global__ void cg_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__ z,
-                            const double *__restrict__ sc, int first) {
-    const double b = first ? 0.0 : sc[13];
+                            const double *__restrict__ sc, int first, int flexible) {
+    const double beta = first ? 0.0 : (flexible ? (sc[9] - sc[11]) : sc[9]) / sc[14];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = first ? z[i] : z[i] + b * p[i];
+        p[i] = first ? z[i] : z[i] + beta * p[i];
 }
 
 __global__ void scale_copy_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ den,
@@ -164,7 +341,7 @@ __global__ void axpy_dev_kernel(int64_t n, double *__restrict__ w, const double 
         w[i] = w[i] - c * v[i];
 }
 
-// FGMRES Givens step on column j (H row-major (m+1) x m); g rhs; res -> sc[15]
+// FGMRES Givens step on column j (H row-major (m+1) x m); g rhs; |g_{j+1}| -> sc[15]
 __global__ void fg_givens_kernel(int m, int j, double *H, double *cs, double *sn, double *g, double *sc) {
     const double hn = sqrt(sc[8]);
     H[(j + 1) * m + j] = hn;
@@ -208,7 +385,24 @@ __global__ void fg_update_kernel(int64_t n, int k, double *__restrict__ x, const
 }
 
 // ================================================================== host side
-static int pick_spmv_g(double avg) {
+static Fin make_fin(rn_hierarchy &h, int mode, double *out = nullptr) {
+    Fin f;
+    f.mode = mode;
+    f.partial = h.partial.p;
+    f.counter = h.counters.p;
+    f.out = out;
+    f.sc = h.scal.p;
+    f.fl = h.iflags.p;
+    return f;
+}
+
+// lanes per row so that a tile (256/G rows) fits one stage; 0 = rows too long
+static int tile_group(int32_t maxlen) {
+    for (int G = 1; G <= 32; G *= 2)
+        if ((int64_t)(kS / G) * maxlen <= kTileNnz) return G;
+    return 0;
+}
+static int fallback_group(double avg) {
     if (avg <= 3.0) return 2;
     if (avg <= 12.0) return 4;
     if (avg <= 24.0) return 8;
@@ -223,36 +417,72 @@ const double *vals_of<double>(const DCsr &A) { return A.val.p; }
 template <>
 const float *vals_of<float>(const DCsr &A) { return A.val32.p; }
 
-template <typename T, int OP>
-static void spmv_launch(const char *name, const DCsr &A, int G, const T *x, const T *b, const T *diag, T omega, T *y,
-                        double *partial, int *grid_out, cudaStream_t s) {
-    const int32_t n = A.n;
-    if (n == 0) return;
-    int grid = grid_for(n, kS / G, 8);
-    if (grid > kReduceBlocks) grid = kReduceBlocks;
-    if (grid_out) *grid_out = grid;
-    const double vb = sizeof(T);
-    // algorithmic bytes: matrix (index + value), row pointers, x gathered once,
-    // output (and b, diag, x_i where used) once
-    double bytes = (4.0 + vb) * A.nnz + 4.0 * (n + 1) + vb * A.m + vb * n;
-    if (OP == OP_SPMV_ADD) bytes += vb * n;
-    if (OP == OP_RESID) bytes += vb * n;
-    if (OP == OP_JACOBI) bytes += 2.0 * vb * n;
-    const T *val = vals_of<T>(A);
-#define RN_SPMV_CASE(GG)                                                                                   \
-    case GG:                                                                                               \
-        RN_LAUNCH(name, bytes, s, (spmv_kernel<T, GG, OP>), grid, kS, 0, n, A.rowptr.p, A.col.p, val, x, b, \
-                  diag, omega, y, partial);                                                                \
-        break;
-    switch (G) {
-        RN_SPMV_CASE(2)
-        RN_SPMV_CASE(4)
-        RN_SPMV_CASE(8)
-        RN_SPMV_CASE(16)
-        RN_SPMV_CASE(32)
-        default: fail(RN_EINTERNAL, "bad spmv group");
+template <typename T, typename TB, typename TO, int G, int OP>
+static void launch_tile(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
+                        T omega, TO *y, const Fin &fin, int32_t *err, cudaStream_t s) {
+    constexpr int SL = kTileNnz + kTileSlack;
+    constexpr int RL = kS / G + 8;
+    const size_t smem = (2 * SL + 2 * RL) * sizeof(int32_t) + 2 * SL * sizeof(T);
+    static bool configured = false;
+    if (!configured) {
+        RN_CUDA_CHECK(cudaFuncSetAttribute(spmv_tile_kernel<T, TB, TO, G, OP>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
     }
-#undef RN_SPMV_CASE
+    const int32_t ntiles = (M.n + (kS / G) - 1) / (kS / G);
+    const int per_sm = sizeof(T) == 8 ? 3 : 4;  // CTAs that fit one SM's shared memory
+    int grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
+    grid = std::max(1, std::min(grid, kReduceBlocks));
+    RN_LAUNCH(name, bytes, s, (spmv_tile_kernel<T, TB, TO, G, OP>), grid, kS, smem, M.n, ntiles, M.rowptr.p, M.col.p,
+              vals_of<T>(M), x, b, diag, omega, y, fin, err);
+}
+
+template <typename T, typename TB, typename TO, int G, int OP>
+static void launch_group(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
+                         T omega, TO *y, const Fin &fin, cudaStream_t s) {
+    int grid = grid_for(M.n, kS / G, 8);
+    grid = std::min(grid, kReduceBlocks);
+    RN_LAUNCH(name, bytes, s, (spmv_group_kernel<T, TB, TO, G, OP>), grid, kS, 0, M.n, M.rowptr.p, M.col.p,
+              vals_of<T>(M), x, b, diag, omega, y, fin);
+}
+
+// y = op(M, x, b): picks the staged tile kernel when the rows fit a stage.
+template <typename T, typename TB, typename TO, int OP>
+static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, const TB *b, const T *diag, T omega,
+                 TO *y, const Fin &fin) {
+    cudaStream_t s = h.s;
+    if (M.n == 0) return;
+    const double vb = sizeof(T);
+    // algorithmic bytes: matrix (index + value) and row pointers once, x gathered
+    // once, the output (and b, diag, x_i where read) once
+    double bytes = (4.0 + vb) * M.nnz + 4.0 * (M.n + 1) + vb * M.m + (double)sizeof(TO) * M.n;
+    if (OP == OP_SPMV_ADD) bytes += sizeof(TO) * (double)M.n;
+    if (OP == OP_RESID) bytes += sizeof(TB) * (double)M.n;
+    if (OP == OP_JACOBI) bytes += (sizeof(TB) + vb) * (double)M.n;
+    int32_t *err = h.iflags.p + 8;
+    const int G = M.tile_group;
+#define RN_TILE_CASE(GG) \
+    case GG: launch_tile<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, fin, err, s); return;
+#define RN_GROUP_CASE(GG) \
+    case GG: launch_group<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, fin, s); return;
+    switch (G) {
+        RN_TILE_CASE(1)
+        RN_TILE_CASE(2)
+        RN_TILE_CASE(4)
+        RN_TILE_CASE(8)
+        RN_TILE_CASE(16)
+        RN_TILE_CASE(32)
+        default: break;
+    }
+    switch (fallback_group(M.n ? (double)M.nnz / M.n : 1.0)) {
+        RN_GROUP_CASE(2)
+        RN_GROUP_CASE(4)
+        RN_GROUP_CASE(8)
+        RN_GROUP_CASE(16)
+        default: launch_group<T, TB, TO, 32, OP>(name, bytes, M, x, b, diag, omega, y, fin, s); return;
+    }
+#undef RN_TILE_CASE
+#undef RN_GROUP_CASE
 }
 
 template <typename T>
@@ -274,76 +504,114 @@ struct LevelBufs<float> {
     static const float *d(rn_level &L) { return L.diag32.p; }
 };
 
-static const char *kJacobiName[2] = {"cycle_jacobi_f64", "cycle_jacobi_f32"};
-static const char *kResidName[2] = {"cycle_residual_f64", "cycle_residual_f32"};
-static const char *kRestrictName[2] = {"cycle_restrict_f64", "cycle_restrict_f32"};
-static const char *kProlongName[2] = {"cycle_prolong_f64", "cycle_prolong_f32"};
+struct CycleNames {
+    const char *jacobi, *jacobi0, *resid, *restr, *prolong, *coarse;
+};
+static const CycleNames kNames[2][2] = {
+    // [precision: 0 f64, 1 f32][level: 0 finest, 1 coarser]
+    {{"cycle_jacobi_f64_L0", "cycle_jacobi0_f64_L0", "cycle_residual_f64_L0", "cycle_restrict_f64_L0",
+      "cycle_prolong_f64_L0", "cycle_coarse_solve"},
+     {"cycle_jacobi_f64_Lc", "cycle_jacobi0_f64_Lc", "cycle_residual_f64_Lc", "cycle_restrict_f64_Lc",
+      "cycle_prolong_f64_Lc", "cycle_coarse_solve"}},
+    {{"cycle_jacobi_f32_L0", "cycle_jacobi0_f32_L0", "cycle_residual_f32_L0", "cycle_restrict_f32_L0",
+      "cycle_prolong_f32_L0", "cycle_coarse_solve"},
+     {"cycle_jacobi_f32_Lc", "cycle_jacobi0_f32_Lc", "cycle_residual_f32_Lc", "cycle_restrict_f32_Lc",
+      "cycle_prolong_f32_Lc", "cycle_coarse_solve"}}};
 
-// One cycle on level l with zero initial guess: b_l must hold the right-hand
-// side.  Returns the buffer with the result; when `out` is given (level 0)
-// the last relaxation writes there.
+// One cycle on level l >= 1 with zero initial guess; b_l holds the right-hand
+// side.  Returns the buffer holding the result.
 template <typename T>
-static T *vcycle(rn_hierarchy &h, int l, T *out) {
+static T *vcycle_level(rn_hierarchy &h, int l) {
     using LB = LevelBufs<T>;
     cudaStream_t s = h.s;
     rn_level &L = *h.lev[l];
-    const int prec = (sizeof(T) == 4);
+    const CycleNames &nm = kNames[sizeof(T) == 4][1];
     const int32_t n = L.A.n;
     T *b = LB::b(L);
+    const Fin none;
     if (l == (int)h.lev.size() - 1) {
-        T *x = out ? out : LB::x(L);
-        RN_LAUNCH("cycle_coarse_solve", 8.0 * n * n + 2.0 * sizeof(T) * n, s, coarse_solve_kernel<T>,
+        T *x = LB::x(L);
+        RN_LAUNCH(nm.coarse, 8.0 * n * n + 2.0 * sizeof(T) * n, s, (coarse_solve_kernel<T, T>),
                   grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, b, x);
         return x;
     }
     const T omega = (T)h.p.omega;
     const T *d = LB::d(L);
     T *cur = LB::x(L), *oth = LB::t(L);
-    const int npre = h.p.nu_pre, npost = h.p.nu_post;
-    for (int k = 0; k < npre; k++) {
+    for (int k = 0; k < h.p.nu_pre; k++) {
         if (k == 0) {
-            RN_LAUNCH(kJacobiName[prec], 3.0 * sizeof(T) * n, s, jacobi_zero_kernel<T>, grid_for(n, 1024), 256, 0, n,
-                      b, d, omega, cur);
+            RN_LAUNCH(nm.jacobi0, 3.0 * sizeof(T) * n, s, (jacobi_zero_kernel<T, T>), grid_for(n, 1024), 256, 0, n, b,
+                      d, omega, cur);
         } else {
-            spmv_launch<T, OP_JACOBI>(kJacobiName[prec], L.A, L.spmv_group, cur, b, d, omega, oth, nullptr, nullptr, s);
+            spmv<T, T, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, b, d, omega, oth, none);
             std::swap(cur, oth);
         }
     }
-    if (npre == 0) RN_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(T) * n, s));
+    if (h.p.nu_pre == 0) RN_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(T) * n, s));
     T *r = LB::r(L);
-    spmv_launch<T, OP_RESID>(kResidName[prec], L.A, L.spmv_group, cur, b, nullptr, T(0), r, nullptr, nullptr, s);
+    spmv<T, T, T, OP_RESID>(h, nm.resid, L.A, cur, b, nullptr, T(0), r, none);
     rn_level &Lc = *h.lev[l + 1];
-    spmv_launch<T, OP_SPMV>(kRestrictName[prec], L.R, L.r_group, r, nullptr, nullptr, T(0), LB::b(Lc), nullptr,
-                            nullptr, s);
-    T *xc = vcycle<T>(h, l + 1, nullptr);
-    spmv_launch<T, OP_SPMV_ADD>(kProlongName[prec], L.P, L.p_group, xc, nullptr, nullptr, T(0), cur, nullptr, nullptr,
-                                s);
-    for (int k = 0; k < npost; k++) {
-        T *dst = (out && k == npost - 1) ? out : oth;
-        spmv_launch<T, OP_JACOBI>(kJacobiName[prec], L.A, L.spmv_group, cur, b, d, omega, dst, nullptr, nullptr, s);
-        if (dst == out) return out;
+    spmv<T, T, T, OP_SPMV>(h, nm.restr, L.R, r, (const T *)nullptr, nullptr, T(0), LB::b(Lc), none);
+    T *xc = vcycle_level<T>(h, l + 1);
+    spmv<T, T, T, OP_SPMV_ADD>(h, nm.prolong, L.P, xc, (const T *)nullptr, nullptr, T(0), cur, none);
+    for (int k = 0; k < h.p.nu_post; k++) {
+        spmv<T, T, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, b, d, omega, oth, none);
         std::swap(cur, oth);
-    }
-    if (out) {
-        d2d(out, cur, n, s);
-        return out;
     }
     return cur;
 }
 
-// out = M rhs (FP64 in/out; level-0 size), without the graph
-static void cycle_direct(rn_hierarchy &h, const double *rhs, double *out) {
+// out = M rhs on level 0 (FP64 in/out); the cycle itself runs in T.
+template <typename T>
+static void vcycle_top(rn_hierarchy &h, const double *rhs, double *out) {
+    using LB = LevelBufs<T>;
     cudaStream_t s = h.s;
-    rn_level &L0 = *h.lev[0];
-    const int64_t n = L0.A.n;
-    if (h.p.precision == RN_MIXED) {
-        RN_LAUNCH("convert", 12.0 * n, s, d2f_kernel, grid_for(n, 1024), 256, 0, n, rhs, L0.b32.p);
-        float *res = vcycle<float>(h, 0, nullptr);
-        RN_LAUNCH("convert", 12.0 * n, s, f2d_kernel, grid_for(n, 1024), 256, 0, n, res, out);
-    } else {
-        d2d(L0.b.p, rhs, n, s);
-        vcycle<double>(h, 0, out);
+    rn_level &L = *h.lev[0];
+    const CycleNames &nm = kNames[sizeof(T) == 4][0];
+    const int32_t n = L.A.n;
+    const Fin none;
+    if (h.lev.size() == 1) {
+        RN_LAUNCH(nm.coarse, 8.0 * n * n + 16.0 * n, s, (coarse_solve_kernel<double, double>),
+                  grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, rhs, out);
+        return;
     }
+    const T omega = (T)h.p.omega;
+    const T *d = LB::d(L);
+    T *cur = LB::x(L), *oth = LB::t(L);
+    for (int k = 0; k < h.p.nu_pre; k++) {
+        if (k == 0) {
+            RN_LAUNCH(nm.jacobi0, (8.0 + 2.0 * sizeof(T)) * n, s, (jacobi_zero_kernel<T, double>), grid_for(n, 1024),
+                      256, 0, n, rhs, d, omega, cur);
+        } else {
+            spmv<T, double, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, rhs, d, omega, oth, none);
+            std::swap(cur, oth);
+        }
+    }
+    if (h.p.nu_pre == 0) RN_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(T) * n, s));
+    T *r = LB::r(L);
+    spmv<T, double, T, OP_RESID>(h, nm.resid, L.A, cur, rhs, nullptr, T(0), r, none);
+    rn_level &Lc = *h.lev[1];
+    spmv<T, T, T, OP_SPMV>(h, nm.restr, L.R, r, (const T *)nullptr, nullptr, T(0), LevelBufs<T>::b(Lc), none);
+    T *xc = vcycle_level<T>(h, 1);
+    spmv<T, T, T, OP_SPMV_ADD>(h, nm.prolong, L.P, xc, (const T *)nullptr, nullptr, T(0), cur, none);
+    const int npost = h.p.nu_post;
+    for (int k = 0; k < npost; k++) {
+        if (k == npost - 1) {
+            spmv<T, double, double, OP_JACOBI>(h, nm.jacobi, L.A, cur, rhs, d, omega, out, none);
+            return;
+        }
+        spmv<T, double, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, rhs, d, omega, oth, none);
+        std::swap(cur, oth);
+    }
+    // no post-smoothing: copy the iterate out
+    if (sizeof(T) == 8) d2d(out, reinterpret_cast<const double *>(cur), n, s);
+    else RN_LAUNCH("convert", 12.0 * n, s, f2d_kernel, grid_for(n, 1024), 256, 0, (int64_t)n,
+                   reinterpret_cast<const float *>(cur), out);
+}
+
+static void cycle_direct(rn_hierarchy &h, const double *rhs, double *out) {
+    if (h.p.precision == RN_MIXED) vcycle_top<float>(h, rhs, out);
+    else vcycle_top<double>(h, rhs, out);
 }
 
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out) {
@@ -376,9 +644,18 @@ void apply_cycle(rn_hierarchy &h, const double *rhs, double *out) {
     if (out != h.graph_out) d2d(out, h.graph_out, n, s);
 }
 
+static void set_tile_group(rn_hierarchy &h, DCsr &M, int32_t *tmp) {
+    if (M.n == 0) return;
+    RN_CUDA_CHECK(cudaMemsetAsync(tmp, 0, sizeof(int32_t), h.s));
+    RN_LAUNCH("prepare", 4.0 * M.n, h.s, row_maxlen_kernel, grid_for(M.n, 1024), 256, 0, M.n, M.rowptr.p, tmp);
+    M.maxlen = read_scalar(tmp, h.s);
+    M.tile_group = tile_group(M.maxlen);
+}
+
 void prepare_solve(rn_hierarchy &h) {
     cudaStream_t s = h.s;
     const bool mixed = h.p.precision == RN_MIXED;
+    DVec<int32_t> tmp(1, s);
     for (size_t l = 0; l < h.lev.size(); l++) {
         rn_level &L = *h.lev[l];
         const int32_t n = L.A.n;
@@ -386,9 +663,9 @@ void prepare_solve(rn_hierarchy &h) {
         L.x.alloc(n, s);
         L.t.alloc(n, s);
         L.r.alloc(n, s);
-        L.spmv_group = pick_spmv_g(n ? (double)L.A.nnz / n : 1.0);
-        if (L.P.n) L.p_group = pick_spmv_g((double)L.P.nnz / L.P.n);
-        if (L.R.n) L.r_group = pick_spmv_g((double)L.R.nnz / L.R.n);
+        set_tile_group(h, L.A, tmp.p);
+        set_tile_group(h, L.P, tmp.p);
+        set_tile_group(h, L.R, tmp.p);
         if (mixed) {
             L.b32.alloc(n, s);
             L.x32.alloc(n, s);
@@ -415,8 +692,6 @@ void prepare_solve(rn_hierarchy &h) {
     h.q.alloc(n0, s);
     h.w.alloc(n0, s);
     h.rold.alloc(n0, s);
-    // the partial-sum buffer needs room for two reductions at once
-    h.partial.alloc(2 * kReduceBlocks, s);
     h.graph_in = h.r.p;
     h.graph_out = h.z.p;
     if (h.p.outer == RN_OUTER_FGMRES) {
@@ -427,100 +702,93 @@ void prepare_solve(rn_hierarchy &h) {
     }
 }
 
-static double norm_from(double *sc_slot, cudaStream_t s) { return std::sqrt(read_scalar(sc_slot, s)); }
+static void check_tile_error(rn_hierarchy &h) {
+    if (read_scalar(h.iflags.p + 8, h.s)) {
+        RN_CUDA_CHECK(cudaMemsetAsync(h.iflags.p + 8, 0, sizeof(int32_t), h.s));
+        fail(RN_ETIMEOUT, "a shared-memory staging wait gave up (bulk copy did not complete)");
+    }
+}
+
+void cycle_checked(rn_hierarchy &h, const double *rhs, double *out) {
+    apply_cycle(h, rhs, out);
+    check_tile_error(h);
+}
 
 rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int maxit, rn_solve_info *info) {
     cudaStream_t s = h.s;
     rn_level &L0 = *h.lev[0];
     const int64_t n = L0.A.n;
     double *sc = h.scal.p;
-    double *part = h.partial.p;
-    int grid = 1;
     const double t0 = now_ms();
-    // ||b||
-    dot(b, b, n, sc + 17, s, part);
-    double nb = norm_from(sc + 17, s);
+    const Fin none;
+    const int eg = grid_for(n, 1024);
+    const int rg = std::min(grid_for(n, kS * 4, 8), kReduceBlocks);
+    auto residual = [&]() {  // r = b - A x, sc[8] = ||r||^2
+        spmv<double, double, double, OP_RESID>(h, "outer_residual", L0.A, x, b, nullptr, 0.0, h.r.p,
+                                               make_fin(h, FIN_STORE, sc + 8));
+        return std::sqrt(read_scalar(sc + 8, s));
+    };
+    dot(b, b, n, sc + 17, s, h.partial.p, h.counters.p);
+    double nb = std::sqrt(read_scalar(sc + 17, s));
     if (nb == 0.0) nb = 1.0;
-    // r = b - A x
-    spmv_launch<double, OP_RESID>("outer_residual", L0.A, L0.spmv_group, x, b, nullptr, 0.0, h.r.p, part, &grid, s);
-    reduce_partials(part, grid, sc + 8, s);
-    const double r0 = norm_from(sc + 8, s);
+    const double r0 = residual();
     double rn = r0;
     int it = 0;
     rn_status st = RN_ENOTCONV;
-    const int eg = grid_for(n, 1024);
-    const int rg = std::min(grid_for(n, kS * 4, 8), kReduceBlocks);
     if (rn / nb < rtol) st = RN_OK;
     if (st != RN_OK && h.p.outer == RN_OUTER_STATIONARY) {
         // x <- x + M (b - A x): the cycle applied to the current iterate
         for (it = 1; it <= maxit; it++) {
             apply_cycle(h, h.r.p, h.z.p);
             RN_LAUNCH("outer_axpy", 24.0 * n, s, axpy_kernel, eg, 256, 0, n, x, h.z.p);
-            spmv_launch<double, OP_RESID>("outer_residual", L0.A, L0.spmv_group, x, b, nullptr, 0.0, h.r.p, part,
-                                          &grid, s);
-            reduce_partials(part, grid, sc + 8, s);
-            rn = norm_from(sc + 8, s);
+            rn = residual();
             if (rn / nb < rtol) { st = RN_OK; break; }
         }
         if (it > maxit) it = maxit;
     } else if (st != RN_OK && h.p.outer == RN_OUTER_CG) {
         const bool flexible = h.p.precision == RN_MIXED;
         apply_cycle(h, h.r.p, h.z.p);
-        RN_LAUNCH("outer_cg_vec", 16.0 * n, s, cg_rz_kernel, rg, kS, 0, n, h.r.p, h.z.p, nullptr, part);
-        reduce_partials(part, rg, sc + 9, s);
-        RN_LAUNCH("outer_cg_vec", 24.0 * n, s, cg_p_kernel, eg, 256, 0, n, h.pv.p, h.z.p, sc, 1);
-        d2d(sc + 14, sc + 9, 1, s);
+        RN_LAUNCH("outer_cg_vec", 16.0 * n, s, cg_rz_kernel, rg, kS, 0, n, h.r.p, h.z.p, nullptr,
+                  make_fin(h, FIN_RZ));
+        RN_LAUNCH("outer_cg_vec", 16.0 * n, s, cg_p_kernel, eg, 256, 0, n, h.pv.p, h.z.p, sc, 1, 0);
         for (it = 1; it <= maxit; it++) {
-            // q = A p, <p, q>
-            spmv_launch<double, OP_SPMV>("outer_spmv", L0.A, L0.spmv_group, h.pv.p, nullptr, nullptr, 0.0, h.q.p,
-                                         nullptr, nullptr, s);
-            dot(h.pv.p, h.q.p, n, sc + 10, s, part);
-            RN_LAUNCH("outer_cg_scalar", 0, s, cg_alpha_kernel, 1, 1, 0, sc);
-            RN_LAUNCH("outer_cg_vec", 56.0 * n, s, cg_xr_kernel, rg, kS, 0, n, x, h.r.p, h.pv.p, h.q.p,
-                      flexible ? h.rold.p : nullptr, sc, part);
-            reduce_partials(part, rg, sc + 8, s);
-            rn = norm_from(sc + 8, s);
+            // q = A p and <p, q> in one pass
+            spmv<double, double, double, OP_SPMV_DOT>(h, "outer_spmv", L0.A, h.pv.p, (const double *)nullptr,
+                                                      nullptr, 0.0, h.q.p, make_fin(h, FIN_STORE, sc + 10));
+            RN_LAUNCH("outer_cg_vec", 48.0 * n + (flexible ? 8.0 * n : 0.0), s, cg_xr_kernel, rg, kS, 0, n, x,
+                      h.r.p, h.pv.p, h.q.p, flexible ? h.rold.p : nullptr, sc, make_fin(h, FIN_STORE, sc + 8));
+            rn = std::sqrt(read_scalar(sc + 8, s));
             if (rn / nb < rtol) { st = RN_OK; break; }
             apply_cycle(h, h.r.p, h.z.p);
-            RN_LAUNCH("outer_cg_vec", 24.0 * n, s, cg_rz_kernel, rg, kS, 0, n, h.r.p, h.z.p,
-                      flexible ? h.rold.p : nullptr, part);
-            reduce_partials(part, rg, sc + 9, s);
-            if (flexible) reduce_partials(part + kReduceBlocks, rg, sc + 11, s);
-            RN_LAUNCH("outer_cg_scalar", 0, s, cg_beta_kernel, 1, 1, 0, sc, flexible ? 1 : 0);
-            RN_LAUNCH("outer_cg_vec", 24.0 * n, s, cg_p_kernel, eg, 256, 0, n, h.pv.p, h.z.p, sc, 0);
+            RN_LAUNCH("outer_cg_vec", (flexible ? 24.0 : 16.0) * n, s, cg_rz_kernel, rg, kS, 0, n, h.r.p, h.z.p,
+                      flexible ? h.rold.p : nullptr, make_fin(h, FIN_RZ));
+            RN_LAUNCH("outer_cg_vec", 24.0 * n, s, cg_p_kernel, eg, 256, 0, n, h.pv.p, h.z.p, sc, 0,
+                      flexible ? 1 : 0);
         }
         if (it > maxit) it = maxit;
-        spmv_launch<double, OP_RESID>("outer_residual", L0.A, L0.spmv_group, x, b, nullptr, 0.0, h.r.p, part, &grid,
-                                      s);
-        reduce_partials(part, grid, sc + 8, s);
-        rn = norm_from(sc + 8, s);
+        rn = residual();
         st = (rn / nb < rtol) ? RN_OK : RN_ENOTCONV;
     } else if (st != RN_OK && h.p.outer == RN_OUTER_FGMRES) {
         const int m = std::max(1, h.p.restart);
         double *H = h.H.p, *cs = H + (m + 1) * m, *sn = cs + (m + 1), *g = sn + (m + 1), *y = g + (m + 1);
         it = 0;
         while (it < maxit && st != RN_OK) {
-            // r = b - A x, V0 = r / ||r||
-            spmv_launch<double, OP_RESID>("outer_residual", L0.A, L0.spmv_group, x, b, nullptr, 0.0, h.r.p, part,
-                                          &grid, s);
-            reduce_partials(part, grid, sc + 8, s);
-            rn = norm_from(sc + 8, s);
-            if (rn / nb < rtol) { st = RN_OK; break; }
+            // V0 = r / ||r|| (r and ||r||^2 are current)
             RN_LAUNCH("outer_gmres_scalar", 0, s, fg_start_kernel, 1, 1, 0, g, m, sc);
             RN_LAUNCH("outer_gmres_vec", 16.0 * n, s, scale_copy_kernel, eg, 256, 0, n, h.r.p, sc + 8, h.V.p, 1);
             int k = 0;
             for (int j = 0; j < m && it < maxit; j++) {
                 double *vj = h.V.p + (int64_t)j * n, *zj = h.Z.p + (int64_t)j * n;
                 apply_cycle(h, vj, zj);
-                spmv_launch<double, OP_SPMV>("outer_spmv", L0.A, L0.spmv_group, zj, nullptr, nullptr, 0.0, h.w.p,
-                                             nullptr, nullptr, s);
+                spmv<double, double, double, OP_SPMV>(h, "outer_spmv", L0.A, zj, (const double *)nullptr, nullptr,
+                                                      0.0, h.w.p, none);
                 for (int i = 0; i <= j; i++) {
                     double *vi = h.V.p + (int64_t)i * n;
-                    dot(h.w.p, vi, n, H + i * m + j, s, part);
+                    dot(h.w.p, vi, n, H + i * m + j, s, h.partial.p, h.counters.p);
                     RN_LAUNCH("outer_gmres_vec", 24.0 * n, s, axpy_dev_kernel, eg, 256, 0, n, h.w.p, vi,
                               H + i * m + j);
                 }
-                dot(h.w.p, h.w.p, n, sc + 8, s, part);
+                dot(h.w.p, h.w.p, n, sc + 8, s, h.partial.p, h.counters.p);
                 RN_LAUNCH("outer_gmres_scalar", 0, s, fg_givens_kernel, 1, 1, 0, m, j, H, cs, sn, g, sc);
                 it++;
                 k = j + 1;
@@ -533,16 +801,14 @@ rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int ma
             }
             RN_LAUNCH("outer_gmres_scalar", 0, s, fg_backsolve_kernel, 1, 1, 0, m, k, H, g, y);
             RN_LAUNCH("outer_gmres_vec", (8.0 * k + 16.0) * n, s, fg_update_kernel, eg, 256, 0, n, k, x, h.Z.p, y);
-            spmv_launch<double, OP_RESID>("outer_residual", L0.A, L0.spmv_group, x, b, nullptr, 0.0, h.r.p, part,
-                                          &grid, s);
-            reduce_partials(part, grid, sc + 8, s);
-            rn = norm_from(sc + 8, s);
+            rn = residual();
             if (rn / nb < rtol) st = RN_OK;
         }
     } else if (st != RN_OK) {
         fail(RN_EINVAL, "unknown outer iteration");
     }
     RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    check_tile_error(h);
     if (info) {
         info->iters = it;
         info->rel_res = rn / nb;

@@ -57,10 +57,17 @@ sym_warp_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__res
     __shared__ int32_t list[kSymWarps][kHashMaxUnique];
     __shared__ int32_t cnt[kSymWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr uint32_t bits = 10;
     for (int32_t i = blockIdx.x * kSymWarps + w; i < n; i += gridDim.x * kSymWarps) {
         if (FILL && crp[i + 1] - crp[i] > kHashMaxUnique) continue;  // long row: block tier
-        for (int s = lane; s < kHashSlots; s += 32) tab[w][s] = -1;
+        // table size: the smallest power of two >= 2 x (products in the row), 32..1024
+        int32_t ub = 0;
+        for (int32_t e = arp[i] + lane; e < arp[i + 1]; e += 32) ub += brp[acol[e] + 1] - brp[acol[e]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ub += __shfl_xor_sync(0xffffffffu, ub, o);
+        uint32_t bits = 5;
+        while (bits < 10 && (1 << bits) < 2 * ub) bits++;
+        const int slots = 1 << bits;
+        for (int s = lane; s < slots; s += 32) tab[w][s] = -1;
         if (lane == 0) cnt[w] = 0;
         __syncwarp();
         bool ovf = false;
@@ -87,7 +94,7 @@ sym_warp_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__res
         } else {
             // compact the keys, then rank-sort them into the row
             int base = 0;
-            for (int s0 = 0; s0 < kHashSlots; s0 += 32) {
+            for (int s0 = 0; s0 < slots; s0 += 32) {
                 int32_t key = tab[w][s0 + lane];
                 unsigned b = __ballot_sync(0xffffffffu, key >= 0);
                 if (key >= 0) list[w][base + __popc(b & ((1u << lane) - 1u))] = key;
@@ -200,7 +207,7 @@ masked_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t 
                       const int32_t *__restrict__ xcol, const double *__restrict__ xval,
                       const int32_t *__restrict__ crp, const int32_t *__restrict__ ccol, double *__restrict__ cval,
                       const int32_t *__restrict__ rowtype, const double *__restrict__ Bc, double scale,
-                      const double *__restrict__ Y, double *__restrict__ partial) {
+                      const double *__restrict__ Y, Fin fin) {
     constexpr int GPB = kMpThreads / G;  // groups per block
     constexpr int CAP = 8 * G;           // pattern columns per chunk
     __shared__ int32_t s_col[GPB][CAP];
@@ -269,9 +276,9 @@ masked_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t 
             }
         }
     }
-    if (PROJ && partial) {
-        const double t = block_sum<kMpThreads>(dot_acc, s_red);
-        if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    if (PROJ) {
+        const double v[1] = {dot_acc};
+        grid_finish<kMpThreads, 1>(v, fin, s_red);
     }
 }
 
@@ -279,11 +286,11 @@ template <bool EXACT, bool PROJ>
 static void launch_mp(int G, int grid, cudaStream_t s, const char *name, double bytes, int32_t n, const int32_t *arp,
                       const int32_t *acol, const double *aval, const int32_t *xrp, const int32_t *xcol,
                       const double *xval, const int32_t *crp, const int32_t *ccol, double *cval,
-                      const int32_t *rowtype, const double *Bc, double scale, const double *Y, double *partial) {
+                      const int32_t *rowtype, const double *Bc, double scale, const double *Y, const Fin &fin) {
 #define RN_MP_CASE(GG)                                                                                         \
     case GG:                                                                                                   \
         RN_LAUNCH(name, bytes, s, (masked_product_kernel<GG, EXACT, PROJ>), grid, kMpThreads, 0, n, arp, acol, \
-                  aval, xrp, xcol, xval, crp, ccol, cval, rowtype, Bc, scale, Y, partial);                     \
+                  aval, xrp, xcol, xval, crp, ccol, cval, rowtype, Bc, scale, Y, fin);                         \
         break;
     switch (G) {
         RN_MP_CASE(4)
@@ -309,17 +316,18 @@ void spgemm_numeric(const CsrView &A, const CsrView &B, DCsr &C, bool exact, cud
     const int grid = grid_for(A.n, kMpThreads / G, 8);
     // algorithmic bytes: A and the pattern of C once, B gathered once, C written once
     const double bytes = 12.0 * A.nnz + 4.0 * A.n + 12.0 * B.nnz + 12.0 * C.nnz;
+    const Fin none;
     if (exact)
         launch_mp<true, false>(G, grid, s, "spgemm_numeric_exact", bytes, A.n, A.rowptr, A.col, A.val, B.rowptr,
-                               B.col, B.val, C.rowptr.p, C.col.p, C.val.p, nullptr, nullptr, 1.0, nullptr, nullptr);
+                               B.col, B.val, C.rowptr.p, C.col.p, C.val.p, nullptr, nullptr, 1.0, nullptr, none);
     else
         launch_mp<false, false>(G, grid, s, "spgemm_numeric", bytes, A.n, A.rowptr, A.col, A.val, B.rowptr, B.col,
-                                B.val, C.rowptr.p, C.col.p, C.val.p, nullptr, nullptr, 1.0, nullptr, nullptr);
+                                B.val, C.rowptr.p, C.col.p, C.val.p, nullptr, nullptr, 1.0, nullptr, none);
 }
 
 void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, int32_t nc,
                          const double *X, double *W, const ProjArgs &pa, double scale, const double *Y,
-                         double *dot_out, double *partial, cudaStream_t s) {
+                         const Fin &fin, cudaStream_t s) {
     if (A.n == 0) return;
     const int G = pick_group((double)nnzN / A.n);
     int grid = grid_for(A.n, kMpThreads / G, 8);
@@ -330,8 +338,7 @@ void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t
     const double bytes = 12.0 * A.nnz + 4.0 * (A.n + 1) + 4.0 * A.n + 4.0 * nnzN + 8.0 * nnzN + 8.0 * nnzN +
                          (Y ? 8.0 * nnzN : 0.0) + 8.0 * nc;
     launch_mp<false, true>(G, grid, s, "energy_masked_product", bytes, A.n, A.rowptr, A.col, A.val, nrowptr, ncol, X,
-                           nrowptr, ncol, W, pa.rowtype, pa.Bc, scale, Y, dot_out ? partial : nullptr);
-    if (dot_out) reduce_partials(partial, grid, dot_out, s);
+                           nrowptr, ncol, W, pa.rowtype, pa.Bc, scale, Y, fin);
 }
 
 }  // namespace rn

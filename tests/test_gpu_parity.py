@@ -225,6 +225,46 @@ def test_deterministic_repeat(rn, torch_dev):
     assert np.array_equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
 
 
+@pytest.mark.parametrize("case,method,sweeps", [("aniso96", 0, 6), ("poisson64", 0, 4), ("aniso255", 0, 6),
+                                                ("convdiff80", 1, 2), ("aniso96", 1, 3)])
+def test_energy_min_entry_point_matches_oracle(rn, torch_dev, oracle, case, method, sweeps):
+    """rn_energy_min (Alg. 3 'improve') on the oracle's own level-0 pattern, T,
+    row types and Bc, against the oracle's CG / GMRES energy minimisation."""
+    pr = CASES[case]()
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, Bhat=pr.Bhat, **pr.params)
+    L = oh.levels[0]
+    A, N, T = L.A, L.N, L.T
+    if method == 0:
+        Po, _ = oracle.energy_min_cg(A, T, L.rowtype, L.Bc, sweeps)
+    else:
+        Po, _ = oracle.energy_min_gmres(A, T, L.rowtype, L.Bc, sweeps)
+    d = lambda a: dev(torch_dev, a)
+    P = d(T.data.astype(np.float64))
+    rn.energy_min(d(A.indptr.astype(np.int32)), d(A.indices.astype(np.int32)), d(A.data), d(N.indptr.astype(np.int32)),
+                  d(N.indices.astype(np.int32)), N.shape[1], d(L.rowtype), d(L.Bc), P, sweeps, method=method)
+    Pg = P.cpu().numpy()
+    assert np.max(np.abs(Pg - Po.data)) <= TOL * np.max(np.abs(Po.data))
+    # constraints: root rows stay identity rows, P Bc = B on aggregated rows
+    Pm = sp.csr_matrix((Pg, N.indices, N.indptr), shape=N.shape)
+    agg = L.agg >= 0
+    assert np.max(np.abs((Pm @ L.Bc)[agg] - L.B[agg])) <= 1e-13 * np.max(np.abs(L.B))
+
+
+def test_energy_min_entry_point_rejects_bad_input(rn, torch_dev):
+    d = lambda a: dev(torch_dev, a)
+    A = PR.poisson5(5)
+    rp, ci, va = d(A.rowptr), d(A.col), d(A.val)
+    N_rp = d(np.arange(A.n_rows + 1, dtype=np.int32))
+    N_ci = d(np.zeros(A.n_rows, np.int32))
+    P = d(np.ones(A.n_rows))
+    with pytest.raises(rn.RNError) as e:
+        rn.energy_min(rp, ci, va, N_rp, N_ci, 1, d(np.zeros(A.n_rows, np.int32)), d(np.ones(1)), P, -1)
+    assert e.value.status == rn.RN_EINVAL
+    with pytest.raises(rn.RNError) as e:
+        rn.energy_min(rp, ci, va, N_rp, N_ci, 1, d(np.zeros(A.n_rows, np.int32)), d(np.ones(1)), P, 2, method=7)
+    assert e.value.status == rn.RN_EINVAL
+
+
 # ------------------------------------------------------------------ edge cases
 def _mk(rn, torch_dev, rowptr, col, val, **over):
     params = rn.default_params(**over)
