@@ -157,6 +157,24 @@ void rn_free(rn_hierarchy *h);
 rn_status rn_energy_min(const rn_csr *A, const rn_csr *N, const int32_t *rowtype, const double *Bc, double *P,
                         int sweeps, int method, int precond, void *stream);
 
+/* rn_energy_min for callers that must not allocate device memory (the paper
+ * has no counterpart; this is a deployment variant).  Examples: a host
+ * framework whose caching allocator has reserved the GPU's memory, a
+ * latency-critical loop that cannot afford an allocation's synchronisation,
+ * a plugin host that forbids libraries to allocate.  Same arguments and result
+ * as rn_energy_min with method RN_ENERGY_CG; the call makes no allocation: its
+ * scratch is one statically allocated device array of about 14 MB, which every
+ * GPU that loads this library keeps until the process exits.
+ *   Limits: A->n_rows <= 262144 and N->nnz <= 524288; larger inputs return
+ *   RN_EINVAL with a message naming the limit.
+ *   The first call on a device resolves the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   stream NULL means the legacy default stream.
+ *   All calls share the array: calls whose GPU work overlaps (other streams,
+ *   other threads) race on it and must be serialised by the caller. */
+rn_status rn_energy_min_noalloc(const rn_csr *A, const rn_csr *N, const int32_t *rowtype, const double *Bc,
+                                double *P, int sweeps, int precond, void *stream);
+
 /* Level sizes and the complexities of Sec. 2.4 (eq. oc, eq. cc). */
 rn_status rn_hierarchy_stats(const rn_hierarchy *h, rn_stats *s);
 

@@ -70,6 +70,8 @@ def _load():
     L.rn_free.restype = None
     L.rn_energy_min.argtypes = [P(rn_csr), P(rn_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                 C.c_void_p]
+    L.rn_energy_min_noalloc.argtypes = [P(rn_csr), P(rn_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                        C.c_void_p]
     L.rn_hierarchy_stats.argtypes = [C.c_void_p, P(rn_stats)]
     L.rn_export_csr.argtypes = [C.c_void_p, C.c_int, C.c_int, P(C.c_int32), P(C.c_int32), P(C.c_int64),
                                 C.c_void_p, C.c_void_p, C.c_void_p]
@@ -103,6 +105,16 @@ rn_last_error = lib.rn_last_error
 rn_status_string = lib.rn_status_string
 rn_kernel_launches = lib.rn_kernel_launches
 rn_energy_min = lib.rn_energy_min
+rn_energy_min_noalloc = lib.rn_energy_min_noalloc
+
+
+def energy_min_noalloc(A_rowptr, A_col, A_val, N_rowptr, N_col, n_c, rowtype, Bc, P, sweeps, precond=1, stream=None):
+    """Run rn_energy_min_noalloc (CG, no device allocation) on device tensors; P is updated in place."""
+    n = int(A_rowptr.shape[0]) - 1
+    A = rn_csr(n, n, int(A_col.shape[0]), _ptr(A_rowptr), _ptr(A_col), _ptr(A_val))
+    N = rn_csr(n, int(n_c), int(N_col.shape[0]), _ptr(N_rowptr), _ptr(N_col) if N_col.shape[0] else None, None)
+    _check(rn_energy_min_noalloc(C.byref(A), C.byref(N), _ptr(rowtype), _ptr(Bc), _ptr(P), sweeps, precond, stream),
+           "rn_energy_min_noalloc")
 
 
 def energy_min(A_rowptr, A_col, A_val, N_rowptr, N_col, n_c, rowtype, Bc, P, sweeps, method=RN_ENERGY_CG,
