@@ -39,10 +39,21 @@ void orc_csr_copy(const orc_csr *a, orc_csr *b) {
     if (a->val) memcpy(b->val, a->val, (size_t)a->nnz * sizeof(double));
 }
 
+/* Inner product with Neumaier's compensated summation (Neumaier 1974, an
+ * improvement of Kahan's): the running sum's rounding errors are collected
+ * and added back, so the result's error does not grow with n.  These sums
+ * run over millions of terms (Frobenius products on the interpolation
+ * pattern), where a plain sequential sum would dominate the comparison. */
 double orc_dot(int64_t n, const double *x, const double *y) {
-    double s = 0.0;
-    for (int64_t i = 0; i < n; i++) s += x[i] * y[i];
-    return s;
+    double s = 0.0, c = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        const double p = x[i] * y[i];
+        const double t = s + p;
+        if (fabs(s) >= fabs(p)) c += (s - t) + p;
+        else c += (p - t) + s;
+        s = t;
+    }
+    return s + c;
 }
 
 double orc_nrm2(int64_t n, const double *x) { return sqrt(orc_dot(n, x, x)); }
