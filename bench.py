@@ -119,6 +119,19 @@ def dist_env():
     return ws, rank, local
 
 
+def job_step_seconds(step_s: float, device=None) -> float:
+    """Replicas run independently; the job's step time is the slowest rank's
+    (max over ranks).  No-op without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return step_s
+    t = torch.tensor([step_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_oracle_sample(pr, iters_target: int | None, cg_sample_iters: int = 25):
     """Oracle setup (full) + a bounded CG solve; returns seconds and the sample description."""
     from oracle import oracle as O
@@ -142,7 +155,7 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    pr = PR.aniso_problem(WORKLOAD_NE)
+    pr = PR.aniso_problem(args.ne)
     # iteration count of the oracle on this workload: one full FP64 CG solve up front (not timed)
     from oracle import oracle as O
 
@@ -275,11 +288,7 @@ def main():
         times, infos = timed(prec, args.steps)
     launches = int(rn.rn_kernel_launches()) - l0
     torch.cuda.synchronize()
-    step_s = float(np.mean(times))
-    if ws > 1:
-        tt = torch.tensor([step_s], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        step_s = float(tt.item())
+    step_s = job_step_seconds(float(np.mean(times)), dev)
     times_other, infos_other = timed(other, args.steps)
 
     # per-kernel device times of one step (events around every launch)

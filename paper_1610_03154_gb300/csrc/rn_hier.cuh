@@ -12,7 +12,8 @@ struct rn_level {
     rn::DCsr A, P, R;                       // operator, interpolation, restriction
     rn::DCsr S, N, T;                       // kept only with keep_aux
     rn::DVec<double> diag;                  // a_ii
-    rn::DVec<float> diag32;
+    rn::DVec<double> wd;                    // omega / a_ii (the cycle's relaxation weights)
+    rn::DVec<float> wd32;
     rn::DVec<int32_t> agg, roots, rowtype;  // aggregation (agg/roots kept with keep_aux)
     int32_t nc = 0;
     rn::DVec<double> B, Bc, Bhat, Bhatc;    // smoothed candidates and their injections

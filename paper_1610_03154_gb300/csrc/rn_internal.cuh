@@ -162,12 +162,10 @@ void transpose(const CsrView &A, bool with_val, DCsr &At, cudaStream_t s);
 void to_float(const double *x, float *y, int64_t n, cudaStream_t s);
 
 // --------------------------------------------------------------- products (rn_spgemm.cu)
-// Symbolic product pattern of A*B (explicit zeros kept), rows sorted.
-void spgemm_symbolic(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s);
-// Values of C = A*B on C's pattern (which must contain every product).
-// exact = true: products and sums in ascending k order with no fused
-// multiply-add (matches a plain sequential CPU evaluation bit for bit).
-void spgemm_numeric(const CsrView &A, const CsrView &B, DCsr &C, bool exact, cudaStream_t s);
+// C = A*B in one hash pass per row: the symbolic pattern (explicit zeros kept,
+// rows sorted) and the values, each summed in ascending k with a rounded
+// multiply then a rounded add (bit-identical to a sequential evaluation).
+void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s);
 
 // Energy-minimisation operator on the fixed pattern N shared by X and W:
 //   W = Proj(Mask_N(A X)) (scale = -1 negates), plus, when dot_out != nullptr,

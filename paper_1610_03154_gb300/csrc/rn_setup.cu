@@ -898,8 +898,7 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
                       cur.val.p);
             for (int t = 0; t < p.degree; t++) {
                 DCsr nxt;
-                spgemm_symbolic(view(S), view(cur), nxt, s);
-                spgemm_numeric(view(S), view(cur), nxt, true, s);
+                spgemm(view(S), view(cur), nxt, s);
                 cur = std::move(nxt);
             }
             DVec<int32_t> cnt(n + 1, s);
@@ -937,10 +936,8 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         auto Lc = std::make_unique<rn_level>();
         {
             DCsr AP;
-            spgemm_symbolic(A, view(L.P), AP, s);
-            spgemm_numeric(A, view(L.P), AP, false, s);
-            spgemm_symbolic(view(L.R), view(AP), Lc->A, s);
-            spgemm_numeric(view(L.R), view(AP), Lc->A, false, s);
+            spgemm(A, view(L.P), AP, s);
+            spgemm(view(L.R), view(AP), Lc->A, s);
         }
         Lc->B.alloc(nc, s);
         d2d(Lc->B.p, L.Bc.p, nc, s);

@@ -28,7 +28,9 @@ constexpr int kTileNnz = 3072;    // matrix entries per shared-memory stage
 constexpr int kTileSlack = 8;     // room for 16-byte alignment of the bulk copies
 constexpr uint32_t kMaxSpin = 1u << 24;  // bound on mbarrier polls before giving up
 
-enum SpOp { OP_SPMV = 0, OP_SPMV_ADD = 1, OP_RESID = 2, OP_JACOBI = 3, OP_SPMV_DOT = 4 };
+enum SpOp { OP_SPMV = 0, OP_SPMV_ADD = 1, OP_RESID = 2, OP_JACOBI = 3, OP_SPMV_DOT = 4, OP_JZ_RESID = 5 };
+// OP_JZ_RESID: first relaxation from a zero guess fused with the residual:
+//   xz = omega b / d,  y = b - A xz
 
 // ------------------------------------------------------------------ mbarrier / bulk-copy helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -62,9 +64,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// The operand gathered at column j: x_j, or, for the fused first sweep from a
+// zero guess, x_j = omega b_j / d_j computed on the fly (the same expression
+// jacobi_zero_kernel stores, so the residual is bit-identical to the unfused
+// pair of kernels).
+template <typename T, typename TB, int OP>
+__device__ __forceinline__ T xget(int32_t j, const T *__restrict__ x, const TB *__restrict__ b,
+                                  const T *__restrict__ diag, T omega) {
+    if (OP == OP_JZ_RESID) return diag[j] * (T)b[j];  // diag holds omega / a_jj
+    return x[j];
+}
+
 template <typename T, typename TB, typename TO, int OP>
 __device__ __forceinline__ void spmv_epilogue(int32_t i, T acc, const T *__restrict__ x, const TB *__restrict__ b,
-                                              const T *__restrict__ diag, T omega, TO *__restrict__ y, double &red) {
+                                              const T *__restrict__ diag, T omega, TO *__restrict__ y,
+                                              T *__restrict__ xz, double &red) {
     if (OP == OP_SPMV) {
         y[i] = (TO)acc;
     } else if (OP == OP_SPMV_ADD) {
@@ -74,7 +88,10 @@ __device__ __forceinline__ void spmv_epilogue(int32_t i, T acc, const T *__restr
         y[i] = (TO)r;
         red += (double)r * (double)r;
     } else if (OP == OP_JACOBI) {
-        y[i] = (TO)(x[i] + omega * ((T)b[i] - acc) / diag[i]);
+        y[i] = (TO)(x[i] + diag[i] * ((T)b[i] - acc));
+    } else if (OP == OP_JZ_RESID) {
+        xz[i] = diag[i] * (T)b[i];
+        y[i] = (TO)((T)b[i] - acc);
     } else {  // OP_SPMV_DOT
         y[i] = (TO)acc;
         red += (double)x[i] * (double)acc;
@@ -90,7 +107,8 @@ template <typename T, typename TB, typename TO, int G, int OP>
 __global__ void __launch_bounds__(kS)
 spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                  const T *__restrict__ val, const T *__restrict__ x, const TB *__restrict__ b,
-                 const T *__restrict__ diag, T omega, TO *__restrict__ y, Fin fin, int32_t *__restrict__ err) {
+                 const T *__restrict__ diag, T omega, TO *__restrict__ y, T *__restrict__ xz, Fin fin,
+                 int32_t *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int SL = kTileNnz + kTileSlack;
     constexpr int RPT = kS / G;
@@ -156,8 +174,8 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
         TO yi = TO(0);
         if (live && lane == 0) {
             if (OP == OP_JACOBI || OP == OP_SPMV_DOT) xi = x[row];
-            if (OP == OP_RESID || OP == OP_JACOBI) bi = b[row];
-            if (OP == OP_JACOBI) di = diag[row];
+            if (OP == OP_RESID || OP == OP_JACOBI || OP == OP_JZ_RESID) bi = b[row];
+            if (OP == OP_JACOBI || OP == OP_JZ_RESID) di = diag[row];
             if (OP == OP_SPMV_ADD) yi = y[row];
         }
         const bool ok = mbar_wait_bounded(&bar[st], (parity >> st) & 1u);
@@ -180,13 +198,14 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
             for (; k + 3 * G < e; k += 4 * G) {  // four independent gathers in flight
                 const int32_t j0 = sc[k - c0], j1 = sc[k + G - c0], j2 = sc[k + 2 * G - c0], j3 = sc[k + 3 * G - c0];
                 const T a0 = sv[k - v0], a1 = sv[k + G - v0], a2 = sv[k + 2 * G - v0], a3 = sv[k + 3 * G - v0];
-                const T x0 = x[j0], x1 = x[j1], x2 = x[j2], x3 = x[j3];
+                const T x0 = xget<T, TB, OP>(j0, x, b, diag, omega), x1 = xget<T, TB, OP>(j1, x, b, diag, omega),
+                        x2 = xget<T, TB, OP>(j2, x, b, diag, omega), x3 = xget<T, TB, OP>(j3, x, b, diag, omega);
                 acc = fma(a0, x0, acc);
                 acc = fma(a1, x1, acc);
                 acc = fma(a2, x2, acc);
                 acc = fma(a3, x3, acc);
             }
-            for (; k < e; k += G) acc = fma(sv[k - v0], x[sc[k - c0]], acc);
+            for (; k < e; k += G) acc = fma(sv[k - v0], xget<T, TB, OP>(sc[k - c0], x, b, diag, omega), acc);
         }
         if (G > 1) {
             const unsigned mask = group_mask<G>();
@@ -203,7 +222,10 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
                 y[row] = (TO)r;
                 red[0] += (double)r * (double)r;
             } else if (OP == OP_JACOBI) {
-                y[row] = (TO)(xi + omega * ((T)bi - acc) / di);
+                y[row] = (TO)(xi + di * ((T)bi - acc));
+            } else if (OP == OP_JZ_RESID) {
+                xz[row] = di * (T)bi;
+                y[row] = (TO)((T)bi - acc);
             } else {
                 y[row] = (TO)acc;
                 red[0] += (double)xi * (double)acc;
@@ -228,7 +250,7 @@ template <typename T, typename TB, typename TO, int G, int OP>
 __global__ void __launch_bounds__(kS)
 spmv_group_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                   const T *__restrict__ val, const T *__restrict__ x, const TB *__restrict__ b,
-                  const T *__restrict__ diag, T omega, TO *__restrict__ y, Fin fin) {
+                  const T *__restrict__ diag, T omega, TO *__restrict__ y, T *__restrict__ xz, Fin fin) {
     __shared__ double sm[32];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     double red[1] = {0.0};
@@ -236,13 +258,14 @@ spmv_group_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__re
         const int32_t i = i0 + g;
         T acc = T(0);
         if (i < n)
-            for (int32_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(val[e], x[col[e]], acc);
+            for (int32_t e = rp[i] + lane; e < rp[i + 1]; e += G)
+                acc = fma(val[e], xget<T, TB, OP>(col[e], x, b, diag, omega), acc);
         if (G > 1) {
             const unsigned mask = group_mask<G>();
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
         }
-        if (lane == 0 && i < n) spmv_epilogue<T, TB, TO, OP>(i, acc, x, b, diag, omega, y, red[0]);
+        if (lane == 0 && i < n) spmv_epilogue<T, TB, TO, OP>(i, acc, x, b, diag, omega, y, xz, red[0]);
     }
     if (OP == OP_RESID || OP == OP_SPMV_DOT) grid_finish<kS, 1>(red, fin, sm);
 }
@@ -251,7 +274,7 @@ template <typename T, typename TB>
 __global__ void jacobi_zero_kernel(int32_t n, const TB *__restrict__ b, const T *__restrict__ diag, T omega,
                                    T *__restrict__ y) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        y[i] = omega * (T)b[i] / diag[i];
+        y[i] = diag[i] * (T)b[i];  // diag holds omega / a_ii
 }
 
 // x = A_L^{-1} b on the coarsest level (FP64 arithmetic), warp per row
@@ -419,7 +442,7 @@ const float *vals_of<float>(const DCsr &A) { return A.val32.p; }
 
 template <typename T, typename TB, typename TO, int G, int OP>
 static void launch_tile(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
-                        T omega, TO *y, const Fin &fin, int32_t *err, cudaStream_t s) {
+                        T omega, TO *y, T *xz, const Fin &fin, int32_t *err, cudaStream_t s) {
     constexpr int SL = kTileNnz + kTileSlack;
     constexpr int RL = kS / G + 8;
     const size_t smem = (2 * SL + 2 * RL) * sizeof(int32_t) + 2 * SL * sizeof(T);
@@ -434,22 +457,23 @@ static void launch_tile(const char *name, double bytes, const DCsr &M, const T *
     int grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
     grid = std::max(1, std::min(grid, kReduceBlocks));
     RN_LAUNCH(name, bytes, s, (spmv_tile_kernel<T, TB, TO, G, OP>), grid, kS, smem, M.n, ntiles, M.rowptr.p, M.col.p,
-              vals_of<T>(M), x, b, diag, omega, y, fin, err);
+              vals_of<T>(M), x, b, diag, omega, y, xz, fin, err);
 }
 
 template <typename T, typename TB, typename TO, int G, int OP>
 static void launch_group(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
-                         T omega, TO *y, const Fin &fin, cudaStream_t s) {
+                         T omega, TO *y, T *xz, const Fin &fin, cudaStream_t s) {
     int grid = grid_for(M.n, kS / G, 8);
     grid = std::min(grid, kReduceBlocks);
     RN_LAUNCH(name, bytes, s, (spmv_group_kernel<T, TB, TO, G, OP>), grid, kS, 0, M.n, M.rowptr.p, M.col.p,
-              vals_of<T>(M), x, b, diag, omega, y, fin);
+              vals_of<T>(M), x, b, diag, omega, y, xz, fin);
 }
 
 // y = op(M, x, b): picks the staged tile kernel when the rows fit a stage.
+// xz: second output of OP_JZ_RESID (the relaxed iterate).
 template <typename T, typename TB, typename TO, int OP>
 static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, const TB *b, const T *diag, T omega,
-                 TO *y, const Fin &fin) {
+                 TO *y, const Fin &fin, T *xz = nullptr) {
     cudaStream_t s = h.s;
     if (M.n == 0) return;
     const double vb = sizeof(T);
@@ -459,12 +483,13 @@ static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, c
     if (OP == OP_SPMV_ADD) bytes += sizeof(TO) * (double)M.n;
     if (OP == OP_RESID) bytes += sizeof(TB) * (double)M.n;
     if (OP == OP_JACOBI) bytes += (sizeof(TB) + vb) * (double)M.n;
+    if (OP == OP_JZ_RESID) bytes += (sizeof(TB) + 2.0 * vb) * (double)M.n - vb * M.m;  // b, d read; x written
     int32_t *err = h.iflags.p + 8;
     const int G = M.tile_group;
 #define RN_TILE_CASE(GG) \
-    case GG: launch_tile<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, fin, err, s); return;
+    case GG: launch_tile<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, fin, err, s); return;
 #define RN_GROUP_CASE(GG) \
-    case GG: launch_group<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, fin, s); return;
+    case GG: launch_group<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, fin, s); return;
     switch (G) {
         RN_TILE_CASE(1)
         RN_TILE_CASE(2)
@@ -479,7 +504,7 @@ static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, c
         RN_GROUP_CASE(4)
         RN_GROUP_CASE(8)
         RN_GROUP_CASE(16)
-        default: launch_group<T, TB, TO, 32, OP>(name, bytes, M, x, b, diag, omega, y, fin, s); return;
+        default: launch_group<T, TB, TO, 32, OP>(name, bytes, M, x, b, diag, omega, y, xz, fin, s); return;
     }
 #undef RN_TILE_CASE
 #undef RN_GROUP_CASE
@@ -493,7 +518,7 @@ struct LevelBufs<double> {
     static double *x(rn_level &L) { return L.x.p; }
     static double *t(rn_level &L) { return L.t.p; }
     static double *r(rn_level &L) { return L.r.p; }
-    static const double *d(rn_level &L) { return L.diag.p; }
+    static const double *d(rn_level &L) { return L.wd.p; }  // omega / a_ii
 };
 template <>
 struct LevelBufs<float> {
@@ -501,22 +526,52 @@ struct LevelBufs<float> {
     static float *x(rn_level &L) { return L.x32.p; }
     static float *t(rn_level &L) { return L.t32.p; }
     static float *r(rn_level &L) { return L.r32.p; }
-    static const float *d(rn_level &L) { return L.diag32.p; }
+    static const float *d(rn_level &L) { return L.wd32.p; }  // omega / a_ii
 };
 
 struct CycleNames {
-    const char *jacobi, *jacobi0, *resid, *restr, *prolong, *coarse;
+    const char *jacobi, *jacobi0, *resid, *jzresid, *restr, *prolong, *coarse;
 };
 static const CycleNames kNames[2][2] = {
     // [precision: 0 f64, 1 f32][level: 0 finest, 1 coarser]
-    {{"cycle_jacobi_f64_L0", "cycle_jacobi0_f64_L0", "cycle_residual_f64_L0", "cycle_restrict_f64_L0",
-      "cycle_prolong_f64_L0", "cycle_coarse_solve"},
-     {"cycle_jacobi_f64_Lc", "cycle_jacobi0_f64_Lc", "cycle_residual_f64_Lc", "cycle_restrict_f64_Lc",
-      "cycle_prolong_f64_Lc", "cycle_coarse_solve"}},
-    {{"cycle_jacobi_f32_L0", "cycle_jacobi0_f32_L0", "cycle_residual_f32_L0", "cycle_restrict_f32_L0",
-      "cycle_prolong_f32_L0", "cycle_coarse_solve"},
-     {"cycle_jacobi_f32_Lc", "cycle_jacobi0_f32_Lc", "cycle_residual_f32_Lc", "cycle_restrict_f32_Lc",
-      "cycle_prolong_f32_Lc", "cycle_coarse_solve"}}};
+    {{"cycle_jacobi_f64_L0", "cycle_jacobi0_f64_L0", "cycle_residual_f64_L0", "cycle_relax0_residual_f64_L0",
+      "cycle_restrict_f64_L0", "cycle_prolong_f64_L0", "cycle_coarse_solve"},
+     {"cycle_jacobi_f64_Lc", "cycle_jacobi0_f64_Lc", "cycle_residual_f64_Lc", "cycle_relax0_residual_f64_Lc",
+      "cycle_restrict_f64_Lc", "cycle_prolong_f64_Lc", "cycle_coarse_solve"}},
+    {{"cycle_jacobi_f32_L0", "cycle_jacobi0_f32_L0", "cycle_residual_f32_L0", "cycle_relax0_residual_f32_L0",
+      "cycle_restrict_f32_L0", "cycle_prolong_f32_L0", "cycle_coarse_solve"},
+     {"cycle_jacobi_f32_Lc", "cycle_jacobi0_f32_Lc", "cycle_residual_f32_Lc", "cycle_relax0_residual_f32_Lc",
+      "cycle_restrict_f32_Lc", "cycle_prolong_f32_Lc", "cycle_coarse_solve"}}};
+
+// Pre-relaxation from a zero guess followed by the residual on one level:
+// returns the iterate buffer; r receives b - A x.  With one pre-sweep both
+// happen in one fused pass.
+template <typename T, typename TB>
+static T *relax0_and_residual(rn_hierarchy &h, const CycleNames &nm, rn_level &L, const TB *b, T *r) {
+    using LB = LevelBufs<T>;
+    cudaStream_t s = h.s;
+    const int32_t n = L.A.n;
+    const T omega = (T)h.p.omega;
+    const T *d = LB::d(L);
+    T *cur = LB::x(L), *oth = LB::t(L);
+    const Fin none;
+    if (h.p.nu_pre == 1) {
+        spmv<T, TB, T, OP_JZ_RESID>(h, nm.jzresid, L.A, (const T *)nullptr, b, d, omega, r, none, cur);
+        return cur;
+    }
+    for (int k = 0; k < h.p.nu_pre; k++) {
+        if (k == 0) {
+            RN_LAUNCH(nm.jacobi0, (sizeof(TB) + 2.0 * sizeof(T)) * n, s, (jacobi_zero_kernel<T, TB>),
+                      grid_for(n, 1024), 256, 0, n, b, d, omega, cur);
+        } else {
+            spmv<T, TB, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, b, d, omega, oth, none);
+            std::swap(cur, oth);
+        }
+    }
+    if (h.p.nu_pre == 0) RN_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(T) * n, s));
+    spmv<T, TB, T, OP_RESID>(h, nm.resid, L.A, cur, b, nullptr, T(0), r, none);
+    return cur;
+}
 
 // One cycle on level l >= 1 with zero initial guess; b_l holds the right-hand
 // side.  Returns the buffer holding the result.
@@ -537,19 +592,9 @@ static T *vcycle_level(rn_hierarchy &h, int l) {
     }
     const T omega = (T)h.p.omega;
     const T *d = LB::d(L);
-    T *cur = LB::x(L), *oth = LB::t(L);
-    for (int k = 0; k < h.p.nu_pre; k++) {
-        if (k == 0) {
-            RN_LAUNCH(nm.jacobi0, 3.0 * sizeof(T) * n, s, (jacobi_zero_kernel<T, T>), grid_for(n, 1024), 256, 0, n, b,
-                      d, omega, cur);
-        } else {
-            spmv<T, T, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, b, d, omega, oth, none);
-            std::swap(cur, oth);
-        }
-    }
-    if (h.p.nu_pre == 0) RN_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(T) * n, s));
     T *r = LB::r(L);
-    spmv<T, T, T, OP_RESID>(h, nm.resid, L.A, cur, b, nullptr, T(0), r, none);
+    T *cur = relax0_and_residual<T, T>(h, nm, L, b, r);
+    T *oth = (cur == LB::x(L)) ? LB::t(L) : LB::x(L);
     rn_level &Lc = *h.lev[l + 1];
     spmv<T, T, T, OP_SPMV>(h, nm.restr, L.R, r, (const T *)nullptr, nullptr, T(0), LB::b(Lc), none);
     T *xc = vcycle_level<T>(h, l + 1);
@@ -577,19 +622,9 @@ static void vcycle_top(rn_hierarchy &h, const double *rhs, double *out) {
     }
     const T omega = (T)h.p.omega;
     const T *d = LB::d(L);
-    T *cur = LB::x(L), *oth = LB::t(L);
-    for (int k = 0; k < h.p.nu_pre; k++) {
-        if (k == 0) {
-            RN_LAUNCH(nm.jacobi0, (8.0 + 2.0 * sizeof(T)) * n, s, (jacobi_zero_kernel<T, double>), grid_for(n, 1024),
-                      256, 0, n, rhs, d, omega, cur);
-        } else {
-            spmv<T, double, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, rhs, d, omega, oth, none);
-            std::swap(cur, oth);
-        }
-    }
-    if (h.p.nu_pre == 0) RN_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(T) * n, s));
     T *r = LB::r(L);
-    spmv<T, double, T, OP_RESID>(h, nm.resid, L.A, cur, rhs, nullptr, T(0), r, none);
+    T *cur = relax0_and_residual<T, double>(h, nm, L, rhs, r);
+    T *oth = (cur == LB::x(L)) ? LB::t(L) : LB::x(L);
     rn_level &Lc = *h.lev[1];
     spmv<T, T, T, OP_SPMV>(h, nm.restr, L.R, r, (const T *)nullptr, nullptr, T(0), LevelBufs<T>::b(Lc), none);
     T *xc = vcycle_level<T>(h, 1);
@@ -652,6 +687,15 @@ static void set_tile_group(rn_hierarchy &h, DCsr &M, int32_t *tmp) {
     M.tile_group = tile_group(M.maxlen);
 }
 
+__global__ void omega_over_diag_kernel(int64_t n, double omega, const double *__restrict__ d,
+                                       double *__restrict__ wd, float *__restrict__ wd32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double w = omega / d[i];
+        wd[i] = w;
+        if (wd32) wd32[i] = (float)w;
+    }
+}
+
 void prepare_solve(rn_hierarchy &h) {
     cudaStream_t s = h.s;
     const bool mixed = h.p.precision == RN_MIXED;
@@ -671,10 +715,16 @@ void prepare_solve(rn_hierarchy &h) {
             L.x32.alloc(n, s);
             L.t32.alloc(n, s);
             L.r32.alloc(n, s);
+        }
+        // relaxation weights omega / a_ii (a multiply in the sweeps instead of
+        // a divide: FP64 division is slow on this part's reduced FP64 pipe)
+        L.wd.alloc(n, s);
+        if (mixed) L.wd32.alloc(n, s);
+        RN_LAUNCH("prepare", 20.0 * n, s, omega_over_diag_kernel, grid_for(n, 1024), 256, 0, (int64_t)n, h.p.omega,
+                  L.diag.p, L.wd.p, mixed ? L.wd32.p : nullptr);
+        if (mixed) {
             L.A.val32.alloc(L.A.nnz, s);
             to_float(L.A.val.p, L.A.val32.p, L.A.nnz, s);
-            L.diag32.alloc(n, s);
-            to_float(L.diag.p, L.diag32.p, n, s);
             if (L.P.nnz) {
                 L.P.val32.alloc(L.P.nnz, s);
                 to_float(L.P.val.p, L.P.val32.p, L.P.nnz, s);
