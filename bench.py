@@ -302,13 +302,19 @@ def main():
     rn.profile_enable(False)
     total_ms = sum(v["ms"] for v in prof.values())
     top = sorted(prof.items(), key=lambda kv: -kv[1]["ms"])
-    name, st = top[0]
+    # the roofline is claimed for the dominant kernel among those that stream
+    # level-0-sized data; coarse-level kernels ("_Lc", the dense coarse solve)
+    # work on L2-resident data and are latency-bound (their times under
+    # per-launch events also include host submission gaps)
+    big = [(k, v) for k, v in top if not k.endswith("_Lc") and k != "cycle_coarse_solve" and v["bytes"] > 0]
+    name, st = big[0] if big else top[0]
     peak, peak_kind = load_peaks()
     achieved = st["bytes"] / (st["ms"] / 1e3) / 1e9 if st["ms"] > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                 "launches": st["launches"], "avg_launch_us": st["ms"] * 1e3 / max(st["launches"], 1),
-                "share_of_step_device_time": st["ms"] / total_ms if total_ms else None}
+                "share_of_step_device_time": st["ms"] / total_ms if total_ms else None,
+                "rule": "dominant kernel on level-0-sized data (coarse levels are L2-resident and latency-bound)"}
     kernels = {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
                    "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] > 0 else None}
                for k, v in top[:12]}

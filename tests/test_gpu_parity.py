@@ -45,7 +45,9 @@ def dev(torch_dev, a):
 
 def gpu_hierarchy(rn, torch_dev, pr, **over):
     A = pr.A
-    params = rn.params_from_config(pr.params, keep_aux=1, **over)
+    kw = dict(keep_aux=1)
+    kw.update(over)
+    params = rn.params_from_config(pr.params, **kw)
     Bh = None if pr.Bhat is None else dev(torch_dev, pr.Bhat.reshape(-1))
     return rn.Hierarchy(dev(torch_dev, A.rowptr), dev(torch_dev, A.col), dev(torch_dev, A.val),
                         dev(torch_dev, pr.B.reshape(-1)), Bh, params=params)
