@@ -291,33 +291,36 @@ def main():
     step_s = job_step_seconds(float(np.mean(times)), dev)
     times_other, infos_other = timed(other, args.steps)
 
-    # per-kernel device times of one step (events around every launch)
-    rn.profile_reset()
-    rn.profile_enable(True)
-    flush.fill_(1.0)
-    torch.cuda.synchronize()
-    step(prec)
-    torch.cuda.synchronize()
-    prof = rn.profile_read()
-    rn.profile_enable(False)
-    total_ms = sum(v["ms"] for v in prof.values())
-    top = sorted(prof.items(), key=lambda kv: -kv[1]["ms"])
-    # the roofline is claimed for the dominant kernel among those that stream
-    # level-0-sized data; coarse-level kernels ("_Lc", the dense coarse solve)
-    # work on L2-resident data and are latency-bound (their times under
-    # per-launch events also include host submission gaps)
-    big = [(k, v) for k, v in top if not k.endswith("_Lc") and k != "cycle_coarse_solve" and v["bytes"] > 0]
-    name, st = big[0] if big else top[0]
+    # per-launch device times of the solve's level-0 operations, each timed in
+    # isolation with CUDA events on the hierarchy's stream, a 256 MB write before
+    # every launch (cold L2; the GPU stays busy while the launch is enqueued).
+    # Each runs once per outer iteration.
+    h = rn.Hierarchy(rp, ci, va, Bd, params=params(prec), stream=sptr)
+    xd.zero_()
+    h.solve(bd, xd, rtol=1e-8, maxit=5000)
+    ops = {}
+    for op in range(rn.RN_OP_COUNT):
+        if op == rn.RN_OP_CG_RZ:  # not issued: the cycle's last level-0 sweep carries these reductions
+            continue
+        r = h.time_op(op, reps=20)
+        if r is not None:
+            ops[r[0]] = {"us": r[1], "bytes": r[2]}
+    h.close()
+    iters = infos[0]["iters"]
     peak, peak_kind = load_peaks()
-    achieved = st["bytes"] / (st["ms"] / 1e3) / 1e9 if st["ms"] > 0 else 0.0
+    bw = {k: v for k, v in ops.items() if v["bytes"] > 0}
+    name = max(bw, key=lambda k: bw[k]["us"])
+    st = bw[name]
+    achieved = st["bytes"] / (st["us"] * 1e-6) / 1e9
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                "launches": st["launches"], "avg_launch_us": st["ms"] * 1e3 / max(st["launches"], 1),
-                "share_of_step_device_time": st["ms"] / total_ms if total_ms else None,
-                "rule": "dominant kernel on level-0-sized data (coarse levels are L2-resident and latency-bound)"}
-    kernels = {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
-                   "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] > 0 else None}
-               for k, v in top[:12]}
+                "avg_launch_us": st["us"], "algorithmic_bytes": st["bytes"], "launches_per_step": iters,
+                "share_of_step": st["us"] * 1e-6 * iters / step_s,
+                "rule": "longest level-0 launch of the outer iteration (each runs once per iteration), timed "
+                        "alone with CUDA events after a 256 MB L2 flush"}
+    kernels = {k: {"us": round(v["us"], 2), "launches_per_step": iters,
+                   "GBps": round(v["bytes"] / (v["us"] * 1e-6) / 1e9, 1) if v["bytes"] > 0 else None}
+               for k, v in sorted(ops.items(), key=lambda kv: -kv[1]["us"])}
 
     # end to end through the C ABI with host buffers
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -367,7 +370,7 @@ def main():
             "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roofline,
-            "kernels_top": kernels,
+            "level0_launches": kernels,
             "gpu_launches": launches // max(args.steps, 1),
             "gpu_launches_timed_region": launches,
             "clocks": clk.summary(),

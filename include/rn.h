@@ -91,6 +91,9 @@ typedef struct {
     int restart;             /* FGMRES restart length */
     int use_graphs;          /* 1: capture the preconditioner cycle in a CUDA graph */
     int keep_aux;            /* 1: keep S, N, T, agg, roots per level for rn_export_* */
+    int coarse_cluster;      /* > 0: the cycle on the smallest levels (every operation taking at most
+                                this many passes of one thread-block cluster's threads) runs as one
+                                cluster launch; 0: one launch per operation on every level */
     void *stream;            /* cudaStream_t */
 } rn_params;
 
@@ -117,7 +120,8 @@ typedef struct rn_hierarchy rn_hierarchy;
 
 /* Fill *p with the defaults (theta 0.25, d 2, 4 CG sweeps, no filtering,
  * max_coarse 64, 4 candidate sweeps, omega 2/3, symmetric, V(1,1), FP64,
- * CG outer, graphs on).  Returns RN_EINVAL for p == NULL. */
+ * CG outer, graphs on, coarse_cluster 1).  Returns RN_EINVAL for
+ * p == NULL. */
 rn_status rn_default_params(rn_params *p);
 
 /* Build the hierarchy (Alg. 3) for A with candidates B (n x k, row-major,
@@ -163,7 +167,7 @@ rn_status rn_energy_min(const rn_csr *A, const rn_csr *N, const int32_t *rowtype
  * latency-critical loop that cannot afford an allocation's synchronisation,
  * a plugin host that forbids libraries to allocate.  Same arguments and result
  * as rn_energy_min with method RN_ENERGY_CG; the call makes no allocation: its
- * scratch is one statically allocated device array of about 14 MB, which every
+ * scratch is one statically allocated device array of about 16 MB, which every
  * GPU that loads this library keeps until the process exits.
  *   Limits: A->n_rows <= 262144 and N->nnz <= 524288; larger inputs return
  *   RN_EINVAL with a message naming the limit.
@@ -210,6 +214,35 @@ rn_status rn_profile_read(rn_kernel_stat *out, int max, int *count);
 /* Number of library kernels launched by this process so far (kernels inside
  * a replayed CUDA graph are counted one by one). */
 int64_t rn_kernel_launches(void);
+
+/* Measurement hook (no counterpart in the paper): time one level-0 launch of
+ * the solve in isolation.  The operation is enqueued `reps` times on the
+ * hierarchy's stream exactly as rn_solve issues it (kernel, launch shape,
+ * buffers), each launch bracketed by CUDA events and preceded by a write of
+ * `flush_bytes` bytes to a buffer the call allocates (0: no write), so that
+ * every launch starts with a cold L2 and the GPU is busy while the launch is
+ * enqueued.  Outputs: *us the mean device time of one launch in microseconds,
+ * *bytes its algorithmic bytes (0 for RN_OP_COARSE_CLUSTER), name (>= 48
+ * chars, may be NULL) the launch's name.  The solve workspaces are left in an
+ * unspecified state; the hierarchy stays valid (rn_solve and rn_vcycle
+ * initialise them).  Returns RN_EINVAL for an operation this hierarchy does
+ * not run (a one-level hierarchy, RN_OP_COARSE_CLUSTER with the cluster path
+ * off) or reps outside [1, 100000]. */
+enum {
+    RN_OP_OUTER_SPMV = 0,      /* q = A p with <p, q> (FP64) */
+    RN_OP_RELAX0_RESIDUAL = 1, /* level 0: first sweep from zero fused with the residual */
+    RN_OP_JACOBI_OUT = 2,      /* level 0: last post-sweep, writing the FP64 preconditioned vector z,
+                                  fused with the outer CG's <r, z> (and <z, r_old>) */
+    RN_OP_RESTRICT = 3,        /* b_1 = R_0 r_0 */
+    RN_OP_PROLONG = 4,         /* x_0 += P_0 x_1 */
+    RN_OP_CG_XR = 5,           /* x += alpha p, r -= alpha q, ||r||^2 */
+    RN_OP_CG_RZ = 6,           /* <r, z> (and <z, r_old>) on its own: used only when the cycle has no
+                                  level-0 post-sweep */
+    RN_OP_CG_P = 7,            /* p = z + beta p */
+    RN_OP_COARSE_CLUSTER = 8,  /* the cycle on the smallest levels, one cluster launch */
+    RN_OP_COUNT = 9
+};
+rn_status rn_time_op(rn_hierarchy *h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, char *name);
 
 const char *rn_last_error(void);
 const char *rn_status_string(rn_status s);

@@ -415,7 +415,8 @@ static double pattern_energy(const orc_csr *A, const orc_csr *P) {
  * report; we run preconditioned CG in the Frobenius inner product on the
  * constraint space, with the operator X -> Proj(Mask_N(A X)), started from
  * P = T, preconditioned by the row scaling D^{-1} (which commutes with the
- * row projection; precond = 0 disables it).
+ * row projection; precond = 0 disables it), formed once as the inverted
+ * diagonal and applied as a product.
  * energy_trace (optional, sweeps+1 entries): energy before and after each sweep.
  */
 int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc,
@@ -430,6 +431,9 @@ int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, cons
     orc_csr Dm = *P; /* Dd viewed on the pattern */
     Dm.val = Dd;
     int it_done = sweeps;
+    /* the preconditioner D^{-1}: the inverted diagonal, applied as a product */
+    double *dinv = (double *)orc_xmalloc((size_t)(P->nrows > 0 ? P->nrows : 1) * sizeof(double));
+    for (int32_t i = 0; i < P->nrows; i++) dinv[i] = 1.0 / diag[i];
     if (energy_trace) energy_trace[0] = pattern_energy(A, P);
     orc_masked_product(A, P, &W);
     orc_project(&W, rowtype, Bc);
@@ -438,7 +442,7 @@ int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, cons
     for (int it = 0; it < sweeps; it++) {
         for (int32_t i = 0; i < P->nrows; i++)
             for (int32_t q = P->rowptr[i]; q < P->rowptr[i + 1]; q++)
-                Z[q] = precond ? R[q] / diag[i] : R[q];
+                Z[q] = precond ? R[q] * dinv[i] : R[q];
         double rho = frob_dot(P, R, Z);
         if (it == 0) rho0 = rho;
         /* converged to rounding: further steps only amplify noise */
@@ -464,6 +468,7 @@ int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, cons
     if (energy_trace)
         for (int it = it_done; it < sweeps; it++) energy_trace[it + 1] = energy_trace[it_done];
     free(diag);
+    free(dinv);
     free(R);
     free(Z);
     free(Dd);

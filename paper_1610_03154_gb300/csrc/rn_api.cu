@@ -12,6 +12,8 @@ const std::string &last_error_ref();
 rn_hierarchy::~rn_hierarchy() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     if (graph) cudaGraphDestroy(graph);
+    if (cg_exec) cudaGraphExecDestroy(cg_exec);
+    if (cg_graph) cudaGraphDestroy(cg_graph);
 }
 
 #define RN_API_BEGIN try {
@@ -54,6 +56,7 @@ extern "C" rn_status rn_default_params(rn_params *p) {
     p->restart = 30;
     p->use_graphs = 1;
     p->keep_aux = 0;
+    p->coarse_cluster = 1;
     p->stream = nullptr;
     return RN_OK;
 }
@@ -71,6 +74,7 @@ static void check_params(const rn_params *p) {
     if (p->outer < RN_OUTER_STATIONARY || p->outer > RN_OUTER_FGMRES) fail(RN_EINVAL, "outer");
     if (p->outer == RN_OUTER_FGMRES && (p->restart < 1 || p->restart > 1000)) fail(RN_EINVAL, "restart");
     if (!(p->omega > 0.0)) fail(RN_EINVAL, "omega must be > 0");
+    if (p->coarse_cluster < 0) fail(RN_EINVAL, "coarse_cluster must be >= 0");
 }
 
 extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bhat, int k, int location,
@@ -179,6 +183,20 @@ extern "C" rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x) {
     RN_API_END
 }
 
+extern "C" rn_status rn_time_op(rn_hierarchy *h, int op, int reps, int64_t flush_bytes, double *us, double *bytes,
+                                char *name) {
+    RN_API_BEGIN
+    if (!h || !us || !bytes) rn::fail(RN_EINVAL, "null argument");
+    std::string nm;
+    rn::time_op(*h, op, reps, flush_bytes, us, bytes, nm);
+    if (name) {
+        std::strncpy(name, nm.c_str(), 47);
+        name[47] = '\0';
+    }
+    return RN_OK;
+    RN_API_END
+}
+
 namespace {
 // A stream the call owns when the caller passes none (blocking, so it stays
 // ordered with the legacy default stream).
@@ -234,6 +252,7 @@ extern "C" rn_status rn_energy_min(const rn_csr *A, const rn_csr *N, const int32
     c.precond = precond ? 1 : 0;
     c.method = method;
     rn::Pattern pat{n, N->n_cols, N->nnz, N->rowptr, N->col};
+    rn::reciprocal(diag.p, diag.p, n, s);  // the preconditioner D^{-1}
     rn::energy_min(c, Av, pat, P, rowtype, Bc, diag.p, sweeps);
     RN_CUDA_CHECK(cudaStreamSynchronize(s));
     return RN_OK;

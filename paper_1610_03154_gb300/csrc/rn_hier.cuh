@@ -36,7 +36,7 @@ struct rn_hierarchy {
     rn::DVec<double> scal;                        // device scalars
     rn::DVec<int32_t> iflags;                     // device int flags
     // outer-iteration vectors (level-0 size)
-    rn::DVec<double> r, z, pv, q, w, rold;
+    rn::DVec<double> r, z, pv, q, w, rold, xs;     // xs: the CG solve graph's iterate
     rn::DVec<double> V, Z, H, gv;                 // FGMRES basis, preconditioned basis, Hessenberg, rhs
     // CUDA graph of one preconditioner application (FP64 or FP32 cycle)
     cudaGraph_t graph = nullptr;
@@ -44,6 +44,13 @@ struct rn_hierarchy {
     const double *graph_in = nullptr;
     double *graph_out = nullptr;
     int64_t graph_kernels = 0;                    // kernel nodes in the captured cycle
+    // CUDA graph of the whole outer CG loop (conditional WHILE / IF nodes)
+    cudaGraph_t cg_graph = nullptr;
+    cudaGraphExec_t cg_exec = nullptr;
+    int64_t cg_kernels[2] = {0, 0};               // kernel nodes of the two halves of an iteration
+    // cycle below level sub_k run by one thread-block cluster (sub_k < 0: off)
+    rn::DVec<unsigned char> sub_desc;             // SubPhase<T>[sub_nph]
+    int sub_k = -1, sub_cs = 0, sub_nph = 0;
     // statistics
     double setup_ms = 0.0;
     int agg_rounds = 0;
@@ -51,6 +58,30 @@ struct rn_hierarchy {
 };
 
 namespace rn {
+// Smallest coarse levels in one cluster launch (rn_cluster.cu)
+constexpr int32_t kSubMaxCoarse = 1024;  // coarsest size the cluster solves densely
+constexpr int kSubMaxPhases = 96;        // longest phase list the kernel stages
+enum SubOp { SUB_SPMV = 0, SUB_SPMV_ADD = 1, SUB_RESID = 2, SUB_JACOBI = 3, SUB_JZ_RESID = 4, SUB_SCALE = 5,
+             SUB_COARSE = 6 };
+template <typename T>
+struct SubMat {  // CSR view with the lanes per row the cluster kernel uses (trivial type: staged in shared memory)
+    int32_t n;
+    int g;
+    const int32_t *rp, *col;
+    const T *val;
+};
+// One phase: y = op(M, x, b) with relaxation weights d (omega / a_ii); xz is
+// the second output of SUB_JZ_RESID; SUB_COARSE reads the dense inverse.
+template <typename T>
+struct SubPhase {
+    int op;
+    SubMat<T> M;
+    const T *x, *b, *d;
+    T *y, *xz;
+};
+void prepare_subcycle(rn_hierarchy &h);
+template <typename T>
+void launch_subcycle(rn_hierarchy &h, T *cur_k, const char *name);
 // setup (rn_setup.cu)
 void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const double *Bhat0);
 
@@ -60,8 +91,8 @@ struct Pattern {  // borrowed view of a fixed interpolation pattern
     const int32_t *rp, *col;
 };
 // Context of one energy minimisation: stream, reduction scratch, scalar block
-// (>= 8 doubles), flags (>= 2 ints), settings, and optional CG workspaces
-// (nnz(N) doubles each; allocated internally when null).
+// (>= 8 doubles), flags (>= 2 ints), settings, and optional workspaces
+// (CG: nnz(N) doubles each; rs2: n doubles; allocated internally when null).
 struct EmCtx {
     cudaStream_t s = nullptr;
     double *partial = nullptr;
@@ -71,12 +102,17 @@ struct EmCtx {
     int precond = 1;
     int method = RN_ENERGY_CG;
     double *R = nullptr, *Dd = nullptr, *W = nullptr;
+    double *rs2 = nullptr;  // n rows: the row projection's scales (allocated internally when null)
 };
+// dinv: the inverted diagonal of A (CG's preconditioner D^{-1} when c.precond)
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
-                const double *Bc, const double *diag, int sweeps);
+                const double *Bc, const double *dinv, int sweeps);
 // solve (rn_solve.cu)
 void prepare_solve(rn_hierarchy &h);
 rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int maxit, rn_solve_info *info);
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out);
 void cycle_checked(rn_hierarchy &h, const double *rhs, double *out);  // + staging-error check
+void time_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, std::string &name);
+template <typename T>
+T *pre_smoothed(rn_level &L, int nu_pre);
 }  // namespace rn

@@ -97,6 +97,20 @@ inline CsrView view(const DCsr &a) { return CsrView{a.n, a.m, a.nnz, a.rowptr.p,
 // --------------------------------------------------------------- launches
 int num_sms();
 int grid_for(int64_t work_items, int items_per_block, int blocks_per_sm = 8);
+// Blocks of `fn` (with this block size and dynamic shared memory) resident on
+// one SM, from the occupancy calculator (registers included); cached.
+int resident_blocks(const void *fn, int block, size_t smem);
+// Grid for a grid-stride kernel: enough blocks for the work, at most one wave
+// of resident blocks (and at most cap).
+template <typename K>
+int grid_resident(K kernel, int block, size_t smem, int64_t work_items, int items_per_block,
+                  int cap = 1 << 30) {
+    int64_t need = (work_items + items_per_block - 1) / items_per_block;
+    const int64_t wave = (int64_t)resident_blocks((const void *)kernel, block, smem) * num_sms();
+    if (need > wave) need = wave;
+    if (need > cap) need = cap;
+    return (int)(need < 1 ? 1 : need);
+}
 
 // Profiled launch: records CUDA events around the kernel when profiling is on
 // and attributes `bytes` of algorithmic traffic to `name`.
@@ -119,6 +133,31 @@ int64_t launches_so_far();
         kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);        \
         ::rn::check_launch(name);                                          \
     } while (0)
+
+// Launch with programmatic dependent launch (PDL): the kernel may be
+// scheduled while its predecessor in the stream (or graph) is still draining.
+// Such kernels call pdl_wait() before they read anything the predecessor
+// writes and before their own first global write; on a launch without the
+// attribute pdl_wait() returns at once.
+template <typename... K, typename... A>
+void launch_pdl(const char *name, double bytes, cudaStream_t s, void (*kernel)(K...), dim3 grid, dim3 block,
+                size_t smem, A &&...args) {
+    ProfScope ps(name, bytes, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+    if (e != cudaSuccess) fail(RN_ECUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+}
+#define RN_LAUNCH_PDL(name, bytes, stream, kernel, grid, block, smem, ...) \
+    ::rn::launch_pdl((name), (double)(bytes), (stream), kernel, dim3(grid), dim3(block), (size_t)(smem), __VA_ARGS__)
 
 template <typename T>
 void h2d(T *dst, const T *src, size_t n, cudaStream_t s) {
@@ -160,6 +199,8 @@ void extract_diag(const CsrView &A, double *diag, int32_t *bad, cudaStream_t s);
 // Transpose with sorted rows (values optional).
 void transpose(const CsrView &A, bool with_val, DCsr &At, cudaStream_t s);
 void to_float(const double *x, float *y, int64_t n, cudaStream_t s);
+// y = 1 / x elementwise (y may be x)
+void reciprocal(const double *x, double *y, int64_t n, cudaStream_t s);
 
 // --------------------------------------------------------------- products (rn_spgemm.cu)
 // C = A*B in one hash pass per row: the symbolic pattern (explicit zeros kept,
@@ -173,7 +214,11 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s);
 struct ProjArgs {
     const int32_t *rowtype;  // 0 free, 1 root, 2 unaggregated
     const double *Bc;        // coarse candidates
+    const double *rs2;       // per row 1 / sum_{j in N_i} Bc_j^2 (proj_scales)
 };
+// rs2 for ProjArgs: the row projection's scale on pattern N (n rows)
+void proj_scales(int32_t n, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, const int32_t *rowtype,
+                 const double *Bc, double *rs2, cudaStream_t s);
 void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, int32_t nc,
                          const double *X, double *W, const ProjArgs &pa, double scale, const double *Y,
                          const Fin &fin, cudaStream_t s);
@@ -186,6 +231,9 @@ double now_ms();
 
 // --------------------------------------------------------------- device helpers
 namespace rn {
+// Wait until the preceding grid in the stream has completed and its memory
+// is visible (programmatic dependent launch); a no-op for ordinary launches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -233,7 +281,11 @@ __device__ __forceinline__ double block_sum(double v, double *smem32) {
 }
 
 // What the last block does with the finished sums of a grid reduction.
-enum FinMode { FIN_NONE = 0, FIN_STORE = 1, FIN_CG_RHO = 2, FIN_CG_DW = 3, FIN_RZ = 4 };
+enum FinMode { FIN_NONE = 0, FIN_STORE = 1, FIN_CG_RHO = 2, FIN_CG_DW = 3, FIN_RZ = 4, FIN_PQ = 5, FIN_XR = 6 };
+// Outer CG scalars in sc: [8] ||r||^2, [9] <r,z>, [10] <p,Ap>, [11] <z,r_old>,
+// [12] alpha, [13] beta, [14] previous <r,z>, [17] ||b||^2, [18] ||b|| (1 when
+// b = 0), [19] rtol; int flags fl: [9] iterations done, [10] iteration limit,
+// [11] converged.
 struct Fin {
     int mode = FIN_NONE;
     double *partial = nullptr;   // >= 2 * kReduceBlocks slots
@@ -241,8 +293,11 @@ struct Fin {
     double *out = nullptr;       // FIN_STORE: out[0] = s0 (and out[1] = s1 when two sums)
     double *sc = nullptr;        // scalar block of the CG recurrences
     int32_t *fl = nullptr;       // fl[0]: energy-minimisation "done"
-    int it = 0;
+    int it = 0;                  // energy CG: iteration; FIN_RZ: bit 0 first, bit 1 flexible
     double stop = 0.0;
+    // FIN_XR inside the solve graph: conditional handles of the next
+    // iteration and of this iteration's preconditioning half (0: none)
+    unsigned long long cond_loop = 0, cond_body = 0;
 };
 
 __device__ __forceinline__ void apply_fin(const Fin &f, const double *s, int nv) {
@@ -273,11 +328,29 @@ __device__ __forceinline__ void apply_fin(const Fin &f, const double *s, int nv)
             f.sc[4] = f.sc[0] / s[0];
             break;
         }
-        case FIN_RZ:  // outer CG: keep the previous <r,z>, store <r,z> and <z, r_old>
+        case FIN_RZ: {  // outer CG: keep the previous <r,z>, store <r,z> and <z, r_old>; beta
             f.sc[14] = f.sc[9];
             f.sc[9] = s[0];
-            if (nv > 1) f.sc[11] = s[1];
+            const double zro = nv > 1 ? s[1] : 0.0;
+            f.sc[11] = zro;
+            // beta = <z,r>/<z,r>_prev, or (<z,r> - <z,r_old>)/<z,r>_prev for the flexible variant
+            f.sc[13] = (f.it & 1) ? 0.0 : ((f.it & 2) ? s[0] - zro : s[0]) / f.sc[14];
             break;
+        }
+        case FIN_PQ:  // outer CG: <p, Ap> and alpha = <r,z> / <p, Ap>
+            f.sc[10] = s[0];
+            f.sc[12] = f.sc[9] / s[0];
+            break;
+        case FIN_XR: {  // outer CG: ||r||^2, iteration count, stopping test
+            f.sc[8] = s[0];
+            const int it = ++f.fl[9];
+            const bool conv = sqrt(s[0]) / f.sc[18] < f.sc[19];
+            const bool stop = conv || it >= f.fl[10];
+            f.fl[11] = conv ? 1 : 0;
+            if (f.cond_loop) cudaGraphSetConditional(f.cond_loop, stop ? 0u : 1u);
+            if (f.cond_body) cudaGraphSetConditional(f.cond_body, stop ? 0u : 1u);
+            break;
+        }
         default: break;
     }
 }

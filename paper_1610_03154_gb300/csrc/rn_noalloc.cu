@@ -32,7 +32,8 @@ constexpr size_t kOffDiag = 0;
 constexpr size_t kOffR = align_up(kOffDiag + sizeof(double) * kNaMaxRows);
 constexpr size_t kOffD = align_up(kOffR + sizeof(double) * kNaMaxPattern);
 constexpr size_t kOffW = align_up(kOffD + sizeof(double) * kNaMaxPattern);
-constexpr size_t kOffPartial = align_up(kOffW + sizeof(double) * kNaMaxPattern);
+constexpr size_t kOffS2 = align_up(kOffW + sizeof(double) * kNaMaxPattern);
+constexpr size_t kOffPartial = align_up(kOffS2 + sizeof(double) * kNaMaxRows);
 constexpr size_t kOffSc = align_up(kOffPartial + sizeof(double) * 2 * kReduceBlocks);
 constexpr size_t kOffCounter = align_up(kOffSc + sizeof(double) * 64);
 constexpr size_t kOffFlags = align_up(kOffCounter + sizeof(unsigned) * 4);
@@ -104,7 +105,9 @@ extern "C" rn_status rn_energy_min_noalloc(const rn_csr *A, const rn_csr *N, con
         c.R = reinterpret_cast<double *>(base + kOffR);
         c.Dd = reinterpret_cast<double *>(base + kOffD);
         c.W = reinterpret_cast<double *>(base + kOffW);
+        c.rs2 = reinterpret_cast<double *>(base + kOffS2);
         Pattern pat{n, N->n_cols, N->nnz, N->rowptr, N->col};
+        reciprocal(diag, diag, n, s);  // the preconditioner D^{-1}, in place
         energy_min(c, Av, pat, P, rowtype, Bc, diag, sweeps);
         RN_CUDA_CHECK(cudaStreamSynchronize(s));
         return RN_OK;

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <chrono>
 #include <map>
+#include <tuple>
 #include <mutex>
 
 #include "rn_internal.cuh"
@@ -81,6 +82,22 @@ int grid_for(int64_t work_items, int items_per_block, int blocks_per_sm) {
     int64_t cap = (int64_t)num_sms() * blocks_per_sm;
     if (need < 1) need = 1;
     return (int)(need < cap ? need : cap);
+}
+
+int resident_blocks(const void *fn, int block, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, size_t, int>, int> cache;
+    int dev = 0;
+    RN_CUDA_CHECK(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(fn, block, smem, dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    RN_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem));
+    if (per_sm < 1) per_sm = 1;
+    cache[key] = per_sm;
+    return per_sm;
 }
 
 void check_launch(const char *name) {
@@ -309,8 +326,7 @@ __global__ void dot_kernel(const double *__restrict__ x, const double *__restric
 
 void dot(const double *x, const double *y, int64_t n, double *result, cudaStream_t s, double *partial,
          unsigned *counter) {
-    int nb = grid_for(n, kRedThreads * 4, 8);
-    if (nb > kReduceBlocks) nb = kReduceBlocks;
+    const int nb = grid_resident((const void *)dot_kernel, kRedThreads, 0, n, kRedThreads * 4, kReduceBlocks);
     Fin f;
     f.mode = FIN_STORE;
     f.partial = partial;
@@ -341,6 +357,15 @@ void fill_f64(double *p, double v, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     RN_LAUNCH("fill", 8.0 * n, s, fill_f64_kernel, grid_for(n, 1024), 256, 0, p, v, n);
 }
+__global__ void reciprocal_kernel(int64_t n, const double *x, double *y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = 1.0 / x[i];
+}
+void reciprocal(const double *x, double *y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    RN_LAUNCH("reciprocal", 16.0 * n, s, reciprocal_kernel, grid_for(n, 1024), 256, 0, n, x, y);
+}
+
 void to_float(const double *x, float *y, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     RN_LAUNCH("to_float", 12.0 * n, s, to_float_kernel, grid_for(n, 1024), 256, 0, x, y, n);

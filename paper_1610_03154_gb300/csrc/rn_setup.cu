@@ -45,40 +45,69 @@ __device__ __forceinline__ double soc_value(double aij, double di, double dj) {
     return __ddiv_rn(fabs(aij), __dsqrt_rn(__dmul_rn(fabs(di), fabs(dj))));
 }
 
+// soc_value(aij, di, dj) >= thr, decided exactly as the FP64 expression
+// decides it.  The test is |a|^2 >= thr^2 |di dj|; evaluated in FP32 its
+// relative error is below 1e-6 when every operand lies in [2^-40, 2^40] (no
+// FP32 underflow or overflow on the way), so a margin of 1e-5 either side
+// settles it; only entries within that band of the threshold (or with
+// operands out of range) take the FP64 square root and division.
+__device__ __forceinline__ bool soc_strong(double aij, double di, double dj, double thr, float thr2f, bool fast) {
+    const double aa = fabs(aij), ai = fabs(di), aj = fabs(dj);
+    constexpr double lo = 0x1p-40, hi = 0x1p40;
+    if (fast && aa >= lo && aa <= hi && ai >= lo && ai <= hi && aj >= lo && aj <= hi) {
+        const float af = (float)aa;
+        const float lhs = af * af;
+        const float rhs = thr2f * ((float)ai * (float)aj);
+        if (lhs > rhs * 1.00001f) return true;
+        if (lhs < rhs * 0.99999f) return false;
+    }
+    return soc_value(aij, di, dj) >= thr;
+}
+
+// Pass 1 (FILL false): per row the count of S's entries (strong entries plus
+// the diagonal), each strong entry's value v in vtmp (-1 for the others) and
+// the row's largest strong value.  Pass 2: S's columns, and values v / vmax
+// (1 on the diagonal).
 template <bool FILL>
 __global__ void strength_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                                 const double *__restrict__ aval, const double *__restrict__ diag, double thr,
-                                int32_t *__restrict__ count, const int32_t *__restrict__ srp,
-                                int32_t *__restrict__ scol, double *__restrict__ sval) {
+                                int32_t *__restrict__ count, double *__restrict__ vtmp, double *__restrict__ vmaxv,
+                                const int32_t *__restrict__ srp, int32_t *__restrict__ scol,
+                                double *__restrict__ sval) {
+    const bool fast = thr >= 0x1p-10 && thr <= 0x1p10;  // thr^2 stays a normal FP32 number
+    const float thr2f = (float)(thr * thr);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double di = diag[i];
+        const int32_t e0 = arp[i], e1 = arp[i + 1];
         if (!FILL) {
+            const double di = diag[i];
             int32_t c = 1;
-            for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
-                int32_t j = acol[e];
-                if (j != i && soc_value(aval[e], di, diag[j]) >= thr) c++;
+            double vmax = 0.0;
+            for (int32_t e = e0; e < e1; e++) {
+                const int32_t j = acol[e];
+                double v = -1.0;
+                if (j != i && soc_strong(aval[e], di, diag[j], thr, thr2f, fast)) {
+                    v = soc_value(aval[e], di, diag[j]);
+                    if (v > vmax) vmax = v;
+                    c++;
+                }
+                vtmp[e] = v;
             }
             count[i] = c;
+            vmaxv[i] = vmax;
         } else {
-            double vmax = 0.0;
-            for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
-                int32_t j = acol[e];
-                if (j == i) continue;
-                double v = soc_value(aval[e], di, diag[j]);
-                if (v >= thr && v > vmax) vmax = v;
-            }
+            const double vmax = vmaxv[i];
             int32_t dst = srp[i];
-            for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
-                int32_t j = acol[e];
+            for (int32_t e = e0; e < e1; e++) {
+                const int32_t j = acol[e];
                 if (j == i) {
                     scol[dst] = i;
                     sval[dst++] = 1.0;
-                    continue;
-                }
-                double v = soc_value(aval[e], di, diag[j]);
-                if (v >= thr) {
-                    scol[dst] = j;
-                    sval[dst++] = __ddiv_rn(v, vmax);
+                } else {
+                    const double v = vtmp[e];
+                    if (v >= 0.0) {
+                        scol[dst] = j;
+                        sval[dst++] = __ddiv_rn(v, vmax);
+                    }
                 }
             }
         }
@@ -315,32 +344,34 @@ __global__ void tentative_kernel(int32_t n, const int32_t *__restrict__ rp, cons
 // ------------------------------------------------------------------ CG energy minimisation (Sec. 3.6)
 // Device scalars: sc[0] rho, sc[1] rho0, sc[2] beta, sc[3] <Dd,W>, sc[4] alpha; fl[0] = done.
 // The scalar recurrences run in the finishing block of each reduction (Fin).
+// dinv: the preconditioner D^{-1} as the inverted diagonal (nullptr: none)
 template <int G>
 __global__ void __launch_bounds__(kT)
-cg_rho_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ diag,
-              int precond, Fin fin) {
+cg_rho_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ dinv,
+              Fin fin) {
     __shared__ double sm[32];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     double acc[1] = {0.0};
     for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
-        const double d = precond ? diag[i] : 1.0;
-        for (int32_t q = rp[i] + lane; q < rp[i + 1]; q += G) acc[0] = fma(R[q], R[q] / d, acc[0]);
+        const int32_t q0 = rp[i], q1 = rp[i + 1];
+        const double di = dinv ? dinv[i] : 1.0;
+        for (int32_t q = q0 + lane; q < q1; q += G) acc[0] = fma(R[q], R[q] * di, acc[0]);
     }
     grid_finish<kT, 1>(acc, fin, sm);
 }
 
 template <int G>
 __global__ void __launch_bounds__(kT)
-cg_dd_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ diag,
-             int precond, const double *__restrict__ sc, const int32_t *__restrict__ fl, int first,
-             double *__restrict__ Dd) {
+cg_dd_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ dinv,
+             const double *__restrict__ sc, const int32_t *__restrict__ fl, int first, double *__restrict__ Dd) {
     if (fl[0]) return;
     const double beta = sc[2];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
-        const double d = precond ? diag[i] : 1.0;
-        for (int32_t q = rp[i] + lane; q < rp[i + 1]; q += G) {
-            const double z = R[q] / d;
+        const int32_t q0 = rp[i], q1 = rp[i + 1];
+        const double di = dinv ? dinv[i] : 1.0;
+        for (int32_t q = q0 + lane; q < q1; q += G) {
+            const double z = R[q] * di;
             Dd[q] = first ? z : z + beta * Dd[q];
         }
     }
@@ -349,8 +380,8 @@ cg_dd_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict
 template <int G>
 __global__ void __launch_bounds__(kT)
 cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, double *__restrict__ P, double *__restrict__ R,
-                 const double *__restrict__ Dd, const double *__restrict__ W, const double *__restrict__ diag,
-                 int precond, const double *__restrict__ sc, const int32_t *__restrict__ fl, Fin fin) {
+                 const double *__restrict__ Dd, const double *__restrict__ W, const double *__restrict__ dinv,
+                 const double *__restrict__ sc, const int32_t *__restrict__ fl, Fin fin) {
     __shared__ double sm[32];
     const bool done = fl[0] != 0;
     const double alpha = sc[4];
@@ -358,12 +389,13 @@ cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, double *__restrict__
     double acc[1] = {0.0};
     if (!done) {
         for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
-            const double d = precond ? diag[i] : 1.0;
-            for (int32_t q = rp[i] + lane; q < rp[i + 1]; q += G) {
+            const int32_t q0 = rp[i], q1 = rp[i + 1];
+            const double di = dinv ? dinv[i] : 1.0;
+            for (int32_t q = q0 + lane; q < q1; q += G) {
                 P[q] = P[q] + alpha * Dd[q];
                 const double r = R[q] - alpha * W[q];
                 R[q] = r;
-                acc[0] = fma(r, r / d, acc[0]);
+                acc[0] = fma(r, r * di, acc[0]);
             }
         }
     }
@@ -613,7 +645,7 @@ static int pick_g(double avg) {
 
 // CG energy minimisation of the values X (in/out) on pattern N.
 void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
-                   const double *Bc, const double *diag, int sweeps) {
+                   const double *Bc, const double *c_dinv, int sweeps) {
     cudaStream_t s = c.s;
     const int precond = c.precond;
     DVec<double> Rv, Dv, Wv;
@@ -624,7 +656,11 @@ void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X
     double *sc = c.sc;
     int32_t *fl = c.fl;
     fill_i32(fl, 0, 1, s);
-    ProjArgs pa{rowtype, Bc};
+    DVec<double> Sv;
+    double *rs2 = c.rs2;
+    if (!rs2) { Sv.alloc(N.n, s); rs2 = Sv.p; }
+    proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);
+    ProjArgs pa{rowtype, Bc, rs2};
     const int G = pick_g(N.n ? (double)N.nnz / N.n : 1.0);
     int gridp = 1;
     (void)gridp;
@@ -639,16 +675,17 @@ void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X
     masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, R, pa, -1.0, nullptr, none, s);
     fin.mode = FIN_CG_RHO;
     fin.it = 0;
-    RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R, diag, precond, fin);
+    const double *dinv = precond ? c_dinv : nullptr;
+    RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R, dinv, fin);
     for (int it = 0; it < sweeps; it++) {
-        RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R, diag, precond,
-                       sc, fl, it == 0 ? 1 : 0, Dd);
+        RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R, dinv, sc, fl,
+                       it == 0 ? 1 : 0, Dd);
         fin.mode = FIN_CG_DW;
         masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, Dd, W, pa, 1.0, Dd, fin, s);
         fin.mode = FIN_CG_RHO;
         fin.it = it + 1;
-        RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R, Dd, W, diag,
-                       precond, sc, fl, fin);
+        RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R, Dd, W, dinv,
+                       sc, fl, fin);
     }
 }
 
@@ -664,7 +701,10 @@ void energy_min_gmres(const EmCtx &c, const CsrView &A, const Pattern &N, double
     double *H = Hm.p, *cs = H + (m + 1) * m, *sn = cs + (m + 1), *g = sn + (m + 1), *y = g + (m + 1);
     double *sc = c.sc;
     int32_t *fl = c.fl;
-    ProjArgs pa{rowtype, Bc};
+    DVec<double> Sv(c.rs2 ? 0 : N.n, s);
+    double *rs2 = c.rs2 ? c.rs2 : Sv.p;
+    proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);
+    ProjArgs pa{rowtype, Bc, rs2};
     const int eg = grid_for(nz, 1024);
     const double nzb = 8.0 * nz;
     masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, V.p, pa, -1.0, nullptr, Fin(), s);
@@ -692,9 +732,9 @@ void energy_min_gmres(const EmCtx &c, const CsrView &A, const Pattern &N, double
 }
 
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
-                const double *Bc, const double *diag, int sweeps) {
+                const double *Bc, const double *dinv, int sweeps) {
     if (c.method == RN_ENERGY_GMRES) energy_min_gmres(c, A, N, X, rowtype, Bc, sweeps);
-    else energy_min_cg(c, A, N, X, rowtype, Bc, diag, sweeps);
+    else energy_min_cg(c, A, N, X, rowtype, Bc, dinv, sweeps);
 }
 
 static EmCtx ctx_of(rn_hierarchy &h) {
@@ -752,7 +792,9 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
         d2d(Tkeep->val.p, Pout.val.p, N.nnz, s);
     }
     Pattern pat{n, nc, N.nnz, Pout.rowptr.p, Pout.col.p};
-    energy_min(ctx_of(h), A, pat, Pout.val.p, rowtype, Bc, diag, h.p.n_sweeps);
+    DVec<double> dinv(n, s);  // the energy CG's preconditioner D^{-1}
+    reciprocal(diag, dinv.p, n, s);
+    energy_min(ctx_of(h), A, pat, Pout.val.p, rowtype, Bc, dinv.p, h.p.n_sweeps);
     if (h.p.postfilter > 0.0) {
         const double omg = 1.0 - kGuard;
         DVec<int32_t> cnt(n + 1, s);
@@ -771,7 +813,7 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
                   F.val.p, rowtype, Bsm, Bc);
         Pout = std::move(F);
         Pattern pf{n, nc, Pout.nnz, Pout.rowptr.p, Pout.col.p};
-        energy_min(ctx_of(h), A, pf, Pout.val.p, rowtype, Bc, diag, 1);
+        energy_min(ctx_of(h), A, pf, Pout.val.p, rowtype, Bc, dinv.p, 1);
     }
 }
 
@@ -824,14 +866,16 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         S.n = S.m = n;
         {
             DVec<int32_t> cnt(n + 1, s);
-            RN_LAUNCH("strength", 12.0 * A.nnz + 16.0 * n, s, strength_kernel<false>, rows_grid(n), kT, 0, n,
-                      A.rowptr, A.col, A.val, L.diag.p, thr, cnt.p, nullptr, nullptr, nullptr);
+            DVec<double> vtmp(A.nnz, s), vmax(n, s);
+            RN_LAUNCH("strength", 20.0 * A.nnz + 20.0 * n, s, strength_kernel<false>, rows_grid(n), kT, 0, n,
+                      A.rowptr, A.col, A.val, L.diag.p, thr, cnt.p, vtmp.p, vmax.p, nullptr, nullptr, nullptr);
             S.rowptr.alloc(n + 1, s);
             S.nnz = scan_counts(cnt.p, S.rowptr.p, n, s);
             S.col.alloc(S.nnz, s);
             S.val.alloc(S.nnz, s);
-            RN_LAUNCH("strength", 12.0 * A.nnz + 16.0 * n + 12.0 * S.nnz, s, strength_kernel<true>, rows_grid(n), kT,
-                      0, n, A.rowptr, A.col, A.val, L.diag.p, thr, nullptr, S.rowptr.p, S.col.p, S.val.p);
+            RN_LAUNCH("strength", 12.0 * A.nnz + 12.0 * n + 12.0 * S.nnz, s, strength_kernel<true>, rows_grid(n), kT,
+                      0, n, A.rowptr, A.col, A.val, L.diag.p, thr, nullptr, vtmp.p, vmax.p, S.rowptr.p, S.col.p,
+                      S.val.p);
         }
         // ---- aggregation graph and seeded MIS-2 (line 'aggregate')
         DCsr Gr;
@@ -954,7 +998,8 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
     // ---- coarsest level: dense LU with partial pivoting, kept as an explicit inverse
     rn_level &C = *h.lev.back();
     const int32_t nL = C.A.n;
-    if (nL > kMaxDense) fail(RN_ESTALL, fmt("coarsening stalled with %d rows (> %d for the dense solve)", nL, kMaxDense));
+    if (nL > kMaxDense)
+        fail(RN_ESTALL, fmt("coarsening stalled with %d rows (> %d for the dense solve)", nL, kMaxDense));
     h.nL = nL;
     DVec<double> M((size_t)nL * nL, s), work((size_t)nL * nL, s);
     DVec<int32_t> piv(nL, s);

@@ -28,9 +28,20 @@ constexpr int kTileNnz = 3072;    // matrix entries per shared-memory stage
 constexpr int kTileSlack = 8;     // room for 16-byte alignment of the bulk copies
 constexpr uint32_t kMaxSpin = 1u << 24;  // bound on mbarrier polls before giving up
 
-enum SpOp { OP_SPMV = 0, OP_SPMV_ADD = 1, OP_RESID = 2, OP_JACOBI = 3, OP_SPMV_DOT = 4, OP_JZ_RESID = 5 };
+enum SpOp { OP_SPMV = 0, OP_SPMV_ADD = 1, OP_RESID = 2, OP_JACOBI = 3, OP_SPMV_DOT = 4, OP_JZ_RESID = 5,
+            OP_JACOBI_RZ = 6 };
 // OP_JZ_RESID: first relaxation from a zero guess fused with the residual:
 //   xz = omega b / d,  y = b - A xz
+// OP_JACOBI_RZ: the cycle's last sweep on level 0 (b = r of the outer CG,
+//   y = z) fused with the outer CG's <r, z> and <z, r_old> (aux = r_old)
+template <int OP>
+struct OpNV {  // values reduced over the grid
+    static constexpr int value = OP == OP_JACOBI_RZ ? 2 : 1;
+};
+template <int OP>
+constexpr bool op_reduces() {
+    return OP == OP_RESID || OP == OP_SPMV_DOT || OP == OP_JACOBI_RZ;
+}
 
 // ------------------------------------------------------------------ mbarrier / bulk-copy helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -78,7 +89,7 @@ __device__ __forceinline__ T xget(int32_t j, const T *__restrict__ x, const TB *
 template <typename T, typename TB, typename TO, int OP>
 __device__ __forceinline__ void spmv_epilogue(int32_t i, T acc, const T *__restrict__ x, const TB *__restrict__ b,
                                               const T *__restrict__ diag, T omega, TO *__restrict__ y,
-                                              T *__restrict__ xz, double &red) {
+                                              T *__restrict__ xz, const double *__restrict__ aux, double *red) {
     if (OP == OP_SPMV) {
         y[i] = (TO)acc;
     } else if (OP == OP_SPMV_ADD) {
@@ -86,15 +97,20 @@ __device__ __forceinline__ void spmv_epilogue(int32_t i, T acc, const T *__restr
     } else if (OP == OP_RESID) {
         const T r = (T)b[i] - acc;
         y[i] = (TO)r;
-        red += (double)r * (double)r;
+        red[0] += (double)r * (double)r;
     } else if (OP == OP_JACOBI) {
         y[i] = (TO)(x[i] + diag[i] * ((T)b[i] - acc));
+    } else if (OP == OP_JACOBI_RZ) {
+        const TO z = (TO)(x[i] + diag[i] * ((T)b[i] - acc));
+        y[i] = z;
+        red[0] = fma((double)b[i], (double)z, red[0]);
+        if (aux) red[1] = fma((double)z, aux[i], red[1]);
     } else if (OP == OP_JZ_RESID) {
         xz[i] = diag[i] * (T)b[i];
         y[i] = (TO)((T)b[i] - acc);
     } else {  // OP_SPMV_DOT
         y[i] = (TO)acc;
-        red += (double)x[i] * (double)acc;
+        red[0] += (double)x[i] * (double)acc;
     }
 }
 
@@ -107,9 +123,10 @@ template <typename T, typename TB, typename TO, int G, int OP>
 __global__ void __launch_bounds__(kS)
 spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                  const T *__restrict__ val, const T *__restrict__ x, const TB *__restrict__ b,
-                 const T *__restrict__ diag, T omega, TO *__restrict__ y, T *__restrict__ xz, Fin fin,
-                 int32_t *__restrict__ err) {
+                 const T *__restrict__ diag, T omega, TO *__restrict__ y, T *__restrict__ xz,
+                 const double *__restrict__ aux, Fin fin, int32_t *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NV = OpNV<OP>::value;
     constexpr int SL = kTileNnz + kTileSlack;
     constexpr int RPT = kS / G;
     constexpr int RL = RPT + 8;  // staged row pointers per stage (RPT + 1, rounded to 16 bytes)
@@ -147,7 +164,7 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
         if (vb) bulk_g2s(sval + stage * SL, val + v0, vb, &bar[stage]);
         pend |= 1u << stage;
     };
-    double red[1] = {0.0};
+    double red[NV] = {};
     uint32_t parity = 0u;  // bit s = phase parity to wait for on stage s
     bool failed = false;
     int st = 0;
@@ -172,11 +189,13 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
         T xi = T(0), di = T(1);
         TB bi = TB(0);
         TO yi = TO(0);
+        double ai = 0.0;
         if (live && lane == 0) {
-            if (OP == OP_JACOBI || OP == OP_SPMV_DOT) xi = x[row];
-            if (OP == OP_RESID || OP == OP_JACOBI || OP == OP_JZ_RESID) bi = b[row];
-            if (OP == OP_JACOBI || OP == OP_JZ_RESID) di = diag[row];
+            if (OP == OP_JACOBI || OP == OP_JACOBI_RZ || OP == OP_SPMV_DOT) xi = x[row];
+            if (OP == OP_RESID || OP == OP_JACOBI || OP == OP_JACOBI_RZ || OP == OP_JZ_RESID) bi = b[row];
+            if (OP == OP_JACOBI || OP == OP_JACOBI_RZ || OP == OP_JZ_RESID) di = diag[row];
             if (OP == OP_SPMV_ADD) yi = y[row];
+            if (OP == OP_JACOBI_RZ && aux) ai = aux[row];
         }
         const bool ok = mbar_wait_bounded(&bar[st], (parity >> st) & 1u);
         if (__syncthreads_or(!ok)) {
@@ -223,6 +242,11 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
                 red[0] += (double)r * (double)r;
             } else if (OP == OP_JACOBI) {
                 y[row] = (TO)(xi + di * ((T)bi - acc));
+            } else if (OP == OP_JACOBI_RZ) {
+                const TO z = (TO)(xi + di * ((T)bi - acc));
+                y[row] = z;
+                red[0] = fma((double)bi, (double)z, red[0]);
+                red[NV - 1] = fma((double)z, ai, red[NV - 1]);  // ai = 0 without r_old
             } else if (OP == OP_JZ_RESID) {
                 xz[row] = di * (T)bi;
                 y[row] = (TO)((T)bi - acc);
@@ -241,7 +265,7 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
         }
         __syncthreads();
     }
-    if (OP == OP_RESID || OP == OP_SPMV_DOT) grid_finish<kS, 1>(red, fin, sm);
+    if (op_reduces<OP>()) grid_finish<kS, NV>(red, fin, sm);
 }
 
 // Fallback for matrices with rows too long for a stage: G lanes per row
@@ -250,10 +274,12 @@ template <typename T, typename TB, typename TO, int G, int OP>
 __global__ void __launch_bounds__(kS)
 spmv_group_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                   const T *__restrict__ val, const T *__restrict__ x, const TB *__restrict__ b,
-                  const T *__restrict__ diag, T omega, TO *__restrict__ y, T *__restrict__ xz, Fin fin) {
+                  const T *__restrict__ diag, T omega, TO *__restrict__ y, T *__restrict__ xz,
+                  const double *__restrict__ aux, Fin fin) {
     __shared__ double sm[32];
+    constexpr int NV = OpNV<OP>::value;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    double red[1] = {0.0};
+    double red[NV] = {};
     for (int32_t i0 = blockIdx.x * (kS / G); i0 < n; i0 += gridDim.x * (kS / G)) {
         const int32_t i = i0 + g;
         T acc = T(0);
@@ -265,9 +291,9 @@ spmv_group_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__re
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
         }
-        if (lane == 0 && i < n) spmv_epilogue<T, TB, TO, OP>(i, acc, x, b, diag, omega, y, xz, red[0]);
+        if (lane == 0 && i < n) spmv_epilogue<T, TB, TO, OP>(i, acc, x, b, diag, omega, y, xz, aux, red);
     }
-    if (OP == OP_RESID || OP == OP_SPMV_DOT) grid_finish<kS, 1>(red, fin, sm);
+    if (op_reduces<OP>()) grid_finish<kS, NV>(red, fin, sm);
 }
 
 template <typename T, typename TB>
@@ -304,50 +330,122 @@ __global__ void row_maxlen_kernel(int32_t n, const int32_t *__restrict__ rp, int
 }
 
 // ------------------------------------------------------------------ outer-iteration vector kernels
-// Device scalars: sc[8] ||r||^2, sc[9] <r,z>, sc[10] <p,Ap>, sc[11] <z,r_old>, sc[14] previous <r,z>,
-// sc[15] |g_{j+1}| (FGMRES), sc[16] h_{j+1,j}, sc[17] ||b||^2.
+// Scalars live on the device (see Fin); alpha and beta are formed once by the
+// finisher of the reduction that completes them, not per thread (FP64 division
+// is a long sequence on this part's narrow FP64 pipe).  The level-0 vector
+// kernels give each thread kVecU elements a grid stride apart, loaded before
+// any is used.
+constexpr int kVecU = 4;
+
 __global__ void axpy_kernel(int64_t n, double *__restrict__ x, const double *__restrict__ z) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] += z[i];
 }
 
-// alpha = <r,z>/<p,Ap>; x += alpha p; r_old = r (flexible); r -= alpha q; ||r||^2
+// x += alpha p; r_old = r (flexible); r -= alpha q; ||r||^2 (FIN_XR: stopping test)
 __global__ void __launch_bounds__(kS)
 cg_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
              const double *__restrict__ q, double *__restrict__ rold, const double *__restrict__ sc, Fin fin) {
     __shared__ double sm[32];
-    const double a = sc[9] / sc[10];
+    const double a = sc[12];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double acc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] = x[i] + a * p[i];
-        const double ri = r[i];
-        if (rold) rold[i] = ri;
-        const double rn = ri - a * q[i];
-        r[i] = rn;
-        acc[0] = fma(rn, rn, acc[0]);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
+        double xv[kVecU], pv[kVecU], rv[kVecU], qv[kVecU];
+#pragma unroll
+        for (int u = 0; u < kVecU; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                xv[u] = x[i];
+                pv[u] = p[i];
+                rv[u] = r[i];
+                qv[u] = q[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecU; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                x[i] = xv[u] + a * pv[u];
+                if (rold) rold[i] = rv[u];
+                const double rn = rv[u] - a * qv[u];
+                r[i] = rn;
+                acc[0] = fma(rn, rn, acc[0]);
+            }
+        }
     }
     grid_finish<kS, 1>(acc, fin, sm);
 }
 
-// <r,z> and (flexible) <z, r_old>; the finisher keeps the previous <r,z>
+// <r,z> and (flexible) <z, r_old>; the finisher keeps the previous <r,z> and forms beta
 __global__ void __launch_bounds__(kS)
 cg_rz_kernel(int64_t n, const double *__restrict__ r, const double *__restrict__ z, const double *__restrict__ rold,
              Fin fin) {
     __shared__ double sm[32];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double acc[2] = {0.0, 0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        acc[0] = fma(r[i], z[i], acc[0]);
-        if (rold) acc[1] = fma(z[i], rold[i], acc[1]);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
+        double rv[kVecU], zv[kVecU], ov[kVecU];
+#pragma unroll
+        for (int u = 0; u < kVecU; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                rv[u] = r[i];
+                zv[u] = z[i];
+                ov[u] = rold ? rold[i] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecU; u++) {
+            if (i0 + u * stride < n) {
+                acc[0] = fma(rv[u], zv[u], acc[0]);
+                if (rold) acc[1] = fma(zv[u], ov[u], acc[1]);
+            }
+        }
     }
     grid_finish<kS, 2>(acc, fin, sm);
 }
 
-// p = z + beta p, beta = <z,r>/<z,r>_prev (standard) or (<z,r> - <z,r_old>)/<z,r>_prev (flexible)
-__global__ void cg_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__ z,
-                            const double *__restrict__ sc, int first, int flexible) {
-    const double beta = first ? 0.0 : (flexible ? (sc[9] - sc[11]) : sc[9]) / sc[14];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = first ? z[i] : z[i] + beta * p[i];
+// p = z (first) or z + beta p, beta = sc[13]
+__global__ void __launch_bounds__(kS)
+cg_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__ z, const double *__restrict__ sc,
+            int first) {
+    const double beta = sc[13];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
+        double zv[kVecU], pv[kVecU];
+#pragma unroll
+        for (int u = 0; u < kVecU; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                zv[u] = z[i];
+                pv[u] = first ? 0.0 : p[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecU; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) p[i] = first ? zv[u] : zv[u] + beta * pv[u];
+        }
+    }
+}
+
+// one wave of resident blocks for the level-0 vector kernels
+static int vec_grid(const void *k, int64_t n) {
+    const int64_t need = (n + (int64_t)kS * kVecU - 1) / ((int64_t)kS * kVecU);
+    const int64_t wave = (int64_t)resident_blocks(k, kS, 0) * num_sms();
+    return (int)std::max<int64_t>(1, std::min<int64_t>({need, wave, (int64_t)kReduceBlocks}));
+}
+
+#define VG(kernel) vec_grid((const void *)(kernel), n)
+
+// loop state of the outer CG: ||b||, rtol, iteration count and limit
+__global__ void cg_loop_init_kernel(double *sc, int32_t *fl, double nb, double rtol, int maxit) {
+    sc[18] = nb;
+    sc[19] = rtol;
+    fl[9] = 0;
+    fl[10] = maxit;
+    fl[11] = 0;
 }
 
 __global__ void scale_copy_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ den,
@@ -442,7 +540,7 @@ const float *vals_of<float>(const DCsr &A) { return A.val32.p; }
 
 template <typename T, typename TB, typename TO, int G, int OP>
 static void launch_tile(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
-                        T omega, TO *y, T *xz, const Fin &fin, int32_t *err, cudaStream_t s) {
+                        T omega, TO *y, T *xz, const double *aux, const Fin &fin, int32_t *err, cudaStream_t s) {
     constexpr int SL = kTileNnz + kTileSlack;
     constexpr int RL = kS / G + 8;
     const size_t smem = (2 * SL + 2 * RL) * sizeof(int32_t) + 2 * SL * sizeof(T);
@@ -457,39 +555,47 @@ static void launch_tile(const char *name, double bytes, const DCsr &M, const T *
     int grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
     grid = std::max(1, std::min(grid, kReduceBlocks));
     RN_LAUNCH(name, bytes, s, (spmv_tile_kernel<T, TB, TO, G, OP>), grid, kS, smem, M.n, ntiles, M.rowptr.p, M.col.p,
-              vals_of<T>(M), x, b, diag, omega, y, xz, fin, err);
+              vals_of<T>(M), x, b, diag, omega, y, xz, aux, fin, err);
 }
 
 template <typename T, typename TB, typename TO, int G, int OP>
 static void launch_group(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
-                         T omega, TO *y, T *xz, const Fin &fin, cudaStream_t s) {
+                         T omega, TO *y, T *xz, const double *aux, const Fin &fin, cudaStream_t s) {
     int grid = grid_for(M.n, kS / G, 8);
     grid = std::min(grid, kReduceBlocks);
     RN_LAUNCH(name, bytes, s, (spmv_group_kernel<T, TB, TO, G, OP>), grid, kS, 0, M.n, M.rowptr.p, M.col.p,
-              vals_of<T>(M), x, b, diag, omega, y, xz, fin);
+              vals_of<T>(M), x, b, diag, omega, y, xz, aux, fin);
+}
+
+// Algorithmic bytes of one SpMV-family launch: the matrix (index + value) and
+// row pointers once, x gathered once, the output (and b, diag, x_i where
+// read) once.
+template <typename T, typename TB, typename TO, int OP>
+static double spmv_bytes(const DCsr &M) {
+    const double vb = sizeof(T);
+    double bytes = (4.0 + vb) * M.nnz + 4.0 * (M.n + 1) + vb * M.m + (double)sizeof(TO) * M.n;
+    if (OP == OP_SPMV_ADD) bytes += sizeof(TO) * (double)M.n;
+    if (OP == OP_RESID) bytes += sizeof(TB) * (double)M.n;
+    if (OP == OP_JACOBI) bytes += (sizeof(TB) + vb) * (double)M.n;
+    if (OP == OP_JACOBI_RZ) bytes += (sizeof(TB) + vb) * (double)M.n;  // + r_old when flexible (not counted)
+    if (OP == OP_JZ_RESID) bytes += (sizeof(TB) + 2.0 * vb) * (double)M.n - vb * M.m;  // b, d read; x written
+    return bytes;
 }
 
 // y = op(M, x, b): picks the staged tile kernel when the rows fit a stage.
 // xz: second output of OP_JZ_RESID (the relaxed iterate).
 template <typename T, typename TB, typename TO, int OP>
 static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, const TB *b, const T *diag, T omega,
-                 TO *y, const Fin &fin, T *xz = nullptr) {
+                 TO *y, const Fin &fin, T *xz = nullptr, const double *aux = nullptr) {
     cudaStream_t s = h.s;
     if (M.n == 0) return;
-    const double vb = sizeof(T);
-    // algorithmic bytes: matrix (index + value) and row pointers once, x gathered
-    // once, the output (and b, diag, x_i where read) once
-    double bytes = (4.0 + vb) * M.nnz + 4.0 * (M.n + 1) + vb * M.m + (double)sizeof(TO) * M.n;
-    if (OP == OP_SPMV_ADD) bytes += sizeof(TO) * (double)M.n;
-    if (OP == OP_RESID) bytes += sizeof(TB) * (double)M.n;
-    if (OP == OP_JACOBI) bytes += (sizeof(TB) + vb) * (double)M.n;
-    if (OP == OP_JZ_RESID) bytes += (sizeof(TB) + 2.0 * vb) * (double)M.n - vb * M.m;  // b, d read; x written
+    const double bytes = spmv_bytes<T, TB, TO, OP>(M);
     int32_t *err = h.iflags.p + 8;
     const int G = M.tile_group;
 #define RN_TILE_CASE(GG) \
-    case GG: launch_tile<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, fin, err, s); return;
+    case GG: launch_tile<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, err, s); return;
 #define RN_GROUP_CASE(GG) \
-    case GG: launch_group<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, fin, s); return;
+    case GG: launch_group<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, s); return;
     switch (G) {
         RN_TILE_CASE(1)
         RN_TILE_CASE(2)
@@ -504,7 +610,7 @@ static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, c
         RN_GROUP_CASE(4)
         RN_GROUP_CASE(8)
         RN_GROUP_CASE(16)
-        default: launch_group<T, TB, TO, 32, OP>(name, bytes, M, x, b, diag, omega, y, xz, fin, s); return;
+        default: launch_group<T, TB, TO, 32, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, s); return;
     }
 #undef RN_TILE_CASE
 #undef RN_GROUP_CASE
@@ -573,6 +679,28 @@ static T *relax0_and_residual(rn_hierarchy &h, const CycleNames &nm, rn_level &L
     return cur;
 }
 
+template <typename T>
+static T *vcycle_level(rn_hierarchy &h, int l);
+
+// Coarse-grid correction of level l: b_{l+1} = R_l r, the cycle on level
+// l+1, cur += P_l x_{l+1}.  From the cluster's level on, all of it (transfers
+// included) is one cluster launch.
+template <typename T>
+static void coarse_correction(rn_hierarchy &h, int l, const T *r, T *cur) {
+    using LB = LevelBufs<T>;
+    rn_level &L = *h.lev[l];
+    rn_level &Lc = *h.lev[l + 1];
+    const CycleNames &nm = kNames[sizeof(T) == 4][l > 0];
+    const Fin none;
+    if (h.sub_k == l) {
+        launch_subcycle<T>(h, cur, sizeof(T) == 4 ? "cycle_coarse_cluster_f32" : "cycle_coarse_cluster_f64");
+        return;
+    }
+    spmv<T, T, T, OP_SPMV>(h, nm.restr, L.R, r, (const T *)nullptr, nullptr, T(0), LB::b(Lc), none);
+    T *xc = vcycle_level<T>(h, l + 1);
+    spmv<T, T, T, OP_SPMV_ADD>(h, nm.prolong, L.P, xc, (const T *)nullptr, nullptr, T(0), cur, none);
+}
+
 // One cycle on level l >= 1 with zero initial guess; b_l holds the right-hand
 // side.  Returns the buffer holding the result.
 template <typename T>
@@ -595,10 +723,7 @@ static T *vcycle_level(rn_hierarchy &h, int l) {
     T *r = LB::r(L);
     T *cur = relax0_and_residual<T, T>(h, nm, L, b, r);
     T *oth = (cur == LB::x(L)) ? LB::t(L) : LB::x(L);
-    rn_level &Lc = *h.lev[l + 1];
-    spmv<T, T, T, OP_SPMV>(h, nm.restr, L.R, r, (const T *)nullptr, nullptr, T(0), LB::b(Lc), none);
-    T *xc = vcycle_level<T>(h, l + 1);
-    spmv<T, T, T, OP_SPMV_ADD>(h, nm.prolong, L.P, xc, (const T *)nullptr, nullptr, T(0), cur, none);
+    coarse_correction<T>(h, l, r, cur);
     for (int k = 0; k < h.p.nu_post; k++) {
         spmv<T, T, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, b, d, omega, oth, none);
         std::swap(cur, oth);
@@ -606,9 +731,12 @@ static T *vcycle_level(rn_hierarchy &h, int l) {
     return cur;
 }
 
-// out = M rhs on level 0 (FP64 in/out); the cycle itself runs in T.
+// out = M rhs on level 0 (FP64 in/out); the cycle itself runs in T.  With rz
+// set, the last post-sweep also reduces the outer CG's <rhs, out> and
+// <out, rz_rold> into *rz (FIN_RZ); returns whether it did (it cannot without
+// a post-sweep on a multilevel hierarchy).
 template <typename T>
-static void vcycle_top(rn_hierarchy &h, const double *rhs, double *out) {
+static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fin *rz, const double *rz_rold) {
     using LB = LevelBufs<T>;
     cudaStream_t s = h.s;
     rn_level &L = *h.lev[0];
@@ -618,22 +746,24 @@ static void vcycle_top(rn_hierarchy &h, const double *rhs, double *out) {
     if (h.lev.size() == 1) {
         RN_LAUNCH(nm.coarse, 8.0 * n * n + 16.0 * n, s, (coarse_solve_kernel<double, double>),
                   grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, rhs, out);
-        return;
+        return false;
     }
     const T omega = (T)h.p.omega;
     const T *d = LB::d(L);
     T *r = LB::r(L);
     T *cur = relax0_and_residual<T, double>(h, nm, L, rhs, r);
     T *oth = (cur == LB::x(L)) ? LB::t(L) : LB::x(L);
-    rn_level &Lc = *h.lev[1];
-    spmv<T, T, T, OP_SPMV>(h, nm.restr, L.R, r, (const T *)nullptr, nullptr, T(0), LevelBufs<T>::b(Lc), none);
-    T *xc = vcycle_level<T>(h, 1);
-    spmv<T, T, T, OP_SPMV_ADD>(h, nm.prolong, L.P, xc, (const T *)nullptr, nullptr, T(0), cur, none);
+    coarse_correction<T>(h, 0, r, cur);
     const int npost = h.p.nu_post;
     for (int k = 0; k < npost; k++) {
         if (k == npost - 1) {
+            if (rz) {
+                spmv<T, double, double, OP_JACOBI_RZ>(h, nm.jacobi, L.A, cur, rhs, d, omega, out, *rz, nullptr,
+                                                      rz_rold);
+                return true;
+            }
             spmv<T, double, double, OP_JACOBI>(h, nm.jacobi, L.A, cur, rhs, d, omega, out, none);
-            return;
+            return false;
         }
         spmv<T, double, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, rhs, d, omega, oth, none);
         std::swap(cur, oth);
@@ -642,11 +772,13 @@ static void vcycle_top(rn_hierarchy &h, const double *rhs, double *out) {
     if (sizeof(T) == 8) d2d(out, reinterpret_cast<const double *>(cur), n, s);
     else RN_LAUNCH("convert", 12.0 * n, s, f2d_kernel, grid_for(n, 1024), 256, 0, (int64_t)n,
                    reinterpret_cast<const float *>(cur), out);
+    return false;
 }
 
-static void cycle_direct(rn_hierarchy &h, const double *rhs, double *out) {
-    if (h.p.precision == RN_MIXED) vcycle_top<float>(h, rhs, out);
-    else vcycle_top<double>(h, rhs, out);
+static bool cycle_direct(rn_hierarchy &h, const double *rhs, double *out, const Fin *rz = nullptr,
+                         const double *rz_rold = nullptr) {
+    if (h.p.precision == RN_MIXED) return vcycle_top<float>(h, rhs, out, rz, rz_rold);
+    return vcycle_top<double>(h, rhs, out, rz, rz_rold);
 }
 
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out) {
@@ -742,8 +874,10 @@ void prepare_solve(rn_hierarchy &h) {
     h.q.alloc(n0, s);
     h.w.alloc(n0, s);
     h.rold.alloc(n0, s);
+    h.xs.alloc(n0, s);
     h.graph_in = h.r.p;
     h.graph_out = h.z.p;
+    prepare_subcycle(h);
     if (h.p.outer == RN_OUTER_FGMRES) {
         const int m = std::max(1, h.p.restart);
         h.V.alloc((size_t)(m + 1) * n0, s);
@@ -764,6 +898,120 @@ void cycle_checked(rn_hierarchy &h, const double *rhs, double *out) {
     check_tile_error(h);
 }
 
+// Outer CG (Sec. 2: the cycle as preconditioner), one iteration in two halves:
+// q = A p with <p,q> and alpha, then x, r and the stopping test; after the
+// preconditioner z = M r, <r,z> (and <z,r_old>) with beta, then p.
+static void cg_iteration_first_half(rn_hierarchy &h, double *x, const Fin &cond) {
+    rn_level &L0 = *h.lev[0];
+    const int64_t n = L0.A.n;
+    double *sc = h.scal.p;
+    const bool flexible = h.p.precision == RN_MIXED;
+    spmv<double, double, double, OP_SPMV_DOT>(h, "outer_spmv", L0.A, h.pv.p, (const double *)nullptr, nullptr, 0.0,
+                                              h.q.p, make_fin(h, FIN_PQ));
+    Fin fx = make_fin(h, FIN_XR);
+    fx.cond_loop = cond.cond_loop;
+    fx.cond_body = cond.cond_body;
+    RN_LAUNCH("outer_cg_vec", 48.0 * n + (flexible ? 8.0 * n : 0.0), h.s, cg_xr_kernel, VG(cg_xr_kernel), kS, 0,
+              n, x, h.r.p, h.pv.p, h.q.p, flexible ? h.rold.p : nullptr, sc, fx);
+}
+
+// z = M r, <r,z> (and <z,r_old>) with beta, then p.  The reductions ride on
+// the cycle's last level-0 sweep when it has one.
+static void cg_iteration_second_half(rn_hierarchy &h, bool flexible) {
+    const int64_t n = h.lev[0]->A.n;
+    Fin fr = make_fin(h, FIN_RZ);
+    fr.it = flexible ? 2 : 0;
+    const double *rold = flexible ? h.rold.p : nullptr;
+    if (!cycle_direct(h, h.r.p, h.z.p, &fr, rold))
+        RN_LAUNCH("outer_cg_vec", (flexible ? 24.0 : 16.0) * n, h.s, cg_rz_kernel, VG(cg_rz_kernel), kS, 0, n,
+                  h.r.p, h.z.p, rold, fr);
+    RN_LAUNCH("outer_cg_vec", 24.0 * n, h.s, cg_p_kernel, VG(cg_p_kernel), kS, 0, n, h.pv.p, h.z.p, h.scal.p, 0);
+}
+
+// Capture stream work into a standalone graph.
+template <typename F>
+static cudaGraph_t capture(rn_hierarchy &h, F &&work) {
+    cudaGraph_t g = nullptr;
+    RN_CUDA_CHECK(cudaStreamBeginCapture(h.s, cudaStreamCaptureModeThreadLocal));
+    try {
+        work();
+    } catch (...) {
+        cudaStreamEndCapture(h.s, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    RN_CUDA_CHECK(cudaStreamEndCapture(h.s, &g));
+    return g;
+}
+
+// The solve graph: kCgGraphIters iterations, each
+//   IF(a_j) { first half }  ->  IF(b_j) { cycle; second half }
+// The first half's reduction finisher sets b_j and a_{j+1} (iterate while not
+// converged and below the iteration limit), so the host only relaunches the
+// graph, and reads the loop state, once per kCgGraphIters iterations.  The
+// graph holds no loop: whatever the conditions, one launch ends.
+constexpr int kCgGraphIters = 16;
+
+static void build_cg_graph(rn_hierarchy &h) {
+    const bool flexible = h.p.precision == RN_MIXED;
+    cudaGraph_t g = nullptr;
+    RN_CUDA_CHECK(cudaGraphCreate(&g, 0));
+    struct GraphGuard {
+        cudaGraph_t *g;
+        ~GraphGuard() {
+            if (*g) cudaGraphDestroy(*g);
+        }
+    } guard{&g};
+    cudaGraphConditionalHandle ha[kCgGraphIters + 1] = {}, hb[kCgGraphIters] = {};
+    for (int j = 0; j < kCgGraphIters; j++) {
+        RN_CUDA_CHECK(cudaGraphConditionalHandleCreate(&ha[j], g, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault));
+        RN_CUDA_CHECK(cudaGraphConditionalHandleCreate(&hb[j], g, 0u, cudaGraphCondAssignDefault));
+    }
+    const int64_t k0 = launches_so_far();
+    cudaGraph_t g2 = capture(h, [&] { cg_iteration_second_half(h, flexible); });
+    const int64_t k1 = launches_so_far();
+    cudaGraphNode_t prev = nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < kCgGraphIters && e == cudaSuccess; j++) {
+        Fin cond;
+        cond.cond_loop = ha[j + 1];  // 0 after the last copy: nothing to set
+        cond.cond_body = hb[j];
+        cudaGraph_t g1 = nullptr;
+        try {
+            g1 = capture(h, [&] { cg_iteration_first_half(h, h.xs.p, cond); });
+        } catch (...) {
+            cudaGraphDestroy(g2);
+            throw;
+        }
+        cudaGraphNodeParams pa = {};
+        pa.type = cudaGraphNodeTypeConditional;
+        pa.conditional.handle = ha[j];
+        pa.conditional.type = cudaGraphCondTypeIf;
+        pa.conditional.size = 1;
+        cudaGraphNode_t na = nullptr, nb = nullptr, c1 = nullptr, c2 = nullptr;
+        e = cudaGraphAddNode(&na, g, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &pa);
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&c1, pa.conditional.phGraph_out[0], nullptr, 0, g1);
+        cudaGraphDestroy(g1);
+        cudaGraphNodeParams pb = {};
+        pb.type = cudaGraphNodeTypeConditional;
+        pb.conditional.handle = hb[j];
+        pb.conditional.type = cudaGraphCondTypeIf;
+        pb.conditional.size = 1;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&nb, g, &na, nullptr, 1, &pb);
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&c2, pb.conditional.phGraph_out[0], nullptr, 0, g2);
+        prev = nb;
+    }
+    const int64_t k2 = launches_so_far();
+    h.cg_kernels[0] = (k2 - k1) / kCgGraphIters;
+    h.cg_kernels[1] = k1 - k0;
+    add_launches(k0 - k2);  // captured, not launched
+    cudaGraphDestroy(g2);
+    RN_CUDA_CHECK(e);
+    RN_CUDA_CHECK(cudaGraphInstantiate(&h.cg_exec, g, 0));
+    h.cg_graph = g;
+    g = nullptr;
+}
+
 rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int maxit, rn_solve_info *info) {
     cudaStream_t s = h.s;
     rn_level &L0 = *h.lev[0];
@@ -772,7 +1020,6 @@ rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int ma
     const double t0 = now_ms();
     const Fin none;
     const int eg = grid_for(n, 1024);
-    const int rg = std::min(grid_for(n, kS * 4, 8), kReduceBlocks);
     auto residual = [&]() {  // r = b - A x, sc[8] = ||r||^2
         spmv<double, double, double, OP_RESID>(h, "outer_residual", L0.A, x, b, nullptr, 0.0, h.r.p,
                                                make_fin(h, FIN_STORE, sc + 8));
@@ -798,24 +1045,41 @@ rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int ma
     } else if (st != RN_OK && h.p.outer == RN_OUTER_CG) {
         const bool flexible = h.p.precision == RN_MIXED;
         apply_cycle(h, h.r.p, h.z.p);
-        RN_LAUNCH("outer_cg_vec", 16.0 * n, s, cg_rz_kernel, rg, kS, 0, n, h.r.p, h.z.p, nullptr,
-                  make_fin(h, FIN_RZ));
-        RN_LAUNCH("outer_cg_vec", 16.0 * n, s, cg_p_kernel, eg, 256, 0, n, h.pv.p, h.z.p, sc, 1, 0);
-        for (it = 1; it <= maxit; it++) {
-            // q = A p and <p, q> in one pass
-            spmv<double, double, double, OP_SPMV_DOT>(h, "outer_spmv", L0.A, h.pv.p, (const double *)nullptr,
-                                                      nullptr, 0.0, h.q.p, make_fin(h, FIN_STORE, sc + 10));
-            RN_LAUNCH("outer_cg_vec", 48.0 * n + (flexible ? 8.0 * n : 0.0), s, cg_xr_kernel, rg, kS, 0, n, x,
-                      h.r.p, h.pv.p, h.q.p, flexible ? h.rold.p : nullptr, sc, make_fin(h, FIN_STORE, sc + 8));
-            rn = std::sqrt(read_scalar(sc + 8, s));
-            if (rn / nb < rtol) { st = RN_OK; break; }
-            apply_cycle(h, h.r.p, h.z.p);
-            RN_LAUNCH("outer_cg_vec", (flexible ? 24.0 : 16.0) * n, s, cg_rz_kernel, rg, kS, 0, n, h.r.p, h.z.p,
-                      flexible ? h.rold.p : nullptr, make_fin(h, FIN_RZ));
-            RN_LAUNCH("outer_cg_vec", 24.0 * n, s, cg_p_kernel, eg, 256, 0, n, h.pv.p, h.z.p, sc, 0,
-                      flexible ? 1 : 0);
+        Fin f0 = make_fin(h, FIN_RZ);
+        f0.it = 1;  // first: beta = 0
+        RN_LAUNCH("outer_cg_vec", 16.0 * n, s, cg_rz_kernel, VG(cg_rz_kernel), kS, 0, n, h.r.p, h.z.p, nullptr, f0);
+        RN_LAUNCH("outer_cg_vec", 16.0 * n, s, cg_p_kernel, VG(cg_p_kernel), kS, 0, n, h.pv.p, h.z.p, sc, 1);
+        RN_LAUNCH("outer_cg_state", 0, s, cg_loop_init_kernel, 1, 1, 0, sc, h.iflags.p, nb, rtol, maxit);
+        if (maxit <= 0) {
+            it = 0;
+        } else if (h.p.use_graphs && !profiling_enabled()) {
+            // iterations run in graph launches of kCgGraphIters; the device decides when to stop
+            d2d(h.xs.p, x, n, s);
+            if (!h.cg_exec) build_cg_graph(h);
+            it = 0;
+            for (;;) {
+                RN_CUDA_CHECK(cudaGraphLaunch(h.cg_exec, s));
+                int32_t fl[3];  // iterations done, limit, converged
+                RN_CUDA_CHECK(cudaMemcpyAsync(fl, h.iflags.p + 9, sizeof fl, cudaMemcpyDeviceToHost, s));
+                RN_CUDA_CHECK(cudaStreamSynchronize(s));
+                const int done = fl[0] - it;
+                const bool stopped = fl[2] != 0 || fl[0] >= maxit;
+                // the second half runs in every iteration but a stopping one
+                add_launches((int64_t)done * h.cg_kernels[0] + (int64_t)(done - (stopped ? 1 : 0)) * h.cg_kernels[1]);
+                it = fl[0];
+                if (stopped) break;
+                if (done != kCgGraphIters) fail(RN_EINTERNAL, "solve graph: conditional nodes were not honoured");
+            }
+            d2d(x, h.xs.p, n, s);
+        } else {
+            for (it = 1; it <= maxit; it++) {
+                cg_iteration_first_half(h, x, Fin());
+                rn = std::sqrt(read_scalar(sc + 8, s));
+                if (rn / nb < rtol) break;
+                cg_iteration_second_half(h, flexible);
+            }
+            if (it > maxit) it = maxit;
         }
-        if (it > maxit) it = maxit;
         rn = residual();
         st = (rn / nb < rtol) ? RN_OK : RN_ENOTCONV;
     } else if (st != RN_OK && h.p.outer == RN_OUTER_FGMRES) {
@@ -867,6 +1131,114 @@ rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int ma
         info->status = st;
     }
     return st;
+}
+
+// ------------------------------------------------------------------ measurement
+// One level-0 launch of the solve, as the solve issues it (kernel, launch
+// shape, buffers), for timing in isolation.  Returns its algorithmic bytes.
+template <typename T>
+static double enqueue_op(rn_hierarchy &h, int op, std::string &name) {
+    using LB = LevelBufs<T>;
+    rn_level &L0 = *h.lev[0];
+    const int64_t n = L0.A.n;
+    const bool mixed = sizeof(T) == 4;
+    const CycleNames &nm = kNames[mixed][0];
+    const Fin none;
+    double *sc = h.scal.p;
+    const bool multi = h.lev.size() > 1;
+    if (op >= RN_OP_RELAX0_RESIDUAL && op <= RN_OP_PROLONG && !multi) fail(RN_EINVAL, "operation needs two levels");
+    const T omega = (T)h.p.omega;
+    switch (op) {
+        case RN_OP_OUTER_SPMV:
+            name = "outer_spmv";
+            spmv<double, double, double, OP_SPMV_DOT>(h, "outer_spmv", L0.A, h.pv.p, (const double *)nullptr, nullptr,
+                                                      0.0, h.q.p, make_fin(h, FIN_STORE, sc + 20));
+            return spmv_bytes<double, double, double, OP_SPMV_DOT>(L0.A);
+        case RN_OP_RELAX0_RESIDUAL:
+            name = nm.jzresid;
+            spmv<T, double, T, OP_JZ_RESID>(h, nm.jzresid, L0.A, (const T *)nullptr, h.r.p, LB::d(L0), omega,
+                                            LB::r(L0), none, LB::x(L0));
+            return spmv_bytes<T, double, T, OP_JZ_RESID>(L0.A);
+        case RN_OP_JACOBI_OUT:  // as the CG solve issues it: fused with <r,z> (and <z,r_old>)
+            name = nm.jacobi;
+            spmv<T, double, double, OP_JACOBI_RZ>(h, nm.jacobi, L0.A, LB::x(L0), h.r.p, LB::d(L0), omega, h.z.p,
+                                                  make_fin(h, FIN_STORE, sc + 20), nullptr,
+                                                  mixed ? h.rold.p : nullptr);
+            return spmv_bytes<T, double, double, OP_JACOBI_RZ>(L0.A) + (mixed ? 8.0 * n : 0.0);
+        case RN_OP_RESTRICT:
+            name = nm.restr;
+            spmv<T, T, T, OP_SPMV>(h, nm.restr, L0.R, LB::r(L0), (const T *)nullptr, nullptr, T(0),
+                                   LB::b(*h.lev[1]), none);
+            return spmv_bytes<T, T, T, OP_SPMV>(L0.R);
+        case RN_OP_PROLONG:
+            name = nm.prolong;
+            spmv<T, T, T, OP_SPMV_ADD>(h, nm.prolong, L0.P, LB::x(*h.lev[1]), (const T *)nullptr, nullptr, T(0),
+                                       LB::x(L0), none);
+            return spmv_bytes<T, T, T, OP_SPMV_ADD>(L0.P);
+        case RN_OP_CG_XR: {
+            name = "outer_cg_xr";
+            const double b = 48.0 * n + (mixed ? 8.0 * n : 0.0);
+            RN_LAUNCH("outer_cg_vec", b, h.s, cg_xr_kernel, VG(cg_xr_kernel), kS, 0, n, h.xs.p, h.r.p, h.pv.p, h.q.p,
+                      mixed ? h.rold.p : nullptr, sc, make_fin(h, FIN_STORE, sc + 20));
+            return b;
+        }
+        case RN_OP_CG_RZ: {  // runs only when the cycle has no level-0 post-sweep to carry it
+            name = "outer_cg_rz";
+            const double b = (mixed ? 24.0 : 16.0) * n;
+            RN_LAUNCH("outer_cg_vec", b, h.s, cg_rz_kernel, VG(cg_rz_kernel), kS, 0, n, h.r.p, h.z.p,
+                      mixed ? h.rold.p : nullptr, make_fin(h, FIN_STORE, sc + 20));
+            return b;
+        }
+        case RN_OP_CG_P: {
+            name = "outer_cg_p";
+            const double b = 24.0 * n;
+            RN_LAUNCH("outer_cg_vec", b, h.s, cg_p_kernel, VG(cg_p_kernel), kS, 0, n, h.pv.p, h.z.p, sc, 0);
+            return b;
+        }
+        case RN_OP_COARSE_CLUSTER: {
+            if (h.sub_k < 0) fail(RN_EINVAL, "this hierarchy runs no cluster cycle");
+            name = mixed ? "cycle_coarse_cluster_f32" : "cycle_coarse_cluster_f64";
+            launch_subcycle<T>(h, pre_smoothed<T>(*h.lev[h.sub_k], h.p.nu_pre), name.c_str());
+            return 0.0;  // latency-bound: no bandwidth claim
+        }
+        default: fail(RN_EINVAL, "unknown operation");
+    }
+    return 0.0;
+}
+
+void time_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, std::string &name) {
+    cudaStream_t s = h.s;
+    if (reps < 1 || reps > 100000) fail(RN_EINVAL, "reps must be in [1, 100000]");
+    if (flush_bytes < 0) fail(RN_EINVAL, "flush_bytes must be >= 0");
+    DVec<unsigned char> fl(flush_bytes > 0 ? (size_t)flush_bytes : 0, s);
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+    struct EvGuard {
+        std::vector<cudaEvent_t> &ev;
+        ~EvGuard() {
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } guard{ev};
+    for (auto &e : ev) RN_CUDA_CHECK(cudaEventCreate(&e));
+    const bool mixed = h.p.precision == RN_MIXED;
+    double b = 0.0;
+    for (int r = 0; r < reps; r++) {
+        // the flush keeps the GPU busy while the launch is enqueued and leaves L2 cold
+        if (flush_bytes > 0) RN_CUDA_CHECK(cudaMemsetAsync(fl.p, r & 0xff, (size_t)flush_bytes, s));
+        RN_CUDA_CHECK(cudaEventRecord(ev[2 * r], s));
+        b = mixed ? enqueue_op<float>(h, op, name) : enqueue_op<double>(h, op, name);
+        RN_CUDA_CHECK(cudaEventRecord(ev[2 * r + 1], s));
+    }
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    check_tile_error(h);
+    double tot = 0.0;
+    for (int r = 0; r < reps; r++) {
+        float ms = 0.f;
+        RN_CUDA_CHECK(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]));
+        tot += ms;
+    }
+    *us = tot * 1e3 / reps;
+    *bytes = b;
 }
 
 }  // namespace rn

@@ -8,39 +8,160 @@
 // * masked_product_proj: the energy-minimisation operator
 //   W = scale * Proj(Mask_N(A X)) on a fixed pattern, with the row-wise
 //   constraint projection and a Frobenius product fused in.
+#include <climits>
+
 #include "rn_internal.cuh"
 
 namespace rn {
 
 // ------------------------------------------------------------------ fused product (pattern + values)
-// One hash pass per row: the products a_ik b_kj of row i are inserted in
-// ascending k into a shared-memory table of (column, value) slots; a value
-// accumulates as a rounded multiply followed by a rounded add, in the order of
-// k, which is the order of a plain sequential evaluation.  The row's entries,
-// sorted by column, go to a temporary at the row's offset in the prefix sum of
-// its product counts (an upper bound of its length); a scan of the true
-// lengths and a compaction produce C.
+// Rows are binned by their product count (the number of terms a_ik b_kj):
+// * at most kSmallProd: a group of G lanes lists the row's products in
+//   (k, position in B_k) order - ascending k, the order of a sequential
+//   evaluation - in shared memory; the first product of each column sums its
+//   column's run in list order (a rounded multiply, then one rounded add per
+//   further term: bit-identical to the sequential evaluation) and is written
+//   at its rank among the columns;
+// * more: a shared-memory hash table per row, filled in ascending k, and one
+//   block per row past its capacity.
+// Rows go to a temporary at the row's offset in the prefix sum of the product
+// counts (an upper bound of its length); a scan of the true lengths and a
+// compaction produce C.
 constexpr int kFuThreads = 128;
+constexpr int kSmallProd = 64;
 
+// Product counts, and the row lists of the two bins: rows with at most
+// kSmallProd products fill bins from the front, the others from the back.
 __global__ void product_bound_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                                      const int32_t *__restrict__ brp, int32_t *__restrict__ ub,
-                                     int32_t *__restrict__ err) {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+                                     int32_t *__restrict__ bins, int32_t *__restrict__ flags) {
+    const int lane = threadIdx.x & 31;
+    for (int32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int32_t i = base + threadIdx.x;
+        const bool valid = i < n;
         int64_t u = 0;
-        for (int32_t e = arp[i]; e < arp[i + 1]; e++) u += brp[acol[e] + 1] - brp[acol[e]];
-        if (u > INT32_MAX / 2) {
-            atomicMax(err, i + 1);
-            u = 0;
+        if (valid) {
+            for (int32_t e = arp[i]; e < arp[i + 1]; e++) u += brp[acol[e] + 1] - brp[acol[e]];
+            if (u > INT32_MAX / 2) {
+                atomicMax(flags + 2, i + 1);
+                u = 0;
+            }
+            ub[i] = (int32_t)u;
         }
-        ub[i] = (int32_t)u;
+        const bool small = valid && u <= kSmallProd, large = valid && u > kSmallProd;
+        const unsigned bs = __ballot_sync(0xffffffffu, small), bl = __ballot_sync(0xffffffffu, large);
+        int32_t os = 0, ol = 0;
+        if (lane == 0) {
+            if (bs) os = atomicAdd(flags + 0, __popc(bs));
+            if (bl) ol = atomicAdd(flags + 1, __popc(bl));
+        }
+        os = __shfl_sync(0xffffffffu, os, 0);
+        ol = __shfl_sync(0xffffffffu, ol, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (small) bins[os + __popc(bs & below)] = i;
+        if (large) bins[n - 1 - (ol + __popc(bl & below))] = i;
     }
 }
 
-// G lanes per row, SLOTS table entries per group; rows with product bound in
-// (lo, hi] only.  Rows whose distinct columns exceed SLOTS/2 go to ovf_list.
+template <int G>
+__global__ void __launch_bounds__(kFuThreads)
+small_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
+                     const int32_t *__restrict__ acol, const double *__restrict__ aval,
+                     const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
+                     const double *__restrict__ bval, const int32_t *__restrict__ ubp, int32_t *__restrict__ tcol,
+                     double *__restrict__ tval, int32_t *__restrict__ count) {
+    constexpr int GPB = kFuThreads / G;
+    constexpr int ST = kSmallProd + 1;  // padded stride: groups of one warp start in different banks
+    __shared__ long long s_k[GPB * ST];
+    __shared__ double s_v[GPB * ST];
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const unsigned mask = group_mask<G>();
+    long long *K = s_k + g * ST;  // (column << 8) | list position
+    double *V = s_v + g * ST;     // products in list order
+    for (int32_t r0 = blockIdx.x * GPB; r0 < nrows; r0 += gridDim.x * GPB) {
+        if (r0 + g >= nrows) continue;  // the whole group leaves together
+        const int32_t i = rows[r0 + g];
+        const int32_t as = arp[i], ae = arp[i + 1];
+        // 1. the products in (k, position in B_k) order
+        int32_t m = 0;
+        for (int32_t e0 = as; e0 < ae; e0 += G) {
+            const int32_t e = e0 + lane;
+            int32_t b0 = 0, c = 0;
+            double a = 0.0;
+            if (e < ae) {
+                const int32_t k = acol[e];
+                a = aval[e];
+                b0 = brp[k];
+                c = brp[k + 1] - b0;
+            }
+            int32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const int32_t t = __shfl_up_sync(mask, incl, o, G);
+                if (lane >= o) incl += t;
+            }
+            const int32_t off = m + incl - c;
+            for (int32_t f = 0; f < c; f++) {
+                K[off + f] = ((long long)bcol[b0 + f] << 8) | (long long)(off + f);
+                V[off + f] = __dmul_rn(a, bval[b0 + f]);
+            }
+            m += __shfl_sync(mask, incl, G - 1, G);
+        }
+        // 2. bitonic sort of the keys (padded to a power of two): each column's
+        //    products become one run, in list order
+        int P = 1;
+        while (P < m) P <<= 1;
+        for (int t = m + lane; t < P; t += G) K[t] = LLONG_MAX;
+        __syncwarp(mask);
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int t = lane; t < (P >> 1); t += G) {
+                    const int lo = (t / jj) * 2 * jj + (t % jj), hi = lo + jj;
+                    const long long x = K[lo], y = K[hi];
+                    if ((x > y) == ((lo & k) == 0)) {
+                        K[lo] = y;
+                        K[hi] = x;
+                    }
+                }
+                __syncwarp(mask);
+            }
+        }
+        // 3. each lane takes a contiguous slice of the sorted list; a run's
+        //    first entry sums the run (one rounded add per further product) and
+        //    goes to its rank among the row's columns
+        const int chunk = (m + G - 1) / G;
+        const int s0 = min(m, lane * chunk), s1 = min(m, s0 + chunk);
+        int mine = 0;
+        for (int q = s0; q < s1; q++) mine += (q == 0 || (K[q] >> 8) != (K[q - 1] >> 8)) ? 1 : 0;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const int t = __shfl_up_sync(mask, incl, o, G);
+            if (lane >= o) incl += t;
+        }
+        int pos = incl - mine;
+        const int32_t base = ubp[i];
+        for (int q = s0; q < s1; q++) {
+            const long long key = K[q];
+            const long long j = key >> 8;
+            if (q > 0 && (K[q - 1] >> 8) == j) continue;
+            double sum = V[key & 255];  // 0 + a b
+            for (int u = q + 1; u < m && (K[u] >> 8) == j; u++) sum = __dadd_rn(sum, V[K[u] & 255]);
+            tcol[base + pos] = (int32_t)j;
+            tval[base + pos] = sum;
+            pos++;
+        }
+        const int total = __shfl_sync(mask, incl, G - 1, G);
+        if (lane == 0) count[i] = total;
+        __syncwarp(mask);
+    }
+}
+
+// G lanes per row, SLOTS table entries per group, for the rows listed in
+// rows.  Rows whose distinct columns exceed SLOTS/2 go to ovf_list.
 template <int G, int SLOTS>
 __global__ void __launch_bounds__(kFuThreads)
-hash_product_kernel(int32_t n, int32_t lo, int32_t hi, const int32_t *__restrict__ arp,
+hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
                     const int32_t *__restrict__ acol, const double *__restrict__ aval,
                     const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
                     const double *__restrict__ bval, const int32_t *__restrict__ ubp, int32_t *__restrict__ tcol,
@@ -57,9 +178,9 @@ hash_product_kernel(int32_t n, int32_t lo, int32_t hi, const int32_t *__restrict
     double *vals = vals_all + g * SLOTS;
     int32_t *keys = keys_all + g * SLOTS;
     int32_t *list = list_all + g * (SLOTS / 2);
-    for (int32_t i = blockIdx.x * GPB + g; i < n; i += gridDim.x * GPB) {
+    for (int32_t r = blockIdx.x * GPB + g; r < nrows; r += gridDim.x * GPB) {
+        const int32_t i = rows[r];
         const int32_t ub = ubp[i + 1] - ubp[i];
-        if (ub <= lo || ub > hi) continue;  // another bin handles this row
         int slots = 32;
         while (slots < SLOTS && slots < 2 * ub) slots <<= 1;
         const unsigned hmask = (unsigned)slots - 1u;
@@ -206,8 +327,8 @@ __global__ void compact_rows_kernel(int32_t n, const int32_t *__restrict__ ubp, 
 }
 
 template <int G, int SLOTS>
-static void launch_hash(int32_t lo, int32_t hi, const CsrView &A, const CsrView &B, const int32_t *ubp, int32_t *tcol,
-                        double *tval, int32_t *count, int32_t *ovf_list, int32_t *ovf_n, double bytes,
+static void launch_hash(int32_t nrows, const int32_t *rows, const CsrView &A, const CsrView &B, const int32_t *ubp,
+                        int32_t *tcol, double *tval, int32_t *count, int32_t *ovf_list, int32_t *ovf_n, double bytes,
                         cudaStream_t s) {
     constexpr int GPB = kFuThreads / G;
     const size_t smem = (size_t)GPB * SLOTS * (sizeof(double) + sizeof(int32_t)) + (size_t)GPB * (SLOTS / 2) * 4;
@@ -217,9 +338,18 @@ static void launch_hash(int32_t lo, int32_t hi, const CsrView &A, const CsrView 
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
-    const int grid = grid_for(A.n, GPB, 16);
-    RN_LAUNCH("spgemm_hash", bytes, s, (hash_product_kernel<G, SLOTS>), grid, kFuThreads, smem, A.n, lo, hi, A.rowptr,
-              A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count, ovf_list, ovf_n);
+    const int grid = grid_resident(hash_product_kernel<G, SLOTS>, kFuThreads, smem, nrows, GPB);
+    RN_LAUNCH("spgemm_hash", bytes, s, (hash_product_kernel<G, SLOTS>), grid, kFuThreads, smem, nrows, rows,
+              A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count, ovf_list, ovf_n);
+}
+
+template <int G>
+static void launch_small(int32_t nrows, const int32_t *rows, const CsrView &A, const CsrView &B, const int32_t *ubp,
+                         int32_t *tcol, double *tval, int32_t *count, double bytes, cudaStream_t s) {
+    constexpr int GPB = kFuThreads / G;
+    const int grid = grid_resident(small_product_kernel<G>, kFuThreads, 0, nrows, GPB);
+    RN_LAUNCH("spgemm_small", bytes, s, small_product_kernel<G>, grid, kFuThreads, 0, nrows, rows, A.rowptr, A.col,
+              A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count);
 }
 
 void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
@@ -227,28 +357,39 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
     C.n = A.n;
     C.m = B.m;
     const int32_t n = A.n;
-    DVec<int32_t> ub(n + 1, s), ubp(n + 1, s), count(n + 1, s), flags(4, s), ovf_list(n > 0 ? n : 1, s);
-    fill_i32(flags.p, 0, 4, s);
+    // flags: [0] small rows, [1] large rows, [2] count overflow, [3] rows past the hash tables, [4] past kBigProd
+    DVec<int32_t> ub(n + 1, s), ubp(n + 1, s), count(n + 1, s), flags(8, s), bins(n > 0 ? n : 1, s),
+        ovf_list(n > 0 ? n : 1, s);
+    fill_i32(flags.p, 0, 8, s);
     if (n)
-        RN_LAUNCH("spgemm_bound", 8.0 * A.nnz + 12.0 * n, s, product_bound_kernel, grid_for(n, 256), 256, 0, n,
-                  A.rowptr, A.col, B.rowptr, ub.p, flags.p + 2);
+        RN_LAUNCH("spgemm_bound", 8.0 * A.nnz + 16.0 * n, s, product_bound_kernel, grid_for(n, 256), 256, 0, n,
+                  A.rowptr, A.col, B.rowptr, ub.p, bins.p, flags.p);
     const int64_t total = scan_counts(ub.p, ubp.p, n, s);
-    if (read_scalar(flags.p + 2, s)) fail(RN_EINTERNAL, "spgemm: a row's product count exceeds int32");
+    int32_t fl[3];
+    RN_CUDA_CHECK(cudaMemcpyAsync(fl, flags.p, sizeof fl, cudaMemcpyDeviceToHost, s));
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (fl[2]) fail(RN_EINTERNAL, "spgemm: a row's product count exceeds int32");
     DVec<int32_t> tcol(total > 0 ? total : 1, s);
     DVec<double> tval(total > 0 ? total : 1, s);
     const double bytes = 12.0 * A.nnz + 8.0 * n + 12.0 * B.nnz + 12.0 * total;
-    if (n) {
-        launch_hash<8, 128>(-1, 64, A, B, ubp.p, tcol.p, tval.p, count.p, ovf_list.p, flags.p, bytes, s);
-        launch_hash<32, 1024>(64, INT32_MAX, A, B, ubp.p, tcol.p, tval.p, count.p, ovf_list.p, flags.p, bytes, s);
+    const int32_t nsmall = fl[0], nlarge = fl[1];
+    if (nsmall) {
+        const double avg = (double)A.nnz / std::max(1, n) * ((double)B.nnz / std::max(1, B.n));
+        if (avg <= 8.0) launch_small<4>(nsmall, bins.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+        else if (avg <= 24.0) launch_small<8>(nsmall, bins.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+        else launch_small<16>(nsmall, bins.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
     }
-    const int32_t novf = read_scalar(flags.p, s);
+    if (nlarge)
+        launch_hash<32, 1024>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf_list.p,
+                              flags.p + 3, bytes, s);
+    const int32_t novf = nlarge ? read_scalar(flags.p + 3, s) : 0;
     if (novf > 0) {
         const size_t smem = (size_t)kBigProd * (sizeof(double) + 2 * sizeof(int32_t));
         RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
         RN_LAUNCH("spgemm_hash_long", 0, s, hash_product_block_kernel, novf, 512, smem, ovf_list.p, A.rowptr, A.col,
-                  A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p, count.p, flags.p + 1);
-        if (read_scalar(flags.p + 1, s))
+                  A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p, count.p, flags.p + 4);
+        if (read_scalar(flags.p + 4, s))
             fail(RN_EINTERNAL, fmt("product row has more than %d distinct columns", kBigProd / 2));
     }
     C.rowptr.alloc(n + 1, s);
@@ -276,8 +417,8 @@ __global__ void __launch_bounds__(kEpThreads, 4)
 energy_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                       const double *__restrict__ aval, const int32_t *__restrict__ nrp,
                       const int32_t *__restrict__ ncol, const double *__restrict__ X, double *__restrict__ W,
-                      const int32_t *__restrict__ rowtype, const double *__restrict__ Bc, double scale,
-                      const double *__restrict__ Y, Fin fin) {
+                      const int32_t *__restrict__ rowtype, const double *__restrict__ Bc,
+                      const double *__restrict__ rs2v, double scale, const double *__restrict__ Y, Fin fin) {
     __shared__ double s_red[32];
     constexpr int GPB = kEpThreads / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
@@ -292,7 +433,8 @@ energy_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t 
             continue;
         }
         const int32_t as = arp[i], ae = arp[i + 1];
-        double s1 = 0.0, s2 = 0.0, acc_first = 0.0;
+        const double rs2 = rs2v[i];
+        double s1 = 0.0, acc_first = 0.0;
         for (int32_t q0 = cs; q0 < ce; q0 += G) {
             const int32_t q = q0 + lane;
             const bool active = q < ce;
@@ -313,16 +455,13 @@ energy_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t 
                 }
             }
             if (active) {
-                const double b = Bc[j];
-                s1 = fma(acc, b, s1);
-                s2 = fma(b, b, s2);
+                s1 = fma(acc, Bc[j], s1);
                 if (q0 == cs) acc_first = acc;  // the first chunk stays in registers
                 else W[q] = acc;
             }
         }
         s1 = group_sum<G>(s1, mask);
-        s2 = group_sum<G>(s2, mask);
-        const double c = s1 / s2;
+        const double c = s1 * rs2;
         for (int32_t q = cs + lane; q < ce; q += G) {
             const double v = (q - cs < G) ? acc_first : W[q];  // each lane re-reads only what it wrote
             const double w = scale * (v - c * Bc[ncol[q]]);
@@ -331,6 +470,52 @@ energy_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t 
         }
     }
     grid_finish<kEpThreads, 1>(dot_acc, fin, s_red);
+}
+
+// 1 / sum_j Bc_j^2 over N_i: the scale of the row projection (eq. Tproj),
+// which depends only on the pattern and Bc; 0 on rows the operator zeroes.
+template <int G>
+__global__ void __launch_bounds__(kEpThreads)
+proj_scale_kernel(int32_t n, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
+                  const int32_t *__restrict__ rowtype, const double *__restrict__ Bc, double *__restrict__ rs2) {
+    constexpr int GPB = kEpThreads / G;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const unsigned mask = group_mask<G>();
+    for (int32_t i0 = blockIdx.x * GPB; i0 < n; i0 += gridDim.x * GPB) {
+        const int32_t i = i0 + g;
+        if (i >= n) continue;  // whole group leaves together
+        const int32_t cs = nrp[i], ce = nrp[i + 1];
+        double s2 = 0.0;
+        for (int32_t q = cs + lane; q < ce; q += G) {
+            const double b = Bc[ncol[q]];
+            s2 = fma(b, b, s2);
+        }
+        s2 = group_sum<G>(s2, mask);
+        if (lane == 0) rs2[i] = (rowtype[i] != 0 || ce - cs <= 1) ? 0.0 : 1.0 / s2;
+    }
+}
+
+static int pick_group(double avg_len);
+
+void proj_scales(int32_t n, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, const int32_t *rowtype,
+                 const double *Bc, double *rs2, cudaStream_t s) {
+    if (n == 0) return;
+    const int G = pick_group((double)nnzN / n);
+    const double bytes = 8.0 * (n + 1) + 12.0 * nnzN + 8.0 * n;
+#define RN_PS_CASE(GG)                                                                                          \
+    case GG:                                                                                                    \
+        RN_LAUNCH("energy_proj_scale", bytes, s, proj_scale_kernel<GG>,                                         \
+                  grid_resident(proj_scale_kernel<GG>, kEpThreads, 0, n, kEpThreads / GG), kEpThreads, 0, n,     \
+                  nrowptr, ncol, rowtype, Bc, rs2);                                                             \
+        break;
+    switch (G) {
+        RN_PS_CASE(4)
+        RN_PS_CASE(8)
+        RN_PS_CASE(16)
+        RN_PS_CASE(32)
+        default: fail(RN_EINTERNAL, "bad group size");
+    }
+#undef RN_PS_CASE
 }
 
 static int pick_group(double avg_len) {
@@ -345,8 +530,10 @@ void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t
                          const Fin &fin, cudaStream_t s) {
     if (A.n == 0) return;
     const int G = pick_group((double)nnzN / A.n);
-    int grid = grid_for(A.n, kEpThreads / G, 8);
-    if (grid > kReduceBlocks) grid = kReduceBlocks;
+    const void *fn = G == 4 ? (const void *)energy_product_kernel<4>
+                   : G == 8 ? (const void *)energy_product_kernel<8>
+                   : G == 16 ? (const void *)energy_product_kernel<16> : (const void *)energy_product_kernel<32>;
+    const int grid = grid_resident(fn, kEpThreads, 0, A.n, kEpThreads / G, kReduceBlocks);
     // algorithmic bytes of one energy-minimisation product: A once, the
     // pattern (row pointers + columns) once, X once, W written once, Y once
     // when the Frobenius product is taken, row types and Bc once.
@@ -355,7 +542,7 @@ void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t
 #define RN_EP_CASE(GG)                                                                                           \
     case GG:                                                                                                     \
         RN_LAUNCH("energy_masked_product", bytes, s, energy_product_kernel<GG>, grid, kEpThreads, 0, A.n, A.rowptr, \
-                  A.col, A.val, nrowptr, ncol, X, W, pa.rowtype, pa.Bc, scale, Y, fin);                          \
+                  A.col, A.val, nrowptr, ncol, X, W, pa.rowtype, pa.Bc, pa.rs2, scale, Y, fin);                  \
         break;
     switch (G) {
         RN_EP_CASE(4)

@@ -22,6 +22,8 @@ RN_ENERGY_CG, RN_ENERGY_GMRES = 0, 1
 RN_FP64, RN_MIXED = 0, 1
 RN_OUTER_STATIONARY, RN_OUTER_CG, RN_OUTER_FGMRES = 0, 1, 2
 RN_MAX_LEVELS = 32
+(RN_OP_OUTER_SPMV, RN_OP_RELAX0_RESIDUAL, RN_OP_JACOBI_OUT, RN_OP_RESTRICT, RN_OP_PROLONG, RN_OP_CG_XR,
+ RN_OP_CG_RZ, RN_OP_CG_P, RN_OP_COARSE_CLUSTER, RN_OP_COUNT) = range(10)
 STATUS_NAMES = ["RN_OK", "RN_EINVAL", "RN_ENOMEM", "RN_ESINGULAR", "RN_ESTALL", "RN_ENOTCONV", "RN_ETIMEOUT",
                 "RN_ECUDA", "RN_EINTERNAL"]
 
@@ -38,7 +40,7 @@ class rn_params(C.Structure):
                 ("max_levels", C.c_int), ("b_sweeps", C.c_int), ("omega", C.c_double), ("seed", C.c_uint64),
                 ("symmetric", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int), ("precision", C.c_int),
                 ("outer", C.c_int), ("restart", C.c_int), ("use_graphs", C.c_int), ("keep_aux", C.c_int),
-                ("stream", C.c_void_p)]
+                ("coarse_cluster", C.c_int), ("stream", C.c_void_p)]
 
 
 class rn_solve_info(C.Structure):
@@ -81,6 +83,7 @@ def _load():
     L.rn_profile_read.argtypes = [P(rn_kernel_stat), C.c_int, P(C.c_int)]
     L.rn_kernel_launches.argtypes = []
     L.rn_kernel_launches.restype = C.c_int64
+    L.rn_time_op.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, P(C.c_double), P(C.c_double), C.c_char_p]
     L.rn_last_error.restype = C.c_char_p
     L.rn_status_string.argtypes = [C.c_int]
     L.rn_status_string.restype = C.c_char_p
@@ -104,6 +107,7 @@ rn_profile_read = lib.rn_profile_read
 rn_last_error = lib.rn_last_error
 rn_status_string = lib.rn_status_string
 rn_kernel_launches = lib.rn_kernel_launches
+rn_time_op = lib.rn_time_op
 rn_energy_min = lib.rn_energy_min
 rn_energy_min_noalloc = lib.rn_energy_min_noalloc
 
@@ -162,7 +166,8 @@ def params_from_config(cfg: dict, **overrides) -> rn_params:
               max_levels=m.get("max_levels", 25), b_sweeps=m.get("b_sweeps", 4), omega=m.get("omega", 2.0 / 3.0),
               seed=m.get("seed", 12345), symmetric=m.get("symmetric", 1), nu_pre=m.get("nu_pre", 1),
               nu_post=m.get("nu_post", 1), precision=m.get("precision", RN_FP64), outer=m.get("outer", RN_OUTER_CG),
-              restart=m.get("restart", 30), use_graphs=m.get("use_graphs", 1), keep_aux=m.get("keep_aux", 0))
+              restart=m.get("restart", 30), use_graphs=m.get("use_graphs", 1), keep_aux=m.get("keep_aux", 0),
+              coarse_cluster=m.get("coarse_cluster", 1))
     return default_params(**kw)
 
 
@@ -222,6 +227,17 @@ class Hierarchy:
 
     def vcycle(self, b, x):
         _check(rn_vcycle(self._h, _ptr(b), _ptr(x)), "rn_vcycle")
+
+    def time_op(self, op: int, reps: int = 20, flush_bytes: int = 256 << 20):
+        """(name, mean device us per launch, algorithmic bytes) of one level-0 launch of the solve
+        timed in isolation (rn_time_op); None when this hierarchy does not run it."""
+        us, by = C.c_double(), C.c_double()
+        nm = C.create_string_buffer(48)
+        st = rn_time_op(self._h, op, reps, flush_bytes, C.byref(us), C.byref(by), nm)
+        if st == RN_EINVAL:
+            return None
+        _check(st, "rn_time_op")
+        return nm.value.decode(), us.value, by.value
 
     def stats(self) -> dict:
         s = rn_stats()

@@ -178,10 +178,11 @@ def test_mixed_precision_reaches_fp64_tolerance(rn, torch_dev, case):
     h.close()
 
 
-def test_vcycle_matches_oracle_cycle(rn, torch_dev, oracle):
+@pytest.mark.parametrize("cluster", [0, 1])
+def test_vcycle_matches_oracle_cycle(rn, torch_dev, oracle, cluster):
     torch, d = torch_dev
     pr = CASES["aniso96"]()
-    h = gpu_hierarchy(rn, torch_dev, pr, use_graphs=0)
+    h = gpu_hierarchy(rn, torch_dev, pr, use_graphs=0, coarse_cluster=cluster)
     oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
     b = dev(torch_dev, pr.b)
     x = torch.zeros_like(b)
@@ -190,13 +191,41 @@ def test_vcycle_matches_oracle_cycle(rn, torch_dev, oracle):
     xg = x.cpu().numpy()
     assert np.max(np.abs(xg - xo)) <= 1e-10 * np.max(np.abs(xo))
     # the graph-captured cycle gives the same result as direct launches
-    h2 = gpu_hierarchy(rn, torch_dev, pr, use_graphs=1)
+    h2 = gpu_hierarchy(rn, torch_dev, pr, use_graphs=1, coarse_cluster=cluster)
     x2 = torch.zeros_like(b)
     h2.vcycle(b, x2)
     h2.vcycle(b, x2)
     assert np.array_equal(x2.cpu().numpy(), xg)
     h.close()
     h2.close()
+
+
+def _cycle(rn, torch_dev, pr, b, **over):
+    """One V-cycle with direct launches; returns (x, kernels launched)."""
+    torch, d = torch_dev
+    h = gpu_hierarchy(rn, torch_dev, pr, use_graphs=0, **over)
+    x = torch.zeros_like(b)
+    k0 = rn.rn_kernel_launches()
+    h.vcycle(b, x)
+    k1 = rn.rn_kernel_launches()
+    h.close()
+    return x.cpu().numpy(), k1 - k0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 2), (0, 1), (1, 0), (3, 1)])
+@pytest.mark.parametrize("case,passes", [("aniso96", 1), ("aniso96", 2), ("poisson64", 1), ("convdiff80", 1)])
+def test_cluster_cycle_matches_per_level_launches(rn, torch_dev, precision, nu, case, passes):
+    """The smallest levels run as one cluster launch or as one launch per
+    operation: the same cycle, rows summed with a different lane count only."""
+    pr = CASES[case]()
+    b = dev(torch_dev, pr.b)
+    kw = dict(precision=precision, nu_pre=nu[0], nu_post=nu[1])
+    ref, k_ref = _cycle(rn, torch_dev, pr, b, coarse_cluster=0, **kw)
+    got, k_got = _cycle(rn, torch_dev, pr, b, coarse_cluster=passes, **kw)
+    assert k_got < k_ref  # the cluster path was taken
+    tol = 1e-12 if precision == 0 else 1e-4
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
 
 
 def test_host_location_matches_device(rn, torch_dev):
@@ -349,3 +378,61 @@ def test_full_size_aniso_hierarchy_parity_and_solve(rn, torch_dev, oracle):
         xs, info, res = gpu_solve(rn, torch_dev, h, pr, maxit=2000)
         assert info["status"] == 0 and res < 1e-8, (prec, info, res)
         h.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_time_op_measures_every_solve_launch(rn, torch_dev, precision):
+    """The measurement hook times each level-0 launch of the solve and leaves
+    the hierarchy usable: a solve afterwards still converges."""
+    pr = CASES["aniso96"]()
+    h = gpu_hierarchy(rn, torch_dev, pr, precision=precision)
+    seen = {}
+    for op in range(rn.RN_OP_COUNT):
+        r = h.time_op(op, reps=3, flush_bytes=1 << 20)
+        assert r is not None, op
+        name, us, by = r
+        assert name and us > 0.0
+        assert (by == 0.0) == (op == rn.RN_OP_COARSE_CLUSTER)
+        seen[op] = name
+    assert len(set(seen.values())) == rn.RN_OP_COUNT
+    xs, info, res = gpu_solve(rn, torch_dev, h, pr)
+    assert info["status"] == 0 and res < 1e-8
+    h.close()
+    h = gpu_hierarchy(rn, torch_dev, pr, precision=precision, coarse_cluster=0)
+    assert h.time_op(rn.RN_OP_COARSE_CLUSTER, reps=1, flush_bytes=0) is None
+    h.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nu", [(1, 1), (1, 0), (2, 2)])
+def test_cg_graph_loop_matches_host_loop(rn, torch_dev, precision, nu):
+    """Outer CG driven on the device (graph launches of several iterations,
+    conditional nodes, stop decided by the reduction finisher) against the
+    host-driven loop: the same kernels in the same order, so the same
+    iterates bit for bit, for every iteration limit (stops inside a launch).
+    V(1,0) is not a symmetric preconditioner, so plain FP64 CG need not
+    converge with it; the two loops must still agree."""
+    pr = CASES["aniso96"]()
+    for maxit in (400, 5, 16, 17):
+        out = []
+        for graphs in (1, 0):
+            h = gpu_hierarchy(rn, torch_dev, pr, precision=precision, nu_pre=nu[0], nu_post=nu[1],
+                              use_graphs=graphs)
+            xs, info = _solve_capped(rn, torch_dev, h, pr, maxit)
+            out.append((xs, info["iters"], info["status"]))
+            h.close()
+        assert out[0][1:] == out[1][1:], (maxit, out[0][1:], out[1][1:])
+        assert np.array_equal(out[0][0], out[1][0]), maxit
+        if maxit == 400 and (nu[0] == nu[1] or precision == 1):
+            res = np.linalg.norm(pr.b - pr.A.to_scipy() @ out[0][0]) / np.linalg.norm(pr.b)
+            assert out[0][2] == 0 and res < 1e-8
+        if maxit < 400:
+            assert out[0][1] == maxit
+
+
+def _solve_capped(rn, torch_dev, h, pr, maxit):
+    torch, d = torch_dev
+    b = dev(torch_dev, pr.b)
+    x = torch.zeros_like(b)
+    info = h.solve(b, x, rtol=1e-8, maxit=maxit, raise_on_notconv=False)
+    return x.cpu().numpy(), info
