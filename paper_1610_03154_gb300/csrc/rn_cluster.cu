@@ -69,7 +69,9 @@ subcycle_cluster_kernel(const SubPhase<T> *__restrict__ phases, int nph, const d
             av[u] = q < e ? __ldg(P.M.val + q) : T(0);
         }
     };
-    prefetch(ph[0]);
+    prefetch(ph[0]);  // matrix data only: may run while the predecessor finishes
+    pdl_wait();
+    pdl_trigger();
     for (int p = 0; p < nph; p++) {
         const SubPhase<T> &P = ph[p];
         const int op = P.op;
@@ -325,13 +327,15 @@ void launch_subcycle(rn_hierarchy &h, T *cur_k, const char *name) {
     cfg.gridDim = dim3(h.sub_cs);
     cfg.blockDim = dim3(kClusterThreads);
     cfg.stream = h.s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = h.sub_cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = h.pdl ? 2 : 1;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, subcycle_cluster_kernel<T>,
                                              reinterpret_cast<const SubPhase<T> *>(h.sub_desc.p), h.sub_nph,
                                              (const double *)h.Ainv.p);

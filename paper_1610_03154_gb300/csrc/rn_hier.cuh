@@ -51,6 +51,8 @@ struct rn_hierarchy {
     // cycle below level sub_k run by one thread-block cluster (sub_k < 0: off)
     rn::DVec<unsigned char> sub_desc;             // SubPhase<T>[sub_nph]
     int sub_k = -1, sub_cs = 0, sub_nph = 0;
+    // solve-path kernels launched with programmatic dependent launch
+    bool pdl = true;
     // statistics
     double setup_ms = 0.0;
     int agg_rounds = 0;

@@ -169,11 +169,13 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
     bool failed = false;
     int st = 0;
     int tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles) {
+    if (tid == 0 && tile < ntiles) {  // the matrix is constant: stage it before the predecessor finishes
         load_bounds(tile);
         issue(0, tile);
         load_bounds(tile + gridDim.x);
     }
+    pdl_wait();
+    pdl_trigger();
     for (; tile < ntiles; tile += gridDim.x, st ^= 1) {
         const int nxt = tile + gridDim.x;
         if (tid == 0 && nxt < ntiles) {
@@ -280,6 +282,8 @@ spmv_group_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__re
     constexpr int NV = OpNV<OP>::value;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     double red[NV] = {};
+    pdl_wait();
+    pdl_trigger();
     for (int32_t i0 = blockIdx.x * (kS / G); i0 < n; i0 += gridDim.x * (kS / G)) {
         const int32_t i = i0 + g;
         T acc = T(0);
@@ -299,6 +303,8 @@ spmv_group_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__re
 template <typename T, typename TB>
 __global__ void jacobi_zero_kernel(int32_t n, const TB *__restrict__ b, const T *__restrict__ diag, T omega,
                                    T *__restrict__ y) {
+    pdl_wait();
+    pdl_trigger();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         y[i] = diag[i] * (T)b[i];  // diag holds omega / a_ii
 }
@@ -307,6 +313,8 @@ __global__ void jacobi_zero_kernel(int32_t n, const TB *__restrict__ b, const T 
 template <typename TB, typename TO>
 __global__ void coarse_solve_kernel(int32_t n, const double *__restrict__ Ainv, const TB *__restrict__ b,
                                     TO *__restrict__ x) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
         double acc = 0.0;
@@ -317,6 +325,8 @@ __global__ void coarse_solve_kernel(int32_t n, const double *__restrict__ Ainv, 
 }
 
 __global__ void f2d_kernel(int64_t n, const float *__restrict__ x, double *__restrict__ y) {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (double)x[i];
 }
@@ -347,6 +357,8 @@ __global__ void __launch_bounds__(kS)
 cg_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
              const double *__restrict__ q, double *__restrict__ rold, const double *__restrict__ sc, Fin fin) {
     __shared__ double sm[32];
+    pdl_wait();
+    pdl_trigger();
     const double a = sc[12];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double acc[1] = {0.0};
@@ -382,6 +394,8 @@ __global__ void __launch_bounds__(kS)
 cg_rz_kernel(int64_t n, const double *__restrict__ r, const double *__restrict__ z, const double *__restrict__ rold,
              Fin fin) {
     __shared__ double sm[32];
+    pdl_wait();
+    pdl_trigger();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double acc[2] = {0.0, 0.0};
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
@@ -410,6 +424,8 @@ cg_rz_kernel(int64_t n, const double *__restrict__ r, const double *__restrict__
 __global__ void __launch_bounds__(kS)
 cg_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__ z, const double *__restrict__ sc,
             int first) {
+    pdl_wait();
+    pdl_trigger();
     const double beta = sc[13];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
@@ -429,6 +445,14 @@ cg_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__ z, con
         }
     }
 }
+
+// Solve-path launches: with programmatic dependent launch when the hierarchy
+// uses it (every kernel launched this way calls pdl_wait first).
+#define RN_SLAUNCH(h, name, bytes, stream, kernel, grid, block, smem, ...)              \
+    do {                                                                                 \
+        if ((h).pdl) RN_LAUNCH_PDL(name, bytes, stream, kernel, grid, block, smem, __VA_ARGS__); \
+        else RN_LAUNCH(name, bytes, stream, kernel, grid, block, smem, __VA_ARGS__);     \
+    } while (0)
 
 // one wave of resident blocks for the level-0 vector kernels
 static int vec_grid(const void *k, int64_t n) {
@@ -540,7 +564,8 @@ const float *vals_of<float>(const DCsr &A) { return A.val32.p; }
 
 template <typename T, typename TB, typename TO, int G, int OP>
 static void launch_tile(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
-                        T omega, TO *y, T *xz, const double *aux, const Fin &fin, int32_t *err, cudaStream_t s) {
+                        T omega, TO *y, T *xz, const double *aux, const Fin &fin, int32_t *err, cudaStream_t s,
+                        bool pdl) {
     constexpr int SL = kTileNnz + kTileSlack;
     constexpr int RL = kS / G + 8;
     const size_t smem = (2 * SL + 2 * RL) * sizeof(int32_t) + 2 * SL * sizeof(T);
@@ -554,17 +579,23 @@ static void launch_tile(const char *name, double bytes, const DCsr &M, const T *
     const int per_sm = sizeof(T) == 8 ? 3 : 4;  // CTAs that fit one SM's shared memory
     int grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
     grid = std::max(1, std::min(grid, kReduceBlocks));
-    RN_LAUNCH(name, bytes, s, (spmv_tile_kernel<T, TB, TO, G, OP>), grid, kS, smem, M.n, ntiles, M.rowptr.p, M.col.p,
-              vals_of<T>(M), x, b, diag, omega, y, xz, aux, fin, err);
+    struct {
+        bool pdl;
+    } hh{pdl};
+    RN_SLAUNCH(hh, name, bytes, s, (spmv_tile_kernel<T, TB, TO, G, OP>), grid, kS, smem, M.n, ntiles, M.rowptr.p,
+               M.col.p, vals_of<T>(M), x, b, diag, omega, y, xz, aux, fin, err);
 }
 
 template <typename T, typename TB, typename TO, int G, int OP>
 static void launch_group(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
-                         T omega, TO *y, T *xz, const double *aux, const Fin &fin, cudaStream_t s) {
+                         T omega, TO *y, T *xz, const double *aux, const Fin &fin, cudaStream_t s, bool pdl) {
     int grid = grid_for(M.n, kS / G, 8);
     grid = std::min(grid, kReduceBlocks);
-    RN_LAUNCH(name, bytes, s, (spmv_group_kernel<T, TB, TO, G, OP>), grid, kS, 0, M.n, M.rowptr.p, M.col.p,
-              vals_of<T>(M), x, b, diag, omega, y, xz, aux, fin);
+    struct {
+        bool pdl;
+    } hh{pdl};
+    RN_SLAUNCH(hh, name, bytes, s, (spmv_group_kernel<T, TB, TO, G, OP>), grid, kS, 0, M.n, M.rowptr.p, M.col.p,
+               vals_of<T>(M), x, b, diag, omega, y, xz, aux, fin);
 }
 
 // Algorithmic bytes of one SpMV-family launch: the matrix (index + value) and
@@ -593,9 +624,9 @@ static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, c
     int32_t *err = h.iflags.p + 8;
     const int G = M.tile_group;
 #define RN_TILE_CASE(GG) \
-    case GG: launch_tile<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, err, s); return;
+    case GG: launch_tile<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, err, s, h.pdl); return;
 #define RN_GROUP_CASE(GG) \
-    case GG: launch_group<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, s); return;
+    case GG: launch_group<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, s, h.pdl); return;
     switch (G) {
         RN_TILE_CASE(1)
         RN_TILE_CASE(2)
@@ -610,7 +641,7 @@ static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, c
         RN_GROUP_CASE(4)
         RN_GROUP_CASE(8)
         RN_GROUP_CASE(16)
-        default: launch_group<T, TB, TO, 32, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, s); return;
+        default: launch_group<T, TB, TO, 32, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, s, h.pdl); return;
     }
 #undef RN_TILE_CASE
 #undef RN_GROUP_CASE
@@ -667,7 +698,7 @@ static T *relax0_and_residual(rn_hierarchy &h, const CycleNames &nm, rn_level &L
     }
     for (int k = 0; k < h.p.nu_pre; k++) {
         if (k == 0) {
-            RN_LAUNCH(nm.jacobi0, (sizeof(TB) + 2.0 * sizeof(T)) * n, s, (jacobi_zero_kernel<T, TB>),
+            RN_SLAUNCH(h, nm.jacobi0, (sizeof(TB) + 2.0 * sizeof(T)) * n, s, (jacobi_zero_kernel<T, TB>),
                       grid_for(n, 1024), 256, 0, n, b, d, omega, cur);
         } else {
             spmv<T, TB, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, b, d, omega, oth, none);
@@ -714,7 +745,7 @@ static T *vcycle_level(rn_hierarchy &h, int l) {
     const Fin none;
     if (l == (int)h.lev.size() - 1) {
         T *x = LB::x(L);
-        RN_LAUNCH(nm.coarse, 8.0 * n * n + 2.0 * sizeof(T) * n, s, (coarse_solve_kernel<T, T>),
+        RN_SLAUNCH(h, nm.coarse, 8.0 * n * n + 2.0 * sizeof(T) * n, s, (coarse_solve_kernel<T, T>),
                   grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, b, x);
         return x;
     }
@@ -744,7 +775,7 @@ static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fi
     const int32_t n = L.A.n;
     const Fin none;
     if (h.lev.size() == 1) {
-        RN_LAUNCH(nm.coarse, 8.0 * n * n + 16.0 * n, s, (coarse_solve_kernel<double, double>),
+        RN_SLAUNCH(h, nm.coarse, 8.0 * n * n + 16.0 * n, s, (coarse_solve_kernel<double, double>),
                   grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, rhs, out);
         return false;
     }
@@ -770,7 +801,7 @@ static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fi
     }
     // no post-smoothing: copy the iterate out
     if (sizeof(T) == 8) d2d(out, reinterpret_cast<const double *>(cur), n, s);
-    else RN_LAUNCH("convert", 12.0 * n, s, f2d_kernel, grid_for(n, 1024), 256, 0, (int64_t)n,
+    else RN_SLAUNCH(h, "convert", 12.0 * n, s, f2d_kernel, grid_for(n, 1024), 256, 0, (int64_t)n,
                    reinterpret_cast<const float *>(cur), out);
     return false;
 }
@@ -911,7 +942,7 @@ static void cg_iteration_first_half(rn_hierarchy &h, double *x, const Fin &cond)
     Fin fx = make_fin(h, FIN_XR);
     fx.cond_loop = cond.cond_loop;
     fx.cond_body = cond.cond_body;
-    RN_LAUNCH("outer_cg_vec", 48.0 * n + (flexible ? 8.0 * n : 0.0), h.s, cg_xr_kernel, VG(cg_xr_kernel), kS, 0,
+    RN_SLAUNCH(h, "outer_cg_vec", 48.0 * n + (flexible ? 8.0 * n : 0.0), h.s, cg_xr_kernel, VG(cg_xr_kernel), kS, 0,
               n, x, h.r.p, h.pv.p, h.q.p, flexible ? h.rold.p : nullptr, sc, fx);
 }
 
@@ -923,9 +954,9 @@ static void cg_iteration_second_half(rn_hierarchy &h, bool flexible) {
     fr.it = flexible ? 2 : 0;
     const double *rold = flexible ? h.rold.p : nullptr;
     if (!cycle_direct(h, h.r.p, h.z.p, &fr, rold))
-        RN_LAUNCH("outer_cg_vec", (flexible ? 24.0 : 16.0) * n, h.s, cg_rz_kernel, VG(cg_rz_kernel), kS, 0, n,
+        RN_SLAUNCH(h, "outer_cg_vec", (flexible ? 24.0 : 16.0) * n, h.s, cg_rz_kernel, VG(cg_rz_kernel), kS, 0, n,
                   h.r.p, h.z.p, rold, fr);
-    RN_LAUNCH("outer_cg_vec", 24.0 * n, h.s, cg_p_kernel, VG(cg_p_kernel), kS, 0, n, h.pv.p, h.z.p, h.scal.p, 0);
+    RN_SLAUNCH(h, "outer_cg_vec", 24.0 * n, h.s, cg_p_kernel, VG(cg_p_kernel), kS, 0, n, h.pv.p, h.z.p, h.scal.p, 0);
 }
 
 // Capture stream work into a standalone graph.
@@ -1007,7 +1038,24 @@ static void build_cg_graph(rn_hierarchy &h) {
     add_launches(k0 - k2);  // captured, not launched
     cudaGraphDestroy(g2);
     RN_CUDA_CHECK(e);
-    RN_CUDA_CHECK(cudaGraphInstantiate(&h.cg_exec, g, 0));
+    e = cudaGraphInstantiate(&h.cg_exec, g, 0);
+    if (e != cudaSuccess && h.pdl) {
+        // programmatic edges inside conditional bodies not accepted here: plain edges
+        cudaGetLastError();
+        h.cg_exec = nullptr;
+        h.pdl = false;
+        if (h.graph_exec) {  // keep the cycle graph consistent with the launches
+            cudaGraphExecDestroy(h.graph_exec);
+            cudaGraphDestroy(h.graph);
+            h.graph_exec = nullptr;
+            h.graph = nullptr;
+        }
+        cudaGraphDestroy(g);
+        g = nullptr;
+        build_cg_graph(h);
+        return;
+    }
+    RN_CUDA_CHECK(e);
     h.cg_graph = g;
     g = nullptr;
 }
