@@ -120,7 +120,7 @@ typedef struct rn_hierarchy rn_hierarchy;
 
 /* Fill *p with the defaults (theta 0.25, d 2, 4 CG sweeps, no filtering,
  * max_coarse 64, 4 candidate sweeps, omega 2/3, symmetric, V(1,1), FP64,
- * CG outer, graphs on, coarse_cluster 1).  Returns RN_EINVAL for
+ * CG outer, graphs on, coarse_cluster 0).  Returns RN_EINVAL for
  * p == NULL. */
 rn_status rn_default_params(rn_params *p);
 
@@ -230,12 +230,13 @@ int64_t rn_kernel_launches(void);
  * off) or reps outside [1, 100000]. */
 enum {
     RN_OP_OUTER_SPMV = 0,      /* q = A p with <p, q> (FP64) */
-    RN_OP_RELAX0_RESIDUAL = 1, /* level 0: first sweep from zero fused with the residual */
+    RN_OP_RELAX0_RESIDUAL = 1, /* level 0: residual after the first sweep from zero (the sweep's
+                                  x0 = omega D^{-1} r is formed by RN_OP_CG_XR) */
     RN_OP_JACOBI_OUT = 2,      /* level 0: last post-sweep, writing the FP64 preconditioned vector z,
                                   fused with the outer CG's <r, z> (and <z, r_old>) */
     RN_OP_RESTRICT = 3,        /* b_1 = R_0 r_0 */
     RN_OP_PROLONG = 4,         /* x_0 += P_0 x_1 */
-    RN_OP_CG_XR = 5,           /* x += alpha p, r -= alpha q, ||r||^2 */
+    RN_OP_CG_XR = 5,           /* x += alpha p, r -= alpha q, ||r||^2, and the cycle's level-0 x0 */
     RN_OP_CG_RZ = 6,           /* <r, z> (and <z, r_old>) on its own: used only when the cycle has no
                                   level-0 post-sweep */
     RN_OP_CG_P = 7,            /* p = z + beta p */

@@ -56,7 +56,7 @@ extern "C" rn_status rn_default_params(rn_params *p) {
     p->restart = 30;
     p->use_graphs = 1;
     p->keep_aux = 0;
-    p->coarse_cluster = 1;
+    p->coarse_cluster = 0;
     p->stream = nullptr;
     return RN_OK;
 }

@@ -8,11 +8,12 @@
 // memory traffic.  Here every operation of the cycle from level k+1 down to
 // the coarsest and back up is one phase of a single cluster launch, phases
 // separated by the cluster barrier (hardware, release/acquire at cluster
-// scope).  The host writes the phase list once (the buffers each phase reads
+// scope, split into arrive and wait).  The host writes the phase list once (the buffers each phase reads
 // and writes are fixed by nu_pre / nu_post); the kernel stages it in shared
-// memory and walks it.  Before each barrier every thread loads the row bounds
-// and its first matrix entries of the next phase, which do not depend on the
-// phase being finished, so after the barrier only the gathers of x remain.
+// memory and walks it.  Between arriving at a barrier and waiting on it every
+// thread loads the row bounds and its first matrix entries of the next phase,
+// which do not depend on the phase being finished, so after the barrier only
+// the gathers of x remain.
 //
 // Rows are summed lane-strided in storage order, like the per-level launches;
 // only the number of lanes per row may differ.  Vectors written inside the
@@ -124,8 +125,11 @@ subcycle_cluster_kernel(const SubPhase<T> *__restrict__ phases, int nph, const d
             }
         }
         if (p + 1 < nph) {
+            // split barrier: this phase's stores are released on arrival; the next
+            // phase's matrix loads then fly while the other CTAs arrive
+            asm volatile("barrier.cluster.arrive.release;" ::: "memory");
             prefetch(ph[p + 1]);
-            cl.sync();
+            asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
         }
     }
 }

@@ -241,7 +241,7 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
             } else if (OP == OP_RESID) {
                 const T r = (T)bi - acc;
                 y[row] = (TO)r;
-                red[0] += (double)r * (double)r;
+                if (fin.mode != FIN_NONE) red[0] += (double)r * (double)r;
             } else if (OP == OP_JACOBI) {
                 y[row] = (TO)(xi + di * ((T)bi - acc));
             } else if (OP == OP_JACOBI_RZ) {
@@ -352,10 +352,14 @@ __global__ void axpy_kernel(int64_t n, double *__restrict__ x, const double *__r
         x[i] += z[i];
 }
 
-// x += alpha p; r_old = r (flexible); r -= alpha q; ||r||^2 (FIN_XR: stopping test)
+// x += alpha p; r_old = r (flexible); r -= alpha q; ||r||^2 (FIN_XR: stopping test);
+// and, when x0 is given, the next cycle's first-sweep iterate x0 = w (XT) r
+// (w = omega / a_ii on level 0), exactly as jacobi_zero_kernel forms it.
+template <typename XT>
 __global__ void __launch_bounds__(kS)
 cg_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-             const double *__restrict__ q, double *__restrict__ rold, const double *__restrict__ sc, Fin fin) {
+             const double *__restrict__ q, double *__restrict__ rold, const double *__restrict__ sc,
+             const XT *__restrict__ w, XT *__restrict__ x0, Fin fin) {
     __shared__ double sm[32];
     pdl_wait();
     pdl_trigger();
@@ -382,6 +386,7 @@ cg_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r, const do
                 if (rold) rold[i] = rv[u];
                 const double rn = rv[u] - a * qv[u];
                 r[i] = rn;
+                if (x0) x0[i] = w[i] * (XT)rn;
                 acc[0] = fma(rn, rn, acc[0]);
             }
         }
@@ -684,7 +689,8 @@ static const CycleNames kNames[2][2] = {
 // returns the iterate buffer; r receives b - A x.  With one pre-sweep both
 // happen in one fused pass.
 template <typename T, typename TB>
-static T *relax0_and_residual(rn_hierarchy &h, const CycleNames &nm, rn_level &L, const TB *b, T *r) {
+static T *relax0_and_residual(rn_hierarchy &h, const CycleNames &nm, rn_level &L, const TB *b, T *r,
+                               bool x0_ready = false) {
     using LB = LevelBufs<T>;
     cudaStream_t s = h.s;
     const int32_t n = L.A.n;
@@ -693,6 +699,16 @@ static T *relax0_and_residual(rn_hierarchy &h, const CycleNames &nm, rn_level &L
     T *cur = LB::x(L), *oth = LB::t(L);
     const Fin none;
     if (h.p.nu_pre == 1) {
+        if (sizeof(TB) == 8) {
+            // level 0 (FP64 right-hand side): x = (omega / a_ii) b is formed once per row (by the
+            // outer CG's update when x0_ready), so the residual gathers plain T values - no
+            // FP64 conversion or product per gathered entry on the narrow FP64 pipe
+            if (!x0_ready)
+                RN_SLAUNCH(h, nm.jacobi0, (sizeof(TB) + 2.0 * sizeof(T)) * n, s, (jacobi_zero_kernel<T, TB>),
+                           grid_for(n, 1024), 256, 0, n, b, d, omega, cur);
+            spmv<T, TB, T, OP_RESID>(h, nm.resid, L.A, cur, b, nullptr, T(0), r, none);
+            return cur;
+        }
         spmv<T, TB, T, OP_JZ_RESID>(h, nm.jzresid, L.A, (const T *)nullptr, b, d, omega, r, none, cur);
         return cur;
     }
@@ -767,7 +783,8 @@ static T *vcycle_level(rn_hierarchy &h, int l) {
 // <out, rz_rold> into *rz (FIN_RZ); returns whether it did (it cannot without
 // a post-sweep on a multilevel hierarchy).
 template <typename T>
-static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fin *rz, const double *rz_rold) {
+static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fin *rz, const double *rz_rold,
+                       bool x0_ready) {
     using LB = LevelBufs<T>;
     cudaStream_t s = h.s;
     rn_level &L = *h.lev[0];
@@ -782,7 +799,7 @@ static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fi
     const T omega = (T)h.p.omega;
     const T *d = LB::d(L);
     T *r = LB::r(L);
-    T *cur = relax0_and_residual<T, double>(h, nm, L, rhs, r);
+    T *cur = relax0_and_residual<T, double>(h, nm, L, rhs, r, x0_ready);
     T *oth = (cur == LB::x(L)) ? LB::t(L) : LB::x(L);
     coarse_correction<T>(h, 0, r, cur);
     const int npost = h.p.nu_post;
@@ -806,11 +823,16 @@ static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fi
     return false;
 }
 
+// x0_ready: level 0's first-sweep iterate (omega / a_ii) rhs is already in its
+// buffer (written by the outer CG's update of rhs).
 static bool cycle_direct(rn_hierarchy &h, const double *rhs, double *out, const Fin *rz = nullptr,
-                         const double *rz_rold = nullptr) {
-    if (h.p.precision == RN_MIXED) return vcycle_top<float>(h, rhs, out, rz, rz_rold);
-    return vcycle_top<double>(h, rhs, out, rz, rz_rold);
+                         const double *rz_rold = nullptr, bool x0_ready = false) {
+    if (h.p.precision == RN_MIXED) return vcycle_top<float>(h, rhs, out, rz, rz_rold, x0_ready);
+    return vcycle_top<double>(h, rhs, out, rz, rz_rold, x0_ready);
 }
+
+// Whether the outer CG's update forms level 0's first-sweep iterate.
+static bool cg_forms_x0(const rn_hierarchy &h) { return h.p.nu_pre == 1 && h.lev.size() > 1; }
 
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out) {
     cudaStream_t s = h.s;
@@ -942,8 +964,16 @@ static void cg_iteration_first_half(rn_hierarchy &h, double *x, const Fin &cond)
     Fin fx = make_fin(h, FIN_XR);
     fx.cond_loop = cond.cond_loop;
     fx.cond_body = cond.cond_body;
-    RN_SLAUNCH(h, "outer_cg_vec", 48.0 * n + (flexible ? 8.0 * n : 0.0), h.s, cg_xr_kernel, VG(cg_xr_kernel), kS, 0,
-              n, x, h.r.p, h.pv.p, h.q.p, flexible ? h.rold.p : nullptr, sc, fx);
+    rn_level &L0r = *h.lev[0];
+    const bool fx0 = cg_forms_x0(h);
+    if (h.p.precision == RN_MIXED)
+        RN_SLAUNCH(h, "outer_cg_vec", 48.0 * n + 8.0 * n + (fx0 ? 8.0 * n : 0.0), h.s, cg_xr_kernel<float>,
+                   VG(cg_xr_kernel<float>), kS, 0, n, x, h.r.p, h.pv.p, h.q.p, h.rold.p, sc,
+                   (const float *)L0r.wd32.p, fx0 ? L0r.x32.p : nullptr, fx);
+    else
+        RN_SLAUNCH(h, "outer_cg_vec", 48.0 * n + (fx0 ? 16.0 * n : 0.0), h.s, cg_xr_kernel<double>,
+                   VG(cg_xr_kernel<double>), kS, 0, n, x, h.r.p, h.pv.p, h.q.p, (double *)nullptr, sc,
+                   (const double *)L0r.wd.p, fx0 ? L0r.x.p : nullptr, fx);
 }
 
 // z = M r, <r,z> (and <z,r_old>) with beta, then p.  The reductions ride on
@@ -953,7 +983,7 @@ static void cg_iteration_second_half(rn_hierarchy &h, bool flexible) {
     Fin fr = make_fin(h, FIN_RZ);
     fr.it = flexible ? 2 : 0;
     const double *rold = flexible ? h.rold.p : nullptr;
-    if (!cycle_direct(h, h.r.p, h.z.p, &fr, rold))
+    if (!cycle_direct(h, h.r.p, h.z.p, &fr, rold, cg_forms_x0(h)))
         RN_SLAUNCH(h, "outer_cg_vec", (flexible ? 24.0 : 16.0) * n, h.s, cg_rz_kernel, VG(cg_rz_kernel), kS, 0, n,
                   h.r.p, h.z.p, rold, fr);
     RN_SLAUNCH(h, "outer_cg_vec", 24.0 * n, h.s, cg_p_kernel, VG(cg_p_kernel), kS, 0, n, h.pv.p, h.z.p, h.scal.p, 0);
@@ -1202,11 +1232,10 @@ static double enqueue_op(rn_hierarchy &h, int op, std::string &name) {
             spmv<double, double, double, OP_SPMV_DOT>(h, "outer_spmv", L0.A, h.pv.p, (const double *)nullptr, nullptr,
                                                       0.0, h.q.p, make_fin(h, FIN_STORE, sc + 20));
             return spmv_bytes<double, double, double, OP_SPMV_DOT>(L0.A);
-        case RN_OP_RELAX0_RESIDUAL:
-            name = nm.jzresid;
-            spmv<T, double, T, OP_JZ_RESID>(h, nm.jzresid, L0.A, (const T *)nullptr, h.r.p, LB::d(L0), omega,
-                                            LB::r(L0), none, LB::x(L0));
-            return spmv_bytes<T, double, T, OP_JZ_RESID>(L0.A);
+        case RN_OP_RELAX0_RESIDUAL:  // x0 = (omega / a_ii) r formed by the outer CG's update
+            name = nm.resid;
+            spmv<T, double, T, OP_RESID>(h, nm.resid, L0.A, LB::x(L0), h.r.p, nullptr, T(0), LB::r(L0), none);
+            return spmv_bytes<T, double, T, OP_RESID>(L0.A);
         case RN_OP_JACOBI_OUT:  // as the CG solve issues it: fused with <r,z> (and <z,r_old>)
             name = nm.jacobi;
             spmv<T, double, double, OP_JACOBI_RZ>(h, nm.jacobi, L0.A, LB::x(L0), h.r.p, LB::d(L0), omega, h.z.p,
@@ -1225,9 +1254,11 @@ static double enqueue_op(rn_hierarchy &h, int op, std::string &name) {
             return spmv_bytes<T, T, T, OP_SPMV_ADD>(L0.P);
         case RN_OP_CG_XR: {
             name = "outer_cg_xr";
-            const double b = 48.0 * n + (mixed ? 8.0 * n : 0.0);
-            RN_LAUNCH("outer_cg_vec", b, h.s, cg_xr_kernel, VG(cg_xr_kernel), kS, 0, n, h.xs.p, h.r.p, h.pv.p, h.q.p,
-                      mixed ? h.rold.p : nullptr, sc, make_fin(h, FIN_STORE, sc + 20));
+            const bool fx0 = cg_forms_x0(h);
+            const double b = 48.0 * n + (mixed ? 8.0 * n : 0.0) + (fx0 ? (mixed ? 8.0 : 16.0) * n : 0.0);
+            T *x0 = fx0 ? LB::x(L0) : nullptr;
+            RN_LAUNCH("outer_cg_vec", b, h.s, cg_xr_kernel<T>, VG(cg_xr_kernel<T>), kS, 0, n, h.xs.p, h.r.p, h.pv.p,
+                      h.q.p, mixed ? h.rold.p : nullptr, sc, LB::d(L0), x0, make_fin(h, FIN_STORE, sc + 20));
             return b;
         }
         case RN_OP_CG_RZ: {  // runs only when the cycle has no level-0 post-sweep to carry it

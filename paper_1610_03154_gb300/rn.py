@@ -167,7 +167,7 @@ def params_from_config(cfg: dict, **overrides) -> rn_params:
               seed=m.get("seed", 12345), symmetric=m.get("symmetric", 1), nu_pre=m.get("nu_pre", 1),
               nu_post=m.get("nu_post", 1), precision=m.get("precision", RN_FP64), outer=m.get("outer", RN_OUTER_CG),
               restart=m.get("restart", 30), use_graphs=m.get("use_graphs", 1), keep_aux=m.get("keep_aux", 0),
-              coarse_cluster=m.get("coarse_cluster", 1))
+              coarse_cluster=m.get("coarse_cluster", 0))
     return default_params(**kw)
 
 

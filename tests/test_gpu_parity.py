@@ -385,7 +385,7 @@ def test_time_op_measures_every_solve_launch(rn, torch_dev, precision):
     """The measurement hook times each level-0 launch of the solve and leaves
     the hierarchy usable: a solve afterwards still converges."""
     pr = CASES["aniso96"]()
-    h = gpu_hierarchy(rn, torch_dev, pr, precision=precision)
+    h = gpu_hierarchy(rn, torch_dev, pr, precision=precision, coarse_cluster=1)
     seen = {}
     for op in range(rn.RN_OP_COUNT):
         r = h.time_op(op, reps=3, flush_bytes=1 << 20)
