@@ -342,6 +342,18 @@ def main():
 
     stats_h = rn.Hierarchy(rp, ci, va, Bd, params=params(prec), stream=sptr)
     hs = stats_h.stats()
+    # the mixed setup's error against the FP64 setup (which matches the FP64
+    # oracle to 1e-12): level-0 P after the FP32 energy-minimisation sweeps
+    setup_err = None
+    if prec == "mixed":
+        ref_h = rn.Hierarchy(rp, ci, va, Bd, params=params("fp64"), stream=sptr)
+        Pm, Pf = stats_h.export_csr(0, 4), ref_h.export_csr(0, 4)
+        same = np.array_equal(Pm[0], Pf[0]) and np.array_equal(Pm[1], Pf[1])
+        setup_err = {"level0_P_pattern_equal": bool(same),
+                     "level0_P_max_rel_err": float(np.max(np.abs(Pm[2] - Pf[2])) / np.max(np.abs(Pf[2])))
+                     if same else None,
+                     "levels": [hs["n"], ref_h.stats()["n"]]}
+        ref_h.close()
     stats_h.close()
 
     cpu = None
@@ -369,6 +381,7 @@ def main():
                           "oc": hs["oc"], "cc": hs["cc"], "setup_ms_last": hs["setup_ms"]},
             "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
+            "mixed_setup_vs_fp64": setup_err,
             "roofline": roofline,
             "level0_launches": kernels,
             "gpu_launches": launches // max(args.steps, 1),

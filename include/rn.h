@@ -215,6 +215,17 @@ rn_status rn_profile_read(rn_kernel_stat *out, int max, int *count);
  * a replayed CUDA graph are counted one by one). */
 int64_t rn_kernel_launches(void);
 
+/* Differentiation through a solve (x = A^{-1} b): given lambda = A^{-T} dL/dx,
+ * the gradient with respect to A's stored values is dL/dA_ij = -lambda_i x_j.
+ * Writes grad[e] = -lambda[row(e)] * x[col[e]] for every stored entry e of A,
+ * in A's CSR order (A->val is not read and may be NULL).
+ *   A        n_rows x n_cols CSR pattern (device), nnz entries;
+ *   lambda   n_rows adjoint values (device); x  n_cols solution values (device);
+ *   grad     nnz outputs (device, written).
+ * Work runs on `stream` (NULL: a stream the call creates); the call returns
+ * when it is done.  Returns RN_EINVAL for null arguments or bad sizes. */
+rn_status rn_adjoint_grad(const rn_csr *A, const double *lambda, const double *x, double *grad, void *stream);
+
 /* Measurement hook (no counterpart in the paper): time one level-0 launch of
  * the solve in isolation.  The operation is enqueued `reps` times on the
  * hierarchy's stream exactly as rn_solve issues it (kernel, launch shape,

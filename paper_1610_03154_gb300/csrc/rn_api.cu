@@ -219,6 +219,21 @@ struct CallStream {
 };
 }  // namespace
 
+extern "C" rn_status rn_adjoint_grad(const rn_csr *A, const double *lambda, const double *x, double *grad,
+                                     void *stream) {
+    RN_API_BEGIN
+    using rn::fail;
+    if (!A || !lambda || !x || !grad) fail(RN_EINVAL, "null argument");
+    if (A->n_rows < 0 || A->n_cols < 0 || A->nnz < 0 || A->nnz > INT32_MAX - 1) fail(RN_EINVAL, "A");
+    if (A->n_rows > 0 && (!A->rowptr || (A->nnz > 0 && !A->col))) fail(RN_EINVAL, "null CSR array");
+    CallStream cs(stream);
+    rn::CsrView Av{A->n_rows, A->n_cols, A->nnz, A->rowptr, A->col, A->val};
+    rn::adjoint_grad(Av, lambda, x, grad, cs.s);
+    RN_CUDA_CHECK(cudaStreamSynchronize(cs.s));
+    return RN_OK;
+    RN_API_END
+}
+
 extern "C" rn_status rn_energy_min(const rn_csr *A, const rn_csr *N, const int32_t *rowtype, const double *Bc,
                                    double *P, int sweeps, int method, int precond, void *stream) {
     RN_API_BEGIN

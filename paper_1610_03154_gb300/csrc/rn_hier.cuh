@@ -105,6 +105,7 @@ struct EmCtx {
     int method = RN_ENERGY_CG;
     double *R = nullptr, *Dd = nullptr, *W = nullptr;
     double *rs2 = nullptr;  // n rows: the row projection's scales (allocated internally when null)
+    bool fp32 = false;      // CG sweeps in FP32 (mixed precision); workspaces then allocated internally
 };
 // dinv: the inverted diagonal of A (CG's preconditioner D^{-1} when c.precond)
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,

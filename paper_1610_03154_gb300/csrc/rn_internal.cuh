@@ -82,7 +82,8 @@ struct DCsr {
     DVec<double> val;
     DVec<float> val32;
     int32_t maxlen = 0;     // longest row (set before solving)
-    int tile_group = 0;     // lanes per row of the staged SpMV (0: rows too long, unstaged kernel)
+    int tile_group = 0;     // lanes per row of the staged SpMV, FP32 values (0: rows too long, unstaged kernel)
+    int tile_group64 = 0;   // the same for FP64 values (smaller stages)
 };
 
 // Borrowed view of a CSR (device pointers).
@@ -199,6 +200,9 @@ void extract_diag(const CsrView &A, double *diag, int32_t *bad, cudaStream_t s);
 // Transpose with sorted rows (values optional).
 void transpose(const CsrView &A, bool with_val, DCsr &At, cudaStream_t s);
 void to_float(const double *x, float *y, int64_t n, cudaStream_t s);
+void to_double(const float *x, double *y, int64_t n, cudaStream_t s);
+// g_e = -lam_i x_j for every stored entry e = (i, j) of A (values unused)
+void adjoint_grad(const CsrView &A, const double *lam, const double *x, double *g, cudaStream_t s);
 // y = 1 / x elementwise (y may be x)
 void reciprocal(const double *x, double *y, int64_t n, cudaStream_t s);
 
@@ -209,19 +213,40 @@ void reciprocal(const double *x, double *y, int64_t n, cudaStream_t s);
 void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s);
 
 // Energy-minimisation operator on the fixed pattern N shared by X and W:
-//   W = Proj(Mask_N(A X)) (scale = -1 negates), plus, when dot_out != nullptr,
-//   the Frobenius product <Y, W> reduced deterministically into *dot_out.
-struct ProjArgs {
+//   W = scale * Proj(Mask_N(A X)) with A's values aval (TV = double, or float
+//   for the mixed-precision sweeps), plus, when Y != nullptr, the Frobenius
+//   product <Y, W> reduced into fin.
+template <typename TV>
+struct ProjArgsT {
     const int32_t *rowtype;  // 0 free, 1 root, 2 unaggregated
-    const double *Bc;        // coarse candidates
-    const double *rs2;       // per row 1 / sum_{j in N_i} Bc_j^2 (proj_scales)
+    const TV *Bc;            // coarse candidates
+    const TV *rs2;           // per row 1 / sum_{j in N_i} Bc_j^2 (proj_scales, FP64; rounded for float)
 };
+using ProjArgs = ProjArgsT<double>;
+// The energy product's gather map for a fixed pattern N (see rn_spgemm.cu):
+// built once per minimisation, then each product gathers directly.
+struct EpMap {
+    DVec<int32_t> base;        // per-row byte offsets (n + 1)
+    DVec<unsigned char> map;   // per row: [position in A_i] x [entry of N_i] offsets into N_k
+    int64_t bytes = 0;
+    int G = 4;
+    bool ok = false;
+};
+// false (and m unusable) when a row of N is too long for byte offsets or the
+// map would exceed int32 offsets; the scanning product is then used
+bool ep_map_build(EpMap &m, const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN,
+                  const int32_t *rowtype, cudaStream_t s);
+template <typename TV>
+void masked_product_mapped(const EpMap &m, const CsrView &A, const TV *aval, const int32_t *nrowptr,
+                           const int32_t *ncol, int64_t nnzN, int32_t nc, const TV *X, TV *W, const ProjArgsT<TV> &pa,
+                           double scale, const TV *Y, const Fin &fin, cudaStream_t s);
 // rs2 for ProjArgs: the row projection's scale on pattern N (n rows)
 void proj_scales(int32_t n, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, const int32_t *rowtype,
                  const double *Bc, double *rs2, cudaStream_t s);
-void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, int32_t nc,
-                         const double *X, double *W, const ProjArgs &pa, double scale, const double *Y,
-                         const Fin &fin, cudaStream_t s);
+template <typename TV>
+void masked_product_proj(const CsrView &A, const TV *aval, const int32_t *nrowptr, const int32_t *ncol,
+                         int64_t nnzN, int32_t nc, const TV *X, TV *W, const ProjArgsT<TV> &pa, double scale,
+                         const TV *Y, const Fin &fin, cudaStream_t s);
 
 // --------------------------------------------------------------- misc
 std::string fmt(const char *f, ...);

@@ -357,6 +357,35 @@ void fill_f64(double *p, double v, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     RN_LAUNCH("fill", 8.0 * n, s, fill_f64_kernel, grid_for(n, 1024), 256, 0, p, v, n);
 }
+// Gradient of a loss through x = A^{-1} b with respect to A's stored values:
+// dL/dA_ij = -lambda_i x_j (lambda = A^{-T} dL/dx), one value per stored
+// entry.  Warp per row; the row's entries are contiguous, so the lanes'
+// stores coalesce.
+__global__ void adjoint_grad_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                    const double *__restrict__ lam, const double *__restrict__ x,
+                                    double *__restrict__ g) {
+    const int lane = threadIdx.x & 31;
+    for (int32_t i = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < n;
+         i += (int32_t)(((int64_t)gridDim.x * blockDim.x) >> 5)) {
+        const double li = lam[i];
+        for (int32_t e = rp[i] + lane; e < rp[i + 1]; e += 32) g[e] = -li * x[col[e]];
+    }
+}
+void adjoint_grad(const CsrView &A, const double *lam, const double *x, double *g, cudaStream_t s) {
+    if (A.n <= 0) return;
+    RN_LAUNCH("adjoint_grad", 16.0 * A.nnz + 4.0 * (A.n + 1) + 16.0 * A.n, s, adjoint_grad_kernel,
+              grid_for((int64_t)A.n * 32, 256), 256, 0, A.n, A.rowptr, A.col, lam, x, g);
+}
+
+__global__ void to_double_kernel(int64_t n, const float *x, double *y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (double)x[i];
+}
+void to_double(const float *x, double *y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    RN_LAUNCH("to_double", 12.0 * n, s, to_double_kernel, grid_for(n, 1024), 256, 0, n, x, y);
+}
+
 __global__ void reciprocal_kernel(int64_t n, const double *x, double *y) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = 1.0 / x[i];

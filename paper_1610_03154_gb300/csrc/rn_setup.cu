@@ -344,62 +344,66 @@ __global__ void tentative_kernel(int32_t n, const int32_t *__restrict__ rp, cons
 // ------------------------------------------------------------------ CG energy minimisation (Sec. 3.6)
 // Device scalars: sc[0] rho, sc[1] rho0, sc[2] beta, sc[3] <Dd,W>, sc[4] alpha; fl[0] = done.
 // The scalar recurrences run in the finishing block of each reduction (Fin).
-// dinv: the preconditioner D^{-1} as the inverted diagonal (nullptr: none)
-template <int G>
+// dinv: the preconditioner D^{-1} as the inverted diagonal (nullptr: none).
+// TV: the value type of the sweeps (double; float in mixed precision, with
+// per-thread sums in TV joining the FP64 grid reduction).
+template <int G, typename TV>
 __global__ void __launch_bounds__(kT)
-cg_rho_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ dinv,
+cg_rho_kernel(int32_t n, const int32_t *__restrict__ rp, const TV *__restrict__ R, const TV *__restrict__ dinv,
               Fin fin) {
     __shared__ double sm[32];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    double acc[1] = {0.0};
+    TV acc = TV(0);
     for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
         const int32_t q0 = rp[i], q1 = rp[i + 1];
-        const double di = dinv ? dinv[i] : 1.0;
-        for (int32_t q = q0 + lane; q < q1; q += G) acc[0] = fma(R[q], R[q] * di, acc[0]);
+        const TV di = dinv ? dinv[i] : TV(1);
+        for (int32_t q = q0 + lane; q < q1; q += G) acc = fma(R[q], R[q] * di, acc);
     }
-    grid_finish<kT, 1>(acc, fin, sm);
+    const double v[1] = {(double)acc};
+    grid_finish<kT, 1>(v, fin, sm);
 }
 
-template <int G>
+template <int G, typename TV>
 __global__ void __launch_bounds__(kT)
-cg_dd_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ R, const double *__restrict__ dinv,
-             const double *__restrict__ sc, const int32_t *__restrict__ fl, int first, double *__restrict__ Dd) {
+cg_dd_kernel(int32_t n, const int32_t *__restrict__ rp, const TV *__restrict__ R, const TV *__restrict__ dinv,
+             const double *__restrict__ sc, const int32_t *__restrict__ fl, int first, TV *__restrict__ Dd) {
     if (fl[0]) return;
-    const double beta = sc[2];
+    const TV beta = (TV)sc[2];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
         const int32_t q0 = rp[i], q1 = rp[i + 1];
-        const double di = dinv ? dinv[i] : 1.0;
+        const TV di = dinv ? dinv[i] : TV(1);
         for (int32_t q = q0 + lane; q < q1; q += G) {
-            const double z = R[q] * di;
+            const TV z = R[q] * di;
             Dd[q] = first ? z : z + beta * Dd[q];
         }
     }
 }
 
-template <int G>
+template <int G, typename TV>
 __global__ void __launch_bounds__(kT)
-cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, double *__restrict__ P, double *__restrict__ R,
-                 const double *__restrict__ Dd, const double *__restrict__ W, const double *__restrict__ dinv,
+cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, TV *__restrict__ P, TV *__restrict__ R,
+                 const TV *__restrict__ Dd, const TV *__restrict__ W, const TV *__restrict__ dinv,
                  const double *__restrict__ sc, const int32_t *__restrict__ fl, Fin fin) {
     __shared__ double sm[32];
     const bool done = fl[0] != 0;
-    const double alpha = sc[4];
+    const TV alpha = (TV)sc[4];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    double acc[1] = {0.0};
+    TV acc = TV(0);
     if (!done) {
         for (int32_t i = blockIdx.x * (kT / G) + g; i < n; i += gridDim.x * (kT / G)) {
             const int32_t q0 = rp[i], q1 = rp[i + 1];
-            const double di = dinv ? dinv[i] : 1.0;
+            const TV di = dinv ? dinv[i] : TV(1);
             for (int32_t q = q0 + lane; q < q1; q += G) {
                 P[q] = P[q] + alpha * Dd[q];
-                const double r = R[q] - alpha * W[q];
+                const TV r = R[q] - alpha * W[q];
                 R[q] = r;
-                acc[0] = fma(r, r * di, acc[0]);
+                acc = fma(r, r * di, acc);
             }
         }
     }
-    grid_finish<kT, 1>(acc, fin, sm);  // the finisher ignores the sum once done is set
+    const double v[1] = {(double)acc};
+    grid_finish<kT, 1>(v, fin, sm);  // the finisher ignores the sum once done is set
 }
 
 // ------------------------------------------------------------------ GMRES energy minimisation (Sec. 4.2)
@@ -635,36 +639,64 @@ static int pick_g(double avg) {
     do {                                                                                                  \
         const int grid_ = std::min(grid_for((n), kT / (G), 8), kReduceBlocks);                            \
         switch (G) {                                                                                      \
-            case 4: RN_LAUNCH(name, bytes, s, kern<4>, grid_, kT, 0, n, __VA_ARGS__); break;              \
-            case 8: RN_LAUNCH(name, bytes, s, kern<8>, grid_, kT, 0, n, __VA_ARGS__); break;              \
-            case 16: RN_LAUNCH(name, bytes, s, kern<16>, grid_, kT, 0, n, __VA_ARGS__); break;            \
-            default: RN_LAUNCH(name, bytes, s, kern<32>, grid_, kT, 0, n, __VA_ARGS__); break;            \
+            case 4: RN_LAUNCH(name, bytes, s, (kern<4, TV>), grid_, kT, 0, n, __VA_ARGS__); break;        \
+            case 8: RN_LAUNCH(name, bytes, s, (kern<8, TV>), grid_, kT, 0, n, __VA_ARGS__); break;        \
+            case 16: RN_LAUNCH(name, bytes, s, (kern<16, TV>), grid_, kT, 0, n, __VA_ARGS__); break;      \
+            default: RN_LAUNCH(name, bytes, s, (kern<32, TV>), grid_, kT, 0, n, __VA_ARGS__); break;      \
         }                                                                                                 \
-        gridp = grid_;                                                                                    \
     } while (0)
 
-// CG energy minimisation of the values X (in/out) on pattern N.
-void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
-                   const double *Bc, const double *c_dinv, int sweeps) {
+// CG energy minimisation of the values X (in/out, FP64) on pattern N, with
+// sweeps in TV: double, or float for the mixed-precision setup (A, X and the
+// CG vectors in FP32; the row projection and the scalar recurrences FP64).
+template <typename TV>
+static void energy_min_cg_t(const EmCtx &c, const CsrView &A, const Pattern &N, double *X64,
+                            const int32_t *rowtype, const double *Bc, const double *c_dinv, int sweeps) {
     cudaStream_t s = c.s;
+    constexpr bool f32 = sizeof(TV) == 4;
+    DVec<TV> Rv, Dv, Wv, Xv, Av, Iv;
+    TV *R, *Dd, *W, *X;
+    const TV *aval, *dinv_t;
+    if constexpr (f32) {
+        Rv.alloc(N.nnz, s); Dv.alloc(N.nnz, s); Wv.alloc(N.nnz, s); Xv.alloc(N.nnz, s);
+        Av.alloc(A.nnz, s); Iv.alloc(N.n, s);
+        R = Rv.p; Dd = Dv.p; W = Wv.p; X = Xv.p;
+        to_float(X64, X, N.nnz, s);
+        to_float(A.val, Av.p, A.nnz, s);
+        to_float(c_dinv, Iv.p, N.n, s);
+        aval = Av.p;
+        dinv_t = Iv.p;
+    } else {
+        R = c.R; Dd = c.Dd; W = c.W; X = X64;
+        if (!R) { Rv.alloc(N.nnz, s); R = Rv.p; }
+        if (!Dd) { Dv.alloc(N.nnz, s); Dd = Dv.p; }
+        if (!W) { Wv.alloc(N.nnz, s); W = Wv.p; }
+        aval = A.val;
+        dinv_t = c_dinv;
+    }
     const int precond = c.precond;
-    DVec<double> Rv, Dv, Wv;
-    double *R = c.R, *Dd = c.Dd, *W = c.W;
-    if (!R) { Rv.alloc(N.nnz, s); R = Rv.p; }
-    if (!Dd) { Dv.alloc(N.nnz, s); Dd = Dv.p; }
-    if (!W) { Wv.alloc(N.nnz, s); W = Wv.p; }
     double *sc = c.sc;
     int32_t *fl = c.fl;
     fill_i32(fl, 0, 1, s);
     DVec<double> Sv;
     double *rs2 = c.rs2;
     if (!rs2) { Sv.alloc(N.n, s); rs2 = Sv.p; }
-    proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);
-    ProjArgs pa{rowtype, Bc, rs2};
+    proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);  // FP64
+    ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
+    DVec<TV> Bcv, Rsv;
+    if constexpr (f32) {
+        Bcv.alloc(N.nc, s);
+        Rsv.alloc(N.n, s);
+        to_float(Bc, Bcv.p, N.nc, s);
+        to_float(rs2, Rsv.p, N.n, s);
+        pa.Bc = Bcv.p;
+        pa.rs2 = Rsv.p;
+    } else {
+        pa.Bc = Bc;
+        pa.rs2 = rs2;
+    }
     const int G = pick_g(N.n ? (double)N.nnz / N.n : 1.0);
-    int gridp = 1;
-    (void)gridp;
-    const double nzb = 8.0 * N.nnz, rpb = 4.0 * (N.n + 1), db = 8.0 * N.n;
+    const double nzb = (double)sizeof(TV) * N.nnz, rpb = 4.0 * (N.n + 1), db = (double)sizeof(TV) * N.n;
     Fin fin;
     fin.partial = c.partial;
     fin.counter = c.counter;
@@ -672,21 +704,36 @@ void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X
     fin.fl = fl;
     fin.stop = kCgStop;
     const Fin none;
-    masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, R, pa, -1.0, nullptr, none, s);
+    // the pattern is fixed for all sweeps: gather map built once (falls back
+    // to the scanning product for rows of N too long for the map)
+    EpMap em;
+    ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
+    auto product = [&](const TV *Xin, TV *Wout, double scale, const TV *Y, const Fin &f) {
+        if (em.ok) masked_product_mapped<TV>(em, A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, Y, f, s);
+        else masked_product_proj<TV>(A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, Y, f, s);
+    };
+    product(X, R, -1.0, nullptr, none);
     fin.mode = FIN_CG_RHO;
     fin.it = 0;
-    const double *dinv = precond ? c_dinv : nullptr;
+    const TV *dinv = precond ? dinv_t : nullptr;
     RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R, dinv, fin);
     for (int it = 0; it < sweeps; it++) {
         RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R, dinv, sc, fl,
                        it == 0 ? 1 : 0, Dd);
         fin.mode = FIN_CG_DW;
-        masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, Dd, W, pa, 1.0, Dd, fin, s);
+        product(Dd, W, 1.0, Dd, fin);
         fin.mode = FIN_CG_RHO;
         fin.it = it + 1;
         RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R, Dd, W, dinv,
                        sc, fl, fin);
     }
+    if constexpr (f32) to_double(X, X64, N.nnz, s);
+}
+
+void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                   const double *Bc, const double *c_dinv, int sweeps) {
+    if (c.fp32) energy_min_cg_t<float>(c, A, N, X, rowtype, Bc, c_dinv, sweeps);
+    else energy_min_cg_t<double>(c, A, N, X, rowtype, Bc, c_dinv, sweeps);
 }
 
 // GMRES energy minimisation (m Arnoldi steps, modified Gram-Schmidt).
@@ -707,13 +754,21 @@ void energy_min_gmres(const EmCtx &c, const CsrView &A, const Pattern &N, double
     ProjArgs pa{rowtype, Bc, rs2};
     const int eg = grid_for(nz, 1024);
     const double nzb = 8.0 * nz;
-    masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, X, V.p, pa, -1.0, nullptr, Fin(), s);
+    EpMap em;
+    ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
+    auto product = [&](const double *Xin, double *Wout, double scale) {
+        if (em.ok)
+            masked_product_mapped<double>(em, A, A.val, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, nullptr,
+                                          Fin(), s);
+        else masked_product_proj<double>(A, A.val, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, nullptr, Fin(), s);
+    };
+    product(X, V.p, -1.0);
     dot(V.p, V.p, nz, sc + 1, s, c.partial, c.counter);
     RN_LAUNCH("energy_gmres_scalar", 0, s, gm_start_kernel, 1, 1, 0, sc, fl, g);
     RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel, eg, 256, 0, nz, V.p, sc, fl);
     for (int j = 0; j < m; j++) {
         double *vj = V.p + (int64_t)j * nz;
-        masked_product_proj(A, N.rp, N.col, N.nnz, N.nc, vj, W.p, pa, 1.0, nullptr, Fin(), s);
+        product(vj, W.p, 1.0);
         for (int i = 0; i <= j; i++) {
             double *vi = V.p + (int64_t)i * nz;
             dot(W.p, vi, nz, H + i * m + j, s, c.partial, c.counter);
@@ -746,6 +801,7 @@ static EmCtx ctx_of(rn_hierarchy &h) {
     c.fl = h.iflags.p;
     c.precond = h.p.energy_precond;
     c.method = h.p.energy_method;
+    c.fp32 = h.p.precision == RN_MIXED;  // FP32 sweeps in the mixed-precision setup (CG)
     return c;
 }
 

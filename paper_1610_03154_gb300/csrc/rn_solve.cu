@@ -24,7 +24,12 @@
 namespace rn {
 
 constexpr int kS = 256;           // threads per block, SpMV family
-constexpr int kTileNnz = 3072;    // matrix entries per shared-memory stage
+// matrix entries per shared-memory stage (four FP32 or three FP64 CTAs fit
+// one SM; smaller FP64 stages with two lanes per row measured slower)
+template <typename T>
+constexpr int tile_nnz() {
+    return 3072;
+}
 constexpr int kTileSlack = 8;     // room for 16-byte alignment of the bulk copies
 constexpr uint32_t kMaxSpin = 1u << 24;  // bound on mbarrier polls before giving up
 
@@ -115,7 +120,7 @@ __device__ __forceinline__ void spmv_epilogue(int32_t i, T acc, const T *__restr
 }
 
 // Tile kernel: G lanes per row, RPT = 256/G rows per tile.  The tile's row
-// pointers and its matrix segment (<= kTileNnz entries; guaranteed by the
+// pointers and its matrix segment (<= tile_nnz<T>() entries; guaranteed by the
 // host's choice of G) are staged by bulk copies into a two-stage buffer.
 // Thread 0 keeps the next tile's copies in flight and prefetches the bounds
 // of the tile after that.  err[0] is set if an mbarrier wait gives up.
@@ -127,7 +132,7 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
                  const double *__restrict__ aux, Fin fin, int32_t *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NV = OpNV<OP>::value;
-    constexpr int SL = kTileNnz + kTileSlack;
+    constexpr int SL = tile_nnz<T>() + kTileSlack;
     constexpr int RPT = kS / G;
     constexpr int RL = RPT + 8;  // staged row pointers per stage (RPT + 1, rounded to 16 bytes)
     constexpr int VA = 16 / (int)sizeof(T);
@@ -547,9 +552,9 @@ static Fin make_fin(rn_hierarchy &h, int mode, double *out = nullptr) {
 }
 
 // lanes per row so that a tile (256/G rows) fits one stage; 0 = rows too long
-static int tile_group(int32_t maxlen) {
+static int tile_group(int32_t maxlen, int nnz_per_stage) {
     for (int G = 1; G <= 32; G *= 2)
-        if ((int64_t)(kS / G) * maxlen <= kTileNnz) return G;
+        if ((int64_t)(kS / G) * maxlen <= nnz_per_stage) return G;
     return 0;
 }
 static int fallback_group(double avg) {
@@ -571,7 +576,7 @@ template <typename T, typename TB, typename TO, int G, int OP>
 static void launch_tile(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
                         T omega, TO *y, T *xz, const double *aux, const Fin &fin, int32_t *err, cudaStream_t s,
                         bool pdl) {
-    constexpr int SL = kTileNnz + kTileSlack;
+    constexpr int SL = tile_nnz<T>() + kTileSlack;
     constexpr int RL = kS / G + 8;
     const size_t smem = (2 * SL + 2 * RL) * sizeof(int32_t) + 2 * SL * sizeof(T);
     static bool configured = false;
@@ -627,7 +632,7 @@ static void spmv(rn_hierarchy &h, const char *name, const DCsr &M, const T *x, c
     if (M.n == 0) return;
     const double bytes = spmv_bytes<T, TB, TO, OP>(M);
     int32_t *err = h.iflags.p + 8;
-    const int G = M.tile_group;
+    const int G = sizeof(T) == 8 ? M.tile_group64 : M.tile_group;
 #define RN_TILE_CASE(GG) \
     case GG: launch_tile<T, TB, TO, GG, OP>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, err, s, h.pdl); return;
 #define RN_GROUP_CASE(GG) \
@@ -869,7 +874,8 @@ static void set_tile_group(rn_hierarchy &h, DCsr &M, int32_t *tmp) {
     RN_CUDA_CHECK(cudaMemsetAsync(tmp, 0, sizeof(int32_t), h.s));
     RN_LAUNCH("prepare", 4.0 * M.n, h.s, row_maxlen_kernel, grid_for(M.n, 1024), 256, 0, M.n, M.rowptr.p, tmp);
     M.maxlen = read_scalar(tmp, h.s);
-    M.tile_group = tile_group(M.maxlen);
+    M.tile_group = tile_group(M.maxlen, tile_nnz<float>());
+    M.tile_group64 = tile_group(M.maxlen, tile_nnz<double>());
 }
 
 __global__ void omega_over_diag_kernel(int64_t n, double omega, const double *__restrict__ d,

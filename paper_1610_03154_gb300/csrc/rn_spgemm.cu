@@ -412,37 +412,42 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
 // one-entry rows get W = 0.
 constexpr int kEpThreads = 256;
 
-template <int G>
+// TV: the value type of A, X, W, Y and of the projection's Bc and row scales
+// (double; float for the mixed-precision sweeps, where the row scales are
+// formed in FP64 once per minimisation and rounded).  Per-thread parts of the
+// Frobenius product accumulate in TV and join the FP64 grid reduction.
+template <int G, typename TV>
 __global__ void __launch_bounds__(kEpThreads, 4)
 energy_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
-                      const double *__restrict__ aval, const int32_t *__restrict__ nrp,
-                      const int32_t *__restrict__ ncol, const double *__restrict__ X, double *__restrict__ W,
-                      const int32_t *__restrict__ rowtype, const double *__restrict__ Bc,
-                      const double *__restrict__ rs2v, double scale, const double *__restrict__ Y, Fin fin) {
+                      const TV *__restrict__ aval, const int32_t *__restrict__ nrp,
+                      const int32_t *__restrict__ ncol, const TV *__restrict__ X, TV *__restrict__ W,
+                      const int32_t *__restrict__ rowtype, const TV *__restrict__ Bc,
+                      const TV *__restrict__ rs2v, TV scale, const TV *__restrict__ Y, Fin fin) {
     __shared__ double s_red[32];
     constexpr int GPB = kEpThreads / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned mask = group_mask<G>();
-    double dot_acc[1] = {0.0};
+    TV dot_t = TV(0);
     for (int32_t i0 = blockIdx.x * GPB; i0 < n; i0 += gridDim.x * GPB) {
         const int32_t i = i0 + g;
         if (i >= n) continue;  // whole group leaves together
         const int32_t cs = nrp[i], ce = nrp[i + 1];
         if (rowtype[i] != 0 || ce - cs == 1) {  // fixed rows; one-entry rows: constraint space {0}
-            for (int32_t q = cs + lane; q < ce; q += G) W[q] = 0.0;
+            for (int32_t q = cs + lane; q < ce; q += G) W[q] = TV(0);
             continue;
         }
         const int32_t as = arp[i], ae = arp[i + 1];
-        const double rs2 = rs2v[i];
-        double s1 = 0.0, acc_first = 0.0;
+        const TV rs2 = rs2v[i];
+        TV s1 = TV(0);
+        TV acc_first = TV(0);
         for (int32_t q0 = cs; q0 < ce; q0 += G) {
             const int32_t q = q0 + lane;
             const bool active = q < ce;
             const int32_t j = active ? ncol[q] : INT32_MAX;
-            double acc = 0.0;
+            TV acc = TV(0);
             for (int32_t e = as; e < ae; e++) {
                 const int32_t k = acol[e];
-                const double a = aval[e];
+                const TV a = aval[e];
                 const int32_t ks = nrp[k], ke = nrp[k + 1];
                 if (active) {
                     for (int32_t f = ks; f < ke; f++) {
@@ -460,15 +465,130 @@ energy_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t 
                 else W[q] = acc;
             }
         }
-        s1 = group_sum<G>(s1, mask);
-        const double c = s1 * rs2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s1 += __shfl_xor_sync(mask, s1, o, G);
+        const TV c = s1 * rs2;
         for (int32_t q = cs + lane; q < ce; q += G) {
-            const double v = (q - cs < G) ? acc_first : W[q];  // each lane re-reads only what it wrote
-            const double w = scale * (v - c * Bc[ncol[q]]);
+            const TV v = (q - cs < G) ? acc_first : W[q];  // each lane re-reads only what it wrote
+            const TV w = scale * (v - c * Bc[ncol[q]]);
             W[q] = w;
-            if (Y) dot_acc[0] = fma(Y[q], w, dot_acc[0]);
+            if (Y) dot_t = fma(Y[q], w, dot_t);
         }
     }
+    const double dot_acc[1] = {(double)dot_t};
+    grid_finish<kEpThreads, 1>(dot_acc, fin, s_red);
+}
+
+// ------------------------------------------------------------------ energy product on a precomputed map
+// The pattern N is fixed for a whole minimisation, and so is, for every entry
+// (i, j) of N and every a_ik of row i, whether j occurs in the sorted row N_k
+// and where.  ep_map_kernel records that position once (one byte: the offset
+// in N_k, kMapNone when absent; row-major per row i as [k position in A_i]
+// x [entry of N_i]); ep_mapped_kernel then forms Mask_N(A X) for every sweep
+// by direct gathers, in the same order (ascending k, one fma per term) as
+// energy_product_kernel, so its results are bit-identical.
+constexpr unsigned char kMapNone = 255;
+
+// map bytes of row i: |A_i| * |N_i| (0 for rows the operator zeroes); the
+// longest row of N goes to *maxlen (its offsets must fit a byte)
+__global__ void ep_map_sizes_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ nrp,
+                                    const int32_t *__restrict__ rowtype, int32_t *__restrict__ sz,
+                                    int32_t *__restrict__ maxlen) {
+    int32_t m = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t len = nrp[i + 1] - nrp[i];
+        const int64_t b = (rowtype[i] != 0 || len == 1) ? 0 : (int64_t)(arp[i + 1] - arp[i]) * len;
+        sz[i] = (int32_t)(b < (int64_t)(INT32_MAX / 4) ? b : (int64_t)(INT32_MAX / 4));
+        m = max(m, len);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxlen, m);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kEpThreads)
+ep_map_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
+              const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol, const int32_t *__restrict__ rowtype,
+              const int32_t *__restrict__ mbase, unsigned char *__restrict__ map) {
+    constexpr int GPB = kEpThreads / G;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    for (int32_t i0 = blockIdx.x * GPB; i0 < n; i0 += gridDim.x * GPB) {
+        const int32_t i = i0 + g;
+        if (i >= n) continue;
+        const int32_t cs = nrp[i], ce = nrp[i + 1], len = ce - cs;
+        if (rowtype[i] != 0 || len == 1) continue;  // rows the operator zeroes: no map needed
+        const int32_t as = arp[i], ae = arp[i + 1];
+        unsigned char *mrow = map + mbase[i];
+        for (int32_t q0 = cs; q0 < ce; q0 += G) {
+            const int32_t q = q0 + lane;
+            if (q >= ce) continue;
+            const int32_t j = ncol[q];
+            for (int32_t e = as; e < ae; e++) {
+                const int32_t k = acol[e];
+                const int32_t ks = nrp[k], ke = nrp[k + 1];
+                unsigned char pos = kMapNone;
+                for (int32_t f = ks; f < ke; f++) {
+                    const int32_t c = ncol[f];
+                    if (c >= j) {
+                        if (c == j) pos = (unsigned char)(f - ks);
+                        break;
+                    }
+                }
+                mrow[(int64_t)(e - as) * len + (q - cs)] = pos;
+            }
+        }
+    }
+}
+
+template <int G, typename TV>
+__global__ void __launch_bounds__(kEpThreads, 4)
+ep_mapped_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                 const TV *__restrict__ aval, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
+                 const int32_t *__restrict__ mbase, const unsigned char *__restrict__ map, const TV *__restrict__ X,
+                 TV *__restrict__ W, const int32_t *__restrict__ rowtype, const TV *__restrict__ Bc,
+                 const TV *__restrict__ rs2v, TV scale, const TV *__restrict__ Y, Fin fin) {
+    __shared__ double s_red[32];
+    constexpr int GPB = kEpThreads / G;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const unsigned mask = group_mask<G>();
+    TV dot_t = TV(0);
+    for (int32_t i0 = blockIdx.x * GPB; i0 < n; i0 += gridDim.x * GPB) {
+        const int32_t i = i0 + g;
+        if (i >= n) continue;  // whole group leaves together
+        const int32_t cs = nrp[i], ce = nrp[i + 1], len = ce - cs;
+        if (rowtype[i] != 0 || len == 1) {  // fixed rows; one-entry rows: constraint space {0}
+            for (int32_t q = cs + lane; q < ce; q += G) W[q] = TV(0);
+            continue;
+        }
+        const int32_t as = arp[i], ae = arp[i + 1];
+        const unsigned char *mrow = map + mbase[i];
+        const TV rs2 = rs2v[i];
+        TV s1 = TV(0), acc_first = TV(0);
+        for (int32_t q0 = cs; q0 < ce; q0 += G) {
+            const int32_t q = q0 + lane;
+            const bool active = q < ce;
+            TV acc = TV(0);
+            if (active) {
+                for (int32_t e = as; e < ae; e++) {
+                    const unsigned char pos = mrow[(int64_t)(e - as) * len + (q - cs)];
+                    if (pos != kMapNone) acc = fma(aval[e], X[nrp[acol[e]] + pos], acc);
+                }
+                s1 = fma(acc, Bc[ncol[q]], s1);
+                if (q0 == cs) acc_first = acc;
+                else W[q] = acc;
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s1 += __shfl_xor_sync(mask, s1, o, G);
+        const TV c = s1 * rs2;
+        for (int32_t q = cs + lane; q < ce; q += G) {
+            const TV v = (q - cs < G) ? acc_first : W[q];
+            const TV w = scale * (v - c * Bc[ncol[q]]);
+            W[q] = w;
+            if (Y) dot_t = fma(Y[q], w, dot_t);
+        }
+    }
+    const double dot_acc[1] = {(double)dot_t};
     grid_finish<kEpThreads, 1>(dot_acc, fin, s_red);
 }
 
@@ -525,24 +645,27 @@ static int pick_group(double avg_len) {
     return 32;
 }
 
-void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, int32_t nc,
-                         const double *X, double *W, const ProjArgs &pa, double scale, const double *Y,
-                         const Fin &fin, cudaStream_t s) {
+template <typename TV>
+void masked_product_proj(const CsrView &A, const TV *aval, const int32_t *nrowptr, const int32_t *ncol,
+                         int64_t nnzN, int32_t nc, const TV *X, TV *W, const ProjArgsT<TV> &pa, double scale,
+                         const TV *Y, const Fin &fin, cudaStream_t s) {
     if (A.n == 0) return;
     const int G = pick_group((double)nnzN / A.n);
-    const void *fn = G == 4 ? (const void *)energy_product_kernel<4>
-                   : G == 8 ? (const void *)energy_product_kernel<8>
-                   : G == 16 ? (const void *)energy_product_kernel<16> : (const void *)energy_product_kernel<32>;
+    const void *fn = G == 4 ? (const void *)energy_product_kernel<4, TV>
+                   : G == 8 ? (const void *)energy_product_kernel<8, TV>
+                   : G == 16 ? (const void *)energy_product_kernel<16, TV>
+                             : (const void *)energy_product_kernel<32, TV>;
     const int grid = grid_resident(fn, kEpThreads, 0, A.n, kEpThreads / G, kReduceBlocks);
     // algorithmic bytes of one energy-minimisation product: A once, the
     // pattern (row pointers + columns) once, X once, W written once, Y once
-    // when the Frobenius product is taken, row types and Bc once.
-    const double bytes = 12.0 * A.nnz + 4.0 * (A.n + 1) + 4.0 * A.n + 4.0 * nnzN + 8.0 * nnzN + 8.0 * nnzN +
-                         (Y ? 8.0 * nnzN : 0.0) + 8.0 * nc;
-#define RN_EP_CASE(GG)                                                                                           \
-    case GG:                                                                                                     \
-        RN_LAUNCH("energy_masked_product", bytes, s, energy_product_kernel<GG>, grid, kEpThreads, 0, A.n, A.rowptr, \
-                  A.col, A.val, nrowptr, ncol, X, W, pa.rowtype, pa.Bc, pa.rs2, scale, Y, fin);                  \
+    // when the Frobenius product is taken, row types, scales and Bc once.
+    const double vb = sizeof(TV);
+    const double bytes = (4.0 + vb) * A.nnz + 4.0 * (A.n + 1) + 4.0 * (A.n + 1) + 4.0 * A.n + 8.0 * A.n +
+                         4.0 * nnzN + 2.0 * vb * nnzN + (Y ? vb * nnzN : 0.0) + 8.0 * nc;
+#define RN_EP_CASE(GG)                                                                                            \
+    case GG:                                                                                                      \
+        RN_LAUNCH("energy_masked_product", bytes, s, (energy_product_kernel<GG, TV>), grid, kEpThreads, 0, A.n,    \
+                  A.rowptr, A.col, aval, nrowptr, ncol, X, W, pa.rowtype, pa.Bc, pa.rs2, (TV)scale, Y, fin);      \
         break;
     switch (G) {
         RN_EP_CASE(4)
@@ -553,5 +676,82 @@ void masked_product_proj(const CsrView &A, const int32_t *nrowptr, const int32_t
     }
 #undef RN_EP_CASE
 }
+bool ep_map_build(EpMap &m, const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN,
+                  const int32_t *rowtype, cudaStream_t s) {
+    m.ok = false;
+    if (A.n == 0) return false;
+    DVec<int32_t> sz((size_t)A.n, s), mx(1, s);
+    fill_i32(mx.p, 0, 1, s);
+    RN_LAUNCH("energy_map", 16.0 * A.n, s, ep_map_sizes_kernel, grid_for(A.n, 256), 256, 0, A.n, A.rowptr, nrowptr,
+              rowtype, sz.p, mx.p);
+    if (read_scalar(mx.p, s) >= (int32_t)kMapNone) return false;  // offsets must fit a byte
+    m.base.alloc((size_t)A.n + 1, s);
+    int64_t total = 0;
+    try {
+        total = scan_counts(sz.p, m.base.p, A.n, s);
+    } catch (const Error &) {
+        return false;  // larger than int32 offsets: the scanning product is used
+    }
+    m.map.alloc((size_t)std::max<int64_t>(total, 1), s);
+    m.G = pick_group((double)nnzN / A.n);
+#define RN_MAP_CASE(GG)                                                                                          \
+    case GG:                                                                                                     \
+        RN_LAUNCH("energy_map", 8.0 * A.nnz + (double)total, s, ep_map_kernel<GG>,                               \
+                  grid_resident(ep_map_kernel<GG>, kEpThreads, 0, A.n, kEpThreads / GG), kEpThreads, 0, A.n,     \
+                  A.rowptr, A.col, nrowptr, ncol, rowtype, m.base.p, m.map.p);                                   \
+        break;
+    switch (m.G) {
+        RN_MAP_CASE(4)
+        RN_MAP_CASE(8)
+        RN_MAP_CASE(16)
+        RN_MAP_CASE(32)
+        default: fail(RN_EINTERNAL, "bad group size");
+    }
+#undef RN_MAP_CASE
+    m.bytes = total;
+    m.ok = true;
+    return true;
+}
+
+template <typename TV>
+void masked_product_mapped(const EpMap &m, const CsrView &A, const TV *aval, const int32_t *nrowptr,
+                           const int32_t *ncol, int64_t nnzN, int32_t nc, const TV *X, TV *W, const ProjArgsT<TV> &pa,
+                           double scale, const TV *Y, const Fin &fin, cudaStream_t s) {
+    if (A.n == 0) return;
+    const double vb = sizeof(TV);
+    // algorithmic bytes: the map once, A's columns and values once, the row
+    // pointers of A and N, X gathered once, W written once, Y once, scales, Bc
+    const double bytes = (double)m.bytes + (4.0 + vb) * A.nnz + 8.0 * (A.n + 1) + 4.0 * A.n + 4.0 * A.n +
+                         vb * A.n + 4.0 * nnzN + 2.0 * vb * nnzN + (Y ? vb * nnzN : 0.0) + vb * nc;
+#define RN_MP_CASE(GG)                                                                                           \
+    case GG:                                                                                                     \
+        RN_LAUNCH("energy_masked_product", bytes, s, (ep_mapped_kernel<GG, TV>),                                 \
+                  grid_resident(ep_mapped_kernel<GG, TV>, kEpThreads, 0, A.n, kEpThreads / GG, kReduceBlocks),   \
+                  kEpThreads, 0, A.n, A.rowptr, A.col, aval, nrowptr, ncol, m.base.p, m.map.p, X, W, pa.rowtype, \
+                  pa.Bc, pa.rs2, (TV)scale, Y, fin);                                                             \
+        break;
+    switch (m.G) {
+        RN_MP_CASE(4)
+        RN_MP_CASE(8)
+        RN_MP_CASE(16)
+        RN_MP_CASE(32)
+        default: fail(RN_EINTERNAL, "bad group size");
+    }
+#undef RN_MP_CASE
+}
+template void masked_product_mapped<double>(const EpMap &, const CsrView &, const double *, const int32_t *,
+                                            const int32_t *, int64_t, int32_t, const double *, double *,
+                                            const ProjArgsT<double> &, double, const double *, const Fin &,
+                                            cudaStream_t);
+template void masked_product_mapped<float>(const EpMap &, const CsrView &, const float *, const int32_t *,
+                                           const int32_t *, int64_t, int32_t, const float *, float *,
+                                           const ProjArgsT<float> &, double, const float *, const Fin &, cudaStream_t);
+
+template void masked_product_proj<double>(const CsrView &, const double *, const int32_t *, const int32_t *, int64_t,
+                                          int32_t, const double *, double *, const ProjArgsT<double> &, double,
+                                          const double *, const Fin &, cudaStream_t);
+template void masked_product_proj<float>(const CsrView &, const float *, const int32_t *, const int32_t *, int64_t,
+                                         int32_t, const float *, float *, const ProjArgsT<float> &, double,
+                                         const float *, const Fin &, cudaStream_t);
 
 }  // namespace rn

@@ -245,6 +245,11 @@ PARAMS_CONVDIFF = dict(soc_theta=0.25, soc_theta_coarse=-1.0, degree=1, n_sweeps
                        symmetric=0, nu_pre=1, nu_post=1, outer=2, restart=30)
 
 
+PARAMS_VARCOEF = dict(soc_theta=0.25, soc_theta_coarse=0.1, degree=2, n_sweeps=4, method=0, prefilter=0.0,
+                      postfilter=0.0, max_coarse=64, max_levels=25, b_sweeps=4, omega=2.0 / 3.0, seed=12345,
+                      symmetric=1, nu_pre=1, nu_post=1, outer=1)
+
+
 def poisson_problem(m: int = 64, seed: int = 1) -> Problem:
     A = poisson5(m)
     n = A.n_rows

@@ -84,6 +84,7 @@ def _load():
     L.rn_kernel_launches.argtypes = []
     L.rn_kernel_launches.restype = C.c_int64
     L.rn_time_op.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, P(C.c_double), P(C.c_double), C.c_char_p]
+    L.rn_adjoint_grad.argtypes = [P(rn_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     L.rn_last_error.restype = C.c_char_p
     L.rn_status_string.argtypes = [C.c_int]
     L.rn_status_string.restype = C.c_char_p
@@ -108,6 +109,7 @@ rn_last_error = lib.rn_last_error
 rn_status_string = lib.rn_status_string
 rn_kernel_launches = lib.rn_kernel_launches
 rn_time_op = lib.rn_time_op
+rn_adjoint_grad = lib.rn_adjoint_grad
 rn_energy_min = lib.rn_energy_min
 rn_energy_min_noalloc = lib.rn_energy_min_noalloc
 
@@ -129,6 +131,13 @@ def energy_min(A_rowptr, A_col, A_val, N_rowptr, N_col, n_c, rowtype, Bc, P, swe
     N = rn_csr(n, int(n_c), int(N_col.shape[0]), _ptr(N_rowptr), _ptr(N_col) if N_col.shape[0] else None, None)
     _check(rn_energy_min(C.byref(A), C.byref(N), _ptr(rowtype), _ptr(Bc), _ptr(P), sweeps, method, precond,
                          stream), "rn_energy_min")
+
+
+def adjoint_grad(rowptr, col, lam, x, grad, n_cols=None, stream=None):
+    """grad[e] = -lam[i] * x[col[e]] on the CSR pattern (rn_adjoint_grad); device tensors, grad written."""
+    n = int(rowptr.shape[0]) - 1
+    A = rn_csr(n, int(n if n_cols is None else n_cols), int(col.shape[0]), _ptr(rowptr), _ptr(col), None)
+    _check(rn_adjoint_grad(C.byref(A), _ptr(lam), _ptr(x), _ptr(grad), stream), "rn_adjoint_grad")
 
 
 class RNError(RuntimeError):

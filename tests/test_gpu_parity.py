@@ -436,3 +436,30 @@ def _solve_capped(rn, torch_dev, h, pr, maxit):
     x = torch.zeros_like(b)
     info = h.solve(b, x, rtol=1e-8, maxit=maxit, raise_on_notconv=False)
     return x.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("case", ["poisson64", "aniso96", "aniso255"])
+def test_mixed_precision_setup_error_against_fp64(rn, torch_dev, oracle, case):
+    """Mixed precision runs the CG energy-minimisation sweeps in FP32 (the row
+    projection and the CG scalars stay FP64).  Level 0's pattern comes from
+    FP64 steps before the sweeps; after them P differs from the FP64 oracle
+    by FP32 rounding only, and still reproduces B on the candidates."""
+    pr = CASES[case]()
+    hm = gpu_hierarchy(rn, torch_dev, pr, precision=rn.RN_MIXED)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, Bhat=pr.Bhat, **pr.params)
+    Pm = as_csr(hm.export_csr(0, 4))
+    Po = oh.levels[0].P.tocsr()
+    hm.close()
+    assert Pm.shape == Po.shape
+    same = (Pm.indptr.shape == Po.indptr.shape and np.array_equal(Pm.indptr, Po.indptr)
+            and np.array_equal(Pm.indices, Po.indices))
+    if pr.params.get("postfilter", 0.0) <= 0.0:
+        assert same  # no value-dependent filtering after the sweeps
+    if same:
+        err = np.max(np.abs(Pm.data - Po.data)) / np.max(np.abs(Po.data))
+        assert err < 1e-4, err
+    else:  # the post-filter kept or dropped a near-threshold entry differently
+        assert abs(Pm.nnz - Po.nnz) <= 1e-4 * Po.nnz
+    Bc, B = oh.levels[0].Bc, oh.levels[0].B  # the smoothed candidates P must reproduce
+    resid = np.max(np.abs(Pm @ Bc - B))
+    assert resid < 1e-5 * np.max(np.abs(B)), resid

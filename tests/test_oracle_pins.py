@@ -610,3 +610,37 @@ def test_energy_monotone_on_every_level(oracle):
     for L in h.levels[:-1]:
         P, tr = oracle.energy_min_cg(L.A, L.T, L.rowtype, L.Bc, 6)
         assert np.all(np.diff(tr) <= 1e-12 * abs(tr[0])), tr
+
+
+# --------------------------------------------------------------------------- adjoint reference
+def test_adjoint_reference_gradient_matches_central_differences():
+    """The hand-derived adjoint gradient of the FV solve (NEXT-2 workload)
+    against central differences of the loss on a tiny grid, with direct
+    solves; pins the chain rule through the harmonic-mean faces and the
+    boundary terms (a dropped term or a wrong sign moves it by O(1))."""
+    from oracle import adjoint_ref as ar
+    m = 6
+    th = PR.gaussian_field(m, 11)
+    th_obs = PR.gaussian_field(m, 12)
+    f = np.full(m * m, 1.0 / (m * m))
+    u_obs = __import__("scipy.sparse.linalg", fromlist=["spsolve"]).spsolve(ar.operator(m, th_obs).tocsc(), f)
+    L, g, _ = ar.loss_and_grad(m, th, f, u_obs)
+    h = 1e-6
+    fd = np.empty(m * m)
+    for c in range(m * m):
+        tp, tm = th.copy(), th.copy()
+        tp[c] += h
+        tm[c] -= h
+        fd[c] = (ar.loss(m, tp, f, u_obs) - ar.loss(m, tm, f, u_obs)) / (2 * h)
+    assert np.max(np.abs(g - fd)) <= 1e-6 * np.max(np.abs(fd))
+    assert L > 0
+
+
+def test_adjoint_reference_operator_matches_generator():
+    """The reference's face-by-face assembly equals the input generator's."""
+    from oracle import adjoint_ref as ar
+    m = 9
+    th = PR.gaussian_field(m, 3)
+    A, f = PR.varcoef_fv(m, th)
+    B = ar.operator(m, th)
+    assert np.max(np.abs((A.to_scipy() - B).toarray())) < 1e-13
