@@ -137,6 +137,38 @@ rn_status rn_setup(const rn_csr *A, const double *B, const double *Bhat, int k, 
 rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int location, double rtol, int maxit,
                    rn_solve_info *info);
 
+/* Solve A X = B for s right-hand sides at once (B and X: n x s, row-major;
+ * X holds the initial guesses on entry and the solutions on exit).  The
+ * stationary iteration X <- X + M(B - A X) applies the V-cycle to all s
+ * columns together: every operator row is read once per operation for all
+ * columns (SpMM in place of SpMV).  The cycle runs in the hierarchy's
+ * precision (FP32 when mixed); residuals are FP64.  It stops when every
+ * column satisfies ||b_c - A x_c|| < rtol ||b_c|| (a zero column when
+ * ||b_c - A x_c|| < rtol).  info (may be NULL): iterations, the largest
+ * column's relative residual, its average convergence factor, wall time.
+ * Returns RN_EINVAL for s outside [1, 2048] or null arguments, RN_ENOTCONV
+ * when a column is above the tolerance after maxit iterations. */
+rn_status rn_solve_multi(rn_hierarchy *h, const double *B, double *X, int s, int location, double rtol, int maxit,
+                         rn_solve_info *info);
+
+/* Many independent problems (the paper has no batched form; a deployment
+ * variant).  rn_setup_batched builds hierarchy i for (A[i], B[i], Bhat[i]),
+ * all device data, k = 1, with the same params, whose stream must be NULL:
+ * every problem gets a stream of its own and host threads (at most `threads`;
+ * 0: one per hardware thread, at most 16) drive the setups, so they overlap
+ * on the GPU.  Bhat may be NULL when p->symmetric.  out[i] receives problem
+ * i's hierarchy; on any error every hierarchy is freed, out[] is all NULL and
+ * the status of the first failing problem in index order is returned (its
+ * message, prefixed with its index, is the last error).
+ * rn_solve_batched solves A_i x_i = b_i (device vectors, x_i in/out) for all
+ * i the same way, each on its hierarchy's stream; info (may be NULL) gets one
+ * record per problem.  Results are those of rn_setup / rn_solve on each
+ * problem alone. */
+rn_status rn_setup_batched(int count, const rn_csr *A, const double *const *B, const double *const *Bhat,
+                           const rn_params *p, int threads, rn_hierarchy **out);
+rn_status rn_solve_batched(int count, rn_hierarchy *const *h, const double *const *b, double *const *x, double rtol,
+                           int maxit, int threads, rn_solve_info *info);
+
 /* Apply one V-cycle to b with zero initial guess: x = M^{-1} b (device
  * pointers, FP64, level-0 size).  Used to check the cycle itself. */
 rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x);

@@ -86,7 +86,8 @@ class AMGSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, values, b, rowptr, col, params, rtol, maxit, symmetric, tmap):
         B = torch.ones(rowptr.shape[0] - 1, dtype=torch.float64, device=values.device)
-        h = rn.Hierarchy(rowptr, col, values.detach().contiguous(), B, params=params)
+        Bh = None if params.symmetric else B  # candidates for A^T when R is built from A^T
+        h = rn.Hierarchy(rowptr, col, values.detach().contiguous(), B, Bh, params=params)
         x = torch.zeros_like(b)
         h.solve(b.detach().contiguous(), x, rtol=rtol, maxit=maxit)
         ctx.h = h
@@ -104,7 +105,8 @@ class AMGSolve(torch.autograd.Function):
         else:  # a hierarchy for A^T
             rpt, colt, perm = ctx.tmap
             B = torch.ones_like(x)
-            ht = rn.Hierarchy(rpt, colt, values.detach()[perm].contiguous(), B, params=ctx.params)
+            ht = rn.Hierarchy(rpt, colt, values.detach()[perm].contiguous(), B, None if ctx.params.symmetric else B,
+                              params=ctx.params)
             ht.solve(gx.contiguous(), lam, rtol=ctx.rtol, maxit=ctx.maxit)
             ht.close()
         ctx.h.close()

@@ -2,6 +2,10 @@
 // Each entry point converts internal errors (rn::Error) into status codes and
 // records a thread-local message; nothing aborts.
 #include <cstring>
+#include <string>
+#include <vector>
+#include <atomic>
+#include <thread>
 
 #include "rn_hier.cuh"
 
@@ -147,6 +151,76 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
     RN_API_END
 }
 
+namespace {
+// Run work(i) for i < count on up to `threads` host threads (0: one per
+// hardware thread, at most 16); each item's status and error message are
+// kept; returns the first non-OK status in index order and makes its message
+// this thread's last error.
+template <typename F>
+rn_status run_batch(int count, int threads, F &&work) {
+    std::vector<rn_status> st((size_t)count, RN_OK);
+    std::vector<std::string> msg((size_t)count);
+    int nt = threads > 0 ? threads : (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+    nt = std::max(1, std::min(nt, count));
+    std::atomic<int> next{0};
+    auto body = [&]() {
+        for (int i = next++; i < count; i = next++) {
+            st[i] = work(i);
+            if (st[i] != RN_OK) msg[i] = rn_last_error();
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; t++) pool.emplace_back(body);
+    body();
+    for (auto &t : pool) t.join();
+    for (int i = 0; i < count; i++)
+        if (st[i] != RN_OK) {
+            rn::set_last_error(rn::fmt("problem %d: %s", i, msg[i].c_str()));
+            return st[i];
+        }
+    return RN_OK;
+}
+}  // namespace
+
+extern "C" rn_status rn_setup_batched(int count, const rn_csr *A, const double *const *B, const double *const *Bhat,
+                                      const rn_params *p, int threads, rn_hierarchy **out) {
+    if (!out || count < 0) {
+        rn::set_last_error("null argument or negative count");
+        return RN_EINVAL;
+    }
+    for (int i = 0; i < count; i++) out[i] = nullptr;
+    if (count == 0) return RN_OK;
+    if (!A || !B || !p) {
+        rn::set_last_error("null argument");
+        return RN_EINVAL;
+    }
+    if (p->stream) {
+        rn::set_last_error("batched setup: params.stream must be NULL (every problem gets its own stream)");
+        return RN_EINVAL;
+    }
+    const rn_status st = run_batch(count, threads, [&](int i) {
+        return rn_setup(&A[i], B[i], Bhat ? Bhat[i] : nullptr, 1, RN_DEVICE, p, &out[i]);
+    });
+    if (st != RN_OK) {
+        for (int i = 0; i < count; i++) {
+            rn_free(out[i]);
+            out[i] = nullptr;
+        }
+    }
+    return st;
+}
+
+extern "C" rn_status rn_solve_batched(int count, rn_hierarchy *const *h, const double *const *b, double *const *x,
+                                      double rtol, int maxit, int threads, rn_solve_info *info) {
+    if (count < 0 || (count > 0 && (!h || !b || !x))) {
+        rn::set_last_error("null argument or negative count");
+        return RN_EINVAL;
+    }
+    return run_batch(count, threads, [&](int i) {
+        return rn_solve(h[i], b[i], x[i], RN_DEVICE, rtol, maxit, info ? &info[i] : nullptr);
+    });
+}
+
 extern "C" rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int location, double rtol, int maxit,
                               rn_solve_info *info) {
     RN_API_BEGIN
@@ -171,6 +245,34 @@ extern "C" rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int l
     if (info) info->solve_ms = rn::now_ms() - t0;
     if (st == RN_ENOTCONV) rn::set_last_error("solve did not reach the tolerance within maxit");
     return st;
+    RN_API_END
+}
+
+extern "C" rn_status rn_solve_multi(rn_hierarchy *h, const double *B, double *X, int s, int location, double rtol,
+                                    int maxit, rn_solve_info *info) {
+    RN_API_BEGIN
+    using rn::fail;
+    if (!h || !B || !X) fail(RN_EINVAL, "null argument");
+    if (s < 1 || s > 2048) fail(RN_EINVAL, "s must be in [1, 2048]");
+    if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
+    if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
+    cudaStream_t st = h->s;
+    const int64_t tot = (int64_t)h->lev[0]->A.n * s;
+    const double t0 = rn::now_ms();
+    rn_status r;
+    if (location == RN_HOST) {
+        rn::DVec<double> bd(tot, st), xd(tot, st);
+        rn::h2d(bd.p, B, tot, st);
+        rn::h2d(xd.p, X, tot, st);
+        r = rn::solve_multi(*h, bd.p, xd.p, s, rtol, maxit, info);
+        rn::d2h(X, xd.p, tot, st);
+    } else {
+        r = rn::solve_multi(*h, B, X, s, rtol, maxit, info);
+    }
+    RN_CUDA_CHECK(cudaStreamSynchronize(st));
+    if (info) info->solve_ms = rn::now_ms() - t0;
+    if (r == RN_ENOTCONV) rn::set_last_error("a column did not reach the tolerance within maxit");
+    return r;
     RN_API_END
 }
 

@@ -116,6 +116,9 @@ rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int ma
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out);
 void cycle_checked(rn_hierarchy &h, const double *rhs, double *out);  // + staging-error check
 void time_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, std::string &name);
+// many right-hand sides (rn_multi.cu)
+rn_status solve_multi(rn_hierarchy &h, const double *B, double *X, int ns, double rtol, int maxit,
+                      rn_solve_info *info);
 template <typename T>
 T *pre_smoothed(rn_level &L, int nu_pre);
 }  // namespace rn

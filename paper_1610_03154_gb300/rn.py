@@ -68,6 +68,12 @@ def _load():
     L.rn_setup.argtypes = [P(rn_csr), C.c_void_p, C.c_void_p, C.c_int, C.c_int, P(rn_params), P(C.c_void_p)]
     L.rn_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, P(rn_solve_info)]
     L.rn_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.rn_solve_multi.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
+                                 P(rn_solve_info)]
+    L.rn_setup_batched.argtypes = [C.c_int, P(rn_csr), P(C.c_void_p), P(C.c_void_p), P(rn_params), C.c_int,
+                                   P(C.c_void_p)]
+    L.rn_solve_batched.argtypes = [C.c_int, P(C.c_void_p), P(C.c_void_p), P(C.c_void_p), C.c_double, C.c_int,
+                                   C.c_int, P(rn_solve_info)]
     L.rn_free.argtypes = [C.c_void_p]
     L.rn_free.restype = None
     L.rn_energy_min.argtypes = [P(rn_csr), P(rn_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
@@ -98,6 +104,9 @@ rn_default_params = lib.rn_default_params
 rn_setup = lib.rn_setup
 rn_solve = lib.rn_solve
 rn_vcycle = lib.rn_vcycle
+rn_solve_multi = lib.rn_solve_multi
+rn_setup_batched = lib.rn_setup_batched
+rn_solve_batched = lib.rn_solve_batched
 rn_free = lib.rn_free
 rn_hierarchy_stats = lib.rn_hierarchy_stats
 rn_export_csr = lib.rn_export_csr
@@ -138,6 +147,48 @@ def adjoint_grad(rowptr, col, lam, x, grad, n_cols=None, stream=None):
     n = int(rowptr.shape[0]) - 1
     A = rn_csr(n, int(n if n_cols is None else n_cols), int(col.shape[0]), _ptr(rowptr), _ptr(col), None)
     _check(rn_adjoint_grad(C.byref(A), _ptr(lam), _ptr(x), _ptr(grad), stream), "rn_adjoint_grad")
+
+
+def setup_batched(problems, params=None, threads=0):
+    """Hierarchies for many problems at once (rn_setup_batched).  problems: a
+    list of (rowptr, col, val, B) or (rowptr, col, val, B, Bhat) device
+    tensors; returns a list of Hierarchy."""
+    if params is None:
+        params = default_params()
+    k = len(problems)
+    A = (rn_csr * k)()
+    Bp = (C.c_void_p * k)()
+    Bh = (C.c_void_p * k)()
+    for i, pr in enumerate(problems):
+        rp, ci, va, B = pr[:4]
+        n = int(rp.shape[0]) - 1
+        A[i] = rn_csr(n, n, int(ci.shape[0]), _ptr(rp), _ptr(ci), _ptr(va))
+        Bp[i] = _ptr(B)
+        Bh[i] = _ptr(pr[4]) if len(pr) > 4 and pr[4] is not None else None
+    out = (C.c_void_p * k)()
+    _check(rn_setup_batched(k, A, Bp, Bh, C.byref(params), threads, out), "rn_setup_batched")
+    hs = []
+    for i in range(k):
+        h = Hierarchy.__new__(Hierarchy)
+        h.n = int(problems[i][0].shape[0]) - 1
+        h.params = params
+        h._keep = None
+        h._h = C.c_void_p(out[i])
+        hs.append(h)
+    return hs
+
+
+def solve_batched(hierarchies, bs, xs, rtol=1e-8, maxit=500, threads=0, raise_on_notconv=True):
+    """Solve every (hierarchy, b, x) at once (rn_solve_batched); x updated in place."""
+    k = len(hierarchies)
+    H = (C.c_void_p * k)(*[h._h.value for h in hierarchies])
+    Bv = (C.c_void_p * k)(*[_ptr(b) for b in bs])
+    Xv = (C.c_void_p * k)(*[_ptr(x) for x in xs])
+    infos = (rn_solve_info * k)()
+    st = rn_solve_batched(k, H, Bv, Xv, rtol, maxit, threads, infos)
+    if st != RN_OK and (st != RN_ENOTCONV or raise_on_notconv):
+        raise RNError(st, "rn_solve_batched")
+    return [dict(iters=i.iters, rel_res=i.rel_res, rho=i.rho, solve_ms=i.solve_ms, status=i.status) for i in infos]
 
 
 class RNError(RuntimeError):
@@ -232,6 +283,17 @@ class Hierarchy:
         st = rn_solve(self._h, _ptr(b), _ptr(x), RN_HOST if host else RN_DEVICE, rtol, maxit, C.byref(info))
         if st != RN_OK and (st != RN_ENOTCONV or raise_on_notconv):
             raise RNError(st, "rn_solve")
+        return dict(iters=info.iters, rel_res=info.rel_res, rho=info.rho, solve_ms=info.solve_ms, status=st)
+
+    def solve_multi(self, B, X, rtol=1e-8, maxit=500, raise_on_notconv=True):
+        """Solve for the s columns of B (n x s, row-major) at once; X (n x s) is updated in place."""
+        host = _is_host(B)
+        s = int(B.shape[1])
+        info = rn_solve_info()
+        st = rn_solve_multi(self._h, _ptr(B), _ptr(X), s, RN_HOST if host else RN_DEVICE, rtol, maxit,
+                            C.byref(info))
+        if st != RN_OK and (st != RN_ENOTCONV or raise_on_notconv):
+            raise RNError(st, "rn_solve_multi")
         return dict(iters=info.iters, rel_res=info.rel_res, rho=info.rho, solve_ms=info.solve_ms, status=st)
 
     def vcycle(self, b, x):
