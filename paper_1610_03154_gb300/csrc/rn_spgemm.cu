@@ -74,16 +74,26 @@ small_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
     constexpr int ST = kSmallProd + 1;  // padded stride: groups of one warp start in different banks
     __shared__ long long s_k[GPB * ST];
     __shared__ double s_v[GPB * ST];
+    // flattened listing (G >= 8, long rows B_k): the contributing entries'
+    // a_ik, B_k starts and list offsets
+    constexpr bool FLAT = G >= 8;
+    constexpr int ET = FLAT ? kSmallProd : 1;
+    __shared__ double s_ea[GPB * ET];
+    __shared__ int32_t s_eb[GPB * ET];
+    __shared__ int32_t s_eo[GPB * ET];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned mask = group_mask<G>();
     long long *K = s_k + g * ST;  // (column << 8) | list position
     double *V = s_v + g * ST;     // products in list order
+    double *Ea = s_ea + g * ET;
+    int32_t *Eb = s_eb + g * ET, *Eo = s_eo + g * ET;
     for (int32_t r0 = blockIdx.x * GPB; r0 < nrows; r0 += gridDim.x * GPB) {
         if (r0 + g >= nrows) continue;  // the whole group leaves together
         const int32_t i = rows[r0 + g];
         const int32_t as = arp[i], ae = arp[i + 1];
-        // 1. the products in (k, position in B_k) order
-        int32_t m = 0;
+        // 1a. the row's entries a_ik with a non-empty B_k, in order, and where
+        //     their products start in the list ((k, position in B_k) order)
+        int32_t m = 0, ne = 0;
         for (int32_t e0 = as; e0 < ae; e0 += G) {
             const int32_t e = e0 + lane;
             int32_t b0 = 0, c = 0;
@@ -94,18 +104,48 @@ small_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
                 b0 = brp[k];
                 c = brp[k + 1] - b0;
             }
-            int32_t incl = c;
+            int32_t incl = c, ninc = c > 0 ? 1 : 0;
 #pragma unroll
             for (int o = 1; o < G; o <<= 1) {
                 const int32_t t = __shfl_up_sync(mask, incl, o, G);
-                if (lane >= o) incl += t;
+                const int32_t u = __shfl_up_sync(mask, ninc, o, G);
+                if (lane >= o) {
+                    incl += t;
+                    ninc += u;
+                }
             }
-            const int32_t off = m + incl - c;
-            for (int32_t f = 0; f < c; f++) {
-                K[off + f] = ((long long)bcol[b0 + f] << 8) | (long long)(off + f);
-                V[off + f] = __dmul_rn(a, bval[b0 + f]);
+            if (FLAT) {
+                if (c > 0) {
+                    const int32_t slot = ne + ninc - 1;
+                    Ea[slot] = a;
+                    Eb[slot] = b0;
+                    Eo[slot] = m + incl - c;
+                }
+            } else {  // short rows B_k: each lane lists its entry's products
+                const int32_t off = m + incl - c;
+                for (int32_t f = 0; f < c; f++) {
+                    K[off + f] = ((long long)bcol[b0 + f] << 8) | (long long)(off + f);
+                    V[off + f] = __dmul_rn(a, bval[b0 + f]);
+                }
             }
             m += __shfl_sync(mask, incl, G - 1, G);
+            ne += __shfl_sync(mask, ninc, G - 1, G);
+        }
+        __syncwarp(mask);
+        // 1b. every lane takes list positions: the entry by binary search over
+        //     the offsets, then one product each (independent loads)
+        if (FLAT) {
+            for (int t = lane; t < m; t += G) {
+                int lo = 0, hi = ne - 1;
+                while (lo < hi) {  // last slot with offset <= t
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (Eo[mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int32_t f = Eb[lo] + (t - Eo[lo]);
+                K[t] = ((long long)bcol[f] << 8) | (long long)t;
+                V[t] = __dmul_rn(Ea[lo], bval[f]);
+            }
         }
         // 2. bitonic sort of the keys (padded to a power of two): each column's
         //    products become one run, in list order
