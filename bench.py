@@ -48,6 +48,29 @@ METRIC = "setup+solve s to 1e-8 rel. residual (FP64 vs mixed/batched); HBM GB/s 
 WORKLOAD_NE = 1024
 
 
+def load_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    (profiles/roofline_traffic.txt, JSON), or None when there is none or when a
+    source file it was captured from has changed since."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None, None
+    ent = rec.get(kernel)
+    if not ent:
+        return None, None
+    for f, md5 in ent.get("sources_md5", {}).items():
+        try:
+            if hashlib.md5(open(os.path.join(ROOT, f), "rb").read()).hexdigest() != md5:
+                return None, "stale: " + f + " changed since the capture"
+        except OSError:
+            return None, "missing " + f
+    return float(ent["dram_bytes_per_launch"]), ent.get("profile")
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -312,8 +335,9 @@ def main():
     name = max(bw, key=lambda k: bw[k]["us"])
     st = bw[name]
     achieved = st["bytes"] / (st["us"] * 1e-6) / 1e9
+    traffic, traffic_src = load_traffic(name)
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic, "traffic_source": traffic_src,
                 "avg_launch_us": st["us"], "algorithmic_bytes": st["bytes"], "launches_per_step": iters,
                 "share_of_step": st["us"] * 1e-6 * iters / step_s,
                 "rule": "longest level-0 launch of the outer iteration (each runs once per iteration), timed "

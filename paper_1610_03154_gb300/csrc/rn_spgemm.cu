@@ -156,7 +156,8 @@ small_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
         for (int k = 2; k <= P; k <<= 1) {
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
                 for (int t = lane; t < (P >> 1); t += G) {
-                    const int lo = (t / jj) * 2 * jj + (t % jj), hi = lo + jj;
+                    // the t-th pair: a zero bit inserted at jj (a power of two)
+                    const int lo = ((t & ~(jj - 1)) << 1) | (t & (jj - 1)), hi = lo + jj;
                     const long long x = K[lo], y = K[hi];
                     if ((x > y) == ((lo & k) == 0)) {
                         K[lo] = y;
