@@ -421,20 +421,36 @@ __global__ void gm_start_kernel(double *sc, int32_t *fl, double *g) {
     g[0] = beta;
 }
 
-__global__ void gm_scale_kernel(int64_t nz, double *__restrict__ v, const double *__restrict__ den,
+// TV: the sweeps' value type (double; float in mixed precision, the Arnoldi
+// scalars staying FP64)
+template <typename TV>
+__global__ void gm_scale_kernel(int64_t nz, TV *__restrict__ v, const double *__restrict__ den,
                                 const int32_t *__restrict__ fl) {
     if (fl[0]) return;
-    const double d = *den;
+    const TV d = (TV)*den;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x)
         v[q] = v[q] / d;
 }
 
-__global__ void gm_axpy_kernel(int64_t nz, double *__restrict__ w, const double *__restrict__ v,
+template <typename TV>
+__global__ void gm_axpy_kernel(int64_t nz, TV *__restrict__ w, const TV *__restrict__ v,
                                const double *__restrict__ h, const int32_t *__restrict__ fl) {
     if (fl[0]) return;
-    const double c = *h;
+    const TV c = (TV)*h;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x)
         w[q] = w[q] - c * v[q];
+}
+
+// <x, y> of two TV arrays: per-thread sums in TV, grid reduction in FP64
+template <typename TV>
+__global__ void __launch_bounds__(kT) gm_dot_kernel(int64_t nz, const TV *__restrict__ x, const TV *__restrict__ y,
+                                                    Fin fin) {
+    __shared__ double sm[32];
+    TV acc = TV(0);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(x[q], y[q], acc);
+    const double v[1] = {(double)acc};
+    grid_finish<kT, 1>(v, fin, sm);
 }
 
 // Givens update of Hessenberg column j; H row-major (m+1) x m
@@ -474,12 +490,13 @@ __global__ void gm_backsolve_kernel(int m, const double *H, const double *g, dou
     for (int i = k; i < m; i++) y[i] = 0.0;
 }
 
-__global__ void gm_combine_kernel(int64_t nz, int m, double *__restrict__ P, const double *__restrict__ V,
+template <typename TV>
+__global__ void gm_combine_kernel(int64_t nz, int m, TV *__restrict__ P, const TV *__restrict__ V,
                                   const double *__restrict__ y, const int32_t *__restrict__ fl) {
     const int k = fl[1];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x) {
-        double p = P[q];
-        for (int j = 0; j < k; j++) p = p + y[j] * V[(int64_t)j * nz + q];
+        TV p = P[q];
+        for (int j = 0; j < k; j++) p = p + (TV)y[j] * V[(int64_t)j * nz + q];
         P[q] = p;
     }
 }
@@ -736,13 +753,17 @@ void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X
     else energy_min_cg_t<double>(c, A, N, X, rowtype, Bc, c_dinv, sweeps);
 }
 
-// GMRES energy minimisation (m Arnoldi steps, modified Gram-Schmidt).
-void energy_min_gmres(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
-                      const double *Bc, int m) {
+// GMRES energy minimisation (m Arnoldi steps, modified Gram-Schmidt), sweeps
+// in TV (double; float in mixed precision: A, the basis and the projection's
+// scales in FP32, the Hessenberg matrix, rotations and dot products FP64).
+template <typename TV>
+static void energy_min_gmres_t(const EmCtx &c, const CsrView &A, const Pattern &N, double *X64,
+                               const int32_t *rowtype, const double *Bc, int m) {
     if (m <= 0) return;
+    constexpr bool f32 = sizeof(TV) == 4;
     cudaStream_t s = c.s;
     const int64_t nz = N.nnz;
-    DVec<double> V((size_t)(m + 1) * (nz > 0 ? nz : 1), s), W(nz > 0 ? nz : 1, s);
+    DVec<TV> V((size_t)(m + 1) * (nz > 0 ? nz : 1), s), W(nz > 0 ? nz : 1, s), Xv, Av, Bcv, Rsv;
     DVec<double> Hm((size_t)(m + 1) * m + 4 * (m + 1), s);
     fill_f64(Hm.p, 0.0, (int64_t)Hm.n, s);
     double *H = Hm.p, *cs = H + (m + 1) * m, *sn = cs + (m + 1), *g = sn + (m + 1), *y = g + (m + 1);
@@ -751,39 +772,76 @@ void energy_min_gmres(const EmCtx &c, const CsrView &A, const Pattern &N, double
     DVec<double> Sv(c.rs2 ? 0 : N.n, s);
     double *rs2 = c.rs2 ? c.rs2 : Sv.p;
     proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);
-    ProjArgs pa{rowtype, Bc, rs2};
+    ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
+    TV *X;
+    const TV *aval;
+    if constexpr (f32) {
+        Xv.alloc(nz > 0 ? nz : 1, s);
+        Av.alloc(A.nnz, s);
+        Bcv.alloc(N.nc, s);
+        Rsv.alloc(N.n, s);
+        to_float(X64, Xv.p, nz, s);
+        to_float(A.val, Av.p, A.nnz, s);
+        to_float(Bc, Bcv.p, N.nc, s);
+        to_float(rs2, Rsv.p, N.n, s);
+        X = Xv.p;
+        aval = Av.p;
+        pa.Bc = Bcv.p;
+        pa.rs2 = Rsv.p;
+    } else {
+        X = X64;
+        aval = A.val;
+        pa.Bc = Bc;
+        pa.rs2 = rs2;
+    }
     const int eg = grid_for(nz, 1024);
-    const double nzb = 8.0 * nz;
+    const double nzb = (double)sizeof(TV) * nz;
     EpMap em;
     ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
-    auto product = [&](const double *Xin, double *Wout, double scale) {
+    auto product = [&](const TV *Xin, TV *Wout, double scale) {
         if (em.ok)
-            masked_product_mapped<double>(em, A, A.val, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, nullptr,
-                                          Fin(), s);
-        else masked_product_proj<double>(A, A.val, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, nullptr, Fin(), s);
+            masked_product_mapped<TV>(em, A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, nullptr, Fin(), s);
+        else masked_product_proj<TV>(A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, nullptr, Fin(), s);
+    };
+    auto dot_t = [&](const TV *a, const TV *b, double *out) {
+        Fin f;
+        f.mode = FIN_STORE;
+        f.partial = c.partial;
+        f.counter = c.counter;
+        f.out = out;
+        RN_LAUNCH("energy_gmres_dot", 2 * nzb, s, gm_dot_kernel<TV>,
+                  grid_resident(gm_dot_kernel<TV>, kT, 0, nz, kT * 4, kReduceBlocks), kT, 0, nz, a, b, f);
     };
     product(X, V.p, -1.0);
-    dot(V.p, V.p, nz, sc + 1, s, c.partial, c.counter);
+    dot_t(V.p, V.p, sc + 1);
     RN_LAUNCH("energy_gmres_scalar", 0, s, gm_start_kernel, 1, 1, 0, sc, fl, g);
-    RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel, eg, 256, 0, nz, V.p, sc, fl);
+    RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel<TV>, eg, 256, 0, nz, V.p, sc, fl);
     for (int j = 0; j < m; j++) {
-        double *vj = V.p + (int64_t)j * nz;
+        TV *vj = V.p + (int64_t)j * nz;
         product(vj, W.p, 1.0);
         for (int i = 0; i <= j; i++) {
-            double *vi = V.p + (int64_t)i * nz;
-            dot(W.p, vi, nz, H + i * m + j, s, c.partial, c.counter);
-            RN_LAUNCH("energy_gmres_vec", 3 * nzb, s, gm_axpy_kernel, eg, 256, 0, nz, W.p, vi, H + i * m + j, fl);
+            TV *vi = V.p + (int64_t)i * nz;
+            dot_t(W.p, vi, H + i * m + j);
+            RN_LAUNCH("energy_gmres_vec", 3 * nzb, s, gm_axpy_kernel<TV>, eg, 256, 0, nz, W.p, vi, H + i * m + j,
+                      fl);
         }
-        dot(W.p, W.p, nz, sc + 1, s, c.partial, c.counter);
+        dot_t(W.p, W.p, sc + 1);
         RN_LAUNCH("energy_gmres_scalar", 0, s, gm_givens_kernel, 1, 1, 0, m, j, H, cs, sn, g, sc, fl, kGmresBreak);
         if (j + 1 < m + 1) {
             d2d(V.p + (int64_t)(j + 1) * nz, W.p, nz, s);
-            RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel, eg, 256, 0, nz, V.p + (int64_t)(j + 1) * nz,
-                      sc + 2, fl);
+            RN_LAUNCH("energy_gmres_vec", 2 * nzb, s, gm_scale_kernel<TV>, eg, 256, 0, nz,
+                      V.p + (int64_t)(j + 1) * nz, sc + 2, fl);
         }
     }
     RN_LAUNCH("energy_gmres_scalar", 0, s, gm_backsolve_kernel, 1, 1, 0, m, H, g, y, fl);
-    RN_LAUNCH("energy_gmres_vec", (m + 2) * nzb, s, gm_combine_kernel, eg, 256, 0, nz, m, X, V.p, y, fl);
+    RN_LAUNCH("energy_gmres_vec", (m + 2) * nzb, s, gm_combine_kernel<TV>, eg, 256, 0, nz, m, X, V.p, y, fl);
+    if constexpr (f32) to_double(X, X64, nz, s);
+}
+
+void energy_min_gmres(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
+                      const double *Bc, int m) {
+    if (c.fp32) energy_min_gmres_t<float>(c, A, N, X, rowtype, Bc, m);
+    else energy_min_gmres_t<double>(c, A, N, X, rowtype, Bc, m);
 }
 
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
@@ -801,7 +859,7 @@ static EmCtx ctx_of(rn_hierarchy &h) {
     c.fl = h.iflags.p;
     c.precond = h.p.energy_precond;
     c.method = h.p.energy_method;
-    c.fp32 = h.p.precision == RN_MIXED;  // FP32 sweeps in the mixed-precision setup (CG)
+    c.fp32 = h.p.precision == RN_MIXED;  // FP32 sweeps (CG and GMRES) in the mixed-precision setup
     return c;
 }
 

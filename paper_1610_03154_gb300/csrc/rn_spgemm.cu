@@ -198,6 +198,153 @@ small_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
     }
 }
 
+// Rows with at most kMergeWays entries (and at most kSmallProd products): a
+// thread per row merges the row's sorted lists B_k (one per a_ik, ascending
+// k).  Each output column is the smallest head; its products are summed in
+// ascending k (the first one alone, then one rounded add per further term),
+// bit-identical to a sequential evaluation.  Rows with more entries go to
+// ovf_list for the sort kernel.
+constexpr int kMergeWays = 12;
+
+__global__ void __launch_bounds__(kFuThreads)
+merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
+                     const int32_t *__restrict__ acol, const double *__restrict__ aval,
+                     const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
+                     const double *__restrict__ bval, const int32_t *__restrict__ ubp, int32_t *__restrict__ tcol,
+                     double *__restrict__ tval, int32_t *__restrict__ count, int32_t *__restrict__ ovf_list,
+                     int32_t *__restrict__ ovf_n) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+        const int32_t i = rows[r];
+        const int32_t as = arp[i], ae = arp[i + 1], na = ae - as;
+        if (na > kMergeWays) {
+            ovf_list[atomicAdd(ovf_n, 1)] = i;
+            continue;
+        }
+        int32_t pos[kMergeWays], end[kMergeWays], cur[kMergeWays];
+#pragma unroll
+        for (int u = 0; u < kMergeWays; u++) {
+            pos[u] = 0;
+            end[u] = 0;
+            cur[u] = INT32_MAX;
+            if (u < na) {
+                const int32_t k = acol[as + u];
+                pos[u] = brp[k];
+                end[u] = brp[k + 1];
+                if (pos[u] < end[u]) cur[u] = bcol[pos[u]];
+            }
+        }
+        const int32_t base = ubp[i];
+        int32_t nout = 0;
+        for (;;) {
+            int32_t cmin = INT32_MAX;
+#pragma unroll
+            for (int u = 0; u < kMergeWays; u++) cmin = min(cmin, cur[u]);
+            if (cmin == INT32_MAX) break;
+            double sum = 0.0;
+            bool first = true;
+#pragma unroll
+            for (int u = 0; u < kMergeWays; u++) {
+                if (cur[u] == cmin) {
+                    const double v = __dmul_rn(aval[as + u], bval[pos[u]]);
+                    sum = first ? v : __dadd_rn(sum, v);
+                    first = false;
+                    pos[u]++;
+                    cur[u] = pos[u] < end[u] ? bcol[pos[u]] : INT32_MAX;
+                }
+            }
+            tcol[base + nout] = cmin;
+            tval[base + nout] = sum;
+            nout++;
+        }
+        count[i] = nout;
+    }
+}
+
+// Rows of many products but at most 32 entries: a warp per row merges the
+// row's sorted lists B_k, lane u holding list u's head (the next entry,
+// prefetched).  Each output column is the warp minimum of the heads; the
+// lanes on it form the products and they are summed in lane (= ascending k)
+// order - the first alone, then one rounded add per further term - so the
+// result is bit-identical to a sequential evaluation.  Outputs are staged in
+// shared memory and written in coalesced chunks.  Rows with more entries go
+// to ovf_list.
+constexpr int kWmWarps = 4;  // warps per block
+
+__global__ void __launch_bounds__(32 * kWmWarps)
+warp_merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
+                          const int32_t *__restrict__ acol, const double *__restrict__ aval,
+                          const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
+                          const double *__restrict__ bval, const int32_t *__restrict__ ubp,
+                          int32_t *__restrict__ tcol, double *__restrict__ tval, int32_t *__restrict__ count,
+                          int32_t *__restrict__ ovf_list, int32_t *__restrict__ ovf_n) {
+    __shared__ int32_t s_c[kWmWarps][32];
+    __shared__ double s_v[kWmWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int32_t r = blockIdx.x * kWmWarps + w; r < nrows; r += gridDim.x * kWmWarps) {
+        const int32_t i = rows[r];
+        const int32_t as = arp[i], ae = arp[i + 1], na = ae - as;
+        if (na > 32) {
+            if (lane == 0) ovf_list[atomicAdd(ovf_n, 1)] = i;
+            continue;
+        }
+        int32_t pos = 0, end = 0, cur = INT32_MAX, nxt = INT32_MAX;
+        double a = 0.0;
+        if (lane < na) {
+            const int32_t k = acol[as + lane];
+            a = aval[as + lane];
+            pos = brp[k];
+            end = brp[k + 1];
+            if (pos < end) cur = bcol[pos];
+            if (pos + 1 < end) nxt = bcol[pos + 1];
+        }
+        const int32_t base = ubp[i];
+        int32_t nout = 0, staged = 0;
+        for (;;) {
+            int32_t cmin = cur;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+            if (cmin == INT32_MAX) break;
+            const bool on = cur == cmin;
+            const unsigned m = __ballot_sync(0xffffffffu, on);
+            const double v = on ? __dmul_rn(a, bval[pos]) : 0.0;
+            unsigned rest = m;
+            const int first = __ffs(rest) - 1;
+            double sum = __shfl_sync(0xffffffffu, v, first);
+            rest &= rest - 1;
+            while (rest) {  // warp-uniform: the remaining contributors in ascending lane order
+                const int b = __ffs(rest) - 1;
+                sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, v, b));
+                rest &= rest - 1;
+            }
+            if (lane == staged) {
+                s_c[w][staged] = cmin;
+                s_v[w][staged] = sum;
+            }
+            staged++;
+            if (staged == 32) {  // flush a full chunk, coalesced
+                __syncwarp();
+                tcol[base + nout + lane] = s_c[w][lane];
+                tval[base + nout + lane] = s_v[w][lane];
+                nout += 32;
+                staged = 0;
+                __syncwarp();
+            }
+            if (on) {  // advance this list; its next head was prefetched
+                pos++;
+                cur = nxt;
+                nxt = (pos + 1 < end) ? bcol[pos + 1] : INT32_MAX;
+            }
+        }
+        __syncwarp();
+        if (lane < staged) {
+            tcol[base + nout + lane] = s_c[w][lane];
+            tval[base + nout + lane] = s_v[w][lane];
+        }
+        if (lane == 0) count[i] = nout + staged;
+        __syncwarp();
+    }
+}
+
 // G lanes per row, SLOTS table entries per group, for the rows listed in
 // rows.  Rows whose distinct columns exceed SLOTS/2 go to ovf_list.
 template <int G, int SLOTS>
@@ -398,7 +545,8 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
     C.n = A.n;
     C.m = B.m;
     const int32_t n = A.n;
-    // flags: [0] small rows, [1] large rows, [2] count overflow, [3] rows past the hash tables, [4] past kBigProd
+    // flags: [0] small rows, [1] large rows, [2] count overflow, [3] rows past the hash tables, [4] past kBigProd,
+    // [5] small rows with too many entries to merge, [6] large rows with more than 32 entries
     DVec<int32_t> ub(n + 1, s), ubp(n + 1, s), count(n + 1, s), flags(8, s), bins(n > 0 ? n : 1, s),
         ovf_list(n > 0 ? n : 1, s);
     fill_i32(flags.p, 0, 8, s);
@@ -415,15 +563,35 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
     const double bytes = 12.0 * A.nnz + 8.0 * n + 12.0 * B.nnz + 12.0 * total;
     const int32_t nsmall = fl[0], nlarge = fl[1];
     if (nsmall) {
-        const double avg = (double)A.nnz / std::max(1, n) * ((double)B.nnz / std::max(1, B.n));
-        if (avg <= 8.0) launch_small<4>(nsmall, bins.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
-        else if (avg <= 24.0) launch_small<8>(nsmall, bins.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
-        else launch_small<16>(nsmall, bins.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+        // merge rows of few entries; the rest of the bin goes to the sort kernel
+        RN_LAUNCH("spgemm_merge", bytes, s, merge_product_kernel,
+                  grid_resident(merge_product_kernel, kFuThreads, 0, nsmall, kFuThreads), kFuThreads, 0, nsmall,
+                  bins.p, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p, count.p,
+                  ovf_list.p, flags.p + 5);
+        const int32_t nrest = read_scalar(flags.p + 5, s);
+        if (nrest) {
+            const double avg = (double)A.nnz / std::max(1, n) * ((double)B.nnz / std::max(1, B.n));
+            if (avg <= 8.0) launch_small<4>(nrest, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+            else if (avg <= 24.0) launch_small<8>(nrest, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+            else launch_small<16>(nrest, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+        }
     }
-    if (nlarge)
-        launch_hash<32, 1024>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf_list.p,
-                              flags.p + 3, bytes, s);
-    const int32_t novf = nlarge ? read_scalar(flags.p + 3, s) : 0;
+    int32_t novf = 0;
+    if (nlarge) {
+        // rows of at most 32 entries by a warp-wide merge; longer rows by hash tables
+        RN_LAUNCH("spgemm_merge", bytes, s, warp_merge_product_kernel,
+                  grid_resident(warp_merge_product_kernel, 32 * kWmWarps, 0, nlarge, kWmWarps), 32 * kWmWarps, 0,
+                  nlarge, bins.p + (n - nlarge), A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p,
+                  tval.p, count.p, ovf_list.p, flags.p + 6);
+        const int32_t nwide = read_scalar(flags.p + 6, s);
+        if (nwide) {
+            DVec<int32_t> wide((size_t)nwide, s);
+            d2d(wide.p, ovf_list.p, nwide, s);
+            launch_hash<32, 1024>(nwide, wide.p, A, B, ubp.p, tcol.p, tval.p, count.p, ovf_list.p, flags.p + 3,
+                                  bytes, s);
+            novf = read_scalar(flags.p + 3, s);
+        }
+    }
     if (novf > 0) {
         const size_t smem = (size_t)kBigProd * (sizeof(double) + 2 * sizeof(int32_t));
         RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

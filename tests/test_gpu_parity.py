@@ -380,6 +380,76 @@ def test_full_size_aniso_hierarchy_parity_and_solve(rn, torch_dev, oracle):
         h.close()
 
 
+def test_full_size_convdiff_hierarchy_parity_and_solve(rn, torch_dev, oracle):
+    """The 2048x2048 upwind convection-diffusion workload (n = 4,194,304,
+    nonsymmetric: R from A^T and B-hat, GMRES energy minimisation, FGMRES
+    outer iteration): every level against the oracle; then the same 20
+    FGMRES(30) iterations on both sides, whose relative residuals must agree
+    (FGMRES(30) with this cycle converges too slowly at this size to run to
+    1e-8 here: the oracle needs 3579 iterations on 1024^2; convergence to 1e-8
+    is checked on 512^2 below)."""
+    pr = PR.convdiff_problem(2048)
+    h = gpu_hierarchy(rn, torch_dev, pr)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, Bhat=pr.Bhat, **pr.params)
+    compare_hierarchies(h, oh, nonsym=True)
+    h.close()
+    K = 20
+    xo, oinfo = oh.solve(pr.b, tol=1e-8, maxit=K, outer=2, restart=30)
+    del oh
+    res = {}
+    for prec in (rn.RN_FP64, rn.RN_MIXED):
+        h = gpu_hierarchy(rn, torch_dev, pr, keep_aux=0, precision=prec)
+        torch, d = torch_dev
+        b = dev(torch_dev, pr.b)
+        x = torch.zeros_like(b)
+        info = h.solve(b, x, rtol=1e-8, maxit=K, raise_on_notconv=False)
+        assert info["iters"] == K
+        res[prec] = np.linalg.norm(pr.b - pr.A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(pr.b)
+        h.close()
+    ro = np.linalg.norm(pr.b - pr.A.to_scipy() @ xo) / np.linalg.norm(pr.b)
+    assert abs(res[rn.RN_FP64] - ro) <= 1e-6 * ro, (res, ro)
+    assert res[rn.RN_MIXED] <= 1.1 * ro, (res, ro)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_convdiff_512_converges(rn, torch_dev, oracle, precision):
+    pr = PR.convdiff_problem(512)
+    h = gpu_hierarchy(rn, torch_dev, pr, keep_aux=0, precision=precision)
+    xs, info, res = gpu_solve(rn, torch_dev, h, pr, maxit=2000)
+    assert info["status"] == 0 and res < 1e-8, (info, res)
+    if precision == 0:  # the oracle needs 169 iterations
+        assert abs(info["iters"] - 169) <= 3, info
+    h.close()
+
+
+def test_full_size_batched_problems(rn, torch_dev):
+    """The batched workload at its full size: 64 rotated-anisotropy problems
+    with element grids of 32..512 per side, set up and solved concurrently;
+    every solution meets the residual bar, and three problems (the smallest,
+    the largest, one between) match their stand-alone solves bit for bit."""
+    torch, d = torch_dev
+    probs = PR.batch_aniso_problems(count=64, seed=7)
+    params = rn.params_from_config(PR.PARAMS_ANISO, precision=rn.RN_MIXED)
+    dp = [(dev(torch_dev, p.A.rowptr), dev(torch_dev, p.A.col), dev(torch_dev, p.A.val),
+           dev(torch_dev, p.B.reshape(-1))) for p in probs]
+    hs = rn.setup_batched(dp, params=params)
+    bs = [dev(torch_dev, p.b) for p in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = rn.solve_batched(hs, bs, xs, rtol=1e-8, maxit=3000)
+    for p, x, info in zip(probs, xs, infos):
+        r = np.linalg.norm(p.b - p.A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(p.b)
+        assert info["status"] == 0 and r < 1e-8, (p.name, info, r)
+    sizes = [p.A.n_rows for p in probs]
+    for k in (int(np.argmin(sizes)), int(np.argmax(sizes)), 17):
+        h1 = rn.Hierarchy(*dp[k], params=params)
+        x1 = torch.zeros_like(xs[k])
+        h1.solve(bs[k], x1, rtol=1e-8, maxit=3000)
+        assert np.array_equal(x1.cpu().numpy(), xs[k].cpu().numpy()), probs[k].name
+        h1.close()
+    for h in hs:
+        h.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_time_op_measures_every_solve_launch(rn, torch_dev, precision):
     """The measurement hook times each level-0 launch of the solve and leaves
@@ -438,7 +508,7 @@ def _solve_capped(rn, torch_dev, h, pr, maxit):
     return x.cpu().numpy(), info
 
 
-@pytest.mark.parametrize("case", ["poisson64", "aniso96", "aniso255"])
+@pytest.mark.parametrize("case", ["poisson64", "aniso96", "aniso255", "convdiff80"])
 def test_mixed_precision_setup_error_against_fp64(rn, torch_dev, oracle, case):
     """Mixed precision runs the CG energy-minimisation sweeps in FP32 (the row
     projection and the CG scalars stay FP64).  Level 0's pattern comes from
