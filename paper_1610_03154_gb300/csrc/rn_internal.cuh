@@ -185,6 +185,8 @@ T read_scalar(const T *dptr, cudaStream_t s) {
 // the total (one device->host read).  Fails with RN_EINTERNAL if the total
 // does not fit in int32.
 int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t s);
+// The same without the host read: the total goes to *total (device).
+void scan_counts_dev(const int32_t *counts, int32_t *out, int64_t n, int64_t *total, cudaStream_t s);
 // Deterministic grid reductions: per-block partial sums, summed in block order
 // by the last block (see grid_finish).  Grids of reducing kernels never exceed
 // kReduceBlocks blocks.

@@ -300,15 +300,19 @@ __global__ void scan_apply(const int32_t *__restrict__ in, int64_t n, const int6
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (int32_t)(*total);
 }
 
-int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t s) {
+void scan_counts_dev(const int32_t *counts, int32_t *out, int64_t n, int64_t *total, cudaStream_t s) {
     int64_t nb = (n + kScanChunk - 1) / kScanChunk;
     if (nb < 1) nb = 1;
-    DVec<int64_t> sums(nb + 1, s);
-    int64_t *total = sums.p + nb;
+    DVec<int64_t> sums(nb, s);
     RN_LAUNCH("scan", 4.0 * n, s, scan_block_sums, (int)nb, kScanThreads, 0, counts, n, sums.p);
     RN_LAUNCH("scan", 8.0 * nb, s, scan_sums, 1, kScanThreads, 0, sums.p, nb, total);
     RN_LAUNCH("scan", 8.0 * n, s, scan_apply, (int)nb, kScanThreads, 0, counts, n, sums.p, total, out);
-    int64_t t = read_scalar(total, s);
+}
+
+int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t s) {
+    DVec<int64_t> total(1, s);
+    scan_counts_dev(counts, out, n, total.p, s);
+    int64_t t = read_scalar(total.p, s);
     if (t > INT32_MAX) fail(RN_EINTERNAL, fmt("scan total %lld exceeds int32", (long long)t));
     return t;
 }

@@ -9,6 +9,7 @@
 //   W = scale * Proj(Mask_N(A X)) on a fixed pattern, with the row-wise
 //   constraint projection and a Frobenius product fused in.
 #include <climits>
+#include <cstring>
 
 #include "rn_internal.cuh"
 
@@ -65,7 +66,8 @@ __global__ void product_bound_kernel(int32_t n, const int32_t *__restrict__ arp,
 
 template <int G>
 __global__ void __launch_bounds__(kFuThreads)
-small_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
+small_product_kernel(int32_t nrows_max, const int32_t *__restrict__ nrows_dev, const int32_t *__restrict__ rows,
+                     const int32_t *__restrict__ arp,
                      const int32_t *__restrict__ acol, const double *__restrict__ aval,
                      const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
                      const double *__restrict__ bval, const int32_t *__restrict__ ubp, int32_t *__restrict__ tcol,
@@ -87,6 +89,7 @@ small_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
     double *V = s_v + g * ST;     // products in list order
     double *Ea = s_ea + g * ET;
     int32_t *Eb = s_eb + g * ET, *Eo = s_eo + g * ET;
+    const int32_t nrows = nrows_dev ? min(*nrows_dev, nrows_max) : nrows_max;  // rows listed on the device
     for (int32_t r0 = blockIdx.x * GPB; r0 < nrows; r0 += gridDim.x * GPB) {
         if (r0 + g >= nrows) continue;  // the whole group leaves together
         const int32_t i = rows[r0 + g];
@@ -260,91 +263,6 @@ merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
     }
 }
 
-// Rows of many products but at most 32 entries: a warp per row merges the
-// row's sorted lists B_k, lane u holding list u's head (the next entry,
-// prefetched).  Each output column is the warp minimum of the heads; the
-// lanes on it form the products and they are summed in lane (= ascending k)
-// order - the first alone, then one rounded add per further term - so the
-// result is bit-identical to a sequential evaluation.  Outputs are staged in
-// shared memory and written in coalesced chunks.  Rows with more entries go
-// to ovf_list.
-constexpr int kWmWarps = 4;  // warps per block
-
-__global__ void __launch_bounds__(32 * kWmWarps)
-warp_merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
-                          const int32_t *__restrict__ acol, const double *__restrict__ aval,
-                          const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
-                          const double *__restrict__ bval, const int32_t *__restrict__ ubp,
-                          int32_t *__restrict__ tcol, double *__restrict__ tval, int32_t *__restrict__ count,
-                          int32_t *__restrict__ ovf_list, int32_t *__restrict__ ovf_n) {
-    __shared__ int32_t s_c[kWmWarps][32];
-    __shared__ double s_v[kWmWarps][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int32_t r = blockIdx.x * kWmWarps + w; r < nrows; r += gridDim.x * kWmWarps) {
-        const int32_t i = rows[r];
-        const int32_t as = arp[i], ae = arp[i + 1], na = ae - as;
-        if (na > 32) {
-            if (lane == 0) ovf_list[atomicAdd(ovf_n, 1)] = i;
-            continue;
-        }
-        int32_t pos = 0, end = 0, cur = INT32_MAX, nxt = INT32_MAX;
-        double a = 0.0;
-        if (lane < na) {
-            const int32_t k = acol[as + lane];
-            a = aval[as + lane];
-            pos = brp[k];
-            end = brp[k + 1];
-            if (pos < end) cur = bcol[pos];
-            if (pos + 1 < end) nxt = bcol[pos + 1];
-        }
-        const int32_t base = ubp[i];
-        int32_t nout = 0, staged = 0;
-        for (;;) {
-            int32_t cmin = cur;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
-            if (cmin == INT32_MAX) break;
-            const bool on = cur == cmin;
-            const unsigned m = __ballot_sync(0xffffffffu, on);
-            const double v = on ? __dmul_rn(a, bval[pos]) : 0.0;
-            unsigned rest = m;
-            const int first = __ffs(rest) - 1;
-            double sum = __shfl_sync(0xffffffffu, v, first);
-            rest &= rest - 1;
-            while (rest) {  // warp-uniform: the remaining contributors in ascending lane order
-                const int b = __ffs(rest) - 1;
-                sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, v, b));
-                rest &= rest - 1;
-            }
-            if (lane == staged) {
-                s_c[w][staged] = cmin;
-                s_v[w][staged] = sum;
-            }
-            staged++;
-            if (staged == 32) {  // flush a full chunk, coalesced
-                __syncwarp();
-                tcol[base + nout + lane] = s_c[w][lane];
-                tval[base + nout + lane] = s_v[w][lane];
-                nout += 32;
-                staged = 0;
-                __syncwarp();
-            }
-            if (on) {  // advance this list; its next head was prefetched
-                pos++;
-                cur = nxt;
-                nxt = (pos + 1 < end) ? bcol[pos + 1] : INT32_MAX;
-            }
-        }
-        __syncwarp();
-        if (lane < staged) {
-            tcol[base + nout + lane] = s_c[w][lane];
-            tval[base + nout + lane] = s_v[w][lane];
-        }
-        if (lane == 0) count[i] = nout + staged;
-        __syncwarp();
-    }
-}
-
 // G lanes per row, SLOTS table entries per group, for the rows listed in
 // rows.  Rows whose distinct columns exceed SLOTS/2 go to ovf_list.
 template <int G, int SLOTS>
@@ -445,7 +363,8 @@ hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32
 // Block per overflowing row, kBigProd slots.
 constexpr int kBigProd = 8192;
 __global__ void __launch_bounds__(512)
-hash_product_block_kernel(const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
+hash_product_block_kernel(const int32_t *__restrict__ nrows_dev, const int32_t *__restrict__ rows,
+                          const int32_t *__restrict__ arp,
                           const int32_t *__restrict__ acol, const double *__restrict__ aval,
                           const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
                           const double *__restrict__ bval, const int32_t *__restrict__ ubp,
@@ -456,48 +375,52 @@ hash_product_block_kernel(const int32_t *__restrict__ rows, const int32_t *__res
     int32_t *keys = reinterpret_cast<int32_t *>(big_smem + kBigProd * sizeof(double));
     int32_t *list = keys + kBigProd;
     __shared__ int cnt, bad, u;
-    const int32_t i = rows[blockIdx.x];
-    for (int q = threadIdx.x; q < kBigProd; q += blockDim.x) keys[q] = -1;
-    if (threadIdx.x == 0) { cnt = 0; bad = 0; u = 0; }
-    __syncthreads();
-    constexpr unsigned hmask = kBigProd - 1;
-    for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
-        const int32_t k = acol[e];
-        const double a = aval[e];
-        for (int32_t f = brp[k] + threadIdx.x; f < brp[k + 1]; f += blockDim.x) {
-            const int32_t j = bcol[f];
-            const double v = __dmul_rn(a, bval[f]);
-            unsigned h = ((uint32_t)j * 2654435761u) & hmask;
-            int p = 0;
-            for (; p < kBigProd; p++) {
-                const int32_t old = atomicCAS(&keys[h], -1, j);
-                if (old == -1) { vals[h] = v; atomicAdd(&cnt, 1); break; }
-                if (old == j) { vals[h] = __dadd_rn(vals[h], v); break; }
-                h = (h + 1) & hmask;
+    const int32_t nrows = *nrows_dev;  // rows listed on the device; blocks loop over them
+    for (int32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        __syncthreads();
+        const int32_t i = rows[r];
+        for (int q = threadIdx.x; q < kBigProd; q += blockDim.x) keys[q] = -1;
+        if (threadIdx.x == 0) { cnt = 0; bad = 0; u = 0; }
+        __syncthreads();
+        constexpr unsigned hmask = kBigProd - 1;
+        for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
+            const int32_t k = acol[e];
+            const double a = aval[e];
+            for (int32_t f = brp[k] + threadIdx.x; f < brp[k + 1]; f += blockDim.x) {
+                const int32_t j = bcol[f];
+                const double v = __dmul_rn(a, bval[f]);
+                unsigned h = ((uint32_t)j * 2654435761u) & hmask;
+                int p = 0;
+                for (; p < kBigProd; p++) {
+                    const int32_t old = atomicCAS(&keys[h], -1, j);
+                    if (old == -1) { vals[h] = v; atomicAdd(&cnt, 1); break; }
+                    if (old == j) { vals[h] = __dadd_rn(vals[h], v); break; }
+                    h = (h + 1) & hmask;
+                }
+                if (p == kBigProd) bad = 1;
             }
-            if (p == kBigProd) bad = 1;
+            __syncthreads();
+            if (bad || cnt > kBigProd / 2) break;
         }
         __syncthreads();
-        if (bad || cnt > kBigProd / 2) break;
+        if (bad || cnt > kBigProd / 2) {
+            if (threadIdx.x == 0) atomicMax(err, i + 1);
+            continue;
+        }
+        for (int q = threadIdx.x; q < kBigProd; q += blockDim.x)
+            if (keys[q] >= 0) list[atomicAdd(&u, 1)] = q;
+        __syncthreads();
+        const int32_t base = ubp[i];
+        for (int e = threadIdx.x; e < u; e += blockDim.x) {
+            const int q = list[e];
+            const int32_t key = keys[q];
+            int rank = 0;
+            for (int f = 0; f < u; f++) rank += (keys[list[f]] < key);
+            tcol[base + rank] = key;
+            tval[base + rank] = vals[q];
+        }
+        if (threadIdx.x == 0) count[i] = u;
     }
-    __syncthreads();
-    if (bad || cnt > kBigProd / 2) {
-        if (threadIdx.x == 0) atomicMax(err, i + 1);
-        return;
-    }
-    for (int q = threadIdx.x; q < kBigProd; q += blockDim.x)
-        if (keys[q] >= 0) list[atomicAdd(&u, 1)] = q;
-    __syncthreads();
-    const int32_t base = ubp[i];
-    for (int e = threadIdx.x; e < u; e += blockDim.x) {
-        const int q = list[e];
-        const int32_t key = keys[q];
-        int rank = 0;
-        for (int f = 0; f < u; f++) rank += (keys[list[f]] < key);
-        tcol[base + rank] = key;
-        tval[base + rank] = vals[q];
-    }
-    if (threadIdx.x == 0) count[i] = u;
 }
 
 // C rows from the temporary (row i's entries at ubp[i], count[i] of them)
@@ -531,13 +454,16 @@ static void launch_hash(int32_t nrows, const int32_t *rows, const CsrView &A, co
               A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count, ovf_list, ovf_n);
 }
 
+// nrows_dev: the number of listed rows on the device (at most nrows_max), or
+// nullptr when nrows_max is exact
 template <int G>
-static void launch_small(int32_t nrows, const int32_t *rows, const CsrView &A, const CsrView &B, const int32_t *ubp,
-                         int32_t *tcol, double *tval, int32_t *count, double bytes, cudaStream_t s) {
+static void launch_small(int32_t nrows_max, const int32_t *nrows_dev, const int32_t *rows, const CsrView &A,
+                         const CsrView &B, const int32_t *ubp, int32_t *tcol, double *tval, int32_t *count,
+                         double bytes, cudaStream_t s) {
     constexpr int GPB = kFuThreads / G;
-    const int grid = grid_resident(small_product_kernel<G>, kFuThreads, 0, nrows, GPB);
-    RN_LAUNCH("spgemm_small", bytes, s, small_product_kernel<G>, grid, kFuThreads, 0, nrows, rows, A.rowptr, A.col,
-              A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count);
+    const int grid = grid_resident(small_product_kernel<G>, kFuThreads, 0, nrows_max, GPB);
+    RN_LAUNCH("spgemm_small", bytes, s, small_product_kernel<G>, grid, kFuThreads, 0, nrows_max, nrows_dev, rows,
+              A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count);
 }
 
 void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
@@ -546,63 +472,61 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
     C.m = B.m;
     const int32_t n = A.n;
     // flags: [0] small rows, [1] large rows, [2] count overflow, [3] rows past the hash tables, [4] past kBigProd,
-    // [5] small rows with too many entries to merge, [6] large rows with more than 32 entries
-    DVec<int32_t> ub(n + 1, s), ubp(n + 1, s), count(n + 1, s), flags(8, s), bins(n > 0 ? n : 1, s),
-        ovf_list(n > 0 ? n : 1, s);
-    fill_i32(flags.p, 0, 8, s);
+    // [5] small rows with too many entries to merge; then two int64 totals at flags + 8 (8-byte aligned)
+    DVec<int32_t> ub(n + 1, s), ubp(n + 1, s), count(n + 1, s), flags(12, s), bins(n > 0 ? n : 1, s),
+        ovf_list(n > 0 ? n : 1, s), ovf2(n > 0 ? n : 1, s);
+    fill_i32(flags.p, 0, 12, s);
+    int64_t *tot = reinterpret_cast<int64_t *>(flags.p + 8);
     if (n)
         RN_LAUNCH("spgemm_bound", 8.0 * A.nnz + 16.0 * n, s, product_bound_kernel, grid_for(n, 256), 256, 0, n,
                   A.rowptr, A.col, B.rowptr, ub.p, bins.p, flags.p);
-    const int64_t total = scan_counts(ub.p, ubp.p, n, s);
-    int32_t fl[3];
+    scan_counts_dev(ub.p, ubp.p, n, tot, s);
+    int32_t fl[12];  // one read: bins, flags and the products' total
     RN_CUDA_CHECK(cudaMemcpyAsync(fl, flags.p, sizeof fl, cudaMemcpyDeviceToHost, s));
     RN_CUDA_CHECK(cudaStreamSynchronize(s));
-    if (fl[2]) fail(RN_EINTERNAL, "spgemm: a row's product count exceeds int32");
+    int64_t total = 0;
+    std::memcpy(&total, fl + 8, sizeof total);
+    if (fl[2] || total > INT32_MAX) fail(RN_EINTERNAL, "spgemm: a row's product count exceeds int32");
     DVec<int32_t> tcol(total > 0 ? total : 1, s);
     DVec<double> tval(total > 0 ? total : 1, s);
     const double bytes = 12.0 * A.nnz + 8.0 * n + 12.0 * B.nnz + 12.0 * total;
     const int32_t nsmall = fl[0], nlarge = fl[1];
     if (nsmall) {
-        // merge rows of few entries; the rest of the bin goes to the sort kernel
+        // merge rows of few entries; the bin's other rows (counted on the
+        // device) go to the sort kernel, launched for at most nsmall rows
         RN_LAUNCH("spgemm_merge", bytes, s, merge_product_kernel,
                   grid_resident(merge_product_kernel, kFuThreads, 0, nsmall, kFuThreads), kFuThreads, 0, nsmall,
                   bins.p, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p, count.p,
                   ovf_list.p, flags.p + 5);
-        const int32_t nrest = read_scalar(flags.p + 5, s);
-        if (nrest) {
-            const double avg = (double)A.nnz / std::max(1, n) * ((double)B.nnz / std::max(1, B.n));
-            if (avg <= 8.0) launch_small<4>(nrest, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
-            else if (avg <= 24.0) launch_small<8>(nrest, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
-            else launch_small<16>(nrest, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
-        }
+        const double avg = (double)A.nnz / std::max(1, n) * ((double)B.nnz / std::max(1, B.n));
+        if (avg <= 8.0)
+            launch_small<4>(nsmall, flags.p + 5, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+        else if (avg <= 24.0)
+            launch_small<8>(nsmall, flags.p + 5, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+        else launch_small<16>(nsmall, flags.p + 5, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
     }
-    int32_t novf = 0;
     if (nlarge) {
-        // rows of at most 32 entries by a warp-wide merge; longer rows by hash tables
-        RN_LAUNCH("spgemm_merge", bytes, s, warp_merge_product_kernel,
-                  grid_resident(warp_merge_product_kernel, 32 * kWmWarps, 0, nlarge, kWmWarps), 32 * kWmWarps, 0,
-                  nlarge, bins.p + (n - nlarge), A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p,
-                  tval.p, count.p, ovf_list.p, flags.p + 6);
-        const int32_t nwide = read_scalar(flags.p + 6, s);
-        if (nwide) {
-            DVec<int32_t> wide((size_t)nwide, s);
-            d2d(wide.p, ovf_list.p, nwide, s);
-            launch_hash<32, 1024>(nwide, wide.p, A, B, ubp.p, tcol.p, tval.p, count.p, ovf_list.p, flags.p + 3,
-                                  bytes, s);
-            novf = read_scalar(flags.p + 3, s);
-        }
-    }
-    if (novf > 0) {
+        launch_hash<32, 1024>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
+                              flags.p + 3, bytes, s);
+        // rows past the tables (counted on the device): a block per row, looping
         const size_t smem = (size_t)kBigProd * (sizeof(double) + 2 * sizeof(int32_t));
-        RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        RN_LAUNCH("spgemm_hash_long", 0, s, hash_product_block_kernel, novf, 512, smem, ovf_list.p, A.rowptr, A.col,
-                  A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p, count.p, flags.p + 4);
-        if (read_scalar(flags.p + 4, s))
-            fail(RN_EINTERNAL, fmt("product row has more than %d distinct columns", kBigProd / 2));
+        static bool configured = false;
+        if (!configured) {
+            RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_block_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            configured = true;
+        }
+        RN_LAUNCH("spgemm_hash_long", 0, s, hash_product_block_kernel, std::min(nlarge, 2 * num_sms()), 512, smem,
+                  flags.p + 3, ovf2.p, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p,
+                  count.p, flags.p + 4);
     }
     C.rowptr.alloc(n + 1, s);
-    C.nnz = scan_counts(count.p, C.rowptr.p, n, s);
+    scan_counts_dev(count.p, C.rowptr.p, n, tot + 1, s);
+    RN_CUDA_CHECK(cudaMemcpyAsync(fl, flags.p, sizeof fl, cudaMemcpyDeviceToHost, s));
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (fl[4]) fail(RN_EINTERNAL, fmt("product row has more than %d distinct columns", kBigProd / 2));
+    std::memcpy(&total, fl + 10, sizeof total);
+    C.nnz = total;
     C.col.alloc(C.nnz, s);
     C.val.alloc(C.nnz, s);
     if (n)
