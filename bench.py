@@ -315,8 +315,9 @@ def main():
     times_other, infos_other = timed(other, args.steps)
 
     # per-launch device times of the solve's level-0 operations, each timed in
-    # isolation with CUDA events on the hierarchy's stream, a 256 MB write before
-    # every launch (cold L2; the GPU stays busy while the launch is enqueued).
+    # isolation with CUDA events on the hierarchy's stream, a 256 MB read before
+    # every launch (cold L2 without dirty lines; the GPU stays busy while the
+    # launch is enqueued).
     # Each runs once per outer iteration.
     h = rn.Hierarchy(rp, ci, va, Bd, params=params(prec), stream=sptr)
     xd.zero_()
@@ -341,7 +342,7 @@ def main():
                 "avg_launch_us": st["us"], "algorithmic_bytes": st["bytes"], "launches_per_step": iters,
                 "share_of_step": st["us"] * 1e-6 * iters / step_s,
                 "rule": "longest level-0 launch of the outer iteration (each runs once per iteration), timed "
-                        "alone with CUDA events after a 256 MB L2 flush"}
+                        "alone with CUDA events after a 256 MB L2 read flush (cold, no dirty lines)"}
     kernels = {k: {"us": round(v["us"], 2), "launches_per_step": iters,
                    "GBps": round(v["bytes"] / (v["us"] * 1e-6) / 1e9, 1) if v["bytes"] > 0 else None}
                for k, v in sorted(ops.items(), key=lambda kv: -kv[1]["us"])}

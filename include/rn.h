@@ -261,10 +261,10 @@ rn_status rn_adjoint_grad(const rn_csr *A, const double *lambda, const double *x
 /* Measurement hook (no counterpart in the paper): time one level-0 launch of
  * the solve in isolation.  The operation is enqueued `reps` times on the
  * hierarchy's stream exactly as rn_solve issues it (kernel, launch shape,
- * buffers), each launch bracketed by CUDA events and preceded by a write of
- * `flush_bytes` bytes to a buffer the call allocates (0: no write), so that
- * every launch starts with a cold L2 and the GPU is busy while the launch is
- * enqueued.  Outputs: *us the mean device time of one launch in microseconds,
+ * buffers), each launch bracketed by CUDA events and preceded by a read of
+ * `flush_bytes` bytes from a buffer the call allocates (0: no flush), so that
+ * every launch starts with a cold L2 holding no dirty lines and the GPU is
+ * busy while the launch is enqueued.  Outputs: *us the mean device time of one launch in microseconds,
  * *bytes its algorithmic bytes (0 for RN_OP_COARSE_CLUSTER), name (>= 48
  * chars, may be NULL) the launch's name.  The solve workspaces are left in an
  * unspecified state; the hierarchy stays valid (rn_solve and rn_vcycle

@@ -1291,11 +1291,29 @@ static double enqueue_op(rn_hierarchy &h, int op, std::string &name) {
     return 0.0;
 }
 
+// Reads the flush buffer (16-byte words) so that L2 ends up holding only its
+// clean lines: a write flush would leave up to 129 MB of dirty lines whose
+// write-back the timed kernel would pay for.  One word per block is stored so
+// the loads are not dead.
+__global__ void flush_read_kernel(const uint4 *__restrict__ p, int64_t n16, uint32_t *__restrict__ sink) {
+    uint32_t a = 0u;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n16; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 v = p[k];  // default policy: the lines displace what L2 held
+        a ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    a = __reduce_xor_sync(0xffffffffu, a);
+    if ((threadIdx.x & 31) == 0) atomicXor(sink + blockIdx.x, a);
+}
+
 void time_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, std::string &name) {
     cudaStream_t s = h.s;
     if (reps < 1 || reps > 100000) fail(RN_EINVAL, "reps must be in [1, 100000]");
     if (flush_bytes < 0) fail(RN_EINVAL, "flush_bytes must be >= 0");
-    DVec<unsigned char> fl(flush_bytes > 0 ? (size_t)flush_bytes : 0, s);
+    const int64_t n16 = flush_bytes / 16;
+    DVec<uint4> fl(n16 > 0 ? (size_t)n16 : 0, s);
+    const int fgrid = 4 * num_sms();
+    DVec<uint32_t> sink(fgrid, s);
+    if (n16 > 0) RN_CUDA_CHECK(cudaMemsetAsync(fl.p, 0x5a, (size_t)n16 * 16, s));
     std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
     struct EvGuard {
         std::vector<cudaEvent_t> &ev;
@@ -1308,8 +1326,11 @@ void time_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us,
     const bool mixed = h.p.precision == RN_MIXED;
     double b = 0.0;
     for (int r = 0; r < reps; r++) {
-        // the flush keeps the GPU busy while the launch is enqueued and leaves L2 cold
-        if (flush_bytes > 0) RN_CUDA_CHECK(cudaMemsetAsync(fl.p, r & 0xff, (size_t)flush_bytes, s));
+        // the flush keeps the GPU busy while the launch is enqueued and leaves L2 cold and clean
+        if (n16 > 0) {
+            flush_read_kernel<<<fgrid, 512, 0, s>>>(fl.p, n16, sink.p);
+            RN_CUDA_CHECK(cudaGetLastError());
+        }
         RN_CUDA_CHECK(cudaEventRecord(ev[2 * r], s));
         b = mixed ? enqueue_op<float>(h, op, name) : enqueue_op<double>(h, op, name);
         RN_CUDA_CHECK(cudaEventRecord(ev[2 * r + 1], s));
