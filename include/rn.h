@@ -29,8 +29,10 @@
  *   - Inputs are borrowed for the duration of the call only; rn_setup copies
  *     what it keeps.  The hierarchy is owned by the library until rn_free.
  *   - Device work runs on params.stream (a cudaStream_t; NULL means the
- *     legacy default stream).  Device memory comes from the stream-ordered
- *     allocator (cudaMallocAsync) on that stream.  rn_setup and rn_solve
+ *     legacy default stream).  Device memory comes from the caller's hooks
+ *     (params.alloc / dealloc, e.g. torch's caching allocator) or, without
+ *     them, from the stream-ordered allocator (cudaMallocAsync) on that
+ *     stream.  rn_setup and rn_solve
  *     return after their last host read-back; outputs are complete when they
  *     return.
  *   - k (the number of candidates) must be 1.
@@ -95,6 +97,17 @@ typedef struct {
                                 this many passes of one thread-block cluster's threads) runs as one
                                 cluster launch; 0: one launch per operation on every level */
     void *stream;            /* cudaStream_t */
+    /* Device-memory hooks (both NULL: the stream-ordered pool, cudaMallocAsync;
+     * one without the other is RN_EINVAL).  alloc(bytes, stream, ctx) returns
+     * device memory for use in stream order on `stream`, or NULL, which fails
+     * the call with RN_ENOMEM; dealloc(p, bytes, stream, ctx) takes it back in
+     * stream order.  A hierarchy allocates and frees with the hooks of its
+     * rn_setup call for its whole life (rn_solve and rn_free included), so they
+     * and alloc_ctx must stay valid until rn_free.  Calls without an rn_params
+     * argument (rn_energy_min, rn_adjoint_grad) use the pool. */
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*dealloc)(void *p, size_t bytes, void *stream, void *ctx);
+    void *alloc_ctx;
 } rn_params;
 
 typedef struct {

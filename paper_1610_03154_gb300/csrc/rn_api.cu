@@ -79,6 +79,16 @@ static void check_params(const rn_params *p) {
     if (p->outer == RN_OUTER_FGMRES && (p->restart < 1 || p->restart > 1000)) fail(RN_EINVAL, "restart");
     if (!(p->omega > 0.0)) fail(RN_EINVAL, "omega must be > 0");
     if (p->coarse_cluster < 0) fail(RN_EINVAL, "coarse_cluster must be >= 0");
+    if ((p->alloc == nullptr) != (p->dealloc == nullptr))
+        fail(RN_EINVAL, "alloc and dealloc must both be set or both be NULL");
+}
+
+static rn::Allocator alloc_of(const rn_params &p) {
+    rn::Allocator a;
+    a.alloc = p.alloc;
+    a.dealloc = p.dealloc;
+    a.ctx = p.alloc_ctx;
+    return a;
 }
 
 extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bhat, int k, int location,
@@ -94,6 +104,7 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
     if (!A->rowptr || !A->col || !A->val) fail(RN_EINVAL, "null CSR array");
     check_params(p);
     if (!p->symmetric && !Bhat) fail(RN_EINVAL, "nonsymmetric setup needs Bhat");
+    const rn::AllocScope alloc_scope(alloc_of(*p));  // every buffer of the hierarchy comes from p's hooks
     // With no stream given, work goes to a stream the hierarchy creates: a
     // blocking stream, so it stays ordered with the legacy default stream,
     // and unlike that stream it can be captured into a CUDA graph.
@@ -228,6 +239,7 @@ extern "C" rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int l
     if (!h || !b || !x) fail(RN_EINVAL, "null argument");
     if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
     if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
+    const rn::AllocScope alloc_scope(alloc_of(h->p));
     cudaStream_t s = h->s;
     const int64_t n = h->lev[0]->A.n;
     const double t0 = rn::now_ms();
@@ -256,6 +268,7 @@ extern "C" rn_status rn_solve_multi(rn_hierarchy *h, const double *B, double *X,
     if (s < 1 || s > 2048) fail(RN_EINVAL, "s must be in [1, 2048]");
     if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
     if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
+    const rn::AllocScope alloc_scope(alloc_of(h->p));
     cudaStream_t st = h->s;
     const int64_t tot = (int64_t)h->lev[0]->A.n * s;
     const double t0 = rn::now_ms();
@@ -279,6 +292,7 @@ extern "C" rn_status rn_solve_multi(rn_hierarchy *h, const double *B, double *X,
 extern "C" rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x) {
     RN_API_BEGIN
     if (!h || !b || !x) rn::fail(RN_EINVAL, "null argument");
+    const rn::AllocScope alloc_scope(alloc_of(h->p));
     rn::cycle_checked(*h, b, x);
     RN_CUDA_CHECK(cudaStreamSynchronize(h->s));
     return RN_OK;
@@ -289,6 +303,7 @@ extern "C" rn_status rn_time_op(rn_hierarchy *h, int op, int reps, int64_t flush
                                 char *name) {
     RN_API_BEGIN
     if (!h || !us || !bytes) rn::fail(RN_EINVAL, "null argument");
+    const rn::AllocScope alloc_scope(alloc_of(h->p));
     std::string nm;
     rn::time_op(*h, op, reps, flush_bytes, us, bytes, nm);
     if (name) {

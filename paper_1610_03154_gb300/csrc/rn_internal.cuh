@@ -36,36 +36,60 @@ void set_last_error(const std::string &msg);
     } while (0)
 
 // --------------------------------------------------------------- device memory
-void *dmalloc(size_t bytes, cudaStream_t s);
-void dfree(void *p, cudaStream_t s);
+// Where device memory comes from: the caller's hooks (rn_params alloc /
+// dealloc / alloc_ctx), or the stream-ordered pool when alloc is null.
+struct Allocator {
+    void *(*alloc)(size_t, void *, void *) = nullptr;
+    void (*dealloc)(void *, size_t, void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+// The allocator new buffers take on this thread; the API entry points set it
+// for the duration of a call (AllocScope) from the call's parameters.
+Allocator &current_allocator();
+struct AllocScope {
+    Allocator saved;
+    explicit AllocScope(const Allocator &a) : saved(current_allocator()) { current_allocator() = a; }
+    ~AllocScope() { current_allocator() = saved; }
+    AllocScope(const AllocScope &) = delete;
+    AllocScope &operator=(const AllocScope &) = delete;
+};
+// bytes is rounded up (with tail slack) inside; *got receives the size asked of the allocator
+void *dmalloc(size_t bytes, cudaStream_t s, const Allocator &a, size_t *got);
+void dfree(void *p, size_t got, cudaStream_t s, const Allocator &a);
 
+// A device buffer; it is freed by the allocator it came from, whatever the
+// thread's allocator is at that time.
 template <typename T>
 struct DVec {
     T *p = nullptr;
     size_t n = 0;
     cudaStream_t s = nullptr;
+    Allocator a;
+    size_t got = 0;
     DVec() = default;
     DVec(size_t n_, cudaStream_t s_) { alloc(n_, s_); }
     void alloc(size_t n_, cudaStream_t s_) {
         release();
         s = s_;
+        a = current_allocator();
+        p = n_ ? static_cast<T *>(dmalloc(n_ * sizeof(T), s, a, &got)) : nullptr;
         n = n_;
-        p = n ? static_cast<T *>(dmalloc(n * sizeof(T), s)) : nullptr;
     }
     void release() {
-        if (p) dfree(p, s);
+        if (p) dfree(p, got, s, a);
         p = nullptr;
         n = 0;
+        got = 0;
     }
     ~DVec() { release(); }
     DVec(const DVec &) = delete;
     DVec &operator=(const DVec &) = delete;
-    DVec(DVec &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DVec(DVec &&o) noexcept : p(o.p), n(o.n), s(o.s), a(o.a), got(o.got) { o.p = nullptr; o.n = 0; o.got = 0; }
     DVec &operator=(DVec &&o) noexcept {
         if (this != &o) {
             release();
-            p = o.p; n = o.n; s = o.s;
-            o.p = nullptr; o.n = 0;
+            p = o.p; n = o.n; s = o.s; a = o.a; got = o.got;
+            o.p = nullptr; o.n = 0; o.got = 0;
         }
         return *this;
     }

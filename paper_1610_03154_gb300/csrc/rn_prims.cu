@@ -36,7 +36,26 @@ double now_ms() {
 // --------------------------------------------------------------------- memory
 static bool g_pool_configured = false;
 
-void *dmalloc(size_t bytes, cudaStream_t s) {
+Allocator &current_allocator() {
+    thread_local Allocator a;
+    return a;
+}
+
+void *dmalloc(size_t bytes, cudaStream_t s, const Allocator &a, size_t *got) {
+    // every buffer gets >= 256 bytes of tail slack: the tile kernels copy CSR
+    // segments with 16-byte-granular bulk copies that may end up to 15 bytes
+    // past the last element (the slack is never interpreted)
+    bytes = ((bytes + 255) / 256) * 256 + 256;
+    *got = bytes;
+    if (a.alloc) {
+        void *p = a.alloc(bytes, (void *)s, a.ctx);
+        if (!p) fail(RN_ENOMEM, fmt("the caller's allocator returned NULL for %zu bytes", bytes));
+        if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {  // bulk copies and vector loads need alignment
+            a.dealloc(p, bytes, (void *)s, a.ctx);
+            fail(RN_EINVAL, "the caller's allocator returned memory not aligned to 256 bytes");
+        }
+        return p;
+    }
     if (!g_pool_configured) {
         // keep freed blocks cached in the device's default pool: setup makes
         // many short-lived allocations
@@ -49,10 +68,6 @@ void *dmalloc(size_t bytes, cudaStream_t s) {
         g_pool_configured = true;
     }
     void *p = nullptr;
-    // every buffer gets >= 256 bytes of tail slack: the tile kernels copy CSR
-    // segments with 16-byte-granular bulk copies that may end up to 15 bytes
-    // past the last element (the slack is never interpreted)
-    bytes = ((bytes + 255) / 256) * 256 + 256;
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -62,8 +77,10 @@ void *dmalloc(size_t bytes, cudaStream_t s) {
     return p;
 }
 
-void dfree(void *p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+void dfree(void *p, size_t got, cudaStream_t s, const Allocator &a) {
+    if (!p) return;
+    if (a.alloc) a.dealloc(p, got, (void *)s, a.ctx);
+    else cudaFreeAsync(p, s);
 }
 
 // --------------------------------------------------------------------- launch helpers

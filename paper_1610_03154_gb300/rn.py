@@ -33,6 +33,10 @@ class rn_csr(C.Structure):
                 ("col", C.c_void_p), ("val", C.c_void_p)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+DEALLOC_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
 class rn_params(C.Structure):
     _fields_ = [("soc_theta", C.c_double), ("soc_theta_coarse", C.c_double), ("degree", C.c_int),
                 ("n_sweeps", C.c_int), ("energy_method", C.c_int), ("energy_precond", C.c_int),
@@ -40,7 +44,8 @@ class rn_params(C.Structure):
                 ("max_levels", C.c_int), ("b_sweeps", C.c_int), ("omega", C.c_double), ("seed", C.c_uint64),
                 ("symmetric", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int), ("precision", C.c_int),
                 ("outer", C.c_int), ("restart", C.c_int), ("use_graphs", C.c_int), ("keep_aux", C.c_int),
-                ("coarse_cluster", C.c_int), ("stream", C.c_void_p)]
+                ("coarse_cluster", C.c_int), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("dealloc", DEALLOC_FN),
+                ("alloc_ctx", C.c_void_p)]
 
 
 class rn_solve_info(C.Structure):
@@ -242,6 +247,46 @@ def _ptr(a) -> int:
 
 def _is_host(a) -> bool:
     return isinstance(a, np.ndarray) or (hasattr(a, "is_cuda") and not a.is_cuda)
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        import torch
+
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+    except Exception:  # out of memory or no CUDA: the library reports RN_ENOMEM
+        return None
+
+
+def _torch_dealloc(ptr, nbytes, stream, ctx):
+    try:
+        import torch
+
+        torch.cuda.caching_allocator_delete(ptr)
+    except Exception:  # interpreter shutdown: the process is releasing the device anyway
+        pass
+
+
+# module-level callback objects: they must outlive every hierarchy that uses them
+TORCH_ALLOC = ALLOC_FN(_torch_alloc)
+TORCH_DEALLOC = DEALLOC_FN(_torch_dealloc)
+
+
+def use_torch_allocator(p: rn_params, stream=None) -> rn_params:
+    """Route every device allocation of a hierarchy set up with p through
+    torch's caching allocator (rn_params alloc/dealloc hooks), on `stream`
+    (default: torch's current stream), so the library shares torch's memory
+    pool instead of holding a pool of its own."""
+    import torch
+
+    p.alloc = TORCH_ALLOC
+    p.dealloc = TORCH_DEALLOC
+    p.alloc_ctx = None
+    if stream is None and not p.stream:
+        stream = torch.cuda.current_stream().cuda_stream
+    if stream is not None:
+        p.stream = C.c_void_p(stream)
+    return p
 
 
 class Hierarchy:

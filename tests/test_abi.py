@@ -64,6 +64,21 @@ def test_setup_rejects_bad_arguments_without_gpu(rn):
     rn.rn_free(None)
 
 
+def test_allocator_hooks_must_come_in_pairs(rn):
+    """alloc without dealloc (or the reverse) is rejected before any allocation."""
+    A = rn.rn_csr(4, 4, 4, C.c_void_p(8), C.c_void_p(8), C.c_void_p(8))
+    h = C.c_void_p()
+    p = rn.default_params()
+    assert not p.alloc and not p.dealloc and p.alloc_ctx is None
+    p.alloc = rn.TORCH_ALLOC
+    assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, 1, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
+    assert b"alloc and dealloc" in rn.rn_last_error()
+    p = rn.default_params()
+    p.dealloc = rn.TORCH_DEALLOC
+    assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, 1, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
+    assert h.value is None
+
+
 def test_status_strings(rn):
     for i, name in enumerate(rn.STATUS_NAMES):
         assert rn.rn_status_string(i).decode() == name
