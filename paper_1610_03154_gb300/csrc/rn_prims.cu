@@ -265,40 +265,31 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t *out_excl, int64_t *s
     return total;
 }
 
-__global__ void scan_block_sums(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ sums) {
-    __shared__ int64_t smem[32];
-    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
-    int64_t v = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; k++)
-        if (base + k < n) v += in[base + k];
-    int64_t ex;
-    int64_t tot = block_exclusive_scan(v, &ex, smem);
-    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
+// Single-pass exclusive scan with decoupled look-back (Merrill and Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016): tiles of
+// kScanChunk counts are claimed in order through a ticket, so every tile a
+// block waits on belongs to a block that is already running; each tile
+// publishes its sum, then its inclusive prefix, in one word of tile_state
+// (flag in the top two bits).  A block that has waited kScanMaxSpin polls
+// for a predecessor sums the raw counts before its tile instead, so the scan
+// always ends.
+constexpr unsigned long long kScanAgg = 1ull << 62, kScanPre = 2ull << 62, kScanVal = (1ull << 62) - 1;
+constexpr uint32_t kScanMaxSpin = 1u << 22;
 
-__global__ void scan_sums(int64_t *__restrict__ sums, int64_t nb, int64_t *__restrict__ total) {
+__global__ void __launch_bounds__(kScanThreads)
+scan_onepass_kernel(const int32_t *__restrict__ in, int64_t n, int32_t *__restrict__ out, int64_t *__restrict__ total,
+                    unsigned long long *__restrict__ state, unsigned int *__restrict__ ticket, int64_t ntiles) {
     __shared__ int64_t smem[32];
-    // each thread takes a contiguous slice of the block sums
-    int64_t per = (nb + blockDim.x - 1) / blockDim.x;
-    int64_t lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
-    int64_t v = 0;
-    for (int64_t i = lo; i < hi; i++) v += sums[i];
-    int64_t ex;
-    int64_t tot = block_exclusive_scan(v, &ex, smem);
-    int64_t run = ex;
-    for (int64_t i = lo; i < hi; i++) {
-        int64_t t = sums[i];
-        sums[i] = run;
-        run += t;
+    __shared__ unsigned int tile_sh;
+    __shared__ int64_t excl_sh;
+    __shared__ int gave_up;
+    if (threadIdx.x == 0) {
+        tile_sh = atomicAdd(ticket, 1u);
+        gave_up = 0;
     }
-    if (threadIdx.x == 0) *total = tot;
-}
-
-__global__ void scan_apply(const int32_t *__restrict__ in, int64_t n, const int64_t *__restrict__ offs,
-                           const int64_t *__restrict__ total, int32_t *__restrict__ out) {
-    __shared__ int64_t smem[32];
-    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    __syncthreads();
+    const int64_t tile = tile_sh;
+    const int64_t base = tile * kScanChunk + (int64_t)threadIdx.x * kScanItems;
     int32_t vals[kScanItems];
     int64_t v = 0;
 #pragma unroll
@@ -307,23 +298,62 @@ __global__ void scan_apply(const int32_t *__restrict__ in, int64_t n, const int6
         v += vals[k];
     }
     int64_t ex;
-    block_exclusive_scan(v, &ex, smem);
-    int64_t run = offs[blockIdx.x] + ex;
+    const int64_t agg = block_exclusive_scan(v, &ex, smem);
+    if (threadIdx.x == 0) {
+        int64_t pre = 0;
+        if (tile == 0) {
+            atomicExch(&state[0], kScanPre | (unsigned long long)agg);
+        } else {
+            atomicExch(&state[tile], kScanAgg | (unsigned long long)agg);
+            const volatile unsigned long long *st = state;
+            for (int64_t j = tile - 1; j >= 0; j--) {
+                unsigned long long w = st[j];
+                for (uint32_t spin = 0; (w >> 62) == 0 && spin < kScanMaxSpin; spin++) {
+                    __nanosleep(64);
+                    w = st[j];
+                }
+                if ((w >> 62) == 0) {
+                    gave_up = 1;
+                    break;
+                }
+                pre += (int64_t)(w & kScanVal);
+                if ((w >> 62) == 2) break;
+            }
+            if (!gave_up) atomicExch(&state[tile], kScanPre | (unsigned long long)(pre + agg));
+        }
+        excl_sh = pre;
+    }
+    __syncthreads();
+    if (gave_up) {  // sum every count before this tile directly
+        int64_t t = 0;
+        for (int64_t i = threadIdx.x; i < tile * kScanChunk; i += blockDim.x) t += in[i];
+        int64_t dummy;
+        const int64_t pre = block_exclusive_scan(t, &dummy, smem);
+        if (threadIdx.x == 0) {
+            excl_sh = pre;
+            atomicExch(&state[tile], kScanPre | (unsigned long long)(pre + agg));
+        }
+        __syncthreads();
+    }
+    int64_t run = excl_sh + ex;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
         if (base + k < n) out[base + k] = (int32_t)run;
         run += vals[k];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (int32_t)(*total);
+    if (tile == ntiles - 1 && threadIdx.x == 0) {
+        out[n] = (int32_t)(excl_sh + agg);
+        *total = excl_sh + agg;
+    }
 }
 
 void scan_counts_dev(const int32_t *counts, int32_t *out, int64_t n, int64_t *total, cudaStream_t s) {
     int64_t nb = (n + kScanChunk - 1) / kScanChunk;
     if (nb < 1) nb = 1;
-    DVec<int64_t> sums(nb, s);
-    RN_LAUNCH("scan", 4.0 * n, s, scan_block_sums, (int)nb, kScanThreads, 0, counts, n, sums.p);
-    RN_LAUNCH("scan", 8.0 * nb, s, scan_sums, 1, kScanThreads, 0, sums.p, nb, total);
-    RN_LAUNCH("scan", 8.0 * n, s, scan_apply, (int)nb, kScanThreads, 0, counts, n, sums.p, total, out);
+    DVec<unsigned long long> st(nb + 1, s);  // tile words, then the ticket
+    RN_CUDA_CHECK(cudaMemsetAsync(st.p, 0, st.bytes(), s));
+    RN_LAUNCH("scan", 8.0 * n, s, scan_onepass_kernel, (int)nb, kScanThreads, 0, counts, n, out, total, st.p,
+              reinterpret_cast<unsigned int *>(st.p + nb), nb);
 }
 
 int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t s) {
