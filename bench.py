@@ -274,18 +274,18 @@ def main():
     xd = torch.zeros_like(bd)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
-    def params(prec):
+    def params(prec, **over):
         return rn.params_from_config(pr.params, precision=rn.RN_MIXED if prec == "mixed" else rn.RN_FP64,
-                                     outer=rn.RN_OUTER_CG, use_graphs=1)
+                                     outer=rn.RN_OUTER_CG, use_graphs=1, **over)
 
-    def step(prec):
+    def step(prec, **over):
         xd.zero_()
-        h = rn.Hierarchy(rp, ci, va, Bd, params=params(prec), stream=sptr)
+        h = rn.Hierarchy(rp, ci, va, Bd, params=params(prec, **over), stream=sptr)
         info = h.solve(bd, xd, rtol=1e-8, maxit=5000)
         h.close()
         return info
 
-    def timed(prec, k):
+    def timed(prec, k, **over):
         times, infos = [], []
         for _ in range(k):
             flush.fill_(1.0)
@@ -293,7 +293,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            infos.append(step(prec))
+            infos.append(step(prec, **over))
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
@@ -318,6 +318,9 @@ def main():
     torch.cuda.synchronize()
     step_s = job_step_seconds(float(np.mean(times)), dev)
     times_other, infos_other = timed(other, args.steps)
+    # the same step with W(1,1) cycles (Sec. 5.2), one warm-up and one timed step
+    step(prec, gamma=2)
+    times_w, infos_w = timed(prec, 1, gamma=2)
 
     # per-launch device times of the solve's level-0 operations, each timed in
     # isolation with CUDA events on the hierarchy's stream, a 256 MB read before
@@ -412,6 +415,8 @@ def main():
             "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "mixed_setup_vs_fp64": setup_err,
+            "w_cycle": {"step_s": times_w[0], "iters": infos_w[0]["iters"], "rel_res": infos_w[0]["rel_res"],
+                        "cycle": "W(1,1)", "precision": prec},
             "roofline": roofline,
             "level0_launches": kernels,
             "gpu_launches": launches // max(args.steps, 1),

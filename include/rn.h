@@ -63,6 +63,9 @@ enum { RN_DEVICE = 0, RN_HOST = 1 };
 enum { RN_ENERGY_CG = 0, RN_ENERGY_GMRES = 1 };
 enum { RN_FP64 = 0, RN_MIXED = 1 };
 enum { RN_OUTER_STATIONARY = 0, RN_OUTER_CG = 1, RN_OUTER_FGMRES = 2 };
+/* Strength measures (Sec. 3.2): symmetric |a_ij| / sqrt(|a_ii a_jj|) >= theta;
+ * classical (Ruge-Stueben) -a_ij >= theta max_{k != i} (-a_ik).  Both scaled by eq. soc. */
+enum { RN_SOC_SYMMETRIC = 0, RN_SOC_CLASSICAL = 1 };
 
 typedef struct {
     int32_t n_rows, n_cols;
@@ -96,6 +99,9 @@ typedef struct {
     int coarse_cluster;      /* > 0: the cycle on the smallest levels (every operation taking at most
                                 this many passes of one thread-block cluster's threads) runs as one
                                 cluster launch; 0: one launch per operation on every level */
+    int gamma;               /* coarse-grid corrections per level: 1 V-cycle, 2 W-cycle (Sec. 5.2's
+                                W(1,1)); a level whose next level is the coarsest corrects once */
+    int soc_kind;            /* strength measure (Sec. 3.2): RN_SOC_SYMMETRIC or RN_SOC_CLASSICAL */
     void *stream;            /* cudaStream_t */
     /* Device-memory hooks (both NULL: the stream-ordered pool, cudaMallocAsync;
      * one without the other is RN_EINVAL).  alloc(bytes, stream, ctx) returns

@@ -49,6 +49,8 @@ typedef struct {
     int nu_pre, nu_post;
     int precond;       /* 1: Jacobi-preconditioned CG energy minimisation */
     double soc_theta_coarse; /* strength theta on levels >= 1 (< 0: same as soc_theta) */
+    int gamma;         /* coarse-grid corrections per level: 1 V-cycle, 2 W-cycle */
+    int soc_kind;      /* 0 symmetric strength, 1 classical strength */
 } orc_params;
 
 /* Row classes of the interpolation pattern. */
@@ -70,6 +72,7 @@ void orc_free(void *p);
 
 /* ---- setup steps (each exported for pin tests) ---- */
 int orc_strength(const orc_csr *A, double theta, orc_csr *S);
+int orc_strength_classical(const orc_csr *A, double theta, orc_csr *S);
 int orc_aggregate(const orc_csr *S, uint64_t seed, int32_t *agg, int32_t **roots, int32_t *nc);
 uint64_t orc_splitmix64(uint64_t x);
 void orc_smooth_candidates(const orc_csr *A, double *B, int sweeps, double omega);

@@ -76,6 +76,57 @@ int orc_strength(const orc_csr *A, double theta, orc_csr *S) {
     return ORC_OK;
 }
 
+/* Classical strength (Sec. 3.2, the measure of Ruge and Stueben 1987 that
+ * the paper lists beside the symmetric one): j is strong for i when
+ * -a_ij >= theta (1 - g) m_i, m_i = max_{k != i} (-a_ik).  A row whose
+ * off-diagonals are all >= 0 (m_i <= 0) has no strong entry.  Values are
+ * -a_ij / m_i, so the row's largest off-diagonal is 1 (eq. soc); S_ii = 1. */
+int orc_strength_classical(const orc_csr *A, double theta, orc_csr *S) {
+    int32_t n = A->nrows;
+    double thr = theta * (1.0 - ORC_GUARD);
+    double *m = (double *)orc_xmalloc((size_t)n * sizeof(double));
+    int32_t *rowptr = (int32_t *)orc_xcalloc((size_t)n + 1, sizeof(int32_t));
+    for (int32_t i = 0; i < n; i++) {
+        double mi = 0.0;
+        int found = 0;
+        for (int32_t e = A->rowptr[i]; e < A->rowptr[i + 1]; e++) {
+            if (A->col[e] == i) {
+                if (A->val[e] != 0.0) found = 1;
+                continue;
+            }
+            double v = -A->val[e];
+            if (v > mi) mi = v;
+        }
+        if (!found) { free(m); free(rowptr); return ORC_EINVAL; }
+        m[i] = mi;
+        int32_t cnt = 1;
+        for (int32_t e = A->rowptr[i]; e < A->rowptr[i + 1]; e++)
+            if (A->col[e] != i && mi > 0.0 && -A->val[e] >= thr * mi) cnt++;
+        rowptr[i + 1] = rowptr[i] + cnt;
+    }
+    S->nrows = n;
+    S->ncols = n;
+    S->nnz = rowptr[n];
+    S->rowptr = rowptr;
+    S->col = (int32_t *)orc_xmalloc((size_t)S->nnz * sizeof(int32_t));
+    S->val = (double *)orc_xmalloc((size_t)S->nnz * sizeof(double));
+    for (int32_t i = 0; i < n; i++) {
+        int32_t dst = rowptr[i];
+        for (int32_t e = A->rowptr[i]; e < A->rowptr[i + 1]; e++) {
+            int32_t j = A->col[e];
+            if (j == i) {
+                S->col[dst] = i;
+                S->val[dst++] = 1.0;
+            } else if (m[i] > 0.0 && -A->val[e] >= thr * m[i]) {
+                S->col[dst] = j;
+                S->val[dst++] = -A->val[e] / m[i];
+            }
+        }
+    }
+    free(m);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* SplitMix64 mixing function (Steele, Lea, Flood, "Fast splittable
  * pseudorandom number generators", OOPSLA 2014), written from its published
@@ -731,7 +782,8 @@ int orc_setup(const orc_csr *A0, const double *B0, const double *Bhat0, const or
         n = L->A.nrows;
         L->diag = row_diag(&L->A);
         double theta = (lvl > 0 && p->soc_theta_coarse >= 0.0) ? p->soc_theta_coarse : p->soc_theta;
-        rc = orc_strength(&L->A, theta, &L->S);                                  /* strength */
+        rc = p->soc_kind == 1 ? orc_strength_classical(&L->A, theta, &L->S)     /* strength */
+                              : orc_strength(&L->A, theta, &L->S);
         if (rc) break;
         L->agg = (int32_t *)orc_xmalloc((size_t)n * sizeof(int32_t));
         rc = orc_aggregate(&L->S, p->seed + (uint64_t)lvl, L->agg, &L->roots, &L->nc); /* aggregate */

@@ -4,9 +4,11 @@
  *
  * Cycle (Sec. 2, two-grid description and eq. twogrid, applied recursively):
  *   x <- x + omega D^{-1} (b - A x)       nu_pre times
- *   r  = b - A x;  b_c = R r
- *   x_c = 0; recurse (coarsest: dense LU solve)
- *   x <- x + P x_c
+ *   gamma times (V-cycle 1, W-cycle 2; once when the next level is the
+ *   coarsest, whose exact solve leaves R (b - A x) = 0 for a second pass):
+ *     r  = b - A x;  b_c = R r
+ *     x_c = 0; recurse (coarsest: dense LU solve)
+ *     x <- x + P x_c
  *   x <- x + omega D^{-1} (b - A x)       nu_post times
  * Outer: 0 stationary cycling, 1 CG preconditioned by one cycle, 2 GMRES(m)
  * right-preconditioned by one cycle (flexible form, Saad 1993, which equals
@@ -78,15 +80,19 @@ void orc_vcycle(const orc_hier *h, int lvl, const double *b, double *x) {
     }
     double *tmp = (double *)orc_xmalloc((size_t)n * sizeof(double));
     for (int s = 0; s < h->p.nu_pre; s++) jacobi(&L->A, L->diag, b, x, h->p.omega, tmp);
-    orc_spmv(&L->A, x, tmp);
-    for (int32_t i = 0; i < n; i++) tmp[i] = b[i] - tmp[i];
     int32_t nc = L->nc;
     double *bc = (double *)orc_xmalloc((size_t)nc * sizeof(double));
-    double *xc = (double *)orc_xcalloc((size_t)nc, sizeof(double));
-    orc_spmv(&L->R, tmp, bc);
-    orc_vcycle(h, lvl + 1, bc, xc);
-    orc_spmv(&L->P, xc, tmp);
-    for (int32_t i = 0; i < n; i++) x[i] = x[i] + tmp[i];
+    double *xc = (double *)orc_xmalloc((size_t)nc * sizeof(double));
+    const int passes = (lvl + 1 == h->nlev - 1 || h->p.gamma < 1) ? 1 : h->p.gamma;
+    for (int c = 0; c < passes; c++) {
+        orc_spmv(&L->A, x, tmp);
+        for (int32_t i = 0; i < n; i++) tmp[i] = b[i] - tmp[i];
+        orc_spmv(&L->R, tmp, bc);
+        memset(xc, 0, (size_t)nc * sizeof(double));
+        orc_vcycle(h, lvl + 1, bc, xc);
+        orc_spmv(&L->P, xc, tmp);
+        for (int32_t i = 0; i < n; i++) x[i] = x[i] + tmp[i];
+    }
     for (int s = 0; s < h->p.nu_post; s++) jacobi(&L->A, L->diag, b, x, h->p.omega, tmp);
     free(bc);
     free(xc);

@@ -61,6 +61,8 @@ extern "C" rn_status rn_default_params(rn_params *p) {
     p->use_graphs = 1;
     p->keep_aux = 0;
     p->coarse_cluster = 0;
+    p->gamma = 1;
+    p->soc_kind = RN_SOC_SYMMETRIC;
     p->stream = nullptr;
     return RN_OK;
 }
@@ -79,6 +81,8 @@ static void check_params(const rn_params *p) {
     if (p->outer == RN_OUTER_FGMRES && (p->restart < 1 || p->restart > 1000)) fail(RN_EINVAL, "restart");
     if (!(p->omega > 0.0)) fail(RN_EINVAL, "omega must be > 0");
     if (p->coarse_cluster < 0) fail(RN_EINVAL, "coarse_cluster must be >= 0");
+    if (p->gamma != 1 && p->gamma != 2) fail(RN_EINVAL, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
+    if (p->soc_kind != RN_SOC_SYMMETRIC && p->soc_kind != RN_SOC_CLASSICAL) fail(RN_EINVAL, "soc_kind");
     if ((p->alloc == nullptr) != (p->dealloc == nullptr))
         fail(RN_EINVAL, "alloc and dealloc must both be set or both be NULL");
 }
@@ -266,6 +270,7 @@ extern "C" rn_status rn_solve_multi(rn_hierarchy *h, const double *B, double *X,
     using rn::fail;
     if (!h || !B || !X) fail(RN_EINVAL, "null argument");
     if (s < 1 || s > 2048) fail(RN_EINVAL, "s must be in [1, 2048]");
+    if (h->p.gamma != 1) fail(RN_EINVAL, "the many-right-hand-side cycle is a V-cycle (gamma 1)");
     if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
     if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
     const rn::AllocScope alloc_scope(alloc_of(h->p));

@@ -227,7 +227,7 @@ static void prepare_sub_t(rn_hierarchy &h) {
     const int L = (int)h.lev.size();
     const int maxp = h.p.coarse_cluster;
     h.sub_k = -1;
-    if (maxp <= 0 || L < 3 || h.lev[L - 1]->A.n > kSubMaxCoarse) return;
+    if (maxp <= 0 || L < 3 || h.lev[L - 1]->A.n > kSubMaxCoarse || h.p.gamma != 1) return;  // V-cycles only
     const int cs = cluster_size_for<T>();
     if (cs == 0) return;
     const int nthr = cs * kClusterThreads;

@@ -68,17 +68,36 @@ __device__ __forceinline__ bool soc_strong(double aij, double di, double dj, dou
 // the diagonal), each strong entry's value v in vtmp (-1 for the others) and
 // the row's largest strong value.  Pass 2: S's columns, and values v / vmax
 // (1 on the diagonal).
+// With classical (pass 1 only): v = -a_ij is strong when the row's largest
+// such value m_i is positive and v >= thr m_i; vmaxv[i] = m_i, so pass 2
+// writes -a_ij / m_i.
 template <bool FILL>
 __global__ void strength_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                                 const double *__restrict__ aval, const double *__restrict__ diag, double thr,
                                 int32_t *__restrict__ count, double *__restrict__ vtmp, double *__restrict__ vmaxv,
                                 const int32_t *__restrict__ srp, int32_t *__restrict__ scol,
-                                double *__restrict__ sval) {
+                                double *__restrict__ sval, int classical) {
     const bool fast = thr >= 0x1p-10 && thr <= 0x1p10;  // thr^2 stays a normal FP32 number
     const float thr2f = (float)(thr * thr);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t e0 = arp[i], e1 = arp[i + 1];
-        if (!FILL) {
+        if (!FILL && classical) {
+            double m = 0.0;
+            for (int32_t e = e0; e < e1; e++)
+                if (acol[e] != i && -aval[e] > m) m = -aval[e];
+            const double cut = __dmul_rn(thr, m);
+            int32_t c = 1;
+            for (int32_t e = e0; e < e1; e++) {
+                double v = -1.0;
+                if (acol[e] != i && m > 0.0 && -aval[e] >= cut) {
+                    v = -aval[e];
+                    c++;
+                }
+                vtmp[e] = v;
+            }
+            count[i] = c;
+            vmaxv[i] = m;
+        } else if (!FILL) {
             const double di = diag[i];
             int32_t c = 1;
             double vmax = 0.0;
@@ -982,14 +1001,15 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             DVec<int32_t> cnt(n + 1, s);
             DVec<double> vtmp(A.nnz, s), vmax(n, s);
             RN_LAUNCH("strength", 20.0 * A.nnz + 20.0 * n, s, strength_kernel<false>, rows_grid(n), kT, 0, n,
-                      A.rowptr, A.col, A.val, L.diag.p, thr, cnt.p, vtmp.p, vmax.p, nullptr, nullptr, nullptr);
+                      A.rowptr, A.col, A.val, L.diag.p, thr, cnt.p, vtmp.p, vmax.p, nullptr, nullptr, nullptr,
+                      p.soc_kind == RN_SOC_CLASSICAL ? 1 : 0);
             S.rowptr.alloc(n + 1, s);
             S.nnz = scan_counts(cnt.p, S.rowptr.p, n, s);
             S.col.alloc(S.nnz, s);
             S.val.alloc(S.nnz, s);
             RN_LAUNCH("strength", 12.0 * A.nnz + 12.0 * n + 12.0 * S.nnz, s, strength_kernel<true>, rows_grid(n), kT,
                       0, n, A.rowptr, A.col, A.val, L.diag.p, thr, nullptr, vtmp.p, vmax.p, S.rowptr.p, S.col.p,
-                      S.val.p);
+                      S.val.p, 0);
         }
         // ---- aggregation graph and seeded MIS-2 (line 'aggregate')
         DCsr Gr;

@@ -448,6 +448,12 @@ static T *relax0_and_residual(rn_hierarchy &h, const CycleNames &nm, rn_level &L
 template <typename T>
 static T *vcycle_level(rn_hierarchy &h, int l);
 
+// Coarse-grid corrections on level l: gamma (1 V-cycle, 2 W-cycle), but one
+// when level l+1 is the coarsest: its exact solve leaves R (b - A x) = 0.
+static int corrections(const rn_hierarchy &h, int l) {
+    return l + 2 >= (int)h.lev.size() ? 1 : h.p.gamma;
+}
+
 // Coarse-grid correction of level l: b_{l+1} = R_l r, the cycle on level
 // l+1, cur += P_l x_{l+1}.  From the cluster's level on, all of it (transfers
 // included) is one cluster launch.
@@ -490,6 +496,10 @@ static T *vcycle_level(rn_hierarchy &h, int l) {
     T *cur = relax0_and_residual<T, T>(h, nm, L, b, r);
     T *oth = (cur == LB::x(L)) ? LB::t(L) : LB::x(L);
     coarse_correction<T>(h, l, r, cur);
+    for (int c = 1; c < corrections(h, l); c++) {  // W-cycle: correct again from the new residual
+        spmv<T, T, T, OP_RESID>(h, nm.resid, L.A, cur, b, nullptr, T(0), r, none);
+        coarse_correction<T>(h, l, r, cur);
+    }
     for (int k = 0; k < h.p.nu_post; k++) {
         spmv<T, T, T, OP_JACOBI>(h, nm.jacobi, L.A, cur, b, d, omega, oth, none);
         std::swap(cur, oth);
@@ -521,6 +531,10 @@ static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fi
     T *cur = relax0_and_residual<T, double>(h, nm, L, rhs, r, x0_ready);
     T *oth = (cur == LB::x(L)) ? LB::t(L) : LB::x(L);
     coarse_correction<T>(h, 0, r, cur);
+    for (int c = 1; c < corrections(h, 0); c++) {
+        spmv<T, double, T, OP_RESID>(h, nm.resid, L.A, cur, rhs, nullptr, T(0), r, none);
+        coarse_correction<T>(h, 0, r, cur);
+    }
     const int npost = h.p.nu_post;
     for (int k = 0; k < npost; k++) {
         if (k == npost - 1) {
@@ -583,11 +597,15 @@ void apply_cycle(rn_hierarchy &h, const double *rhs, double *out) {
     if (out != h.graph_out) d2d(out, h.graph_out, n, s);
 }
 
-static void set_tile_group(rn_hierarchy &h, DCsr &M, int32_t *tmp) {
+// Longest row of M into *slot (one launch; the caller reads all slots at once).
+static void launch_maxlen(rn_hierarchy &h, const DCsr &M, int32_t *slot) {
     if (M.n == 0) return;
-    RN_CUDA_CHECK(cudaMemsetAsync(tmp, 0, sizeof(int32_t), h.s));
-    RN_LAUNCH("prepare", 4.0 * M.n, h.s, row_maxlen_kernel, grid_for(M.n, 1024), 256, 0, M.n, M.rowptr.p, tmp);
-    M.maxlen = read_scalar(tmp, h.s);
+    RN_LAUNCH("prepare", 4.0 * M.n, h.s, row_maxlen_kernel, grid_for(M.n, 1024), 256, 0, M.n, M.rowptr.p, slot);
+}
+
+static void set_tile_group(DCsr &M, int32_t maxlen) {
+    if (M.n == 0) return;
+    M.maxlen = maxlen;
     M.tile_group = tile_group(M.maxlen, tile_nnz<float>());
     M.tile_group64 = tile_group(M.maxlen, tile_nnz<double>());
 }
@@ -604,7 +622,18 @@ __global__ void omega_over_diag_kernel(int64_t n, double omega, const double *__
 void prepare_solve(rn_hierarchy &h) {
     cudaStream_t s = h.s;
     const bool mixed = h.p.precision == RN_MIXED;
-    DVec<int32_t> tmp(1, s);
+    // longest rows of every level's A, P and R: one read-back for all
+    const size_t nmat = 3 * h.lev.size();
+    DVec<int32_t> ml(nmat, s);
+    RN_CUDA_CHECK(cudaMemsetAsync(ml.p, 0, ml.bytes(), s));
+    for (size_t l = 0; l < h.lev.size(); l++) {
+        launch_maxlen(h, h.lev[l]->A, ml.p + 3 * l);
+        launch_maxlen(h, h.lev[l]->P, ml.p + 3 * l + 1);
+        launch_maxlen(h, h.lev[l]->R, ml.p + 3 * l + 2);
+    }
+    std::vector<int32_t> mlh(nmat);
+    RN_CUDA_CHECK(cudaMemcpyAsync(mlh.data(), ml.p, ml.bytes(), cudaMemcpyDeviceToHost, s));
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
     for (size_t l = 0; l < h.lev.size(); l++) {
         rn_level &L = *h.lev[l];
         const int32_t n = L.A.n;
@@ -612,9 +641,9 @@ void prepare_solve(rn_hierarchy &h) {
         L.x.alloc(n, s);
         L.t.alloc(n, s);
         L.r.alloc(n, s);
-        set_tile_group(h, L.A, tmp.p);
-        set_tile_group(h, L.P, tmp.p);
-        set_tile_group(h, L.R, tmp.p);
+        set_tile_group(L.A, mlh[3 * l]);
+        set_tile_group(L.P, mlh[3 * l + 1]);
+        set_tile_group(L.R, mlh[3 * l + 2]);
         if (mixed) {
             L.b32.alloc(n, s);
             L.x32.alloc(n, s);

@@ -22,6 +22,7 @@ RN_ENERGY_CG, RN_ENERGY_GMRES = 0, 1
 RN_FP64, RN_MIXED = 0, 1
 RN_OUTER_STATIONARY, RN_OUTER_CG, RN_OUTER_FGMRES = 0, 1, 2
 RN_MAX_LEVELS = 32
+RN_SOC_SYMMETRIC, RN_SOC_CLASSICAL = 0, 1
 (RN_OP_OUTER_SPMV, RN_OP_RELAX0_RESIDUAL, RN_OP_JACOBI_OUT, RN_OP_RESTRICT, RN_OP_PROLONG, RN_OP_CG_XR,
  RN_OP_CG_RZ, RN_OP_CG_P, RN_OP_COARSE_CLUSTER, RN_OP_COUNT) = range(10)
 STATUS_NAMES = ["RN_OK", "RN_EINVAL", "RN_ENOMEM", "RN_ESINGULAR", "RN_ESTALL", "RN_ENOTCONV", "RN_ETIMEOUT",
@@ -44,7 +45,7 @@ class rn_params(C.Structure):
                 ("max_levels", C.c_int), ("b_sweeps", C.c_int), ("omega", C.c_double), ("seed", C.c_uint64),
                 ("symmetric", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int), ("precision", C.c_int),
                 ("outer", C.c_int), ("restart", C.c_int), ("use_graphs", C.c_int), ("keep_aux", C.c_int),
-                ("coarse_cluster", C.c_int), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("dealloc", DEALLOC_FN),
+                ("coarse_cluster", C.c_int), ("gamma", C.c_int), ("soc_kind", C.c_int), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("dealloc", DEALLOC_FN),
                 ("alloc_ctx", C.c_void_p)]
 
 
@@ -232,7 +233,7 @@ def params_from_config(cfg: dict, **overrides) -> rn_params:
               seed=m.get("seed", 12345), symmetric=m.get("symmetric", 1), nu_pre=m.get("nu_pre", 1),
               nu_post=m.get("nu_post", 1), precision=m.get("precision", RN_FP64), outer=m.get("outer", RN_OUTER_CG),
               restart=m.get("restart", 30), use_graphs=m.get("use_graphs", 1), keep_aux=m.get("keep_aux", 0),
-              coarse_cluster=m.get("coarse_cluster", 0))
+              coarse_cluster=m.get("coarse_cluster", 0), gamma=m.get("gamma", 1), soc_kind=m.get("soc_kind", 0))
     return default_params(**kw)
 
 

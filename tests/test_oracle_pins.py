@@ -644,3 +644,125 @@ def test_adjoint_reference_operator_matches_generator():
     A, f = PR.varcoef_fv(m, th)
     B = ar.operator(m, th)
     assert np.max(np.abs((A.to_scipy() - B).toarray())) < 1e-13
+
+
+def _classical_dense(A, theta):
+    """Classical strength written out row by row (the measure of Ruge and
+    Stueben the paper lists in Sec. 3.2), for the pins below."""
+    A = A.tocsr()
+    n = A.shape[0]
+    thr = theta * (1.0 - 1e-10)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        idx = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        dat = A.data[A.indptr[i]:A.indptr[i + 1]]
+        m = max([-v for j, v in zip(idx, dat) if j != i] + [0.0])
+        for j, v in zip(idx, dat):
+            if j == i:
+                rows.append(i), cols.append(i), vals.append(1.0)
+            elif m > 0.0 and -v >= thr * m:
+                rows.append(i), cols.append(j), vals.append(-v / m)
+    return sp.csr_matrix((vals, (rows, cols)), shape=A.shape)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_classical_strength_bruteforce(oracle, seed):
+    # mixed-sign off-diagonals, rows whose off-diagonals are all positive
+    # (no strong entry), exact ties at theta
+    rng = np.random.default_rng(seed)
+    n = 40
+    M = sp.random(n, n, density=0.15, random_state=seed, data_rvs=lambda k: rng.choice([-2.0, -1.0, -0.5, 0.5, 1.0], k))
+    M = M.tolil()
+    for i in range(0, n, 7):  # positive off-diagonals only
+        for j in M.rows[i]:
+            if j != i:
+                M[i, j] = abs(M[i, j])
+    M = M.tocsr() + sp.identity(n) * 5.0
+    M.sort_indices()
+    for theta in (0.25, 0.5):
+        S = oracle.strength_classical(M, theta)
+        R = _classical_dense(M, theta)
+        R.sort_indices()
+        assert np.array_equal(S.indptr, R.indptr) and np.array_equal(S.indices, R.indices)
+        assert np.array_equal(S.data, R.data)
+
+
+def test_classical_strength_special_cases(oracle):
+    # 5-point Laplacian: every off-diagonal is the row's largest negative one
+    A = PR.poisson5(10).to_scipy()
+    S = oracle.strength_classical(A, 0.25)
+    assert np.array_equal(S.indptr, A.indptr) and np.array_equal(S.indices, A.indices)
+    assert np.all(S.data == 1.0)
+    # grid-aligned Q1 anisotropy, eps = 1e-3: the x-neighbours (-2/3 + eps/3) and
+    # the corners (-(1 + eps)/6 >= theta (2/3 - eps/3)) are strong; the
+    # y-neighbours (1/3 - 2 eps/3 > 0) are positive and never strong
+    ne = 9
+    m = ne - 1
+    A = PR.q1_aniso(ne, 1e-3, 0.0).to_scipy()
+    S = oracle.strength_classical(A, 0.25)
+    for i in range(A.shape[0]):
+        cols = set(S.indices[S.indptr[i]:S.indptr[i + 1]].tolist())
+        nb = set(A.indices[A.indptr[i]:A.indptr[i + 1]].tolist())
+        vertical = {j for j in nb if j % m == i % m and j != i}
+        assert cols == nb - vertical
+
+
+def test_classical_strength_drives_setup(oracle):
+    pr = PR.aniso_problem(48)
+    params = dict(pr.params)
+    params["soc_kind"] = 1
+    h = oracle.Hierarchy(pr.A.to_scipy(), pr.B, keep_aux=1, **params)
+    S0 = oracle.strength_classical(pr.A.to_scipy(), params.get("soc_theta", 0.25))
+    assert (h.levels[0].S != S0).nnz == 0
+    assert len(h.levels) >= 3
+
+
+def _cycle_dense(levels, gamma, omega, b, nu=(1, 1)):
+    """The cycle x = B_0 b (zero initial guess) by its recursive definition,
+    with dense matrices (Sec. 2: smoothing, coarse-grid correction, smoothing;
+    gamma corrections per level, one when the next level is the coarsest)."""
+    def cyc(l, rhs):
+        A = levels[l].A.toarray()
+        if l == len(levels) - 1:
+            return np.linalg.solve(A, rhs)
+        d = np.diag(A)
+        P, R = levels[l].P.toarray(), levels[l].R.toarray()
+        x = np.zeros_like(rhs)
+        for _ in range(nu[0]):
+            x = x + omega * ((rhs - A @ x) / d)
+        for _ in range(1 if l + 1 == len(levels) - 1 else gamma):
+            x = x + P @ cyc(l + 1, R @ (rhs - A @ x))
+        for _ in range(nu[1]):
+            x = x + omega * ((rhs - A @ x) / d)
+        return x
+    return cyc(0, b)
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_cycle_matches_dense_recursion(oracle, gamma):
+    pr = PR.poisson_problem(32)
+    params = dict(pr.params)
+    params["gamma"] = gamma
+    params["max_coarse"] = 30
+    h = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **params)
+    assert len(h.levels) >= 4
+    b = np.random.default_rng(3).standard_normal(pr.A.n_rows)
+    got = h.vcycle(b, np.zeros_like(b))
+    ref = _cycle_dense(h.levels, gamma, params.get("omega", 2.0 / 3.0), b)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_w_cycle_differs_from_v_and_converges_faster(oracle):
+    pr = PR.poisson_problem(32)
+    out = {}
+    for gamma in (1, 2):
+        params = dict(pr.params, gamma=gamma, max_coarse=30)
+        h = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **params)
+        x, info = h.solve(pr.b, tol=1e-8, outer=0)
+        out[gamma] = info["iters"]
+    assert out[2] <= out[1]
+    params = dict(pr.params, max_coarse=200)  # two levels: W and V coincide
+    hv = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **dict(params, gamma=1))
+    hw = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **dict(params, gamma=2))
+    b = np.random.default_rng(4).standard_normal(pr.A.n_rows)
+    assert np.array_equal(hv.vcycle(b, np.zeros_like(b)), hw.vcycle(b, np.zeros_like(b)))
