@@ -49,7 +49,7 @@ class _Params(C.Structure):
                 ("prefilter", C.c_double), ("postfilter", C.c_double), ("max_coarse", C.c_int),
                 ("max_levels", C.c_int), ("b_sweeps", C.c_int), ("omega", C.c_double), ("seed", C.c_uint64),
                 ("symmetric", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int), ("precond", C.c_int),
-                ("soc_theta_coarse", C.c_double), ("gamma", C.c_int), ("soc_kind", C.c_int)]
+                ("soc_theta_coarse", C.c_double), ("gamma", C.c_int), ("soc_kind", C.c_int), ("ncand", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -70,6 +70,12 @@ def lib():
         L.orc_free.argtypes = [C.c_void_p]
         L.orc_strength.argtypes = [P(_CSR), C.c_double, P(_CSR)]
         L.orc_strength_classical.argtypes = [P(_CSR), C.c_double, P(_CSR)]
+        L.orc_tentative_k.argtypes = [P(_CSR), i32p, i32p, i32p, dp, C.c_int, dp]
+        L.orc_project_k.argtypes = [P(_CSR), i32p, dp, C.c_int]
+        L.orc_enforce_k.argtypes = [P(_CSR), i32p, dp, dp, C.c_int]
+        L.orc_energy_min_cg_k.argtypes = [P(_CSR), P(_CSR), i32p, dp, C.c_int, C.c_int, C.c_int, dp]
+        L.orc_smooth_candidates_k.argtypes = [P(_CSR), dp, C.c_int, C.c_int, C.c_double]
+        L.orc_sym_pinv.argtypes = [C.c_int, dp, dp]
         L.orc_aggregate.argtypes = [P(_CSR), C.c_uint64, i32p, P(i32p), i32p]
         L.orc_splitmix64.argtypes = [C.c_uint64]
         L.orc_splitmix64.restype = C.c_uint64
@@ -220,6 +226,44 @@ def masked_product(A, X) -> sp.csr_matrix:
     return sp.csr_matrix((w.val, w.col, w.rowptr), shape=X.shape)
 
 
+def sym_pinv(G: np.ndarray) -> np.ndarray:
+    G = np.ascontiguousarray(G, np.float64)
+    k = G.shape[0]
+    out = np.zeros((k, k))
+    lib().orc_sym_pinv(k, _dp(G), _dp(out))
+    return out
+
+
+def tentative_k(N, agg, roots, rowtype, B):
+    """T and Bc (nc x k) for the k columns of B (n x k)."""
+    n = _In(N)
+    B = np.ascontiguousarray(B, np.float64)
+    k = B.shape[1]
+    agg = np.ascontiguousarray(agg, np.int32)
+    roots = np.ascontiguousarray(roots, np.int32)
+    rt = np.ascontiguousarray(rowtype, np.int32)
+    Bc = np.zeros((N.shape[1], k))
+    _check(lib().orc_tentative_k(C.byref(n.s), _ip(agg), _ip(roots), _ip(rt), _dp(B.reshape(-1)), k, _dp(Bc)),
+           "tentative_k")
+    return sp.csr_matrix((n.val.copy(), n.col.copy(), n.rowptr.copy()), shape=N.shape), Bc
+
+
+def project_k(W, rowtype, Bc) -> sp.csr_matrix:
+    w = _In(W)
+    Bc = np.ascontiguousarray(Bc, np.float64)
+    lib().orc_project_k(C.byref(w.s), _ip(np.ascontiguousarray(rowtype, np.int32)), _dp(Bc), Bc.shape[1])
+    return sp.csr_matrix((w.val, w.col, w.rowptr), shape=W.shape)
+
+
+def energy_min_cg_k(A, P0, rowtype, Bc, sweeps: int, precond: int = 1):
+    a, p = _In(A), _In(P0)
+    Bc = np.ascontiguousarray(Bc, np.float64)
+    trace = np.zeros(sweeps + 1)
+    _check(lib().orc_energy_min_cg_k(C.byref(a.s), C.byref(p.s), _ip(np.ascontiguousarray(rowtype, np.int32)),
+                                     _dp(Bc), Bc.shape[1], sweeps, precond, _dp(trace)), "energy_min_cg_k")
+    return sp.csr_matrix((p.val, p.col, p.rowptr), shape=P0.shape), trace
+
+
 def project(W, rowtype, Bc) -> sp.csr_matrix:
     w = _In(W)
     rt = np.ascontiguousarray(rowtype, np.int32)
@@ -296,7 +340,7 @@ def lu_solve_dense(M: np.ndarray, rhs: np.ndarray) -> np.ndarray:
 def make_params(**kw) -> _Params:
     d = dict(soc_theta=0.25, degree=2, n_sweeps=4, method=0, prefilter=0.0, postfilter=0.0, max_coarse=64,
              max_levels=25, b_sweeps=4, omega=2.0 / 3.0, seed=12345, symmetric=1, nu_pre=1, nu_post=1, precond=1,
-             soc_theta_coarse=-1.0, gamma=1, soc_kind=0)
+             soc_theta_coarse=-1.0, gamma=1, soc_kind=0, ncand=1)
     for k, v in kw.items():
         if k in d:
             d[k] = v
@@ -350,10 +394,15 @@ class Hierarchy:
                 p = L.orc_hier_ivec(h, l, which, C.byref(ln))
                 return np.ctypeslib.as_array(p, shape=(ln.value,)).copy() if p and ln.value > 0 else None
 
+            kc = max(1, int(params.get("ncand", 1)))
+
             def dvec(which):
                 ln = C.c_int32()
                 p = L.orc_hier_dvec(h, l, which, C.byref(ln))
-                return np.ctypeslib.as_array(p, shape=(ln.value,)).copy() if p and ln.value > 0 else None
+                if not (p and ln.value > 0):
+                    return None
+                v = np.ctypeslib.as_array(p, shape=(ln.value,)).copy()
+                return v if kc == 1 else v.reshape(-1, kc)
 
             self.levels.append(Level(A=csr(0), S=csr(1), N=csr(2), T=csr(3), P=csr(4), R=csr(5), agg=ivec(0),
                                      roots=ivec(1), rowtype=ivec(2), B=dvec(0), Bc=dvec(1), Bhat=dvec(2),

@@ -51,6 +51,7 @@ typedef struct {
     double soc_theta_coarse; /* strength theta on levels >= 1 (< 0: same as soc_theta) */
     int gamma;         /* coarse-grid corrections per level: 1 V-cycle, 2 W-cycle */
     int soc_kind;      /* 0 symmetric strength, 1 classical strength */
+    int ncand;         /* k, the number of candidate vectors (B is n x k, row-major) */
 } orc_params;
 
 /* Row classes of the interpolation pattern. */
@@ -80,6 +81,17 @@ int orc_pattern(const orc_csr *S, const int32_t *agg, const int32_t *roots, int3
                 double theta_pre, orc_csr *N);
 void orc_row_types(int32_t n, const int32_t *agg, const int32_t *roots, int32_t nc, int32_t *rowtype);
 int orc_tentative(orc_csr *N, const int32_t *agg, const int32_t *roots, const double *B, double *Bc);
+/* k candidates: B n x k, Bc nc x k (row-major) */
+void orc_smooth_candidates_k(const orc_csr *A, double *B, int k, int sweeps, double omega);
+int orc_tentative_k(orc_csr *N, const int32_t *agg, const int32_t *roots, const int32_t *rowtype, const double *B,
+                    int k, double *Bc);
+void orc_project_k(orc_csr *W, const int32_t *rowtype, const double *Bc, int k);
+void orc_enforce_k(orc_csr *P, const int32_t *rowtype, const double *B, const double *Bc, int k);
+int orc_energy_min_cg_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc, int k,
+                        int sweeps, int precond, double *energy_trace);
+int orc_energy_min_gmres_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc, int k,
+                           int m, double *res_trace);
+void orc_sym_pinv(int k, const double *G, double *Gp);
 void orc_masked_product(const orc_csr *A, const orc_csr *X, orc_csr *W);
 void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc);
 int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc,

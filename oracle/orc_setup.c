@@ -434,6 +434,146 @@ void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc) {
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* k > 1 candidates (Sec. 3.6, eq. Tproj): every row-wise fit and projection
+ * uses the k x k Gram matrix G_i = Bc_J^T Bc_J of the row's pattern J and its
+ * pseudo-inverse (min-norm least squares; the system is underdetermined when
+ * |J| >= k and Bc_J has full rank).  k = 1 keeps the scalar formulas above. */
+
+/* Pseudo-inverse of a symmetric k x k matrix (k <= ORC_KMAX, row-major) by the
+ * cyclic Jacobi eigenvalue method (rotations zeroing one off-diagonal pair at
+ * a time until the off-diagonal mass is negligible); eigenvalues at most
+ * 1e-12 of the largest are dropped. */
+#define ORC_KMAX 8
+void orc_sym_pinv(int k, const double *G, double *Gp) {
+    double a[ORC_KMAX * ORC_KMAX], v[ORC_KMAX * ORC_KMAX];
+    for (int i = 0; i < k * k; i++) a[i] = G[i];
+    for (int i = 0; i < k; i++)
+        for (int j = 0; j < k; j++) v[i * k + j] = (i == j);
+    for (int sweep = 0; sweep < 64; sweep++) {
+        double off = 0.0, dia = 0.0;
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < k; j++) {
+                if (i == j) dia += a[i * k + i] * a[i * k + i];
+                else off += a[i * k + j] * a[i * k + j];
+            }
+        if (off <= 1e-32 * dia || off == 0.0) break;
+        for (int p = 0; p < k - 1; p++)
+            for (int q = p + 1; q < k; q++) {
+                double apq = a[p * k + q];
+                if (apq == 0.0) continue;
+                double th = (a[q * k + q] - a[p * k + p]) / (2.0 * apq);
+                double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int r = 0; r < k; r++) { /* columns p, q of a */
+                    double arp = a[r * k + p], arq = a[r * k + q];
+                    a[r * k + p] = c * arp - sn * arq;
+                    a[r * k + q] = sn * arp + c * arq;
+                }
+                for (int r = 0; r < k; r++) { /* rows p, q of a */
+                    double apr = a[p * k + r], aqr = a[q * k + r];
+                    a[p * k + r] = c * apr - sn * aqr;
+                    a[q * k + r] = sn * apr + c * aqr;
+                }
+                for (int r = 0; r < k; r++) { /* eigenvectors: columns of v */
+                    double vrp = v[r * k + p], vrq = v[r * k + q];
+                    v[r * k + p] = c * vrp - sn * vrq;
+                    v[r * k + q] = sn * vrp + c * vrq;
+                }
+            }
+    }
+    double lmax = 0.0;
+    for (int i = 0; i < k; i++) if (fabs(a[i * k + i]) > lmax) lmax = fabs(a[i * k + i]);
+    for (int i = 0; i < k * k; i++) Gp[i] = 0.0;
+    for (int e = 0; e < k; e++) {
+        double lam = a[e * k + e];
+        if (!(lam > 1e-12 * lmax)) continue;
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < k; j++) Gp[i * k + j] += v[i * k + e] * v[j * k + e] / lam;
+    }
+}
+
+/* Min-norm update of one row's values t (pattern columns col[s..e)) so that
+ * (t + u) Bc_J = target (target NULL: 0):  r = target - t Bc_J,
+ * u_j = (r G_i^+) . Bc_j. */
+static void row_fit_k(int32_t s, int32_t e, const int32_t *col, double *val, const double *target,
+                      const double *Bc, int k) {
+    double G[ORC_KMAX * ORC_KMAX] = {0}, Gp[ORC_KMAX * ORC_KMAX], r[ORC_KMAX], y[ORC_KMAX];
+    for (int a = 0; a < k; a++) r[a] = target ? target[a] : 0.0;
+    for (int32_t q = s; q < e; q++) {
+        const double *b = Bc + (size_t)col[q] * k;
+        for (int a = 0; a < k; a++) {
+            r[a] = r[a] - val[q] * b[a];
+            for (int c = 0; c < k; c++) G[a * k + c] += b[a] * b[c];
+        }
+    }
+    orc_sym_pinv(k, G, Gp);
+    for (int c = 0; c < k; c++) {
+        y[c] = 0.0;
+        for (int a = 0; a < k; a++) y[c] += r[a] * Gp[a * k + c];
+    }
+    for (int32_t q = s; q < e; q++) {
+        const double *b = Bc + (size_t)col[q] * k;
+        double u = 0.0;
+        for (int c = 0; c < k; c++) u += y[c] * b[c];
+        val[q] = val[q] + u;
+    }
+}
+
+void orc_smooth_candidates_k(const orc_csr *A, double *B, int k, int sweeps, double omega) {
+    if (k == 1) { orc_smooth_candidates(A, B, sweeps, omega); return; }
+    int32_t n = A->nrows;
+    double *col = (double *)orc_xmalloc((size_t)n * sizeof(double));
+    for (int c = 0; c < k; c++) {  /* each column as the single-candidate case */
+        for (int32_t i = 0; i < n; i++) col[i] = B[(size_t)i * k + c];
+        orc_smooth_candidates(A, col, sweeps, omega);
+        for (int32_t i = 0; i < n; i++) B[(size_t)i * k + c] = col[i];
+    }
+    free(col);
+}
+
+/* T for k candidates: Bc = B(roots, :); the first candidate is injected as
+ * for k = 1 (root rows exactly 1), then every free row is fitted, (t + u) Bc_J
+ * = B_i, on its pattern (eq. Tproj); root rows keep the identity and
+ * unaggregated rows stay zero. */
+int orc_tentative_k(orc_csr *N, const int32_t *agg, const int32_t *roots, const int32_t *rowtype, const double *B,
+                    int k, double *Bc) {
+    if (k == 1) return orc_tentative(N, agg, roots, B, Bc);
+    if (k > ORC_KMAX) return ORC_EINVAL;
+    for (int32_t c = 0; c < N->ncols; c++) {
+        for (int a = 0; a < k; a++) Bc[(size_t)c * k + a] = B[(size_t)roots[c] * k + a];
+        if (fabs(Bc[(size_t)c * k]) < 1e-300) return ORC_EINVAL;
+    }
+    for (int32_t i = 0; i < N->nrows; i++) {
+        for (int32_t e = N->rowptr[i]; e < N->rowptr[i + 1]; e++) {
+            int32_t j = N->col[e];
+            N->val[e] = (j == agg[i]) ? B[(size_t)i * k] / Bc[(size_t)j * k] : 0.0;
+        }
+        if (rowtype[i] == ORC_FREE)
+            row_fit_k(N->rowptr[i], N->rowptr[i + 1], N->col, N->val, B + (size_t)i * k, Bc, k);
+    }
+    return ORC_OK;
+}
+
+void orc_project_k(orc_csr *W, const int32_t *rowtype, const double *Bc, int k) {
+    if (k == 1) { orc_project(W, rowtype, Bc); return; }
+    for (int32_t i = 0; i < W->nrows; i++) {
+        int32_t s = W->rowptr[i], e = W->rowptr[i + 1];
+        if (rowtype[i] != ORC_FREE || e - s == 1) {
+            for (int32_t q = s; q < e; q++) W->val[q] = 0.0;
+            continue;
+        }
+        row_fit_k(s, e, W->col, W->val, NULL, Bc, k);
+    }
+}
+
+void orc_enforce_k(orc_csr *P, const int32_t *rowtype, const double *B, const double *Bc, int k) {
+    if (k == 1) { orc_enforce(P, rowtype, B, Bc); return; }
+    for (int32_t i = 0; i < P->nrows; i++)
+        if (rowtype[i] == ORC_FREE)
+            row_fit_k(P->rowptr[i], P->rowptr[i + 1], P->col, P->val, B + (size_t)i * k, Bc, k);
+}
+
 static double frob_dot(const orc_csr *X, const double *a, const double *b) {
     return orc_dot(X->nnz, a, b);
 }
@@ -472,6 +612,11 @@ static double pattern_energy(const orc_csr *A, const orc_csr *P) {
  */
 int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc,
                       int sweeps, int precond, double *energy_trace) {
+    return orc_energy_min_cg_k(A, P, rowtype, Bc, 1, sweeps, precond, energy_trace);
+}
+
+int orc_energy_min_cg_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc, int k,
+                        int sweeps, int precond, double *energy_trace) {
     int64_t nz = P->nnz;
     double *diag = row_diag(A);
     orc_csr W;
@@ -487,7 +632,7 @@ int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, cons
     for (int32_t i = 0; i < P->nrows; i++) dinv[i] = 1.0 / diag[i];
     if (energy_trace) energy_trace[0] = pattern_energy(A, P);
     orc_masked_product(A, P, &W);
-    orc_project(&W, rowtype, Bc);
+    orc_project_k(&W, rowtype, Bc, k);
     for (int64_t q = 0; q < nz; q++) R[q] = -W.val[q];
     double rho_old = 0.0, rho0 = 0.0;
     for (int it = 0; it < sweeps; it++) {
@@ -505,7 +650,7 @@ int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, cons
             for (int64_t q = 0; q < nz; q++) Dd[q] = Z[q] + beta * Dd[q];
         }
         orc_masked_product(A, &Dm, &W);
-        orc_project(&W, rowtype, Bc);
+        orc_project_k(&W, rowtype, Bc, k);
         double dw = frob_dot(P, Dd, W.val);
         if (dw <= 0.0) { it_done = it; break; }
         double alpha = rho / dw;
@@ -539,6 +684,11 @@ int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, cons
  */
 int orc_energy_min_gmres(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc,
                          int m, double *res_trace) {
+    return orc_energy_min_gmres_k(A, P, rowtype, Bc, 1, m, res_trace);
+}
+
+int orc_energy_min_gmres_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc, int kc,
+                           int m, double *res_trace) {
     int64_t nz = P->nnz;
     if (m <= 0) return ORC_OK;
     double **V = (double **)orc_xcalloc((size_t)m + 1, sizeof(double *));
@@ -551,7 +701,7 @@ int orc_energy_min_gmres(const orc_csr *A, orc_csr *P, const int32_t *rowtype, c
     orc_csr_copy(P, &W);
     Vm = *P;
     orc_masked_product(A, P, &W);
-    orc_project(&W, rowtype, Bc);
+    orc_project_k(&W, rowtype, Bc, kc);
     V[0] = (double *)orc_xmalloc((size_t)nz * sizeof(double));
     for (int64_t q = 0; q < nz; q++) V[0][q] = -W.val[q];
     double beta = sqrt(frob_dot(P, V[0], V[0]));
@@ -563,7 +713,7 @@ int orc_energy_min_gmres(const orc_csr *A, orc_csr *P, const int32_t *rowtype, c
         for (int j = 0; j < m; j++) {
             Vm.val = V[j];
             orc_masked_product(A, &Vm, &W);
-            orc_project(&W, rowtype, Bc);
+            orc_project_k(&W, rowtype, Bc, kc);
             for (int i = 0; i <= j; i++) {
                 double hij = frob_dot(P, W.val, V[i]);
                 H[i * m + j] = hij;
@@ -704,11 +854,12 @@ const int32_t *orc_hier_ivec(const orc_hier *h, int lvl, int which, int32_t *len
 const double *orc_hier_dvec(const orc_hier *h, int lvl, int which, int32_t *len) {
     if (lvl < 0 || lvl >= h->nlev) return NULL;
     const orc_level *L = &h->lev[lvl];
-    switch (which) {
-        case 0: *len = L->A.nrows; return L->B;
-        case 1: *len = L->nc; return L->Bc;
-        case 2: *len = L->A.nrows; return L->Bhat;
-        case 3: *len = L->nc; return L->Bhatc;
+    const int k = h->p.ncand > 0 ? h->p.ncand : 1;
+    switch (which) {  /* row-major n x k / nc x k */
+        case 0: *len = L->A.nrows * k; return L->B;
+        case 1: *len = L->nc * k; return L->Bc;
+        case 2: *len = L->A.nrows * k; return L->Bhat;
+        case 3: *len = L->nc * k; return L->Bhatc;
     }
     return NULL;
 }
@@ -735,20 +886,21 @@ void orc_hier_free(orc_hier *h) {
 static int build_transfer(const orc_csr *A, const orc_csr *N, const int32_t *agg, const int32_t *roots,
                           const int32_t *rowtype, const double *Bsm, const orc_params *p, orc_csr *Pout,
                           double *Bc, int64_t *near_ties) {
+    const int k = p->ncand > 0 ? p->ncand : 1;
     orc_csr P;
     orc_csr_copy(N, &P);
-    int rc = orc_tentative(&P, agg, roots, Bsm, Bc);
+    int rc = orc_tentative_k(&P, agg, roots, rowtype, Bsm, k, Bc);
     if (rc) { orc_csr_free(&P); return rc; }
-    rc = (p->method == 0) ? orc_energy_min_cg(A, &P, rowtype, Bc, p->n_sweeps, p->precond, NULL)
-                          : orc_energy_min_gmres(A, &P, rowtype, Bc, p->n_sweeps, NULL);
+    rc = (p->method == 0) ? orc_energy_min_cg_k(A, &P, rowtype, Bc, k, p->n_sweeps, p->precond, NULL)
+                          : orc_energy_min_gmres_k(A, &P, rowtype, Bc, k, p->n_sweeps, NULL);
     if (rc) { orc_csr_free(&P); return rc; }
     if (p->postfilter > 0.0) {
         orc_csr Pf;
         orc_postfilter(&P, agg, rowtype, p->postfilter, &Pf, near_ties);
         orc_csr_free(&P);
-        orc_enforce(&Pf, rowtype, Bsm, Bc);
-        rc = (p->method == 0) ? orc_energy_min_cg(A, &Pf, rowtype, Bc, 1, p->precond, NULL)
-                              : orc_energy_min_gmres(A, &Pf, rowtype, Bc, 1, NULL);
+        orc_enforce_k(&Pf, rowtype, Bsm, Bc, k);
+        rc = (p->method == 0) ? orc_energy_min_cg_k(A, &Pf, rowtype, Bc, k, 1, p->precond, NULL)
+                              : orc_energy_min_gmres_k(A, &Pf, rowtype, Bc, k, 1, NULL);
         P = Pf;
     }
     *Pout = P;
@@ -766,14 +918,16 @@ int orc_setup(const orc_csr *A0, const double *B0, const double *Bhat0, const or
     h->p = *p;
     int cap = p->max_levels > 0 ? p->max_levels : 1;
     h->lev = (orc_level *)orc_xcalloc((size_t)cap, sizeof(orc_level));
+    const int k = p->ncand > 0 ? p->ncand : 1;
+    if (k > ORC_KMAX) { free(h->lev); free(h); return ORC_EINVAL; }
     orc_level *L = &h->lev[0];
     orc_csr_copy(A0, &L->A);
     int32_t n = A0->nrows;
-    L->B = (double *)orc_xmalloc((size_t)n * sizeof(double));
-    memcpy(L->B, B0, (size_t)n * sizeof(double));
+    L->B = (double *)orc_xmalloc((size_t)n * k * sizeof(double));
+    memcpy(L->B, B0, (size_t)n * k * sizeof(double));
     if (!p->symmetric) {
-        L->Bhat = (double *)orc_xmalloc((size_t)n * sizeof(double));
-        memcpy(L->Bhat, Bhat0, (size_t)n * sizeof(double));
+        L->Bhat = (double *)orc_xmalloc((size_t)n * k * sizeof(double));
+        memcpy(L->Bhat, Bhat0, (size_t)n * k * sizeof(double));
     }
     int lvl = 0;
     int rc = ORC_OK;
@@ -797,10 +951,10 @@ int orc_setup(const orc_csr *A0, const double *B0, const double *Bhat0, const or
         orc_row_types(n, L->agg, L->roots, L->nc, L->rowtype);
         rc = orc_pattern(&L->S, L->agg, L->roots, L->nc, p->degree, p->prefilter, &L->N); /* N = S^d C */
         if (rc) break;
-        orc_smooth_candidates(&L->A, L->B, p->b_sweeps, p->omega);              /* smooth(A, B) */
-        L->Bc = (double *)orc_xmalloc((size_t)L->nc * sizeof(double));
+        orc_smooth_candidates_k(&L->A, L->B, k, p->b_sweeps, p->omega);        /* smooth(A, B) */
+        L->Bc = (double *)orc_xmalloc((size_t)L->nc * k * sizeof(double));
         orc_csr_copy(&L->N, &L->T);
-        rc = orc_tentative(&L->T, L->agg, L->roots, L->B, L->Bc);               /* inject */
+        rc = orc_tentative_k(&L->T, L->agg, L->roots, L->rowtype, L->B, k, L->Bc); /* inject */
         if (rc) break;
         rc = build_transfer(&L->A, &L->N, L->agg, L->roots, L->rowtype, L->B, p, &L->P, L->Bc,
                             &h->near_ties);                                      /* improve (+filter) */
@@ -810,8 +964,8 @@ int orc_setup(const orc_csr *A0, const double *B0, const double *Bhat0, const or
         } else {
             orc_csr At, Rt;
             orc_transpose(&L->A, &At);
-            orc_smooth_candidates(&At, L->Bhat, p->b_sweeps, p->omega);
-            L->Bhatc = (double *)orc_xmalloc((size_t)L->nc * sizeof(double));
+            orc_smooth_candidates_k(&At, L->Bhat, k, p->b_sweeps, p->omega);
+            L->Bhatc = (double *)orc_xmalloc((size_t)L->nc * k * sizeof(double));
             rc = build_transfer(&At, &L->N, L->agg, L->roots, L->rowtype, L->Bhat, p, &Rt, L->Bhatc,
                                 &h->near_ties);
             orc_csr_free(&At);
@@ -826,11 +980,11 @@ int orc_setup(const orc_csr *A0, const double *B0, const double *Bhat0, const or
         rc = orc_spgemm(&L->R, &AP, &Lc->A);
         orc_csr_free(&AP);
         if (rc) break;
-        Lc->B = (double *)orc_xmalloc((size_t)L->nc * sizeof(double));
-        memcpy(Lc->B, L->Bc, (size_t)L->nc * sizeof(double));
+        Lc->B = (double *)orc_xmalloc((size_t)L->nc * k * sizeof(double));
+        memcpy(Lc->B, L->Bc, (size_t)L->nc * k * sizeof(double));
         if (!p->symmetric) {
-            Lc->Bhat = (double *)orc_xmalloc((size_t)L->nc * sizeof(double));
-            memcpy(Lc->Bhat, L->Bhatc, (size_t)L->nc * sizeof(double));
+            Lc->Bhat = (double *)orc_xmalloc((size_t)L->nc * k * sizeof(double));
+            memcpy(Lc->Bhat, L->Bhatc, (size_t)L->nc * k * sizeof(double));
         }
         lvl++;
     }

@@ -766,3 +766,114 @@ def test_w_cycle_differs_from_v_and_converges_faster(oracle):
     hw = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **dict(params, gamma=2))
     b = np.random.default_rng(4).standard_normal(pr.A.n_rows)
     assert np.array_equal(hv.vcycle(b, np.zeros_like(b)), hw.vcycle(b, np.zeros_like(b)))
+
+
+# --------------------------------------------------------------------------- k > 1 candidates (NEXT-3)
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_sym_pinv_matches_numpy(oracle, k):
+    rng = np.random.default_rng(k)
+    for rank in range(0, k + 1):
+        M = rng.standard_normal((k, rank))
+        G = M @ M.T * 10.0 ** rng.uniform(-3, 3)
+        ref = np.linalg.pinv(G, rcond=1e-10, hermitian=True)
+        got = oracle.sym_pinv(G)
+        assert np.allclose(got, ref, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(ref).max()))
+
+
+def _grid_candidates(n):
+    """1, x, y on the lexicographic (m x m) interior grid of n = m^2 nodes."""
+    m = int(round(math.sqrt(n)))
+    i = np.arange(n)
+    h = 1.0 / (m + 1)
+    return np.column_stack([np.ones(n), (i % m + 1) * h, (i // m + 1) * h])
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_tentative_k_is_min_norm_fit(oracle, k):
+    """eq. Tproj: each free row of T is the injected row plus the minimal-norm
+    update that fits all k candidates (numpy least squares on the row)."""
+    A = PR.q1_aniso(17, 1e-2, math.pi / 8).to_scipy()
+    n = A.shape[0]
+    B = _grid_candidates(n)[:, :k].copy()
+    lev = _setup_level(oracle, A, 2)
+    T1, _ = oracle.tentative(lev["N"], lev["agg"], lev["roots"], B[:, 0])
+    T, Bc = oracle.tentative_k(lev["N"], lev["agg"], lev["roots"], lev["rt"], B)
+    assert np.array_equal(Bc, B[lev["roots"]])
+    for i in range(n):
+        s, e = T.indptr[i], T.indptr[i + 1]
+        J = T.indices[s:e]
+        if lev["rt"][i] != 0:
+            assert np.array_equal(T.data[s:e], T1.data[s:e])  # roots (identity) and empty rows untouched
+            continue
+        t0 = T1.data[s:e]
+        M = Bc[J].T  # k x |J|
+        u = np.linalg.lstsq(M, B[i] - M @ t0, rcond=1e-10)[0]
+        assert np.allclose(T.data[s:e], t0 + u, rtol=1e-9, atol=1e-12)
+
+
+def test_cg_k_converged_equals_dense_kkt(oracle):
+    """k = 2: converged CG energy minimisation equals the dense KKT solution of
+    min trace(P^T A P) over the free entries subject to P_i Bc_J = B_i (two
+    equations per free row)."""
+    A = PR.poisson5(7).to_scipy()
+    n = A.shape[0]
+    B = _grid_candidates(n)[:, :2].copy()
+    lev = _setup_level(oracle, A, 2)
+    T, Bc = oracle.tentative_k(lev["N"], lev["agg"], lev["roots"], lev["rt"], B)
+    Ad = A.toarray()
+    N = lev["N"]
+    I, J = [], []
+    for i in range(n):
+        if lev["rt"][i] == 0:
+            for j in N.indices[N.indptr[i]:N.indptr[i + 1]]:
+                I.append(i), J.append(j)
+    I, J = np.array(I), np.array(J)
+    m = len(I)
+    H = Ad[np.ix_(I, I)] * (J[:, None] == J[None, :])
+    rows = sorted(set(I.tolist()))
+    rix = {r: q for q, r in enumerate(rows)}
+    Cm = np.zeros((2 * len(rows), m))
+    for t in range(m):
+        Cm[2 * rix[I[t]], t] = Bc[J[t], 0]
+        Cm[2 * rix[I[t]] + 1, t] = Bc[J[t], 1]
+    X0 = T.toarray().copy()
+    xT = X0[I, J].copy()
+    X0[I, J] = 0.0
+    hvec = (Ad @ X0)[I, J]
+    # CG moves inside {x : Cm (x - x_T) = 0}; rows whose pattern cannot carry both
+    # candidates (one entry, or collinear Bc rows) make Cm rank-deficient, so the
+    # constraints are taken on an orthonormal basis Q of Cm's row space
+    U, sv, Vt = np.linalg.svd(Cm, full_matrices=False)
+    Q = Vt[sv > 1e-10 * sv[0]]
+    K = np.block([[2 * H, Q.T], [Q, np.zeros((Q.shape[0], Q.shape[0]))]])
+    x = np.linalg.solve(K, np.concatenate([-2 * hvec, Q @ xT]))[:m]
+    P, trace = oracle.energy_min_cg_k(A, T, lev["rt"], Bc, 800)
+    assert np.allclose(P.toarray()[I, J], x, atol=1e-9)
+    assert np.allclose(Cm @ P.toarray()[I, J], Cm @ xT, atol=1e-12)  # constraints as T left them
+    assert np.all(np.diff(trace) <= 1e-12 * abs(trace[0]))
+
+
+def test_hierarchy_with_three_candidates(oracle):
+    """Whole setup with B = [1, x, y]: on every level P Bc = B (the level's
+    smoothed candidates) on free rows whose pattern can carry the three
+    candidates, root rows are identity rows, Bc is B at the roots, and the
+    cycle converges."""
+    pr = PR.aniso_problem(48)
+    n = pr.A.n_rows
+    B = _grid_candidates(n)
+    params = dict(pr.params, ncand=3)
+    h = oracle.Hierarchy(pr.A.to_scipy(), B, **params)
+    assert len(h.levels) >= 3
+    for l, L in enumerate(h.levels[:-1]):
+        P = L.P
+        assert L.B.shape == (L.A.shape[0], 3) and L.Bc.shape == (P.shape[1], 3)
+        assert np.array_equal(L.Bc, L.B[L.roots])
+        PB = P @ L.Bc
+        for i in range(P.shape[0]):
+            s, e = P.indptr[i], P.indptr[i + 1]
+            if L.rowtype[i] == 1:
+                assert e - s == 1 and P.data[s] == 1.0
+            elif L.rowtype[i] == 0 and np.linalg.matrix_rank(L.Bc[P.indices[s:e]]) == 3:
+                assert np.allclose(PB[i], L.B[i], rtol=1e-10, atol=1e-12 * np.abs(L.B).max())
+    x, info = h.solve(pr.b, tol=1e-8, outer=1)
+    assert info["status"] == 0
