@@ -278,14 +278,19 @@ def main():
         return rn.params_from_config(pr.params, precision=rn.RN_MIXED if prec == "mixed" else rn.RN_FP64,
                                      outer=rn.RN_OUTER_CG, use_graphs=1, **over)
 
-    def step(prec, **over):
+    # candidates 1, x, y of the interior grid (the several-candidate setup, k = 3)
+    m_int = int(round(math.sqrt(A.n_rows)))
+    ii = np.arange(A.n_rows)
+    B3 = t(np.column_stack([np.ones(A.n_rows), (ii % m_int + 1) / (m_int + 1), (ii // m_int + 1) / (m_int + 1)]))
+
+    def step(prec, B=None, **over):
         xd.zero_()
-        h = rn.Hierarchy(rp, ci, va, Bd, params=params(prec, **over), stream=sptr)
+        h = rn.Hierarchy(rp, ci, va, Bd if B is None else B, params=params(prec, **over), stream=sptr)
         info = h.solve(bd, xd, rtol=1e-8, maxit=5000)
         h.close()
         return info
 
-    def timed(prec, k, **over):
+    def timed(prec, k, B=None, **over):
         times, infos = [], []
         for _ in range(k):
             flush.fill_(1.0)
@@ -293,7 +298,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            infos.append(step(prec, **over))
+            infos.append(step(prec, B, **over))
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
@@ -327,6 +332,9 @@ def main():
     # the same step with W(1,1) cycles (Sec. 5.2), one warm-up and one timed step
     step(prec, gamma=2)
     times_w, infos_w = timed(prec, 1, gamma=2)
+    # the same step with three candidates (1, x, y), Sec. 3.6
+    step(prec, B3)
+    times_k3, infos_k3 = timed(prec, 1, B3)
 
     # per-launch device times of the solve's level-0 operations, each timed in
     # isolation with CUDA events on the hierarchy's stream, a 256 MB read before
@@ -423,6 +431,8 @@ def main():
             "mixed_setup_vs_fp64": setup_err,
             "w_cycle": {"step_s": times_w[0], "iters": infos_w[0]["iters"], "rel_res": infos_w[0]["rel_res"],
                         "cycle": "W(1,1)", "precision": prec},
+            "candidates_3": {"step_s": times_k3[0], "iters": infos_k3[0]["iters"], "rel_res": infos_k3[0]["rel_res"],
+                             "B": "1, x, y", "precision": prec},
             "roofline": roofline,
             "level0_launches": kernels,
             "gpu_launches": launches // max(args.steps, 1),

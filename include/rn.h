@@ -125,6 +125,7 @@ typedef struct {
 } rn_solve_info;
 
 #define RN_MAX_LEVELS 32
+#define RN_MAX_CANDIDATES 4  /* k, the number of candidate vectors */
 typedef struct {
     int levels;
     int32_t n[RN_MAX_LEVELS];
@@ -144,7 +145,11 @@ typedef struct rn_hierarchy rn_hierarchy;
 rn_status rn_default_params(rn_params *p);
 
 /* Build the hierarchy (Alg. 3) for A with candidates B (n x k, row-major,
- * k == 1) and, when p->symmetric == 0, Bhat (candidates for A^T).
+ * 1 <= k <= RN_MAX_CANDIDATES) and, when p->symmetric == 0, Bhat (candidates
+ * for A^T, n x k).  Scalar problems (block size m = 1): the first candidate
+ * is injected (root rows of P are identity rows) and the others are fitted
+ * row by row on the pattern (eq. Tproj, Sec. 3.6), each row's k x k Gram
+ * matrix inverted by its pseudo-inverse; every coarse level has k candidates.
  * `location` applies to A's arrays, B and Bhat.  On success *out owns the
  * hierarchy; on any error *out is NULL and nothing is leaked. */
 rn_status rn_setup(const rn_csr *A, const double *B, const double *Bhat, int k, int location,

@@ -76,6 +76,7 @@ def lib():
         L.orc_energy_min_cg_k.argtypes = [P(_CSR), P(_CSR), i32p, dp, C.c_int, C.c_int, C.c_int, dp]
         L.orc_smooth_candidates_k.argtypes = [P(_CSR), dp, C.c_int, C.c_int, C.c_double]
         L.orc_sym_pinv.argtypes = [C.c_int, dp, dp]
+        L.orc_sym_pinv.restype = C.c_int
         L.orc_aggregate.argtypes = [P(_CSR), C.c_uint64, i32p, P(i32p), i32p]
         L.orc_splitmix64.argtypes = [C.c_uint64]
         L.orc_splitmix64.restype = C.c_uint64

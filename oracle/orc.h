@@ -91,7 +91,7 @@ int orc_energy_min_cg_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, co
                         int sweeps, int precond, double *energy_trace);
 int orc_energy_min_gmres_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc, int k,
                            int m, double *res_trace);
-void orc_sym_pinv(int k, const double *G, double *Gp);
+int orc_sym_pinv(int k, const double *G, double *Gp);  /* returns the rank kept */
 void orc_masked_product(const orc_csr *A, const orc_csr *X, orc_csr *W);
 void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc);
 int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc,

@@ -443,9 +443,11 @@ void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc) {
 /* Pseudo-inverse of a symmetric k x k matrix (k <= ORC_KMAX, row-major) by the
  * cyclic Jacobi eigenvalue method (rotations zeroing one off-diagonal pair at
  * a time until the off-diagonal mass is negligible); eigenvalues at most
- * 1e-12 of the largest are dropped. */
+ * 1e-6 of the largest are dropped (singular values of Bc_J below 1e-3 of the
+ * largest): candidate combinations that are nearly dependent on a row's
+ * pattern stay unfitted, which bounds the fit's amplification by 1e6. */
 #define ORC_KMAX 8
-void orc_sym_pinv(int k, const double *G, double *Gp) {
+int orc_sym_pinv(int k, const double *G, double *Gp) {
     double a[ORC_KMAX * ORC_KMAX], v[ORC_KMAX * ORC_KMAX];
     for (int i = 0; i < k * k; i++) a[i] = G[i];
     for (int i = 0; i < k; i++)
@@ -485,17 +487,22 @@ void orc_sym_pinv(int k, const double *G, double *Gp) {
     double lmax = 0.0;
     for (int i = 0; i < k; i++) if (fabs(a[i * k + i]) > lmax) lmax = fabs(a[i * k + i]);
     for (int i = 0; i < k * k; i++) Gp[i] = 0.0;
+    int rank = 0;
     for (int e = 0; e < k; e++) {
         double lam = a[e * k + e];
-        if (!(lam > 1e-12 * lmax)) continue;
+        if (!(lam > 1e-6 * lmax)) continue;
+        rank++;
         for (int i = 0; i < k; i++)
             for (int j = 0; j < k; j++) Gp[i * k + j] += v[i * k + e] * v[j * k + e] / lam;
     }
+    return rank;
 }
 
 /* Min-norm update of one row's values t (pattern columns col[s..e)) so that
  * (t + u) Bc_J = target (target NULL: 0):  r = target - t Bc_J,
- * u_j = (r G_i^+) . Bc_j. */
+ * u_j = (r G_i^+) . Bc_j.  With target NULL (the projection) a row whose
+ * pattern has no more entries than the rank of Bc_J is fixed by the
+ * constraints and set to exactly 0, as a one-entry row is for k = 1. */
 static void row_fit_k(int32_t s, int32_t e, const int32_t *col, double *val, const double *target,
                       const double *Bc, int k) {
     double G[ORC_KMAX * ORC_KMAX] = {0}, Gp[ORC_KMAX * ORC_KMAX], r[ORC_KMAX], y[ORC_KMAX];
@@ -507,7 +514,11 @@ static void row_fit_k(int32_t s, int32_t e, const int32_t *col, double *val, con
             for (int c = 0; c < k; c++) G[a * k + c] += b[a] * b[c];
         }
     }
-    orc_sym_pinv(k, G, Gp);
+    const int rank = orc_sym_pinv(k, G, Gp);
+    if (!target && rank >= e - s) {  /* the constraints fix the row: its constraint space is {0} */
+        for (int32_t q = s; q < e; q++) val[q] = 0.0;
+        return;
+    }
     for (int c = 0; c < k; c++) {
         y[c] = 0.0;
         for (int a = 0; a < k; a++) y[c] += r[a] * Gp[a * k + c];

@@ -101,7 +101,7 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
     RN_API_BEGIN
     using rn::fail;
     if (!A || !B || !p || !out) fail(RN_EINVAL, "null argument");
-    if (k != 1) fail(RN_EINVAL, "only k = 1 candidate is supported");
+    if (k < 1 || k > RN_MAX_CANDIDATES) fail(RN_EINVAL, "k must be in [1, RN_MAX_CANDIDATES]");
     if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
     if (A->n_rows <= 0 || A->n_rows != A->n_cols) fail(RN_EINVAL, "A must be square and non-empty");
     if (A->nnz <= 0 || A->nnz > INT32_MAX - 1) fail(RN_EINVAL, "nnz out of range");
@@ -128,6 +128,7 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
     }
     std::unique_ptr<rn_hierarchy> h(new rn_hierarchy());
     h->p = *p;
+    h->k = k;
     h->s = s;
     h->own_stream = (own.s != nullptr);
     const double t0 = rn::now_ms();
@@ -140,18 +141,18 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
         rp.alloc(n + 1, s);
         ci.alloc(A->nnz, s);
         va.alloc(A->nnz, s);
-        Bd.alloc(n, s);
+        Bd.alloc((size_t)n * k, s);
         rn::h2d(rp.p, A->rowptr, n + 1, s);
         rn::h2d(ci.p, A->col, A->nnz, s);
         rn::h2d(va.p, A->val, A->nnz, s);
-        rn::h2d(Bd.p, B, n, s);
+        rn::h2d(Bd.p, B, (size_t)n * k, s);
         Av.rowptr = rp.p;
         Av.col = ci.p;
         Av.val = va.p;
         Bp = Bd.p;
         if (!p->symmetric) {
-            Bhd.alloc(n, s);
-            rn::h2d(Bhd.p, Bhat, n, s);
+            Bhd.alloc((size_t)n * k, s);
+            rn::h2d(Bhd.p, Bhat, (size_t)n * k, s);
             Bhp = Bhd.p;
         }
     }

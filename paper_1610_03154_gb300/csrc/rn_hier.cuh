@@ -26,6 +26,7 @@ struct rn_level {
 
 struct rn_hierarchy {
     rn_params p{};
+    int k = 1;                 // candidate vectors: B is n x k, Bc nc x k (row-major) on every level
     cudaStream_t s = nullptr;  // params.stream, or a stream the hierarchy created (own_stream)
     bool own_stream = false;
     std::vector<std::unique_ptr<rn_level>> lev;  // lev.back() is the coarsest
@@ -106,6 +107,7 @@ struct EmCtx {
     double *R = nullptr, *Dd = nullptr, *W = nullptr;
     double *rs2 = nullptr;  // n rows: the row projection's scales (allocated internally when null)
     bool fp32 = false;      // CG sweeps in FP32 (mixed precision); workspaces then allocated internally
+    int k = 1;              // candidates (Bc is nc x k); k > 1 projects with per-row Gram pseudo-inverses
 };
 // dinv: the inverted diagonal of A (CG's preconditioner D^{-1} when c.precond)
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,

@@ -298,6 +298,144 @@ __global__ void gather_kernel(int32_t nc, const int32_t *__restrict__ roots, con
     }
 }
 
+// k > 1 candidates: the k columns of the row-major n x k B swept together,
+// each column summed exactly as the single-candidate kernel sums it
+__global__ void cand_jacobi_k_kernel(int32_t n, int k, const int32_t *__restrict__ arp,
+                                     const int32_t *__restrict__ acol, const double *__restrict__ aval,
+                                     const double *__restrict__ B, double omega, double *__restrict__ Bn) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc[RN_MAX_CANDIDATES] = {}, d = 0.0;
+        for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
+            const int32_t j = acol[e];
+            for (int c = 0; c < k; c++) acc[c] = __dadd_rn(acc[c], __dmul_rn(aval[e], B[(int64_t)j * k + c]));
+            if (j == i) d = aval[e];
+        }
+        for (int c = 0; c < k; c++)
+            Bn[(int64_t)i * k + c] = __dsub_rn(B[(int64_t)i * k + c], __dmul_rn(omega, __ddiv_rn(acc[c], d)));
+    }
+}
+
+// Bc = B at the roots (nc x k); the first candidate must not vanish there
+__global__ void gather_k_kernel(int32_t nc, int k, const int32_t *__restrict__ roots, const double *__restrict__ B,
+                                double *__restrict__ Bc, int32_t *__restrict__ bad) {
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        for (int a = 0; a < k; a++) Bc[(int64_t)c * k + a] = B[(int64_t)roots[c] * k + a];
+        if (!(fabs(Bc[(int64_t)c * k]) >= 1e-300)) atomicMax(bad, c + 1);
+    }
+}
+
+// Pseudo-inverse of the symmetric k x k matrix g (k <= RN_MAX_CANDIDATES,
+// row-major, overwritten) into gp: eigen-decomposition by cyclic Jacobi
+// rotations (each zeroes one off-diagonal pair; sweeps until the off-diagonal
+// mass is negligible), eigenvalues at most 1e-6 of the largest dropped:
+// candidate combinations nearly dependent on a row's pattern stay unfitted,
+// bounding the fit's amplification of rounding by 1e6.
+__device__ int sym_pinv_dev(int k, double *g, double *gp) {
+    double v[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES];
+    for (int i = 0; i < k; i++)
+        for (int j = 0; j < k; j++) v[i * k + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 64; sweep++) {
+        double off = 0.0, dia = 0.0;
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < k; j++) {
+                const double x = g[i * k + j] * g[i * k + j];
+                if (i == j) dia += x;
+                else off += x;
+            }
+        if (off == 0.0 || off <= 1e-32 * dia) break;
+        for (int p = 0; p < k - 1; p++)
+            for (int q = p + 1; q < k; q++) {
+                const double apq = g[p * k + q];
+                if (apq == 0.0) continue;
+                const double th = (g[q * k + q] - g[p * k + p]) / (2.0 * apq);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int r = 0; r < k; r++) {
+                    const double x = g[r * k + p], y = g[r * k + q];
+                    g[r * k + p] = c * x - sn * y;
+                    g[r * k + q] = sn * x + c * y;
+                }
+                for (int r = 0; r < k; r++) {
+                    const double x = g[p * k + r], y = g[q * k + r];
+                    g[p * k + r] = c * x - sn * y;
+                    g[q * k + r] = sn * x + c * y;
+                }
+                for (int r = 0; r < k; r++) {
+                    const double x = v[r * k + p], y = v[r * k + q];
+                    v[r * k + p] = c * x - sn * y;
+                    v[r * k + q] = sn * x + c * y;
+                }
+            }
+    }
+    double lmax = 0.0;
+    for (int i = 0; i < k; i++) lmax = fmax(lmax, fabs(g[i * k + i]));
+    for (int i = 0; i < k * k; i++) gp[i] = 0.0;
+    int rank = 0;
+    for (int e = 0; e < k; e++) {
+        const double lam = g[e * k + e];
+        if (!(lam > 1e-6 * lmax)) continue;
+        rank++;
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < k; j++) gp[i * k + j] += v[i * k + e] * v[j * k + e] / lam;
+    }
+    return rank;  // eigenvalues kept
+}
+
+// G_i^+ of every row's Gram matrix G_i = Bc_J^T Bc_J on its pattern J, and
+// whether the constraints fix the row (no more pattern entries than the rank
+// of Bc_J: constraint space {0}, like a one-entry row for k = 1); fixed,
+// one-entry and such rows are projected to exactly 0.
+__global__ void gram_pinv_kernel(int32_t n, int k, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const int32_t *__restrict__ rowtype, const double *__restrict__ Bc,
+                                 double *__restrict__ Gp, int32_t *__restrict__ zero_row) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double g[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES] = {}, gp[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES] = {};
+        const int32_t len = rp[i + 1] - rp[i];
+        int z = 1;
+        if (rowtype[i] == FREE_ROW && len > 1) {
+            for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+                const double *b = Bc + (int64_t)col[e] * k;
+                for (int a = 0; a < k; a++)
+                    for (int c = 0; c < k; c++) g[a * k + c] += b[a] * b[c];
+            }
+            z = sym_pinv_dev(k, g, gp) >= len;
+        }
+        for (int q = 0; q < k * k; q++) Gp[(int64_t)i * k * k + q] = gp[q];
+        zero_row[i] = z;
+    }
+}
+
+// Minimal-norm fit of every free row (eq. Tproj): (t + u) Bc_J = B_i with
+// u_j = ((B_i - t Bc_J) G_i^+) . Bc_j; T's construction and enforce for k > 1.
+__global__ void row_fit_k_kernel(int32_t n, int k, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 double *__restrict__ val, const int32_t *__restrict__ rowtype,
+                                 const double *__restrict__ B, const double *__restrict__ Bc) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (rowtype[i] != FREE_ROW) continue;
+        double g[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES] = {}, gp[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES];
+        double r[RN_MAX_CANDIDATES], y[RN_MAX_CANDIDATES];
+        for (int a = 0; a < k; a++) r[a] = B[(int64_t)i * k + a];
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            const double *b = Bc + (int64_t)col[e] * k;
+            for (int a = 0; a < k; a++) {
+                r[a] -= val[e] * b[a];
+                for (int c = 0; c < k; c++) g[a * k + c] += b[a] * b[c];
+            }
+        }
+        sym_pinv_dev(k, g, gp);
+        for (int c = 0; c < k; c++) {
+            y[c] = 0.0;
+            for (int a = 0; a < k; a++) y[c] += r[a] * gp[a * k + c];
+        }
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            const double *b = Bc + (int64_t)col[e] * k;
+            double u = 0.0;
+            for (int c = 0; c < k; c++) u += y[c] * b[c];
+            val[e] += u;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ pattern (Sec. 3.4-3.5)
 __global__ void aggflag_kernel(int32_t n, const int32_t *__restrict__ agg, int32_t *__restrict__ flag) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -350,15 +488,90 @@ __global__ void prefilter_kernel(int32_t n, const int32_t *__restrict__ rp, cons
 }
 
 // T on the pattern (eq. root-nodeform): T_{i,agg(i)} = B_i / Bc_{agg(i)}
+// (first candidate; k the row stride of B and Bc)
 __global__ void tentative_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                  const int32_t *__restrict__ agg, const double *__restrict__ B,
-                                 const double *__restrict__ Bc, double *__restrict__ T) {
+                                 const double *__restrict__ Bc, double *__restrict__ T, int k) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
             int32_t j = col[e];
-            T[e] = (j == agg[i]) ? __ddiv_rn(B[i], Bc[j]) : 0.0;
+            T[e] = (j == agg[i]) ? __ddiv_rn(B[(int64_t)i * k], Bc[(int64_t)j * k]) : 0.0;
         }
 }
+
+// ------------------------------------------------------------------ k > 1: the row projection as a pass
+// W <- scale (W - (c G_i^+) Bc_J) with c = W_i Bc_J on every free row of more
+// than one entry (eq. Tproj with a zero right-hand side); the product kernels
+// ran unprojected (their row scales are zero).  <Y, W> finishes in Fin.
+template <typename TV>
+__global__ void __launch_bounds__(256)
+proj_k_kernel(int32_t n, int k, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
+              const int32_t *__restrict__ zero_row, const TV *__restrict__ Bc, const TV *__restrict__ Gp,
+              TV *__restrict__ W, TV scale, const TV *__restrict__ Y, Fin fin) {
+    __shared__ double s_red[32];
+    TV dot = TV(0);
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t cs = nrp[i], ce = nrp[i + 1];
+        if (zero_row[i]) {  // constraint space {0}
+            for (int32_t q = cs; q < ce; q++) W[q] = TV(0);
+            continue;
+        }
+        TV c[RN_MAX_CANDIDATES] = {}, y[RN_MAX_CANDIDATES] = {};
+        for (int32_t q = cs; q < ce; q++) {
+            const TV *b = Bc + (int64_t)ncol[q] * k;
+            for (int a = 0; a < k; a++) c[a] = fma(W[q], b[a], c[a]);
+        }
+        const TV *g = Gp + (int64_t)i * k * k;
+        for (int b = 0; b < k; b++)
+            for (int a = 0; a < k; a++) y[b] = fma(c[a], g[a * k + b], y[b]);
+        for (int32_t q = cs; q < ce; q++) {
+            const TV *b = Bc + (int64_t)ncol[q] * k;
+            TV u = TV(0);
+            for (int a = 0; a < k; a++) u = fma(y[a], b[a], u);
+            const TV w = scale * (W[q] - u);
+            W[q] = w;
+            if (Y) dot = fma(Y[q], w, dot);
+        }
+    }
+    const double d[1] = {(double)dot};
+    grid_finish<256, 1>(d, fin, s_red);
+}
+
+// Per-minimisation data of the k > 1 projection: G_i^+ (FP64, rounded for
+// FP32 sweeps) and Bc in the sweeps' type.
+template <typename TV>
+struct KProj {
+    int k = 1;
+    DVec<double> gp64;
+    DVec<int32_t> zero_row;
+    DVec<TV> gpv, bcv;
+    const TV *gp = nullptr, *bc = nullptr;
+    void build(int k_, const Pattern &N, const int32_t *rowtype, const double *Bc, cudaStream_t s) {
+        k = k_;
+        if (k == 1) return;
+        gp64.alloc((size_t)N.n * k * k, s);
+        zero_row.alloc(N.n, s);
+        RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 8.0 * k * N.nnz + 8.0 * k * k * N.n, s, gram_pinv_kernel,
+                  grid_for(N.n, 256), 256, 0, N.n, k, N.rp, N.col, rowtype, Bc, gp64.p, zero_row.p);
+        if constexpr (sizeof(TV) == 4) {
+            gpv.alloc((size_t)N.n * k * k, s);
+            bcv.alloc((size_t)N.nc * k, s);
+            to_float(gp64.p, gpv.p, (int64_t)N.n * k * k, s);
+            to_float(Bc, bcv.p, (int64_t)N.nc * k, s);
+            gp = gpv.p;
+            bc = bcv.p;
+        } else {
+            gp = gp64.p;
+            bc = Bc;
+        }
+    }
+    void apply(const Pattern &N, const int32_t *rowtype, TV *W, double scale, const TV *Y, const Fin &f,
+               cudaStream_t s) const {
+        const int g = grid_resident(proj_k_kernel<TV>, 256, 0, N.n, 256, kReduceBlocks);
+        RN_LAUNCH("energy_masked_product", (2.0 * sizeof(TV) + 4.0 + sizeof(TV) * k) * N.nnz, s, proj_k_kernel<TV>,
+                  g, 256, 0, N.n, k, N.rp, N.col, zero_row.p, bc, gp, W, (TV)scale, Y, f);
+    }
+};
 
 // ------------------------------------------------------------------ CG energy minimisation (Sec. 3.6)
 // Device scalars: sc[0] rho, sc[1] rho0, sc[2] beta, sc[3] <Dd,W>, sc[4] alpha; fl[0] = done.
@@ -717,13 +930,16 @@ static void energy_min_cg_t(const EmCtx &c, const CsrView &A, const Pattern &N, 
     DVec<double> Sv;
     double *rs2 = c.rs2;
     if (!rs2) { Sv.alloc(N.n, s); rs2 = Sv.p; }
-    proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);  // FP64
+    KProj<TV> kp;
+    kp.build(c.k, N, rowtype, Bc, s);
+    if (c.k == 1) proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);  // FP64
+    else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
     ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
     DVec<TV> Bcv, Rsv;
     if constexpr (f32) {
-        Bcv.alloc(N.nc, s);
+        Bcv.alloc((size_t)N.nc * c.k, s);
         Rsv.alloc(N.n, s);
-        to_float(Bc, Bcv.p, N.nc, s);
+        to_float(Bc, Bcv.p, (int64_t)N.nc * c.k, s);
         to_float(rs2, Rsv.p, N.n, s);
         pa.Bc = Bcv.p;
         pa.rs2 = Rsv.p;
@@ -745,8 +961,15 @@ static void energy_min_cg_t(const EmCtx &c, const CsrView &A, const Pattern &N, 
     EpMap em;
     ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
     auto product = [&](const TV *Xin, TV *Wout, double scale, const TV *Y, const Fin &f) {
-        if (em.ok) masked_product_mapped<TV>(em, A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, Y, f, s);
-        else masked_product_proj<TV>(A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, Y, f, s);
+        const bool k1 = c.k == 1;
+        const Fin none0;
+        if (em.ok)
+            masked_product_mapped<TV>(em, A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, k1 ? scale : 1.0,
+                                      k1 ? Y : nullptr, k1 ? f : none0, s);
+        else
+            masked_product_proj<TV>(A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, k1 ? scale : 1.0,
+                                    k1 ? Y : nullptr, k1 ? f : none0, s);
+        if (!k1) kp.apply(N, rowtype, Wout, scale, Y, f, s);
     };
     product(X, R, -1.0, nullptr, none);
     fin.mode = FIN_CG_RHO;
@@ -790,18 +1013,21 @@ static void energy_min_gmres_t(const EmCtx &c, const CsrView &A, const Pattern &
     int32_t *fl = c.fl;
     DVec<double> Sv(c.rs2 ? 0 : N.n, s);
     double *rs2 = c.rs2 ? c.rs2 : Sv.p;
-    proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);
+    KProj<TV> kp;
+    kp.build(c.k, N, rowtype, Bc, s);
+    if (c.k == 1) proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);
+    else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
     ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
     TV *X;
     const TV *aval;
     if constexpr (f32) {
         Xv.alloc(nz > 0 ? nz : 1, s);
         Av.alloc(A.nnz, s);
-        Bcv.alloc(N.nc, s);
+        Bcv.alloc((size_t)N.nc * c.k, s);
         Rsv.alloc(N.n, s);
         to_float(X64, Xv.p, nz, s);
         to_float(A.val, Av.p, A.nnz, s);
-        to_float(Bc, Bcv.p, N.nc, s);
+        to_float(Bc, Bcv.p, (int64_t)N.nc * c.k, s);
         to_float(rs2, Rsv.p, N.n, s);
         X = Xv.p;
         aval = Av.p;
@@ -818,9 +1044,11 @@ static void energy_min_gmres_t(const EmCtx &c, const CsrView &A, const Pattern &
     EpMap em;
     ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
     auto product = [&](const TV *Xin, TV *Wout, double scale) {
+        const double sc0 = c.k == 1 ? scale : 1.0;
         if (em.ok)
-            masked_product_mapped<TV>(em, A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, nullptr, Fin(), s);
-        else masked_product_proj<TV>(A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, scale, nullptr, Fin(), s);
+            masked_product_mapped<TV>(em, A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, sc0, nullptr, Fin(), s);
+        else masked_product_proj<TV>(A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, sc0, nullptr, Fin(), s);
+        if (c.k > 1) kp.apply(N, rowtype, Wout, scale, nullptr, Fin(), s);
     };
     auto dot_t = [&](const TV *a, const TV *b, double *out) {
         Fin f;
@@ -879,6 +1107,7 @@ static EmCtx ctx_of(rn_hierarchy &h) {
     c.precond = h.p.energy_precond;
     c.method = h.p.energy_method;
     c.fp32 = h.p.precision == RN_MIXED;  // FP32 sweeps (CG and GMRES) in the mixed-precision setup
+    c.k = h.k;
     return c;
 }
 
@@ -894,17 +1123,26 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
                            double *Bc, DCsr &Pout, DCsr *Tkeep) {
     cudaStream_t s = h.s;
     const int32_t n = A.n;
+    const int k = h.k;
     // candidates: b_sweeps weighted-Jacobi sweeps on A B = 0 (exact)
     {
-        DVec<double> tmp(n, s);
+        DVec<double> tmp((size_t)n * k, s);
         for (int sw = 0; sw < h.p.b_sweeps; sw++) {
-            RN_LAUNCH("candidates", 12.0 * A.nnz + 24.0 * n, s, cand_jacobi_kernel, rows_grid(n), kT, 0, n, A.rowptr,
-                      A.col, A.val, Bsm, h.p.omega, tmp.p);
-            d2d(Bsm, tmp.p, n, s);
+            if (k == 1)
+                RN_LAUNCH("candidates", 12.0 * A.nnz + 24.0 * n, s, cand_jacobi_kernel, rows_grid(n), kT, 0, n,
+                          A.rowptr, A.col, A.val, Bsm, h.p.omega, tmp.p);
+            else
+                RN_LAUNCH("candidates", 12.0 * A.nnz + 8.0 * k * (A.nnz + 2.0 * n), s, cand_jacobi_k_kernel,
+                          rows_grid(n), kT, 0, n, k, A.rowptr, A.col, A.val, Bsm, h.p.omega, tmp.p);
+            d2d(Bsm, tmp.p, (size_t)n * k, s);
         }
     }
     fill_i32(h.iflags.p + 2, 0, 1, s);
-    RN_LAUNCH("inject", 16.0 * nc, s, gather_kernel, rows_grid(nc), kT, 0, nc, roots, Bsm, Bc, h.iflags.p + 2);
+    if (k == 1)
+        RN_LAUNCH("inject", 16.0 * nc, s, gather_kernel, rows_grid(nc), kT, 0, nc, roots, Bsm, Bc, h.iflags.p + 2);
+    else
+        RN_LAUNCH("inject", 16.0 * nc * k, s, gather_k_kernel, rows_grid(nc), kT, 0, nc, k, roots, Bsm, Bc,
+                  h.iflags.p + 2);
     check_flag(h.iflags.p + 2, s, RN_EINVAL, "candidate vanishes at a root node");
     // P = T on N
     Pout.n = n;
@@ -916,7 +1154,10 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
     d2d(Pout.rowptr.p, N.rowptr.p, n + 1, s);
     d2d(Pout.col.p, N.col.p, N.nnz, s);
     RN_LAUNCH("tentative", 16.0 * N.nnz + 16.0 * n, s, tentative_kernel, rows_grid(n), kT, 0, n, N.rowptr.p, N.col.p,
-              agg, Bsm, Bc, Pout.val.p);
+              agg, Bsm, Bc, Pout.val.p, k);
+    if (k > 1)  // the other candidates: minimal-norm row fits (eq. Tproj)
+        RN_LAUNCH("tentative", 12.0 * N.nnz + 8.0 * k * (N.nnz + n), s, row_fit_k_kernel, rows_grid(n), kT, 0, n, k,
+                  Pout.rowptr.p, Pout.col.p, Pout.val.p, rowtype, Bsm, Bc);
     if (Tkeep) {
         Tkeep->n = n; Tkeep->m = nc; Tkeep->nnz = N.nnz;
         Tkeep->rowptr.alloc(n + 1, s); Tkeep->col.alloc(N.nnz, s); Tkeep->val.alloc(N.nnz, s);
@@ -942,8 +1183,12 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
         RN_LAUNCH("postfilter", 24.0 * Pout.nnz + 12.0 * F.nnz, s, postfilter_kernel<true>, rows_grid(n), kT, 0, n,
                   Pout.rowptr.p, Pout.col.p, Pout.val.p, rowtype, agg, h.p.postfilter, omg, nullptr, F.rowptr.p,
                   F.col.p, F.val.p);
-        RN_LAUNCH("enforce", 28.0 * F.nnz + 8.0 * n, s, enforce_kernel, rows_grid(n), kT, 0, n, F.rowptr.p, F.col.p,
-                  F.val.p, rowtype, Bsm, Bc);
+        if (k == 1)
+            RN_LAUNCH("enforce", 28.0 * F.nnz + 8.0 * n, s, enforce_kernel, rows_grid(n), kT, 0, n, F.rowptr.p,
+                      F.col.p, F.val.p, rowtype, Bsm, Bc);
+        else
+            RN_LAUNCH("enforce", 12.0 * F.nnz + 8.0 * k * (F.nnz + n), s, row_fit_k_kernel, rows_grid(n), kT, 0, n,
+                      k, F.rowptr.p, F.col.p, F.val.p, rowtype, Bsm, Bc);
         Pout = std::move(F);
         Pattern pf{n, nc, Pout.nnz, Pout.rowptr.p, Pout.col.p};
         energy_min(ctx_of(h), A, pf, Pout.val.p, rowtype, Bc, dinv.p, 1);
@@ -969,11 +1214,11 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         d2d(L->A.rowptr.p, A0.rowptr, A0.n + 1, s);
         d2d(L->A.col.p, A0.col, A0.nnz, s);
         d2d(L->A.val.p, A0.val, A0.nnz, s);
-        L->B.alloc(A0.n, s);
-        d2d(L->B.p, B0, A0.n, s);
+        L->B.alloc((size_t)A0.n * h.k, s);
+        d2d(L->B.p, B0, (size_t)A0.n * h.k, s);
         if (!p.symmetric) {
-            L->Bhat.alloc(A0.n, s);
-            d2d(L->Bhat.p, Bhat0, A0.n, s);
+            L->Bhat.alloc((size_t)A0.n * h.k, s);
+            d2d(L->Bhat.p, Bhat0, (size_t)A0.n * h.k, s);
         }
         fill_i32(h.iflags.p + 3, 0, 1, s);
         RN_LAUNCH("validate", 12.0 * A0.nnz + 4.0 * A0.n, s, validate_kernel, rows_grid(A0.n), kT, 0, A0.n, A0.nnz,
@@ -1094,7 +1339,7 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
                       N.rowptr.p, N.col.p, N.val.p);
         }
         // ---- candidates, T, energy minimisation, filtering -> P
-        L.Bc.alloc(nc, s);
+        L.Bc.alloc((size_t)nc * h.k, s);
         build_transfer(h, A, N, L.agg.p, L.roots.p, nc, L.rowtype.p, L.B.p, L.diag.p, L.Bc.p, L.P,
                        p.keep_aux ? &L.T : nullptr);
         // ---- R
@@ -1105,7 +1350,7 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             transpose(A, true, At, s);
             DVec<double> diagT(n, s);
             d2d(diagT.p, L.diag.p, n, s);  // the diagonal of A^T is the diagonal of A
-            L.Bhatc.alloc(nc, s);
+            L.Bhatc.alloc((size_t)nc * h.k, s);
             build_transfer(h, view(At), N, L.agg.p, L.roots.p, nc, L.rowtype.p, L.Bhat.p, diagT.p, L.Bhatc.p, Rt,
                            nullptr);
             transpose(view(Rt), true, L.R, s);
@@ -1117,11 +1362,11 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             spgemm(A, view(L.P), AP, s);
             spgemm(view(L.R), view(AP), Lc->A, s);
         }
-        Lc->B.alloc(nc, s);
-        d2d(Lc->B.p, L.Bc.p, nc, s);
+        Lc->B.alloc((size_t)nc * h.k, s);
+        d2d(Lc->B.p, L.Bc.p, (size_t)nc * h.k, s);
         if (!p.symmetric) {
-            Lc->Bhat.alloc(nc, s);
-            d2d(Lc->Bhat.p, L.Bhatc.p, nc, s);
+            Lc->Bhat.alloc((size_t)nc * h.k, s);
+            d2d(Lc->Bhat.p, L.Bhatc.p, (size_t)nc * h.k, s);
         }
         if (p.keep_aux) {
             L.S = std::move(S);

@@ -291,17 +291,23 @@ def use_torch_allocator(p: rn_params, stream=None) -> rn_params:
 
 
 class Hierarchy:
-    """Owns an rn_hierarchy.  A, B, Bhat: torch CUDA tensors or numpy arrays."""
+    """Owns an rn_hierarchy.  A, B, Bhat: torch CUDA tensors or numpy arrays;
+    B (and Bhat) is n or n x k (k candidate vectors, row-major)."""
 
     def __init__(self, rowptr, col, val, B, Bhat=None, params: rn_params | None = None, stream=None):
         host = _is_host(val)
+        n = int(rowptr.shape[0]) - 1
+        k = 1 if len(B.shape) == 1 else int(B.shape[1])
         if host:
             rowptr = np.ascontiguousarray(rowptr, np.int32)
             col = np.ascontiguousarray(col, np.int32)
             val = np.ascontiguousarray(val, np.float64)
             B = np.ascontiguousarray(B, np.float64).reshape(-1)
             Bhat = None if Bhat is None else np.ascontiguousarray(Bhat, np.float64).reshape(-1)
-        n = int(rowptr.shape[0]) - 1
+        else:
+            B = B.contiguous()
+            Bhat = None if Bhat is None else Bhat.contiguous()
+        self.k = k
         self.n = n
         self.params = params if params is not None else default_params()
         if stream is not None:
@@ -309,7 +315,7 @@ class Hierarchy:
         A = rn_csr(n, n, int(col.shape[0]), _ptr(rowptr), _ptr(col), _ptr(val))
         h = C.c_void_p()
         self._keep = (rowptr, col, val, B, Bhat)
-        st = rn_setup(C.byref(A), _ptr(B), _ptr(Bhat) if Bhat is not None else None, 1,
+        st = rn_setup(C.byref(A), _ptr(B), _ptr(Bhat) if Bhat is not None else None, k,
                       RN_HOST if host else RN_DEVICE, C.byref(self.params), C.byref(h))
         self._keep = None
         _check(st, "rn_setup")
@@ -376,12 +382,14 @@ class Hierarchy:
         return rp, ci[: nz.value], va[: nz.value], (nr.value, nc.value)
 
     def export_vec(self, lvl: int, which: int):
-        """0 agg, 1 roots, 2 row types (int32); 3 B, 4 Bc, 5 Bhat, 6 Bhat_c (float64)."""
+        """0 agg, 1 roots, 2 row types (int32); 3 B, 4 Bc, 5 Bhat, 6 Bhat_c (float64; n x k when k > 1)."""
         ln = C.c_int64()
         _check(rn_export_vec(self._h, lvl, which, C.byref(ln), None), "rn_export_vec")
         out = np.zeros(max(ln.value, 1), np.int32 if which <= 2 else np.float64)
         _check(rn_export_vec(self._h, lvl, which, C.byref(ln), out.ctypes.data), "rn_export_vec")
-        return out[: ln.value]
+        out = out[: ln.value]
+        k = getattr(self, "k", 1)
+        return out.reshape(-1, k) if which >= 3 and k > 1 else out
 
 
 def profile_enable(on: bool = True):

@@ -54,8 +54,9 @@ def test_setup_rejects_bad_arguments_without_gpu(rn):
     A = rn.rn_csr(0, 0, 0, None, None, None)
     assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, 1, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
     A = rn.rn_csr(4, 4, 4, C.c_void_p(8), C.c_void_p(8), C.c_void_p(8))
-    assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, 2, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
-    assert b"candidate" in rn.rn_last_error()
+    for k in (0, 5):  # 1 <= k <= RN_MAX_CANDIDATES = 4
+        assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, k, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
+        assert b"k must be" in rn.rn_last_error()
     p.degree = -1
     assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, 1, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
     p = rn.default_params(symmetric=0)
