@@ -442,7 +442,8 @@ void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc) {
 
 /* Pseudo-inverse of a symmetric k x k matrix (k <= ORC_KMAX, row-major) by the
  * cyclic Jacobi eigenvalue method (rotations zeroing one off-diagonal pair at
- * a time until the off-diagonal mass is negligible); eigenvalues at most
+ * a time until a sweep finds every off-diagonal below 1e-18 of its diagonal
+ * pair, at most 16 sweeps); eigenvalues at most
  * 1e-6 of the largest are dropped (singular values of Bc_J below 1e-3 of the
  * largest): candidate combinations that are nearly dependent on a row's
  * pattern stay unfitted, which bounds the fit's amplification by 1e6. */
@@ -452,18 +453,14 @@ int orc_sym_pinv(int k, const double *G, double *Gp) {
     for (int i = 0; i < k * k; i++) a[i] = G[i];
     for (int i = 0; i < k; i++)
         for (int j = 0; j < k; j++) v[i * k + j] = (i == j);
-    for (int sweep = 0; sweep < 64; sweep++) {
-        double off = 0.0, dia = 0.0;
-        for (int i = 0; i < k; i++)
-            for (int j = 0; j < k; j++) {
-                if (i == j) dia += a[i * k + i] * a[i * k + i];
-                else off += a[i * k + j] * a[i * k + j];
-            }
-        if (off <= 1e-32 * dia || off == 0.0) break;
+    for (int sweep = 0; sweep < 16; sweep++) {
+        int rotated = 0;
         for (int p = 0; p < k - 1; p++)
             for (int q = p + 1; q < k; q++) {
                 double apq = a[p * k + q];
-                if (apq == 0.0) continue;
+                /* negligible against the diagonal pair (1e-18 relative): no rotation */
+                if (apq * apq <= 1e-36 * fabs(a[p * k + p] * a[q * k + q])) continue;
+                rotated = 1;
                 double th = (a[q * k + q] - a[p * k + p]) / (2.0 * apq);
                 double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
                 double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
@@ -483,6 +480,7 @@ int orc_sym_pinv(int k, const double *G, double *Gp) {
                     v[r * k + q] = sn * vrp + c * vrq;
                 }
             }
+        if (!rotated) break; /* every off-diagonal negligible: converged */
     }
     double lmax = 0.0;
     for (int i = 0; i < k; i++) if (fabs(a[i * k + i]) > lmax) lmax = fabs(a[i * k + i]);

@@ -324,117 +324,147 @@ __global__ void gather_k_kernel(int32_t nc, int k, const int32_t *__restrict__ r
     }
 }
 
-// Pseudo-inverse of the symmetric k x k matrix g (k <= RN_MAX_CANDIDATES,
-// row-major, overwritten) into gp: eigen-decomposition by cyclic Jacobi
-// rotations (each zeroes one off-diagonal pair; sweeps until the off-diagonal
-// mass is negligible), eigenvalues at most 1e-6 of the largest dropped:
-// candidate combinations nearly dependent on a row's pattern stay unfitted,
-// bounding the fit's amplification of rounding by 1e6.
-__device__ int sym_pinv_dev(int k, double *g, double *gp) {
-    double v[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES];
-    for (int i = 0; i < k; i++)
-        for (int j = 0; j < k; j++) v[i * k + j] = (i == j) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 64; sweep++) {
-        double off = 0.0, dia = 0.0;
-        for (int i = 0; i < k; i++)
-            for (int j = 0; j < k; j++) {
-                const double x = g[i * k + j] * g[i * k + j];
-                if (i == j) dia += x;
-                else off += x;
-            }
-        if (off == 0.0 || off <= 1e-32 * dia) break;
-        for (int p = 0; p < k - 1; p++)
-            for (int q = p + 1; q < k; q++) {
-                const double apq = g[p * k + q];
-                if (apq == 0.0) continue;
-                const double th = (g[q * k + q] - g[p * k + p]) / (2.0 * apq);
+// Pseudo-inverse of the symmetric K x K matrix g (row-major, overwritten)
+// into gp: eigen-decomposition by cyclic Jacobi rotations (each zeroes one
+// off-diagonal pair; sweeps until a whole sweep finds every off-diagonal
+// below 1e-18 of its diagonal pair, at most 16), with
+// eigenvalues at most 1e-6 of the largest dropped: candidate combinations
+// nearly dependent on a row's pattern stay unfitted, bounding the fit's
+// amplification of rounding by 1e6.  K is a template argument so that the
+// matrices stay in registers.  Returns the number of eigenvalues kept.
+template <int K>
+__device__ int sym_pinv_dev(double (&g)[K * K], double (&gp)[K * K]) {
+    double v[K * K];
+#pragma unroll
+    for (int i = 0; i < K; i++)
+#pragma unroll
+        for (int j = 0; j < K; j++) v[i * K + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 16; sweep++) {
+        bool rotated = false;
+#pragma unroll
+        for (int p = 0; p < K - 1; p++)
+#pragma unroll
+            for (int q = p + 1; q < K; q++) {
+                const double apq = g[p * K + q];
+                // negligible against the diagonal pair (1e-18 relative): no rotation
+                if (apq * apq <= 1e-36 * fabs(g[p * K + p] * g[q * K + q])) continue;
+                rotated = true;
+                const double th = (g[q * K + q] - g[p * K + p]) / (2.0 * apq);
                 const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
                 const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-                for (int r = 0; r < k; r++) {
-                    const double x = g[r * k + p], y = g[r * k + q];
-                    g[r * k + p] = c * x - sn * y;
-                    g[r * k + q] = sn * x + c * y;
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const double x = g[r * K + p], y = g[r * K + q];
+                    g[r * K + p] = c * x - sn * y;
+                    g[r * K + q] = sn * x + c * y;
                 }
-                for (int r = 0; r < k; r++) {
-                    const double x = g[p * k + r], y = g[q * k + r];
-                    g[p * k + r] = c * x - sn * y;
-                    g[q * k + r] = sn * x + c * y;
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const double x = g[p * K + r], y = g[q * K + r];
+                    g[p * K + r] = c * x - sn * y;
+                    g[q * K + r] = sn * x + c * y;
                 }
-                for (int r = 0; r < k; r++) {
-                    const double x = v[r * k + p], y = v[r * k + q];
-                    v[r * k + p] = c * x - sn * y;
-                    v[r * k + q] = sn * x + c * y;
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const double x = v[r * K + p], y = v[r * K + q];
+                    v[r * K + p] = c * x - sn * y;
+                    v[r * K + q] = sn * x + c * y;
                 }
             }
+        if (!rotated) break;  // every off-diagonal negligible: converged
     }
     double lmax = 0.0;
-    for (int i = 0; i < k; i++) lmax = fmax(lmax, fabs(g[i * k + i]));
-    for (int i = 0; i < k * k; i++) gp[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < K; i++) lmax = fmax(lmax, fabs(g[i * K + i]));
+#pragma unroll
+    for (int i = 0; i < K * K; i++) gp[i] = 0.0;
     int rank = 0;
-    for (int e = 0; e < k; e++) {
-        const double lam = g[e * k + e];
+#pragma unroll
+    for (int e = 0; e < K; e++) {
+        const double lam = g[e * K + e];
         if (!(lam > 1e-6 * lmax)) continue;
         rank++;
-        for (int i = 0; i < k; i++)
-            for (int j = 0; j < k; j++) gp[i * k + j] += v[i * k + e] * v[j * k + e] / lam;
+        const double il = 1.0 / lam;
+#pragma unroll
+        for (int i = 0; i < K; i++)
+#pragma unroll
+            for (int j = 0; j < K; j++) gp[i * K + j] += v[i * K + e] * v[j * K + e] * il;
     }
-    return rank;  // eigenvalues kept
+    return rank;
 }
 
 // G_i^+ of every row's Gram matrix G_i = Bc_J^T Bc_J on its pattern J, and
 // whether the constraints fix the row (no more pattern entries than the rank
 // of Bc_J: constraint space {0}, like a one-entry row for k = 1); fixed,
 // one-entry and such rows are projected to exactly 0.
-__global__ void gram_pinv_kernel(int32_t n, int k, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+template <int K>
+__global__ void gram_pinv_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                  const int32_t *__restrict__ rowtype, const double *__restrict__ Bc,
                                  double *__restrict__ Gp, int32_t *__restrict__ zero_row) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double g[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES] = {}, gp[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES] = {};
+        double g[K * K] = {}, gp[K * K] = {};
         const int32_t len = rp[i + 1] - rp[i];
         int z = 1;
         if (rowtype[i] == FREE_ROW && len > 1) {
             for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
-                const double *b = Bc + (int64_t)col[e] * k;
-                for (int a = 0; a < k; a++)
-                    for (int c = 0; c < k; c++) g[a * k + c] += b[a] * b[c];
+                const double *b = Bc + (int64_t)col[e] * K;
+#pragma unroll
+                for (int a = 0; a < K; a++)
+#pragma unroll
+                    for (int c = 0; c < K; c++) g[a * K + c] += b[a] * b[c];
             }
-            z = sym_pinv_dev(k, g, gp) >= len;
+            z = sym_pinv_dev<K>(g, gp) >= len;
         }
-        for (int q = 0; q < k * k; q++) Gp[(int64_t)i * k * k + q] = gp[q];
+#pragma unroll
+        for (int q = 0; q < K * K; q++) Gp[(int64_t)i * K * K + q] = gp[q];
         zero_row[i] = z;
     }
 }
 
 // Minimal-norm fit of every free row (eq. Tproj): (t + u) Bc_J = B_i with
 // u_j = ((B_i - t Bc_J) G_i^+) . Bc_j; T's construction and enforce for k > 1.
-__global__ void row_fit_k_kernel(int32_t n, int k, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+template <int K>
+__global__ void row_fit_k_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                  double *__restrict__ val, const int32_t *__restrict__ rowtype,
                                  const double *__restrict__ B, const double *__restrict__ Bc) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (rowtype[i] != FREE_ROW) continue;
-        double g[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES] = {}, gp[RN_MAX_CANDIDATES * RN_MAX_CANDIDATES];
-        double r[RN_MAX_CANDIDATES], y[RN_MAX_CANDIDATES];
-        for (int a = 0; a < k; a++) r[a] = B[(int64_t)i * k + a];
+        double g[K * K] = {}, gp[K * K], r[K], y[K];
+#pragma unroll
+        for (int a = 0; a < K; a++) r[a] = B[(int64_t)i * K + a];
         for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
-            const double *b = Bc + (int64_t)col[e] * k;
-            for (int a = 0; a < k; a++) {
+            const double *b = Bc + (int64_t)col[e] * K;
+#pragma unroll
+            for (int a = 0; a < K; a++) {
                 r[a] -= val[e] * b[a];
-                for (int c = 0; c < k; c++) g[a * k + c] += b[a] * b[c];
+#pragma unroll
+                for (int c = 0; c < K; c++) g[a * K + c] += b[a] * b[c];
             }
         }
-        sym_pinv_dev(k, g, gp);
-        for (int c = 0; c < k; c++) {
+        sym_pinv_dev<K>(g, gp);
+#pragma unroll
+        for (int c = 0; c < K; c++) {
             y[c] = 0.0;
-            for (int a = 0; a < k; a++) y[c] += r[a] * gp[a * k + c];
+#pragma unroll
+            for (int a = 0; a < K; a++) y[c] += r[a] * gp[a * K + c];
         }
         for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
-            const double *b = Bc + (int64_t)col[e] * k;
+            const double *b = Bc + (int64_t)col[e] * K;
             double u = 0.0;
-            for (int c = 0; c < k; c++) u += y[c] * b[c];
+#pragma unroll
+            for (int c = 0; c < K; c++) u += y[c] * b[c];
             val[e] += u;
         }
     }
 }
+
+// launch of a K-templated row kernel for the runtime k (2..RN_MAX_CANDIDATES)
+#define RN_K_SWITCH(k, CALL)          \
+    switch (k) {                      \
+        case 2: { constexpr int KK = 2; CALL; } break; \
+        case 3: { constexpr int KK = 3; CALL; } break; \
+        default: { constexpr int KK = 4; CALL; } break; \
+    }
 
 // ------------------------------------------------------------------ pattern (Sec. 3.4-3.5)
 __global__ void aggflag_kernel(int32_t n, const int32_t *__restrict__ agg, int32_t *__restrict__ flag) {
@@ -503,9 +533,9 @@ __global__ void tentative_kernel(int32_t n, const int32_t *__restrict__ rp, cons
 // W <- scale (W - (c G_i^+) Bc_J) with c = W_i Bc_J on every free row of more
 // than one entry (eq. Tproj with a zero right-hand side); the product kernels
 // ran unprojected (their row scales are zero).  <Y, W> finishes in Fin.
-template <typename TV>
+template <typename TV, int K>
 __global__ void __launch_bounds__(256)
-proj_k_kernel(int32_t n, int k, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
+proj_k_kernel(int32_t n, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
               const int32_t *__restrict__ zero_row, const TV *__restrict__ Bc, const TV *__restrict__ Gp,
               TV *__restrict__ W, TV scale, const TV *__restrict__ Y, Fin fin) {
     __shared__ double s_red[32];
@@ -516,18 +546,22 @@ proj_k_kernel(int32_t n, int k, const int32_t *__restrict__ nrp, const int32_t *
             for (int32_t q = cs; q < ce; q++) W[q] = TV(0);
             continue;
         }
-        TV c[RN_MAX_CANDIDATES] = {}, y[RN_MAX_CANDIDATES] = {};
+        TV c[K] = {}, y[K] = {};
         for (int32_t q = cs; q < ce; q++) {
-            const TV *b = Bc + (int64_t)ncol[q] * k;
-            for (int a = 0; a < k; a++) c[a] = fma(W[q], b[a], c[a]);
+            const TV *b = Bc + (int64_t)ncol[q] * K;
+#pragma unroll
+            for (int a = 0; a < K; a++) c[a] = fma(W[q], b[a], c[a]);
         }
-        const TV *g = Gp + (int64_t)i * k * k;
-        for (int b = 0; b < k; b++)
-            for (int a = 0; a < k; a++) y[b] = fma(c[a], g[a * k + b], y[b]);
+        const TV *g = Gp + (int64_t)i * K * K;
+#pragma unroll
+        for (int b = 0; b < K; b++)
+#pragma unroll
+            for (int a = 0; a < K; a++) y[b] = fma(c[a], g[a * K + b], y[b]);
         for (int32_t q = cs; q < ce; q++) {
-            const TV *b = Bc + (int64_t)ncol[q] * k;
+            const TV *b = Bc + (int64_t)ncol[q] * K;
             TV u = TV(0);
-            for (int a = 0; a < k; a++) u = fma(y[a], b[a], u);
+#pragma unroll
+            for (int a = 0; a < K; a++) u = fma(y[a], b[a], u);
             const TV w = scale * (W[q] - u);
             W[q] = w;
             if (Y) dot = fma(Y[q], w, dot);
@@ -551,8 +585,9 @@ struct KProj {
         if (k == 1) return;
         gp64.alloc((size_t)N.n * k * k, s);
         zero_row.alloc(N.n, s);
-        RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 8.0 * k * N.nnz + 8.0 * k * k * N.n, s, gram_pinv_kernel,
-                  grid_for(N.n, 256), 256, 0, N.n, k, N.rp, N.col, rowtype, Bc, gp64.p, zero_row.p);
+        RN_K_SWITCH(k, RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 8.0 * k * N.nnz + 8.0 * k * k * N.n, s,
+                                 gram_pinv_kernel<KK>, grid_for(N.n, 256), 256, 0, N.n, N.rp, N.col, rowtype, Bc,
+                                 gp64.p, zero_row.p));
         if constexpr (sizeof(TV) == 4) {
             gpv.alloc((size_t)N.n * k * k, s);
             bcv.alloc((size_t)N.nc * k, s);
@@ -567,9 +602,11 @@ struct KProj {
     }
     void apply(const Pattern &N, const int32_t *rowtype, TV *W, double scale, const TV *Y, const Fin &f,
                cudaStream_t s) const {
-        const int g = grid_resident(proj_k_kernel<TV>, 256, 0, N.n, 256, kReduceBlocks);
-        RN_LAUNCH("energy_masked_product", (2.0 * sizeof(TV) + 4.0 + sizeof(TV) * k) * N.nnz, s, proj_k_kernel<TV>,
-                  g, 256, 0, N.n, k, N.rp, N.col, zero_row.p, bc, gp, W, (TV)scale, Y, f);
+        RN_K_SWITCH(k, {
+            const int g = grid_resident(proj_k_kernel<TV, KK>, 256, 0, N.n, 256, kReduceBlocks);
+            RN_LAUNCH("energy_masked_product", (2.0 * sizeof(TV) + 4.0 + sizeof(TV) * k) * N.nnz, s,
+                      (proj_k_kernel<TV, KK>), g, 256, 0, N.n, N.rp, N.col, zero_row.p, bc, gp, W, (TV)scale, Y, f);
+        });
     }
 };
 
@@ -1156,8 +1193,8 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
     RN_LAUNCH("tentative", 16.0 * N.nnz + 16.0 * n, s, tentative_kernel, rows_grid(n), kT, 0, n, N.rowptr.p, N.col.p,
               agg, Bsm, Bc, Pout.val.p, k);
     if (k > 1)  // the other candidates: minimal-norm row fits (eq. Tproj)
-        RN_LAUNCH("tentative", 12.0 * N.nnz + 8.0 * k * (N.nnz + n), s, row_fit_k_kernel, rows_grid(n), kT, 0, n, k,
-                  Pout.rowptr.p, Pout.col.p, Pout.val.p, rowtype, Bsm, Bc);
+        RN_K_SWITCH(k, RN_LAUNCH("tentative", 12.0 * N.nnz + 8.0 * k * (N.nnz + n), s, row_fit_k_kernel<KK>,
+                                 rows_grid(n), kT, 0, n, Pout.rowptr.p, Pout.col.p, Pout.val.p, rowtype, Bsm, Bc));
     if (Tkeep) {
         Tkeep->n = n; Tkeep->m = nc; Tkeep->nnz = N.nnz;
         Tkeep->rowptr.alloc(n + 1, s); Tkeep->col.alloc(N.nnz, s); Tkeep->val.alloc(N.nnz, s);
@@ -1187,8 +1224,8 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
             RN_LAUNCH("enforce", 28.0 * F.nnz + 8.0 * n, s, enforce_kernel, rows_grid(n), kT, 0, n, F.rowptr.p,
                       F.col.p, F.val.p, rowtype, Bsm, Bc);
         else
-            RN_LAUNCH("enforce", 12.0 * F.nnz + 8.0 * k * (F.nnz + n), s, row_fit_k_kernel, rows_grid(n), kT, 0, n,
-                      k, F.rowptr.p, F.col.p, F.val.p, rowtype, Bsm, Bc);
+            RN_K_SWITCH(k, RN_LAUNCH("enforce", 12.0 * F.nnz + 8.0 * k * (F.nnz + n), s, row_fit_k_kernel<KK>,
+                                     rows_grid(n), kT, 0, n, F.rowptr.p, F.col.p, F.val.p, rowtype, Bsm, Bc));
         Pout = std::move(F);
         Pattern pf{n, nc, Pout.nnz, Pout.rowptr.p, Pout.col.p};
         energy_min(ctx_of(h), A, pf, Pout.val.p, rowtype, Bc, dinv.p, 1);
@@ -1287,7 +1324,9 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
                       r1.p);
             RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_remove_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, r1.p,
                       state.p, h.iflags.p + 5);
-            if (read_scalar(h.iflags.p + 5, s) == 0) break;
+            // read the flag every second round: a round after the last is a no-op
+            // (no undecided node), cheaper than a host synchronisation
+            if ((rounds & 1) == 1 && read_scalar(h.iflags.p + 5, s) == 0) break;
         }
         h.agg_rounds += rounds + 1;
         DVec<int32_t> cidx(n + 1, s);
