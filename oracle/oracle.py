@@ -49,7 +49,8 @@ class _Params(C.Structure):
                 ("prefilter", C.c_double), ("postfilter", C.c_double), ("max_coarse", C.c_int),
                 ("max_levels", C.c_int), ("b_sweeps", C.c_int), ("omega", C.c_double), ("seed", C.c_uint64),
                 ("symmetric", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int), ("precond", C.c_int),
-                ("soc_theta_coarse", C.c_double), ("gamma", C.c_int), ("soc_kind", C.c_int), ("ncand", C.c_int)]
+                ("soc_theta_coarse", C.c_double), ("gamma", C.c_int), ("soc_kind", C.c_int), ("ncand", C.c_int),
+                ("block_size", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -77,6 +78,7 @@ def lib():
         L.orc_smooth_candidates_k.argtypes = [P(_CSR), dp, C.c_int, C.c_int, C.c_double]
         L.orc_sym_pinv.argtypes = [C.c_int, dp, dp]
         L.orc_sym_pinv.restype = C.c_int
+        L.orc_amalgamate.argtypes = [P(_CSR), C.c_int, P(_CSR)]
         L.orc_aggregate.argtypes = [P(_CSR), C.c_uint64, i32p, P(i32p), i32p]
         L.orc_splitmix64.argtypes = [C.c_uint64]
         L.orc_splitmix64.restype = C.c_uint64
@@ -170,6 +172,13 @@ def strength_classical(A, theta: float) -> sp.csr_matrix:
     S = _CSR()
     _check(lib().orc_strength_classical(C.byref(a.s), theta, C.byref(S)), "strength_classical")
     return _out(S)
+
+
+def amalgamate(S, m: int) -> sp.csr_matrix:
+    s_ = _In(S)
+    out = _CSR()
+    _check(lib().orc_amalgamate(C.byref(s_.s), m, C.byref(out)), "amalgamate")
+    return _out(out)
 
 
 def aggregate(S, seed: int):
@@ -341,7 +350,7 @@ def lu_solve_dense(M: np.ndarray, rhs: np.ndarray) -> np.ndarray:
 def make_params(**kw) -> _Params:
     d = dict(soc_theta=0.25, degree=2, n_sweeps=4, method=0, prefilter=0.0, postfilter=0.0, max_coarse=64,
              max_levels=25, b_sweeps=4, omega=2.0 / 3.0, seed=12345, symmetric=1, nu_pre=1, nu_post=1, precond=1,
-             soc_theta_coarse=-1.0, gamma=1, soc_kind=0, ncand=1)
+             soc_theta_coarse=-1.0, gamma=1, soc_kind=0, ncand=1, block_size=1)
     for k, v in kw.items():
         if k in d:
             d[k] = v

@@ -52,6 +52,7 @@ typedef struct {
     int gamma;         /* coarse-grid corrections per level: 1 V-cycle, 2 W-cycle */
     int soc_kind;      /* 0 symmetric strength, 1 classical strength */
     int ncand;         /* k, the number of candidate vectors (B is n x k, row-major) */
+    int block_size;    /* m, unknowns per node (node-major; 1 = scalar problem) */
 } orc_params;
 
 /* Row classes of the interpolation pattern. */
@@ -92,6 +93,13 @@ int orc_energy_min_cg_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, co
 int orc_energy_min_gmres_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc, int k,
                            int m, double *res_trace);
 int orc_sym_pinv(int k, const double *G, double *Gp);  /* returns the rank kept */
+/* systems (block size m > 1) */
+int orc_amalgamate(const orc_csr *S, int m, orc_csr *Sm);
+int orc_postfilter_m(const orc_csr *P, const int32_t *agg, const int32_t *rowtype, double theta, int mb,
+                     orc_csr *Pf, int64_t *near_ties);
+int orc_unamalgamate_pattern(const orc_csr *Nm, int m, const int32_t *agg, const int32_t *rowtype, orc_csr *N);
+int orc_tentative_block(orc_csr *N, const int32_t *agg, const int32_t *roots, const int32_t *rowtype, const double *B,
+                        int k, int m, double *Bc);
 void orc_masked_product(const orc_csr *A, const orc_csr *X, orc_csr *W);
 void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc);
 int orc_energy_min_cg(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc,

@@ -773,6 +773,12 @@ int orc_energy_min_gmres_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype,
  */
 int orc_postfilter(const orc_csr *P, const int32_t *agg, const int32_t *rowtype, double theta,
                    orc_csr *Pf, int64_t *near_ties) {
+    return orc_postfilter_m(P, agg, rowtype, theta, 1, Pf, near_ties);
+}
+
+/* m > 1: the row's own aggregate is the block of columns m agg .. m agg + m - 1 */
+int orc_postfilter_m(const orc_csr *P, const int32_t *agg, const int32_t *rowtype, double theta, int mb,
+                     orc_csr *Pf, int64_t *near_ties) {
     int32_t n = P->nrows;
     char *keep = (char *)orc_xcalloc((size_t)P->nnz, 1);
     int32_t *rowptr = (int32_t *)orc_xcalloc((size_t)n + 1, sizeof(int32_t));
@@ -786,8 +792,9 @@ int orc_postfilter(const orc_csr *P, const int32_t *agg, const int32_t *rowtype,
             double thr = theta * m * (1.0 - ORC_GUARD);
             double ref = theta * m;
             for (int32_t e = P->rowptr[i]; e < P->rowptr[i + 1]; e++) {
-                int k = (fabs(P->val[e]) >= thr) || (P->col[e] == agg[i]);
-                if (P->col[e] != agg[i] && fabs(fabs(P->val[e]) - ref) < 1e-9 * ref) ties++;
+                int own = (P->col[e] / mb == agg[i]);
+                int k = (fabs(P->val[e]) >= thr) || own;
+                if (!own && fabs(fabs(P->val[e]) - ref) < 1e-9 * ref) ties++;
                 keep[e] = (char)k;
                 cnt += k;
             }
@@ -827,6 +834,157 @@ void orc_enforce(orc_csr *P, const int32_t *rowtype, const double *B, const doub
         for (int32_t e = P->rowptr[i]; e < P->rowptr[i + 1]; e++)
             P->val[e] = P->val[e] + c * Bc[P->col[e]];
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Systems (Sec. 3.2 amalgamate, Sec. 3.4 unamalgamate, Sec. 3.6 eq.
+ * root-nodeform for m > 1): unknowns node-major, m per node. */
+
+/* S_m(I, J) = the largest entry of S's m x m block (I, J), over the entries
+ * S stores; columns ascending. */
+int orc_amalgamate(const orc_csr *S, int m, orc_csr *Sm) {
+    int32_t nn = S->nrows / m;
+    int32_t *rowptr = (int32_t *)orc_xcalloc((size_t)nn + 1, sizeof(int32_t));
+    double *acc = (double *)orc_xmalloc((size_t)nn * sizeof(double));
+    char *seen = (char *)orc_xcalloc((size_t)nn, 1);
+    int32_t *list = (int32_t *)orc_xmalloc((size_t)nn * sizeof(int32_t));
+    /* pass 1: count */
+    for (int32_t I = 0; I < nn; I++) {
+        int32_t cnt = 0;
+        for (int32_t i = I * m; i < I * m + m; i++)
+            for (int32_t e = S->rowptr[i]; e < S->rowptr[i + 1]; e++) {
+                int32_t J = S->col[e] / m;
+                if (!seen[J]) { seen[J] = 1; list[cnt++] = J; }
+            }
+        for (int32_t q = 0; q < cnt; q++) seen[list[q]] = 0;
+        rowptr[I + 1] = rowptr[I] + cnt;
+    }
+    Sm->nrows = Sm->ncols = nn;
+    Sm->nnz = rowptr[nn];
+    Sm->rowptr = rowptr;
+    Sm->col = (int32_t *)orc_xmalloc((size_t)(Sm->nnz > 0 ? Sm->nnz : 1) * sizeof(int32_t));
+    Sm->val = (double *)orc_xmalloc((size_t)(Sm->nnz > 0 ? Sm->nnz : 1) * sizeof(double));
+    /* pass 2: block maxima, columns sorted */
+    for (int32_t I = 0; I < nn; I++) {
+        int32_t cnt = 0;
+        for (int32_t i = I * m; i < I * m + m; i++)
+            for (int32_t e = S->rowptr[i]; e < S->rowptr[i + 1]; e++) {
+                int32_t J = S->col[e] / m;
+                if (!seen[J]) { seen[J] = 1; acc[J] = S->val[e]; list[cnt++] = J; }
+                else if (S->val[e] > acc[J]) acc[J] = S->val[e];
+            }
+        for (int32_t a = 1; a < cnt; a++) { /* insertion sort of the row's columns */
+            int32_t x = list[a], b = a - 1;
+            while (b >= 0 && list[b] > x) { list[b + 1] = list[b]; b--; }
+            list[b + 1] = x;
+        }
+        for (int32_t q = 0; q < cnt; q++) {
+            Sm->col[rowptr[I] + q] = list[q];
+            Sm->val[rowptr[I] + q] = acc[list[q]];
+            seen[list[q]] = 0;
+        }
+    }
+    free(acc); free(seen); free(list);
+    return ORC_OK;
+}
+
+/* N(i, m J + c) = N_m(floor(i/m), J) for c < m; root rows become identity
+ * rows: root unknown i of aggregate a has the single entry (i, m a + i mod m). */
+int orc_unamalgamate_pattern(const orc_csr *Nm, int m, const int32_t *agg, const int32_t *rowtype, orc_csr *N) {
+    int32_t n = Nm->nrows * m;
+    int32_t *rowptr = (int32_t *)orc_xcalloc((size_t)n + 1, sizeof(int32_t));
+    for (int32_t i = 0; i < n; i++) {
+        int32_t I = i / m;
+        int32_t cnt = rowtype[i] == ORC_ROOT ? 1 : m * (Nm->rowptr[I + 1] - Nm->rowptr[I]);
+        rowptr[i + 1] = rowptr[i] + cnt;
+    }
+    N->nrows = n;
+    N->ncols = Nm->ncols * m;
+    N->nnz = rowptr[n];
+    N->rowptr = rowptr;
+    N->col = (int32_t *)orc_xmalloc((size_t)(N->nnz > 0 ? N->nnz : 1) * sizeof(int32_t));
+    N->val = (double *)orc_xmalloc((size_t)(N->nnz > 0 ? N->nnz : 1) * sizeof(double));
+    for (int32_t i = 0; i < n; i++) {
+        int32_t I = i / m, dst = rowptr[i];
+        if (rowtype[i] == ORC_ROOT) {
+            N->col[dst] = m * agg[i] + i % m;
+            N->val[dst] = 1.0;
+            continue;
+        }
+        for (int32_t e = Nm->rowptr[I]; e < Nm->rowptr[I + 1]; e++)
+            for (int c = 0; c < m; c++) {
+                N->col[dst] = m * Nm->col[e] + c;
+                N->val[dst++] = Nm->val[e];
+            }
+    }
+    return ORC_OK;
+}
+
+/* T for block size m (eq. root-nodeform): Bc = B at the root unknowns; the
+ * first m candidates are injected over each aggregate and normalised by the
+ * root node's m x m block, T_i,(m a + .) = B_i,0:m Broot_a^{-1}, so root
+ * rows are identity rows; candidates beyond m are then fitted row by row
+ * (eq. Tproj).  agg is the node aggregate of every unknown, roots lists the
+ * root unknowns (m per aggregate, m a + c at position m a + c). */
+int orc_tentative_block(orc_csr *N, const int32_t *agg, const int32_t *roots, const int32_t *rowtype, const double *B,
+                        int k, int m, double *Bc) {
+    if (m > ORC_KMAX || k < m) return ORC_EINVAL;
+    int32_t nc = N->ncols, na = nc / m;
+    for (int32_t c = 0; c < nc; c++)
+        for (int a = 0; a < k; a++) Bc[(size_t)c * k + a] = B[(size_t)roots[c] * k + a];
+    double *Binv = (double *)orc_xmalloc((size_t)na * m * m * sizeof(double));
+    for (int32_t a = 0; a < na; a++) { /* Gauss-Jordan with partial pivoting on the m x m root block */
+        double M[ORC_KMAX * ORC_KMAX], X[ORC_KMAX * ORC_KMAX];
+        double amax = 0.0;
+        for (int r = 0; r < m; r++)
+            for (int c = 0; c < m; c++) {
+                M[r * m + c] = B[(size_t)roots[m * a + r] * k + c];
+                X[r * m + c] = (r == c);
+                if (fabs(M[r * m + c]) > amax) amax = fabs(M[r * m + c]);
+            }
+        for (int col = 0; col < m; col++) {
+            int piv = col;
+            for (int r = col + 1; r < m; r++) if (fabs(M[r * m + col]) > fabs(M[piv * m + col])) piv = r;
+            if (!(fabs(M[piv * m + col]) > 1e-12 * amax)) { free(Binv); return ORC_EINVAL; }
+            for (int c = 0; c < m; c++) {
+                double t = M[col * m + c]; M[col * m + c] = M[piv * m + c]; M[piv * m + c] = t;
+                t = X[col * m + c]; X[col * m + c] = X[piv * m + c]; X[piv * m + c] = t;
+            }
+            double d = M[col * m + col];
+            for (int c = 0; c < m; c++) { M[col * m + c] = M[col * m + c] / d; X[col * m + c] = X[col * m + c] / d; }
+            for (int r = 0; r < m; r++) {
+                if (r == col) continue;
+                double f = M[r * m + col];
+                for (int c = 0; c < m; c++) {
+                    M[r * m + c] = M[r * m + c] - f * M[col * m + c];
+                    X[r * m + c] = X[r * m + c] - f * X[col * m + c];
+                }
+            }
+        }
+        memcpy(Binv + (size_t)a * m * m, X, (size_t)m * m * sizeof(double));
+    }
+    for (int32_t i = 0; i < N->nrows; i++) {
+        int32_t s = N->rowptr[i], e = N->rowptr[i + 1];
+        for (int32_t q = s; q < e; q++) N->val[q] = 0.0;
+        if (agg[i] < 0) continue;
+        int32_t a = agg[i];
+        if (rowtype[i] == ORC_ROOT) {
+            for (int32_t q = s; q < e; q++) N->val[q] = (N->col[q] == m * a + i % m) ? 1.0 : 0.0;
+            continue;
+        }
+        const double *bi = B + (size_t)i * k, *Xi = Binv + (size_t)a * m * m;
+        for (int32_t q = s; q < e; q++) {
+            int32_t col = N->col[q];
+            if (col / m != a) continue;
+            int c = col % m;
+            double t = 0.0;
+            for (int r = 0; r < m; r++) t += bi[r] * Xi[r * m + c];
+            N->val[q] = t;
+        }
+        if (k > m) row_fit_k(s, e, N->col, N->val, bi, Bc, k);
+    }
+    free(Binv);
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -896,16 +1054,18 @@ static int build_transfer(const orc_csr *A, const orc_csr *N, const int32_t *agg
                           const int32_t *rowtype, const double *Bsm, const orc_params *p, orc_csr *Pout,
                           double *Bc, int64_t *near_ties) {
     const int k = p->ncand > 0 ? p->ncand : 1;
+    const int mb = p->block_size > 0 ? p->block_size : 1;
     orc_csr P;
     orc_csr_copy(N, &P);
-    int rc = orc_tentative_k(&P, agg, roots, rowtype, Bsm, k, Bc);
+    int rc = mb > 1 ? orc_tentative_block(&P, agg, roots, rowtype, Bsm, k, mb, Bc)
+                    : orc_tentative_k(&P, agg, roots, rowtype, Bsm, k, Bc);
     if (rc) { orc_csr_free(&P); return rc; }
     rc = (p->method == 0) ? orc_energy_min_cg_k(A, &P, rowtype, Bc, k, p->n_sweeps, p->precond, NULL)
                           : orc_energy_min_gmres_k(A, &P, rowtype, Bc, k, p->n_sweeps, NULL);
     if (rc) { orc_csr_free(&P); return rc; }
     if (p->postfilter > 0.0) {
         orc_csr Pf;
-        orc_postfilter(&P, agg, rowtype, p->postfilter, &Pf, near_ties);
+        orc_postfilter_m(&P, agg, rowtype, p->postfilter, mb, &Pf, near_ties);
         orc_csr_free(&P);
         orc_enforce_k(&Pf, rowtype, Bsm, Bc, k);
         rc = (p->method == 0) ? orc_energy_min_cg_k(A, &Pf, rowtype, Bc, k, 1, p->precond, NULL)
@@ -928,7 +1088,8 @@ int orc_setup(const orc_csr *A0, const double *B0, const double *Bhat0, const or
     int cap = p->max_levels > 0 ? p->max_levels : 1;
     h->lev = (orc_level *)orc_xcalloc((size_t)cap, sizeof(orc_level));
     const int k = p->ncand > 0 ? p->ncand : 1;
-    if (k > ORC_KMAX) { free(h->lev); free(h); return ORC_EINVAL; }
+    const int mb = p->block_size > 0 ? p->block_size : 1;
+    if (k > ORC_KMAX || k < mb || A0->nrows % mb != 0) { free(h->lev); free(h); return ORC_EINVAL; }
     orc_level *L = &h->lev[0];
     orc_csr_copy(A0, &L->A);
     int32_t n = A0->nrows;
@@ -949,21 +1110,46 @@ int orc_setup(const orc_csr *A0, const double *B0, const double *Bhat0, const or
                               : orc_strength(&L->A, theta, &L->S);
         if (rc) break;
         L->agg = (int32_t *)orc_xmalloc((size_t)n * sizeof(int32_t));
-        rc = orc_aggregate(&L->S, p->seed + (uint64_t)lvl, L->agg, &L->roots, &L->nc); /* aggregate */
-        if (rc) break;
+        orc_csr Sm = {0};
+        int32_t *aggm = NULL, *rootsm = NULL, ncm = 0;
+        if (mb > 1) {                                                            /* amalgamate */
+            orc_amalgamate(&L->S, mb, &Sm);
+            aggm = (int32_t *)orc_xmalloc((size_t)(n / mb) * sizeof(int32_t));
+            rc = orc_aggregate(&Sm, p->seed + (uint64_t)lvl, aggm, &rootsm, &ncm);
+            if (rc) { orc_csr_free(&Sm); free(aggm); free(rootsm); break; }
+            for (int32_t i = 0; i < n; i++) L->agg[i] = aggm[i / mb];          /* unamalgamate */
+            L->nc = mb * ncm;
+            L->roots = (int32_t *)orc_xmalloc((size_t)(L->nc > 0 ? L->nc : 1) * sizeof(int32_t));
+            for (int32_t r = 0; r < ncm; r++)
+                for (int c = 0; c < mb; c++) L->roots[mb * r + c] = mb * rootsm[r] + c;
+        } else {
+            rc = orc_aggregate(&L->S, p->seed + (uint64_t)lvl, L->agg, &L->roots, &L->nc); /* aggregate */
+            if (rc) break;
+        }
         if (L->nc == 0 || L->nc >= n) {                                          /* stalled */
             free(L->agg); free(L->roots); L->agg = L->roots = NULL; L->nc = 0;
             orc_csr_free(&L->S);
+            if (mb > 1) { orc_csr_free(&Sm); free(aggm); free(rootsm); }
             break;
         }
         L->rowtype = (int32_t *)orc_xmalloc((size_t)n * sizeof(int32_t));
         orc_row_types(n, L->agg, L->roots, L->nc, L->rowtype);
-        rc = orc_pattern(&L->S, L->agg, L->roots, L->nc, p->degree, p->prefilter, &L->N); /* N = S^d C */
+        if (mb > 1) {                            /* N = S_m^d C on nodes, then on unknowns */
+            orc_csr Nm;
+            rc = orc_pattern(&Sm, aggm, rootsm, ncm, p->degree, p->prefilter, &Nm);
+            orc_csr_free(&Sm); free(aggm); free(rootsm);
+            if (rc) break;
+            rc = orc_unamalgamate_pattern(&Nm, mb, L->agg, L->rowtype, &L->N);
+            orc_csr_free(&Nm);
+        } else {
+            rc = orc_pattern(&L->S, L->agg, L->roots, L->nc, p->degree, p->prefilter, &L->N); /* N = S^d C */
+        }
         if (rc) break;
         orc_smooth_candidates_k(&L->A, L->B, k, p->b_sweeps, p->omega);        /* smooth(A, B) */
         L->Bc = (double *)orc_xmalloc((size_t)L->nc * k * sizeof(double));
         orc_csr_copy(&L->N, &L->T);
-        rc = orc_tentative_k(&L->T, L->agg, L->roots, L->rowtype, L->B, k, L->Bc); /* inject */
+        rc = mb > 1 ? orc_tentative_block(&L->T, L->agg, L->roots, L->rowtype, L->B, k, mb, L->Bc)
+                    : orc_tentative_k(&L->T, L->agg, L->roots, L->rowtype, L->B, k, L->Bc); /* inject */
         if (rc) break;
         rc = build_transfer(&L->A, &L->N, L->agg, L->roots, L->rowtype, L->B, p, &L->P, L->Bc,
                             &h->near_ties);                                      /* improve (+filter) */

@@ -136,6 +136,71 @@ def q1_aniso(ne: int, eps: float = 1.0, psi: float = 0.0, dirichlet: bool = True
     return _finish(A)
 
 
+def q1_elasticity_element(E: float, nu: float, hx: float, hy: float) -> np.ndarray:
+    """8 x 8 plane-strain stiffness of a bilinear (Q1) element of size hx x hy,
+    DOFs node-major (u, v) at the corners (0,0), (hx,0), (hx,hy), (0,hy); 2 x 2
+    Gauss rule, exact for this integrand on a rectangle."""
+    lam_fac = E / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    D = lam_fac * np.array([[1.0 - nu, nu, 0.0], [nu, 1.0 - nu, 0.0], [0.0, 0.0, (1.0 - 2.0 * nu) / 2.0]])
+    g = 1.0 / math.sqrt(3.0)
+    xi_n = np.array([-1.0, 1.0, 1.0, -1.0])
+    eta_n = np.array([-1.0, -1.0, 1.0, 1.0])
+    K = np.zeros((8, 8))
+    for xi in (-g, g):
+        for eta in (-g, g):
+            dNdxi = 0.25 * xi_n * (1.0 + eta * eta_n)
+            dNdeta = 0.25 * eta_n * (1.0 + xi * xi_n)
+            dNdx, dNdy = dNdxi * (2.0 / hx), dNdeta * (2.0 / hy)
+            Bm = np.zeros((3, 8))
+            Bm[0, 0::2] = dNdx
+            Bm[1, 1::2] = dNdy
+            Bm[2, 0::2] = dNdy
+            Bm[2, 1::2] = dNdx
+            K += Bm.T @ D @ Bm * (hx * hy / 4.0)
+    return K
+
+
+def q1_elasticity(ny: int, E: float = 1.0, nu: float = 0.3, aspect: int = 8):
+    """Plane-strain isotropic linear elasticity on the beam [0, aspect] x [0, 1]
+    with (aspect * ny) x ny bilinear elements, clamped (u = 0) on the east
+    side x = aspect, which is eliminated.  Unknowns node-major (u, v per node,
+    nodes x-fastest); returns (CSR, node coordinates (n_nodes x 2))."""
+    nx = aspect * ny
+    hx, hy = aspect / nx, 1.0 / ny
+    Ke = q1_elasticity_element(E, nu, hx, hy)
+    nnx, nny = nx + 1, ny + 1
+    gy, gx = np.divmod(np.arange(nnx * nny), nnx)
+    free = gx < nx
+    newid = np.full(nnx * nny, -1, dtype=np.int64)
+    newid[free] = np.arange(int(free.sum()))
+    ey, ex = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ey, ex = ey.ravel(), ex.ravel()
+    nodes = np.stack([ey * nnx + ex, ey * nnx + ex + 1, (ey + 1) * nnx + ex + 1, (ey + 1) * nnx + ex], axis=1)
+    nid = newid[nodes]
+    dof = np.stack([2 * nid, 2 * nid + 1], axis=2).reshape(len(ey), 8)
+    dof = np.where(np.repeat(nid, 2, axis=1) >= 0, dof, -1)
+    r = np.repeat(dof, 8, axis=1).ravel()
+    c = np.tile(dof, (1, 8)).ravel()
+    v = np.tile(Ke.ravel(), len(ey))
+    ok = (r >= 0) & (c >= 0)
+    n = 2 * int(free.sum())
+    A = sp.coo_matrix((v[ok], (r[ok], c[ok])), shape=(n, n))
+    coords = np.stack([gx[free] * hx, gy[free] * hy], axis=1)
+    return _finish(A), coords
+
+
+def rigid_body_modes(coords: np.ndarray) -> np.ndarray:
+    """The three rigid-body modes of 2-D elasticity at node-major (u, v) DOFs:
+    translations in x and y, and the rotation (-y, x)."""
+    nn = coords.shape[0]
+    B = np.zeros((2 * nn, 3))
+    B[0::2, 0] = 1.0
+    B[1::2, 1] = 1.0
+    B[0::2, 2] = -coords[:, 1]
+    B[1::2, 2] = coords[:, 0]
+    return B
+
+
 def convdiff_upwind(m: int, nu: float = 1e-3) -> CSR:
     """First-order upwind FD for ``-nu Lap u + w.grad u`` on ``[-1,1]^2``, ``m x m`` interior points.
 
@@ -250,6 +315,23 @@ PARAMS_CONVDIFF = dict(soc_theta=0.25, soc_theta_coarse=-1.0, degree=1, n_sweeps
 PARAMS_VARCOEF = dict(soc_theta=0.1, soc_theta_coarse=0.1, degree=2, n_sweeps=4, method=0, prefilter=0.0,
                       postfilter=0.0, max_coarse=64, max_levels=25, b_sweeps=4, omega=2.0 / 3.0, seed=12345,
                       symmetric=1, nu_pre=1, nu_post=1, outer=1)
+
+
+# The paper's systems setting (Sec. 5.4: classical strength, drop tolerance
+# 0.5, CG-accelerated V(1,1)) with the cycle's weighted Jacobi; 2 x 2 blocks
+# and the three rigid-body modes.
+PARAMS_ELASTICITY = dict(soc_theta=0.5, soc_theta_coarse=-1.0, soc_kind=1, degree=2, n_sweeps=4, method=0,
+                         prefilter=0.0, postfilter=0.0, max_coarse=64, max_levels=25, b_sweeps=4, omega=0.5,
+                         seed=12345, symmetric=1, nu_pre=1, nu_post=1, outer=1, block_size=2, ncand=3)
+
+
+def elasticity_problem(ny: int = 16, nu: float = 0.3, seed: int = 5) -> Problem:
+    A, coords = q1_elasticity(ny, 1.0, nu)
+    n = A.n_rows
+    return Problem(f"elasticity_q1_{8 * ny}x{ny}", A, rigid_body_modes(coords), rhs_uniform(n, seed),
+                   dict(PARAMS_ELASTICITY),
+                   description=f"2D plane-strain elasticity (nu={nu}), Q1 on an 8:1 beam with {8 * ny}x{ny} "
+                               f"elements, clamped east side (n={n}, 2x2 blocks, 3 rigid-body modes)")
 
 
 def poisson_problem(m: int = 64, seed: int = 1) -> Problem:

@@ -885,3 +885,78 @@ def test_hierarchy_with_three_candidates(oracle):
                 assert np.allclose(PB[i], L.B[i], rtol=1e-10, atol=1e-12 * np.abs(L.B).max())
     x, info = h.solve(pr.b, tol=1e-8, outer=1)
     assert info["status"] == 0
+
+
+# --------------------------------------------------------------------------- block systems (NEXT-3)
+def test_elasticity_element_is_symmetric_and_kills_rigid_modes():
+    """The Q1 plane-strain element stiffness is symmetric, positive
+    semi-definite with exactly the three rigid-body modes as its null space."""
+    Ke = PR.q1_elasticity_element(1.0, 0.3, 0.5, 0.25)
+    xy = np.array([[0.0, 0.0], [0.5, 0.0], [0.5, 0.25], [0.0, 0.25]])
+    Rb = PR.rigid_body_modes(xy)
+    assert np.abs(Ke - Ke.T).max() < 1e-15
+    assert np.abs(Ke @ Rb).max() < 1e-14
+    ev = np.linalg.eigvalsh(Ke)
+    assert np.all(ev[:3] < 1e-12) and ev[3] > 1e-3
+
+
+def test_elasticity_operator_spd_and_rigid_modes_away_from_clamp():
+    pr = PR.elasticity_problem(4)
+    A = pr.A.to_scipy().toarray()
+    assert np.abs(A - A.T).max() < 1e-14 and np.linalg.eigvalsh(A)[0] > 0
+    # rows of nodes not next to the clamped side annihilate the rigid-body modes
+    R = A @ pr.B
+    nodes = np.arange(A.shape[0] // 2)
+    ny = 4
+    x = (nodes % (8 * ny)) * (8.0 / (8 * ny))
+    far = np.repeat(x < 8.0 - 1.5 * (8.0 / (8 * ny)), 2)
+    assert np.abs(R[far]).max() < 1e-12
+
+
+@pytest.mark.parametrize("m", [2, 3])
+def test_amalgamate_is_block_maximum(oracle, m):
+    rng = np.random.default_rng(m)
+    nn = 30
+    n = m * nn
+    S = sp.random(n, n, density=0.08, random_state=m, data_rvs=lambda k: rng.random(k)).tocsr()
+    S = (S + sp.identity(n)).tocsr()
+    S.sort_indices()
+    Sm = oracle.amalgamate(S, m)
+    D = S.toarray()
+    P = S.copy()
+    P.data[:] = 1.0
+    Pd = P.toarray()
+    for I in range(nn):
+        for J in range(nn):
+            blk = D[I * m:(I + 1) * m, J * m:(J + 1) * m]
+            has = Pd[I * m:(I + 1) * m, J * m:(J + 1) * m].any()
+            got = Sm[I, J]
+            if has:
+                assert got == blk[Pd[I * m:(I + 1) * m, J * m:(J + 1) * m] > 0].max()
+            else:
+                assert got == 0.0 and not (Sm.indices[Sm.indptr[I]:Sm.indptr[I + 1]] == J).any()
+
+
+def test_elasticity_hierarchy_blocks_and_constraints(oracle):
+    """2 x 2 blocks and the three rigid-body modes: aggregates and roots come
+    in node pairs, root rows are identity rows over their aggregate's block,
+    T and P reproduce every candidate where the pattern carries them, and
+    CG with the cycle reaches 1e-8."""
+    pr = PR.elasticity_problem(8)
+    h = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    assert len(h.levels) >= 3
+    for L in h.levels[:-1]:
+        n = L.A.shape[0]
+        assert np.array_equal(L.agg[0::2], L.agg[1::2])
+        r = L.roots.reshape(-1, 2)
+        assert np.all(r[:, 0] % 2 == 0) and np.array_equal(r[:, 1], r[:, 0] + 1)
+        for T in (L.T, L.P):
+            for i in range(n):
+                s, e = T.indptr[i], T.indptr[i + 1]
+                if L.rowtype[i] == 1:
+                    assert e - s == 1 and T.indices[s] == 2 * L.agg[i] + i % 2 and T.data[s] == 1.0
+                elif L.rowtype[i] == 0 and _fits_all(L.Bc[T.indices[s:e]]):
+                    assert np.allclose(T[i] @ L.Bc, L.B[i], rtol=1e-9, atol=1e-12 * np.abs(L.B).max())
+    x, info = h.solve(pr.b, tol=1e-8, maxit=300, outer=1)
+    assert info["status"] == 0
+    assert np.linalg.norm(pr.b - pr.A.to_scipy() @ x) < 1e-8 * np.linalg.norm(pr.b)
