@@ -335,6 +335,30 @@ def main():
     # the same step with three candidates (1, x, y), Sec. 3.6
     step(prec, B3)
     times_k3, infos_k3 = timed(prec, 1, B3)
+    # a block system of the same size class (Sec. 3.2, Sec. 5.4): plane-strain
+    # elasticity, 2 unknowns per node, 3 rigid-body modes; one warm-up and one
+    # timed step (setup + CG solve), inputs resident
+    prs = PR.elasticity_problem(args.ne // 4)
+    es = dict(rp=t(prs.A.rowptr), ci=t(prs.A.col), va=t(prs.A.val), B=t(prs.B), b=t(prs.b))
+    xs_d = torch.zeros_like(es["b"])
+    es_times, es_infos = [], []
+    for rep in range(2):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xs_d.zero_()
+        hs = rn.Hierarchy(es["rp"], es["ci"], es["va"], es["B"],
+                          params=rn.params_from_config(prs.params, precision=rn.RN_MIXED if prec == "mixed"
+                                                       else rn.RN_FP64, outer=rn.RN_OUTER_CG, use_graphs=1),
+                          stream=sptr)
+        es_infos.append(hs.solve(es["b"], xs_d, rtol=1e-8, maxit=5000))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        es_times.append(e0.elapsed_time(e1) / 1e3)
+        es_levels = hs.stats()["levels"]
+        hs.close()
+    del es, xs_d
 
     # per-launch device times of the solve's level-0 operations, each timed in
     # isolation with CUDA events on the hierarchy's stream, a 256 MB read before
@@ -433,6 +457,9 @@ def main():
                         "cycle": "W(1,1)", "precision": prec},
             "candidates_3": {"step_s": times_k3[0], "iters": infos_k3[0]["iters"], "rel_res": infos_k3[0]["rel_res"],
                              "B": "1, x, y", "precision": prec},
+            "block_system": {"step_s": es_times[1], "iters": es_infos[1]["iters"], "rel_res": es_infos[1]["rel_res"],
+                             "levels": es_levels, "problem": prs.name, "n": prs.A.n_rows, "nnz": prs.A.nnz,
+                             "block_size": 2, "B": "3 rigid-body modes", "precision": prec},
             "roofline": roofline,
             "level0_launches": kernels,
             "gpu_launches": launches // max(args.steps, 1),

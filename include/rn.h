@@ -102,6 +102,12 @@ typedef struct {
     int gamma;               /* coarse-grid corrections per level: 1 V-cycle, 2 W-cycle (Sec. 5.2's
                                 W(1,1)); a level whose next level is the coarsest corrects once */
     int soc_kind;            /* strength measure (Sec. 3.2): RN_SOC_SYMMETRIC or RN_SOC_CLASSICAL */
+    int block_size;          /* m, unknowns per node (node-major, m <= RN_MAX_BLOCK; 1: scalar problem).
+                                m > 1 (systems, Sec. 3.2-3.6): S is amalgamated to nodes (largest entry of
+                                each m x m block), aggregation and the pattern run on nodes and are
+                                unamalgamated to unknowns, each root node carries m coarse unknowns, and
+                                T injects the first m candidates normalised by the root node's block;
+                                needs k >= m and n divisible by m */
     void *stream;            /* cudaStream_t */
     /* Device-memory hooks (both NULL: the stream-ordered pool, cudaMallocAsync;
      * one without the other is RN_EINVAL).  alloc(bytes, stream, ctx) returns
@@ -126,6 +132,7 @@ typedef struct {
 
 #define RN_MAX_LEVELS 32
 #define RN_MAX_CANDIDATES 4  /* k, the number of candidate vectors */
+#define RN_MAX_BLOCK 3       /* m, unknowns per node */
 typedef struct {
     int levels;
     int32_t n[RN_MAX_LEVELS];

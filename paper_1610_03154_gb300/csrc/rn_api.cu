@@ -63,6 +63,7 @@ extern "C" rn_status rn_default_params(rn_params *p) {
     p->coarse_cluster = 0;
     p->gamma = 1;
     p->soc_kind = RN_SOC_SYMMETRIC;
+    p->block_size = 1;
     p->stream = nullptr;
     return RN_OK;
 }
@@ -83,6 +84,7 @@ static void check_params(const rn_params *p) {
     if (p->coarse_cluster < 0) fail(RN_EINVAL, "coarse_cluster must be >= 0");
     if (p->gamma != 1 && p->gamma != 2) fail(RN_EINVAL, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
     if (p->soc_kind != RN_SOC_SYMMETRIC && p->soc_kind != RN_SOC_CLASSICAL) fail(RN_EINVAL, "soc_kind");
+    if (p->block_size < 1 || p->block_size > RN_MAX_BLOCK) fail(RN_EINVAL, "block_size must be in [1, RN_MAX_BLOCK]");
     if ((p->alloc == nullptr) != (p->dealloc == nullptr))
         fail(RN_EINVAL, "alloc and dealloc must both be set or both be NULL");
 }
@@ -102,6 +104,8 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
     using rn::fail;
     if (!A || !B || !p || !out) fail(RN_EINVAL, "null argument");
     if (k < 1 || k > RN_MAX_CANDIDATES) fail(RN_EINVAL, "k must be in [1, RN_MAX_CANDIDATES]");
+    if (p && (p->block_size > k || (p->block_size >= 1 && A->n_rows % p->block_size != 0)))
+        fail(RN_EINVAL, "block_size must divide n and not exceed k");
     if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
     if (A->n_rows <= 0 || A->n_rows != A->n_cols) fail(RN_EINVAL, "A must be square and non-empty");
     if (A->nnz <= 0 || A->nnz > INT32_MAX - 1) fail(RN_EINVAL, "nnz out of range");
@@ -129,6 +133,7 @@ extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bh
     std::unique_ptr<rn_hierarchy> h(new rn_hierarchy());
     h->p = *p;
     h->k = k;
+    h->mb = p->block_size;
     h->s = s;
     h->own_stream = (own.s != nullptr);
     const double t0 = rn::now_ms();

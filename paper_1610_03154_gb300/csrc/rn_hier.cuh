@@ -27,6 +27,7 @@ struct rn_level {
 struct rn_hierarchy {
     rn_params p{};
     int k = 1;                 // candidate vectors: B is n x k, Bc nc x k (row-major) on every level
+    int mb = 1;                // unknowns per node (block size m); nodes are m consecutive unknowns
     cudaStream_t s = nullptr;  // params.stream, or a stream the hierarchy created (own_stream)
     bool own_stream = false;
     std::vector<std::unique_ptr<rn_level>> lev;  // lev.back() is the coarsest

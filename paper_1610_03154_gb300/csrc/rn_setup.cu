@@ -466,6 +466,158 @@ __global__ void row_fit_k_kernel(int32_t n, const int32_t *__restrict__ rp, cons
         default: { constexpr int KK = 4; CALL; } break; \
     }
 
+// ------------------------------------------------------------------ systems (Sec. 3.2-3.6, block size m > 1)
+constexpr int kAmalMax = 256;  // entries of one node row of S gathered for amalgamation
+
+// S_m(I, J) = the largest entry of S's m x m block (I, J) (entries S stores):
+// thread per node, its m rows' entries merged by node column in a sorted
+// list.  Pass 1 (FILL false) counts; pass 2 writes.
+template <bool FILL>
+__global__ void amalgamate_kernel(int32_t nn, int m, const int32_t *__restrict__ srp, const int32_t *__restrict__ scol,
+                                  const double *__restrict__ sval, int32_t *__restrict__ count,
+                                  const int32_t *__restrict__ orp, int32_t *__restrict__ ocol, double *__restrict__ oval,
+                                  int32_t *__restrict__ bad) {
+    for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nn; I += gridDim.x * blockDim.x) {
+        int32_t cols[kAmalMax];
+        double vals[kAmalMax];
+        int u = 0;
+        bool over = false;
+        for (int32_t i = I * m; i < I * m + m && !over; i++)
+            for (int32_t e = srp[i]; e < srp[i + 1]; e++) {
+                const int32_t J = scol[e] / m;
+                const double v = sval[e];
+                int q = u;
+                while (q > 0 && cols[q - 1] > J) q--;
+                if (q > 0 && cols[q - 1] == J) {
+                    if (v > vals[q - 1]) vals[q - 1] = v;
+                    continue;
+                }
+                if (u == kAmalMax) { over = true; break; }
+                for (int t = u; t > q; t--) { cols[t] = cols[t - 1]; vals[t] = vals[t - 1]; }
+                cols[q] = J;
+                vals[q] = v;
+                u++;
+            }
+        if (over) atomicMax(bad, I + 1);
+        if (!FILL) {
+            count[I] = u;
+        } else {
+            for (int q = 0; q < u; q++) {
+                ocol[orp[I] + q] = cols[q];
+                oval[orp[I] + q] = vals[q];
+            }
+        }
+    }
+}
+
+// node aggregates and row types to unknowns; root nodes to their m root unknowns
+__global__ void unamalgamate_nodes_kernel(int32_t n, int m, const int32_t *__restrict__ aggn,
+                                          const int32_t *__restrict__ rtn, int32_t *__restrict__ agg,
+                                          int32_t *__restrict__ rowtype) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        agg[i] = aggn[i / m];
+        rowtype[i] = rtn[i / m];
+    }
+}
+__global__ void unamalgamate_roots_kernel(int32_t ncn, int m, const int32_t *__restrict__ rootsn,
+                                          int32_t *__restrict__ roots) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ncn; r += gridDim.x * blockDim.x)
+        for (int c = 0; c < m; c++) roots[m * r + c] = m * rootsn[r] + c;
+}
+
+// N(i, m J + c) = N_m(floor(i/m), J), c < m; a root unknown i of aggregate a
+// gets the identity row {m a + i mod m}
+template <bool FILL>
+__global__ void unamalgamate_pattern_kernel(int32_t n, int m, const int32_t *__restrict__ nrp,
+                                            const int32_t *__restrict__ ncol, const double *__restrict__ nval,
+                                            const int32_t *__restrict__ agg, const int32_t *__restrict__ rowtype,
+                                            int32_t *__restrict__ count, const int32_t *__restrict__ orp,
+                                            int32_t *__restrict__ ocol, double *__restrict__ oval) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t I = i / m;
+        if (!FILL) {
+            count[i] = rowtype[i] == ROOT_ROW ? 1 : m * (nrp[I + 1] - nrp[I]);
+            continue;
+        }
+        int32_t dst = orp[i];
+        if (rowtype[i] == ROOT_ROW) {
+            ocol[dst] = m * agg[i] + i % m;
+            oval[dst] = 1.0;
+            continue;
+        }
+        for (int32_t e = nrp[I]; e < nrp[I + 1]; e++)
+            for (int c = 0; c < m; c++) {
+                ocol[dst] = m * ncol[e] + c;
+                oval[dst++] = nval[e];
+            }
+    }
+}
+
+// The inverse of every aggregate's root block Broot_a (m x m: the first m
+// candidates at its m root unknowns), Gauss-Jordan with partial pivoting;
+// a pivot at most 1e-12 of the block's largest entry flags the aggregate.
+__global__ void root_block_inverse_kernel(int32_t na, int m, int k, const int32_t *__restrict__ roots,
+                                          const double *__restrict__ B, double *__restrict__ Binv,
+                                          int32_t *__restrict__ bad) {
+    for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x) {
+        double M[RN_MAX_BLOCK * RN_MAX_BLOCK], X[RN_MAX_BLOCK * RN_MAX_BLOCK];
+        double amax = 0.0;
+        for (int r = 0; r < m; r++)
+            for (int c = 0; c < m; c++) {
+                M[r * m + c] = B[(int64_t)roots[m * a + r] * k + c];
+                X[r * m + c] = (r == c) ? 1.0 : 0.0;
+                amax = fmax(amax, fabs(M[r * m + c]));
+            }
+        bool ok = true;
+        for (int col = 0; col < m && ok; col++) {
+            int piv = col;
+            for (int r = col + 1; r < m; r++)
+                if (fabs(M[r * m + col]) > fabs(M[piv * m + col])) piv = r;
+            if (!(fabs(M[piv * m + col]) > 1e-12 * amax)) { ok = false; break; }
+            for (int c = 0; c < m; c++) {
+                double t = M[col * m + c]; M[col * m + c] = M[piv * m + c]; M[piv * m + c] = t;
+                t = X[col * m + c]; X[col * m + c] = X[piv * m + c]; X[piv * m + c] = t;
+            }
+            const double d = M[col * m + col];
+            for (int c = 0; c < m; c++) { M[col * m + c] /= d; X[col * m + c] /= d; }
+            for (int r = 0; r < m; r++) {
+                if (r == col) continue;
+                const double f = M[r * m + col];
+                for (int c = 0; c < m; c++) {
+                    M[r * m + c] -= f * M[col * m + c];
+                    X[r * m + c] -= f * X[col * m + c];
+                }
+            }
+        }
+        if (!ok) atomicMax(bad, a + 1);
+        for (int q = 0; q < m * m; q++) Binv[(int64_t)a * m * m + q] = ok ? X[q] : 0.0;
+    }
+}
+
+// T for block size m (eq. root-nodeform): T_i,(m a + c) = (B_i,0:m Broot_a^{-1})_c
+// on the own aggregate's block, 0 elsewhere; root unknowns exact identity rows
+__global__ void tentative_block_kernel(int32_t n, int m, int k, const int32_t *__restrict__ rp,
+                                       const int32_t *__restrict__ col, const int32_t *__restrict__ agg,
+                                       const int32_t *__restrict__ rowtype, const double *__restrict__ B,
+                                       const double *__restrict__ Binv, double *__restrict__ T) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t a = agg[i];
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            const int32_t j = col[e];
+            double t = 0.0;
+            if (a >= 0 && j / m == a) {
+                if (rowtype[i] == ROOT_ROW) {
+                    t = (j == m * a + i % m) ? 1.0 : 0.0;
+                } else {
+                    const double *X = Binv + (int64_t)a * m * m;
+                    for (int r = 0; r < m; r++) t += B[(int64_t)i * k + r] * X[r * m + j % m];
+                }
+            }
+            T[e] = t;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ pattern (Sec. 3.4-3.5)
 __global__ void aggflag_kernel(int32_t n, const int32_t *__restrict__ agg, int32_t *__restrict__ flag) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -776,7 +928,7 @@ __global__ void postfilter_kernel(int32_t n, const int32_t *__restrict__ rp, con
                                   const double *__restrict__ val, const int32_t *__restrict__ rowtype,
                                   const int32_t *__restrict__ agg, double theta, double omg,
                                   int32_t *__restrict__ count, const int32_t *__restrict__ frp,
-                                  int32_t *__restrict__ fcol, double *__restrict__ fval) {
+                                  int32_t *__restrict__ fcol, double *__restrict__ fval, int mb) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const bool fr = rowtype[i] == FREE_ROW;
         double thr = 0.0;
@@ -788,7 +940,7 @@ __global__ void postfilter_kernel(int32_t n, const int32_t *__restrict__ rp, con
         }
         int32_t c = 0, dst = FILL ? frp[i] : 0;
         for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
-            bool keep = !fr || fabs(val[e]) >= thr || col[e] == agg[i];
+            bool keep = !fr || fabs(val[e]) >= thr || col[e] / mb == agg[i];  // own aggregate's block kept
             if (keep) {
                 if (FILL) {
                     fcol[dst] = col[e];
@@ -1180,7 +1332,16 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
     else
         RN_LAUNCH("inject", 16.0 * nc * k, s, gather_k_kernel, rows_grid(nc), kT, 0, nc, k, roots, Bsm, Bc,
                   h.iflags.p + 2);
-    check_flag(h.iflags.p + 2, s, RN_EINVAL, "candidate vanishes at a root node");
+    DVec<double> binv;
+    if (h.mb > 1) {  // systems: the root node's m x m block of the first m candidates must be invertible
+        fill_i32(h.iflags.p + 2, 0, 1, s);
+        binv.alloc((size_t)nc * h.mb, s);  // (nc / m) blocks of m x m
+        RN_LAUNCH("inject", 8.0 * nc * h.mb * 2, s, root_block_inverse_kernel, rows_grid(nc / h.mb), kT, 0,
+                  nc / h.mb, h.mb, k, roots, Bsm, binv.p, h.iflags.p + 2);
+        check_flag(h.iflags.p + 2, s, RN_EINVAL, "candidate block singular at a root node");
+    } else {
+        check_flag(h.iflags.p + 2, s, RN_EINVAL, "candidate vanishes at a root node");
+    }
     // P = T on N
     Pout.n = n;
     Pout.m = nc;
@@ -1190,9 +1351,13 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
     Pout.val.alloc(N.nnz, s);
     d2d(Pout.rowptr.p, N.rowptr.p, n + 1, s);
     d2d(Pout.col.p, N.col.p, N.nnz, s);
-    RN_LAUNCH("tentative", 16.0 * N.nnz + 16.0 * n, s, tentative_kernel, rows_grid(n), kT, 0, n, N.rowptr.p, N.col.p,
-              agg, Bsm, Bc, Pout.val.p, k);
-    if (k > 1)  // the other candidates: minimal-norm row fits (eq. Tproj)
+    if (h.mb > 1)
+        RN_LAUNCH("tentative", 16.0 * N.nnz + 8.0 * k * n, s, tentative_block_kernel, rows_grid(n), kT, 0, n, h.mb,
+                  k, N.rowptr.p, N.col.p, agg, rowtype, Bsm, binv.p, Pout.val.p);
+    else
+        RN_LAUNCH("tentative", 16.0 * N.nnz + 16.0 * n, s, tentative_kernel, rows_grid(n), kT, 0, n, N.rowptr.p,
+                  N.col.p, agg, Bsm, Bc, Pout.val.p, k);
+    if (k > h.mb)  // the other candidates: minimal-norm row fits (eq. Tproj)
         RN_K_SWITCH(k, RN_LAUNCH("tentative", 12.0 * N.nnz + 8.0 * k * (N.nnz + n), s, row_fit_k_kernel<KK>,
                                  rows_grid(n), kT, 0, n, Pout.rowptr.p, Pout.col.p, Pout.val.p, rowtype, Bsm, Bc));
     if (Tkeep) {
@@ -1210,7 +1375,7 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
         const double omg = 1.0 - kGuard;
         DVec<int32_t> cnt(n + 1, s);
         RN_LAUNCH("postfilter", 24.0 * Pout.nnz, s, postfilter_kernel<false>, rows_grid(n), kT, 0, n, Pout.rowptr.p,
-                  Pout.col.p, Pout.val.p, rowtype, agg, h.p.postfilter, omg, cnt.p, nullptr, nullptr, nullptr);
+                  Pout.col.p, Pout.val.p, rowtype, agg, h.p.postfilter, omg, cnt.p, nullptr, nullptr, nullptr, h.mb);
         DCsr F;
         F.n = n; F.m = nc;
         F.rowptr.alloc(n + 1, s);
@@ -1219,7 +1384,7 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
         F.val.alloc(F.nnz, s);
         RN_LAUNCH("postfilter", 24.0 * Pout.nnz + 12.0 * F.nnz, s, postfilter_kernel<true>, rows_grid(n), kT, 0, n,
                   Pout.rowptr.p, Pout.col.p, Pout.val.p, rowtype, agg, h.p.postfilter, omg, nullptr, F.rowptr.p,
-                  F.col.p, F.val.p);
+                  F.col.p, F.val.p, h.mb);
         if (k == 1)
             RN_LAUNCH("enforce", 28.0 * F.nnz + 8.0 * n, s, enforce_kernel, rows_grid(n), kT, 0, n, F.rowptr.p,
                       F.col.p, F.val.p, rowtype, Bsm, Bc);
@@ -1293,89 +1458,139 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
                       0, n, A.rowptr, A.col, A.val, L.diag.p, thr, nullptr, vtmp.p, vmax.p, S.rowptr.p, S.col.p,
                       S.val.p, 0);
         }
-        // ---- aggregation graph and seeded MIS-2 (line 'aggregate')
+        // ---- systems: S amalgamated to nodes (m unknowns each); scalar problems aggregate S itself
+        const int mb = h.mb;
+        const int32_t nn = n / mb;
+        DCsr Sm;
+        if (mb > 1) {
+            DVec<int32_t> cnt(nn + 1, s);
+            fill_i32(h.iflags.p + 6, 0, 1, s);
+            RN_LAUNCH("amalgamate", 12.0 * S.nnz + 4.0 * n, s, amalgamate_kernel<false>, rows_grid(nn), kT, 0, nn, mb,
+                      S.rowptr.p, S.col.p, S.val.p, cnt.p, nullptr, nullptr, nullptr, h.iflags.p + 6);
+            check_flag(h.iflags.p + 6, s, RN_EINVAL, "a node row of S has too many entries to amalgamate");
+            Sm.n = Sm.m = nn;
+            Sm.rowptr.alloc(nn + 1, s);
+            Sm.nnz = scan_counts(cnt.p, Sm.rowptr.p, nn, s);
+            Sm.col.alloc(Sm.nnz, s);
+            Sm.val.alloc(Sm.nnz, s);
+            RN_LAUNCH("amalgamate", 12.0 * S.nnz + 12.0 * Sm.nnz, s, amalgamate_kernel<true>, rows_grid(nn), kT, 0, nn,
+                      mb, S.rowptr.p, S.col.p, S.val.p, nullptr, Sm.rowptr.p, Sm.col.p, Sm.val.p, h.iflags.p + 6);
+        }
+        const DCsr &SG = mb > 1 ? Sm : S;  // the strength graph aggregation and the pattern run on
+        // ---- aggregation graph and seeded MIS-2 (line 'aggregate'), on nodes
         DCsr Gr;
         {
             DCsr St;
-            transpose(view(S), false, St, s);
-            DVec<int32_t> cnt(n + 1, s);
-            RN_LAUNCH("agg_graph", 8.0 * S.nnz + 8.0 * n, s, union_kernel<false>, rows_grid(n), kT, 0, n, S.rowptr.p,
-                      S.col.p, St.rowptr.p, St.col.p, cnt.p, nullptr, nullptr);
-            Gr.n = Gr.m = n;
-            Gr.rowptr.alloc(n + 1, s);
-            Gr.nnz = scan_counts(cnt.p, Gr.rowptr.p, n, s);
+            transpose(view(SG), false, St, s);
+            DVec<int32_t> cnt(nn + 1, s);
+            RN_LAUNCH("agg_graph", 8.0 * SG.nnz + 8.0 * nn, s, union_kernel<false>, rows_grid(nn), kT, 0, nn,
+                      SG.rowptr.p, SG.col.p, St.rowptr.p, St.col.p, cnt.p, nullptr, nullptr);
+            Gr.n = Gr.m = nn;
+            Gr.rowptr.alloc(nn + 1, s);
+            Gr.nnz = scan_counts(cnt.p, Gr.rowptr.p, nn, s);
             Gr.col.alloc(Gr.nnz, s);
-            RN_LAUNCH("agg_graph", 8.0 * S.nnz + 8.0 * n + 4.0 * Gr.nnz, s, union_kernel<true>, rows_grid(n), kT, 0, n,
-                      S.rowptr.p, S.col.p, St.rowptr.p, St.col.p, nullptr, Gr.rowptr.p, Gr.col.p);
+            RN_LAUNCH("agg_graph", 8.0 * SG.nnz + 8.0 * nn + 4.0 * Gr.nnz, s, union_kernel<true>, rows_grid(nn), kT, 0,
+                      nn, SG.rowptr.p, SG.col.p, St.rowptr.p, St.col.p, nullptr, Gr.rowptr.p, Gr.col.p);
         }
         const uint64_t seed = p.seed + (uint64_t)l;
-        DVec<int32_t> state(n, s), m1(n, s), r1(n, s);
-        const double gb = 4.0 * Gr.nnz + 8.0 * n;
-        RN_LAUNCH("mis2", gb, s, mis_init_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, state.p);
+        DVec<int32_t> state(nn, s), m1(nn, s), r1(nn, s);
+        const double gb = 4.0 * Gr.nnz + 8.0 * nn;
+        RN_LAUNCH("mis2", gb, s, mis_init_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, state.p);
         int rounds = 0;
         for (;; rounds++) {
             if (rounds >= kMaxAggRounds) fail(RN_ETIMEOUT, fmt("aggregation did not finish in %d rounds", rounds));
             fill_i32(h.iflags.p + 5, 0, 1, s);
-            RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_m1_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, state.p,
+            RN_LAUNCH("mis2", gb + 8.0 * nn, s, mis_m1_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p, state.p,
                       seed, m1.p);
-            RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_take_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, m1.p,
+            RN_LAUNCH("mis2", gb + 8.0 * nn, s, mis_take_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p, m1.p,
                       seed, state.p);
-            RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_r1_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, state.p,
+            RN_LAUNCH("mis2", gb + 8.0 * nn, s, mis_r1_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p, state.p,
                       r1.p);
-            RN_LAUNCH("mis2", gb + 8.0 * n, s, mis_remove_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p, r1.p,
+            RN_LAUNCH("mis2", gb + 8.0 * nn, s, mis_remove_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p, r1.p,
                       state.p, h.iflags.p + 5);
             // read the flag every second round: a round after the last is a no-op
             // (no undecided node), cheaper than a host synchronisation
             if ((rounds & 1) == 1 && read_scalar(h.iflags.p + 5, s) == 0) break;
         }
         h.agg_rounds += rounds + 1;
-        DVec<int32_t> cidx(n + 1, s);
-        RN_LAUNCH("aggregate", 8.0 * n, s, flag_taken_kernel, rows_grid(n), kT, 0, n, state.p, m1.p);
-        const int32_t nc = (int32_t)scan_counts(m1.p, cidx.p, n, s);
-        if (nc == 0 || nc >= n) break;  // stalled: this level is the coarsest
+        DVec<int32_t> cidx(nn + 1, s);
+        RN_LAUNCH("aggregate", 8.0 * nn, s, flag_taken_kernel, rows_grid(nn), kT, 0, nn, state.p, m1.p);
+        const int32_t ncn = (int32_t)scan_counts(m1.p, cidx.p, nn, s);  // node aggregates
+        if (ncn == 0 || ncn >= nn) break;  // stalled: this level is the coarsest
+        const int32_t nc = mb * ncn;       // coarse unknowns: m per root node
         L.nc = nc;
         L.roots.alloc(nc, s);
         L.agg.alloc(n, s);
         L.rowtype.alloc(n, s);
-        RN_LAUNCH("aggregate", 12.0 * n, s, roots_kernel, rows_grid(n), kT, 0, n, state.p, cidx.p, L.roots.p);
-        RN_LAUNCH("aggregate", gb + 12.0 * n, s, agg_pass1_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p,
+        DVec<int32_t> rootsN, aggN, rtN;  // node level (m > 1)
+        if (mb > 1) {
+            rootsN.alloc(ncn, s);
+            aggN.alloc(nn, s);
+            rtN.alloc(nn, s);
+        }
+        int32_t *roots_n = mb > 1 ? rootsN.p : L.roots.p, *agg_n = mb > 1 ? aggN.p : L.agg.p;
+        int32_t *rt_n = mb > 1 ? rtN.p : L.rowtype.p;
+        RN_LAUNCH("aggregate", 12.0 * nn, s, roots_kernel, rows_grid(nn), kT, 0, nn, state.p, cidx.p, roots_n);
+        RN_LAUNCH("aggregate", gb + 12.0 * nn, s, agg_pass1_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p,
                   state.p, cidx.p, seed, r1.p);
         fill_i32(h.iflags.p + 6, 0, 1, s);
-        RN_LAUNCH("aggregate", gb + 16.0 * n, s, agg_pass2_kernel, rows_grid(n), kT, 0, n, Gr.rowptr.p, Gr.col.p,
-                  state.p, r1.p, L.roots.p, seed, L.agg.p, h.iflags.p + 6);
+        RN_LAUNCH("aggregate", gb + 16.0 * nn, s, agg_pass2_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p,
+                  state.p, r1.p, roots_n, seed, agg_n, h.iflags.p + 6);
         check_flag(h.iflags.p + 6, s, RN_EINTERNAL, "aggregation pass 2 left a node unassigned");
-        RN_LAUNCH("aggregate", 12.0 * n, s, rowtype_kernel, rows_grid(n), kT, 0, n, state.p, L.agg.p, L.rowtype.p);
-        // ---- pattern N = S^d C, pre-filter, root-node pattern
-        DCsr N;
+        RN_LAUNCH("aggregate", 12.0 * nn, s, rowtype_kernel, rows_grid(nn), kT, 0, nn, state.p, agg_n, rt_n);
+        if (mb > 1) {  // unamalgamate: aggregates, row types and roots of the unknowns
+            RN_LAUNCH("aggregate", 16.0 * n, s, unamalgamate_nodes_kernel, rows_grid(n), kT, 0, n, mb, agg_n, rt_n,
+                      L.agg.p, L.rowtype.p);
+            RN_LAUNCH("aggregate", 8.0 * nc, s, unamalgamate_roots_kernel, rows_grid(ncn), kT, 0, ncn, mb, roots_n,
+                      L.roots.p);
+        }
+        // ---- pattern N = S^d C, pre-filter, root-node pattern (on nodes; unamalgamated for m > 1)
+        DCsr N, Nn;
         {
             DCsr cur;
-            cur.n = n;
-            cur.m = nc;
-            cur.rowptr.alloc(n + 1, s);
-            RN_LAUNCH("pattern", 8.0 * n, s, aggflag_kernel, rows_grid(n), kT, 0, n, L.agg.p, m1.p);
-            cur.nnz = scan_counts(m1.p, cur.rowptr.p, n, s);
+            cur.n = nn;
+            cur.m = ncn;
+            cur.rowptr.alloc(nn + 1, s);
+            RN_LAUNCH("pattern", 8.0 * nn, s, aggflag_kernel, rows_grid(nn), kT, 0, nn, agg_n, m1.p);
+            cur.nnz = scan_counts(m1.p, cur.rowptr.p, nn, s);
             cur.col.alloc(cur.nnz, s);
             cur.val.alloc(cur.nnz, s);
-            RN_LAUNCH("pattern", 16.0 * n, s, c_matrix_kernel, rows_grid(n), kT, 0, n, L.agg.p, cur.rowptr.p, cur.col.p,
-                      cur.val.p);
+            RN_LAUNCH("pattern", 16.0 * nn, s, c_matrix_kernel, rows_grid(nn), kT, 0, nn, agg_n, cur.rowptr.p,
+                      cur.col.p, cur.val.p);
             for (int t = 0; t < p.degree; t++) {
                 DCsr nxt;
-                spgemm(view(S), view(cur), nxt, s);
+                spgemm(view(SG), view(cur), nxt, s);
                 cur = std::move(nxt);
             }
-            DVec<int32_t> cnt(n + 1, s);
-            RN_LAUNCH("prefilter", 12.0 * cur.nnz + 12.0 * n, s, prefilter_kernel<false>, rows_grid(n), kT, 0, n,
-                      cur.rowptr.p, cur.col.p, cur.val.p, L.rowtype.p, L.agg.p, p.prefilter, omg, cnt.p, nullptr,
-                      nullptr, nullptr);
-            N.n = n;
-            N.m = nc;
-            N.rowptr.alloc(n + 1, s);
-            N.nnz = scan_counts(cnt.p, N.rowptr.p, n, s);
-            N.col.alloc(N.nnz, s);
-            N.val.alloc(N.nnz, s);
-            RN_LAUNCH("prefilter", 12.0 * cur.nnz + 12.0 * n + 12.0 * N.nnz, s, prefilter_kernel<true>, rows_grid(n),
-                      kT, 0, n, cur.rowptr.p, cur.col.p, cur.val.p, L.rowtype.p, L.agg.p, p.prefilter, omg, nullptr,
-                      N.rowptr.p, N.col.p, N.val.p);
+            DVec<int32_t> cnt(nn + 1, s);
+            RN_LAUNCH("prefilter", 12.0 * cur.nnz + 12.0 * nn, s, prefilter_kernel<false>, rows_grid(nn), kT, 0, nn,
+                      cur.rowptr.p, cur.col.p, cur.val.p, rt_n, agg_n, p.prefilter, omg, cnt.p, nullptr, nullptr,
+                      nullptr);
+            DCsr &NN = mb > 1 ? Nn : N;  // the node pattern: N itself for scalar problems
+            NN.n = nn;
+            NN.m = ncn;
+            NN.rowptr.alloc(nn + 1, s);
+            NN.nnz = scan_counts(cnt.p, NN.rowptr.p, nn, s);
+            NN.col.alloc(NN.nnz, s);
+            NN.val.alloc(NN.nnz, s);
+            RN_LAUNCH("prefilter", 12.0 * cur.nnz + 12.0 * nn + 12.0 * NN.nnz, s, prefilter_kernel<true>,
+                      rows_grid(nn), kT, 0, nn, cur.rowptr.p, cur.col.p, cur.val.p, rt_n, agg_n, p.prefilter, omg,
+                      nullptr, NN.rowptr.p, NN.col.p, NN.val.p);
+            if (mb > 1) {  // unamalgamate the pattern: m columns per node column, identity root rows
+                DVec<int32_t> cn(n + 1, s);
+                RN_LAUNCH("pattern", 8.0 * n + 4.0 * nn, s, unamalgamate_pattern_kernel<false>, rows_grid(n), kT, 0,
+                          n, mb, Nn.rowptr.p, Nn.col.p, Nn.val.p, L.agg.p, L.rowtype.p, cn.p, nullptr, nullptr,
+                          nullptr);
+                N.n = n;
+                N.m = nc;
+                N.rowptr.alloc(n + 1, s);
+                N.nnz = scan_counts(cn.p, N.rowptr.p, n, s);
+                N.col.alloc(N.nnz, s);
+                N.val.alloc(N.nnz, s);
+                RN_LAUNCH("pattern", 12.0 * N.nnz + 12.0 * Nn.nnz, s, unamalgamate_pattern_kernel<true>, rows_grid(n),
+                          kT, 0, n, mb, Nn.rowptr.p, Nn.col.p, Nn.val.p, L.agg.p, L.rowtype.p, nullptr, N.rowptr.p,
+                          N.col.p, N.val.p);
+            }
         }
         // ---- candidates, T, energy minimisation, filtering -> P
         L.Bc.alloc((size_t)nc * h.k, s);

@@ -57,6 +57,11 @@ def test_setup_rejects_bad_arguments_without_gpu(rn):
     for k in (0, 5):  # 1 <= k <= RN_MAX_CANDIDATES = 4
         assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, k, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
         assert b"k must be" in rn.rn_last_error()
+    for bs, k in ((4, 4), (0, 1), (3, 4), (2, 1)):  # block_size in [1, 3], dividing n = 4, at most k
+        p = rn.default_params(block_size=bs)
+        assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, k, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
+        assert b"block_size" in rn.rn_last_error()
+    p = rn.default_params()
     p.degree = -1
     assert rn.rn_setup(C.byref(A), C.c_void_p(8), None, 1, 0, C.byref(p), C.byref(h)) == rn.RN_EINVAL
     p = rn.default_params(symmetric=0)

@@ -36,29 +36,13 @@ def close(g, o, what, tol=None):
     assert d <= tol * max(np.max(np.abs(o)) if o.size else 0.0, 1e-300), (what, d)
 
 
-def hier(rn, torch_dev, pr, B, Bhat=None, **over):
-    torch, d = torch_dev
-    A = pr.A
-    params = rn.params_from_config(pr.params, keep_aux=1, **over)
-    return rn.Hierarchy(dev(torch_dev, A.rowptr), dev(torch_dev, A.col), dev(torch_dev, A.val),
-                        dev(torch_dev, B), None if Bhat is None else dev(torch_dev, Bhat), params=params)
-
-
-@pytest.mark.parametrize("k", [2, 3])
-@pytest.mark.parametrize("case", ["poisson64", "aniso96", "convdiff80"])
-def test_k_candidates_hierarchy_parity(rn, torch_dev, oracle, case, k):
-    """Patterns (S, aggregates, roots, N, P, R, coarse A) bit-exact; level-0
-    smoothed candidates bit-exact; T, P, R, coarse A and every level's B, Bc
-    within TOL of the oracle; P Bc = B on free rows that can carry the k
-    candidates.  A post-filter decision may flip only on an entry within TOL
-    of its threshold; the comparison stops at that level."""
-    pr = CASES[case]()
-    tol = TOL if pr.Bhat is None else TOL_NONSYM
-    n = pr.A.n_rows
-    B = grid_candidates(n, k)
-    Bhat = None if pr.Bhat is None else B.copy()
-    h = hier(rn, torch_dev, pr, B, Bhat)
-    oh = oracle.Hierarchy(pr.A.to_scipy(), B, Bhat=Bhat, **dict(pr.params, ncand=k))
+def compare_levels(h, oh, theta, tol):
+    """Level by level: S, aggregates, roots, N and the patterns of T, P, R and
+    the coarse A bit-exact; level-0 smoothed candidates bit-exact; values and
+    every level's B, Bc within tol; P Bc = B on free rows whose pattern can
+    carry all k candidates.  With a post-filter (drop threshold theta) a
+    decision may flip only on an entry within 1e-6 of its threshold, and the
+    comparison stops at that level."""
     st = h.stats()
     assert st["levels"] == len(oh.levels)
     for l, L in enumerate(oh.levels[:-1]):
@@ -80,7 +64,6 @@ def test_k_candidates_hierarchy_parity(rn, torch_dev, oracle, case, k):
             # values agree to TOL, so a post-filter decision may flip on an entry
             # within TOL of the drop threshold; every difference must be one, and
             # the levels below then differ legitimately
-            theta = pr.params.get("postfilter", 0.0)
             assert theta > 0.0, f"P[{l}] pattern differs without a post-filter"
             flips = 0
             for i in range(Pg.shape[0]):
@@ -109,6 +92,32 @@ def test_k_candidates_hierarchy_parity(rn, torch_dev, oracle, case, k):
             ev = np.linalg.eigvalsh(Bc[cols].T @ Bc[cols])
             if ev[0] > 2e-6 * ev[-1]:  # the pattern carries all k candidates
                 assert np.allclose(PB[i], Bg[i], rtol=1e-10, atol=1e-12 * np.abs(Bg).max())
+
+
+def hier(rn, torch_dev, pr, B, Bhat=None, **over):
+    torch, d = torch_dev
+    A = pr.A
+    params = rn.params_from_config(pr.params, keep_aux=1, **over)
+    return rn.Hierarchy(dev(torch_dev, A.rowptr), dev(torch_dev, A.col), dev(torch_dev, A.val),
+                        dev(torch_dev, B), None if Bhat is None else dev(torch_dev, Bhat), params=params)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("case", ["poisson64", "aniso96", "convdiff80"])
+def test_k_candidates_hierarchy_parity(rn, torch_dev, oracle, case, k):
+    """Patterns (S, aggregates, roots, N, P, R, coarse A) bit-exact; level-0
+    smoothed candidates bit-exact; T, P, R, coarse A and every level's B, Bc
+    within TOL of the oracle; P Bc = B on free rows that can carry the k
+    candidates.  A post-filter decision may flip only on an entry within TOL
+    of its threshold; the comparison stops at that level."""
+    pr = CASES[case]()
+    tol = TOL if pr.Bhat is None else TOL_NONSYM
+    n = pr.A.n_rows
+    B = grid_candidates(n, k)
+    Bhat = None if pr.Bhat is None else B.copy()
+    h = hier(rn, torch_dev, pr, B, Bhat)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), B, Bhat=Bhat, **dict(pr.params, ncand=k))
+    compare_levels(h, oh, pr.params.get("postfilter", 0.0), tol)
     h.close()
 
 
@@ -137,3 +146,61 @@ def test_one_candidate_as_n_by_1_matches_vector(rn, torch_dev):
         out.append(as_csr(h.export_csr(0, 4)))
         h.close()
     assert (out[0] != out[1]).nnz == 0
+
+
+# ---------------------------------------------------------------- block systems
+@pytest.mark.parametrize("postfilter", [0.0, 0.05])
+@pytest.mark.parametrize("ny", [8, 16])
+def test_block_system_hierarchy_parity(rn, torch_dev, oracle, ny, postfilter):
+    """2D plane-strain elasticity, 2 unknowns per node, 3 rigid-body modes
+    (Sec. 3.2 amalgamation, Sec. 3.6 block root-node form): node aggregates
+    unamalgamated to unknowns, patterns bit-exact and values within TOL of
+    the oracle on every level, with and without the post-filter (whose
+    own-aggregate block of m columns is always kept)."""
+    pr = PR.elasticity_problem(ny)
+    h = hier(rn, torch_dev, pr, pr.B, postfilter=postfilter)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **dict(pr.params, postfilter=postfilter))
+    assert len(oh.levels) >= 3
+    for L in oh.levels[:-1]:  # unknowns stay node-major: coarse unknowns 2 r, 2 r + 1 per root node
+        assert L.roots.size % 2 == 0
+        assert np.array_equal(L.roots[1::2], L.roots[0::2] + 1) and np.all(L.roots[0::2] % 2 == 0)
+    compare_levels(h, oh, postfilter, TOL)
+    h.close()
+
+
+def test_block_system_two_candidates(rn, torch_dev, oracle):
+    """k = m = 2 (the translations only): T is the block-normalised injection
+    alone, with no row fit for further candidates."""
+    pr = PR.elasticity_problem(8)
+    B = np.ascontiguousarray(pr.B[:, :2])
+    h = hier(rn, torch_dev, pr, B)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), B, **dict(pr.params, ncand=2))
+    compare_levels(h, oh, 0.0, TOL)
+    h.close()
+
+
+def test_system_without_amalgamation_is_refused(rn, torch_dev, oracle):
+    """Aggregating the system unknown by unknown (block_size 1) lets
+    aggregates of one displacement component carry rigid-body modes that
+    vanish on it: P grows to ~1e16 and the coarsest matrix is numerically
+    singular; both sides refuse the setup with the same status."""
+    pr = PR.elasticity_problem(8)
+    with pytest.raises(rn.RNError) as e:
+        hier(rn, torch_dev, pr, pr.B, block_size=1)
+    assert e.value.status == rn.RN_ESINGULAR
+    with pytest.raises(RuntimeError, match=f"status {rn.RN_ESINGULAR}"):
+        oracle.Hierarchy(pr.A.to_scipy(), pr.B, **dict(pr.params, block_size=1))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_block_system_solve(rn, torch_dev, oracle, precision):
+    """CG preconditioned by the block hierarchy's V(1,1) cycle reaches 1e-8
+    (true FP64 residual) within 2 iterations of the oracle's count."""
+    pr = PR.elasticity_problem(32)
+    oh = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    _, oinfo = oh.solve(pr.b, tol=1e-8, maxit=1000, outer=1)
+    h = hier(rn, torch_dev, pr, pr.B, precision=precision)
+    x, info, res = gpu_solve(rn, torch_dev, h, pr, maxit=1000)
+    assert res < 1e-8
+    assert abs(info["iters"] - oinfo["iters"]) <= 2
+    h.close()
