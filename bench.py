@@ -236,6 +236,128 @@ def profile_step(args):
     return 0
 
 
+def next_rows(rn, torch, dev, stream, flush, prec):
+    """Records for the batched and differentiable forms, each one warm-up
+    and one timed pass with device-resident inputs (CUDA events, L2 flushed):
+    256 right-hand sides on the 64^2 Poisson operator (setup + rn_solve_multi),
+    64 uneven rotated-anisotropy problems (rn_setup_batched + rn_solve_batched)
+    and a gradient through the solve on 512^2 variable-coefficient cells
+    (forward setup + solve, adjoint solve, dL/dA scatter, chain to theta)."""
+    from paper_1610_03154_gb300 import adjoint
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    precision = rn.RN_MIXED if prec == "mixed" else rn.RN_FP64
+
+    def clock(fn):
+        out = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append((e0.elapsed_time(e1) / 1e3, r))
+        return out[-1]
+
+    # many right-hand sides
+    pp = PR.poisson_problem(64)
+    s_rhs = 256
+    Bm = t(np.random.default_rng(4).uniform(-1.0, 1.0, (pp.A.n_rows, s_rhs)))
+    Xm = torch.zeros_like(Bm)
+    pd = (t(pp.A.rowptr), t(pp.A.col), t(pp.A.val), t(pp.B.reshape(-1)))
+
+    def multi():
+        Xm.zero_()
+        h = rn.Hierarchy(*pd, params=rn.params_from_config(pp.params, precision=precision), stream=stream.cuda_stream)
+        info = h.solve_multi(Bm, Xm, rtol=1e-8, maxit=500)
+        h.close()
+        return info
+
+    tm, im = clock(multi)
+    Bh, Xh = Bm.cpu().numpy(), Xm.cpu().numpy()  # FP64 residual of every column, on the host
+    res_m = float(np.max(np.linalg.norm(Bh - pp.A.to_scipy() @ Xh, axis=0) / np.linalg.norm(Bh, axis=0)))
+
+    # many problems
+    probs = PR.batch_aniso_problems()
+    dp = [(t(p.A.rowptr), t(p.A.col), t(p.A.val), t(p.B.reshape(-1))) for p in probs]
+    bs = [t(p.b) for p in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    bparams = rn.params_from_config(PR.PARAMS_ANISO, precision=precision)
+
+    def batched_streams():
+        for x in xs:
+            x.zero_()
+        hs = rn.setup_batched(dp, params=bparams)
+        infos = rn.solve_batched(hs, bs, xs, rtol=1e-8, maxit=2000)
+        for h in hs:
+            h.close()
+        return infos
+
+    phases = {}
+
+    def batched_merged():
+        for x in xs:
+            x.zero_()
+        t0 = time.perf_counter()
+        hs = rn.setup_batched(dp, params=bparams)
+        t1 = time.perf_counter()
+        batch = rn.Batch(hs)
+        for h in hs:
+            h.close()
+        t2 = time.perf_counter()
+        infos = batch.solve(bs, xs, rtol=1e-8, maxit=2000)
+        t3 = time.perf_counter()
+        batch.close()
+        phases.update(setup_s=t1 - t0, merge_s=t2 - t1, solve_s=t3 - t2)
+        return infos
+
+    tbs, ibs = clock(batched_streams)
+    tb, ib = clock(batched_merged)
+    n_b = sum(p.A.n_rows for p in probs)
+    nnz_b = sum(p.A.nnz for p in probs)
+    del dp, bs, xs
+
+    # gradient through the solve (512^2 cells); the observation comes from a
+    # GPU solve with another coefficient field
+    m = 512
+    op = adjoint.VarCoefFV(m, dev)
+    vparams = rn.params_from_config(PR.PARAMS_VARCOEF)
+    f = torch.full((m * m,), 1.0 / (m * m), dtype=torch.float64, device=dev)
+    with torch.no_grad():
+        u_obs = adjoint.solve(op.values(t(PR.gaussian_field(m, 22))), f, op.rowptr, op.col, params=vparams,
+                              rtol=1e-10)
+    th0 = t(PR.gaussian_field(m, 21))
+
+    def grad():
+        th = th0.clone().requires_grad_(True)
+        u = adjoint.solve(op.values(th), f, op.rowptr, op.col, params=vparams, rtol=1e-10)
+        L = 0.5 * torch.sum((u - u_obs) ** 2)
+        L.backward()
+        return float(L.detach()), float(torch.linalg.norm(th.grad))
+
+    ta, (La, ga) = clock(grad)
+    return {
+        "multi_rhs": {"step_s": tm, "columns": s_rhs, "iters": im["iters"], "max_rel_res": res_m,
+                      "problem": pp.name, "what": "setup + rn_solve_multi (stationary V(1,1), per-column stop)",
+                      "precision": prec},
+        "batched_problems": {"step_s": tb, "problems": len(probs), "n_total": n_b, "nnz_total": nnz_b,
+                             "max_iters": max(i["iters"] for i in ib),
+                             "max_rel_res": max(i["rel_res"] for i in ib),
+                             "phases_s": phases,
+                             "what": "rn_setup_batched + rn_batch_merge + rn_batch_solve (CG per problem, one "
+                                     "launch per step for all problems), sides U{32..512}, eps 10^U[-4,-1], "
+                                     "psi U[0,pi)",
+                             "streams_step_s": tbs, "streams_max_iters": max(i["iters"] for i in ibs),
+                             "streams_what": "rn_setup_batched + rn_solve_batched (a stream and host thread per "
+                                             "problem)", "precision": prec},
+        "adjoint_grad": {"step_s": ta, "cells": m * m, "rtol": 1e-10, "loss": La, "grad_norm": ga,
+                         "what": "forward setup + CG solve, adjoint CG solve, dL/dA on A's pattern, chain to theta",
+                         "precision": "fp64"},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,6 +481,7 @@ def main():
         es_levels = hs.stats()["levels"]
         hs.close()
     del es, xs_d
+    nexts = next_rows(rn, torch, dev, stream, flush, prec)
 
     # per-launch device times of the solve's level-0 operations, each timed in
     # isolation with CUDA events on the hierarchy's stream, a 256 MB read before
@@ -457,6 +580,7 @@ def main():
                         "cycle": "W(1,1)", "precision": prec},
             "candidates_3": {"step_s": times_k3[0], "iters": infos_k3[0]["iters"], "rel_res": infos_k3[0]["rel_res"],
                              "B": "1, x, y", "precision": prec},
+            **nexts,
             "block_system": {"step_s": es_times[1], "iters": es_infos[1]["iters"], "rel_res": es_infos[1]["rel_res"],
                              "levels": es_levels, "problem": prs.name, "n": prs.A.n_rows, "nnz": prs.A.nnz,
                              "block_size": 2, "B": "3 rigid-body modes", "precision": prec},

@@ -200,6 +200,33 @@ rn_status rn_setup_batched(int count, const rn_csr *A, const double *const *B, c
 rn_status rn_solve_batched(int count, rn_hierarchy *const *h, const double *const *b, double *const *x, double rtol,
                            int maxit, int threads, rn_solve_info *info);
 
+/* Independent problems solved as one (the same deployment variant; Sec. 2's
+ * cycle and outer CG per problem).  rn_batch_merge copies the hierarchies
+ * h[0..count) (set up with equal precision, omega, nu_pre, nu_post and
+ * gamma = 1) into one block-diagonal hierarchy: problem p's operators on its
+ * levels, and below its coarsest level identity transfers with relaxation
+ * weight 0, which carry its right-hand side unchanged to the last level,
+ * where every problem's coarsest block is solved with its own dense inverse.
+ * So every cycle step, and every step of the outer CG (per-problem alpha,
+ * beta and stopping, reduced over row chunks in a fixed order), is one launch
+ * for all problems.  The h[i] are only read and may be freed afterwards.
+ * stream: the batch's CUDA stream (NULL: a stream of its own).  Errors:
+ * RN_EINVAL for count < 1, null arguments or differing cycle settings.
+ * rn_batch_solve runs preconditioned CG on every problem (device vectors b[i],
+ * x[i] of problem i's size; x[i] holds the initial guess and receives the
+ * solution): a problem stops when ||b_i - A_i x_i|| < rtol ||b_i|| or after
+ * maxit iterations; info (may be NULL) gets one record per problem (its
+ * iterations, true relative residual, average convergence factor, the
+ * call's wall time, status).  Returns RN_ENOTCONV when a problem did not
+ * converge.  rn_batch_cycle applies one cycle to every problem: x[i] =
+ * M_i^{-1} b[i].  rn_batch_free releases the batch (NULL: no-op). */
+typedef struct rn_batch rn_batch;
+rn_status rn_batch_merge(int count, rn_hierarchy *const *h, void *stream, rn_batch **out);
+rn_status rn_batch_solve(rn_batch *b, const double *const *bvec, double *const *x, double rtol, int maxit,
+                         rn_solve_info *info);
+rn_status rn_batch_cycle(rn_batch *b, const double *const *bvec, double *const *x);
+void rn_batch_free(rn_batch *b);
+
 /* Apply one V-cycle to b with zero initial guess: x = M^{-1} b (device
  * pointers, FP64, level-0 size).  Used to check the cycle itself. */
 rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x);

@@ -242,6 +242,74 @@ extern "C" rn_status rn_solve_batched(int count, rn_hierarchy *const *h, const d
     });
 }
 
+extern "C" rn_status rn_batch_merge(int count, rn_hierarchy *const *h, void *stream, rn_batch **out) {
+    if (out) *out = nullptr;
+    RN_API_BEGIN
+    using rn::fail;
+    if (!out || !h || count < 1) fail(RN_EINVAL, "null argument or count < 1");
+    for (int i = 0; i < count; i++)
+        if (!h[i]) fail(RN_EINVAL, rn::fmt("hierarchy %d is NULL", i));
+    const rn::AllocScope alloc_scope(alloc_of(h[0]->p));
+    struct StreamGuard {
+        cudaStream_t s = nullptr;
+        ~StreamGuard() {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        }
+    } own;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!s) {
+        RN_CUDA_CHECK(cudaStreamCreate(&own.s));
+        s = own.s;
+    }
+    for (int i = 0; i < count; i++) RN_CUDA_CHECK(cudaStreamSynchronize(h[i]->s));
+    rn_batch *b = rn::batch_merge(count, h, s);
+    b->own_stream = own.s != nullptr;
+    own.s = nullptr;
+    *out = b;
+    return RN_OK;
+    RN_API_END
+}
+
+extern "C" rn_status rn_batch_solve(rn_batch *b, const double *const *bvec, double *const *x, double rtol, int maxit,
+                                    rn_solve_info *info) {
+    RN_API_BEGIN
+    using rn::fail;
+    if (!b || !bvec || !x) fail(RN_EINVAL, "null argument");
+    for (int i = 0; i < b->np; i++)
+        if (!bvec[i] || !x[i]) fail(RN_EINVAL, rn::fmt("vector of problem %d is NULL", i));
+    if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
+    const rn::AllocScope alloc_scope(alloc_of(b->M->p));
+    const rn_status st = rn::batch_solve(*b, bvec, x, rtol, maxit, info);
+    if (st == RN_ENOTCONV) rn::set_last_error("a problem did not reach the tolerance within maxit");
+    return st;
+    RN_API_END
+}
+
+extern "C" rn_status rn_batch_cycle(rn_batch *b, const double *const *bvec, double *const *x) {
+    RN_API_BEGIN
+    using rn::fail;
+    if (!b || !bvec || !x) fail(RN_EINVAL, "null argument");
+    const rn::AllocScope alloc_scope(alloc_of(b->M->p));
+    rn::batch_cycle(*b, bvec, x);
+    return RN_OK;
+    RN_API_END
+}
+
+extern "C" void rn_batch_free(rn_batch *b) {
+    if (!b) return;
+    cudaStream_t s = b->M->s;
+    const bool own = b->own_stream;
+    try {
+        delete b;
+    } catch (...) {
+    }
+    cudaStreamSynchronize(s);
+    if (own) cudaStreamDestroy(s);
+}
+
 extern "C" rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int location, double rtol, int maxit,
                               rn_solve_info *info) {
     RN_API_BEGIN

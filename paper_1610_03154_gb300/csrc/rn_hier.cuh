@@ -33,6 +33,11 @@ struct rn_hierarchy {
     std::vector<std::unique_ptr<rn_level>> lev;  // lev.back() is the coarsest
     int32_t nL = 0;
     rn::DVec<double> Ainv;                        // coarsest inverse, row-major nL x nL
+    // merged independent problems: the coarsest level is block diagonal, block
+    // p on rows [cblk_row[p], cblk_row[p+1]) with its inverse at Ainv + cblk_inv[p]
+    rn::DVec<int32_t> cblk_row;
+    rn::DVec<int64_t> cblk_inv;
+    int ncblk = 0;
     rn::DVec<double> partial;                     // block partial sums (2 x kReduceBlocks)
     rn::DVec<unsigned> counters;                  // arrival counter of the grid reductions (kept at 0)
     rn::DVec<double> scal;                        // device scalars
@@ -61,7 +66,37 @@ struct rn_hierarchy {
     ~rn_hierarchy();
 };
 
+// Independent problems merged into one block-diagonal hierarchy (rn_batch.cu):
+// the merged hierarchy, the level-0 row offsets of every problem, the
+// reduction chunks and the per-problem CG state.
+struct rn_batch {
+    std::unique_ptr<rn_hierarchy> M;
+    bool own_stream = false;
+    int np = 0, nch = 0;
+    std::vector<int32_t> off0;                     // level-0 rows of problem p: [off0[p], off0[p+1])
+    rn::DVec<int32_t> ch_lo, ch_hi, ch_pid, pc;    // chunk rows, problem; first chunk of each problem
+    rn::DVec<double> part;                         // chunk partial sums
+    rn::DVec<unsigned> counter;
+    rn::DVec<double> d;                            // per-problem CG scalars
+    rn::DVec<int32_t> iv;                          // per-problem counters and flags, then the active count
+    rn::DVec<double> bm, xm;                       // merged right-hand side and iterate
+    rn::DVec<int32_t> offs;                        // every level's problem row offsets (levels x (np + 1))
+    rn::DVec<unsigned char> lists;                 // tile-list descriptors of the merged matrices
+    int nlists = 0;
+    bool flexible = false;                         // mixed precision: flexible (Polak-Ribiere) beta
+    double rtol = 0.0, graph_rtol = -1.0;
+    int maxit = 0, graph_maxit = -1;
+    cudaGraph_t it_graph = nullptr;                // one CG iteration
+    cudaGraphExec_t it_exec = nullptr;
+    int64_t it_kernels = 0;
+    ~rn_batch();
+};
+
 namespace rn {
+rn_batch *batch_merge(int count, rn_hierarchy *const *hs, cudaStream_t s);
+void batch_cycle(rn_batch &b, const double *const *rhs, double *const *out);
+rn_status batch_solve(rn_batch &b, const double *const *rhs, double *const *x, double rtol, int maxit,
+                      rn_solve_info *info);
 // Smallest coarse levels in one cluster launch (rn_cluster.cu)
 constexpr int32_t kSubMaxCoarse = 1024;  // coarsest size the cluster solves densely
 constexpr int kSubMaxPhases = 96;        // longest phase list the kernel stages
@@ -117,6 +152,9 @@ void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, c
 void prepare_solve(rn_hierarchy &h);
 rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int maxit, rn_solve_info *info);
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out);
+void cycle_launches(rn_hierarchy &h, const double *rhs, double *out);  // the cycle's launches, no graph
+void outer_spmv(rn_hierarchy &h, const double *x, double *y);          // y = A_0 x
+void outer_residual(rn_hierarchy &h, const double *x, const double *b, double *r);  // r = b - A_0 x
 void cycle_checked(rn_hierarchy &h, const double *rhs, double *out);  // + staging-error check
 void time_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, std::string &name);
 // many right-hand sides (rn_multi.cu)

@@ -108,6 +108,9 @@ struct DCsr {
     int32_t maxlen = 0;     // longest row (set before solving)
     int tile_group = 0;     // lanes per row of the staged SpMV, FP32 values (0: rows too long, unstaged kernel)
     int tile_group64 = 0;   // the same for FP64 values (smaller stages)
+    // optional lists of the staged tiles to process (FP32 / FP64 stages) and
+    // their lengths tcnt[0], tcnt[1]; empty: every tile
+    DVec<int32_t> tl32, tl64, tcnt;
 };
 
 // Borrowed view of a CSR (device pointers).

@@ -43,6 +43,34 @@ __global__ void coarse_solve_kernel(int32_t n, const double *__restrict__ Ainv, 
     }
 }
 
+// x = blockdiag(A_p^{-1}) b for independent problems merged into one
+// hierarchy: block p holds rows [ro[p], ro[p+1]) and its row-major inverse at
+// Ainv + ao[p]; warp per row with the lane order of coarse_solve_kernel, so
+// each block's result is bit-identical to solving that problem alone.
+template <typename TB, typename TO>
+__global__ void coarse_solve_blocks_kernel(int nblk, const int32_t *__restrict__ ro, const int64_t *__restrict__ ao,
+                                           const double *__restrict__ Ainv, const TB *__restrict__ b,
+                                           TO *__restrict__ x) {
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    const int32_t ntot = ro[nblk];
+    for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ntot; i += (gridDim.x * blockDim.x) >> 5) {
+        int lo = 0, hi = nblk - 1;  // the block of row i: the largest p with ro[p] <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ro[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t r0 = ro[lo], n = ro[lo + 1] - r0;
+        const double *Ai = Ainv + ao[lo] + (int64_t)(i - r0) * n;
+        double acc = 0.0;
+        for (int32_t j = lane; j < n; j += 32) acc = fma(Ai[j], (double)b[r0 + j], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) x[i] = (TO)acc;
+    }
+}
+
 __global__ void f2d_kernel(int64_t n, const float *__restrict__ x, double *__restrict__ y) {
     pdl_wait();
     pdl_trigger();
@@ -286,16 +314,16 @@ const double *vals_of<double>(const DCsr &A) { return A.val.p; }
 template <>
 const float *vals_of<float>(const DCsr &A) { return A.val32.p; }
 
-template <typename T, typename TB, typename TO, int G, int OP>
-static void launch_tile(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
-                        T omega, TO *y, T *xz, const double *aux, const Fin &fin, int32_t *err, cudaStream_t s,
-                        bool pdl) {
+template <typename T, typename TB, typename TO, int G, int OP, bool TL>
+static void launch_tile_t(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
+                          T omega, TO *y, T *xz, const double *aux, const Fin &fin, int32_t *err, cudaStream_t s,
+                          bool pdl, const int32_t *tlist, const int32_t *tcount) {
     constexpr int SL = tile_nnz<T>() + kTileSlack;
     constexpr int RL = kS / G + 8;
     const size_t smem = (2 * SL + 2 * RL) * sizeof(int32_t) + 2 * SL * sizeof(T);
     static bool configured = false;
     if (!configured) {
-        RN_CUDA_CHECK(cudaFuncSetAttribute(spmv_tile_kernel<T, TB, TO, G, OP>,
+        RN_CUDA_CHECK(cudaFuncSetAttribute(spmv_tile_kernel<T, TB, TO, G, OP, TL>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
@@ -306,8 +334,30 @@ static void launch_tile(const char *name, double bytes, const DCsr &M, const T *
     struct {
         bool pdl;
     } hh{pdl};
-    RN_SLAUNCH(hh, name, bytes, s, (spmv_tile_kernel<T, TB, TO, G, OP>), grid, kS, smem, M.n, ntiles, M.rowptr.p,
-               M.col.p, vals_of<T>(M), x, b, diag, omega, y, xz, aux, fin, err);
+    RN_SLAUNCH(hh, name, bytes, s, (spmv_tile_kernel<T, TB, TO, G, OP, TL>), grid, kS, smem, M.n, ntiles,
+               M.rowptr.p, M.col.p, vals_of<T>(M), x, b, diag, omega, y, xz, aux, fin, err, tlist, tcount);
+}
+
+// Merged independent problems list the tiles that hold rows of problems still
+// iterating; the other matrices (and the fused-reduction operations, which
+// the merged solve does not use) run every tile.
+template <typename T, typename TB, typename TO, int G, int OP>
+static void launch_tile(const char *name, double bytes, const DCsr &M, const T *x, const TB *b, const T *diag,
+                        T omega, TO *y, T *xz, const double *aux, const Fin &fin, int32_t *err, cudaStream_t s,
+                        bool pdl) {
+    constexpr bool f64 = sizeof(T) == 8;
+    const int32_t *tlist = f64 ? M.tl64.p : M.tl32.p;
+    if constexpr (OP != OP_SPMV_DOT && OP != OP_JACOBI_RZ) {
+        if (tlist) {
+            launch_tile_t<T, TB, TO, G, OP, true>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, err, s, pdl,
+                                                  tlist, M.tcnt.p + (f64 ? 1 : 0));
+            return;
+        }
+    } else {
+        if (tlist) fail(RN_EINTERNAL, "tile lists are not used with fused reductions");
+    }
+    launch_tile_t<T, TB, TO, G, OP, false>(name, bytes, M, x, b, diag, omega, y, xz, aux, fin, err, s, pdl, nullptr,
+                                           nullptr);
 }
 
 template <typename T, typename TB, typename TO, int G, int OP>
@@ -486,8 +536,12 @@ static T *vcycle_level(rn_hierarchy &h, int l) {
     const Fin none;
     if (l == (int)h.lev.size() - 1) {
         T *x = LB::x(L);
-        RN_SLAUNCH(h, nm.coarse, 8.0 * n * n + 2.0 * sizeof(T) * n, s, (coarse_solve_kernel<T, T>),
-                  grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, b, x);
+        if (h.ncblk > 0)
+            RN_SLAUNCH(h, nm.coarse, 8.0 * h.Ainv.n + 2.0 * sizeof(T) * n, s, (coarse_solve_blocks_kernel<T, T>),
+                       grid_for((int64_t)n * 32, 256, 4), 256, 0, h.ncblk, h.cblk_row.p, h.cblk_inv.p, h.Ainv.p, b, x);
+        else
+            RN_SLAUNCH(h, nm.coarse, 8.0 * n * n + 2.0 * sizeof(T) * n, s, (coarse_solve_kernel<T, T>),
+                       grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, b, x);
         return x;
     }
     const T omega = (T)h.p.omega;
@@ -521,8 +575,13 @@ static bool vcycle_top(rn_hierarchy &h, const double *rhs, double *out, const Fi
     const int32_t n = L.A.n;
     const Fin none;
     if (h.lev.size() == 1) {
-        RN_SLAUNCH(h, nm.coarse, 8.0 * n * n + 16.0 * n, s, (coarse_solve_kernel<double, double>),
-                  grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, rhs, out);
+        if (h.ncblk > 0)
+            RN_SLAUNCH(h, nm.coarse, 8.0 * h.Ainv.n + 16.0 * n, s, (coarse_solve_blocks_kernel<double, double>),
+                       grid_for((int64_t)n * 32, 256, 4), 256, 0, h.ncblk, h.cblk_row.p, h.cblk_inv.p, h.Ainv.p,
+                       rhs, out);
+        else
+            RN_SLAUNCH(h, nm.coarse, 8.0 * n * n + 16.0 * n, s, (coarse_solve_kernel<double, double>),
+                       grid_for((int64_t)n * 32, 256, 4), 256, 0, n, h.Ainv.p, rhs, out);
         return false;
     }
     const T omega = (T)h.p.omega;
@@ -566,6 +625,17 @@ static bool cycle_direct(rn_hierarchy &h, const double *rhs, double *out, const 
 
 // Whether the outer CG's update forms level 0's first-sweep iterate.
 static bool cg_forms_x0(const rn_hierarchy &h) { return h.p.nu_pre == 1 && h.lev.size() > 1; }
+
+void cycle_launches(rn_hierarchy &h, const double *rhs, double *out) { cycle_direct(h, rhs, out); }
+
+void outer_spmv(rn_hierarchy &h, const double *x, double *y) {
+    spmv<double, double, double, OP_SPMV>(h, "outer_spmv", h.lev[0]->A, x, (const double *)nullptr, nullptr, 0.0, y,
+                                          Fin());
+}
+
+void outer_residual(rn_hierarchy &h, const double *x, const double *b, double *r) {
+    spmv<double, double, double, OP_RESID>(h, "outer_residual", h.lev[0]->A, x, b, nullptr, 0.0, r, Fin());
+}
 
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out) {
     cudaStream_t s = h.s;

@@ -113,12 +113,13 @@ __device__ __forceinline__ void spmv_epilogue(int32_t i, T acc, const T *__restr
 // host's choice of G) are staged by bulk copies into a two-stage buffer.
 // Thread 0 keeps the next tile's copies in flight and prefetches the bounds
 // of the tile after that.  err[0] is set if an mbarrier wait gives up.
-template <typename T, typename TB, typename TO, int G, int OP>
+template <typename T, typename TB, typename TO, int G, int OP, bool TL>
 __global__ void __launch_bounds__(kS)
 spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                  const T *__restrict__ val, const T *__restrict__ x, const TB *__restrict__ b,
                  const T *__restrict__ diag, T omega, TO *__restrict__ y, T *__restrict__ xz,
-                 const double *__restrict__ aux, Fin fin, int32_t *__restrict__ err) {
+                 const double *__restrict__ aux, Fin fin, int32_t *__restrict__ err,
+                 const int32_t *__restrict__ tlist, const int32_t *__restrict__ tcount) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NV = OpNV<OP>::value;
     constexpr int SL = tile_nnz<T>() + kTileSlack;
@@ -139,14 +140,23 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
     __syncthreads();
     uint32_t pend = 0u;             // thread 0: bit s = copies into stage s issued, not yet waited for
     int32_t be0 = 0, be1 = 0;       // thread 0: nnz bounds of the next tile to issue
-    auto load_bounds = [&](int t) {
-        if (t < ntiles) {
+    // the tiles to process: all, or (TL) the first *tcount entries of tlist
+    // (which only change between launches, so they are read before pdl_wait)
+    int32_t nt = ntiles;
+    if constexpr (TL) nt = *tcount;
+    auto tile_of = [&](int i) {
+        if constexpr (TL) return tlist[i];
+        else return i;
+    };
+    auto load_bounds = [&](int i) {
+        if (i < nt) {
+            const int32_t t = tile_of(i);
             be0 = rp[t * RPT];
             be1 = rp[min(n, t * RPT + RPT)];
         }
     };
-    auto issue = [&](int stage, int t) {
-        const int32_t r0 = t * RPT;
+    auto issue = [&](int stage, int i) {
+        const int32_t r0 = tile_of(i) * RPT;
         const int32_t r1 = min(n, r0 + RPT);
         const int32_t c0 = be0 & ~3, c1 = (be1 + 3) & ~3;
         const int32_t v0 = be0 & ~(VA - 1), v1 = (be1 + VA - 1) & ~(VA - 1);
@@ -162,22 +172,22 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
     uint32_t parity = 0u;  // bit s = phase parity to wait for on stage s
     bool failed = false;
     int st = 0;
-    int tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles) {  // the matrix is constant: stage it before the predecessor finishes
-        load_bounds(tile);
-        issue(0, tile);
-        load_bounds(tile + gridDim.x);
+    int it = blockIdx.x;  // position in the tile sequence
+    if (tid == 0 && it < nt) {  // the matrix is constant: stage it before the predecessor finishes
+        load_bounds(it);
+        issue(0, it);
+        load_bounds(it + gridDim.x);
     }
     pdl_wait();
     pdl_trigger();
-    for (; tile < ntiles; tile += gridDim.x, st ^= 1) {
-        const int nxt = tile + gridDim.x;
-        if (tid == 0 && nxt < ntiles) {
+    for (; it < nt; it += gridDim.x, st ^= 1) {
+        const int nxt = it + gridDim.x;
+        if (tid == 0 && nxt < nt) {
             fence_proxy_async();  // earlier generic reads of that stage come before the async writes
             issue(st ^ 1, nxt);
             load_bounds(nxt + gridDim.x);  // lands while this tile is computed
         }
-        const int32_t r0 = tile * RPT;
+        const int32_t r0 = tile_of(it) * RPT;
         const int32_t row = r0 + tid / G;
         const int lane = tid % G;
         const bool live = row < min(n, r0 + RPT);

@@ -83,6 +83,11 @@ def _load():
                                    C.c_int, P(rn_solve_info)]
     L.rn_free.argtypes = [C.c_void_p]
     L.rn_free.restype = None
+    L.rn_batch_merge.argtypes = [C.c_int, P(C.c_void_p), C.c_void_p, P(C.c_void_p)]
+    L.rn_batch_solve.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), C.c_double, C.c_int, P(rn_solve_info)]
+    L.rn_batch_cycle.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p)]
+    L.rn_batch_free.argtypes = [C.c_void_p]
+    L.rn_batch_free.restype = None
     L.rn_energy_min.argtypes = [P(rn_csr), P(rn_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                 C.c_void_p]
     L.rn_energy_min_noalloc.argtypes = [P(rn_csr), P(rn_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
@@ -115,6 +120,10 @@ rn_solve_multi = lib.rn_solve_multi
 rn_setup_batched = lib.rn_setup_batched
 rn_solve_batched = lib.rn_solve_batched
 rn_free = lib.rn_free
+rn_batch_merge = lib.rn_batch_merge
+rn_batch_solve = lib.rn_batch_solve
+rn_batch_cycle = lib.rn_batch_cycle
+rn_batch_free = lib.rn_batch_free
 rn_hierarchy_stats = lib.rn_hierarchy_stats
 rn_export_csr = lib.rn_export_csr
 rn_export_vec = lib.rn_export_vec
@@ -290,6 +299,45 @@ def use_torch_allocator(p: rn_params, stream=None) -> rn_params:
     if stream is not None:
         p.stream = C.c_void_p(stream)
     return p
+
+
+class Batch:
+    """Independent problems merged into one block-diagonal hierarchy
+    (rn_batch_merge): every cycle and CG step is one launch for all of them.
+    hierarchies: Hierarchy objects (only read; they may be closed afterwards)."""
+
+    def __init__(self, hierarchies, stream=None):
+        k = len(hierarchies)
+        H = (C.c_void_p * k)(*[h._h.value for h in hierarchies])
+        self._b = C.c_void_p()
+        self.count = k
+        _check(rn_batch_merge(k, H, C.c_void_p(stream) if stream else None, C.byref(self._b)), "rn_batch_merge")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            rn_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        self.close()
+
+    def solve(self, bs, xs, rtol=1e-8, maxit=500, raise_on_notconv=True):
+        """CG on every problem (device vectors); xs updated in place; one record per problem."""
+        k = self.count
+        Bv = (C.c_void_p * k)(*[_ptr(b) for b in bs])
+        Xv = (C.c_void_p * k)(*[_ptr(x) for x in xs])
+        infos = (rn_solve_info * k)()
+        st = rn_batch_solve(self._b, Bv, Xv, rtol, maxit, infos)
+        if st != RN_OK and (st != RN_ENOTCONV or raise_on_notconv):
+            raise RNError(st, "rn_batch_solve")
+        return [dict(iters=i.iters, rel_res=i.rel_res, rho=i.rho, solve_ms=i.solve_ms, status=i.status) for i in infos]
+
+    def cycle(self, bs, xs):
+        """xs[i] = M_i^{-1} bs[i]: one cycle per problem."""
+        k = self.count
+        Bv = (C.c_void_p * k)(*[_ptr(b) for b in bs])
+        Xv = (C.c_void_p * k)(*[_ptr(x) for x in xs])
+        _check(rn_batch_cycle(self._b, Bv, Xv), "rn_batch_cycle")
 
 
 class Hierarchy:

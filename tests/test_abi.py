@@ -93,3 +93,15 @@ def test_status_strings(rn):
 def test_profile_api_without_launches(rn):
     rn.profile_reset()
     assert rn.profile_read() == {}
+
+
+def test_batch_rejects_bad_arguments_without_gpu(rn):
+    b = C.c_void_p(123)
+    assert rn.rn_batch_merge(0, None, None, C.byref(b)) == rn.RN_EINVAL
+    assert b.value is None
+    H = (C.c_void_p * 2)(None, None)
+    assert rn.rn_batch_merge(2, H, None, C.byref(b)) == rn.RN_EINVAL
+    assert b"NULL" in rn.rn_last_error()
+    assert rn.rn_batch_solve(None, None, None, 1e-8, 10, None) == rn.RN_EINVAL
+    assert rn.rn_batch_cycle(None, None, None) == rn.RN_EINVAL
+    rn.rn_batch_free(None)
