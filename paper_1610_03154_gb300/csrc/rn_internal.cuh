@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <cstring>
 #include <string>
 #include <utility>
 #include <vector>
@@ -199,11 +200,24 @@ template <typename T>
 void d2d(T *dst, const T *src, size_t n, cudaStream_t s) {
     if (n) RN_CUDA_CHECK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
 }
+// This thread's page-locked host scratch (kPinnedBytes): small device->host
+// reads land there by DMA, with no staging through the driver's pageable
+// buffer, so threads driving independent setups do not serialise on it.
+constexpr size_t kPinnedBytes = 1024;
+void *pinned_scratch();
+// Read n elements (n * sizeof(T) <= kPinnedBytes) and wait for them.
+template <typename T>
+void read_small(T *dst, const T *dptr, size_t n, cudaStream_t s) {
+    if (n * sizeof(T) > kPinnedBytes) fail(RN_EINTERNAL, "read_small: more than the pinned scratch holds");
+    T *h = static_cast<T *>(pinned_scratch());
+    RN_CUDA_CHECK(cudaMemcpyAsync(h, dptr, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    std::memcpy(dst, h, n * sizeof(T));
+}
 template <typename T>
 T read_scalar(const T *dptr, cudaStream_t s) {
     T v;
-    RN_CUDA_CHECK(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
-    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    read_small(&v, dptr, 1, s);
     return v;
 }
 

@@ -36,6 +36,30 @@ double now_ms() {
 // --------------------------------------------------------------------- memory
 static bool g_pool_configured = false;
 
+// Pinned scratch: slots of one page-locked pool (allocated once, kept for the
+// process), one per thread; threads past the pool's slots get their own.
+void *pinned_scratch() {
+    constexpr int kSlots = 256;
+    static unsigned char *pool = nullptr;
+    static std::once_flag once;
+    static std::atomic<int> next{0};
+    thread_local void *mine = nullptr;
+    if (mine) return mine;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        if (cudaMallocHost(&p, kSlots * kPinnedBytes) == cudaSuccess) pool = static_cast<unsigned char *>(p);
+    });
+    const int k = next++;
+    if (pool && k < kSlots) {
+        mine = pool + (size_t)k * kPinnedBytes;
+    } else {
+        void *p = nullptr;  // kept for the thread's life (and the process's: a few bytes)
+        RN_CUDA_CHECK(cudaMallocHost(&p, kPinnedBytes));
+        mine = p;
+    }
+    return mine;
+}
+
 Allocator &current_allocator() {
     thread_local Allocator a;
     return a;

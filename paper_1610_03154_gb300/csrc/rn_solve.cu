@@ -702,8 +702,7 @@ void prepare_solve(rn_hierarchy &h) {
         launch_maxlen(h, h.lev[l]->R, ml.p + 3 * l + 2);
     }
     std::vector<int32_t> mlh(nmat);
-    RN_CUDA_CHECK(cudaMemcpyAsync(mlh.data(), ml.p, ml.bytes(), cudaMemcpyDeviceToHost, s));
-    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    read_small(mlh.data(), ml.p, nmat, s);  // at most 3 x 32 levels
     for (size_t l = 0; l < h.lev.size(); l++) {
         rn_level &L = *h.lev[l];
         const int32_t n = L.A.n;
@@ -957,8 +956,7 @@ rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int ma
             for (;;) {
                 RN_CUDA_CHECK(cudaGraphLaunch(h.cg_exec, s));
                 int32_t fl[3];  // iterations done, limit, converged
-                RN_CUDA_CHECK(cudaMemcpyAsync(fl, h.iflags.p + 9, sizeof fl, cudaMemcpyDeviceToHost, s));
-                RN_CUDA_CHECK(cudaStreamSynchronize(s));
+                read_small(fl, h.iflags.p + 9, 3, s);
                 const int done = fl[0] - it;
                 const bool stopped = fl[2] != 0 || fl[0] >= maxit;
                 // the second half runs in every iteration but a stopping one
@@ -1004,8 +1002,7 @@ rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int ma
                 it++;
                 k = j + 1;
                 double res[2];
-                RN_CUDA_CHECK(cudaMemcpyAsync(res, sc + 15, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-                RN_CUDA_CHECK(cudaStreamSynchronize(s));
+                read_small(res, sc + 15, 2, s);
                 if (res[0] / nb < rtol || res[1] == 0.0) break;
                 RN_LAUNCH("outer_gmres_vec", 16.0 * n, s, scale_copy_kernel, eg, 256, 0, n, h.w.p, sc + 16,
                           h.V.p + (int64_t)(j + 1) * n, 0);

@@ -482,8 +482,7 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
                   A.rowptr, A.col, B.rowptr, ub.p, bins.p, flags.p);
     scan_counts_dev(ub.p, ubp.p, n, tot, s);
     int32_t fl[12];  // one read: bins, flags and the products' total
-    RN_CUDA_CHECK(cudaMemcpyAsync(fl, flags.p, sizeof fl, cudaMemcpyDeviceToHost, s));
-    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    read_small(fl, flags.p, 12, s);
     int64_t total = 0;
     std::memcpy(&total, fl + 8, sizeof total);
     if (fl[2] || total > INT32_MAX) fail(RN_EINTERNAL, "spgemm: a row's product count exceeds int32");
@@ -522,8 +521,7 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
     }
     C.rowptr.alloc(n + 1, s);
     scan_counts_dev(count.p, C.rowptr.p, n, tot + 1, s);
-    RN_CUDA_CHECK(cudaMemcpyAsync(fl, flags.p, sizeof fl, cudaMemcpyDeviceToHost, s));
-    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    read_small(fl, flags.p, 12, s);
     if (fl[4]) fail(RN_EINTERNAL, fmt("product row has more than %d distinct columns", kBigProd / 2));
     std::memcpy(&total, fl + 10, sizeof total);
     C.nnz = total;
