@@ -34,7 +34,6 @@ double now_ms() {
 }
 
 // --------------------------------------------------------------------- memory
-static bool g_pool_configured = false;
 
 // Pinned scratch: slots of one page-locked pool (allocated once, kept for the
 // process), one per thread; threads past the pool's slots get their own.
@@ -80,17 +79,18 @@ void *dmalloc(size_t bytes, cudaStream_t s, const Allocator &a, size_t *got) {
         }
         return p;
     }
-    if (!g_pool_configured) {
+    static const bool pool_configured = [] {
         // keep freed blocks cached in the device's default pool: setup makes
-        // many short-lived allocations
+        // many short-lived allocations (once; thread-safe static initialisation)
         int dev = 0;
         RN_CUDA_CHECK(cudaGetDevice(&dev));
         cudaMemPool_t pool;
         RN_CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, dev));
         uint64_t thr = UINT64_MAX;
         RN_CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-        g_pool_configured = true;
-    }
+        return true;
+    }();
+    (void)pool_configured;
     void *p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
@@ -109,12 +109,12 @@ void dfree(void *p, size_t got, cudaStream_t s, const Allocator &a) {
 
 // --------------------------------------------------------------------- launch helpers
 int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {  // thread-safe static initialisation
+        int dev = 0, v = 0;
         RN_CUDA_CHECK(cudaGetDevice(&dev));
-        RN_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    }
+        RN_CUDA_CHECK(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        return v;
+    }();
     return sms;
 }
 

@@ -321,12 +321,12 @@ static void launch_tile_t(const char *name, double bytes, const DCsr &M, const T
     constexpr int SL = tile_nnz<T>() + kTileSlack;
     constexpr int RL = kS / G + 8;
     const size_t smem = (2 * SL + 2 * RL) * sizeof(int32_t) + 2 * SL * sizeof(T);
-    static bool configured = false;
-    if (!configured) {
+    static const bool configured = [&] {  // once per instantiation (thread-safe static initialisation)
         RN_CUDA_CHECK(cudaFuncSetAttribute(spmv_tile_kernel<T, TB, TO, G, OP, TL>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     const int32_t ntiles = (M.n + (kS / G) - 1) / (kS / G);
     const int per_sm = sizeof(T) == 8 ? 3 : 4;  // CTAs that fit one SM's shared memory
     int grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);

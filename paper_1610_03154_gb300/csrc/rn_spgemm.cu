@@ -443,12 +443,12 @@ static void launch_hash(int32_t nrows, const int32_t *rows, const CsrView &A, co
                         cudaStream_t s) {
     constexpr int GPB = kFuThreads / G;
     const size_t smem = (size_t)GPB * SLOTS * (sizeof(double) + sizeof(int32_t)) + (size_t)GPB * (SLOTS / 2) * 4;
-    static bool configured = false;
-    if (!configured) {
+    static const bool configured = [&] {  // once per instantiation (thread-safe static initialisation)
         RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_kernel<G, SLOTS>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     const int grid = grid_resident(hash_product_kernel<G, SLOTS>, kFuThreads, smem, nrows, GPB);
     RN_LAUNCH("spgemm_hash", bytes, s, (hash_product_kernel<G, SLOTS>), grid, kFuThreads, smem, nrows, rows,
               A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count, ovf_list, ovf_n);
@@ -509,12 +509,12 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
                               flags.p + 3, bytes, s);
         // rows past the tables (counted on the device): a block per row, looping
         const size_t smem = (size_t)kBigProd * (sizeof(double) + 2 * sizeof(int32_t));
-        static bool configured = false;
-        if (!configured) {
+        static const bool configured = [&] {
             RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_block_kernel,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            configured = true;
-        }
+            return true;
+        }();
+        (void)configured;
         RN_LAUNCH("spgemm_hash_long", 0, s, hash_product_block_kernel, std::min(nlarge, 2 * num_sms()), 512, smem,
                   flags.p + 3, ovf2.p, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p,
                   count.p, flags.p + 4);
