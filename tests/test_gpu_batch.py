@@ -122,3 +122,26 @@ def test_merged_solve_iteration_limit(env):
     batch.close()
     for h in hs:
         h.close()
+
+
+def test_merged_solve_against_the_oracle(env, oracle):
+    """Uneven problems merged (FP64 cycle): each reaches 1e-8 within 2
+    iterations of the oracle's CG on the same hierarchy recipe."""
+    torch, dev, rn = env
+    probs = PR.batch_aniso_problems(count=4, seed=11, side_lo=16, side_hi=64)
+    probs.append(PR.aniso_problem(8, seed=9))
+    hs, t = _setup(env, probs, 0)
+    batch = rn.Batch(hs)
+    for h in hs:
+        h.close()
+    bs = [t(p.b) for p in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = batch.solve(bs, xs, rtol=1e-8, maxit=1000)
+    batch.close()
+    for p, info, x in zip(probs, infos, xs):
+        oh = oracle.Hierarchy(p.A.to_scipy(), p.B, **dict(PR.PARAMS_ANISO, outer=1))
+        _, oinfo = oh.solve(p.b, tol=1e-8, maxit=1000, outer=1)
+        assert info["status"] == 0
+        assert abs(info["iters"] - oinfo["iters"]) <= 2, (p.name, info["iters"], oinfo["iters"])
+        xh = x.cpu().numpy()
+        assert np.linalg.norm(p.b - p.A.to_scipy() @ xh) / np.linalg.norm(p.b) < 1e-8
