@@ -276,6 +276,23 @@ def next_rows(rn, torch, dev, stream, flush, prec):
         return info
 
     tm, im = clock(multi)
+    # the solve's launches one by one, each bracketed by CUDA events (the
+    # library's profiler): algorithmic bytes / time, L2 + HBM (the 4 MB
+    # multivectors and the operators stay in L2)
+    hm = rn.Hierarchy(*pd, params=rn.params_from_config(pp.params, precision=precision), stream=stream.cuda_stream)
+    Xm.zero_()
+    torch.cuda.synchronize()
+    rn.profile_reset()
+    rn.profile_enable(True)
+    hm.solve_multi(Bm, Xm, rtol=1e-8, maxit=500)
+    rn.profile_enable(False)
+    prof = rn.profile_read()
+    rn.profile_reset()
+    hm.close()
+    mk = {k: v for k, v in prof.items() if k.startswith("multi_")}
+    m_bytes = sum(v["bytes"] for v in mk.values())
+    m_ms = sum(v["ms"] for v in mk.values())
+    top = max(mk.items(), key=lambda kv: kv[1]["ms"]) if mk else ("", {"bytes": 0.0, "ms": 0.0, "launches": 0})
     Bh, Xh = Bm.cpu().numpy(), Xm.cpu().numpy()  # FP64 residual of every column, on the host
     res_m = float(np.max(np.linalg.norm(Bh - pp.A.to_scipy() @ Xh, axis=0) / np.linalg.norm(Bh, axis=0)))
 
@@ -341,6 +358,12 @@ def next_rows(rn, torch, dev, stream, flush, prec):
     return {
         "multi_rhs": {"step_s": tm, "columns": s_rhs, "iters": im["iters"], "max_rel_res": res_m,
                       "problem": pp.name, "what": "setup + rn_solve_multi (stationary V(1,1), per-column stop)",
+                      "solve_gbs_l2_hbm": (m_bytes / (m_ms * 1e-3) / 1e9) if m_ms > 0 else None,
+                      "top_kernel": {"name": top[0], "launches": top[1]["launches"],
+                                     "gbs_l2_hbm": (top[1]["bytes"] / (top[1]["ms"] * 1e-3) / 1e9)
+                                     if top[1]["ms"] > 0 else None},
+                      "gbs_rule": "algorithmic bytes of every solve launch / its CUDA-event time, launches timed "
+                                  "one by one (warm L2)",
                       "precision": prec},
         "batched_problems": {"step_s": tb, "problems": len(probs), "n_total": n_b, "nnz_total": nnz_b,
                              "max_iters": max(i["iters"] for i in ib),
@@ -583,7 +606,8 @@ def main():
             **nexts,
             "block_system": {"step_s": es_times[1], "iters": es_infos[1]["iters"], "rel_res": es_infos[1]["rel_res"],
                              "levels": es_levels, "problem": prs.name, "n": prs.A.n_rows, "nnz": prs.A.nnz,
-                             "block_size": 2, "B": "3 rigid-body modes", "precision": prec},
+                             "block_size": 2, "B": "3 rigid-body modes", "strength": "classical, theta 0.5",
+                             "precision": prec},
             "roofline": roofline,
             "level0_launches": kernels,
             "gpu_launches": launches // max(args.steps, 1),

@@ -87,12 +87,31 @@ spmm_kernel(int32_t n, int s, const int32_t *__restrict__ rp, const int32_t *__r
     }
 }
 
-// column sums of the per-block partials, in block order
-__global__ void col_norms_kernel(int nb, int s, const double *__restrict__ part, double *__restrict__ out) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s; c += gridDim.x * blockDim.x) {
-        double t = 0.0;
-        for (int b = 0; b < nb; b++) t += part[(int64_t)b * s + c];
-        out[c] = t;
+// column sums of the per-block partials: a block per 32 columns, lane =
+// column; warp w sums partials w, w + 8, ... (four chains), and the eight warp
+// sums are added in warp order (a fixed order: reproducible run to run)
+constexpr int kColWarps = 8;
+__global__ void __launch_bounds__(32 * kColWarps)
+col_norms_kernel(int nb, int s, const double *__restrict__ part, double *__restrict__ out) {
+    __shared__ double ws[kColWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    if (c < s) {
+        int b = w;
+        for (; b + 3 * kColWarps < nb; b += 4 * kColWarps) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) t[u] += part[(int64_t)(b + u * kColWarps) * s + c];
+        }
+        for (; b < nb; b += kColWarps) t[0] += part[(int64_t)b * s + c];
+    }
+    ws[w][lane] = (t[0] + t[1]) + (t[2] + t[3]);
+    __syncthreads();
+    if (w == 0 && c < s) {
+        double a = 0.0;
+#pragma unroll
+        for (int k = 0; k < kColWarps; k++) a += ws[k][lane];
+        out[c] = a;
     }
 }
 
@@ -262,7 +281,7 @@ static rn_status solve_multi_t(rn_hierarchy &h, const double *B, double *X, int 
     auto residual = [&](double *out) {  // R = B - A X, out = per-column ||r||^2
         spmm<double, double, double, M_RESID>(s, "multi_outer_residual", L0.A, ns, X, B, (const double *)nullptr,
                                               R.p, (double *)nullptr, part.p, grid);
-        RN_LAUNCH("multi_col_norms", 8.0 * grid * ns, s, col_norms_kernel, grid_for(ns, 256), 256, 0, grid, ns,
+        RN_LAUNCH("multi_col_norms", 8.0 * grid * ns, s, col_norms_kernel, (ns + 31) / 32, 32 * kColWarps, 0, grid, ns,
                   part.p, out);
     };
     // ||b_c||^2 from the same reduction with X = 0
@@ -271,7 +290,7 @@ static rn_status solve_multi_t(rn_hierarchy &h, const double *B, double *X, int 
         RN_CUDA_CHECK(cudaMemsetAsync(zero.p, 0, sizeof(double) * tot, s));
         spmm<double, double, double, M_RESID>(s, "multi_outer_residual", L0.A, ns, zero.p, B, (const double *)nullptr,
                                               R.p, (double *)nullptr, part.p, grid);
-        RN_LAUNCH("multi_col_norms", 8.0 * grid * ns, s, col_norms_kernel, grid_for(ns, 256), 256, 0, grid, ns,
+        RN_LAUNCH("multi_col_norms", 8.0 * grid * ns, s, col_norms_kernel, (ns + 31) / 32, 32 * kColWarps, 0, grid, ns,
                   part.p, nb2.p);
         RN_CUDA_CHECK(cudaMemcpyAsync(hb.data(), nb2.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
     }
