@@ -502,6 +502,7 @@ def main():
         torch.cuda.synchronize()
         es_times.append(e0.elapsed_time(e1) / 1e3)
         es_levels = hs.stats()["levels"]
+        es_setup_ms = hs.stats().get("setup_ms")
         hs.close()
     del es, xs_d
     nexts = next_rows(rn, torch, dev, stream, flush, prec)
@@ -605,7 +606,7 @@ def main():
                              "B": "1, x, y", "precision": prec},
             **nexts,
             "block_system": {"step_s": es_times[1], "iters": es_infos[1]["iters"], "rel_res": es_infos[1]["rel_res"],
-                             "levels": es_levels, "problem": prs.name, "n": prs.A.n_rows, "nnz": prs.A.nnz,
+                             "levels": es_levels, "setup_ms": es_setup_ms, "problem": prs.name, "n": prs.A.n_rows, "nnz": prs.A.nnz,
                              "block_size": 2, "B": "3 rigid-body modes", "strength": "classical, theta 0.5",
                              "precision": prec},
             "roofline": roofline,

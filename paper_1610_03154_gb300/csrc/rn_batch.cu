@@ -338,7 +338,7 @@ void merge_matrix(const std::vector<MergeBlk> &blk, int32_t ncols, DCsr &out, cu
     if (nztot)
         RN_LAUNCH("batch_merge", 24.0 * nztot, s, merge_entries_kernel, grid_for(nztot, 1024), 256, 0, nb, B, nztot,
                   out.col.p, out.val.p);
-    RN_CUDA_CHECK(cudaStreamSynchronize(s));  // bd is released on return
+    // bd is released stream-ordered after the kernels; blk was staged by the upload
 }
 
 BCg bcg_of(rn_batch &b) {
