@@ -144,6 +144,8 @@ struct EmCtx {
     double *rs2 = nullptr;  // n rows: the row projection's scales (allocated internally when null)
     bool fp32 = false;      // CG sweeps in FP32 (mixed precision); workspaces then allocated internally
     int k = 1;              // candidates (Bc is nc x k); k > 1 projects with per-row Gram pseudo-inverses
+    const double *gp64 = nullptr;     // k > 1: G_i^+ already formed on N and Bc (else formed inside)
+    const int32_t *zero_row = nullptr;
 };
 // dinv: the inverted diagonal of A (CG's preconditioner D^{-1} when c.precond)
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,

@@ -405,7 +405,7 @@ __global__ void gram_pinv_kernel(int32_t n, const int32_t *__restrict__ rp, cons
         double g[K * K] = {}, gp[K * K] = {};
         const int32_t len = rp[i + 1] - rp[i];
         int z = 1;
-        if (rowtype[i] == FREE_ROW && len > 1) {
+        if (rowtype[i] == FREE_ROW && len >= 1) {  // G_i^+ of one-entry rows too: the row fits use it
             for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
                 const double *b = Bc + (int64_t)col[e] * K;
 #pragma unroll
@@ -413,7 +413,8 @@ __global__ void gram_pinv_kernel(int32_t n, const int32_t *__restrict__ rp, cons
 #pragma unroll
                     for (int c = 0; c < K; c++) g[a * K + c] += b[a] * b[c];
             }
-            z = sym_pinv_dev<K>(g, gp) >= len;
+            const int rank = sym_pinv_dev<K>(g, gp);
+            z = len > 1 ? rank >= len : 1;
         }
 #pragma unroll
         for (int q = 0; q < K * K; q++) Gp[(int64_t)i * K * K + q] = gp[q];
@@ -442,6 +443,39 @@ __global__ void row_fit_k_kernel(int32_t n, const int32_t *__restrict__ rp, cons
             }
         }
         sym_pinv_dev<K>(g, gp);
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+            y[c] = 0.0;
+#pragma unroll
+            for (int a = 0; a < K; a++) y[c] += r[a] * gp[a * K + c];
+        }
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            const double *b = Bc + (int64_t)col[e] * K;
+            double u = 0.0;
+#pragma unroll
+            for (int c = 0; c < K; c++) u += y[c] * b[c];
+            val[e] += u;
+        }
+    }
+}
+
+// The same fit with G_i^+ from gram_pinv_kernel on the same pattern and Bc.
+template <int K>
+__global__ void row_fit_gp_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                  double *__restrict__ val, const int32_t *__restrict__ rowtype,
+                                  const double *__restrict__ B, const double *__restrict__ Bc,
+                                  const double *__restrict__ Gp) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (rowtype[i] != FREE_ROW) continue;
+        double r[K], y[K];
+#pragma unroll
+        for (int a = 0; a < K; a++) r[a] = B[(int64_t)i * K + a];
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            const double *b = Bc + (int64_t)col[e] * K;
+#pragma unroll
+            for (int a = 0; a < K; a++) r[a] -= val[e] * b[a];
+        }
+        const double *gp = Gp + (int64_t)i * K * K;
 #pragma unroll
         for (int c = 0; c < K; c++) {
             y[c] = 0.0;
@@ -729,26 +763,36 @@ template <typename TV>
 struct KProj {
     int k = 1;
     DVec<double> gp64;
-    DVec<int32_t> zero_row;
+    DVec<int32_t> zero_row_own;
     DVec<TV> gpv, bcv;
     const TV *gp = nullptr, *bc = nullptr;
-    void build(int k_, const Pattern &N, const int32_t *rowtype, const double *Bc, cudaStream_t s) {
+    const int32_t *zero_row = nullptr;
+    // pre_gp / pre_zr: G_i^+ and the fixed-row flags already formed on this
+    // pattern and Bc (gram_pinv_kernel), or null to form them here
+    void build(int k_, const Pattern &N, const int32_t *rowtype, const double *Bc, cudaStream_t s,
+               const double *pre_gp = nullptr, const int32_t *pre_zr = nullptr) {
         k = k_;
         if (k == 1) return;
-        gp64.alloc((size_t)N.n * k * k, s);
-        zero_row.alloc(N.n, s);
-        RN_K_SWITCH(k, RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 8.0 * k * N.nnz + 8.0 * k * k * N.n, s,
-                                 gram_pinv_kernel<KK>, grid_for(N.n, 256), 256, 0, N.n, N.rp, N.col, rowtype, Bc,
-                                 gp64.p, zero_row.p));
+        const double *g64 = pre_gp;
+        zero_row = pre_zr;
+        if (!pre_gp || !pre_zr) {
+            gp64.alloc((size_t)N.n * k * k, s);
+            zero_row_own.alloc(N.n, s);
+            RN_K_SWITCH(k, RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 8.0 * k * N.nnz + 8.0 * k * k * N.n, s,
+                                     gram_pinv_kernel<KK>, grid_for(N.n, 256), 256, 0, N.n, N.rp, N.col, rowtype,
+                                     Bc, gp64.p, zero_row_own.p));
+            g64 = gp64.p;
+            zero_row = zero_row_own.p;
+        }
         if constexpr (sizeof(TV) == 4) {
             gpv.alloc((size_t)N.n * k * k, s);
             bcv.alloc((size_t)N.nc * k, s);
-            to_float(gp64.p, gpv.p, (int64_t)N.n * k * k, s);
+            to_float(g64, gpv.p, (int64_t)N.n * k * k, s);
             to_float(Bc, bcv.p, (int64_t)N.nc * k, s);
             gp = gpv.p;
             bc = bcv.p;
         } else {
-            gp = gp64.p;
+            gp = g64;
             bc = Bc;
         }
     }
@@ -757,7 +801,7 @@ struct KProj {
         RN_K_SWITCH(k, {
             const int g = grid_resident(proj_k_kernel<TV, KK>, 256, 0, N.n, 256, kReduceBlocks);
             RN_LAUNCH("energy_masked_product", (2.0 * sizeof(TV) + 4.0 + sizeof(TV) * k) * N.nnz, s,
-                      (proj_k_kernel<TV, KK>), g, 256, 0, N.n, N.rp, N.col, zero_row.p, bc, gp, W, (TV)scale, Y, f);
+                      (proj_k_kernel<TV, KK>), g, 256, 0, N.n, N.rp, N.col, zero_row, bc, gp, W, (TV)scale, Y, f);
         });
     }
 };
@@ -1120,7 +1164,7 @@ static void energy_min_cg_t(const EmCtx &c, const CsrView &A, const Pattern &N, 
     double *rs2 = c.rs2;
     if (!rs2) { Sv.alloc(N.n, s); rs2 = Sv.p; }
     KProj<TV> kp;
-    kp.build(c.k, N, rowtype, Bc, s);
+    kp.build(c.k, N, rowtype, Bc, s, c.gp64, c.zero_row);
     if (c.k == 1) proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);  // FP64
     else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
     ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
@@ -1203,7 +1247,7 @@ static void energy_min_gmres_t(const EmCtx &c, const CsrView &A, const Pattern &
     DVec<double> Sv(c.rs2 ? 0 : N.n, s);
     double *rs2 = c.rs2 ? c.rs2 : Sv.p;
     KProj<TV> kp;
-    kp.build(c.k, N, rowtype, Bc, s);
+    kp.build(c.k, N, rowtype, Bc, s, c.gp64, c.zero_row);
     if (c.k == 1) proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);
     else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
     ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
@@ -1357,9 +1401,20 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
     else
         RN_LAUNCH("tentative", 16.0 * N.nnz + 16.0 * n, s, tentative_kernel, rows_grid(n), kT, 0, n, N.rowptr.p,
                   N.col.p, agg, Bsm, Bc, Pout.val.p, k);
+    // k > 1: every row's G_i^+ on N, formed once for the row fits and the minimisation's projection
+    DVec<double> gpN;
+    DVec<int32_t> zrN;
+    if (k > 1) {
+        gpN.alloc((size_t)n * k * k, s);
+        zrN.alloc(n, s);
+        RN_K_SWITCH(k, RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 8.0 * k * N.nnz + 8.0 * k * k * n, s,
+                                 gram_pinv_kernel<KK>, rows_grid(n), kT, 0, n, N.rowptr.p, N.col.p, rowtype, Bc,
+                                 gpN.p, zrN.p));
+    }
     if (k > h.mb)  // the other candidates: minimal-norm row fits (eq. Tproj)
-        RN_K_SWITCH(k, RN_LAUNCH("tentative", 12.0 * N.nnz + 8.0 * k * (N.nnz + n), s, row_fit_k_kernel<KK>,
-                                 rows_grid(n), kT, 0, n, Pout.rowptr.p, Pout.col.p, Pout.val.p, rowtype, Bsm, Bc));
+        RN_K_SWITCH(k, RN_LAUNCH("tentative", 12.0 * N.nnz + 8.0 * k * (N.nnz + n) + 8.0 * k * k * n, s,
+                                 row_fit_gp_kernel<KK>, rows_grid(n), kT, 0, n, Pout.rowptr.p, Pout.col.p, Pout.val.p,
+                                 rowtype, Bsm, Bc, gpN.p));
     if (Tkeep) {
         Tkeep->n = n; Tkeep->m = nc; Tkeep->nnz = N.nnz;
         Tkeep->rowptr.alloc(n + 1, s); Tkeep->col.alloc(N.nnz, s); Tkeep->val.alloc(N.nnz, s);
@@ -1370,7 +1425,12 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
     Pattern pat{n, nc, N.nnz, Pout.rowptr.p, Pout.col.p};
     DVec<double> dinv(n, s);  // the energy CG's preconditioner D^{-1}
     reciprocal(diag, dinv.p, n, s);
-    energy_min(ctx_of(h), A, pat, Pout.val.p, rowtype, Bc, dinv.p, h.p.n_sweeps);
+    {
+        EmCtx c = ctx_of(h);
+        c.gp64 = gpN.p;  // the same pattern and Bc
+        c.zero_row = zrN.p;
+        energy_min(c, A, pat, Pout.val.p, rowtype, Bc, dinv.p, h.p.n_sweeps);
+    }
     if (h.p.postfilter > 0.0) {
         const double omg = 1.0 - kGuard;
         DVec<int32_t> cnt(n + 1, s);
