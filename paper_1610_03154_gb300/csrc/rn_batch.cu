@@ -618,6 +618,7 @@ rn_batch *batch_merge(int count, rn_hierarchy *const *hs, cudaStream_t s) {
 }
 
 void batch_cycle(rn_batch &b, const double *const *rhs, double *const *out) {
+    relist(b, true);  // every tile (a failed call may have left lists short)
     gather(b, rhs, b.bm.p);
     apply_cycle(*b.M, b.bm.p, b.xm.p);
     scatter(b, b.xm.p, out);
@@ -633,6 +634,7 @@ rn_status batch_solve(rn_batch &b, const double *const *rhs, double *const *x, d
     const double t0 = now_ms();
     b.rtol = rtol;
     b.maxit = maxit;
+    relist(b, true);  // every tile (a failed call may have left lists short)
     gather(b, rhs, b.bm.p);
     gather(b, x, b.xm.p);
     launch_dot(b, BM_NB, b.bm.p, b.bm.p);
