@@ -184,15 +184,17 @@ rn_status run_batch(int count, int threads, F &&work) {
     int nt = threads > 0 ? threads : (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
     nt = std::max(1, std::min(nt, count));
     std::atomic<int> next{0};
-    auto body = [&]() {
+    auto body = [&](int t) {
+        rn::set_thread_pool(nt > 1 ? t : -1);
         for (int i = next++; i < count; i = next++) {
             st[i] = work(i);
             if (st[i] != RN_OK) msg[i] = rn_last_error();
         }
+        rn::set_thread_pool(-1);
     };
     std::vector<std::thread> pool;
-    for (int t = 1; t < nt; t++) pool.emplace_back(body);
-    body();
+    for (int t = 1; t < nt; t++) pool.emplace_back(body, t);
+    body(0);
     for (auto &t : pool) t.join();
     for (int i = 0; i < count; i++)
         if (st[i] != RN_OK) {

@@ -47,6 +47,7 @@ struct Allocator {
 // The allocator new buffers take on this thread; the API entry points set it
 // for the duration of a call (AllocScope) from the call's parameters.
 Allocator &current_allocator();
+void set_thread_pool(int slot);  // worker threads of batched calls: a device pool per worker (-1: default)
 struct AllocScope {
     Allocator saved;
     explicit AllocScope(const Allocator &a) : saved(current_allocator()) { current_allocator() = a; }

@@ -6,6 +6,7 @@
 #include <map>
 #include <tuple>
 #include <mutex>
+#include <vector>
 
 #include "rn_internal.cuh"
 
@@ -64,6 +65,30 @@ Allocator &current_allocator() {
     return a;
 }
 
+// Host threads driving independent setups allocate from pools of their own
+// (slot = worker index), so they do not contend on the default pool.
+static thread_local int t_pool_slot = -1;
+void set_thread_pool(int slot) { t_pool_slot = slot; }
+static cudaMemPool_t thread_pool() {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    while ((int)pools.size() <= t_pool_slot) {
+        int dev = 0;
+        RN_CUDA_CHECK(cudaGetDevice(&dev));
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t mp;
+        RN_CUDA_CHECK(cudaMemPoolCreate(&mp, &props));
+        uint64_t thr = UINT64_MAX;
+        RN_CUDA_CHECK(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr));
+        pools.push_back(mp);
+    }
+    return pools[t_pool_slot];
+}
+
 void *dmalloc(size_t bytes, cudaStream_t s, const Allocator &a, size_t *got) {
     // every buffer gets >= 256 bytes of tail slack: the tile kernels copy CSR
     // segments with 16-byte-granular bulk copies that may end up to 15 bytes
@@ -92,7 +117,7 @@ void *dmalloc(size_t bytes, cudaStream_t s, const Allocator &a, size_t *got) {
     }();
     (void)pool_configured;
     void *p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    cudaError_t e = t_pool_slot >= 0 ? cudaMallocFromPoolAsync(&p, bytes, thread_pool(), s) : cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(e == cudaErrorMemoryAllocation ? RN_ENOMEM : RN_ECUDA,
