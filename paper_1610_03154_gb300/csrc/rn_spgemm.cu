@@ -505,8 +505,17 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
         else launch_small<16>(nsmall, flags.p + 5, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
     }
     if (nlarge) {
-        launch_hash<32, 1024>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
-                              flags.p + 3, bytes, s);
+        // short B rows (an interpolation operator): rows of the product have few
+        // distinct columns, so half-size tables double the resident groups per
+        // SM; sums per column run in ascending k either way (same result), and
+        // rows past a table go to the block kernel
+        const double avgB = B.n ? (double)B.nnz / B.n : 0.0;
+        if (avgB <= 16.0)
+            launch_hash<32, 512>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
+                                 flags.p + 3, bytes, s);
+        else
+            launch_hash<32, 1024>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
+                                  flags.p + 3, bytes, s);
         // rows past the tables (counted on the device): a block per row, looping
         const size_t smem = (size_t)kBigProd * (sizeof(double) + 2 * sizeof(int32_t));
         static const bool configured = [&] {
