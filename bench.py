@@ -236,6 +236,32 @@ def profile_step(args):
     return 0
 
 
+def profile_setup_op(args):
+    """Build the workload's hierarchy (keep_aux), then run one level-0 setup
+    operation (rn_time_setup_op, one run, no flush) between cudaProfilerStart
+    and cudaProfilerStop, so that `ncu --profile-from-start off` captures that
+    operation's launches and nothing else."""
+    import torch
+
+    from paper_1610_03154_gb300 import rn
+
+    dev = torch.device("cuda", 0)
+    pr = PR.aniso_problem(args.ne)
+    A = pr.A
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    p = rn.params_from_config(pr.params, precision=rn.RN_MIXED if args.precision == "mixed" else rn.RN_FP64,
+                              outer=rn.RN_OUTER_CG, keep_aux=1)
+    h = rn.Hierarchy(t(A.rowptr), t(A.col), t(A.val), t(pr.B.reshape(-1)), params=p)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    name, us, by = h.time_setup_op(args.profile_setup_op, reps=1, flush_bytes=0)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    h.close()
+    print(json.dumps({"profile_setup_op": name, "us": us, "bytes": by}))
+    return 0
+
+
 def next_rows(rn, torch, dev, stream, flush, prec):
     """Records for the batched and differentiable forms, each one warm-up
     and one timed pass with device-resident inputs (CUDA events, L2 flushed):
@@ -393,11 +419,15 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="one setup + --profile-iters outer iterations and nothing else (for ncu captures)")
     ap.add_argument("--profile-iters", type=int, default=10)
+    ap.add_argument("--profile-setup-op", type=int, default=-1,
+                    help="run one level-0 setup operation (rn_time_setup_op index) inside a profiler range")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     if args.profile_step:
         return profile_step(args)
+    if args.profile_setup_op >= 0:
+        return profile_setup_op(args)
 
     import torch
 
@@ -523,8 +553,36 @@ def main():
         if r is not None:
             ops[r[0]] = {"us": r[1], "bytes": r[2]}
     h.close()
-    iters = infos[0]["iters"]
+    # the setup's level-0 operations, each timed alone the same way
+    # (rn_time_setup_op): one energy-minimisation CG sweep and its three
+    # launches, the Galerkin products A P and R (A P), and P^T
     peak, peak_kind = load_peaks()
+    ha = rn.Hierarchy(rp, ci, va, Bd, params=params(prec, keep_aux=1), stream=sptr)
+    sops = {}
+    for op in range(rn.RN_SOP_COUNT):
+        nm, us, by = ha.time_setup_op(op, reps=10)
+        sops[nm] = {"us": round(us, 2), "bytes": by, "GBps": round(by / (us * 1e-6) / 1e9, 1),
+                    "frac": round(by / (us * 1e-6) / 1e9 / peak, 4)}
+    n_sweeps_l0 = pr.params.get("n_sweeps", 4) + (1 if pr.params.get("postfilter", 0.0) > 0 else 0)
+    ha.close()
+
+    def setup_record(key, rule):
+        v = sops[key]
+        ach = v["bytes"] / (v["us"] * 1e-6) / 1e9
+        return {"bound": "hbm", "kernel": key, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_kind": peak_kind, "avg_launch_us": v["us"], "algorithmic_bytes": v["bytes"], "rule": rule}
+
+    energy_rec = setup_record("energy_sweep_L0", "one level-0 CG energy-minimisation sweep (direction, masked "
+                              "product with <D,W>, update with rho) in the setup's precision, timed alone with CUDA "
+                              "events after a 256 MB L2 read flush; bytes = 12 nnzA + 4 nnzN + 64 nnzN + 8 n + 8 n_c "
+                              "(FP64) or 8 nnzA + 4 nnzN + 32 nnzN + 4 n + 4 n_c (FP32 sweeps)")
+    energy_rec["sweeps_per_setup_level0"] = n_sweeps_l0
+    energy_rec["launches"] = {k: sops[k] for k in ("energy_direction_L0", "energy_product_L0", "energy_update_L0")}
+    rap_rec = setup_record("galerkin_RAP_L0", "R_0 (A_0 P_0) as the setup forms it (symbolic and numeric passes with "
+                           "their host synchronisations), timed alone after a 256 MB L2 read flush; bytes = "
+                           "12 (nnzR + nnzAP) + 12 nnzA1")
+    rap_rec["launches"] = {k: sops[k] for k in ("galerkin_AP_L0", "transpose_P_L0")}
+    iters = infos[0]["iters"]
     bw = {k: v for k, v in ops.items() if v["bytes"] > 0}
     name = max(bw, key=lambda k: bw[k]["us"])
     st = bw[name]
@@ -590,7 +648,8 @@ def main():
             "config": {"workload": pr.description, "precision": prec, "outer": "flexible CG" if prec == "mixed"
                        else "CG", "cycle": "V(1,1) weighted Jacobi omega=2/3, dense coarsest solve",
                        "setup": "theta=0.25 symmetric strength, seeded MIS-2 aggregation, d=4, 6 CG energy-min "
-                                "sweeps, pre/post filter 0.1", "l2": "flushed between steps (256 MB write)",
+                                "sweeps, pre/post filter 0.1", "l2": "256 MB torch fill (write) before every timed step; per-launch timings after a 256 MB read",
+                       "setup_roofline": "energy_min and rap records",
                        "parallelism": f"replicas x{ws}"},
             "iters": infos[0]["iters"], "rel_res": infos[0]["rel_res"], "rel_res_host_check": res_check,
             "step_s_all": times,
@@ -612,6 +671,8 @@ def main():
                              "precision": prec},
             "roofline": roofline,
             "level0_launches": kernels,
+            "energy_min": energy_rec,
+            "rap": rap_rec,
             "gpu_launches": launches // max(args.steps, 1),
             "gpu_launches_timed_region": launches,
             "clocks": clk.summary(),

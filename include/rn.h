@@ -35,7 +35,8 @@
  *     stream.  rn_setup and rn_solve
  *     return after their last host read-back; outputs are complete when they
  *     return.
- *   - k (the number of candidates) must be 1.
+ *   - k (the number of candidates) is 1 <= k <= 4 (rn_setup); the batched
+ *     and many-right-hand-side calls state their own limits.
  *   - One hierarchy must not be used by two threads at once.
  */
 #ifndef RN_H
@@ -267,7 +268,9 @@ rn_status rn_energy_min(const rn_csr *A, const rn_csr *N, const int32_t *rowtype
  *   (cudaGetSymbolAddress); make that first call before any stream capture.
  *   stream NULL means the legacy default stream.
  *   All calls share the array: calls whose GPU work overlaps (other streams,
- *   other threads) race on it and must be serialised by the caller. */
+ *   other threads) race on it and must be serialised by the caller.
+ *   The call reads one flag back to the host and synchronises its stream
+ *   before it returns.  rn_allocation_count() is unchanged across the call. */
 rn_status rn_energy_min_noalloc(const rn_csr *A, const rn_csr *N, const int32_t *rowtype, const double *Bc,
                                 double *P, int sweeps, int precond, void *stream);
 
@@ -306,6 +309,12 @@ rn_status rn_profile_read(rn_kernel_stat *out, int max, int *count);
 /* Number of library kernels launched by this process so far (kernels inside
  * a replayed CUDA graph are counted one by one). */
 int64_t rn_kernel_launches(void);
+
+/* Number of memory allocations the library has made in this process so far:
+ * device buffers (from the caller's hooks or the stream-ordered allocator)
+ * and page-locked host scratch.  No counterpart in the paper; it lets a caller
+ * check that a call made no allocation (rn_energy_min_noalloc). */
+int64_t rn_allocation_count(void);
 
 /* Differentiation through a solve (x = A^{-1} b): given lambda = A^{-T} dL/dx,
  * the gradient with respect to A's stored values is dL/dA_ij = -lambda_i x_j.
@@ -347,6 +356,35 @@ enum {
     RN_OP_COUNT = 9
 };
 rn_status rn_time_op(rn_hierarchy *h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, char *name);
+
+/* Measurement hook for the setup (no counterpart in the paper): time one
+ * level-0 operation of Alg. 3 in isolation, with the flush, events and
+ * outputs of rn_time_op.  The energy-minimisation operations run on level 0's
+ * minimisation pattern N (after the pre-filter) from its tentative T, in the
+ * hierarchy's setup precision (FP32 sweeps when precision is RN_MIXED); every
+ * run starts from the CG state after the first sweep, restored before it
+ * outside the timed region, so it times a general sweep.  They need a
+ * hierarchy built with keep_aux and energy_method RN_ENERGY_CG.  The Galerkin
+ * operations form A_0 P_0 and R_0 (A_0 P_0) as the setup does (symbolic and
+ * numeric passes, with the products' host synchronisations), and the
+ * transpose forms P_0^T.  Algorithmic bytes: the sweep 12 nnz(A) + 4 nnz(N)
+ * + 64 nnz(N) + 8 n + 8 k n_c in FP64 (8, 4, 32, 4 and 4 k in place of 12,
+ * 4, 64, 8 and 8 k for FP32 sweeps); A P: 12 (nnz(A) + nnz(P)) + 12 nnz(AP);
+ * R (A P): 12 (nnz(R) + nnz(AP)) + 12 nnz(A_1); P^T: 24 nnz(P).  Returns
+ * RN_EINVAL for an unknown operation, a one-level hierarchy or a hierarchy
+ * without what the operation needs. */
+enum {
+    RN_SOP_ENERGY_SWEEP = 0,     /* one CG sweep: direction, masked product with <D, W>, update with rho */
+    RN_SOP_ENERGY_DIRECTION = 1, /* D = D^{-1} R + beta D */
+    RN_SOP_ENERGY_PRODUCT = 2,   /* W = Proj(Mask_N(A D)) with <D, W> and alpha */
+    RN_SOP_ENERGY_UPDATE = 3,    /* P += alpha D, R -= alpha W, rho and beta */
+    RN_SOP_GALERKIN_AP = 4,      /* A_0 P_0 */
+    RN_SOP_GALERKIN_RAP = 5,     /* R_0 (A_0 P_0) = A_1 */
+    RN_SOP_TRANSPOSE = 6,        /* P_0^T */
+    RN_SOP_COUNT = 7
+};
+rn_status rn_time_setup_op(rn_hierarchy *h, int op, int reps, int64_t flush_bytes, double *us, double *bytes,
+                           char *name);
 
 const char *rn_last_error(void);
 const char *rn_status_string(rn_status s);

@@ -395,6 +395,21 @@ extern "C" rn_status rn_time_op(rn_hierarchy *h, int op, int reps, int64_t flush
     RN_API_END
 }
 
+extern "C" rn_status rn_time_setup_op(rn_hierarchy *h, int op, int reps, int64_t flush_bytes, double *us,
+                                      double *bytes, char *name) {
+    RN_API_BEGIN
+    if (!h || !us || !bytes) rn::fail(RN_EINVAL, "null argument");
+    const rn::AllocScope alloc_scope(alloc_of(h->p));
+    std::string nm;
+    rn::time_setup_op(*h, op, reps, flush_bytes, us, bytes, nm);
+    if (name) {
+        std::strncpy(name, nm.c_str(), 47);
+        name[47] = '\0';
+    }
+    return RN_OK;
+    RN_API_END
+}
+
 namespace {
 // A stream the call owns when the caller passes none (blocking, so it stays
 // ordered with the legacy default stream).

@@ -4,6 +4,7 @@
 // diagonal, and the level vectors; the coarsest level keeps a dense FP64
 // inverse formed from its partially pivoted LU factors.
 #pragma once
+#include <functional>
 #include <memory>
 
 #include "rn_internal.cuh"
@@ -146,6 +147,10 @@ struct EmCtx {
     int k = 1;              // candidates (Bc is nc x k); k > 1 projects with per-row Gram pseudo-inverses
     const double *gp64 = nullptr;     // k > 1: G_i^+ already formed on N and Bc (else formed inside)
     const int32_t *zero_row = nullptr;
+    // true: every product scans the pattern rows (energy_product_kernel) and
+    // no gather map is built; with R, Dd, W, rs2 supplied, k = 1 and FP64
+    // sweeps the minimisation then allocates nothing (same results)
+    bool scan_only = false;
 };
 // dinv: the inverted diagonal of A (CG's preconditioner D^{-1} when c.precond)
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
@@ -159,6 +164,14 @@ void outer_spmv(rn_hierarchy &h, const double *x, double *y);          // y = A_
 void outer_residual(rn_hierarchy &h, const double *x, const double *b, double *r);  // r = b - A_0 x
 void cycle_checked(rn_hierarchy &h, const double *rhs, double *out);  // + staging-error check
 void time_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, std::string &name);
+// Mean device time (us) of `timed`, run reps times on stream s, each run
+// preceded by `before` (untimed; may be empty) and a read of flush_bytes
+// that leaves L2 cold and keeps the GPU busy while the work is enqueued.
+double time_launches(cudaStream_t s, int reps, int64_t flush_bytes, const std::function<void()> &before,
+                     const std::function<void()> &timed);
+// One setup operation of level 0 timed the same way (rn_time_setup_op).
+void time_setup_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes,
+                   std::string &name);
 // many right-hand sides (rn_multi.cu)
 rn_status solve_multi(rn_hierarchy &h, const double *B, double *X, int ns, double rtol, int maxit,
                       rn_solve_info *info);

@@ -58,6 +58,7 @@ struct AllocScope {
 // bytes is rounded up (with tail slack) inside; *got receives the size asked of the allocator
 void *dmalloc(size_t bytes, cudaStream_t s, const Allocator &a, size_t *got);
 void dfree(void *p, size_t got, cudaStream_t s, const Allocator &a);
+int64_t allocation_count();  // allocations made so far (dmalloc and page-locked scratch)
 
 // A device buffer; it is freed by the allocator it came from, whatever the
 // thread's allocator is at that time.

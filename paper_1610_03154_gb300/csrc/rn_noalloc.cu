@@ -13,7 +13,8 @@
 // The array below is created when the library is loaded and every GPU that
 // loads the library keeps it until the process exits.  All calls share it:
 // calls whose GPU work overlaps (on different streams, or from different
-// threads) race on it and must be serialised by the caller.
+// threads) race on it and must be serialised by the caller.  The call reads
+// one flag back to the host and synchronises its stream before it returns.
 #include <mutex>
 
 #include "rn_hier.cuh"
@@ -25,7 +26,14 @@ namespace {
 constexpr int64_t kNaMaxRows = 1 << 18;      // rows of A
 constexpr int64_t kNaMaxPattern = 1 << 19;   // entries of the pattern N
 
-// Layout (bytes, each region 256-byte aligned).
+// Layout (bytes, each region 256-byte aligned): the inverted diagonal D^{-1}
+// (one double per row), CG's residual R, direction Dd and product W (one
+// double per pattern entry each), the row projection's scales (one double per
+// row), the reduction partials (two per reducing block), the CG scalars, the
+// reduction's arrival counters and the flags.  This is the only device memory
+// the call uses besides the caller's buffers: the minimisation runs with FP64
+// sweeps, k = 1 and products that scan the pattern rows (no gather map), a
+// path that allocates nothing once these workspaces are supplied.
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kOffDiag = 0;
@@ -93,7 +101,12 @@ extern "C" rn_status rn_energy_min_noalloc(const rn_csr *A, const rn_csr *N, con
         const int32_t n = A->n_rows;
         CsrView Av{n, n, A->nnz, A->rowptr, A->col, A->val};
         extract_diag(Av, diag, fl + 4, s);
-        if (read_scalar(fl + 4, s)) fail(RN_EINVAL, "missing or zero diagonal");
+        // the flag is read into this stack variable (pageable: the library's
+        // page-locked read slots may not exist yet on this thread)
+        int32_t bad = 0;
+        RN_CUDA_CHECK(cudaMemcpyAsync(&bad, fl + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        RN_CUDA_CHECK(cudaStreamSynchronize(s));
+        if (bad) fail(RN_EINVAL, "missing or zero diagonal");
         EmCtx c;
         c.s = s;
         c.partial = reinterpret_cast<double *>(base + kOffPartial);
@@ -106,6 +119,7 @@ extern "C" rn_status rn_energy_min_noalloc(const rn_csr *A, const rn_csr *N, con
         c.Dd = reinterpret_cast<double *>(base + kOffD);
         c.W = reinterpret_cast<double *>(base + kOffW);
         c.rs2 = reinterpret_cast<double *>(base + kOffS2);
+        c.scan_only = true;  // no gather map: the products scan the pattern rows
         Pattern pat{n, N->n_cols, N->nnz, N->rowptr, N->col};
         reciprocal(diag, diag, n, s);  // the preconditioner D^{-1}, in place
         energy_min(c, Av, pat, P, rowtype, Bc, diag, sweeps);

@@ -36,6 +36,12 @@ double now_ms() {
 
 // --------------------------------------------------------------------- memory
 
+// Allocations the library has made in this process (device buffers through
+// dmalloc, page-locked host scratch through pinned_scratch); read by
+// rn_allocation_count.
+static std::atomic<int64_t> g_allocations{0};
+int64_t allocation_count() { return g_allocations.load(); }
+
 // Pinned scratch: slots of one page-locked pool (allocated once, kept for the
 // process), one per thread; threads past the pool's slots get their own.
 void *pinned_scratch() {
@@ -47,6 +53,7 @@ void *pinned_scratch() {
     if (mine) return mine;
     std::call_once(once, [] {
         void *p = nullptr;
+        g_allocations++;
         if (cudaMallocHost(&p, kSlots * kPinnedBytes) == cudaSuccess) pool = static_cast<unsigned char *>(p);
     });
     const int k = next++;
@@ -54,6 +61,7 @@ void *pinned_scratch() {
         mine = pool + (size_t)k * kPinnedBytes;
     } else {
         void *p = nullptr;  // kept for the thread's life (and the process's: a few bytes)
+        g_allocations++;
         RN_CUDA_CHECK(cudaMallocHost(&p, kPinnedBytes));
         mine = p;
     }
@@ -95,6 +103,7 @@ void *dmalloc(size_t bytes, cudaStream_t s, const Allocator &a, size_t *got) {
     // past the last element (the slack is never interpreted)
     bytes = ((bytes + 255) / 256) * 256 + 256;
     *got = bytes;
+    g_allocations++;
     if (a.alloc) {
         void *p = a.alloc(bytes, (void *)s, a.ctx);
         if (!p) fail(RN_ENOMEM, fmt("the caller's allocator returned NULL for %zu bytes", bytes));
@@ -249,6 +258,7 @@ ProfScope::~ProfScope() noexcept(false) {
 }  // namespace rn
 
 extern "C" int64_t rn_kernel_launches(void) { return rn::launches_so_far(); }
+extern "C" int64_t rn_allocation_count(void) { return rn::allocation_count(); }
 
 extern "C" rn_status rn_profile_enable(int on) {
     rn::g_prof_on = (on != 0);

@@ -1131,69 +1131,83 @@ static int pick_g(double avg) {
 // CG energy minimisation of the values X (in/out, FP64) on pattern N, with
 // sweeps in TV: double, or float for the mixed-precision setup (A, X and the
 // CG vectors in FP32; the row projection and the scalar recurrences FP64).
+// The steps are kept apart (start, direction, product, update, finish) so
+// that the setup and the measurement hook (time_setup_op) run the same
+// launches.
 template <typename TV>
-static void energy_min_cg_t(const EmCtx &c, const CsrView &A, const Pattern &N, double *X64,
-                            const int32_t *rowtype, const double *Bc, const double *c_dinv, int sweeps) {
-    cudaStream_t s = c.s;
-    constexpr bool f32 = sizeof(TV) == 4;
-    DVec<TV> Rv, Dv, Wv, Xv, Av, Iv;
-    TV *R, *Dd, *W, *X;
-    const TV *aval, *dinv_t;
-    if constexpr (f32) {
-        Rv.alloc(N.nnz, s); Dv.alloc(N.nnz, s); Wv.alloc(N.nnz, s); Xv.alloc(N.nnz, s);
-        Av.alloc(A.nnz, s); Iv.alloc(N.n, s);
-        R = Rv.p; Dd = Dv.p; W = Wv.p; X = Xv.p;
-        to_float(X64, X, N.nnz, s);
-        to_float(A.val, Av.p, A.nnz, s);
-        to_float(c_dinv, Iv.p, N.n, s);
-        aval = Av.p;
-        dinv_t = Iv.p;
-    } else {
-        R = c.R; Dd = c.Dd; W = c.W; X = X64;
-        if (!R) { Rv.alloc(N.nnz, s); R = Rv.p; }
-        if (!Dd) { Dv.alloc(N.nnz, s); Dd = Dv.p; }
-        if (!W) { Wv.alloc(N.nnz, s); W = Wv.p; }
-        aval = A.val;
-        dinv_t = c_dinv;
-    }
-    const int precond = c.precond;
-    double *sc = c.sc;
-    int32_t *fl = c.fl;
-    fill_i32(fl, 0, 1, s);
+struct CgSweep {
+    static constexpr bool f32 = sizeof(TV) == 4;
+    const EmCtx &c;
+    const CsrView &A;
+    const Pattern &N;
+    const int32_t *rowtype;
+    const double *Bc;
+    cudaStream_t s;
+    DVec<TV> Rv, Dv, Wv, Xv, Av, Iv, Bcv, Rsv;
     DVec<double> Sv;
-    double *rs2 = c.rs2;
-    if (!rs2) { Sv.alloc(N.n, s); rs2 = Sv.p; }
+    TV *R = nullptr, *Dd = nullptr, *W = nullptr, *X = nullptr;
+    const TV *aval = nullptr, *dinv_t = nullptr, *dinv = nullptr;
+    double *rs2 = nullptr;
     KProj<TV> kp;
-    kp.build(c.k, N, rowtype, Bc, s, c.gp64, c.zero_row);
-    if (c.k == 1) proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);  // FP64
-    else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
-    ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
-    DVec<TV> Bcv, Rsv;
-    if constexpr (f32) {
-        Bcv.alloc((size_t)N.nc * c.k, s);
-        Rsv.alloc(N.n, s);
-        to_float(Bc, Bcv.p, (int64_t)N.nc * c.k, s);
-        to_float(rs2, Rsv.p, N.n, s);
-        pa.Bc = Bcv.p;
-        pa.rs2 = Rsv.p;
-    } else {
-        pa.Bc = Bc;
-        pa.rs2 = rs2;
-    }
-    const int G = pick_g(N.n ? (double)N.nnz / N.n : 1.0);
-    const double nzb = (double)sizeof(TV) * N.nnz, rpb = 4.0 * (N.n + 1), db = (double)sizeof(TV) * N.n;
-    Fin fin;
-    fin.partial = c.partial;
-    fin.counter = c.counter;
-    fin.sc = sc;
-    fin.fl = fl;
-    fin.stop = kCgStop;
-    const Fin none;
-    // the pattern is fixed for all sweeps: gather map built once (falls back
-    // to the scanning product for rows of N too long for the map)
+    ProjArgsT<TV> pa{};
     EpMap em;
-    ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
-    auto product = [&](const TV *Xin, TV *Wout, double scale, const TV *Y, const Fin &f) {
+    Fin fin;
+    int G = 4;
+    double nzb = 0, rpb = 0, db = 0;
+
+    CgSweep(const EmCtx &c_, const CsrView &A_, const Pattern &N_, double *X64, const int32_t *rowtype_,
+            const double *Bc_, const double *c_dinv)
+        : c(c_), A(A_), N(N_), rowtype(rowtype_), Bc(Bc_), s(c_.s) {
+        if constexpr (f32) {
+            Rv.alloc(N.nnz, s); Dv.alloc(N.nnz, s); Wv.alloc(N.nnz, s); Xv.alloc(N.nnz, s);
+            Av.alloc(A.nnz, s); Iv.alloc(N.n, s);
+            R = Rv.p; Dd = Dv.p; W = Wv.p; X = Xv.p;
+            to_float(X64, X, N.nnz, s);
+            to_float(A.val, Av.p, A.nnz, s);
+            to_float(c_dinv, Iv.p, N.n, s);
+            aval = Av.p;
+            dinv_t = Iv.p;
+        } else {
+            R = c.R; Dd = c.Dd; W = c.W; X = X64;
+            if (!R) { Rv.alloc(N.nnz, s); R = Rv.p; }
+            if (!Dd) { Dv.alloc(N.nnz, s); Dd = Dv.p; }
+            if (!W) { Wv.alloc(N.nnz, s); W = Wv.p; }
+            aval = A.val;
+            dinv_t = c_dinv;
+        }
+        fill_i32(c.fl, 0, 1, s);
+        rs2 = c.rs2;
+        if (!rs2) { Sv.alloc(N.n, s); rs2 = Sv.p; }
+        kp.build(c.k, N, rowtype, Bc, s, c.gp64, c.zero_row);
+        if (c.k == 1) proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);  // FP64
+        else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
+        pa.rowtype = rowtype;
+        if constexpr (f32) {
+            Bcv.alloc((size_t)N.nc * c.k, s);
+            Rsv.alloc(N.n, s);
+            to_float(Bc, Bcv.p, (int64_t)N.nc * c.k, s);
+            to_float(rs2, Rsv.p, N.n, s);
+            pa.Bc = Bcv.p;
+            pa.rs2 = Rsv.p;
+        } else {
+            pa.Bc = Bc;
+            pa.rs2 = rs2;
+        }
+        G = pick_g(N.n ? (double)N.nnz / N.n : 1.0);
+        nzb = (double)sizeof(TV) * N.nnz;
+        rpb = 4.0 * (N.n + 1);
+        db = (double)sizeof(TV) * N.n;
+        fin.partial = c.partial;
+        fin.counter = c.counter;
+        fin.sc = c.sc;
+        fin.fl = c.fl;
+        fin.stop = kCgStop;
+        dinv = c.precond ? dinv_t : nullptr;
+        // the pattern is fixed for all sweeps: gather map built once (falls
+        // back to the scanning product for rows of N too long for the map)
+        if (!c.scan_only) ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
+    }
+    void product(const TV *Xin, TV *Wout, double scale, const TV *Y, const Fin &f) {
         const bool k1 = c.k == 1;
         const Fin none0;
         if (em.ok)
@@ -1203,23 +1217,57 @@ static void energy_min_cg_t(const EmCtx &c, const CsrView &A, const Pattern &N, 
             masked_product_proj<TV>(A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, k1 ? scale : 1.0,
                                     k1 ? Y : nullptr, k1 ? f : none0, s);
         if (!k1) kp.apply(N, rowtype, Wout, scale, Y, f, s);
-    };
-    product(X, R, -1.0, nullptr, none);
-    fin.mode = FIN_CG_RHO;
-    fin.it = 0;
-    const TV *dinv = precond ? dinv_t : nullptr;
-    RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R, dinv, fin);
-    for (int it = 0; it < sweeps; it++) {
-        RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R, dinv, sc, fl,
-                       it == 0 ? 1 : 0, Dd);
+    }
+    // R = -Proj(Mask_N(A X)) and rho = <R, D^{-1} R>
+    void start() {
+        const Fin none;
+        product(X, R, -1.0, nullptr, none);
+        fin.mode = FIN_CG_RHO;
+        fin.it = 0;
+        RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R, dinv, fin);
+    }
+    // Dd = D^{-1} R (+ beta Dd after the first sweep)
+    void direction(int it) {
+        RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R, dinv, c.sc,
+                       c.fl, it == 0 ? 1 : 0, Dd);
+    }
+    // W = Proj(Mask_N(A Dd)), <Dd, W> and alpha
+    void sweep_product() {
         fin.mode = FIN_CG_DW;
         product(Dd, W, 1.0, Dd, fin);
+    }
+    // X += alpha Dd, R -= alpha W, rho and beta
+    void update(int it) {
         fin.mode = FIN_CG_RHO;
         fin.it = it + 1;
-        RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R, Dd, W, dinv,
-                       sc, fl, fin);
+        RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R, Dd, W,
+                       dinv, c.sc, c.fl, fin);
     }
-    if constexpr (f32) to_double(X, X64, N.nnz, s);
+    void sweep(int it) {
+        direction(it);
+        sweep_product();
+        update(it);
+    }
+    void finish(double *X64) {
+        if constexpr (f32) to_double(X, X64, N.nnz, s);
+        else (void)X64;
+    }
+    // algorithmic bytes of one sweep: A once, the pattern once, eight passes
+    // over the pattern's values (Dd read for the product and written by the
+    // direction, W written and read, X and R read and written), D^{-1} and Bc
+    double sweep_bytes() const {
+        const double vb = sizeof(TV);
+        return (4.0 + vb) * A.nnz + 4.0 * N.nnz + 8.0 * vb * N.nnz + vb * N.n + vb * c.k * N.nc;
+    }
+};
+
+template <typename TV>
+static void energy_min_cg_t(const EmCtx &c, const CsrView &A, const Pattern &N, double *X64,
+                            const int32_t *rowtype, const double *Bc, const double *c_dinv, int sweeps) {
+    CgSweep<TV> cg(c, A, N, X64, rowtype, Bc, c_dinv);
+    cg.start();
+    for (int it = 0; it < sweeps; it++) cg.sweep(it);
+    cg.finish(X64);
 }
 
 void energy_min_cg(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
@@ -1710,6 +1758,119 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             Lp->agg.release();
             Lp->roots.release();
         }
+    }
+}
+
+// ================================================================== measurement hook
+// Level 0's energy minimisation, one piece at a time: the state every timed
+// run starts from is the one after the first sweep (restored before each
+// run, outside the timed region), so every run times a general sweep (beta
+// term included) on the minimisation's own pattern N, values and precision.
+template <typename TV>
+static void time_energy(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes,
+                        std::string &name) {
+    cudaStream_t s = h.s;
+    rn_level &L = *h.lev[0];
+    const CsrView A = view(L.A);
+    const int32_t n = A.n;
+    const size_t nz = (size_t)L.N.nnz;
+    Pattern pat{n, L.N.m, L.N.nnz, L.N.rowptr.p, L.N.col.p};
+    DVec<double> x0(nz, s), dinv(n, s);
+    d2d(x0.p, L.T.val.p, nz, s);
+    reciprocal(L.diag.p, dinv.p, n, s);
+    EmCtx c = ctx_of(h);
+    CgSweep<TV> cg(c, A, pat, x0.p, L.rowtype.p, L.Bc.p, dinv.p);
+    cg.start();
+    cg.sweep(0);
+    DVec<TV> sX(nz, s), sR(nz, s), sD(nz, s);
+    DVec<double> ssc(8, s);
+    d2d(sX.p, cg.X, nz, s);
+    d2d(sR.p, cg.R, nz, s);
+    d2d(sD.p, cg.Dd, nz, s);
+    d2d(ssc.p, c.sc, 8, s);
+    auto restore = [&]() {
+        d2d(cg.X, sX.p, nz, s);
+        d2d(cg.R, sR.p, nz, s);
+        d2d(cg.Dd, sD.p, nz, s);
+        d2d(c.sc, ssc.p, 8, s);
+        fill_i32(c.fl, 0, 1, s);
+    };
+    const double vb = sizeof(TV);
+    std::function<void()> before, timed;
+    switch (op) {
+        case RN_SOP_ENERGY_SWEEP:
+            name = "energy_sweep_L0";
+            before = restore;
+            timed = [&]() { cg.sweep(1); };
+            *bytes = cg.sweep_bytes();
+            break;
+        case RN_SOP_ENERGY_DIRECTION:
+            name = "energy_direction_L0";
+            before = restore;
+            timed = [&]() { cg.direction(1); };
+            *bytes = cg.rpb + 3.0 * cg.nzb + cg.db;
+            break;
+        case RN_SOP_ENERGY_PRODUCT:
+            name = "energy_product_L0";
+            before = [&]() { restore(); cg.direction(1); };
+            timed = [&]() { cg.sweep_product(); };
+            // A, both row-pointer arrays, row types, row scales, the pattern's
+            // columns, X gathered once, W written, Y read, Bc (no gather map)
+            *bytes = (4.0 + vb) * A.nnz + 8.0 * (n + 1) + 4.0 * n + vb * n + 4.0 * nz + 3.0 * vb * nz +
+                     vb * h.k * L.N.m;
+            break;
+        case RN_SOP_ENERGY_UPDATE:
+            name = "energy_update_L0";
+            before = [&]() { restore(); cg.direction(1); cg.sweep_product(); };
+            timed = [&]() { cg.update(1); };
+            *bytes = cg.rpb + 6.0 * cg.nzb + cg.db;
+            break;
+        default: fail(RN_EINVAL, "unknown setup operation");
+    }
+    *us = time_launches(s, reps, flush_bytes, before, timed);
+}
+
+void time_setup_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes,
+                   std::string &name) {
+    if (op < 0 || op >= RN_SOP_COUNT) fail(RN_EINVAL, "unknown setup operation");
+    if (h.lev.size() < 2) fail(RN_EINVAL, "a one-level hierarchy has no setup operation to time");
+    cudaStream_t s = h.s;
+    rn_level &L = *h.lev[0];
+    const CsrView A = view(L.A);
+    if (op <= RN_SOP_ENERGY_UPDATE) {
+        if (!h.p.keep_aux || !L.N.rowptr.p || !L.T.val.p)
+            fail(RN_EINVAL, "timing the energy minimisation needs a hierarchy built with keep_aux");
+        if (h.p.energy_method != RN_ENERGY_CG) fail(RN_EINVAL, "the energy-minimisation timing covers CG sweeps");
+        if (h.p.precision == RN_MIXED) time_energy<float>(h, op, reps, flush_bytes, us, bytes, name);
+        else time_energy<double>(h, op, reps, flush_bytes, us, bytes, name);
+        return;
+    }
+    const std::function<void()> none;
+    if (op == RN_SOP_TRANSPOSE) {
+        name = "transpose_P_L0";
+        *bytes = 24.0 * L.P.nnz;
+        *us = time_launches(s, reps, flush_bytes, none, [&]() {
+            DCsr Pt;
+            transpose(view(L.P), true, Pt, s);
+        });
+        return;
+    }
+    DCsr AP;
+    spgemm(A, view(L.P), AP, s);  // untimed: its size, and the operand of R (A P)
+    if (op == RN_SOP_GALERKIN_AP) {
+        name = "galerkin_AP_L0";
+        *bytes = 12.0 * (A.nnz + L.P.nnz) + 12.0 * AP.nnz;
+        *us = time_launches(s, reps, flush_bytes, none, [&]() {
+            DCsr C;
+            spgemm(A, view(L.P), C, s);
+        });
+    } else {
+        name = "galerkin_RAP_L0";
+        *bytes = 12.0 * (L.R.nnz + AP.nnz) + 12.0 * h.lev[1]->A.nnz;
+        *us = time_launches(s, reps, flush_bytes, none, [&]() {
+            DCsr C;
+            spgemm(view(L.R), view(AP), C, s);
+        });
     }
 }
 

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <functional>
+
 #include "rn_hier.cuh"
 #include "rn_spmv.cuh"
 
@@ -1113,6 +1115,44 @@ __global__ void flush_read_kernel(const uint4 *__restrict__ p, int64_t n16, uint
     }
     a = __reduce_xor_sync(0xffffffffu, a);
     if ((threadIdx.x & 31) == 0) atomicXor(sink + blockIdx.x, a);
+}
+
+double time_launches(cudaStream_t s, int reps, int64_t flush_bytes, const std::function<void()> &before,
+                     const std::function<void()> &timed) {
+    if (reps < 1 || reps > 100000) fail(RN_EINVAL, "reps must be in [1, 100000]");
+    if (flush_bytes < 0) fail(RN_EINVAL, "flush_bytes must be >= 0");
+    const int64_t n16 = flush_bytes / 16;
+    DVec<uint4> fl(n16 > 0 ? (size_t)n16 : 0, s);
+    const int fgrid = 4 * num_sms();
+    DVec<uint32_t> sink(fgrid, s);
+    if (n16 > 0) RN_CUDA_CHECK(cudaMemsetAsync(fl.p, 0x5a, (size_t)n16 * 16, s));
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+    struct EvGuard {
+        std::vector<cudaEvent_t> &ev;
+        ~EvGuard() {
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } guard{ev};
+    for (auto &e : ev) RN_CUDA_CHECK(cudaEventCreate(&e));
+    for (int r = 0; r < reps; r++) {
+        if (before) before();
+        if (n16 > 0) {
+            flush_read_kernel<<<fgrid, 512, 0, s>>>(fl.p, n16, sink.p);
+            RN_CUDA_CHECK(cudaGetLastError());
+        }
+        RN_CUDA_CHECK(cudaEventRecord(ev[2 * r], s));
+        timed();
+        RN_CUDA_CHECK(cudaEventRecord(ev[2 * r + 1], s));
+    }
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+    double tot = 0.0;
+    for (int r = 0; r < reps; r++) {
+        float ms = 0.f;
+        RN_CUDA_CHECK(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]));
+        tot += ms;
+    }
+    return tot * 1e3 / reps;
 }
 
 void time_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, double *us, double *bytes, std::string &name) {

@@ -25,6 +25,8 @@ RN_MAX_LEVELS = 32
 RN_SOC_SYMMETRIC, RN_SOC_CLASSICAL = 0, 1
 (RN_OP_OUTER_SPMV, RN_OP_RELAX0_RESIDUAL, RN_OP_JACOBI_OUT, RN_OP_RESTRICT, RN_OP_PROLONG, RN_OP_CG_XR,
  RN_OP_CG_RZ, RN_OP_CG_P, RN_OP_COARSE_CLUSTER, RN_OP_COUNT) = range(10)
+(RN_SOP_ENERGY_SWEEP, RN_SOP_ENERGY_DIRECTION, RN_SOP_ENERGY_PRODUCT, RN_SOP_ENERGY_UPDATE, RN_SOP_GALERKIN_AP,
+ RN_SOP_GALERKIN_RAP, RN_SOP_TRANSPOSE, RN_SOP_COUNT) = range(8)
 STATUS_NAMES = ["RN_OK", "RN_EINVAL", "RN_ENOMEM", "RN_ESINGULAR", "RN_ESTALL", "RN_ENOTCONV", "RN_ETIMEOUT",
                 "RN_ECUDA", "RN_EINTERNAL"]
 
@@ -101,7 +103,11 @@ def _load():
     L.rn_profile_read.argtypes = [P(rn_kernel_stat), C.c_int, P(C.c_int)]
     L.rn_kernel_launches.argtypes = []
     L.rn_kernel_launches.restype = C.c_int64
+    L.rn_allocation_count.argtypes = []
+    L.rn_allocation_count.restype = C.c_int64
     L.rn_time_op.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, P(C.c_double), P(C.c_double), C.c_char_p]
+    L.rn_time_setup_op.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, P(C.c_double), P(C.c_double),
+                                   C.c_char_p]
     L.rn_adjoint_grad.argtypes = [P(rn_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     L.rn_last_error.restype = C.c_char_p
     L.rn_status_string.argtypes = [C.c_int]
@@ -133,7 +139,9 @@ rn_profile_read = lib.rn_profile_read
 rn_last_error = lib.rn_last_error
 rn_status_string = lib.rn_status_string
 rn_kernel_launches = lib.rn_kernel_launches
+rn_allocation_count = lib.rn_allocation_count
 rn_time_op = lib.rn_time_op
+rn_time_setup_op = lib.rn_time_setup_op
 rn_adjoint_grad = lib.rn_adjoint_grad
 rn_energy_min = lib.rn_energy_min
 rn_energy_min_noalloc = lib.rn_energy_min_noalloc
@@ -410,6 +418,14 @@ class Hierarchy:
         if st == RN_EINVAL:
             return None
         _check(st, "rn_time_op")
+        return nm.value.decode(), us.value, by.value
+
+    def time_setup_op(self, op: int, reps: int = 10, flush_bytes: int = 256 << 20):
+        """(name, mean device us per run, algorithmic bytes) of one level-0 setup operation timed in
+        isolation (rn_time_setup_op); raises RNError when the hierarchy lacks what it needs."""
+        us, by = C.c_double(), C.c_double()
+        nm = C.create_string_buffer(48)
+        _check(rn_time_setup_op(self._h, op, reps, flush_bytes, C.byref(us), C.byref(by), nm), "rn_time_setup_op")
         return nm.value.decode(), us.value, by.value
 
     def stats(self) -> dict:

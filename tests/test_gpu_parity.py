@@ -474,6 +474,34 @@ def test_time_op_measures_every_solve_launch(rn, torch_dev, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_time_setup_op_measures_every_setup_operation(rn, torch_dev, precision):
+    """The setup's measurement hook times each level-0 operation (energy
+    sweep and its launches, A P, R (A P), P^T) with the algorithmic bytes of
+    its byte model, refuses the energy operations without keep_aux, and leaves
+    the hierarchy usable."""
+    pr = CASES["aniso96"]()
+    h = gpu_hierarchy(rn, torch_dev, pr, precision=precision, keep_aux=1)
+    st = h.stats()
+    names = set()
+    for op in range(rn.RN_SOP_COUNT):
+        name, us, by = h.time_setup_op(op, reps=2, flush_bytes=1 << 20)
+        assert name and us > 0.0 and by > 0.0
+        names.add(name)
+    assert len(names) == rn.RN_SOP_COUNT
+    name, us, by = h.time_setup_op(rn.RN_SOP_TRANSPOSE, reps=1, flush_bytes=0)
+    assert by == 24.0 * st["nnz_P"][0]
+    xs, info, res = gpu_solve(rn, torch_dev, h, pr)
+    assert info["status"] == 0 and res < 1e-8
+    h.close()
+    h = gpu_hierarchy(rn, torch_dev, pr, precision=precision, keep_aux=0)
+    with pytest.raises(rn.RNError) as e:
+        h.time_setup_op(rn.RN_SOP_ENERGY_SWEEP, reps=1, flush_bytes=0)
+    assert e.value.status == rn.RN_EINVAL
+    assert h.time_setup_op(rn.RN_SOP_GALERKIN_RAP, reps=1, flush_bytes=0)[1] > 0.0
+    h.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("nu", [(1, 1), (1, 0), (2, 2)])
 def test_cg_graph_loop_matches_host_loop(rn, torch_dev, precision, nu):
     """Outer CG driven on the device (graph launches of several iterations,

@@ -2,7 +2,9 @@
 allocate device memory (for example a host framework whose caching allocator
 already holds the GPU's memory).  It must give the same result as
 rn_energy_min on the same inputs, on repeated calls (its static scratch keeps
-the previous call's contents), and reject inputs above its stated limits.
+the previous call's contents), make no allocation (the library's allocation
+counter and torch's allocator both unchanged across the call), and reject
+inputs above its stated limits.
 
 This file is named so that pytest collects it last.
 """
@@ -42,11 +44,18 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls(env, oracle):
         args = (d(A.indptr.astype(np.int32)), d(A.indices.astype(np.int32)), d(A.data),
                 d(N.indptr.astype(np.int32)), d(N.indices.astype(np.int32)), N.shape[1], d(L.rowtype), d(L.Bc))
         P_ref = d(T.data.astype(np.float64))
+        a0 = rn.rn_allocation_count()
         rn.energy_min(*args, P_ref, sweeps, method=rn.RN_ENERGY_CG)
+        assert rn.rn_allocation_count() > a0  # the counter sees the allocating entry point's scratch
         ref = P_ref.cpu().numpy()
         for _ in range(2):  # the second call starts from the first call's leftover scratch
             P = d(T.data.astype(np.float64))
+            torch.cuda.synchronize()
+            a1 = rn.rn_allocation_count()
+            t1 = torch.cuda.memory_stats(dev).get("allocation.all.allocated", 0)
             rn.energy_min_noalloc(*args, P, sweeps)
+            assert rn.rn_allocation_count() == a1, "rn_energy_min_noalloc allocated memory"
+            assert torch.cuda.memory_stats(dev).get("allocation.all.allocated", 0) == t1
             got = P.cpu().numpy()
             assert np.max(np.abs(got - ref)) <= TOL * np.max(np.abs(ref))
 
