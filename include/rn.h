@@ -92,7 +92,8 @@ typedef struct {
     uint64_t seed;           /* aggregation priority seed (level l uses seed + l) */
     int symmetric;           /* 1: R = P^T;  0: R built from A^T and B-hat */
     int nu_pre, nu_post;     /* V-cycle relaxation counts */
-    int precision;           /* RN_FP64, or RN_MIXED: FP32 cycle inside the FP64 outer iteration */
+    int precision;           /* RN_FP64, or RN_MIXED: FP32 cycle inside the FP64 outer iteration, and
+                                FP32 energy-minimisation sweeps when k = 1 (FP64 sweeps for k > 1) */
     int outer;               /* RN_OUTER_STATIONARY / RN_OUTER_CG / RN_OUTER_FGMRES */
     int restart;             /* FGMRES restart length */
     int use_graphs;          /* 1: capture the preconditioner cycle in a CUDA graph */
@@ -361,7 +362,7 @@ rn_status rn_time_op(rn_hierarchy *h, int op, int reps, int64_t flush_bytes, dou
  * level-0 operation of Alg. 3 in isolation, with the flush, events and
  * outputs of rn_time_op.  The energy-minimisation operations run on level 0's
  * minimisation pattern N (after the pre-filter) from its tentative T, in the
- * hierarchy's setup precision (FP32 sweeps when precision is RN_MIXED); every
+ * hierarchy's setup precision (FP32 sweeps when precision is RN_MIXED and k = 1); every
  * run starts from the CG state after the first sweep, restored before it
  * outside the timed region, so it times a general sweep.  They need a
  * hierarchy built with keep_aux and energy_method RN_ENERGY_CG.  The Galerkin

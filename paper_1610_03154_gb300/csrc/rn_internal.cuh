@@ -285,6 +285,37 @@ template <typename TV>
 void masked_product_mapped(const EpMap &m, const CsrView &A, const TV *aval, const int32_t *nrowptr,
                            const int32_t *ncol, int64_t nnzN, int32_t nc, const TV *X, TV *W, const ProjArgsT<TV> &pa,
                            double scale, const TV *Y, const Fin &fin, cudaStream_t s);
+// The energy product on a sliced plan (see rn_spgemm.cu), built once per
+// minimisation.  Rows go in slices of 32 / G consecutive rows, one warp per
+// slice and G lanes per row; lane l of row i owns A_i's entries l, l + G, ...
+// Per slice the plan stores, interleaved so that the warp's 32 lanes read 32
+// consecutive words: A's values in the sweeps' type (pa), the start of the
+// neighbour's pattern row nrp[k] (pb), and the positions of row i's pattern
+// columns in N_k, one byte each (255: absent), packed four to a word (pm).
+// rinfo[i] = steps | len << 16 (steps = ceil(|A_i| / G), 0 for rows the
+// operator zeroes; len = |N_i|); bq[q] = Bc at the entry's column and de[q] =
+// the row's D^{-1} (or 1 without preconditioning), per pattern entry, for the
+// projection and for the elementwise CG kernels.
+template <typename TV>
+struct EpPlan {
+    DVec<int32_t> aoff, moff, rinfo, pb;
+    DVec<TV> pa, bq, de;
+    DVec<uint32_t> pm;
+    int G = 1, S = 4;
+    int64_t slots = 0, words = 0;
+    bool ok = false;
+};
+// false (plan unusable) when a row of N is longer than 16 entries, a row N_k
+// longer than 254, or the plan's offsets would pass int32: the caller then
+// uses the gather map or the scanning product.  dinv may be null (no
+// preconditioning: de = 1).
+template <typename TV>
+bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN,
+                   const int32_t *rowtype, const double *Bc, const double *dinv, cudaStream_t s);
+// W = scale * Proj(Mask_N(A X)) (and <Y, W> into fin when Y != null) on the plan
+template <typename TV>
+void masked_product_plan(const EpPlan<TV> &p, int32_t n, const int32_t *nrowptr, int64_t nnzN, const TV *X, TV *W,
+                         const TV *rs2, double scale, const TV *Y, const Fin &fin, cudaStream_t s);
 // rs2 for ProjArgs: the row projection's scale on pattern N (n rows)
 void proj_scales(int32_t n, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN, const int32_t *rowtype,
                  const double *Bc, double *rs2, cudaStream_t s);

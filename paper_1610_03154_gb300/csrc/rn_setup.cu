@@ -871,6 +871,127 @@ cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, TV *__restrict__ P, 
     grid_finish<kT, 1>(v, fin, sm);  // the finisher ignores the sum once done is set
 }
 
+// Elementwise forms of the three kernels above for the plan's per-entry
+// D^{-1} (de): no row structure, four consecutive entries per thread (vector
+// loads when VEC: every array 16-byte aligned), the same expressions per
+// entry.  The reductions add per-thread sums in a fixed order.
+template <typename TV, bool VEC>
+__device__ __forceinline__ void ld4(const TV *__restrict__ p, int64_t q, TV (&v)[4]) {
+    if constexpr (VEC && sizeof(TV) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p + q);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (VEC) {
+        const double2 a = *reinterpret_cast<const double2 *>(p + q);
+        const double2 b = *reinterpret_cast<const double2 *>(p + q + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = p[q + k];
+    }
+}
+template <typename TV, bool VEC>
+__device__ __forceinline__ void st4(TV *__restrict__ p, int64_t q, const TV (&v)[4]) {
+    if constexpr (VEC && sizeof(TV) == 4) {
+        *reinterpret_cast<float4 *>(p + q) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (VEC) {
+        *reinterpret_cast<double2 *>(p + q) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + q + 2) = make_double2(v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) p[q + k] = v[k];
+    }
+}
+
+template <typename TV, bool VEC>
+__global__ void __launch_bounds__(kT)
+cg_rho_flat_kernel(int64_t nz, const TV *__restrict__ R, const TV *__restrict__ de, Fin fin) {
+    __shared__ double sm[32];
+    TV acc = TV(0);
+    const int64_t stride = (int64_t)gridDim.x * kT * 4;
+    for (int64_t q = ((int64_t)blockIdx.x * kT + threadIdx.x) * 4; q < nz; q += stride) {
+        if (q + 4 <= nz) {
+            TV r[4], d[4];
+            ld4<TV, VEC>(R, q, r);
+            ld4<TV, VEC>(de, q, d);
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc = fma(r[k], r[k] * d[k], acc);
+        } else {
+            for (int64_t t = q; t < nz; t++) acc = fma(R[t], R[t] * de[t], acc);
+        }
+    }
+    const double v[1] = {(double)acc};
+    grid_finish<kT, 1>(v, fin, sm);
+}
+
+template <typename TV, bool VEC>
+__global__ void __launch_bounds__(kT)
+cg_dd_flat_kernel(int64_t nz, const TV *__restrict__ R, const TV *__restrict__ de, const double *__restrict__ sc,
+                  const int32_t *__restrict__ fl, int first, TV *__restrict__ Dd) {
+    if (fl[0]) return;
+    const TV beta = (TV)sc[2];
+    const int64_t stride = (int64_t)gridDim.x * kT * 4;
+    for (int64_t q = ((int64_t)blockIdx.x * kT + threadIdx.x) * 4; q < nz; q += stride) {
+        if (q + 4 <= nz) {
+            TV r[4], d[4], o[4];
+            ld4<TV, VEC>(R, q, r);
+            ld4<TV, VEC>(de, q, d);
+            if (!first) ld4<TV, VEC>(Dd, q, o);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const TV z = r[k] * d[k];
+                o[k] = first ? z : z + beta * o[k];
+            }
+            st4<TV, VEC>(Dd, q, o);
+        } else {
+            for (int64_t t = q; t < nz; t++) {
+                const TV z = R[t] * de[t];
+                Dd[t] = first ? z : z + beta * Dd[t];
+            }
+        }
+    }
+}
+
+template <typename TV, bool VEC>
+__global__ void __launch_bounds__(kT)
+cg_update_flat_kernel(int64_t nz, TV *__restrict__ P, TV *__restrict__ R, const TV *__restrict__ Dd,
+                      const TV *__restrict__ W, const TV *__restrict__ de, const double *__restrict__ sc,
+                      const int32_t *__restrict__ fl, Fin fin) {
+    __shared__ double sm[32];
+    const bool done = fl[0] != 0;
+    const TV alpha = (TV)sc[4];
+    TV acc = TV(0);
+    if (!done) {
+        const int64_t stride = (int64_t)gridDim.x * kT * 4;
+        for (int64_t q = ((int64_t)blockIdx.x * kT + threadIdx.x) * 4; q < nz; q += stride) {
+            if (q + 4 <= nz) {
+                TV p[4], r[4], d[4], w[4], di[4];
+                ld4<TV, VEC>(P, q, p);
+                ld4<TV, VEC>(R, q, r);
+                ld4<TV, VEC>(Dd, q, d);
+                ld4<TV, VEC>(W, q, w);
+                ld4<TV, VEC>(de, q, di);
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    p[k] = p[k] + alpha * d[k];
+                    r[k] = r[k] - alpha * w[k];
+                    acc = fma(r[k], r[k] * di[k], acc);
+                }
+                st4<TV, VEC>(P, q, p);
+                st4<TV, VEC>(R, q, r);
+            } else {
+                for (int64_t t = q; t < nz; t++) {
+                    P[t] = P[t] + alpha * Dd[t];
+                    const TV rr = R[t] - alpha * W[t];
+                    R[t] = rr;
+                    acc = fma(rr, rr * de[t], acc);
+                }
+            }
+        }
+    }
+    const double v[1] = {(double)acc};
+    grid_finish<kT, 1>(v, fin, sm);  // the finisher ignores the sum once done is set
+}
+
 // ------------------------------------------------------------------ GMRES energy minimisation (Sec. 4.2)
 // sc[0] beta, sc[1] ||w||^2 / scratch, fl[0] done, fl[1] k (number of finished steps)
 __global__ void gm_start_kernel(double *sc, int32_t *fl, double *g) {
@@ -1150,7 +1271,9 @@ struct CgSweep {
     double *rs2 = nullptr;
     KProj<TV> kp;
     ProjArgsT<TV> pa{};
-    EpMap em;
+    EpPlan<TV> plan;   // the sliced product and the elementwise kernels (when it can be built)
+    EpMap em;          // otherwise: the gather map, else the scanning product
+    bool vec = false;  // elementwise kernels with 16-byte vector accesses
     Fin fin;
     int G = 4;
     double nzb = 0, rpb = 0, db = 0;
@@ -1160,20 +1283,13 @@ struct CgSweep {
         : c(c_), A(A_), N(N_), rowtype(rowtype_), Bc(Bc_), s(c_.s) {
         if constexpr (f32) {
             Rv.alloc(N.nnz, s); Dv.alloc(N.nnz, s); Wv.alloc(N.nnz, s); Xv.alloc(N.nnz, s);
-            Av.alloc(A.nnz, s); Iv.alloc(N.n, s);
             R = Rv.p; Dd = Dv.p; W = Wv.p; X = Xv.p;
             to_float(X64, X, N.nnz, s);
-            to_float(A.val, Av.p, A.nnz, s);
-            to_float(c_dinv, Iv.p, N.n, s);
-            aval = Av.p;
-            dinv_t = Iv.p;
         } else {
             R = c.R; Dd = c.Dd; W = c.W; X = X64;
             if (!R) { Rv.alloc(N.nnz, s); R = Rv.p; }
             if (!Dd) { Dv.alloc(N.nnz, s); Dd = Dv.p; }
             if (!W) { Wv.alloc(N.nnz, s); W = Wv.p; }
-            aval = A.val;
-            dinv_t = c_dinv;
         }
         fill_i32(c.fl, 0, 1, s);
         rs2 = c.rs2;
@@ -1202,15 +1318,37 @@ struct CgSweep {
         fin.sc = c.sc;
         fin.fl = c.fl;
         fin.stop = kCgStop;
-        dinv = c.precond ? dinv_t : nullptr;
-        // the pattern is fixed for all sweeps: gather map built once (falls
-        // back to the scanning product for rows of N too long for the map)
-        if (!c.scan_only) ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
+        // the pattern is fixed for all sweeps: the sliced plan is built once
+        // (it holds A's values in TV and D^{-1} per entry); rows of N too long
+        // for it fall back to the gather map, then to the scanning product
+        if (!c.scan_only)
+            ep_plan_build<TV>(plan, A, N.rp, N.col, N.nnz, rowtype, Bc, c.precond ? c_dinv : nullptr, s);
+        if (!plan.ok) {
+            if constexpr (f32) {
+                Av.alloc(A.nnz, s);
+                Iv.alloc(N.n, s);
+                to_float(A.val, Av.p, A.nnz, s);
+                to_float(c_dinv, Iv.p, N.n, s);
+                aval = Av.p;
+                dinv_t = Iv.p;
+            } else {
+                aval = A.val;
+                dinv_t = c_dinv;
+            }
+            dinv = c.precond ? dinv_t : nullptr;
+            if (!c.scan_only) ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
+        } else {
+            auto al = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+            vec = al(X) && al(R) && al(Dd) && al(W) && al(plan.de.p);
+        }
     }
     void product(const TV *Xin, TV *Wout, double scale, const TV *Y, const Fin &f) {
         const bool k1 = c.k == 1;
         const Fin none0;
-        if (em.ok)
+        if (plan.ok)
+            masked_product_plan<TV>(plan, N.n, N.rp, N.nnz, Xin, Wout, pa.rs2, k1 ? scale : 1.0, k1 ? Y : nullptr,
+                                    k1 ? f : none0, s);
+        else if (em.ok)
             masked_product_mapped<TV>(em, A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, k1 ? scale : 1.0,
                                       k1 ? Y : nullptr, k1 ? f : none0, s);
         else
@@ -1218,18 +1356,37 @@ struct CgSweep {
                                     k1 ? Y : nullptr, k1 ? f : none0, s);
         if (!k1) kp.apply(N, rowtype, Wout, scale, Y, f, s);
     }
+    int flat_grid(const void *fn) const {
+        const int64_t chunks = (N.nnz + 3) / 4;
+        int64_t need = (chunks + kT - 1) / kT;
+        const int64_t wave = (int64_t)resident_blocks(fn, kT, 0) * num_sms();
+        need = std::min<int64_t>(std::min<int64_t>(need, wave), kReduceBlocks);
+        return (int)std::max<int64_t>(need, 1);
+    }
+#define RN_FLAT(name, bytes, kern, ...)                                                                     \
+    do {                                                                                                    \
+        if (vec) RN_LAUNCH(name, bytes, s, (kern<TV, true>), flat_grid((const void *)kern<TV, true>), kT, 0, \
+                           __VA_ARGS__);                                                                    \
+        else RN_LAUNCH(name, bytes, s, (kern<TV, false>), flat_grid((const void *)kern<TV, false>), kT, 0,   \
+                       __VA_ARGS__);                                                                        \
+    } while (0)
     // R = -Proj(Mask_N(A X)) and rho = <R, D^{-1} R>
     void start() {
         const Fin none;
         product(X, R, -1.0, nullptr, none);
         fin.mode = FIN_CG_RHO;
         fin.it = 0;
-        RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R, dinv, fin);
+        if (plan.ok) RN_FLAT("energy_cg_rho", 2 * nzb, cg_rho_flat_kernel, N.nnz, R, plan.de.p, fin);
+        else RN_ROWG_LAUNCH("energy_cg_rho", rpb + nzb + db, s, G, cg_rho_kernel, N.n, N.rp, R, dinv, fin);
     }
     // Dd = D^{-1} R (+ beta Dd after the first sweep)
     void direction(int it) {
-        RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R, dinv, c.sc,
-                       c.fl, it == 0 ? 1 : 0, Dd);
+        if (plan.ok)
+            RN_FLAT("energy_cg_direction", (it == 0 ? 3 : 4) * nzb, cg_dd_flat_kernel, N.nnz, R, plan.de.p, c.sc,
+                    c.fl, it == 0 ? 1 : 0, Dd);
+        else
+            RN_ROWG_LAUNCH("energy_cg_direction", rpb + 3 * nzb + db, s, G, cg_dd_kernel, N.n, N.rp, R, dinv, c.sc,
+                           c.fl, it == 0 ? 1 : 0, Dd);
     }
     // W = Proj(Mask_N(A Dd)), <Dd, W> and alpha
     void sweep_product() {
@@ -1240,9 +1397,14 @@ struct CgSweep {
     void update(int it) {
         fin.mode = FIN_CG_RHO;
         fin.it = it + 1;
-        RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R, Dd, W,
-                       dinv, c.sc, c.fl, fin);
+        if (plan.ok)
+            RN_FLAT("energy_cg_update", 7 * nzb, cg_update_flat_kernel, N.nnz, X, R, Dd, W, plan.de.p, c.sc, c.fl,
+                    fin);
+        else
+            RN_ROWG_LAUNCH("energy_cg_update", rpb + 6 * nzb + db, s, G, cg_update_kernel, N.n, N.rp, X, R, Dd, W,
+                           dinv, c.sc, c.fl, fin);
     }
+#undef RN_FLAT
     void sweep(int it) {
         direction(it);
         sweep_product();
@@ -1300,18 +1462,23 @@ static void energy_min_gmres_t(const EmCtx &c, const CsrView &A, const Pattern &
     else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
     ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
     TV *X;
-    const TV *aval;
+    const TV *aval = nullptr;
+    // the sliced plan holds A's values in TV; without it, A is converted
+    EpPlan<TV> plan;
+    if (!c.scan_only) ep_plan_build<TV>(plan, A, N.rp, N.col, N.nnz, rowtype, Bc, nullptr, s);
     if constexpr (f32) {
         Xv.alloc(nz > 0 ? nz : 1, s);
-        Av.alloc(A.nnz, s);
         Bcv.alloc((size_t)N.nc * c.k, s);
         Rsv.alloc(N.n, s);
         to_float(X64, Xv.p, nz, s);
-        to_float(A.val, Av.p, A.nnz, s);
+        if (!plan.ok) {
+            Av.alloc(A.nnz, s);
+            to_float(A.val, Av.p, A.nnz, s);
+            aval = Av.p;
+        }
         to_float(Bc, Bcv.p, (int64_t)N.nc * c.k, s);
         to_float(rs2, Rsv.p, N.n, s);
         X = Xv.p;
-        aval = Av.p;
         pa.Bc = Bcv.p;
         pa.rs2 = Rsv.p;
     } else {
@@ -1323,10 +1490,12 @@ static void energy_min_gmres_t(const EmCtx &c, const CsrView &A, const Pattern &
     const int eg = grid_for(nz, 1024);
     const double nzb = (double)sizeof(TV) * nz;
     EpMap em;
-    ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
+    if (!plan.ok && !c.scan_only) ep_map_build(em, A, N.rp, N.col, N.nnz, rowtype, s);
     auto product = [&](const TV *Xin, TV *Wout, double scale) {
         const double sc0 = c.k == 1 ? scale : 1.0;
-        if (em.ok)
+        if (plan.ok)
+            masked_product_plan<TV>(plan, N.n, N.rp, N.nnz, Xin, Wout, pa.rs2, sc0, nullptr, Fin(), s);
+        else if (em.ok)
             masked_product_mapped<TV>(em, A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, sc0, nullptr, Fin(), s);
         else masked_product_proj<TV>(A, aval, N.rp, N.col, N.nnz, N.nc, Xin, Wout, pa, sc0, nullptr, Fin(), s);
         if (c.k > 1) kp.apply(N, rowtype, Wout, scale, nullptr, Fin(), s);
@@ -1387,7 +1556,10 @@ static EmCtx ctx_of(rn_hierarchy &h) {
     c.fl = h.iflags.p;
     c.precond = h.p.energy_precond;
     c.method = h.p.energy_method;
-    c.fp32 = h.p.precision == RN_MIXED;  // FP32 sweeps (CG and GMRES) in the mixed-precision setup
+    // FP32 sweeps (CG and GMRES) in the mixed-precision setup when k = 1; with
+    // k > 1 candidates the row projection multiplies rounding by the
+    // conditioning of each row's fit, so the sweeps stay FP64
+    c.fp32 = h.p.precision == RN_MIXED && h.k == 1;
     c.k = h.k;
     return c;
 }

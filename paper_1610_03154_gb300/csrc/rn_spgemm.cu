@@ -8,6 +8,7 @@
 // * masked_product_proj: the energy-minimisation operator
 //   W = scale * Proj(Mask_N(A X)) on a fixed pattern, with the row-wise
 //   constraint projection and a Frobenius product fused in.
+#include <algorithm>
 #include <climits>
 #include <cstring>
 
@@ -879,6 +880,338 @@ void masked_product_mapped(const EpMap &m, const CsrView &A, const TV *aval, con
     }
 #undef RN_MP_CASE
 }
+// ------------------------------------------------------------------ energy product on a sliced plan
+// The scanning and mapped kernels give every lane of a row's group the whole
+// of A_i: each lane reloads a_ik, k and nrp[k] for every k and follows the
+// chain k -> nrp[k] -> X, so the work is dominated by redundant loads and
+// dependent latency.  The plan (EpPlan) is built once per minimisation:
+// lane l of row i owns A_i's entries l, l + G, ..., and for each of them reads
+// a_ik and nrp[k] from slice-interleaved arrays (32 consecutive words per
+// warp) and one map byte per pattern entry of row i; on a hit it gathers
+// X[nrp[k] + pos] into a register accumulator of that entry.  The G partial
+// sums of every entry are added by a butterfly over the group (a fixed order,
+// so runs are bit-reproducible), then the row projection and <Y, W> follow as
+// in the other kernels.
+constexpr int kPlanThreads = 256;
+constexpr int kPlanMaxLen = 16;
+
+// One warp per slice: the slice's A slots (steps x 32) and map words, and the
+// row infos; *mx: [0] longest row of N among rows the operator keeps,
+// [1] longest row of N overall (its positions must fit a byte).
+template <int G>
+__global__ void __launch_bounds__(kPlanThreads)
+ep_plan_sizes_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ nrp,
+                     const int32_t *__restrict__ rowtype, int32_t *__restrict__ na, int32_t *__restrict__ nw,
+                     int32_t *__restrict__ rinfo, int32_t *__restrict__ mx) {
+    constexpr int RW = 32 / G;
+    const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
+    const int64_t nsl = ((int64_t)n + RW - 1) / RW;
+    const int64_t wstride = (int64_t)gridDim.x * (kPlanThreads / 32);
+    int32_t m_keep = 0, m_all = 0;
+    for (int64_t sl = blockIdx.x * (int64_t)(kPlanThreads / 32) + threadIdx.x / 32; sl < nsl; sl += wstride) {
+        const int64_t i = sl * RW + r;
+        int32_t steps = 0, words = 0;
+        if (i < n) {
+            const int32_t len = nrp[i + 1] - nrp[i];
+            const bool fixed = rowtype[i] != 0 || len <= 1;
+            const int32_t a = fixed ? 0 : arp[i + 1] - arp[i];
+            steps = (a + G - 1) / G;
+            words = (int32_t)(((int64_t)steps * len + 3) / 4);
+            if (l == 0) rinfo[i] = (len < 255 && steps <= 0xffff) ? (steps | (len << 16)) : 0;
+            m_all = max(m_all, (steps <= 0xffff) ? len : 255);  // rows no plan can hold reject the plan
+            if (!fixed) m_keep = max(m_keep, len);
+        }
+        const int32_t smax = __reduce_max_sync(0xffffffffu, steps);
+        const int32_t wmax = __reduce_max_sync(0xffffffffu, words);
+        if (lane == 0) {
+            na[sl] = smax * 32;
+            nw[sl] = wmax * 32;
+        }
+    }
+    m_keep = __reduce_max_sync(0xffffffffu, m_keep);
+    m_all = __reduce_max_sync(0xffffffffu, m_all);
+    if (lane == 0) {
+        atomicMax(mx, m_keep);
+        atomicMax(mx + 1, m_all);
+    }
+}
+
+// One warp per slice: fills pa, pb and the map words of every lane, and bq,
+// de of every pattern entry.
+template <int G, typename TV>
+__global__ void __launch_bounds__(kPlanThreads)
+ep_plan_fill_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                    const double *__restrict__ aval, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
+                    const int32_t *__restrict__ rinfo, const int32_t *__restrict__ aoff,
+                    const int32_t *__restrict__ moff, const double *__restrict__ Bc, const double *__restrict__ dinv,
+                    TV *__restrict__ pa, int32_t *__restrict__ pb, uint32_t *__restrict__ pm, TV *__restrict__ bq,
+                    TV *__restrict__ de) {
+    constexpr int RW = 32 / G;
+    const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
+    const int64_t nsl = ((int64_t)n + RW - 1) / RW;
+    const int64_t wstride = (int64_t)gridDim.x * (kPlanThreads / 32);
+    for (int64_t sl = blockIdx.x * (int64_t)(kPlanThreads / 32) + threadIdx.x / 32; sl < nsl; sl += wstride) {
+        const int64_t i = sl * RW + r;
+        const int64_t a0 = aoff[sl], a1 = aoff[sl + 1], m0 = moff[sl], m1 = moff[sl + 1];
+        int32_t steps = 0, len = 0, cs = 0, as = 0;
+        if (i < n) {
+            const int32_t inf = rinfo[i];
+            steps = inf & 0xffff;
+            len = inf >> 16;
+            cs = nrp[i];
+            as = arp[i];
+            const TV di = dinv ? (TV)dinv[i] : TV(1);
+            for (int32_t q = cs + l; q < cs + len; q += G) {
+                bq[q] = (TV)Bc[ncol[q]];
+                de[q] = di;
+            }
+        }
+        const int32_t a = (i < n && steps > 0) ? arp[i + 1] - as : 0;
+        // A slots: every slot of the slice is written (padding: a = 0, base 0)
+        for (int64_t j = 0; a0 + j * 32 + lane < a1; j++) {
+            const int32_t e = (int32_t)j * G + l;
+            const int64_t slot = a0 + j * 32 + lane;
+            if (j < steps && e < a) {
+                pa[slot] = (TV)aval[as + e];
+                pb[slot] = nrp[acol[as + e]];
+            } else {
+                pa[slot] = TV(0);
+                pb[slot] = 0;
+            }
+        }
+        // map bytes in the order the product reads them: b = j * len + q
+        uint32_t word = 0xffffffffu;
+        int64_t b = 0;
+        for (int32_t j = 0; j < steps; j++) {
+            const int32_t e = j * G + l;
+            int32_t ks = 0, ke = 0;
+            if (e < a) {
+                const int32_t k = acol[as + e];
+                ks = nrp[k];
+                ke = nrp[k + 1];
+            }
+            for (int32_t q = 0; q < len; q++, b++) {
+                uint32_t pos = 0xffu;
+                if (e < a) {
+                    const int32_t jc = ncol[cs + q];
+                    for (int32_t f = ks; f < ke; f++) {
+                        const int32_t c = ncol[f];
+                        if (c >= jc) {
+                            if (c == jc) pos = (uint32_t)(f - ks);
+                            break;
+                        }
+                    }
+                }
+                const int sh = (int)(b & 3) * 8;
+                word = (word & ~(0xffu << sh)) | (pos << sh);
+                if ((b & 3) == 3) {
+                    pm[m0 + (b >> 2) * 32 + lane] = word;
+                    word = 0xffffffffu;
+                }
+            }
+        }
+        int64_t w = (b + 3) >> 2;  // the partial last word, then padding words
+        if (b & 3) pm[m0 + (b >> 2) * 32 + lane] = word;
+        for (; m0 + w * 32 + lane < m1; w++) pm[m0 + w * 32 + lane] = 0xffffffffu;
+    }
+}
+
+template <int G, int S, typename TV>
+__global__ void __launch_bounds__(kPlanThreads)
+ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__restrict__ nrp,
+               const int32_t *__restrict__ aoff, const int32_t *__restrict__ moff, const TV *__restrict__ pa,
+               const int32_t *__restrict__ pb, const uint32_t *__restrict__ pm, const TV *__restrict__ bq,
+               const TV *__restrict__ rs2v, const TV *__restrict__ X, TV *__restrict__ W, TV scale,
+               const TV *__restrict__ Y, Fin fin) {
+    __shared__ double s_red[32];
+    constexpr int RW = 32 / G;
+    const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
+    const unsigned gm = group_mask<G>();
+    const int64_t nsl = ((int64_t)n + RW - 1) / RW;
+    const int64_t wstride = (int64_t)gridDim.x * (kPlanThreads / 32);
+    TV dot_t = TV(0);
+    for (int64_t sl = blockIdx.x * (int64_t)(kPlanThreads / 32) + threadIdx.x / 32; sl < nsl; sl += wstride) {
+        const int64_t i = sl * RW + r;
+        if (i >= n) continue;  // the whole group leaves together
+        const int32_t inf = rinfo[i];
+        const int32_t steps = inf & 0xffff, len = inf >> 16;
+        const int32_t cs = nrp[i];
+        if (steps == 0) {  // fixed rows; one-entry rows: constraint space {0}
+            for (int32_t q = cs + l; q < cs + len; q += G) W[q] = TV(0);
+            continue;
+        }
+        TV acc[S];
+#pragma unroll
+        for (int q = 0; q < S; q++) acc[q] = TV(0);
+        const TV *pal = pa + aoff[sl] + lane;
+        const int32_t *pbl = pb + aoff[sl] + lane;
+        const uint32_t *pml = pm + moff[sl] + lane;
+        uint32_t word = 0u;
+        int32_t b = 0;
+        for (int32_t j = 0; j < steps; j++) {
+            const TV a = pal[(int64_t)j * 32];
+            const int32_t nb = pbl[(int64_t)j * 32];
+#pragma unroll
+            for (int q = 0; q < S; q++) {
+                if (q < len) {
+                    if ((b & 3) == 0) word = pml[(int64_t)(b >> 2) * 32];
+                    const uint32_t pos = (word >> ((b & 3) * 8)) & 0xffu;
+                    if (pos != 0xffu) acc[q] = fma(a, X[nb + (int32_t)pos], acc[q]);
+                    b++;
+                }
+            }
+        }
+        if constexpr (G > 1) {
+#pragma unroll
+            for (int q = 0; q < S; q++)
+                if (q < len) {
+#pragma unroll
+                    for (int o = G / 2; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(gm, acc[q], o, G);
+                }
+        }
+        TV s1 = TV(0);
+#pragma unroll
+        for (int q = 0; q < S; q++)
+            if (q < len && (q % G) == l) s1 = fma(acc[q], bq[cs + q], s1);
+        if constexpr (G > 1) {
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) s1 += __shfl_xor_sync(gm, s1, o, G);
+        }
+        const TV c = s1 * rs2v[i];
+#pragma unroll
+        for (int q = 0; q < S; q++)
+            if (q < len && (q % G) == l) {
+                const TV w = scale * (acc[q] - c * bq[cs + q]);
+                W[cs + q] = w;
+                if (Y) dot_t = fma(Y[cs + q], w, dot_t);
+            }
+    }
+    const double dot_acc[1] = {(double)dot_t};
+    grid_finish<kPlanThreads, 1>(dot_acc, fin, s_red);
+}
+
+// lanes per row from the average length of A's rows
+static int plan_group(double avg_a) {
+    if (avg_a <= 12.0) return 1;
+    if (avg_a <= 24.0) return 2;
+    if (avg_a <= 48.0) return 4;
+    return 8;
+}
+
+template <typename TV>
+bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, const int32_t *ncol, int64_t nnzN,
+                   const int32_t *rowtype, const double *Bc, const double *dinv, cudaStream_t s) {
+    p.ok = false;
+    const int32_t n = A.n;
+    if (n == 0 || nnzN == 0) return false;
+    const int G = plan_group((double)A.nnz / n);
+    const int RW = 32 / G;
+    const int64_t nsl = ((int64_t)n + RW - 1) / RW;
+    DVec<int32_t> na((size_t)nsl, s), nw((size_t)nsl, s), mx(2, s);
+    p.rinfo.alloc((size_t)n, s);
+    fill_i32(mx.p, 0, 2, s);
+    const int grid = grid_for(nsl, kPlanThreads / 32, 8);
+#define RN_PLS_CASE(GG)                                                                                        \
+    case GG:                                                                                                   \
+        RN_LAUNCH("energy_map", 12.0 * n + 8.0 * nsl, s, ep_plan_sizes_kernel<GG>, grid, kPlanThreads, 0, n,     \
+                  A.rowptr, nrowptr, rowtype, na.p, nw.p, p.rinfo.p, mx.p);                                    \
+        break;
+    switch (G) {
+        RN_PLS_CASE(1)
+        RN_PLS_CASE(2)
+        RN_PLS_CASE(4)
+        RN_PLS_CASE(8)
+        default: fail(RN_EINTERNAL, "bad group size");
+    }
+#undef RN_PLS_CASE
+    int32_t m[2];
+    read_small(m, mx.p, 2, s);
+    if (m[0] > kPlanMaxLen || m[1] >= 255) {
+        p.rinfo.release();
+        return false;
+    }
+    p.aoff.alloc((size_t)nsl + 1, s);
+    p.moff.alloc((size_t)nsl + 1, s);
+    try {
+        p.slots = scan_counts(na.p, p.aoff.p, nsl, s);
+        p.words = scan_counts(nw.p, p.moff.p, nsl, s);
+    } catch (const Error &) {
+        p.rinfo.release();
+        p.aoff.release();
+        p.moff.release();
+        return false;  // offsets past int32: the caller falls back
+    }
+    p.G = G;
+    p.S = m[0] <= 4 ? 4 : (m[0] <= 8 ? 8 : 16);
+    p.pa.alloc((size_t)std::max<int64_t>(p.slots, 1), s);
+    p.pb.alloc((size_t)std::max<int64_t>(p.slots, 1), s);
+    p.pm.alloc((size_t)std::max<int64_t>(p.words, 1), s);
+    p.bq.alloc((size_t)nnzN, s);
+    p.de.alloc((size_t)nnzN, s);
+    const double vb = sizeof(TV);
+    const double bytes = 8.0 * n + 16.0 * A.nnz + (vb + 4.0) * p.slots + 4.0 * p.words + (8.0 + 2.0 * vb) * nnzN;
+#define RN_PLF_CASE(GG)                                                                                        \
+    case GG:                                                                                                   \
+        RN_LAUNCH("energy_map", bytes, s, (ep_plan_fill_kernel<GG, TV>), grid, kPlanThreads, 0, n, A.rowptr,    \
+                  A.col, A.val, nrowptr, ncol, p.rinfo.p, p.aoff.p, p.moff.p, Bc, dinv, p.pa.p, p.pb.p, p.pm.p, \
+                  p.bq.p, p.de.p);                                                                             \
+        break;
+    switch (G) {
+        RN_PLF_CASE(1)
+        RN_PLF_CASE(2)
+        RN_PLF_CASE(4)
+        RN_PLF_CASE(8)
+        default: fail(RN_EINTERNAL, "bad group size");
+    }
+#undef RN_PLF_CASE
+    p.ok = true;
+    return true;
+}
+
+template <typename TV>
+void masked_product_plan(const EpPlan<TV> &p, int32_t n, const int32_t *nrowptr, int64_t nnzN, const TV *X, TV *W,
+                         const TV *rs2, double scale, const TV *Y, const Fin &fin, cudaStream_t s) {
+    if (n == 0) return;
+    const double vb = sizeof(TV);
+    // algorithmic bytes (the plan's A slots stand for A's values and columns;
+    // the map and bq are not counted): A once, row pointers of N, row scales,
+    // X gathered once, W written once, Y once
+    const double bytes = (4.0 + vb) * (double)p.slots + 4.0 * (n + 1) + vb * n + 2.0 * vb * nnzN +
+                         (Y ? vb * nnzN : 0.0);
+    const int RW = 32 / p.G;
+    const int64_t nsl = ((int64_t)n + RW - 1) / RW;
+#define RN_PLK(GG, SS)                                                                                          \
+    RN_LAUNCH("energy_masked_product", bytes, s, (ep_plan_kernel<GG, SS, TV>),                                  \
+              grid_resident(ep_plan_kernel<GG, SS, TV>, kPlanThreads, 0, nsl, kPlanThreads / 32, kReduceBlocks), \
+              kPlanThreads, 0, n, p.rinfo.p, nrowptr, p.aoff.p, p.moff.p, p.pa.p, p.pb.p, p.pm.p, p.bq.p, rs2, X,  \
+              W, (TV)scale, Y, fin)
+#define RN_PLK_S(GG)                       \
+    case GG:                               \
+        if (p.S == 4) RN_PLK(GG, 4);       \
+        else if (p.S == 8) RN_PLK(GG, 8);  \
+        else RN_PLK(GG, 16);               \
+        break;
+    switch (p.G) {
+        RN_PLK_S(1)
+        RN_PLK_S(2)
+        RN_PLK_S(4)
+        RN_PLK_S(8)
+        default: fail(RN_EINTERNAL, "bad group size");
+    }
+#undef RN_PLK_S
+#undef RN_PLK
+}
+
+template bool ep_plan_build<double>(EpPlan<double> &, const CsrView &, const int32_t *, const int32_t *, int64_t,
+                                    const int32_t *, const double *, const double *, cudaStream_t);
+template bool ep_plan_build<float>(EpPlan<float> &, const CsrView &, const int32_t *, const int32_t *, int64_t,
+                                   const int32_t *, const double *, const double *, cudaStream_t);
+template void masked_product_plan<double>(const EpPlan<double> &, int32_t, const int32_t *, int64_t, const double *,
+                                          double *, const double *, double, const double *, const Fin &,
+                                          cudaStream_t);
+template void masked_product_plan<float>(const EpPlan<float> &, int32_t, const int32_t *, int64_t, const float *,
+                                         float *, const float *, double, const float *, const Fin &, cudaStream_t);
+
 template void masked_product_mapped<double>(const EpMap &, const CsrView &, const double *, const int32_t *,
                                             const int32_t *, int64_t, int32_t, const double *, double *,
                                             const ProjArgsT<double> &, double, const double *, const Fin &,
