@@ -507,6 +507,10 @@ def main():
     # the same step with W(1,1) cycles (Sec. 5.2), one warm-up and one timed step
     step(prec, gamma=2)
     times_w, infos_w = timed(prec, 1, gamma=2)
+    # the same step with the symmetric strength measure (the setting measured
+    # first), one warm-up and one timed step
+    step(prec, soc_kind=0)
+    times_sym, infos_sym = timed(prec, 1, soc_kind=0)
     # the same step with three candidates (1, x, y), Sec. 3.6
     step(prec, B3)
     times_k3, infos_k3 = timed(prec, 1, B3)
@@ -647,7 +651,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": pr.description, "precision": prec, "outer": "flexible CG" if prec == "mixed"
                        else "CG", "cycle": "V(1,1) weighted Jacobi omega=2/3, dense coarsest solve",
-                       "setup": "theta=0.25 symmetric strength, seeded MIS-2 aggregation, d=4, 6 CG energy-min "
+                       "setup": "theta=0.25 classical strength, seeded MIS-2 aggregation, d=4, 6 CG energy-min "
                                 "sweeps, pre/post filter 0.1", "l2": "256 MB torch fill (write) before every timed step; per-launch timings after a 256 MB read",
                        "setup_roofline": "energy_min and rap records",
                        "parallelism": f"replicas x{ws}"},
@@ -660,6 +664,9 @@ def main():
             "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "mixed_setup_vs_fp64": setup_err,
+            "symmetric_soc": {"step_s": times_sym[0], "iters": infos_sym[0]["iters"],
+                              "rel_res": infos_sym[0]["rel_res"], "strength": "symmetric, theta 0.25",
+                              "precision": prec},
             "w_cycle": {"step_s": times_w[0], "iters": infos_w[0]["iters"], "rel_res": infos_w[0]["rel_res"],
                         "cycle": "W(1,1)", "precision": prec},
             "candidates_3": {"step_s": times_k3[0], "iters": infos_k3[0]["iters"], "rel_res": infos_k3[0]["rel_res"],

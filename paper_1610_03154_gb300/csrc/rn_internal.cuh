@@ -291,17 +291,20 @@ void masked_product_mapped(const EpMap &m, const CsrView &A, const TV *aval, con
 // Per slice the plan stores, interleaved so that the warp's 32 lanes read 32
 // consecutive words: A's values in the sweeps' type (pa), the start of the
 // neighbour's pattern row nrp[k] (pb), and the positions of row i's pattern
-// columns in N_k, one byte each (255: absent), packed four to a word (pm).
+// columns in N_k (pm): `bits` bits each (4 when every row of N has at most 15
+// entries, else 8; all ones: absent), wps[s] words per A entry, the same for
+// the whole slice (enough for its longest row), so that entry q of a row is
+// always bit field q % (32 / bits) of word q / (32 / bits).
 // rinfo[i] = steps | len << 16 (steps = ceil(|A_i| / G), 0 for rows the
 // operator zeroes; len = |N_i|); bq[q] = Bc at the entry's column and de[q] =
 // the row's D^{-1} (or 1 without preconditioning), per pattern entry, for the
 // projection and for the elementwise CG kernels.
 template <typename TV>
 struct EpPlan {
-    DVec<int32_t> aoff, moff, rinfo, pb;
+    DVec<int32_t> aoff, moff, wps, slen, rinfo, pb;  // slen: per slice, the longest kept row of N
     DVec<TV> pa, bq, de;
     DVec<uint32_t> pm;
-    int G = 1, S = 4;
+    int G = 1, S = 4, bits = 8;
     int64_t slots = 0, words = 0;
     bool ok = false;
 };

@@ -895,13 +895,13 @@ void masked_product_mapped(const EpMap &m, const CsrView &A, const TV *aval, con
 constexpr int kPlanThreads = 256;
 constexpr int kPlanMaxLen = 16;
 
-// One warp per slice: the slice's A slots (steps x 32) and map words, and the
-// row infos; *mx: [0] longest row of N among rows the operator keeps,
-// [1] longest row of N overall (its positions must fit a byte).
+// One warp per slice: the slice's A slots (steps x 32), its longest kept row
+// of N (slen) and the row infos; *mx: [0] longest row of N among rows the
+// operator keeps, [1] longest row of N overall (positions must fit a field).
 template <int G>
 __global__ void __launch_bounds__(kPlanThreads)
 ep_plan_sizes_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ nrp,
-                     const int32_t *__restrict__ rowtype, int32_t *__restrict__ na, int32_t *__restrict__ nw,
+                     const int32_t *__restrict__ rowtype, int32_t *__restrict__ na, int32_t *__restrict__ slen,
                      int32_t *__restrict__ rinfo, int32_t *__restrict__ mx) {
     constexpr int RW = 32 / G;
     const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
@@ -910,22 +910,22 @@ ep_plan_sizes_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *
     int32_t m_keep = 0, m_all = 0;
     for (int64_t sl = blockIdx.x * (int64_t)(kPlanThreads / 32) + threadIdx.x / 32; sl < nsl; sl += wstride) {
         const int64_t i = sl * RW + r;
-        int32_t steps = 0, words = 0;
+        int32_t steps = 0, klen = 0;
         if (i < n) {
             const int32_t len = nrp[i + 1] - nrp[i];
             const bool fixed = rowtype[i] != 0 || len <= 1;
             const int32_t a = fixed ? 0 : arp[i + 1] - arp[i];
             steps = (a + G - 1) / G;
-            words = (int32_t)(((int64_t)steps * len + 3) / 4);
+            klen = fixed ? 0 : len;
             if (l == 0) rinfo[i] = (len < 255 && steps <= 0xffff) ? (steps | (len << 16)) : 0;
             m_all = max(m_all, (steps <= 0xffff) ? len : 255);  // rows no plan can hold reject the plan
-            if (!fixed) m_keep = max(m_keep, len);
+            m_keep = max(m_keep, klen);
         }
         const int32_t smax = __reduce_max_sync(0xffffffffu, steps);
-        const int32_t wmax = __reduce_max_sync(0xffffffffu, words);
+        const int32_t lmax = __reduce_max_sync(0xffffffffu, klen);
         if (lane == 0) {
             na[sl] = smax * 32;
-            nw[sl] = wmax * 32;
+            slen[sl] = lmax;
         }
     }
     m_keep = __reduce_max_sync(0xffffffffu, m_keep);
@@ -936,23 +936,37 @@ ep_plan_sizes_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *
     }
 }
 
-// One warp per slice: fills pa, pb and the map words of every lane, and bq,
-// de of every pattern entry.
+// Words per A entry of every slice and the slice's word count
+__global__ void ep_plan_words_kernel(int64_t nsl, const int32_t *__restrict__ na, const int32_t *__restrict__ slen,
+                                     int bits, int32_t *__restrict__ wps, int32_t *__restrict__ nw) {
+    for (int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sl < nsl; sl += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t w = (slen[sl] * bits + 31) / 32;
+        wps[sl] = w;
+        nw[sl] = na[sl] * w;  // (steps x 32) x words per step
+    }
+}
+
+// One warp per slice: fills pa, pb and the position words of every lane, and
+// bq, de of every pattern entry.  Word (j, w) of a lane: pm[moff + (j * wps +
+// w) * 32 + lane], field t of it = entry q = w * (32 / bits) + t.
 template <int G, typename TV>
 __global__ void __launch_bounds__(kPlanThreads)
 ep_plan_fill_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                     const double *__restrict__ aval, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
                     const int32_t *__restrict__ rinfo, const int32_t *__restrict__ aoff,
-                    const int32_t *__restrict__ moff, const double *__restrict__ Bc, const double *__restrict__ dinv,
-                    TV *__restrict__ pa, int32_t *__restrict__ pb, uint32_t *__restrict__ pm, TV *__restrict__ bq,
-                    TV *__restrict__ de) {
+                    const int32_t *__restrict__ moff, const int32_t *__restrict__ wps, int bits,
+                    const double *__restrict__ Bc, const double *__restrict__ dinv, TV *__restrict__ pa,
+                    int32_t *__restrict__ pb, uint32_t *__restrict__ pm, TV *__restrict__ bq, TV *__restrict__ de) {
     constexpr int RW = 32 / G;
     const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
     const int64_t nsl = ((int64_t)n + RW - 1) / RW;
     const int64_t wstride = (int64_t)gridDim.x * (kPlanThreads / 32);
+    const uint32_t none = (1u << bits) - 1u;
+    const int per = 32 / bits;
     for (int64_t sl = blockIdx.x * (int64_t)(kPlanThreads / 32) + threadIdx.x / 32; sl < nsl; sl += wstride) {
         const int64_t i = sl * RW + r;
         const int64_t a0 = aoff[sl], a1 = aoff[sl + 1], m0 = moff[sl], m1 = moff[sl + 1];
+        const int32_t ws = wps[sl];
         int32_t steps = 0, len = 0, cs = 0, as = 0;
         if (i < n) {
             const int32_t inf = rinfo[i];
@@ -967,64 +981,65 @@ ep_plan_fill_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *_
             }
         }
         const int32_t a = (i < n && steps > 0) ? arp[i + 1] - as : 0;
-        // A slots: every slot of the slice is written (padding: a = 0, base 0)
+        // A slots and position words: every slot and word of the slice is
+        // written (padding: a = 0, base 0, every field absent)
         for (int64_t j = 0; a0 + j * 32 + lane < a1; j++) {
             const int32_t e = (int32_t)j * G + l;
             const int64_t slot = a0 + j * 32 + lane;
-            if (j < steps && e < a) {
+            const bool live = j < steps && e < a;
+            int32_t ks = 0, ke = 0;
+            if (live) {
+                const int32_t k = acol[as + e];
                 pa[slot] = (TV)aval[as + e];
-                pb[slot] = nrp[acol[as + e]];
+                pb[slot] = ks = nrp[k];
+                ke = nrp[k + 1];
             } else {
                 pa[slot] = TV(0);
                 pb[slot] = 0;
             }
-        }
-        // map bytes in the order the product reads them: b = j * len + q
-        uint32_t word = 0xffffffffu;
-        int64_t b = 0;
-        for (int32_t j = 0; j < steps; j++) {
-            const int32_t e = j * G + l;
-            int32_t ks = 0, ke = 0;
-            if (e < a) {
-                const int32_t k = acol[as + e];
-                ks = nrp[k];
-                ke = nrp[k + 1];
-            }
-            for (int32_t q = 0; q < len; q++, b++) {
-                uint32_t pos = 0xffu;
-                if (e < a) {
-                    const int32_t jc = ncol[cs + q];
-                    for (int32_t f = ks; f < ke; f++) {
-                        const int32_t c = ncol[f];
-                        if (c >= jc) {
-                            if (c == jc) pos = (uint32_t)(f - ks);
-                            break;
+            for (int32_t w = 0; w < ws; w++) {
+                uint32_t word = 0u;
+                for (int t = 0; t < per; t++) {
+                    const int32_t q = w * per + t;
+                    uint32_t pos = none;
+                    if (live && q < len) {
+                        const int32_t jc = ncol[cs + q];
+                        for (int32_t f = ks; f < ke; f++) {
+                            const int32_t c = ncol[f];
+                            if (c >= jc) {
+                                if (c == jc) pos = (uint32_t)(f - ks);
+                                break;
+                            }
                         }
                     }
+                    word |= pos << (t * bits);
                 }
-                const int sh = (int)(b & 3) * 8;
-                word = (word & ~(0xffu << sh)) | (pos << sh);
-                if ((b & 3) == 3) {
-                    pm[m0 + (b >> 2) * 32 + lane] = word;
-                    word = 0xffffffffu;
-                }
+                const int64_t wi = m0 + (j * ws + w) * 32 + lane;
+                if (wi < m1) pm[wi] = word;
             }
         }
-        int64_t w = (b + 3) >> 2;  // the partial last word, then padding words
-        if (b & 3) pm[m0 + (b >> 2) * 32 + lane] = word;
-        for (; m0 + w * 32 + lane < m1; w++) pm[m0 + w * 32 + lane] = 0xffffffffu;
     }
 }
 
-template <int G, int S, typename TV>
+// Field t of a position word
+template <int BITS>
+__device__ __forceinline__ uint32_t plan_field(uint32_t w, int t) {
+    return (w >> (t * BITS)) & ((1u << BITS) - 1u);
+}
+
+template <int G, int S, int BITS, typename TV>
 __global__ void __launch_bounds__(kPlanThreads)
 ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__restrict__ nrp,
-               const int32_t *__restrict__ aoff, const int32_t *__restrict__ moff, const TV *__restrict__ pa,
-               const int32_t *__restrict__ pb, const uint32_t *__restrict__ pm, const TV *__restrict__ bq,
-               const TV *__restrict__ rs2v, const TV *__restrict__ X, TV *__restrict__ W, TV scale,
-               const TV *__restrict__ Y, Fin fin) {
+               const int32_t *__restrict__ aoff, const int32_t *__restrict__ moff, const int32_t *__restrict__ wps,
+               const int32_t *__restrict__ slen, const TV *__restrict__ pa, const int32_t *__restrict__ pb,
+               const uint32_t *__restrict__ pm,
+               const TV *__restrict__ bq, const TV *__restrict__ rs2v, const TV *__restrict__ X, TV *__restrict__ W,
+               TV scale, const TV *__restrict__ Y, Fin fin) {
     __shared__ double s_red[32];
     constexpr int RW = 32 / G;
+    constexpr int PER = 32 / BITS;             // fields per word
+    constexpr int NW = (S + PER - 1) / PER;    // most words per A entry
+    constexpr uint32_t NONE = (1u << BITS) - 1u;
     const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
     const unsigned gm = group_mask<G>();
     const int64_t nsl = ((int64_t)n + RW - 1) / RW;
@@ -1040,24 +1055,31 @@ ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__re
             for (int32_t q = cs + l; q < cs + len; q += G) W[q] = TV(0);
             continue;
         }
+        const int32_t ws = wps[sl], lm = slen[sl];  // the same for the whole warp
         TV acc[S];
 #pragma unroll
         for (int q = 0; q < S; q++) acc[q] = TV(0);
         const TV *pal = pa + aoff[sl] + lane;
         const int32_t *pbl = pb + aoff[sl] + lane;
         const uint32_t *pml = pm + moff[sl] + lane;
-        uint32_t word = 0u;
-        int32_t b = 0;
         for (int32_t j = 0; j < steps; j++) {
             const TV a = pal[(int64_t)j * 32];
             const int32_t nb = pbl[(int64_t)j * 32];
 #pragma unroll
-            for (int q = 0; q < S; q++) {
-                if (q < len) {
-                    if ((b & 3) == 0) word = pml[(int64_t)(b >> 2) * 32];
-                    const uint32_t pos = (word >> ((b & 3) * 8)) & 0xffu;
-                    if (pos != 0xffu) acc[q] = fma(a, X[nb + (int32_t)pos], acc[q]);
-                    b++;
+            for (int w = 0; w < NW; w++) {
+                if (w < ws) {
+                    const uint32_t word = pml[((int64_t)j * ws + w) * 32];
+#pragma unroll
+                    for (int t = 0; t < PER; t++) {
+                        const int q = w * PER + t;
+                        // fields past lm (warp-uniform) are absent: skipped in FP64, where
+                        // even a predicated-off FMA holds GB300's narrow FP64 pipe (FP32:
+                        // the unconditional form measured faster)
+                        if (q < S && (sizeof(TV) == 4 || q < lm)) {
+                            const uint32_t pos = plan_field<BITS>(word, t);
+                            if (pos != NONE) acc[q] = fma(a, X[nb + (int32_t)pos], acc[q]);
+                        }
+                    }
                 }
             }
         }
@@ -1109,12 +1131,14 @@ bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, cons
     const int64_t nsl = ((int64_t)n + RW - 1) / RW;
     DVec<int32_t> na((size_t)nsl, s), nw((size_t)nsl, s), mx(2, s);
     p.rinfo.alloc((size_t)n, s);
+    p.slen.alloc((size_t)nsl, s);
+    int32_t *slen = p.slen.p;
     fill_i32(mx.p, 0, 2, s);
     const int grid = grid_for(nsl, kPlanThreads / 32, 8);
 #define RN_PLS_CASE(GG)                                                                                        \
     case GG:                                                                                                   \
         RN_LAUNCH("energy_map", 12.0 * n + 8.0 * nsl, s, ep_plan_sizes_kernel<GG>, grid, kPlanThreads, 0, n,     \
-                  A.rowptr, nrowptr, rowtype, na.p, nw.p, p.rinfo.p, mx.p);                                    \
+                  A.rowptr, nrowptr, rowtype, na.p, slen, p.rinfo.p, mx.p);                                  \
         break;
     switch (G) {
         RN_PLS_CASE(1)
@@ -1128,8 +1152,13 @@ bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, cons
     read_small(m, mx.p, 2, s);
     if (m[0] > kPlanMaxLen || m[1] >= 255) {
         p.rinfo.release();
+        p.slen.release();
         return false;
     }
+    p.bits = m[1] <= 15 ? 4 : 8;  // positions in N_k < 15 fit four bits (all ones: absent)
+    p.wps.alloc((size_t)nsl, s);
+    RN_LAUNCH("energy_map", 12.0 * nsl, s, ep_plan_words_kernel, grid_for(nsl, 256), 256, 0, nsl, na.p, slen,
+              p.bits, p.wps.p, nw.p);
     p.aoff.alloc((size_t)nsl + 1, s);
     p.moff.alloc((size_t)nsl + 1, s);
     try {
@@ -1137,6 +1166,8 @@ bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, cons
         p.words = scan_counts(nw.p, p.moff.p, nsl, s);
     } catch (const Error &) {
         p.rinfo.release();
+        p.slen.release();
+        p.wps.release();
         p.aoff.release();
         p.moff.release();
         return false;  // offsets past int32: the caller falls back
@@ -1153,8 +1184,8 @@ bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, cons
 #define RN_PLF_CASE(GG)                                                                                        \
     case GG:                                                                                                   \
         RN_LAUNCH("energy_map", bytes, s, (ep_plan_fill_kernel<GG, TV>), grid, kPlanThreads, 0, n, A.rowptr,    \
-                  A.col, A.val, nrowptr, ncol, p.rinfo.p, p.aoff.p, p.moff.p, Bc, dinv, p.pa.p, p.pb.p, p.pm.p, \
-                  p.bq.p, p.de.p);                                                                             \
+                  A.col, A.val, nrowptr, ncol, p.rinfo.p, p.aoff.p, p.moff.p, p.wps.p, p.bits, Bc, dinv, p.pa.p, \
+                  p.pb.p, p.pm.p, p.bq.p, p.de.p);                                                             \
         break;
     switch (G) {
         RN_PLF_CASE(1)
@@ -1174,22 +1205,26 @@ void masked_product_plan(const EpPlan<TV> &p, int32_t n, const int32_t *nrowptr,
     if (n == 0) return;
     const double vb = sizeof(TV);
     // algorithmic bytes (the plan's A slots stand for A's values and columns;
-    // the map and bq are not counted): A once, row pointers of N, row scales,
-    // X gathered once, W written once, Y once
+    // the position words and bq are not counted): A once, row pointers of N,
+    // row scales, X gathered once, W written once, Y once
     const double bytes = (4.0 + vb) * (double)p.slots + 4.0 * (n + 1) + vb * n + 2.0 * vb * nnzN +
                          (Y ? vb * nnzN : 0.0);
     const int RW = 32 / p.G;
     const int64_t nsl = ((int64_t)n + RW - 1) / RW;
-#define RN_PLK(GG, SS)                                                                                          \
-    RN_LAUNCH("energy_masked_product", bytes, s, (ep_plan_kernel<GG, SS, TV>),                                  \
-              grid_resident(ep_plan_kernel<GG, SS, TV>, kPlanThreads, 0, nsl, kPlanThreads / 32, kReduceBlocks), \
-              kPlanThreads, 0, n, p.rinfo.p, nrowptr, p.aoff.p, p.moff.p, p.pa.p, p.pb.p, p.pm.p, p.bq.p, rs2, X,  \
-              W, (TV)scale, Y, fin)
-#define RN_PLK_S(GG)                       \
-    case GG:                               \
-        if (p.S == 4) RN_PLK(GG, 4);       \
-        else if (p.S == 8) RN_PLK(GG, 8);  \
-        else RN_PLK(GG, 16);               \
+#define RN_PLK(GG, SS, BB)                                                                                        \
+    RN_LAUNCH("energy_masked_product", bytes, s, (ep_plan_kernel<GG, SS, BB, TV>),                                \
+              grid_resident(ep_plan_kernel<GG, SS, BB, TV>, kPlanThreads, 0, nsl, kPlanThreads / 32, kReduceBlocks), \
+              kPlanThreads, 0, n, p.rinfo.p, nrowptr, p.aoff.p, p.moff.p, p.wps.p, p.slen.p, p.pa.p, p.pb.p, p.pm.p, \
+              p.bq.p,                                                                                                \
+              rs2, X, W, (TV)scale, Y, fin)
+#define RN_PLK_B(GG, SS)                  \
+    if (p.bits == 4) RN_PLK(GG, SS, 4);   \
+    else RN_PLK(GG, SS, 8);
+#define RN_PLK_S(GG)                        \
+    case GG:                                \
+        if (p.S == 4) { RN_PLK_B(GG, 4) }   \
+        else if (p.S == 8) { RN_PLK_B(GG, 8) } \
+        else { RN_PLK_B(GG, 16) }           \
         break;
     switch (p.G) {
         RN_PLK_S(1)
@@ -1199,6 +1234,7 @@ void masked_product_plan(const EpPlan<TV> &p, int32_t n, const int32_t *nrowptr,
         default: fail(RN_EINTERNAL, "bad group size");
     }
 #undef RN_PLK_S
+#undef RN_PLK_B
 #undef RN_PLK
 }
 
