@@ -17,12 +17,12 @@ the V(1,1) weighted-Jacobi cycle) from x0 = 0 to ||b - A x|| < 1e-8 ||b||.
   roofline   the dominant kernel of the step (by device time), achieved
              algorithmic bytes / measured duration against the measured HBM
              copy bandwidth.
-  cpu_baseline  the FP64 CPU oracle on this machine's host (1 thread): its
-             full setup plus a bounded number of CG iterations, the solve
-             scaled to the iteration count the GPU FP64 form needed.
+  cpu_baseline  the FP64 CPU oracle on this machine's host: one full step
+             (setup + CG solve to 1e-8) on all host threads, and one on a
+             single thread.
 
---impl reference times the oracle alone on the same workload (bounded sample
-per step, as above).  With --gpus N under torchrun every rank solves its own
+--impl reference times the oracle alone on the same workload: every step a
+full setup + solve to 1e-8 on all host threads.  With --gpus N under torchrun every rank solves its own
 replica (no data-path collective; "replicas only").
 """
 from __future__ import annotations
@@ -160,53 +160,59 @@ def job_step_seconds(step_s: float, device=None) -> float:
     return float(t.item())
 
 
-def run_oracle_sample(pr, iters_target: int | None, cg_sample_iters: int = 25):
-    """Oracle setup (full) + a bounded CG solve; returns seconds and the sample description."""
+def run_oracle_step(pr, threads: int):
+    """One full oracle step on the host: setup, then CG with the V(1,1) cycle
+    from x0 = 0 to ||b - A x|| < 1e-8 ||b||, on `threads` OpenMP threads.
+    Returns (seconds, setup seconds, iterations, relative residual)."""
     from oracle import oracle as O
 
+    O.set_threads(threads)
     t0 = time.perf_counter()
     h = O.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
     t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    x, info = h.solve(pr.b, tol=1e-8, maxit=cg_sample_iters, outer=1)
-    t_solve = time.perf_counter() - t0
-    done = max(info["iters"], 1)
-    per_it = t_solve / done
-    need = iters_target if iters_target else done
-    value = t_setup + per_it * need
-    sample = (f"oracle setup in full ({t_setup:.2f} s) + {done} FP64 CG iterations ({t_solve:.2f} s), "
-              f"solve scaled to {need} iterations")
-    return value, sample, t_setup, per_it
+    _, info = h.solve(pr.b, tol=1e-8, maxit=5000, outer=1)
+    total = time.perf_counter() - t0
+    del h
+    return total, t_setup, info["iters"], info["rel_res"]
+
+
+def host_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def reference_arm(args):
+    """The oracle, as it stands, timed on this machine's host cores: every
+    warm-up and timed step is a full setup + CG solve to 1e-8 of the workload
+    on all host threads (results do not depend on the thread count)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     pr = PR.aniso_problem(args.ne)
-    # iteration count of the oracle on this workload: one full FP64 CG solve up front (not timed)
-    from oracle import oracle as O
-
-    h = O.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
-    _, info = h.solve(pr.b, tol=1e-8, maxit=2000, outer=1)
-    iters = info["iters"]
-    del h
-    for _ in range(max(0, args.warmup - 1)):
-        run_oracle_sample(pr, iters)
-    vals, sample = [], ""
+    nth = host_threads()
+    for _ in range(args.warmup):
+        run_oracle_step(pr, nth)
+    vals, setups = [], []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        v, sample, _, _ = run_oracle_sample(pr, iters)
+        v, ts, iters, rr = run_oracle_step(pr, nth)
         vals.append(v)
+        setups.append(ts)
     wall = time.perf_counter() - t_all
     value = float(np.mean(vals))
+    sample = (f"every step a full oracle setup + FP64 CG solve to 1e-8 ({iters} iterations) on {nth} threads; "
+              f"{args.steps} timed steps in {wall:.1f} s")
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": pr.description, "solver": "oracle FP64 CG + V(1,1) Jacobi", "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
-                         "oracle_iters_to_1e-8": iters, "sample_wall_s": wall},
+        "config": {"workload": pr.description, "solver": "oracle FP64 CG + V(1,1) Jacobi", "l2": "n/a (CPU)",
+                   "setup": pr.params},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": nth, "kind": "oracle", "sample": sample,
+                         "setup_s": float(np.mean(setups)), "iters": iters, "rel_res": rr,
+                         "timed_wall_s": wall},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -639,9 +645,15 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        fp64_iters = (infos_other if other == "fp64" else infos)[0]["iters"]
-        v, sample, _, _ = run_oracle_sample(pr, fp64_iters)
-        cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+        # one full step of the oracle (setup + CG to 1e-8) on all host threads,
+        # and one on a single thread
+        nth = host_threads()
+        v, ts, it_o, rr_o = run_oracle_step(pr, nth)
+        v1, ts1, _, _ = run_oracle_step(pr, 1)
+        cpu = {"value": v, "unit": "s", "cores": nth, "kind": "oracle",
+               "sample": f"one full oracle step (setup {ts:.2f} s + FP64 CG to 1e-8, {it_o} iterations) on {nth} "
+                         f"threads",
+               "one_thread": {"value": v1, "unit": "s", "cores": 1, "setup_s": ts1}}
 
     if rank == 0:
         line = {

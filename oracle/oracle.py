@@ -32,7 +32,7 @@ def build(force: bool = False) -> str:
         if os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in srcs):
             return LIB
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
-           "-o", LIB + ".tmp"] + [os.path.join(HERE, s) for s in SOURCES] + ["-lm"]
+           "-fopenmp", "-o", LIB + ".tmp"] + [os.path.join(HERE, s) for s in SOURCES] + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
@@ -66,6 +66,9 @@ def lib():
         build()
         L = C.CDLL(LIB)
         P = C.POINTER
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
+        L.orc_set_threads(1)  # one thread unless a caller asks for more (set_threads)
         i32p, dp = P(C.c_int32), P(C.c_double)
         L.orc_csr_free.argtypes = [P(_CSR)]
         L.orc_free.argtypes = [C.c_void_p]
@@ -121,6 +124,15 @@ def _ip(a: np.ndarray):
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's row loops; results do not depend on the count."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 class _In:
     """Keeps numpy buffers alive while a _CSR view of them is passed to C."""

@@ -71,6 +71,9 @@ typedef struct {
 /* ---- memory ---- */
 void orc_csr_free(orc_csr *a);
 void orc_free(void *p);
+/* OpenMP threads of the oracle's row loops (results do not depend on it) */
+void orc_set_threads(int n);
+int orc_get_threads(void);
 
 /* ---- setup steps (each exported for pin tests) ---- */
 int orc_strength(const orc_csr *A, double theta, orc_csr *S);

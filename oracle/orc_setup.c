@@ -298,6 +298,7 @@ void orc_smooth_candidates(const orc_csr *A, double *B, int sweeps, double omega
     int32_t n = A->nrows;
     double *Bn = (double *)orc_xmalloc((size_t)n * sizeof(double));
     for (int s = 0; s < sweeps; s++) {
+#pragma omp parallel for schedule(static)
         for (int32_t i = 0; i < n; i++) {
             double acc = 0.0, d = 0.0;
             for (int32_t e = A->rowptr[i]; e < A->rowptr[i + 1]; e++) {
@@ -415,6 +416,7 @@ int orc_tentative(orc_csr *N, const int32_t *agg, const int32_t *roots, const do
  *   root and unaggregated rows are fixed: u <- 0.
  */
 void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc) {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < W->nrows; i++) {
         int32_t s = W->rowptr[i], e = W->rowptr[i + 1];
         /* fixed rows, and one-entry rows whose constraint space is exactly {0}
@@ -645,6 +647,7 @@ int orc_energy_min_cg_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, co
     for (int64_t q = 0; q < nz; q++) R[q] = -W.val[q];
     double rho_old = 0.0, rho0 = 0.0;
     for (int it = 0; it < sweeps; it++) {
+#pragma omp parallel for schedule(static)
         for (int32_t i = 0; i < P->nrows; i++)
             for (int32_t q = P->rowptr[i]; q < P->rowptr[i + 1]; q++)
                 Z[q] = precond ? R[q] * dinv[i] : R[q];
@@ -656,6 +659,7 @@ int orc_energy_min_cg_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, co
             for (int64_t q = 0; q < nz; q++) Dd[q] = Z[q];
         } else {
             double beta = rho / rho_old;
+#pragma omp parallel for schedule(static)
             for (int64_t q = 0; q < nz; q++) Dd[q] = Z[q] + beta * Dd[q];
         }
         orc_masked_product(A, &Dm, &W);
@@ -663,6 +667,7 @@ int orc_energy_min_cg_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, co
         double dw = frob_dot(P, Dd, W.val);
         if (dw <= 0.0) { it_done = it; break; }
         double alpha = rho / dw;
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < nz; q++) {
             P->val[q] = P->val[q] + alpha * Dd[q];
             R[q] = R[q] - alpha * W.val[q];

@@ -67,6 +67,7 @@ void orc_lu_solve(int n, const double *LU, const int32_t *piv, double *x) {
 
 static void jacobi(const orc_csr *A, const double *diag, const double *b, double *x, double omega, double *tmp) {
     orc_spmv(A, x, tmp);
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < A->nrows; i++) x[i] = x[i] + omega * ((b[i] - tmp[i]) / diag[i]);
 }
 
@@ -86,11 +87,13 @@ void orc_vcycle(const orc_hier *h, int lvl, const double *b, double *x) {
     const int passes = (lvl + 1 == h->nlev - 1 || h->p.gamma < 1) ? 1 : h->p.gamma;
     for (int c = 0; c < passes; c++) {
         orc_spmv(&L->A, x, tmp);
+#pragma omp parallel for schedule(static)
         for (int32_t i = 0; i < n; i++) tmp[i] = b[i] - tmp[i];
         orc_spmv(&L->R, tmp, bc);
         memset(xc, 0, (size_t)nc * sizeof(double));
         orc_vcycle(h, lvl + 1, bc, xc);
         orc_spmv(&L->P, xc, tmp);
+#pragma omp parallel for schedule(static)
         for (int32_t i = 0; i < n; i++) x[i] = x[i] + tmp[i];
     }
     for (int s = 0; s < h->p.nu_post; s++) jacobi(&L->A, L->diag, b, x, h->p.omega, tmp);
@@ -101,6 +104,7 @@ void orc_vcycle(const orc_hier *h, int lvl, const double *b, double *x) {
 
 static double residual(const orc_csr *A, const double *b, const double *x, double *r) {
     orc_spmv(A, x, r);
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < A->nrows; i++) r[i] = b[i] - r[i];
     return orc_nrm2(A->nrows, r);
 }
@@ -132,6 +136,7 @@ int orc_solve(const orc_hier *h, const double *b, double *x, double tol, int max
         for (it = 1; it <= maxit; it++) {
             orc_spmv(A, p, q);
             double alpha = rz / orc_dot(n, p, q);
+#pragma omp parallel for schedule(static)
             for (int32_t i = 0; i < n; i++) {
                 x[i] = x[i] + alpha * p[i];
                 r[i] = r[i] - alpha * q[i];
@@ -143,6 +148,7 @@ int orc_solve(const orc_hier *h, const double *b, double *x, double tol, int max
             double rz_new = orc_dot(n, r, z);
             double beta = rz_new / rz;
             rz = rz_new;
+#pragma omp parallel for schedule(static)
             for (int32_t i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
         }
         if (it > maxit) it = maxit;

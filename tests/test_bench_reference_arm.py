@@ -1,5 +1,6 @@
-"""The benchmark's reference arm (the FP64 CPU oracle) prints one JSON line
-with the contract's keys; run here on a small grid so it takes seconds."""
+"""The benchmark's reference arm (the FP64 CPU oracle, full setup + solve to
+1e-8 every step) prints one JSON line with the contract's keys; run here on a
+small grid so it takes seconds."""
 import json
 import os
 import subprocess
@@ -18,4 +19,8 @@ def test_reference_arm_json_line():
         assert key in line
     assert line["impl"] == "reference" and line["unit"] == "s" and line["higher_is_better"] is False
     assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1
+    # every claimed step was run in full: the timed wall time covers steps x value
+    assert cb["timed_wall_s"] >= 0.9 * line["steps"] * line["value"]
+    assert cb["rel_res"] < 1e-8
