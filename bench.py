@@ -268,6 +268,114 @@ def profile_setup_op(args):
     return 0
 
 
+def grid_rows(rn, torch, dev, stream, flush, peak):
+    """Setup + solve to 1e-8 on the other grids of the workload list, each in
+    FP64 and mixed precision (one warm-up and one timed step, inputs resident,
+    CUDA events, L2 flushed): upwind convection-diffusion on 2048^2 (FGMRES(30)),
+    variable-coefficient FV on 512^2 (CG) and the 64^2 Poisson problem with one
+    right-hand side (stationary V-cycles).  Each record carries the dominant
+    level-0 launch of its solve timed alone (roofline) and the oracle's
+    iteration count for the same settings on all host threads."""
+    from oracle import oracle as O
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    out = {}
+    for key, pr, latency in (("convdiff_2048", PR.convdiff_problem(2048), False),
+                             ("varcoef_512", PR.varcoef_problem(512), False),
+                             ("poisson_64", PR.poisson_problem(64), True)):
+        A = pr.A
+        dA = (t(A.rowptr), t(A.col), t(A.val), t(pr.B.reshape(-1)))
+        Bh = None if pr.Bhat is None else t(pr.Bhat.reshape(-1))
+        b = t(pr.b)
+        x = torch.zeros_like(b)
+        outer = pr.params.get("outer", 1)
+        rec = {"problem": pr.description, "n": A.n_rows, "nnz": A.nnz,
+               "outer": {0: "stationary", 1: "CG", 2: "FGMRES(30)"}[outer],
+               "setup": {k: pr.params[k] for k in ("soc_kind", "soc_theta", "degree", "n_sweeps", "method",
+                                                    "prefilter", "postfilter") if k in pr.params}}
+
+        def step(prec):
+            x.zero_()
+            h = rn.Hierarchy(*dA, Bh, params=rn.params_from_config(pr.params, precision=prec, use_graphs=1),
+                             stream=stream.cuda_stream)
+            info = h.solve(b, x, rtol=1e-8, maxit=5000)
+            h.close()
+            return info
+
+        for name, prec in (("mixed", rn.RN_MIXED), ("fp64", rn.RN_FP64)):
+            step(prec)
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res = float(np.linalg.norm(pr.b - A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(pr.b))
+            rec[name] = {"step_s": e0.elapsed_time(e1) / 1e3, "iters": info["iters"], "rel_res": res}
+        # the solve's level-0 launches timed alone; the longest is the roofline
+        h = rn.Hierarchy(*dA, Bh, params=rn.params_from_config(pr.params, precision=rn.RN_MIXED, use_graphs=1),
+                         stream=stream.cuda_stream)
+        x.zero_()
+        h.solve(b, x, rtol=1e-8, maxit=5000)
+        ops = {}
+        cg_only = (rn.RN_OP_CG_XR, rn.RN_OP_CG_RZ, rn.RN_OP_CG_P)
+        for op in range(rn.RN_OP_COUNT):
+            if outer != 1 and op in cg_only:  # launches of the CG iteration only
+                continue
+            if outer == 1 and op == rn.RN_OP_CG_RZ:  # not issued: the last level-0 sweep carries it
+                continue
+            r = h.time_op(op, reps=20)
+            if r is not None and r[2] > 0:
+                ops[r[0]] = r
+        h.close()
+        nm, us, by = max(ops.values(), key=lambda r: r[1])
+        ach = by / (us * 1e-6) / 1e9
+        rec["roofline"] = {"bound": "hbm", "kernel": nm, "achieved": ach, "peak": peak, "unit": "GB/s",
+                           "frac": ach / peak, "avg_launch_us": us, "algorithmic_bytes": by,
+                           "note": ("latency-bound: the operator (0.3 MB) is L2-resident" if latency else
+                                    "latency-bound: each level-0 launch moves at most ~20 MB" if A.nnz < 2e6 else None)}
+        rec["level0_launches"] = {k: {"us": round(v[1], 2), "GBps": round(v[2] / (v[1] * 1e-6) / 1e9, 1)}
+                                  for k, v in sorted(ops.items(), key=lambda kv: -kv[1][1])}
+        O.set_threads(host_threads())
+        oh = O.Hierarchy(A.to_scipy(), pr.B, Bhat=pr.Bhat, **pr.params)
+        _, oinfo = oh.solve(pr.b, tol=1e-8, maxit=5000, outer=outer, restart=pr.params.get("restart", 30))
+        del oh
+        rec["oracle_iters"] = oinfo["iters"]
+        out[key] = rec
+        del dA, Bh, b, x
+    return out
+
+
+def profile_op(args):
+    """Build the workload's hierarchy and solve once, then run one level-0
+    launch of the solve (rn_time_op index, one run, no flush) between
+    cudaProfilerStart and cudaProfilerStop, for `ncu --profile-from-start
+    off`."""
+    import torch
+
+    from paper_1610_03154_gb300 import rn
+
+    dev = torch.device("cuda", 0)
+    pr = PR.aniso_problem(args.ne)
+    A = pr.A
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    p = rn.params_from_config(pr.params, precision=rn.RN_MIXED if args.precision == "mixed" else rn.RN_FP64,
+                              outer=rn.RN_OUTER_CG)
+    h = rn.Hierarchy(t(A.rowptr), t(A.col), t(A.val), t(pr.B.reshape(-1)), params=p)
+    b = t(pr.b)
+    x = torch.zeros_like(b)
+    h.solve(b, x, rtol=1e-8, maxit=5000)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    r = h.time_op(args.profile_op, reps=1, flush_bytes=0)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    h.close()
+    print(json.dumps({"profile_op": r[0] if r else None, "us": r[1] if r else None, "bytes": r[2] if r else None}))
+    return 0
+
+
 def next_rows(rn, torch, dev, stream, flush, prec):
     """Records for the batched and differentiable forms, each one warm-up
     and one timed pass with device-resident inputs (CUDA events, L2 flushed):
@@ -425,6 +533,8 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="one setup + --profile-iters outer iterations and nothing else (for ncu captures)")
     ap.add_argument("--profile-iters", type=int, default=10)
+    ap.add_argument("--profile-op", type=int, default=-1,
+                    help="run one level-0 solve launch (rn_time_op index) inside a profiler range")
     ap.add_argument("--profile-setup-op", type=int, default=-1,
                     help="run one level-0 setup operation (rn_time_setup_op index) inside a profiler range")
     args = ap.parse_args()
@@ -434,6 +544,8 @@ def main():
         return profile_step(args)
     if args.profile_setup_op >= 0:
         return profile_setup_op(args)
+    if args.profile_op >= 0:
+        return profile_op(args)
 
     import torch
 
@@ -546,6 +658,7 @@ def main():
         hs.close()
     del es, xs_d
     nexts = next_rows(rn, torch, dev, stream, flush, prec)
+    grids = grid_rows(rn, torch, dev, stream, flush, load_peaks()[0])
 
     # per-launch device times of the solve's level-0 operations, each timed in
     # isolation with CUDA events on the hierarchy's stream, a 256 MB read before
@@ -684,6 +797,7 @@ def main():
             "candidates_3": {"step_s": times_k3[0], "iters": infos_k3[0]["iters"], "rel_res": infos_k3[0]["rel_res"],
                              "B": "1, x, y", "precision": prec},
             **nexts,
+            "grids": grids,
             "block_system": {"step_s": es_times[1], "iters": es_infos[1]["iters"], "rel_res": es_infos[1]["rel_res"],
                              "levels": es_levels, "setup_ms": es_setup_ms, "problem": prs.name, "n": prs.A.n_rows, "nnz": prs.A.nnz,
                              "block_size": 2, "B": "3 rigid-body modes", "strength": "classical, theta 0.5",

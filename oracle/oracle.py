@@ -79,8 +79,8 @@ def lib():
         L.orc_enforce_k.argtypes = [P(_CSR), i32p, dp, dp, C.c_int]
         L.orc_energy_min_cg_k.argtypes = [P(_CSR), P(_CSR), i32p, dp, C.c_int, C.c_int, C.c_int, dp]
         L.orc_smooth_candidates_k.argtypes = [P(_CSR), dp, C.c_int, C.c_int, C.c_double]
-        L.orc_sym_pinv.argtypes = [C.c_int, dp, dp]
-        L.orc_sym_pinv.restype = C.c_int
+        L.orc_row_svd.argtypes = [C.c_int, C.c_int, dp, dp, dp]
+        L.orc_row_svd.restype = C.c_int
         L.orc_amalgamate.argtypes = [P(_CSR), C.c_int, P(_CSR)]
         L.orc_aggregate.argtypes = [P(_CSR), C.c_uint64, i32p, P(i32p), i32p]
         L.orc_splitmix64.argtypes = [C.c_uint64]
@@ -248,12 +248,14 @@ def masked_product(A, X) -> sp.csr_matrix:
     return sp.csr_matrix((w.val, w.col, w.rowptr), shape=X.shape)
 
 
-def sym_pinv(G: np.ndarray) -> np.ndarray:
-    G = np.ascontiguousarray(G, np.float64)
-    k = G.shape[0]
-    out = np.zeros((k, k))
-    lib().orc_sym_pinv(k, _dp(G), _dp(out))
-    return out
+def row_svd(M: np.ndarray):
+    """(U, V Sigma^+, rank) of a row's |J| x k matrix Bc_J (orc_row_svd)."""
+    M = np.ascontiguousarray(M, np.float64)
+    n, k = M.shape
+    U = np.zeros((n, k))
+    VS = np.zeros((k, k))
+    rank = lib().orc_row_svd(n, k, _dp(M.reshape(-1)), _dp(U.reshape(-1)), _dp(VS.reshape(-1)))
+    return U, VS, int(rank)
 
 
 def tentative_k(N, agg, roots, rowtype, B):

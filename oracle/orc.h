@@ -95,7 +95,8 @@ int orc_energy_min_cg_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, co
                         int sweeps, int precond, double *energy_trace);
 int orc_energy_min_gmres_k(const orc_csr *A, orc_csr *P, const int32_t *rowtype, const double *Bc, int k,
                            int m, double *res_trace);
-int orc_sym_pinv(int k, const double *G, double *Gp);  /* returns the rank kept */
+/* one-sided Jacobi SVD of a row's len x k Bc_J: U (len x k), V Sigma^+ (k x k); returns the rank kept */
+int orc_row_svd(int len, int k, const double *M, double *U, double *VS);
 /* systems (block size m > 1) */
 int orc_amalgamate(const orc_csr *S, int m, orc_csr *Sm);
 int orc_postfilter_m(const orc_csr *P, const int32_t *agg, const int32_t *rowtype, double theta, int mb,

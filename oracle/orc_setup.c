@@ -442,93 +442,127 @@ void orc_project(orc_csr *W, const int32_t *rowtype, const double *Bc) {
  * pseudo-inverse (min-norm least squares; the system is underdetermined when
  * |J| >= k and Bc_J has full rank).  k = 1 keeps the scalar formulas above. */
 
-/* Pseudo-inverse of a symmetric k x k matrix (k <= ORC_KMAX, row-major) by the
- * cyclic Jacobi eigenvalue method (rotations zeroing one off-diagonal pair at
- * a time until a sweep finds every off-diagonal below 1e-18 of its diagonal
- * pair, at most 16 sweeps); eigenvalues at most
- * 1e-6 of the largest are dropped (singular values of Bc_J below 1e-3 of the
- * largest): candidate combinations that are nearly dependent on a row's
- * pattern stay unfitted, which bounds the fit's amplification by 1e6. */
+/* Row fits from the singular value decomposition of Bc_J (|J| x k), not from
+ * the Gram matrix G_i = Bc_J^T Bc_J: forming G squares the condition number,
+ * so a fit through G carries rounding amplified by kappa(Bc_J)^2, one through
+ * the SVD by kappa(Bc_J).  Singular values at most ORC_SV_CUT of the largest
+ * are dropped (eigenvalues of G_i at most ORC_SV_CUT^2 = 1e-12 of the
+ * largest): candidate combinations a row's pattern carries only below that
+ * stay unfitted (minimal-norm least squares on the rest). */
 #define ORC_KMAX 8
-int orc_sym_pinv(int k, const double *G, double *Gp) {
-    double a[ORC_KMAX * ORC_KMAX], v[ORC_KMAX * ORC_KMAX];
-    for (int i = 0; i < k * k; i++) a[i] = G[i];
+#define ORC_SV_CUT 1e-6
+
+/* One-sided Jacobi SVD (Hestenes) of the len x k matrix M (row-major, k <=
+ * ORC_KMAX): column pairs of W = M V are rotated until every pair is
+ * orthogonal to 1e-15 of its norms (at most 30 sweeps); sigma_a = |W_a|.
+ * On return U (len x k) holds W_a / sigma_a for the kept directions and zero
+ * columns for the dropped ones, VS (k x k, row-major) holds V_a / sigma_a
+ * (zero when dropped).  Returns the number of directions kept. */
+int orc_row_svd(int len, int k, const double *M, double *U, double *VS) {
+    double V[ORC_KMAX * ORC_KMAX];
     for (int i = 0; i < k; i++)
-        for (int j = 0; j < k; j++) v[i * k + j] = (i == j);
-    for (int sweep = 0; sweep < 16; sweep++) {
+        for (int j = 0; j < k; j++) V[i * k + j] = (i == j);
+    for (int i = 0; i < len * k; i++) U[i] = M[i];  /* W, rotated in place */
+    for (int sweep = 0; sweep < 30; sweep++) {
         int rotated = 0;
         for (int p = 0; p < k - 1; p++)
             for (int q = p + 1; q < k; q++) {
-                double apq = a[p * k + q];
-                /* negligible against the diagonal pair (1e-18 relative): no rotation */
-                if (apq * apq <= 1e-36 * fabs(a[p * k + p] * a[q * k + q])) continue;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < len; i++) {
+                    const double wp = U[i * k + p], wq = U[i * k + q];
+                    al += wp * wp;
+                    be += wq * wq;
+                    ga += wp * wq;
+                }
+                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
                 rotated = 1;
-                double th = (a[q * k + q] - a[p * k + p]) / (2.0 * apq);
-                double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-                for (int r = 0; r < k; r++) { /* columns p, q of a */
-                    double arp = a[r * k + p], arq = a[r * k + q];
-                    a[r * k + p] = c * arp - sn * arq;
-                    a[r * k + q] = sn * arp + c * arq;
+                const double ze = (be - al) / (2.0 * ga);
+                const double t = (ze >= 0.0 ? 1.0 : -1.0) / (fabs(ze) + sqrt(ze * ze + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int i = 0; i < len; i++) {
+                    const double wp = U[i * k + p], wq = U[i * k + q];
+                    U[i * k + p] = c * wp - sn * wq;
+                    U[i * k + q] = sn * wp + c * wq;
                 }
-                for (int r = 0; r < k; r++) { /* rows p, q of a */
-                    double apr = a[p * k + r], aqr = a[q * k + r];
-                    a[p * k + r] = c * apr - sn * aqr;
-                    a[q * k + r] = sn * apr + c * aqr;
-                }
-                for (int r = 0; r < k; r++) { /* eigenvectors: columns of v */
-                    double vrp = v[r * k + p], vrq = v[r * k + q];
-                    v[r * k + p] = c * vrp - sn * vrq;
-                    v[r * k + q] = sn * vrp + c * vrq;
+                for (int r = 0; r < k; r++) {
+                    const double vp = V[r * k + p], vq = V[r * k + q];
+                    V[r * k + p] = c * vp - sn * vq;
+                    V[r * k + q] = sn * vp + c * vq;
                 }
             }
-        if (!rotated) break; /* every off-diagonal negligible: converged */
+        if (!rotated) break;
     }
-    double lmax = 0.0;
-    for (int i = 0; i < k; i++) if (fabs(a[i * k + i]) > lmax) lmax = fabs(a[i * k + i]);
-    for (int i = 0; i < k * k; i++) Gp[i] = 0.0;
+    double sig[ORC_KMAX], smax = 0.0;
+    for (int a = 0; a < k; a++) {
+        double ss = 0.0;
+        for (int i = 0; i < len; i++) ss += U[i * k + a] * U[i * k + a];
+        sig[a] = sqrt(ss);
+        if (sig[a] > smax) smax = sig[a];
+    }
     int rank = 0;
-    for (int e = 0; e < k; e++) {
-        double lam = a[e * k + e];
-        if (!(lam > 1e-6 * lmax)) continue;
-        rank++;
-        for (int i = 0; i < k; i++)
-            for (int j = 0; j < k; j++) Gp[i * k + j] += v[i * k + e] * v[j * k + e] / lam;
+    for (int a = 0; a < k; a++) {
+        const int keep = sig[a] > ORC_SV_CUT * smax;
+        rank += keep;
+        for (int i = 0; i < len; i++) U[i * k + a] = keep ? U[i * k + a] / sig[a] : 0.0;
+        for (int r = 0; r < k; r++) VS[r * k + a] = keep ? V[r * k + a] / sig[a] : 0.0;
     }
     return rank;
 }
 
 /* Min-norm update of one row's values t (pattern columns col[s..e)) so that
- * (t + u) Bc_J = target (target NULL: 0):  r = target - t Bc_J,
- * u_j = (r G_i^+) . Bc_j.  With target NULL (the projection) a row whose
- * pattern has no more entries than the rank of Bc_J is fixed by the
- * constraints and set to exactly 0, as a one-entry row is for k = 1. */
+ * (t + u) Bc_J = target, by least squares on the kept directions of Bc_J =
+ * U Sigma V^T (eq. Tproj):
+ *   target given: r = target - t Bc_J, u = (r V Sigma^+) U^T;
+ *   target NULL (the projection onto {u : u Bc_J = 0}): t <- t - (t U) U^T,
+ *   and a row whose pattern has no more entries than the rank of Bc_J is
+ *   fixed by the constraints and set to exactly 0, as a one-entry row is for
+ *   k = 1. */
+#define ORC_FIT_STACK 64
 static void row_fit_k(int32_t s, int32_t e, const int32_t *col, double *val, const double *target,
                       const double *Bc, int k) {
-    double G[ORC_KMAX * ORC_KMAX] = {0}, Gp[ORC_KMAX * ORC_KMAX], r[ORC_KMAX], y[ORC_KMAX];
-    for (int a = 0; a < k; a++) r[a] = target ? target[a] : 0.0;
-    for (int32_t q = s; q < e; q++) {
-        const double *b = Bc + (size_t)col[q] * k;
+    const int len = e - s;
+    if (len <= 0) return;
+    double Ms[ORC_FIT_STACK * ORC_KMAX], Us[ORC_FIT_STACK * ORC_KMAX], VS[ORC_KMAX * ORC_KMAX];
+    double *M = Ms, *U = Us;
+    if (len > ORC_FIT_STACK) {
+        M = (double *)orc_xmalloc((size_t)len * k * sizeof(double));
+        U = (double *)orc_xmalloc((size_t)len * k * sizeof(double));
+    }
+    for (int q = 0; q < len; q++)
+        for (int a = 0; a < k; a++) M[q * k + a] = Bc[(size_t)col[s + q] * k + a];
+    const int rank = orc_row_svd(len, k, M, U, VS);
+    double c[ORC_KMAX];
+    if (!target) {
+        if (rank >= len) {  /* the constraints fix the row: its constraint space is {0} */
+            for (int q = 0; q < len; q++) val[s + q] = 0.0;
+        } else {
+            for (int a = 0; a < k; a++) {
+                c[a] = 0.0;
+                for (int q = 0; q < len; q++) c[a] += val[s + q] * U[q * k + a];
+            }
+            for (int q = 0; q < len; q++) {
+                double u = 0.0;
+                for (int a = 0; a < k; a++) u += c[a] * U[q * k + a];
+                val[s + q] = val[s + q] - u;
+            }
+        }
+    } else {
+        double r[ORC_KMAX];
+        for (int b = 0; b < k; b++) {
+            r[b] = target[b];
+            for (int q = 0; q < len; q++) r[b] = r[b] - val[s + q] * M[q * k + b];
+        }
         for (int a = 0; a < k; a++) {
-            r[a] = r[a] - val[q] * b[a];
-            for (int c = 0; c < k; c++) G[a * k + c] += b[a] * b[c];
+            c[a] = 0.0;
+            for (int b = 0; b < k; b++) c[a] += r[b] * VS[b * k + a];
+        }
+        for (int q = 0; q < len; q++) {
+            double u = 0.0;
+            for (int a = 0; a < k; a++) u += c[a] * U[q * k + a];
+            val[s + q] = val[s + q] + u;
         }
     }
-    const int rank = orc_sym_pinv(k, G, Gp);
-    if (!target && rank >= e - s) {  /* the constraints fix the row: its constraint space is {0} */
-        for (int32_t q = s; q < e; q++) val[q] = 0.0;
-        return;
-    }
-    for (int c = 0; c < k; c++) {
-        y[c] = 0.0;
-        for (int a = 0; a < k; a++) y[c] += r[a] * Gp[a * k + c];
-    }
-    for (int32_t q = s; q < e; q++) {
-        const double *b = Bc + (size_t)col[q] * k;
-        double u = 0.0;
-        for (int c = 0; c < k; c++) u += y[c] * b[c];
-        val[q] = val[q] + u;
-    }
+    if (M != Ms) { free(M); free(U); }
 }
 
 void orc_smooth_candidates_k(const orc_csr *A, double *B, int k, int sweeps, double omega) {
@@ -568,6 +602,7 @@ int orc_tentative_k(orc_csr *N, const int32_t *agg, const int32_t *roots, const 
 
 void orc_project_k(orc_csr *W, const int32_t *rowtype, const double *Bc, int k) {
     if (k == 1) { orc_project(W, rowtype, Bc); return; }
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < W->nrows; i++) {
         int32_t s = W->rowptr[i], e = W->rowptr[i + 1];
         if (rowtype[i] != ORC_FREE || e - s == 1) {

@@ -145,7 +145,7 @@ struct EmCtx {
     double *rs2 = nullptr;  // n rows: the row projection's scales (allocated internally when null)
     bool fp32 = false;      // CG sweeps in FP32 (mixed precision); workspaces then allocated internally
     int k = 1;              // candidates (Bc is nc x k); k > 1 projects with per-row Gram pseudo-inverses
-    const double *gp64 = nullptr;     // k > 1: G_i^+ already formed on N and Bc (else formed inside)
+    const double *u64 = nullptr;      // k > 1: U of every row's Bc_J already formed on N (else formed inside)
     const int32_t *zero_row = nullptr;
     // true: every product scans the pattern rows (energy_product_kernel) and
     // no gather map is built; with R, Dd, W, rs2 supplied, k = 1 and FP64

@@ -324,147 +324,105 @@ __global__ void gather_k_kernel(int32_t nc, int k, const int32_t *__restrict__ r
     }
 }
 
-// Pseudo-inverse of the symmetric K x K matrix g (row-major, overwritten)
-// into gp: eigen-decomposition by cyclic Jacobi rotations (each zeroes one
-// off-diagonal pair; sweeps until a whole sweep finds every off-diagonal
-// below 1e-18 of its diagonal pair, at most 16), with
-// eigenvalues at most 1e-6 of the largest dropped: candidate combinations
-// nearly dependent on a row's pattern stay unfitted, bounding the fit's
-// amplification of rounding by 1e6.  K is a template argument so that the
-// matrices stay in registers.  Returns the number of eigenvalues kept.
-template <int K>
-__device__ int sym_pinv_dev(double (&g)[K * K], double (&gp)[K * K]) {
-    double v[K * K];
-#pragma unroll
-    for (int i = 0; i < K; i++)
-#pragma unroll
-        for (int j = 0; j < K; j++) v[i * K + j] = (i == j) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 16; sweep++) {
-        bool rotated = false;
-#pragma unroll
-        for (int p = 0; p < K - 1; p++)
-#pragma unroll
-            for (int q = p + 1; q < K; q++) {
-                const double apq = g[p * K + q];
-                // negligible against the diagonal pair (1e-18 relative): no rotation
-                if (apq * apq <= 1e-36 * fabs(g[p * K + p] * g[q * K + q])) continue;
-                rotated = true;
-                const double th = (g[q * K + q] - g[p * K + p]) / (2.0 * apq);
-                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-#pragma unroll
-                for (int r = 0; r < K; r++) {
-                    const double x = g[r * K + p], y = g[r * K + q];
-                    g[r * K + p] = c * x - sn * y;
-                    g[r * K + q] = sn * x + c * y;
-                }
-#pragma unroll
-                for (int r = 0; r < K; r++) {
-                    const double x = g[p * K + r], y = g[q * K + r];
-                    g[p * K + r] = c * x - sn * y;
-                    g[q * K + r] = sn * x + c * y;
-                }
-#pragma unroll
-                for (int r = 0; r < K; r++) {
-                    const double x = v[r * K + p], y = v[r * K + q];
-                    v[r * K + p] = c * x - sn * y;
-                    v[r * K + q] = sn * x + c * y;
-                }
-            }
-        if (!rotated) break;  // every off-diagonal negligible: converged
-    }
-    double lmax = 0.0;
-#pragma unroll
-    for (int i = 0; i < K; i++) lmax = fmax(lmax, fabs(g[i * K + i]));
-#pragma unroll
-    for (int i = 0; i < K * K; i++) gp[i] = 0.0;
-    int rank = 0;
-#pragma unroll
-    for (int e = 0; e < K; e++) {
-        const double lam = g[e * K + e];
-        if (!(lam > 1e-6 * lmax)) continue;
-        rank++;
-        const double il = 1.0 / lam;
-#pragma unroll
-        for (int i = 0; i < K; i++)
-#pragma unroll
-            for (int j = 0; j < K; j++) gp[i * K + j] += v[i * K + e] * v[j * K + e] * il;
-    }
-    return rank;
-}
+// k > 1 candidates (Sec. 3.6, eq. Tproj): every row fit works from the
+// singular value decomposition Bc_J = U Sigma V^T of the row's |J| x k block
+// of candidates, not from the Gram matrix Bc_J^T Bc_J, whose formation would
+// square the condition number that multiplies rounding.  Singular values at
+// most kSvCut of the largest are dropped (Gram eigenvalues at most 1e-12 of
+// the largest): combinations the pattern carries only below that stay
+// unfitted (minimal-norm least squares on the rest).
+constexpr double kSvCut = 1e-6;
 
-// G_i^+ of every row's Gram matrix G_i = Bc_J^T Bc_J on its pattern J, and
-// whether the constraints fix the row (no more pattern entries than the rank
-// of Bc_J: constraint space {0}, like a one-entry row for k = 1); fixed,
-// one-entry and such rows are projected to exactly 0.
+// One-sided Jacobi SVD (Hestenes) of every free row's Bc_J, thread per row:
+// the columns of W = Bc_J V are rotated in U (the row's |J| x k slice,
+// pattern-entry major) until every pair is orthogonal to 1e-15 of its norms
+// (at most 30 sweeps).  On return U holds W_a / sigma_a for the kept
+// directions (zero columns for dropped ones), VS (k x k per row) V_a /
+// sigma_a, and zero_row marks rows whose constraints fix them (no more
+// pattern entries than the rank kept; one-entry rows): those are projected to
+// exactly 0, like a one-entry row for k = 1.
 template <int K>
-__global__ void gram_pinv_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                 const int32_t *__restrict__ rowtype, const double *__restrict__ Bc,
-                                 double *__restrict__ Gp, int32_t *__restrict__ zero_row) {
+__global__ void row_svd_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                               const int32_t *__restrict__ rowtype, const double *__restrict__ Bc,
+                               double *__restrict__ U, double *__restrict__ VS, int32_t *__restrict__ zero_row) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double g[K * K] = {}, gp[K * K] = {};
-        const int32_t len = rp[i + 1] - rp[i];
-        int z = 1;
-        if (rowtype[i] == FREE_ROW && len >= 1) {  // G_i^+ of one-entry rows too: the row fits use it
-            for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
-                const double *b = Bc + (int64_t)col[e] * K;
+        const int32_t s0 = rp[i], len = rp[i + 1] - s0;
+        double *W = U + (int64_t)s0 * K;
+        double v[K * K];
 #pragma unroll
-                for (int a = 0; a < K; a++)
+        for (int a = 0; a < K; a++)
 #pragma unroll
-                    for (int c = 0; c < K; c++) g[a * K + c] += b[a] * b[c];
+            for (int c = 0; c < K; c++) v[a * K + c] = (a == c) ? 1.0 : 0.0;
+        const bool free_row = rowtype[i] == FREE_ROW && len >= 1;
+        for (int32_t q = 0; q < len; q++)
+#pragma unroll
+            for (int a = 0; a < K; a++) W[(int64_t)q * K + a] = free_row ? Bc[(int64_t)col[s0 + q] * K + a] : 0.0;
+        int rank = 0;
+        if (free_row) {
+            for (int sweep = 0; sweep < 30; sweep++) {
+                bool rotated = false;
+#pragma unroll
+                for (int p = 0; p < K - 1; p++)
+#pragma unroll
+                    for (int r = p + 1; r < K; r++) {
+                        double al = 0.0, be = 0.0, ga = 0.0;
+                        for (int32_t q = 0; q < len; q++) {
+                            const double wp = W[(int64_t)q * K + p], wr = W[(int64_t)q * K + r];
+                            al += wp * wp;
+                            be += wr * wr;
+                            ga += wp * wr;
+                        }
+                        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                        rotated = true;
+                        const double ze = (be - al) / (2.0 * ga);
+                        const double t = (ze >= 0.0 ? 1.0 : -1.0) / (fabs(ze) + sqrt(ze * ze + 1.0));
+                        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                        for (int32_t q = 0; q < len; q++) {
+                            const double wp = W[(int64_t)q * K + p], wr = W[(int64_t)q * K + r];
+                            W[(int64_t)q * K + p] = c * wp - sn * wr;
+                            W[(int64_t)q * K + r] = sn * wp + c * wr;
+                        }
+#pragma unroll
+                        for (int x = 0; x < K; x++) {
+                            const double vp = v[x * K + p], vr = v[x * K + r];
+                            v[x * K + p] = c * vp - sn * vr;
+                            v[x * K + r] = sn * vp + c * vr;
+                        }
+                    }
+                if (!rotated) break;
             }
-            const int rank = sym_pinv_dev<K>(g, gp);
-            z = len > 1 ? rank >= len : 1;
+            double sig[K], smax = 0.0;
+#pragma unroll
+            for (int a = 0; a < K; a++) {
+                double ss = 0.0;
+                for (int32_t q = 0; q < len; q++) ss += W[(int64_t)q * K + a] * W[(int64_t)q * K + a];
+                sig[a] = sqrt(ss);
+                smax = fmax(smax, sig[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < K; a++) {
+                const bool keep = sig[a] > kSvCut * smax;
+                rank += keep ? 1 : 0;
+                const double is = keep ? 1.0 / sig[a] : 0.0;
+                for (int32_t q = 0; q < len; q++) W[(int64_t)q * K + a] = keep ? W[(int64_t)q * K + a] * is : 0.0;
+#pragma unroll
+                for (int x = 0; x < K; x++) v[x * K + a] = keep ? v[x * K + a] * is : 0.0;
+            }
         }
 #pragma unroll
-        for (int q = 0; q < K * K; q++) Gp[(int64_t)i * K * K + q] = gp[q];
-        zero_row[i] = z;
+        for (int x = 0; x < K * K; x++) VS[(int64_t)i * K * K + x] = free_row ? v[x] : 0.0;
+        zero_row[i] = free_row ? (len <= 1 || rank >= len) : 1;
     }
 }
 
 // Minimal-norm fit of every free row (eq. Tproj): (t + u) Bc_J = B_i with
-// u_j = ((B_i - t Bc_J) G_i^+) . Bc_j; T's construction and enforce for k > 1.
+// r = B_i - t Bc_J and u = (r V Sigma^+) U^T, from row_svd_kernel on the same
+// pattern and Bc; T's construction and enforce for k > 1.
 template <int K>
-__global__ void row_fit_k_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+__global__ void row_fit_u_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                  double *__restrict__ val, const int32_t *__restrict__ rowtype,
-                                 const double *__restrict__ B, const double *__restrict__ Bc) {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (rowtype[i] != FREE_ROW) continue;
-        double g[K * K] = {}, gp[K * K], r[K], y[K];
-#pragma unroll
-        for (int a = 0; a < K; a++) r[a] = B[(int64_t)i * K + a];
-        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
-            const double *b = Bc + (int64_t)col[e] * K;
-#pragma unroll
-            for (int a = 0; a < K; a++) {
-                r[a] -= val[e] * b[a];
-#pragma unroll
-                for (int c = 0; c < K; c++) g[a * K + c] += b[a] * b[c];
-            }
-        }
-        sym_pinv_dev<K>(g, gp);
-#pragma unroll
-        for (int c = 0; c < K; c++) {
-            y[c] = 0.0;
-#pragma unroll
-            for (int a = 0; a < K; a++) y[c] += r[a] * gp[a * K + c];
-        }
-        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
-            const double *b = Bc + (int64_t)col[e] * K;
-            double u = 0.0;
-#pragma unroll
-            for (int c = 0; c < K; c++) u += y[c] * b[c];
-            val[e] += u;
-        }
-    }
-}
-
-// The same fit with G_i^+ from gram_pinv_kernel on the same pattern and Bc.
-template <int K>
-__global__ void row_fit_gp_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                  double *__restrict__ val, const int32_t *__restrict__ rowtype,
-                                  const double *__restrict__ B, const double *__restrict__ Bc,
-                                  const double *__restrict__ Gp) {
+                                 const double *__restrict__ B, const double *__restrict__ Bc,
+                                 const double *__restrict__ U, const double *__restrict__ VS) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (rowtype[i] != FREE_ROW) continue;
         double r[K], y[K];
@@ -475,19 +433,19 @@ __global__ void row_fit_gp_kernel(int32_t n, const int32_t *__restrict__ rp, con
 #pragma unroll
             for (int a = 0; a < K; a++) r[a] -= val[e] * b[a];
         }
-        const double *gp = Gp + (int64_t)i * K * K;
+        const double *vs = VS + (int64_t)i * K * K;
 #pragma unroll
         for (int c = 0; c < K; c++) {
             y[c] = 0.0;
 #pragma unroll
-            for (int a = 0; a < K; a++) y[c] += r[a] * gp[a * K + c];
+            for (int a = 0; a < K; a++) y[c] += r[a] * vs[a * K + c];
         }
         for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
-            const double *b = Bc + (int64_t)col[e] * K;
-            double u = 0.0;
+            const double *u = U + (int64_t)e * K;
+            double d = 0.0;
 #pragma unroll
-            for (int c = 0; c < K; c++) u += y[c] * b[c];
-            val[e] += u;
+            for (int c = 0; c < K; c++) d += y[c] * u[c];
+            val[e] += d;
         }
     }
 }
@@ -716,14 +674,15 @@ __global__ void tentative_kernel(int32_t n, const int32_t *__restrict__ rp, cons
 }
 
 // ------------------------------------------------------------------ k > 1: the row projection as a pass
-// W <- scale (W - (c G_i^+) Bc_J) with c = W_i Bc_J on every free row of more
-// than one entry (eq. Tproj with a zero right-hand side); the product kernels
-// ran unprojected (their row scales are zero).  <Y, W> finishes in Fin.
+// W <- scale (W - (W_i U) U^T) on every free row that the constraints do not
+// fix (eq. Tproj with a zero right-hand side, through the orthonormal basis U
+// of the range of Bc_J: no division by a singular value), rows they fix <- 0;
+// the product kernels ran unprojected (their row scales are zero).  <Y, W>
+// finishes in Fin.
 template <typename TV, int K>
 __global__ void __launch_bounds__(256)
-proj_k_kernel(int32_t n, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
-              const int32_t *__restrict__ zero_row, const TV *__restrict__ Bc, const TV *__restrict__ Gp,
-              TV *__restrict__ W, TV scale, const TV *__restrict__ Y, Fin fin) {
+proj_k_kernel(int32_t n, const int32_t *__restrict__ nrp, const int32_t *__restrict__ zero_row,
+              const TV *__restrict__ U, TV *__restrict__ W, TV scale, const TV *__restrict__ Y, Fin fin) {
     __shared__ double s_red[32];
     TV dot = TV(0);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -732,23 +691,18 @@ proj_k_kernel(int32_t n, const int32_t *__restrict__ nrp, const int32_t *__restr
             for (int32_t q = cs; q < ce; q++) W[q] = TV(0);
             continue;
         }
-        TV c[K] = {}, y[K] = {};
+        TV c[K] = {};
         for (int32_t q = cs; q < ce; q++) {
-            const TV *b = Bc + (int64_t)ncol[q] * K;
+            const TV *u = U + (int64_t)q * K;
 #pragma unroll
-            for (int a = 0; a < K; a++) c[a] = fma(W[q], b[a], c[a]);
+            for (int a = 0; a < K; a++) c[a] = fma(W[q], u[a], c[a]);
         }
-        const TV *g = Gp + (int64_t)i * K * K;
-#pragma unroll
-        for (int b = 0; b < K; b++)
-#pragma unroll
-            for (int a = 0; a < K; a++) y[b] = fma(c[a], g[a * K + b], y[b]);
         for (int32_t q = cs; q < ce; q++) {
-            const TV *b = Bc + (int64_t)ncol[q] * K;
-            TV u = TV(0);
+            const TV *u = U + (int64_t)q * K;
+            TV d = TV(0);
 #pragma unroll
-            for (int a = 0; a < K; a++) u = fma(y[a], b[a], u);
-            const TV w = scale * (W[q] - u);
+            for (int a = 0; a < K; a++) d = fma(c[a], u[a], d);
+            const TV w = scale * (W[q] - d);
             W[q] = w;
             if (Y) dot = fma(Y[q], w, dot);
         }
@@ -757,51 +711,49 @@ proj_k_kernel(int32_t n, const int32_t *__restrict__ nrp, const int32_t *__restr
     grid_finish<256, 1>(d, fin, s_red);
 }
 
-// Per-minimisation data of the k > 1 projection: G_i^+ (FP64, rounded for
-// FP32 sweeps) and Bc in the sweeps' type.
+// Per-minimisation data of the k > 1 projection: U on the pattern (FP64, or
+// rounded for FP32 sweeps) and the rows the constraints fix.
 template <typename TV>
 struct KProj {
     int k = 1;
-    DVec<double> gp64;
+    DVec<double> u64, vs_own;
     DVec<int32_t> zero_row_own;
-    DVec<TV> gpv, bcv;
-    const TV *gp = nullptr, *bc = nullptr;
+    DVec<TV> uv;
+    const TV *u = nullptr;
     const int32_t *zero_row = nullptr;
-    // pre_gp / pre_zr: G_i^+ and the fixed-row flags already formed on this
-    // pattern and Bc (gram_pinv_kernel), or null to form them here
+    // pre_u / pre_zr: U and the fixed-row flags already formed on this
+    // pattern and Bc (row_svd_kernel), or null to form them here
     void build(int k_, const Pattern &N, const int32_t *rowtype, const double *Bc, cudaStream_t s,
-               const double *pre_gp = nullptr, const int32_t *pre_zr = nullptr) {
+               const double *pre_u = nullptr, const int32_t *pre_zr = nullptr) {
         k = k_;
         if (k == 1) return;
-        const double *g64 = pre_gp;
+        const double *U64 = pre_u;
         zero_row = pre_zr;
-        if (!pre_gp || !pre_zr) {
-            gp64.alloc((size_t)N.n * k * k, s);
+        if (!pre_u || !pre_zr) {
+            u64.alloc((size_t)std::max<int64_t>(N.nnz, 1) * k, s);
+            vs_own.alloc((size_t)N.n * k * k, s);
             zero_row_own.alloc(N.n, s);
-            RN_K_SWITCH(k, RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 8.0 * k * N.nnz + 8.0 * k * k * N.n, s,
-                                     gram_pinv_kernel<KK>, grid_for(N.n, 256), 256, 0, N.n, N.rp, N.col, rowtype,
-                                     Bc, gp64.p, zero_row_own.p));
-            g64 = gp64.p;
+            RN_K_SWITCH(k, RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 16.0 * k * N.nnz + 8.0 * k * k * N.n, s,
+                                     row_svd_kernel<KK>, grid_for(N.n, 256), 256, 0, N.n, N.rp, N.col, rowtype, Bc,
+                                     u64.p, vs_own.p, zero_row_own.p));
+            U64 = u64.p;
             zero_row = zero_row_own.p;
         }
         if constexpr (sizeof(TV) == 4) {
-            gpv.alloc((size_t)N.n * k * k, s);
-            bcv.alloc((size_t)N.nc * k, s);
-            to_float(g64, gpv.p, (int64_t)N.n * k * k, s);
-            to_float(Bc, bcv.p, (int64_t)N.nc * k, s);
-            gp = gpv.p;
-            bc = bcv.p;
+            uv.alloc((size_t)std::max<int64_t>(N.nnz, 1) * k, s);
+            to_float(U64, uv.p, (int64_t)N.nnz * k, s);
+            u = uv.p;
         } else {
-            gp = g64;
-            bc = Bc;
+            u = U64;
         }
     }
     void apply(const Pattern &N, const int32_t *rowtype, TV *W, double scale, const TV *Y, const Fin &f,
                cudaStream_t s) const {
+        (void)rowtype;
         RN_K_SWITCH(k, {
             const int g = grid_resident(proj_k_kernel<TV, KK>, 256, 0, N.n, 256, kReduceBlocks);
-            RN_LAUNCH("energy_masked_product", (2.0 * sizeof(TV) + 4.0 + sizeof(TV) * k) * N.nnz, s,
-                      (proj_k_kernel<TV, KK>), g, 256, 0, N.n, N.rp, N.col, zero_row, bc, gp, W, (TV)scale, Y, f);
+            RN_LAUNCH("energy_masked_product", (2.0 * sizeof(TV) + sizeof(TV) * k) * N.nnz + 8.0 * N.n, s,
+                      (proj_k_kernel<TV, KK>), g, 256, 0, N.n, N.rp, zero_row, u, W, (TV)scale, Y, f);
         });
     }
 };
@@ -1294,7 +1246,7 @@ struct CgSweep {
         fill_i32(c.fl, 0, 1, s);
         rs2 = c.rs2;
         if (!rs2) { Sv.alloc(N.n, s); rs2 = Sv.p; }
-        kp.build(c.k, N, rowtype, Bc, s, c.gp64, c.zero_row);
+        kp.build(c.k, N, rowtype, Bc, s, c.u64, c.zero_row);
         if (c.k == 1) proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);  // FP64
         else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
         pa.rowtype = rowtype;
@@ -1457,7 +1409,7 @@ static void energy_min_gmres_t(const EmCtx &c, const CsrView &A, const Pattern &
     DVec<double> Sv(c.rs2 ? 0 : N.n, s);
     double *rs2 = c.rs2 ? c.rs2 : Sv.p;
     KProj<TV> kp;
-    kp.build(c.k, N, rowtype, Bc, s, c.gp64, c.zero_row);
+    kp.build(c.k, N, rowtype, Bc, s, c.u64, c.zero_row);
     if (c.k == 1) proj_scales(N.n, N.rp, N.col, N.nnz, rowtype, Bc, rs2, s);
     else fill_f64(rs2, 0.0, N.n, s);  // products unprojected; the k-projection pass follows each
     ProjArgsT<TV> pa{rowtype, nullptr, nullptr};
@@ -1621,20 +1573,21 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
     else
         RN_LAUNCH("tentative", 16.0 * N.nnz + 16.0 * n, s, tentative_kernel, rows_grid(n), kT, 0, n, N.rowptr.p,
                   N.col.p, agg, Bsm, Bc, Pout.val.p, k);
-    // k > 1: every row's G_i^+ on N, formed once for the row fits and the minimisation's projection
-    DVec<double> gpN;
+    // k > 1: every row's SVD of Bc_J on N, formed once for the row fits and the minimisation's projection
+    DVec<double> uN, vsN;
     DVec<int32_t> zrN;
     if (k > 1) {
-        gpN.alloc((size_t)n * k * k, s);
+        uN.alloc((size_t)std::max<int64_t>(N.nnz, 1) * k, s);
+        vsN.alloc((size_t)n * k * k, s);
         zrN.alloc(n, s);
-        RN_K_SWITCH(k, RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 8.0 * k * N.nnz + 8.0 * k * k * n, s,
-                                 gram_pinv_kernel<KK>, rows_grid(n), kT, 0, n, N.rowptr.p, N.col.p, rowtype, Bc,
-                                 gpN.p, zrN.p));
+        RN_K_SWITCH(k, RN_LAUNCH("energy_proj_scale", 4.0 * N.nnz + 16.0 * k * N.nnz + 8.0 * k * k * n, s,
+                                 row_svd_kernel<KK>, rows_grid(n), kT, 0, n, N.rowptr.p, N.col.p, rowtype, Bc, uN.p,
+                                 vsN.p, zrN.p));
     }
     if (k > h.mb)  // the other candidates: minimal-norm row fits (eq. Tproj)
-        RN_K_SWITCH(k, RN_LAUNCH("tentative", 12.0 * N.nnz + 8.0 * k * (N.nnz + n) + 8.0 * k * k * n, s,
-                                 row_fit_gp_kernel<KK>, rows_grid(n), kT, 0, n, Pout.rowptr.p, Pout.col.p, Pout.val.p,
-                                 rowtype, Bsm, Bc, gpN.p));
+        RN_K_SWITCH(k, RN_LAUNCH("tentative", 12.0 * N.nnz + 8.0 * k * (2.0 * N.nnz + n) + 8.0 * k * k * n, s,
+                                 row_fit_u_kernel<KK>, rows_grid(n), kT, 0, n, Pout.rowptr.p, Pout.col.p, Pout.val.p,
+                                 rowtype, Bsm, Bc, uN.p, vsN.p));
     if (Tkeep) {
         Tkeep->n = n; Tkeep->m = nc; Tkeep->nnz = N.nnz;
         Tkeep->rowptr.alloc(n + 1, s); Tkeep->col.alloc(N.nnz, s); Tkeep->val.alloc(N.nnz, s);
@@ -1647,7 +1600,7 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
     reciprocal(diag, dinv.p, n, s);
     {
         EmCtx c = ctx_of(h);
-        c.gp64 = gpN.p;  // the same pattern and Bc
+        c.u64 = uN.p;  // the same pattern and Bc
         c.zero_row = zrN.p;
         energy_min(c, A, pat, Pout.val.p, rowtype, Bc, dinv.p, h.p.n_sweeps);
     }
@@ -1668,9 +1621,16 @@ static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, con
         if (k == 1)
             RN_LAUNCH("enforce", 28.0 * F.nnz + 8.0 * n, s, enforce_kernel, rows_grid(n), kT, 0, n, F.rowptr.p,
                       F.col.p, F.val.p, rowtype, Bsm, Bc);
-        else
-            RN_K_SWITCH(k, RN_LAUNCH("enforce", 12.0 * F.nnz + 8.0 * k * (F.nnz + n), s, row_fit_k_kernel<KK>,
-                                     rows_grid(n), kT, 0, n, F.rowptr.p, F.col.p, F.val.p, rowtype, Bsm, Bc));
+        else {  // the fit on the filtered pattern, from that pattern's SVD of Bc_J
+            DVec<double> uF((size_t)std::max<int64_t>(F.nnz, 1) * k, s), vsF((size_t)n * k * k, s);
+            DVec<int32_t> zrF(n, s);
+            RN_K_SWITCH(k, RN_LAUNCH("enforce", 4.0 * F.nnz + 16.0 * k * F.nnz + 8.0 * k * k * n, s,
+                                     row_svd_kernel<KK>, rows_grid(n), kT, 0, n, F.rowptr.p, F.col.p, rowtype, Bc,
+                                     uF.p, vsF.p, zrF.p));
+            RN_K_SWITCH(k, RN_LAUNCH("enforce", 12.0 * F.nnz + 8.0 * k * (2.0 * F.nnz + n) + 8.0 * k * k * n, s,
+                                     row_fit_u_kernel<KK>, rows_grid(n), kT, 0, n, F.rowptr.p, F.col.p, F.val.p,
+                                     rowtype, Bsm, Bc, uF.p, vsF.p));
+        }
         Pout = std::move(F);
         Pattern pf{n, nc, Pout.nnz, Pout.rowptr.p, Pout.col.p};
         energy_min(ctx_of(h), A, pf, Pout.val.p, rowtype, Bc, dinv.p, 1);

@@ -560,16 +560,21 @@ def test_solve_matches_direct_solver(oracle, outer):
 
 
 def test_nonsymmetric_solve_gmres(oracle):
-    pr = PR.convdiff_problem(32)
+    # R^T is built from A^T on the same pattern and roots: without a
+    # post-filter (which drops entries of P and R^T by their own values) R^T
+    # has P's pattern
+    pr = PR.convdiff_problem(32, params=PR.PARAMS_CONVDIFF_RN1)
     h = oracle.Hierarchy(pr.A.to_scipy(), pr.B, Bhat=pr.Bhat, **pr.params)
     assert len(h.levels) >= 2
     L = h.levels[0]
-    # R^T is built from A^T on the same pattern and roots: R^T has P's pattern
-    assert np.array_equal(L.R.T.tocsr().indptr, L.P.indptr)
-    x, info = h.solve(pr.b, tol=1e-8, outer=2, restart=30)
+    Rt = L.R.T.tocsr()
+    assert np.array_equal(Rt.indptr, L.P.indptr) and np.array_equal(Rt.indices, L.P.indices)
     A = pr.A.to_scipy()
-    assert info["status"] == 0
-    assert np.linalg.norm(pr.b - A @ x) / np.linalg.norm(pr.b) < 1e-8
+    for params in (PR.PARAMS_CONVDIFF_RN1, PR.PARAMS_CONVDIFF):
+        h = oracle.Hierarchy(A, pr.B, Bhat=pr.Bhat, **params)
+        x, info = h.solve(pr.b, tol=1e-8, outer=2, restart=30)
+        assert info["status"] == 0
+        assert np.linalg.norm(pr.b - A @ x) / np.linalg.norm(pr.b) < 1e-8
 
 
 def test_one_level_hierarchy_is_exact(oracle):
@@ -770,14 +775,34 @@ def test_w_cycle_differs_from_v_and_converges_faster(oracle):
 
 # --------------------------------------------------------------------------- k > 1 candidates (NEXT-3)
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
-def test_sym_pinv_matches_numpy(oracle, k):
+def test_row_svd_matches_numpy(oracle, k):
+    """The row SVD against LAPACK's: U U^T is the projector onto the kept range
+    (unique), V Sigma^+ U^T is numpy's pseudo-inverse with singular values at
+    most 1e-6 of the largest dropped, and the rank matches; rows of every rank,
+    badly scaled, and nearly dependent columns (condition 1e4 and 1e8, the
+    latter past the cutoff)."""
     rng = np.random.default_rng(k)
+    cases = []
     for rank in range(0, k + 1):
-        M = rng.standard_normal((k, rank))
-        G = M @ M.T * 10.0 ** rng.uniform(-3, 3)
-        ref = np.linalg.pinv(G, rcond=1e-6, hermitian=True)  # the oracle drops eigenvalues <= 1e-6 of the largest
-        got = oracle.sym_pinv(G)
-        assert np.allclose(got, ref, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(ref).max()))
+        for length in (k, k + 3, 17):
+            M = rng.standard_normal((length, rank)) @ rng.standard_normal((rank, k))
+            cases.append(M * 10.0 ** rng.uniform(-3, 3))
+    if k > 1:
+        for cond in (1e4, 1e8):
+            Q1, _ = np.linalg.qr(rng.standard_normal((9, k)))
+            Q2, _ = np.linalg.qr(rng.standard_normal((k, k)))
+            cases.append(Q1 @ np.diag(np.logspace(0, -np.log10(cond), k)) @ Q2)
+    for M in cases:
+        U, VS, rank = oracle.row_svd(M)
+        sv = np.linalg.svd(M, compute_uv=False)
+        keep = int(np.sum(sv > 1e-6 * sv[0])) if sv.size and sv[0] > 0 else 0
+        assert rank == keep
+        ref = np.linalg.pinv(M, rcond=1e-6)  # k x |J|
+        got = VS @ U.T
+        assert np.allclose(got, ref, rtol=1e-8, atol=1e-10 * max(1.0, np.abs(ref).max()))
+        Uc, _, _ = np.linalg.svd(M, full_matrices=False)
+        Pref = Uc[:, :keep] @ Uc[:, :keep].T
+        assert np.allclose(U @ U.T, Pref, atol=1e-12)
 
 
 def _grid_candidates(n):
@@ -807,7 +832,7 @@ def test_tentative_k_is_min_norm_fit(oracle, k):
             continue
         t0 = T1.data[s:e]
         M = Bc[J].T  # k x |J|
-        u = np.linalg.lstsq(M, B[i] - M @ t0, rcond=1e-3)[0]  # singular values of Bc_J below 1e-3 dropped
+        u = np.linalg.lstsq(M, B[i] - M @ t0, rcond=1e-6)[0]  # singular values of Bc_J below 1e-6 dropped
         assert np.allclose(T.data[s:e], t0 + u, rtol=1e-9, atol=1e-12)
 
 
@@ -854,11 +879,11 @@ def test_cg_k_converged_equals_dense_kkt(oracle):
 
 
 def _fits_all(BcJ):
-    """Whether a row's pattern carries every candidate: the Gram matrix's
-    eigenvalues all above the pseudo-inverse's cutoff (1e-6 of the largest),
-    with a margin so that no decision sits on the cutoff."""
-    ev = np.linalg.eigvalsh(BcJ.T @ BcJ)
-    return ev[0] > 2e-6 * ev[-1]
+    """Whether a row's pattern carries every candidate: the singular values of
+    Bc_J all above the fit's cutoff (1e-6 of the largest), with a margin so
+    that no decision sits on the cutoff."""
+    sv = np.linalg.svd(BcJ, compute_uv=False)
+    return sv.size == BcJ.shape[1] and sv[-1] > 2e-6 * sv[0]
 
 
 def test_hierarchy_with_three_candidates(oracle):
