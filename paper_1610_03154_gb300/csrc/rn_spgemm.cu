@@ -1062,13 +1062,30 @@ ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__re
         const TV *pal = pa + aoff[sl] + lane;
         const int32_t *pbl = pb + aoff[sl] + lane;
         const uint32_t *pml = pm + moff[sl] + lane;
+        // the next step's A slot and position words are loaded before this
+        // step's gathers (one step of software pipelining)
+        TV an = pal[0];
+        int32_t nbn = pbl[0];
+        uint32_t wn[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) wn[w] = (w < ws) ? pml[(int64_t)w * 32] : 0u;
         for (int32_t j = 0; j < steps; j++) {
-            const TV a = pal[(int64_t)j * 32];
-            const int32_t nb = pbl[(int64_t)j * 32];
+            const TV a = an;
+            const int32_t nb = nbn;
+            uint32_t wc[NW];
+#pragma unroll
+            for (int w = 0; w < NW; w++) wc[w] = wn[w];
+            if (j + 1 < steps) {
+                an = pal[(int64_t)(j + 1) * 32];
+                nbn = pbl[(int64_t)(j + 1) * 32];
+#pragma unroll
+                for (int w = 0; w < NW; w++)
+                    if (w < ws) wn[w] = pml[((int64_t)(j + 1) * ws + w) * 32];
+            }
 #pragma unroll
             for (int w = 0; w < NW; w++) {
                 if (w < ws) {
-                    const uint32_t word = pml[((int64_t)j * ws + w) * 32];
+                    const uint32_t word = wc[w];
 #pragma unroll
                     for (int t = 0; t < PER; t++) {
                         const int q = w * PER + t;

@@ -19,9 +19,12 @@ pytestmark = pytest.mark.gpu
 # <= 1.9e-12); symmetric setups keep TOL0 on every level.
 TOL0 = 1e-11
 TOL_ROW = 1e-12
-# The nonsymmetric setup (GMRES minimisations for P and for R^T from A^T) on
-# coarse levels, whose inputs already differ: measured <= 3.2e-8 (level 2 of
-# the 80^2 convection-diffusion with two candidates).
+# The nonsymmetric setup (GMRES minimisations for P and for R^T from A^T,
+# whose least-squares steps add to the fits' conditioning): level 0 measured
+# <= 1.8e-11 (80^2 convection-diffusion, d = 3, three candidates, R up to
+# 4.5e3), coarse levels, whose inputs already differ, <= 3.2e-8 (level 2,
+# d = 1, two candidates); well-conditioned level-0 rows of T <= 4e-15.
+TOL_NONSYM0 = 1e-10
 TOL_NONSYM = 1e-7
 TOL = TOL0
 # Block systems (m x m root blocks, rigid-body modes; 1k-4k unknowns):
@@ -136,7 +139,7 @@ def hier(rn, torch_dev, pr, B, Bhat=None, **over):
 
 
 @pytest.mark.parametrize("k", [2, 3])
-@pytest.mark.parametrize("case", ["poisson64", "aniso96", "convdiff80"])
+@pytest.mark.parametrize("case", ["poisson64", "aniso96", "convdiff80", "convdiff80rn1"])
 def test_k_candidates_hierarchy_parity(rn, torch_dev, oracle, case, k):
     """Patterns (S, aggregates, roots, N, P, R, coarse A) bit-exact; level-0
     smoothed candidates bit-exact; level-0 T within 1e-12 on rows whose Bc_J
@@ -155,7 +158,7 @@ def test_k_candidates_hierarchy_parity(rn, torch_dev, oracle, case, k):
     counts = level0_rows(h, oh.levels[0], k)
     assert counts["well"] > 0
     print(f"{case} k={k}: level-0 free rows by kappa(Bc_J): {counts}")
-    compare_levels(h, oh, pr.params.get("postfilter", 0.0), tol)
+    compare_levels(h, oh, pr.params.get("postfilter", 0.0), tol, TOL0 if pr.Bhat is None else TOL_NONSYM0)
     h.close()
 
 
