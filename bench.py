@@ -472,6 +472,12 @@ def next_rows(rn, torch, dev, stream, flush, prec):
 
     tbs, ibs = clock(batched_streams)
     tb, ib = clock(batched_merged)
+    phases_thr = dict(phases)
+    bparams_thr = bparams
+    bparams = rn.params_from_config(PR.PARAMS_ANISO, precision=precision, autotune=1)
+    tba, iba = clock(batched_merged)
+    phases_at = dict(phases)
+    bparams = bparams_thr
     n_b = sum(p.A.n_rows for p in probs)
     nnz_b = sum(p.A.nnz for p in probs)
     del dp, bs, xs
@@ -508,7 +514,10 @@ def next_rows(rn, torch, dev, stream, flush, prec):
         "batched_problems": {"step_s": tb, "problems": len(probs), "n_total": n_b, "nnz_total": nnz_b,
                              "max_iters": max(i["iters"] for i in ib),
                              "max_rel_res": max(i["rel_res"] for i in ib),
-                             "phases_s": phases,
+                             "phases_s": phases_thr,
+                             "autotuned": {"step_s": tba, "max_iters": max(i["iters"] for i in iba), "phases_s": phases_at,
+                                           "what": "the same with the merged hierarchy's SpMV schedules picked by "
+                                                   "timed trials (params.autotune)"},
                              "what": "rn_setup_batched + rn_batch_merge + rn_batch_solve (CG per problem, one "
                                      "launch per step for all problems), sides U{32..512}, eps 10^U[-4,-1], "
                                      "psi U[0,pi)",
@@ -625,6 +634,10 @@ def main():
     # the same step with W(1,1) cycles (Sec. 5.2), one warm-up and one timed step
     step(prec, gamma=2)
     times_w, infos_w = timed(prec, 1, gamma=2)
+    # the same step with SpMV schedules picked by timed trials (params.autotune;
+    # the first setup tunes, later ones take the cached choices)
+    step(prec, autotune=1)
+    times_at, infos_at = timed(prec, 3, autotune=1)
     # the same step with the symmetric strength measure (the setting measured
     # first), one warm-up and one timed step
     step(prec, soc_kind=0)
@@ -789,6 +802,9 @@ def main():
             "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "mixed_setup_vs_fp64": setup_err,
+            "autotuned": {"step_s": float(np.mean(times_at)), "iters": infos_at[0]["iters"],
+                          "what": "SpMV schedules (lanes per row / tile height, or the unstaged kernel) per matrix "
+                                  "picked by timed trials, cached per shape; threshold schedule = value"},
             "symmetric_soc": {"step_s": times_sym[0], "iters": infos_sym[0]["iters"],
                               "rel_res": infos_sym[0]["rel_res"], "strength": "symmetric, theta 0.25",
                               "precision": prec},

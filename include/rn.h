@@ -110,6 +110,10 @@ typedef struct {
                                 unamalgamated to unknowns, each root node carries m coarse unknowns, and
                                 T injects the first m candidates normalised by the root node's block;
                                 needs k >= m and n divisible by m */
+    int autotune;            /* 1: the solve's SpMV schedule per matrix (lanes per row, hence rows per
+                                staged tile, or the unstaged kernel) picked by timed trials on the
+                                matrix, cached per matrix shape for the process; 0: the threshold rule
+                                (the fewest lanes whose tile fits one shared-memory stage) */
     void *stream;            /* cudaStream_t */
     /* Device-memory hooks (both NULL: the stream-ordered pool, cudaMallocAsync;
      * one without the other is RN_EINVAL).  alloc(bytes, stream, ctx) returns

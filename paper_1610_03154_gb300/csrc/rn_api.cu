@@ -64,6 +64,7 @@ extern "C" rn_status rn_default_params(rn_params *p) {
     p->gamma = 1;
     p->soc_kind = RN_SOC_SYMMETRIC;
     p->block_size = 1;
+    p->autotune = 0;
     p->stream = nullptr;
     return RN_OK;
 }
@@ -82,6 +83,7 @@ static void check_params(const rn_params *p) {
     if (p->outer == RN_OUTER_FGMRES && (p->restart < 1 || p->restart > 1000)) fail(RN_EINVAL, "restart");
     if (!(p->omega > 0.0)) fail(RN_EINVAL, "omega must be > 0");
     if (p->coarse_cluster < 0) fail(RN_EINVAL, "coarse_cluster must be >= 0");
+    if (p->autotune != 0 && p->autotune != 1) fail(RN_EINVAL, "autotune must be 0 or 1");
     if (p->gamma != 1 && p->gamma != 2) fail(RN_EINVAL, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
     if (p->soc_kind != RN_SOC_SYMMETRIC && p->soc_kind != RN_SOC_CLASSICAL) fail(RN_EINVAL, "soc_kind");
     if (p->block_size < 1 || p->block_size > RN_MAX_BLOCK) fail(RN_EINVAL, "block_size must be in [1, RN_MAX_BLOCK]");

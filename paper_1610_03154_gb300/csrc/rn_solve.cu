@@ -15,6 +15,9 @@
 #include <cmath>
 
 #include <functional>
+#include <tuple>
+#include <mutex>
+#include <map>
 
 #include "rn_hier.cuh"
 #include "rn_spmv.cuh"
@@ -691,6 +694,98 @@ __global__ void omega_over_diag_kernel(int64_t n, double omega, const double *__
     }
 }
 
+// ------------------------------------------------------------------ schedule autotuner
+// The staged SpMV's schedule for a matrix is its lanes per row G (a tile is
+// 256/G rows): the threshold rule takes the smallest G whose tile fits one
+// shared-memory stage (set_tile_group).  With params.autotune the candidates
+// - that G, every larger power of two up to 32, and the unstaged group kernel
+// (0) - are timed on the matrix itself (y = M x on the level's vectors: one
+// untimed launch, then three timed by CUDA events, the median kept) and the
+// fastest is used; the choice is cached for the process per (rows, columns,
+// entries, longest row, value type), so later hierarchies of the same shapes
+// take it without trials.
+static void check_tile_error(rn_hierarchy &h);
+
+using TuneKey = std::tuple<int32_t, int32_t, int64_t, int32_t, int>;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune;
+
+template <typename T>
+static void tune_matrix(rn_hierarchy &h, DCsr &M, const T *x, T *y) {
+    if (M.n == 0 || M.nnz == 0) return;
+    int &group = sizeof(T) == 8 ? M.tile_group64 : M.tile_group;
+    const TuneKey key{M.n, M.m, M.nnz, M.maxlen, (int)sizeof(T)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            group = it->second;
+            return;
+        }
+    }
+    std::vector<int> cand;
+    if (group > 0)
+        for (int G = group; G <= 32; G *= 2) cand.push_back(G);
+    cand.push_back(0);  // the unstaged kernel
+    cudaStream_t s = h.s;
+    cudaEvent_t ev[2];
+    RN_CUDA_CHECK(cudaEventCreate(&ev[0]));
+    RN_CUDA_CHECK(cudaEventCreate(&ev[1]));
+    int best = group;
+    float best_ms = 1e30f;
+    try {
+        for (int G : cand) {
+            group = G;
+            spmv<T, T, T, OP_SPMV>(h, "autotune", M, x, (const T *)nullptr, nullptr, T(0), y, Fin());
+            float t[3];
+            for (int r = 0; r < 3; r++) {
+                RN_CUDA_CHECK(cudaEventRecord(ev[0], s));
+                spmv<T, T, T, OP_SPMV>(h, "autotune", M, x, (const T *)nullptr, nullptr, T(0), y, Fin());
+                RN_CUDA_CHECK(cudaEventRecord(ev[1], s));
+                RN_CUDA_CHECK(cudaEventSynchronize(ev[1]));
+                RN_CUDA_CHECK(cudaEventElapsedTime(&t[r], ev[0], ev[1]));
+            }
+            std::sort(t, t + 3);
+            if (t[1] < best_ms) {
+                best_ms = t[1];
+                best = G;
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        throw;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    check_tile_error(h);
+    group = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+}
+
+// every level's A, P and R in the cycle's value type, and level 0's A in FP64
+// (the outer iteration's SpMV)
+static void autotune_schedules(rn_hierarchy &h) {
+    const bool mixed = h.p.precision == RN_MIXED;
+    for (size_t l = 0; l < h.lev.size(); l++) {
+        rn_level &L = *h.lev[l];
+        const bool last = l + 1 == h.lev.size();
+        if (mixed) {
+            tune_matrix<float>(h, L.A, L.x32.p, L.t32.p);
+            if (!last) {
+                tune_matrix<float>(h, L.P, h.lev[l + 1]->x32.p, L.t32.p);
+                tune_matrix<float>(h, L.R, L.t32.p, h.lev[l + 1]->b32.p);
+            }
+        }
+        if (!mixed || l == 0) tune_matrix<double>(h, L.A, L.x.p, L.t.p);
+        if (!mixed && !last) {
+            tune_matrix<double>(h, L.P, h.lev[l + 1]->x.p, L.t.p);
+            tune_matrix<double>(h, L.R, L.t.p, h.lev[l + 1]->b.p);
+        }
+    }
+}
+
 void prepare_solve(rn_hierarchy &h) {
     cudaStream_t s = h.s;
     const bool mixed = h.p.precision == RN_MIXED;
@@ -740,6 +835,7 @@ void prepare_solve(rn_hierarchy &h) {
             }
         }
     }
+    if (h.p.autotune) autotune_schedules(h);
     const int64_t n0 = h.lev[0]->A.n;
     h.r.alloc(n0, s);
     h.z.alloc(n0, s);

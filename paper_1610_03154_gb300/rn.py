@@ -48,7 +48,7 @@ class rn_params(C.Structure):
                 ("symmetric", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int), ("precision", C.c_int),
                 ("outer", C.c_int), ("restart", C.c_int), ("use_graphs", C.c_int), ("keep_aux", C.c_int),
                 ("coarse_cluster", C.c_int), ("gamma", C.c_int), ("soc_kind", C.c_int), ("block_size", C.c_int),
-                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("dealloc", DEALLOC_FN),
+                ("autotune", C.c_int), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("dealloc", DEALLOC_FN),
                 ("alloc_ctx", C.c_void_p)]
 
 
@@ -252,7 +252,7 @@ def params_from_config(cfg: dict, **overrides) -> rn_params:
               nu_post=m.get("nu_post", 1), precision=m.get("precision", RN_FP64), outer=m.get("outer", RN_OUTER_CG),
               restart=m.get("restart", 30), use_graphs=m.get("use_graphs", 1), keep_aux=m.get("keep_aux", 0),
               coarse_cluster=m.get("coarse_cluster", 0), gamma=m.get("gamma", 1), soc_kind=m.get("soc_kind", 0),
-              block_size=m.get("block_size", 1))
+              block_size=m.get("block_size", 1), autotune=m.get("autotune", 0))
     return default_params(**kw)
 
 
