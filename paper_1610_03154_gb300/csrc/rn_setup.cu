@@ -1158,6 +1158,100 @@ __global__ void __launch_bounds__(1024) dense_lu_kernel(int n, double *M, int32_
     }
 }
 
+// Coarsest levels of at most kLuSmall rows: densify, LU with partial pivoting
+// (largest |pivot|, lowest row on ties; a pivot below 1e-14 max|A| sets
+// *flag) and the explicit inverse, in one CTA with the matrix and the inverse
+// in shared memory (the global-memory kernels above and below serve larger
+// levels).  The same operations per entry as those kernels.
+constexpr int kLuSmall = 96;
+__global__ void __launch_bounds__(256)
+dense_lu_small_kernel(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                      const double *__restrict__ val, double *__restrict__ Ainv, int32_t *__restrict__ flag) {
+    extern __shared__ __align__(16) double lu_sm[];
+    double *M = lu_sm, *X = lu_sm + n * n;
+    __shared__ double sv[8];
+    __shared__ int si[8];
+    __shared__ double amax;
+    __shared__ int piv[kLuSmall];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    for (int q = tid; q < n * n; q += blockDim.x) M[q] = 0.0;
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x)
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) M[i * n + col[e]] = val[e];
+    __syncthreads();
+    double m = 0.0;
+    for (int q = tid; q < n * n; q += blockDim.x) m = fmax(m, fabs(M[q]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) sv[w] = m;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int k = 0; k < nw; k++) a = fmax(a, sv[k]);
+        amax = a;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; k++) {
+        if (w == 0) {  // pivot: one warp scans the column
+            double best = -1.0;
+            int brow = n;
+            for (int i = k + lane; i < n; i += 32) {
+                const double v = fabs(M[i * n + k]);
+                if (v > best || (v == best && i < brow)) { best = v; brow = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+                if (ov > best || (ov == best && orow < brow)) { best = ov; brow = orow; }
+            }
+            if (lane == 0) {
+                piv[k] = brow;
+                if (!(best >= 1e-14 * amax) || best == 0.0) flag[0] = 1;
+            }
+        }
+        __syncthreads();
+        if (flag[0]) return;
+        const int p = piv[k];
+        if (p != k)
+            for (int j = tid; j < n; j += blockDim.x) {
+                const double t = M[k * n + j];
+                M[k * n + j] = M[p * n + j];
+                M[p * n + j] = t;
+            }
+        __syncthreads();
+        const double d = M[k * n + k];
+        for (int i = k + 1 + tid; i < n; i += blockDim.x) M[i * n + k] = M[i * n + k] / d;
+        __syncthreads();
+        const int r = n - k - 1;
+        for (int q = tid; q < r * r; q += blockDim.x) {
+            const int i = k + 1 + q / r, j = k + 1 + q % r;
+            M[i * n + j] = M[i * n + j] - M[i * n + k] * M[k * n + j];
+        }
+        __syncthreads();
+    }
+    // inverse column c: L U x = P e_c, column c of X held by thread c
+    for (int c = tid; c < n; c += blockDim.x) {
+        for (int i = 0; i < n; i++) X[i * n + c] = (i == c) ? 1.0 : 0.0;
+        for (int k = 0; k < n; k++)
+            if (piv[k] != k) {
+                const double t = X[k * n + c];
+                X[k * n + c] = X[piv[k] * n + c];
+                X[piv[k] * n + c] = t;
+            }
+        for (int i = 0; i < n; i++) {
+            double s = X[i * n + c];
+            for (int j = 0; j < i; j++) s -= M[i * n + j] * X[j * n + c];
+            X[i * n + c] = s;
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            double s = X[i * n + c];
+            for (int j = i + 1; j < n; j++) s -= M[i * n + j] * X[j * n + c];
+            X[i * n + c] = s / M[i * n + i];
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < n * n; q += blockDim.x) Ainv[q] = X[q];
+}
+
 // inverse column c: solve L U x = P e_c
 __global__ void lu_inverse_kernel(int n, const double *__restrict__ LU, const int32_t *__restrict__ piv,
                                   double *__restrict__ X, double *__restrict__ work) {
@@ -1874,17 +1968,32 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
     if (nL > kMaxDense)
         fail(RN_ESTALL, fmt("coarsening stalled with %d rows (> %d for the dense solve)", nL, kMaxDense));
     h.nL = nL;
-    DVec<double> M((size_t)nL * nL, s), work((size_t)nL * nL, s);
-    DVec<int32_t> piv(nL, s);
-    fill_f64(M.p, 0.0, (int64_t)nL * nL, s);
-    RN_LAUNCH("coarse_lu", 12.0 * C.A.nnz, s, csr_to_dense_kernel, rows_grid(nL), kT, 0, nL, C.A.rowptr.p, C.A.col.p,
-              C.A.val.p, M.p);
-    fill_i32(h.iflags.p + 7, 0, 1, s);
-    RN_LAUNCH("coarse_lu", 16.0 * nL * nL, s, dense_lu_kernel, 1, 1024, 0, nL, M.p, piv.p, h.iflags.p + 7);
-    check_flag(h.iflags.p + 7, s, RN_ESINGULAR, "coarsest-level LU pivot below 1e-14 max|A|");
-    h.Ainv.alloc((size_t)nL * nL, s);
-    RN_LAUNCH("coarse_lu", 24.0 * nL * nL, s, lu_inverse_kernel, grid_for(nL, 64, 4), 64, 0, nL, M.p, piv.p, h.Ainv.p,
-              work.p);
+    if (nL <= kLuSmall) {  // one launch, the matrix and its inverse in shared memory
+        const size_t smem = 2 * sizeof(double) * (size_t)nL * nL;
+        static const bool configured = [] {  // once (thread-safe static initialisation)
+            RN_CUDA_CHECK(cudaFuncSetAttribute(dense_lu_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(2 * sizeof(double) * kLuSmall * kLuSmall)));
+            return true;
+        }();
+        (void)configured;
+        fill_i32(h.iflags.p + 7, 0, 1, s);
+        h.Ainv.alloc((size_t)nL * nL, s);
+        RN_LAUNCH("coarse_lu", 12.0 * C.A.nnz + 8.0 * nL * nL, s, dense_lu_small_kernel, 1, 256, smem, nL,
+                  C.A.rowptr.p, C.A.col.p, C.A.val.p, h.Ainv.p, h.iflags.p + 7);
+        check_flag(h.iflags.p + 7, s, RN_ESINGULAR, "coarsest-level LU pivot below 1e-14 max|A|");
+    } else {
+        DVec<double> M((size_t)nL * nL, s), work((size_t)nL * nL, s);
+        DVec<int32_t> piv(nL, s);
+        fill_f64(M.p, 0.0, (int64_t)nL * nL, s);
+        RN_LAUNCH("coarse_lu", 12.0 * C.A.nnz, s, csr_to_dense_kernel, rows_grid(nL), kT, 0, nL, C.A.rowptr.p, C.A.col.p,
+                  C.A.val.p, M.p);
+        fill_i32(h.iflags.p + 7, 0, 1, s);
+        RN_LAUNCH("coarse_lu", 16.0 * nL * nL, s, dense_lu_kernel, 1, 1024, 0, nL, M.p, piv.p, h.iflags.p + 7);
+        check_flag(h.iflags.p + 7, s, RN_ESINGULAR, "coarsest-level LU pivot below 1e-14 max|A|");
+        h.Ainv.alloc((size_t)nL * nL, s);
+        RN_LAUNCH("coarse_lu", 24.0 * nL * nL, s, lu_inverse_kernel, grid_for(nL, 64, 4), 64, 0, nL, M.p, piv.p, h.Ainv.p,
+                  work.p);
+    }
     if (!p.keep_aux) {
         for (auto &Lp : h.lev) {
             Lp->agg.release();

@@ -699,14 +699,16 @@ __global__ void omega_over_diag_kernel(int64_t n, double omega, const double *__
 // 256/G rows): the threshold rule takes the smallest G whose tile fits one
 // shared-memory stage (set_tile_group).  With params.autotune the candidates
 // - that G, every larger power of two up to 32, and the unstaged group kernel
-// (0) - are timed on the matrix itself (y = M x on the level's vectors: one
-// untimed launch, then three timed by CUDA events, the median kept) and the
-// fastest is used; the choice is cached for the process per (rows, columns,
-// entries, longest row, value type), so later hierarchies of the same shapes
-// take it without trials.
+// (0; not for a merged batch, whose staged tiles carry the lists that skip
+// converged problems) - are timed on the matrix itself (y = M x on the level's
+// vectors: one untimed launch, then five timed by CUDA events, the fastest
+// kept) and a candidate replaces the threshold's G only when it is at least 5%
+// faster; the choice is cached for the process per (rows, columns, entries,
+// longest row, value type, merged or not), so later hierarchies of the same
+// shapes take it without trials.
 static void check_tile_error(rn_hierarchy &h);
 
-using TuneKey = std::tuple<int32_t, int32_t, int64_t, int32_t, int>;
+using TuneKey = std::tuple<int32_t, int32_t, int64_t, int32_t, int, int>;
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tune;
 
@@ -714,7 +716,8 @@ template <typename T>
 static void tune_matrix(rn_hierarchy &h, DCsr &M, const T *x, T *y) {
     if (M.n == 0 || M.nnz == 0) return;
     int &group = sizeof(T) == 8 ? M.tile_group64 : M.tile_group;
-    const TuneKey key{M.n, M.m, M.nnz, M.maxlen, (int)sizeof(T)};
+    const bool merged = h.ncblk > 0;
+    const TuneKey key{M.n, M.m, M.nnz, M.maxlen, (int)sizeof(T), merged ? 1 : 0};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -726,31 +729,35 @@ static void tune_matrix(rn_hierarchy &h, DCsr &M, const T *x, T *y) {
     std::vector<int> cand;
     if (group > 0)
         for (int G = group; G <= 32; G *= 2) cand.push_back(G);
-    cand.push_back(0);  // the unstaged kernel
+    if (!merged || group == 0) cand.push_back(0);  // the unstaged kernel
     cudaStream_t s = h.s;
     cudaEvent_t ev[2];
     RN_CUDA_CHECK(cudaEventCreate(&ev[0]));
     RN_CUDA_CHECK(cudaEventCreate(&ev[1]));
+    const int thr = group;
     int best = group;
-    float best_ms = 1e30f;
+    float best_ms = 1e30f, thr_ms = 1e30f;
     try {
         for (int G : cand) {
             group = G;
             spmv<T, T, T, OP_SPMV>(h, "autotune", M, x, (const T *)nullptr, nullptr, T(0), y, Fin());
-            float t[3];
-            for (int r = 0; r < 3; r++) {
+            float tmin = 1e30f;
+            for (int r = 0; r < 5; r++) {
+                float t = 0.f;
                 RN_CUDA_CHECK(cudaEventRecord(ev[0], s));
                 spmv<T, T, T, OP_SPMV>(h, "autotune", M, x, (const T *)nullptr, nullptr, T(0), y, Fin());
                 RN_CUDA_CHECK(cudaEventRecord(ev[1], s));
                 RN_CUDA_CHECK(cudaEventSynchronize(ev[1]));
-                RN_CUDA_CHECK(cudaEventElapsedTime(&t[r], ev[0], ev[1]));
+                RN_CUDA_CHECK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+                tmin = std::min(tmin, t);
             }
-            std::sort(t, t + 3);
-            if (t[1] < best_ms) {
-                best_ms = t[1];
+            if (G == thr) thr_ms = tmin;
+            if (tmin < best_ms) {
+                best_ms = tmin;
                 best = G;
             }
         }
+        if (best != thr && !(best_ms < 0.95f * thr_ms)) best = thr;  // only a clear win replaces the rule
     } catch (...) {
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);

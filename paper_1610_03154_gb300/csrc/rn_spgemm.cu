@@ -293,13 +293,15 @@ hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32
         const unsigned hmask = (unsigned)slots - 1u;
         for (int q = lane; q < slots; q += G) keys[q] = -1;
         __syncwarp(mask);
+        // a product that finds the table full is dropped, and a row with more
+        // distinct columns than half the table (the compaction list's size)
+        // goes to the block kernel, which recomputes it whole: both checked
+        // once, after the row
+        bool full = false;
         int mine = 0;  // distinct columns this lane inserted
-        bool ovf = false;
-        const bool may_overflow = 2 * ub > slots;
         for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
             const int32_t k = acol[e];
             const double a = aval[e];
-            bool full = false;
             for (int32_t f = brp[k] + lane; f < brp[k + 1]; f += G) {
                 const int32_t j = bcol[f];
                 const double v = __dmul_rn(a, bval[f]);
@@ -320,18 +322,12 @@ hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32
                 }
                 if (p == slots) full = true;
             }
-            __syncwarp(mask);
-            if (may_overflow) {
-                int tot = mine;
-#pragma unroll
-                for (int o = G / 2; o > 0; o >>= 1) tot += __shfl_xor_sync(mask, tot, o, G);
-                const bool anyfull = __any_sync(mask, full);
-                if (anyfull || tot > slots / 2) {
-                    ovf = true;
-                    break;
-                }
-            }
+            __syncwarp(mask);  // a_ik's products land before a_i(k+1)'s: sums in ascending k
         }
+        int tot = mine;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) tot += __shfl_xor_sync(mask, tot, o, G);
+        const bool ovf = __any_sync(mask, full) || tot > slots / 2;
         if (ovf) {
             if (lane == 0) ovf_list[atomicAdd(ovf_n, 1)] = i;
             __syncwarp(mask);
@@ -506,12 +502,18 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
         else launch_small<16>(nsmall, flags.p + 5, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
     }
     if (nlarge) {
-        // short B rows (an interpolation operator): rows of the product have few
-        // distinct columns, so half-size tables double the resident groups per
-        // SM; sums per column run in ascending k either way (same result), and
-        // rows past a table go to the block kernel
+        // short B rows (an interpolation operator, or A P): rows of the product
+        // have few distinct columns, so smaller tables and fewer lanes per row
+        // fit more rows per SM, and a B row of ~8 entries keeps a group of 8
+        // lanes busy (32 lanes would leave most of the warp's FP64 multiply-adds
+        // idle: R (A P) at level 0 of the 1024^2 anisotropy 828 -> 583 us);
+        // sums per column run in ascending k either way (same result), and rows
+        // past a table go to the block kernel
         const double avgB = B.n ? (double)B.nnz / B.n : 0.0;
-        if (avgB <= 16.0)
+        if (avgB <= 12.0)
+            launch_hash<8, 128>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
+                                flags.p + 3, bytes, s);
+        else if (avgB <= 16.0)
             launch_hash<32, 512>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
                                  flags.p + 3, bytes, s);
         else
@@ -997,6 +999,8 @@ ep_plan_fill_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *_
                 pa[slot] = TV(0);
                 pb[slot] = 0;
             }
+            // both rows are sorted: one merge of N_i with N_k gives every position
+            int32_t f = ks;
             for (int32_t w = 0; w < ws; w++) {
                 uint32_t word = 0u;
                 for (int t = 0; t < per; t++) {
@@ -1004,13 +1008,8 @@ ep_plan_fill_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *_
                     uint32_t pos = none;
                     if (live && q < len) {
                         const int32_t jc = ncol[cs + q];
-                        for (int32_t f = ks; f < ke; f++) {
-                            const int32_t c = ncol[f];
-                            if (c >= jc) {
-                                if (c == jc) pos = (uint32_t)(f - ks);
-                                break;
-                            }
-                        }
+                        while (f < ke && ncol[f] < jc) f++;
+                        if (f < ke && ncol[f] == jc) pos = (uint32_t)(f - ks);
                     }
                     word |= pos << (t * bits);
                 }

@@ -112,10 +112,29 @@ def close_smoothed_candidates(g, o, A, sweeps, omega, what):
     assert np.all(err <= bar), f"{what}: diff {err[k]:.3e} > bar {bar[k]:.3e} (row {k})"
 
 
+# The nonsymmetric setup's coarse levels: R comes from A^T by GMRES
+# minimisations whose inputs already differ, and the deepest levels inherit two
+# such chains (2048^2 convection-diffusion, level 5: N 1.9e-12, R 1.3e-12,
+# every other matrix and level below 1e-12; symmetric setups below 1e-12).
+TOL_NONSYM_COARSE = 1e-11
+
+
 def compare_hierarchies(h, oh, nonsym=False):
+    global TOL
+    tol0 = TOL
+    try:
+        _compare_hierarchies(h, oh, nonsym)
+    finally:
+        TOL = tol0
+
+
+def _compare_hierarchies(h, oh, nonsym):
+    global TOL
+    base = TOL
     st = h.stats()
     assert st["levels"] == len(oh.levels), (st["n"], [L.A.shape[0] for L in oh.levels])
     for l, L in enumerate(oh.levels):
+        TOL = TOL_NONSYM_COARSE if (nonsym and l >= 1) else base
         Ag = as_csr(h.export_csr(l, 0))
         same_pattern(Ag, L.A, f"A[{l}]")
         close_values(Ag, L.A, f"A[{l}]", exact=(l == 0))
@@ -393,6 +412,17 @@ def test_singular_coarsest_level(rn, torch_dev):
     with pytest.raises(rn.RNError) as e:
         _mk(rn, torch_dev, A.rowptr, A.col, A.val, max_coarse=100)
     assert e.value.status == rn.RN_ESINGULAR
+    # coarsest levels above 96 rows take the global-memory LU: singular, then exact
+    A = PR.q1_aniso(11, 1.0, 0.0, dirichlet=False)  # 144 nodes
+    with pytest.raises(rn.RNError) as e:
+        _mk(rn, torch_dev, A.rowptr, A.col, A.val, max_coarse=200)
+    assert e.value.status == rn.RN_ESINGULAR
+    pr = PR.poisson_problem(12)  # 144 rows: one level, exact solve
+    h = gpu_hierarchy(rn, torch_dev, pr, max_coarse=200)
+    assert h.stats()["levels"] == 1
+    xs, info, res = gpu_solve(rn, torch_dev, h, pr, rtol=1e-13)
+    assert res < 1e-13 and info["iters"] <= 1
+    h.close()
 
 
 def test_not_converged_status(rn, torch_dev):
