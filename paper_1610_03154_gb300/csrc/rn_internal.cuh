@@ -255,7 +255,11 @@ void reciprocal(const double *x, double *y, int64_t n, cudaStream_t s);
 // C = A*B in one hash pass per row: the symbolic pattern (explicit zeros kept,
 // rows sorted) and the values, each summed in ascending k with a rounded
 // multiply then a rounded add (bit-identical to a sequential evaluation).
-void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s);
+// fused: each further term added by a fused multiply-add instead (one FP64
+// instruction instead of two; the Galerkin products, held to 1e-12 rather
+// than bit-exactness), still in ascending k; rows of the sorting kernel keep
+// the separate operations.
+void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fused = false);
 
 // Energy-minimisation operator on the fixed pattern N shared by X and W:
 //   W = scale * Proj(Mask_N(A X)) with A's values aval (TV = double, or float

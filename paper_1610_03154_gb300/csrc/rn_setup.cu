@@ -1947,8 +1947,8 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         auto Lc = std::make_unique<rn_level>();
         {
             DCsr AP;
-            spgemm(A, view(L.P), AP, s);
-            spgemm(view(L.R), view(AP), Lc->A, s);
+            spgemm(A, view(L.P), AP, s, true);
+            spgemm(view(L.R), view(AP), Lc->A, s, true);
         }
         Lc->B.alloc((size_t)nc * h.k, s);
         d2d(Lc->B.p, L.Bc.p, (size_t)nc * h.k, s);
@@ -2097,20 +2097,20 @@ void time_setup_op(rn_hierarchy &h, int op, int reps, int64_t flush_bytes, doubl
         return;
     }
     DCsr AP;
-    spgemm(A, view(L.P), AP, s);  // untimed: its size, and the operand of R (A P)
+    spgemm(A, view(L.P), AP, s, true);  // untimed: its size, and the operand of R (A P)
     if (op == RN_SOP_GALERKIN_AP) {
         name = "galerkin_AP_L0";
         *bytes = 12.0 * (A.nnz + L.P.nnz) + 12.0 * AP.nnz;
         *us = time_launches(s, reps, flush_bytes, none, [&]() {
             DCsr C;
-            spgemm(A, view(L.P), C, s);
+            spgemm(A, view(L.P), C, s, true);
         });
     } else {
         name = "galerkin_RAP_L0";
         *bytes = 12.0 * (L.R.nnz + AP.nnz) + 12.0 * h.lev[1]->A.nnz;
         *us = time_launches(s, reps, flush_bytes, none, [&]() {
             DCsr C;
-            spgemm(view(L.R), view(AP), C, s);
+            spgemm(view(L.R), view(AP), C, s, true);
         });
     }
 }

@@ -210,6 +210,7 @@ small_product_kernel(int32_t nrows_max, const int32_t *__restrict__ nrows_dev, c
 // ovf_list for the sort kernel.
 constexpr int kMergeWays = 12;
 
+template <bool FUSED>
 __global__ void __launch_bounds__(kFuThreads)
 merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
                      const int32_t *__restrict__ acol, const double *__restrict__ aval,
@@ -249,8 +250,9 @@ merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
 #pragma unroll
             for (int u = 0; u < kMergeWays; u++) {
                 if (cur[u] == cmin) {
-                    const double v = __dmul_rn(aval[as + u], bval[pos[u]]);
-                    sum = first ? v : __dadd_rn(sum, v);
+                    const double a = aval[as + u], b = bval[pos[u]];
+                    if (FUSED) sum = first ? __dmul_rn(a, b) : __fma_rn(a, b, sum);
+                    else sum = first ? __dmul_rn(a, b) : __dadd_rn(sum, __dmul_rn(a, b));
                     first = false;
                     pos[u]++;
                     cur[u] = pos[u] < end[u] ? bcol[pos[u]] : INT32_MAX;
@@ -266,7 +268,7 @@ merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
 
 // G lanes per row, SLOTS table entries per group, for the rows listed in
 // rows.  Rows whose distinct columns exceed SLOTS/2 go to ovf_list.
-template <int G, int SLOTS>
+template <int G, int SLOTS, bool FUSED>
 __global__ void __launch_bounds__(kFuThreads)
 hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ arp,
                     const int32_t *__restrict__ acol, const double *__restrict__ aval,
@@ -304,18 +306,18 @@ hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32
             const double a = aval[e];
             for (int32_t f = brp[k] + lane; f < brp[k + 1]; f += G) {
                 const int32_t j = bcol[f];
-                const double v = __dmul_rn(a, bval[f]);
+                const double b = bval[f];
                 unsigned h = ((uint32_t)j * 2654435761u) & hmask;
                 int p = 0;
                 for (; p < slots; p++) {
                     const int32_t old = atomicCAS(&keys[h], -1, j);
                     if (old == -1) {
-                        vals[h] = v;  // 0 + a b
+                        vals[h] = __dmul_rn(a, b);  // 0 + a b
                         mine++;
                         break;
                     }
                     if (old == j) {
-                        vals[h] = __dadd_rn(vals[h], v);
+                        vals[h] = FUSED ? __fma_rn(a, b, vals[h]) : __dadd_rn(vals[h], __dmul_rn(a, b));
                         break;
                     }
                     h = (h + 1) & hmask;
@@ -359,6 +361,7 @@ hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32
 
 // Block per overflowing row, kBigProd slots.
 constexpr int kBigProd = 8192;
+template <bool FUSED>
 __global__ void __launch_bounds__(512)
 hash_product_block_kernel(const int32_t *__restrict__ nrows_dev, const int32_t *__restrict__ rows,
                           const int32_t *__restrict__ arp,
@@ -385,13 +388,16 @@ hash_product_block_kernel(const int32_t *__restrict__ nrows_dev, const int32_t *
             const double a = aval[e];
             for (int32_t f = brp[k] + threadIdx.x; f < brp[k + 1]; f += blockDim.x) {
                 const int32_t j = bcol[f];
-                const double v = __dmul_rn(a, bval[f]);
+                const double b = bval[f];
                 unsigned h = ((uint32_t)j * 2654435761u) & hmask;
                 int p = 0;
                 for (; p < kBigProd; p++) {
                     const int32_t old = atomicCAS(&keys[h], -1, j);
-                    if (old == -1) { vals[h] = v; atomicAdd(&cnt, 1); break; }
-                    if (old == j) { vals[h] = __dadd_rn(vals[h], v); break; }
+                    if (old == -1) { vals[h] = __dmul_rn(a, b); atomicAdd(&cnt, 1); break; }
+                    if (old == j) {
+                        vals[h] = FUSED ? __fma_rn(a, b, vals[h]) : __dadd_rn(vals[h], __dmul_rn(a, b));
+                        break;
+                    }
                     h = (h + 1) & hmask;
                 }
                 if (p == kBigProd) bad = 1;
@@ -434,21 +440,42 @@ __global__ void compact_rows_kernel(int32_t n, const int32_t *__restrict__ ubp, 
     }
 }
 
-template <int G, int SLOTS>
-static void launch_hash(int32_t nrows, const int32_t *rows, const CsrView &A, const CsrView &B, const int32_t *ubp,
-                        int32_t *tcol, double *tval, int32_t *count, int32_t *ovf_list, int32_t *ovf_n, double bytes,
-                        cudaStream_t s) {
+template <int G, int SLOTS, bool FUSED>
+static void launch_hash_t(int32_t nrows, const int32_t *rows, const CsrView &A, const CsrView &B, const int32_t *ubp,
+                          int32_t *tcol, double *tval, int32_t *count, int32_t *ovf_list, int32_t *ovf_n,
+                          double bytes, cudaStream_t s) {
     constexpr int GPB = kFuThreads / G;
     const size_t smem = (size_t)GPB * SLOTS * (sizeof(double) + sizeof(int32_t)) + (size_t)GPB * (SLOTS / 2) * 4;
     static const bool configured = [&] {  // once per instantiation (thread-safe static initialisation)
-        RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_kernel<G, SLOTS>,
+        RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_kernel<G, SLOTS, FUSED>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         return true;
     }();
     (void)configured;
-    const int grid = grid_resident(hash_product_kernel<G, SLOTS>, kFuThreads, smem, nrows, GPB);
-    RN_LAUNCH("spgemm_hash", bytes, s, (hash_product_kernel<G, SLOTS>), grid, kFuThreads, smem, nrows, rows,
+    const int grid = grid_resident(hash_product_kernel<G, SLOTS, FUSED>, kFuThreads, smem, nrows, GPB);
+    RN_LAUNCH("spgemm_hash", bytes, s, (hash_product_kernel<G, SLOTS, FUSED>), grid, kFuThreads, smem, nrows, rows,
               A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count, ovf_list, ovf_n);
+}
+template <int G, int SLOTS>
+static void launch_hash(bool fused, int32_t nrows, const int32_t *rows, const CsrView &A, const CsrView &B,
+                        const int32_t *ubp, int32_t *tcol, double *tval, int32_t *count, int32_t *ovf_list,
+                        int32_t *ovf_n, double bytes, cudaStream_t s) {
+    if (fused) launch_hash_t<G, SLOTS, true>(nrows, rows, A, B, ubp, tcol, tval, count, ovf_list, ovf_n, bytes, s);
+    else launch_hash_t<G, SLOTS, false>(nrows, rows, A, B, ubp, tcol, tval, count, ovf_list, ovf_n, bytes, s);
+}
+template <bool FUSED>
+static void launch_block(int32_t nlarge, const int32_t *nrows_dev, const int32_t *rows, const CsrView &A,
+                         const CsrView &B, const int32_t *ubp, int32_t *tcol, double *tval, int32_t *count,
+                         int32_t *err, cudaStream_t s) {
+    const size_t smem = (size_t)kBigProd * (sizeof(double) + 2 * sizeof(int32_t));
+    static const bool configured = [&] {
+        RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_block_kernel<FUSED>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        return true;
+    }();
+    (void)configured;
+    RN_LAUNCH("spgemm_hash_long", 0, s, hash_product_block_kernel<FUSED>, std::min(nlarge, 2 * num_sms()), 512,
+              smem, nrows_dev, rows, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count, err);
 }
 
 // nrows_dev: the number of listed rows on the device (at most nrows_max), or
@@ -463,7 +490,7 @@ static void launch_small(int32_t nrows_max, const int32_t *nrows_dev, const int3
               A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count);
 }
 
-void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
+void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fused) {
     if (A.m != B.n) fail(RN_EINTERNAL, "spgemm: inner dimensions differ");
     C.n = A.n;
     C.m = B.m;
@@ -490,10 +517,16 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
     if (nsmall) {
         // merge rows of few entries; the bin's other rows (counted on the
         // device) go to the sort kernel, launched for at most nsmall rows
-        RN_LAUNCH("spgemm_merge", bytes, s, merge_product_kernel,
-                  grid_resident(merge_product_kernel, kFuThreads, 0, nsmall, kFuThreads), kFuThreads, 0, nsmall,
-                  bins.p, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p, count.p,
-                  ovf_list.p, flags.p + 5);
+        if (fused)
+            RN_LAUNCH("spgemm_merge", bytes, s, merge_product_kernel<true>,
+                      grid_resident(merge_product_kernel<true>, kFuThreads, 0, nsmall, kFuThreads), kFuThreads, 0,
+                      nsmall, bins.p, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p,
+                      count.p, ovf_list.p, flags.p + 5);
+        else
+            RN_LAUNCH("spgemm_merge", bytes, s, merge_product_kernel<false>,
+                      grid_resident(merge_product_kernel<false>, kFuThreads, 0, nsmall, kFuThreads), kFuThreads, 0,
+                      nsmall, bins.p, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p,
+                      count.p, ovf_list.p, flags.p + 5);
         const double avg = (double)A.nnz / std::max(1, n) * ((double)B.nnz / std::max(1, B.n));
         if (avg <= 8.0)
             launch_small<4>(nsmall, flags.p + 5, ovf_list.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
@@ -511,25 +544,17 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s) {
         // past a table go to the block kernel
         const double avgB = B.n ? (double)B.nnz / B.n : 0.0;
         if (avgB <= 12.0)
-            launch_hash<8, 128>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
+            launch_hash<8, 128>(fused, nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
                                 flags.p + 3, bytes, s);
         else if (avgB <= 16.0)
-            launch_hash<32, 512>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
+            launch_hash<32, 512>(fused, nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
                                  flags.p + 3, bytes, s);
         else
-            launch_hash<32, 1024>(nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
+            launch_hash<32, 1024>(fused, nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
                                   flags.p + 3, bytes, s);
         // rows past the tables (counted on the device): a block per row, looping
-        const size_t smem = (size_t)kBigProd * (sizeof(double) + 2 * sizeof(int32_t));
-        static const bool configured = [&] {
-            RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_block_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            return true;
-        }();
-        (void)configured;
-        RN_LAUNCH("spgemm_hash_long", 0, s, hash_product_block_kernel, std::min(nlarge, 2 * num_sms()), 512, smem,
-                  flags.p + 3, ovf2.p, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp.p, tcol.p, tval.p,
-                  count.p, flags.p + 4);
+        if (fused) launch_block<true>(nlarge, flags.p + 3, ovf2.p, A, B, ubp.p, tcol.p, tval.p, count.p, flags.p + 4, s);
+        else launch_block<false>(nlarge, flags.p + 3, ovf2.p, A, B, ubp.p, tcol.p, tval.p, count.p, flags.p + 4, s);
     }
     C.rowptr.alloc(n + 1, s);
     scan_counts_dev(count.p, C.rowptr.p, n, tot + 1, s);
@@ -1026,6 +1051,54 @@ __device__ __forceinline__ uint32_t plan_field(uint32_t w, int t) {
     return (w >> (t * BITS)) & ((1u << BITS) - 1u);
 }
 
+// The gathers of one row of the plan product into acc[0..SS): per A entry
+// (a_ik, nrp[k], position words) the next entry's are loaded before this
+// entry's gathers (one step of software pipelining); field q of the words is
+// the position of the row's q-th pattern column in N_k.
+template <int SS, int PER, int BITS, typename TV, int S>
+__device__ __forceinline__ void plan_steps(TV (&acc)[S], int32_t steps, int32_t ws, int32_t lm,
+                                           const TV *__restrict__ pal, const int32_t *__restrict__ pbl,
+                                           const uint32_t *__restrict__ pml, const TV *__restrict__ X) {
+    constexpr int NW = (SS + PER - 1) / PER;
+    constexpr uint32_t NONE = (1u << BITS) - 1u;
+    TV an = pal[0];
+    int32_t nbn = pbl[0];
+    uint32_t wn[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) wn[w] = (w < ws) ? pml[(int64_t)w * 32] : 0u;
+    for (int32_t j = 0; j < steps; j++) {
+        const TV a = an;
+        const int32_t nb = nbn;
+        uint32_t wc[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) wc[w] = wn[w];
+        if (j + 1 < steps) {
+            an = pal[(int64_t)(j + 1) * 32];
+            nbn = pbl[(int64_t)(j + 1) * 32];
+#pragma unroll
+            for (int w = 0; w < NW; w++)
+                if (w < ws) wn[w] = pml[((int64_t)(j + 1) * ws + w) * 32];
+        }
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            if (w < ws) {
+                const uint32_t word = wc[w];
+#pragma unroll
+                for (int t = 0; t < PER; t++) {
+                    const int q = w * PER + t;
+                    // fields past lm (warp-uniform) are absent: skipped in FP64, where
+                    // even a predicated-off FMA holds GB300's narrow FP64 pipe (FP32:
+                    // the unconditional form measured faster)
+                    if (q < SS && (sizeof(TV) == 4 || q < lm)) {
+                        const uint32_t pos = plan_field<BITS>(word, t);
+                        if (pos != NONE) acc[q] = fma(a, X[nb + (int32_t)pos], acc[q]);
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <int G, int S, int BITS, typename TV>
 __global__ void __launch_bounds__(kPlanThreads)
 ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__restrict__ nrp,
@@ -1037,8 +1110,6 @@ ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__re
     __shared__ double s_red[32];
     constexpr int RW = 32 / G;
     constexpr int PER = 32 / BITS;             // fields per word
-    constexpr int NW = (S + PER - 1) / PER;    // most words per A entry
-    constexpr uint32_t NONE = (1u << BITS) - 1u;
     const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
     const unsigned gm = group_mask<G>();
     const int64_t nsl = ((int64_t)n + RW - 1) / RW;
@@ -1061,43 +1132,13 @@ ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__re
         const TV *pal = pa + aoff[sl] + lane;
         const int32_t *pbl = pb + aoff[sl] + lane;
         const uint32_t *pml = pm + moff[sl] + lane;
-        // the next step's A slot and position words are loaded before this
-        // step's gathers (one step of software pipelining)
-        TV an = pal[0];
-        int32_t nbn = pbl[0];
-        uint32_t wn[NW];
-#pragma unroll
-        for (int w = 0; w < NW; w++) wn[w] = (w < ws) ? pml[(int64_t)w * 32] : 0u;
-        for (int32_t j = 0; j < steps; j++) {
-            const TV a = an;
-            const int32_t nb = nbn;
-            uint32_t wc[NW];
-#pragma unroll
-            for (int w = 0; w < NW; w++) wc[w] = wn[w];
-            if (j + 1 < steps) {
-                an = pal[(int64_t)(j + 1) * 32];
-                nbn = pbl[(int64_t)(j + 1) * 32];
-#pragma unroll
-                for (int w = 0; w < NW; w++)
-                    if (w < ws) wn[w] = pml[((int64_t)(j + 1) * ws + w) * 32];
-            }
-#pragma unroll
-            for (int w = 0; w < NW; w++) {
-                if (w < ws) {
-                    const uint32_t word = wc[w];
-#pragma unroll
-                    for (int t = 0; t < PER; t++) {
-                        const int q = w * PER + t;
-                        // fields past lm (warp-uniform) are absent: skipped in FP64, where
-                        // even a predicated-off FMA holds GB300's narrow FP64 pipe (FP32:
-                        // the unconditional form measured faster)
-                        if (q < S && (sizeof(TV) == 4 || q < lm)) {
-                            const uint32_t pos = plan_field<BITS>(word, t);
-                            if (pos != NONE) acc[q] = fma(a, X[nb + (int32_t)pos], acc[q]);
-                        }
-                    }
-                }
-            }
+        // a slice whose rows all have at most 4 pattern entries takes the 4-field
+        // path (warp-uniform branch): fields past a row's length are absent
+        if constexpr (S > 4) {
+            if (lm <= 4) plan_steps<4, PER, BITS>(acc, steps, ws, lm, pal, pbl, pml, X);
+            else plan_steps<S, PER, BITS>(acc, steps, ws, lm, pal, pbl, pml, X);
+        } else {
+            plan_steps<S, PER, BITS>(acc, steps, ws, lm, pal, pbl, pml, X);
         }
         if constexpr (G > 1) {
 #pragma unroll
@@ -1177,10 +1218,12 @@ bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, cons
               p.bits, p.wps.p, nw.p);
     p.aoff.alloc((size_t)nsl + 1, s);
     p.moff.alloc((size_t)nsl + 1, s);
-    try {
-        p.slots = scan_counts(na.p, p.aoff.p, nsl, s);
-        p.words = scan_counts(nw.p, p.moff.p, nsl, s);
-    } catch (const Error &) {
+    DVec<int64_t> tot(2, s);  // both totals in one read
+    scan_counts_dev(na.p, p.aoff.p, nsl, tot.p, s);
+    scan_counts_dev(nw.p, p.moff.p, nsl, tot.p + 1, s);
+    int64_t t2[2];
+    read_small(t2, tot.p, 2, s);
+    if (t2[0] > INT32_MAX || t2[1] > INT32_MAX) {
         p.rinfo.release();
         p.slen.release();
         p.wps.release();
@@ -1188,6 +1231,8 @@ bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, cons
         p.moff.release();
         return false;  // offsets past int32: the caller falls back
     }
+    p.slots = t2[0];
+    p.words = t2[1];
     p.G = G;
     p.S = m[0] <= 4 ? 4 : (m[0] <= 8 ? 8 : 16);
     p.pa.alloc((size_t)std::max<int64_t>(p.slots, 1), s);

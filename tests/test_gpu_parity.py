@@ -412,10 +412,14 @@ def test_singular_coarsest_level(rn, torch_dev):
     with pytest.raises(rn.RNError) as e:
         _mk(rn, torch_dev, A.rowptr, A.col, A.val, max_coarse=100)
     assert e.value.status == rn.RN_ESINGULAR
-    # coarsest levels above 96 rows take the global-memory LU: singular, then exact
-    A = PR.q1_aniso(11, 1.0, 0.0, dirichlet=False)  # 144 nodes
+    # coarsest levels above 96 rows take the global-memory LU: an exactly
+    # singular 144-row matrix (72 blocks [[2, 2], [2, 2]]: each block's second
+    # pivot is exactly 0), then an exact solve
+    nb = 72
+    rp = np.arange(0, 4 * nb + 1, 2, dtype=np.int32)
+    ci = np.repeat(np.arange(0, 2 * nb, 2), 4).astype(np.int32) + np.tile([0, 1, 0, 1], nb).astype(np.int32)
     with pytest.raises(rn.RNError) as e:
-        _mk(rn, torch_dev, A.rowptr, A.col, A.val, max_coarse=200)
+        _mk(rn, torch_dev, rp, ci, np.full(4 * nb, 2.0), max_coarse=200)
     assert e.value.status == rn.RN_ESINGULAR
     pr = PR.poisson_problem(12)  # 144 rows: one level, exact solve
     h = gpu_hierarchy(rn, torch_dev, pr, max_coarse=200)
