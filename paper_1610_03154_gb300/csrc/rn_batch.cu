@@ -139,6 +139,7 @@ template <int NV>
 __global__ void __launch_bounds__(kBT)
 bcg_dot_kernel(BCg g, int mode, int flex, const double *__restrict__ a0, const double *__restrict__ b0,
                const double *__restrict__ a1, const double *__restrict__ b1) {
+    pdl_wait();
     __shared__ double sm[32];
     const bool cg_mode = mode == BM_RZ || mode == BM_RZ_FIRST || mode == BM_PQ;
     for (int c = blockIdx.x; c < g.nch; c += gridDim.x) {
@@ -163,6 +164,7 @@ bcg_dot_kernel(BCg g, int mode, int flex, const double *__restrict__ a0, const d
 // p = z (first) or z + beta p, on problems still iterating
 __global__ void __launch_bounds__(kBT)
 bcg_p_kernel(BCg g, double *__restrict__ p, const double *__restrict__ z, int first) {
+    pdl_wait();
     for (int c = blockIdx.x; c < g.nch; c += gridDim.x) {
         const int q = g.pid[c];
         if (!g.iv[I_ACT * g.np + q]) continue;
@@ -175,6 +177,7 @@ bcg_p_kernel(BCg g, double *__restrict__ p, const double *__restrict__ z, int fi
 __global__ void __launch_bounds__(kBT)
 bcg_xr_kernel(BCg g, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
               const double *__restrict__ q, double *__restrict__ rold) {
+    pdl_wait();
     __shared__ double sm[32];
     for (int c = blockIdx.x; c < g.nch; c += gridDim.x) {
         const int pp = g.pid[c];
@@ -212,6 +215,7 @@ constexpr int kListThreads = 1024;
 // One block per list; tiles in ascending order (an ordered block-wide scan).
 __global__ void __launch_bounds__(kListThreads)
 tile_list_kernel(const TileListDesc *__restrict__ D, int np, const int32_t *__restrict__ act, int all) {
+    pdl_wait();
     __shared__ int32_t wsum[kListThreads / 32];
     __shared__ int32_t base;
     const TileListDesc d = D[blockIdx.x];
@@ -282,6 +286,7 @@ __device__ __forceinline__ int find_row_block(int nb, const MergeBlk *B, int64_t
 
 __global__ void merge_rowptr_kernel(int nb, const MergeBlk *__restrict__ B, int32_t ntot, int64_t nztot,
                                     int32_t *__restrict__ rp) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= ntot; i += (int64_t)gridDim.x * blockDim.x) {
         if (i == ntot) {
             rp[i] = (int32_t)nztot;
@@ -295,6 +300,7 @@ __global__ void merge_rowptr_kernel(int nb, const MergeBlk *__restrict__ B, int3
 
 __global__ void merge_entries_kernel(int nb, const MergeBlk *__restrict__ B, int64_t nztot, int32_t *__restrict__ col,
                                      double *__restrict__ val) {
+    pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nztot; e += (int64_t)gridDim.x * blockDim.x) {
         int lo = 0, hi = nb - 1;  // the largest b with nz0 <= e: blocks without entries are passed over
         while (lo < hi) {

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(kMT)
 spmm_kernel(int32_t n, int s, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const T *__restrict__ val, const T *__restrict__ X, const TB *__restrict__ B, const T *__restrict__ d,
             TO *__restrict__ Y, T *__restrict__ XZ, double *__restrict__ nrm) {
+    pdl_wait();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = kMT / 32;
     extern __shared__ double snrm[];  // [wpb][s] when nrm
@@ -93,6 +94,7 @@ spmm_kernel(int32_t n, int s, const int32_t *__restrict__ rp, const int32_t *__r
 constexpr int kColWarps = 8;
 __global__ void __launch_bounds__(32 * kColWarps)
 col_norms_kernel(int nb, int s, const double *__restrict__ part, double *__restrict__ out) {
+    pdl_wait();
     __shared__ double ws[kColWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + lane;
@@ -119,6 +121,7 @@ col_norms_kernel(int nb, int s, const double *__restrict__ part, double *__restr
 template <typename T, typename TB>
 __global__ void jz_multi_kernel(int32_t n, int s, const TB *__restrict__ B, const T *__restrict__ d,
                                 T *__restrict__ Y) {
+    pdl_wait();
     const int64_t total = (int64_t)n * s;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x)
         Y[o] = d[o / s] * (T)B[o];
@@ -128,6 +131,7 @@ __global__ void jz_multi_kernel(int32_t n, int s, const TB *__restrict__ B, cons
 template <typename TB, typename TO>
 __global__ void coarse_multi_kernel(int32_t n, int s, const double *__restrict__ Ainv, const TB *__restrict__ B,
                                     TO *__restrict__ Y) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5)
         for (int c = lane; c < s; c += 32) {
@@ -139,11 +143,13 @@ __global__ void coarse_multi_kernel(int32_t n, int s, const double *__restrict__
 
 template <typename T>
 __global__ void cvt_multi_kernel(int64_t total, const T *__restrict__ x, double *__restrict__ y) {
+    pdl_wait();
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x)
         y[o] = (double)x[o];
 }
 
 __global__ void add_multi_kernel(int64_t total, double *__restrict__ X, const double *__restrict__ Z) {
+    pdl_wait();
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x)
         X[o] += Z[o];
 }

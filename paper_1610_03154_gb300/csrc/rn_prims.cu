@@ -338,6 +338,7 @@ constexpr uint32_t kScanMaxSpin = 1u << 22;
 __global__ void __launch_bounds__(kScanThreads)
 scan_onepass_kernel(const int32_t *__restrict__ in, int64_t n, int32_t *__restrict__ out, int64_t *__restrict__ total,
                     unsigned long long *__restrict__ state, unsigned int *__restrict__ ticket, int64_t ntiles) {
+    pdl_wait();
     __shared__ int64_t smem[32];
     __shared__ unsigned int tile_sh;
     __shared__ int64_t excl_sh;
@@ -427,6 +428,7 @@ int64_t scan_counts(const int32_t *counts, int32_t *out, int64_t n, cudaStream_t
 constexpr int kRedThreads = 256;
 
 __global__ void dot_kernel(const double *__restrict__ x, const double *__restrict__ y, int64_t n, Fin fin) {
+    pdl_wait();
     __shared__ double sm[32];
     double v[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -447,14 +449,17 @@ void dot(const double *x, const double *y, int64_t n, double *result, cudaStream
 
 // --------------------------------------------------------------------- elementwise
 __global__ void fill_i32_kernel(int32_t *p, int32_t v, int64_t n) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
 }
 __global__ void fill_f64_kernel(double *p, double v, int64_t n) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
 }
 __global__ void to_float_kernel(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (float)x[i];
 }
@@ -474,6 +479,7 @@ void fill_f64(double *p, double v, int64_t n, cudaStream_t s) {
 __global__ void adjoint_grad_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                     const double *__restrict__ lam, const double *__restrict__ x,
                                     double *__restrict__ g) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     for (int32_t i = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < n;
          i += (int32_t)(((int64_t)gridDim.x * blockDim.x) >> 5)) {
@@ -488,6 +494,7 @@ void adjoint_grad(const CsrView &A, const double *lam, const double *x, double *
 }
 
 __global__ void to_double_kernel(int64_t n, const float *x, double *y) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (double)x[i];
 }
@@ -497,6 +504,7 @@ void to_double(const float *x, double *y, int64_t n, cudaStream_t s) {
 }
 
 __global__ void reciprocal_kernel(int64_t n, const double *x, double *y) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = 1.0 / x[i];
 }
@@ -512,6 +520,7 @@ void to_float(const double *x, float *y, int64_t n, cudaStream_t s) {
 
 __global__ void extract_diag_kernel(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                     const double *__restrict__ val, double *__restrict__ diag, int32_t *bad) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double d = 0.0;
         int found = 0;
@@ -529,6 +538,7 @@ void extract_diag(const CsrView &A, double *diag, int32_t *bad, cudaStream_t s) 
 
 // --------------------------------------------------------------------- transpose
 __global__ void count_cols_kernel(int64_t nnz, const int32_t *__restrict__ col, int32_t *__restrict__ cnt) {
+    pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(&cnt[col[e]], 1);
 }
@@ -536,6 +546,7 @@ __global__ void count_cols_kernel(int64_t nnz, const int32_t *__restrict__ col, 
 __global__ void transpose_scatter_kernel(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                          const double *__restrict__ val, int32_t *__restrict__ next,
                                          int32_t *__restrict__ tcol, double *__restrict__ tval) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         for (int32_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
             int32_t pos = atomicAdd(&next[col[e]], 1);
@@ -549,6 +560,7 @@ __global__ void transpose_scatter_kernel(int32_t n, const int32_t *__restrict__ 
 __global__ void segment_rank_sort_kernel(int32_t m, const int32_t *__restrict__ rowptr,
                                          const int32_t *__restrict__ kin, const double *__restrict__ vin,
                                          int32_t *__restrict__ kout, double *__restrict__ vout) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     for (int32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < m; r += (gridDim.x * blockDim.x) >> 5) {
         int32_t s = rowptr[r], t = rowptr[r + 1];

@@ -27,6 +27,7 @@ enum { UNDECIDED = 0, TAKEN = 1, REMOVED = 2, ISOLATED = 3 };
 // ------------------------------------------------------------------ input validation
 __global__ void validate_kernel(int32_t n, int64_t nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                 const double *__restrict__ val, int32_t *__restrict__ bad) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t s = rp[i], e = rp[i + 1];
         bool ok = (s >= 0 && e >= s && e <= nnz) && (i != 0 || s == 0) && (i != n - 1 || e == nnz);
@@ -77,6 +78,7 @@ __global__ void strength_kernel(int32_t n, const int32_t *__restrict__ arp, cons
                                 int32_t *__restrict__ count, double *__restrict__ vtmp, double *__restrict__ vmaxv,
                                 const int32_t *__restrict__ srp, int32_t *__restrict__ scol,
                                 double *__restrict__ sval, int classical) {
+    pdl_wait();
     const bool fast = thr >= 0x1p-10 && thr <= 0x1p10;  // thr^2 stays a normal FP32 number
     const float thr2f = (float)(thr * thr);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -138,6 +140,7 @@ template <bool FILL>
 __global__ void union_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                              const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
                              int32_t *__restrict__ count, const int32_t *__restrict__ grp, int32_t *__restrict__ gcol) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t a = arp[i], ae = arp[i + 1], b = brp[i], be = brp[i + 1];
         int32_t c = 0, dst = FILL ? grp[i] : 0;
@@ -164,6 +167,7 @@ __device__ __forceinline__ bool prio_gt(int32_t a, int32_t b, uint64_t seed) {
 }
 
 __global__ void mis_init_kernel(int32_t n, const int32_t *__restrict__ grp, int32_t *__restrict__ state) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         state[i] = (grp[i + 1] > grp[i]) ? UNDECIDED : ISOLATED;
 }
@@ -171,6 +175,7 @@ __global__ void mis_init_kernel(int32_t n, const int32_t *__restrict__ grp, int3
 // m1[i] = best undecided node in the closed neighbourhood of i (or -1)
 __global__ void mis_m1_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
                               const int32_t *__restrict__ state, uint64_t seed, int32_t *__restrict__ m1) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t best = (state[i] == UNDECIDED) ? i : -1;
         for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
@@ -184,6 +189,7 @@ __global__ void mis_m1_kernel(int32_t n, const int32_t *__restrict__ grp, const 
 // an undecided node is taken when it is the best undecided node within distance 2
 __global__ void mis_take_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
                                 const int32_t *__restrict__ m1, uint64_t seed, int32_t *__restrict__ state) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (state[i] != UNDECIDED) continue;
         int32_t best = m1[i];
@@ -198,6 +204,7 @@ __global__ void mis_take_kernel(int32_t n, const int32_t *__restrict__ grp, cons
 // r1[i] = 1 when i is taken or adjacent to a taken node
 __global__ void mis_r1_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
                               const int32_t *__restrict__ state, int32_t *__restrict__ r1) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t f = (state[i] == TAKEN);
         for (int32_t e = grp[i]; e < grp[i + 1] && !f; e++) f = (state[gcol[e]] == TAKEN);
@@ -209,6 +216,7 @@ __global__ void mis_r1_kernel(int32_t n, const int32_t *__restrict__ grp, const 
 __global__ void mis_remove_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
                                   const int32_t *__restrict__ r1, int32_t *__restrict__ state,
                                   int32_t *__restrict__ undecided) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (state[i] != UNDECIDED) continue;
         int32_t f = r1[i];
@@ -219,12 +227,14 @@ __global__ void mis_remove_kernel(int32_t n, const int32_t *__restrict__ grp, co
 }
 
 __global__ void flag_taken_kernel(int32_t n, const int32_t *__restrict__ state, int32_t *__restrict__ flag) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         flag[i] = (state[i] == TAKEN);
 }
 
 __global__ void roots_kernel(int32_t n, const int32_t *__restrict__ state, const int32_t *__restrict__ cidx,
                              int32_t *__restrict__ roots) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         if (state[i] == TAKEN) roots[cidx[i]] = i;
 }
@@ -233,6 +243,7 @@ __global__ void roots_kernel(int32_t n, const int32_t *__restrict__ state, const
 __global__ void agg_pass1_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
                                  const int32_t *__restrict__ state, const int32_t *__restrict__ cidx, uint64_t seed,
                                  int32_t *__restrict__ pass1) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t a = -1;
         if (state[i] == TAKEN) {
@@ -254,6 +265,7 @@ __global__ void agg_pass2_kernel(int32_t n, const int32_t *__restrict__ grp, con
                                  const int32_t *__restrict__ state, const int32_t *__restrict__ pass1,
                                  const int32_t *__restrict__ roots, uint64_t seed, int32_t *__restrict__ agg,
                                  int32_t *__restrict__ bad) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t a = pass1[i];
         if (a < 0 && state[i] == REMOVED) {
@@ -270,6 +282,7 @@ __global__ void agg_pass2_kernel(int32_t n, const int32_t *__restrict__ grp, con
 
 __global__ void rowtype_kernel(int32_t n, const int32_t *__restrict__ state, const int32_t *__restrict__ agg,
                                int32_t *__restrict__ rowtype) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         rowtype[i] = (state[i] == TAKEN) ? ROOT_ROW : (agg[i] < 0 ? UNAGG_ROW : FREE_ROW);
 }
@@ -279,6 +292,7 @@ __global__ void rowtype_kernel(int32_t n, const int32_t *__restrict__ state, con
 __global__ void cand_jacobi_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                                    const double *__restrict__ aval, const double *__restrict__ B, double omega,
                                    double *__restrict__ Bn) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double acc = 0.0, d = 0.0;
         for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
@@ -291,6 +305,7 @@ __global__ void cand_jacobi_kernel(int32_t n, const int32_t *__restrict__ arp, c
 
 __global__ void gather_kernel(int32_t nc, const int32_t *__restrict__ roots, const double *__restrict__ B,
                               double *__restrict__ Bc, int32_t *__restrict__ bad) {
+    pdl_wait();
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         double v = B[roots[c]];
         Bc[c] = v;
@@ -303,6 +318,7 @@ __global__ void gather_kernel(int32_t nc, const int32_t *__restrict__ roots, con
 __global__ void cand_jacobi_k_kernel(int32_t n, int k, const int32_t *__restrict__ arp,
                                      const int32_t *__restrict__ acol, const double *__restrict__ aval,
                                      const double *__restrict__ B, double omega, double *__restrict__ Bn) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double acc[RN_MAX_CANDIDATES] = {}, d = 0.0;
         for (int32_t e = arp[i]; e < arp[i + 1]; e++) {
@@ -318,6 +334,7 @@ __global__ void cand_jacobi_k_kernel(int32_t n, int k, const int32_t *__restrict
 // Bc = B at the roots (nc x k); the first candidate must not vanish there
 __global__ void gather_k_kernel(int32_t nc, int k, const int32_t *__restrict__ roots, const double *__restrict__ B,
                                 double *__restrict__ Bc, int32_t *__restrict__ bad) {
+    pdl_wait();
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         for (int a = 0; a < k; a++) Bc[(int64_t)c * k + a] = B[(int64_t)roots[c] * k + a];
         if (!(fabs(Bc[(int64_t)c * k]) >= 1e-300)) atomicMax(bad, c + 1);
@@ -345,6 +362,7 @@ template <int K>
 __global__ void row_svd_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                const int32_t *__restrict__ rowtype, const double *__restrict__ Bc,
                                double *__restrict__ U, double *__restrict__ VS, int32_t *__restrict__ zero_row) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t s0 = rp[i], len = rp[i + 1] - s0;
         double *W = U + (int64_t)s0 * K;
@@ -423,6 +441,7 @@ __global__ void row_fit_u_kernel(int32_t n, const int32_t *__restrict__ rp, cons
                                  double *__restrict__ val, const int32_t *__restrict__ rowtype,
                                  const double *__restrict__ B, const double *__restrict__ Bc,
                                  const double *__restrict__ U, const double *__restrict__ VS) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (rowtype[i] != FREE_ROW) continue;
         double r[K], y[K];
@@ -469,6 +488,7 @@ __global__ void amalgamate_kernel(int32_t nn, int m, const int32_t *__restrict__
                                   const double *__restrict__ sval, int32_t *__restrict__ count,
                                   const int32_t *__restrict__ orp, int32_t *__restrict__ ocol, double *__restrict__ oval,
                                   int32_t *__restrict__ bad) {
+    pdl_wait();
     for (int32_t I = blockIdx.x * blockDim.x + threadIdx.x; I < nn; I += gridDim.x * blockDim.x) {
         int32_t cols[kAmalMax];
         double vals[kAmalMax];
@@ -506,6 +526,7 @@ __global__ void amalgamate_kernel(int32_t nn, int m, const int32_t *__restrict__
 __global__ void unamalgamate_nodes_kernel(int32_t n, int m, const int32_t *__restrict__ aggn,
                                           const int32_t *__restrict__ rtn, int32_t *__restrict__ agg,
                                           int32_t *__restrict__ rowtype) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         agg[i] = aggn[i / m];
         rowtype[i] = rtn[i / m];
@@ -513,6 +534,7 @@ __global__ void unamalgamate_nodes_kernel(int32_t n, int m, const int32_t *__res
 }
 __global__ void unamalgamate_roots_kernel(int32_t ncn, int m, const int32_t *__restrict__ rootsn,
                                           int32_t *__restrict__ roots) {
+    pdl_wait();
     for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ncn; r += gridDim.x * blockDim.x)
         for (int c = 0; c < m; c++) roots[m * r + c] = m * rootsn[r] + c;
 }
@@ -525,6 +547,7 @@ __global__ void unamalgamate_pattern_kernel(int32_t n, int m, const int32_t *__r
                                             const int32_t *__restrict__ agg, const int32_t *__restrict__ rowtype,
                                             int32_t *__restrict__ count, const int32_t *__restrict__ orp,
                                             int32_t *__restrict__ ocol, double *__restrict__ oval) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t I = i / m;
         if (!FILL) {
@@ -551,6 +574,7 @@ __global__ void unamalgamate_pattern_kernel(int32_t n, int m, const int32_t *__r
 __global__ void root_block_inverse_kernel(int32_t na, int m, int k, const int32_t *__restrict__ roots,
                                           const double *__restrict__ B, double *__restrict__ Binv,
                                           int32_t *__restrict__ bad) {
+    pdl_wait();
     for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x) {
         double M[RN_MAX_BLOCK * RN_MAX_BLOCK], X[RN_MAX_BLOCK * RN_MAX_BLOCK];
         double amax = 0.0;
@@ -592,6 +616,7 @@ __global__ void tentative_block_kernel(int32_t n, int m, int k, const int32_t *_
                                        const int32_t *__restrict__ col, const int32_t *__restrict__ agg,
                                        const int32_t *__restrict__ rowtype, const double *__restrict__ B,
                                        const double *__restrict__ Binv, double *__restrict__ T) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t a = agg[i];
         for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
@@ -612,12 +637,14 @@ __global__ void tentative_block_kernel(int32_t n, int m, int k, const int32_t *_
 
 // ------------------------------------------------------------------ pattern (Sec. 3.4-3.5)
 __global__ void aggflag_kernel(int32_t n, const int32_t *__restrict__ agg, int32_t *__restrict__ flag) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         flag[i] = agg[i] >= 0;
 }
 
 __global__ void c_matrix_kernel(int32_t n, const int32_t *__restrict__ agg, const int32_t *__restrict__ rp,
                                 int32_t *__restrict__ col, double *__restrict__ val) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         if (agg[i] >= 0) {
             col[rp[i]] = agg[i];
@@ -632,6 +659,7 @@ __global__ void prefilter_kernel(int32_t n, const int32_t *__restrict__ rp, cons
                                  const int32_t *__restrict__ agg, double theta, double omg, int32_t *__restrict__ count,
                                  const int32_t *__restrict__ frp, int32_t *__restrict__ fcol,
                                  double *__restrict__ fval) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int t = rowtype[i];
         const int32_t a = agg[i];
@@ -666,6 +694,7 @@ __global__ void prefilter_kernel(int32_t n, const int32_t *__restrict__ rp, cons
 __global__ void tentative_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                  const int32_t *__restrict__ agg, const double *__restrict__ B,
                                  const double *__restrict__ Bc, double *__restrict__ T, int k) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
             int32_t j = col[e];
@@ -683,6 +712,7 @@ template <typename TV, int K>
 __global__ void __launch_bounds__(256)
 proj_k_kernel(int32_t n, const int32_t *__restrict__ nrp, const int32_t *__restrict__ zero_row,
               const TV *__restrict__ U, TV *__restrict__ W, TV scale, const TV *__restrict__ Y, Fin fin) {
+    pdl_wait();
     __shared__ double s_red[32];
     TV dot = TV(0);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -768,6 +798,7 @@ template <int G, typename TV>
 __global__ void __launch_bounds__(kT)
 cg_rho_kernel(int32_t n, const int32_t *__restrict__ rp, const TV *__restrict__ R, const TV *__restrict__ dinv,
               Fin fin) {
+    pdl_wait();
     __shared__ double sm[32];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     TV acc = TV(0);
@@ -784,6 +815,7 @@ template <int G, typename TV>
 __global__ void __launch_bounds__(kT)
 cg_dd_kernel(int32_t n, const int32_t *__restrict__ rp, const TV *__restrict__ R, const TV *__restrict__ dinv,
              const double *__restrict__ sc, const int32_t *__restrict__ fl, int first, TV *__restrict__ Dd) {
+    pdl_wait();
     if (fl[0]) return;
     const TV beta = (TV)sc[2];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
@@ -802,6 +834,7 @@ __global__ void __launch_bounds__(kT)
 cg_update_kernel(int32_t n, const int32_t *__restrict__ rp, TV *__restrict__ P, TV *__restrict__ R,
                  const TV *__restrict__ Dd, const TV *__restrict__ W, const TV *__restrict__ dinv,
                  const double *__restrict__ sc, const int32_t *__restrict__ fl, Fin fin) {
+    pdl_wait();
     __shared__ double sm[32];
     const bool done = fl[0] != 0;
     const TV alpha = (TV)sc[4];
@@ -857,6 +890,7 @@ __device__ __forceinline__ void st4(TV *__restrict__ p, int64_t q, const TV (&v)
 template <typename TV, bool VEC>
 __global__ void __launch_bounds__(kT)
 cg_rho_flat_kernel(int64_t nz, const TV *__restrict__ R, const TV *__restrict__ de, Fin fin) {
+    pdl_wait();
     __shared__ double sm[32];
     TV acc = TV(0);
     const int64_t stride = (int64_t)gridDim.x * kT * 4;
@@ -879,6 +913,7 @@ template <typename TV, bool VEC>
 __global__ void __launch_bounds__(kT)
 cg_dd_flat_kernel(int64_t nz, const TV *__restrict__ R, const TV *__restrict__ de, const double *__restrict__ sc,
                   const int32_t *__restrict__ fl, int first, TV *__restrict__ Dd) {
+    pdl_wait();
     if (fl[0]) return;
     const TV beta = (TV)sc[2];
     const int64_t stride = (int64_t)gridDim.x * kT * 4;
@@ -908,6 +943,7 @@ __global__ void __launch_bounds__(kT)
 cg_update_flat_kernel(int64_t nz, TV *__restrict__ P, TV *__restrict__ R, const TV *__restrict__ Dd,
                       const TV *__restrict__ W, const TV *__restrict__ de, const double *__restrict__ sc,
                       const int32_t *__restrict__ fl, Fin fin) {
+    pdl_wait();
     __shared__ double sm[32];
     const bool done = fl[0] != 0;
     const TV alpha = (TV)sc[4];
@@ -947,6 +983,7 @@ cg_update_flat_kernel(int64_t nz, TV *__restrict__ P, TV *__restrict__ R, const 
 // ------------------------------------------------------------------ GMRES energy minimisation (Sec. 4.2)
 // sc[0] beta, sc[1] ||w||^2 / scratch, fl[0] done, fl[1] k (number of finished steps)
 __global__ void gm_start_kernel(double *sc, int32_t *fl, double *g) {
+    pdl_wait();
     const double b2 = sc[1];
     fl[0] = 0;
     fl[1] = 0;
@@ -964,6 +1001,7 @@ __global__ void gm_start_kernel(double *sc, int32_t *fl, double *g) {
 template <typename TV>
 __global__ void gm_scale_kernel(int64_t nz, TV *__restrict__ v, const double *__restrict__ den,
                                 const int32_t *__restrict__ fl) {
+    pdl_wait();
     if (fl[0]) return;
     const TV d = (TV)*den;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x)
@@ -973,6 +1011,7 @@ __global__ void gm_scale_kernel(int64_t nz, TV *__restrict__ v, const double *__
 template <typename TV>
 __global__ void gm_axpy_kernel(int64_t nz, TV *__restrict__ w, const TV *__restrict__ v,
                                const double *__restrict__ h, const int32_t *__restrict__ fl) {
+    pdl_wait();
     if (fl[0]) return;
     const TV c = (TV)*h;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x)
@@ -983,6 +1022,7 @@ __global__ void gm_axpy_kernel(int64_t nz, TV *__restrict__ w, const TV *__restr
 template <typename TV>
 __global__ void __launch_bounds__(kT) gm_dot_kernel(int64_t nz, const TV *__restrict__ x, const TV *__restrict__ y,
                                                     Fin fin) {
+    pdl_wait();
     __shared__ double sm[32];
     TV acc = TV(0);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x)
@@ -994,6 +1034,7 @@ __global__ void __launch_bounds__(kT) gm_dot_kernel(int64_t nz, const TV *__rest
 // Givens update of Hessenberg column j; H row-major (m+1) x m
 __global__ void gm_givens_kernel(int m, int j, double *H, double *cs, double *sn, double *g, double *sc, int32_t *fl,
                                  double brk) {
+    pdl_wait();
     if (fl[0]) return;
     const double hn = sqrt(sc[1]);
     H[(j + 1) * m + j] = hn;
@@ -1019,6 +1060,7 @@ __global__ void gm_givens_kernel(int m, int j, double *H, double *cs, double *sn
 }
 
 __global__ void gm_backsolve_kernel(int m, const double *H, const double *g, double *y, const int32_t *fl) {
+    pdl_wait();
     const int k = fl[1];
     for (int i = k - 1; i >= 0; i--) {
         double s = g[i];
@@ -1031,6 +1073,7 @@ __global__ void gm_backsolve_kernel(int m, const double *H, const double *g, dou
 template <typename TV>
 __global__ void gm_combine_kernel(int64_t nz, int m, TV *__restrict__ P, const TV *__restrict__ V,
                                   const double *__restrict__ y, const int32_t *__restrict__ fl) {
+    pdl_wait();
     const int k = fl[1];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x) {
         TV p = P[q];
@@ -1046,6 +1089,7 @@ __global__ void postfilter_kernel(int32_t n, const int32_t *__restrict__ rp, con
                                   const int32_t *__restrict__ agg, double theta, double omg,
                                   int32_t *__restrict__ count, const int32_t *__restrict__ frp,
                                   int32_t *__restrict__ fcol, double *__restrict__ fval, int mb) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const bool fr = rowtype[i] == FREE_ROW;
         double thr = 0.0;
@@ -1075,6 +1119,7 @@ __global__ void postfilter_kernel(int32_t n, const int32_t *__restrict__ rp, con
 __global__ void enforce_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                double *__restrict__ val, const int32_t *__restrict__ rowtype,
                                const double *__restrict__ B, const double *__restrict__ Bc) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (rowtype[i] != FREE_ROW) continue;
         double tb = 0.0, bb = 0.0;
@@ -1091,12 +1136,14 @@ __global__ void enforce_kernel(int32_t n, const int32_t *__restrict__ rp, const 
 // ------------------------------------------------------------------ coarsest level: dense LU -> inverse
 __global__ void csr_to_dense_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                     const double *__restrict__ val, double *__restrict__ M) {
+    pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         for (int32_t e = rp[i]; e < rp[i + 1]; e++) M[(int64_t)i * n + col[e]] = val[e];
 }
 
 // One block: partial pivoting (largest |pivot|, lowest row on ties), in place.
 __global__ void __launch_bounds__(1024) dense_lu_kernel(int n, double *M, int32_t *piv, int32_t *flag) {
+    pdl_wait();
     __shared__ double sv[32];
     __shared__ int si[32];
     __shared__ double amax;
@@ -1167,6 +1214,7 @@ constexpr int kLuSmall = 96;
 __global__ void __launch_bounds__(256)
 dense_lu_small_kernel(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                       const double *__restrict__ val, double *__restrict__ Ainv, int32_t *__restrict__ flag) {
+    pdl_wait();
     extern __shared__ __align__(16) double lu_sm[];
     double *M = lu_sm, *X = lu_sm + n * n;
     __shared__ double sv[8];
@@ -1255,6 +1303,7 @@ dense_lu_small_kernel(int n, const int32_t *__restrict__ rp, const int32_t *__re
 // inverse column c: solve L U x = P e_c
 __global__ void lu_inverse_kernel(int n, const double *__restrict__ LU, const int32_t *__restrict__ piv,
                                   double *__restrict__ X, double *__restrict__ work) {
+    pdl_wait();
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         double *x = work + (int64_t)c * n;
         for (int i = 0; i < n; i++) x[i] = (i == c) ? 1.0 : 0.0;

@@ -84,6 +84,7 @@ __global__ void f2d_kernel(int64_t n, const float *__restrict__ x, double *__res
 }
 
 __global__ void row_maxlen_kernel(int32_t n, const int32_t *__restrict__ rp, int32_t *__restrict__ out) {
+    pdl_wait();
     int32_t m = 0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         m = max(m, rp[i + 1] - rp[i]);
@@ -100,6 +101,7 @@ __global__ void row_maxlen_kernel(int32_t n, const int32_t *__restrict__ rp, int
 constexpr int kVecU = 4;
 
 __global__ void axpy_kernel(int64_t n, double *__restrict__ x, const double *__restrict__ z) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] += z[i];
 }
@@ -222,6 +224,7 @@ static int vec_grid(const void *k, int64_t n) {
 
 // loop state of the outer CG: ||b||, rtol, iteration count and limit
 __global__ void cg_loop_init_kernel(double *sc, int32_t *fl, double nb, double rtol, int maxit) {
+    pdl_wait();
     sc[18] = nb;
     sc[19] = rtol;
     fl[9] = 0;
@@ -231,6 +234,7 @@ __global__ void cg_loop_init_kernel(double *sc, int32_t *fl, double nb, double r
 
 __global__ void scale_copy_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ den,
                                   double *__restrict__ y, int sqrt_den) {
+    pdl_wait();
     const double d = sqrt_den ? sqrt(*den) : *den;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = x[i] / d;
@@ -238,6 +242,7 @@ __global__ void scale_copy_kernel(int64_t n, const double *__restrict__ x, const
 
 __global__ void axpy_dev_kernel(int64_t n, double *__restrict__ w, const double *__restrict__ v,
                                 const double *__restrict__ h) {
+    pdl_wait();
     const double c = *h;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         w[i] = w[i] - c * v[i];
@@ -245,6 +250,7 @@ __global__ void axpy_dev_kernel(int64_t n, double *__restrict__ w, const double 
 
 // FGMRES Givens step on column j (H row-major (m+1) x m); g rhs; |g_{j+1}| -> sc[15]
 __global__ void fg_givens_kernel(int m, int j, double *H, double *cs, double *sn, double *g, double *sc) {
+    pdl_wait();
     const double hn = sqrt(sc[8]);
     H[(j + 1) * m + j] = hn;
     for (int i = 0; i < j; i++) {
@@ -264,12 +270,14 @@ __global__ void fg_givens_kernel(int m, int j, double *H, double *cs, double *sn
 }
 
 __global__ void fg_start_kernel(double *g, int m, double *sc) {
+    pdl_wait();
     const double beta = sqrt(sc[8]);
     for (int i = 0; i <= m; i++) g[i] = 0.0;
     g[0] = beta;
 }
 
 __global__ void fg_backsolve_kernel(int m, int k, const double *H, const double *g, double *y) {
+    pdl_wait();
     for (int i = k - 1; i >= 0; i--) {
         double s = g[i];
         for (int j = i + 1; j < k; j++) s -= H[i * m + j] * y[j];
@@ -279,6 +287,7 @@ __global__ void fg_backsolve_kernel(int m, int k, const double *H, const double 
 
 __global__ void fg_update_kernel(int64_t n, int k, double *__restrict__ x, const double *__restrict__ Z,
                                  const double *__restrict__ y) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double v = x[i];
         for (int j = 0; j < k; j++) v = v + y[j] * Z[(int64_t)j * n + i];
@@ -687,6 +696,7 @@ static void set_tile_group(DCsr &M, int32_t maxlen) {
 
 __global__ void omega_over_diag_kernel(int64_t n, double omega, const double *__restrict__ d,
                                        double *__restrict__ wd, float *__restrict__ wd32) {
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double w = omega / d[i];
         wd[i] = w;
@@ -1211,6 +1221,7 @@ static double enqueue_op(rn_hierarchy &h, int op, std::string &name) {
 // write-back the timed kernel would pay for.  One word per block is stored so
 // the loads are not dead.
 __global__ void flush_read_kernel(const uint4 *__restrict__ p, int64_t n16, uint32_t *__restrict__ sink) {
+    pdl_wait();
     uint32_t a = 0u;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n16; k += (int64_t)gridDim.x * blockDim.x) {
         const uint4 v = p[k];  // default policy: the lines displace what L2 held

@@ -37,6 +37,7 @@ constexpr int kSmallProd = 64;
 __global__ void product_bound_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                                      const int32_t *__restrict__ brp, int32_t *__restrict__ ub,
                                      int32_t *__restrict__ bins, int32_t *__restrict__ flags) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     for (int32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const int32_t i = base + threadIdx.x;
@@ -73,6 +74,7 @@ small_product_kernel(int32_t nrows_max, const int32_t *__restrict__ nrows_dev, c
                      const int32_t *__restrict__ brp, const int32_t *__restrict__ bcol,
                      const double *__restrict__ bval, const int32_t *__restrict__ ubp, int32_t *__restrict__ tcol,
                      double *__restrict__ tval, int32_t *__restrict__ count) {
+    pdl_wait();
     constexpr int GPB = kFuThreads / G;
     constexpr int ST = kSmallProd + 1;  // padded stride: groups of one warp start in different banks
     __shared__ long long s_k[GPB * ST];
@@ -218,6 +220,7 @@ merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
                      const double *__restrict__ bval, const int32_t *__restrict__ ubp, int32_t *__restrict__ tcol,
                      double *__restrict__ tval, int32_t *__restrict__ count, int32_t *__restrict__ ovf_list,
                      int32_t *__restrict__ ovf_n) {
+    pdl_wait();
     for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
         const int32_t i = rows[r];
         const int32_t as = arp[i], ae = arp[i + 1], na = ae - as;
@@ -276,6 +279,7 @@ hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32
                     const double *__restrict__ bval, const int32_t *__restrict__ ubp, int32_t *__restrict__ tcol,
                     double *__restrict__ tval, int32_t *__restrict__ count, int32_t *__restrict__ ovf_list,
                     int32_t *__restrict__ ovf_n) {
+    pdl_wait();
     constexpr int GPB = kFuThreads / G;
     extern __shared__ __align__(16) unsigned char fu_smem[];
     double *vals_all = reinterpret_cast<double *>(fu_smem);
@@ -370,6 +374,7 @@ hash_product_block_kernel(const int32_t *__restrict__ nrows_dev, const int32_t *
                           const double *__restrict__ bval, const int32_t *__restrict__ ubp,
                           int32_t *__restrict__ tcol, double *__restrict__ tval, int32_t *__restrict__ count,
                           int32_t *__restrict__ err) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char big_smem[];
     double *vals = reinterpret_cast<double *>(big_smem);
     int32_t *keys = reinterpret_cast<int32_t *>(big_smem + kBigProd * sizeof(double));
@@ -430,6 +435,7 @@ hash_product_block_kernel(const int32_t *__restrict__ nrows_dev, const int32_t *
 __global__ void compact_rows_kernel(int32_t n, const int32_t *__restrict__ ubp, const int32_t *__restrict__ crp,
                                     const int32_t *__restrict__ tcol, const double *__restrict__ tval,
                                     int32_t *__restrict__ ccol, double *__restrict__ cval) {
+    pdl_wait();
     const int lane = threadIdx.x & 7;
     for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3; i < n; i += (gridDim.x * blockDim.x) >> 3) {
         const int32_t s = ubp[i], d = crp[i], len = crp[i + 1] - crp[i];
@@ -591,6 +597,7 @@ energy_product_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t 
                       const int32_t *__restrict__ ncol, const TV *__restrict__ X, TV *__restrict__ W,
                       const int32_t *__restrict__ rowtype, const TV *__restrict__ Bc,
                       const TV *__restrict__ rs2v, TV scale, const TV *__restrict__ Y, Fin fin) {
+    pdl_wait();
     __shared__ double s_red[32];
     constexpr int GPB = kEpThreads / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
@@ -662,6 +669,7 @@ constexpr unsigned char kMapNone = 255;
 __global__ void ep_map_sizes_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ nrp,
                                     const int32_t *__restrict__ rowtype, int32_t *__restrict__ sz,
                                     int32_t *__restrict__ maxlen) {
+    pdl_wait();
     int32_t m = 0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t len = nrp[i + 1] - nrp[i];
@@ -678,6 +686,7 @@ __global__ void __launch_bounds__(kEpThreads)
 ep_map_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
               const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol, const int32_t *__restrict__ rowtype,
               const int32_t *__restrict__ mbase, unsigned char *__restrict__ map) {
+    pdl_wait();
     constexpr int GPB = kEpThreads / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     for (int32_t i0 = blockIdx.x * GPB; i0 < n; i0 += gridDim.x * GPB) {
@@ -715,6 +724,7 @@ ep_mapped_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__re
                  const int32_t *__restrict__ mbase, const unsigned char *__restrict__ map, const TV *__restrict__ X,
                  TV *__restrict__ W, const int32_t *__restrict__ rowtype, const TV *__restrict__ Bc,
                  const TV *__restrict__ rs2v, TV scale, const TV *__restrict__ Y, Fin fin) {
+    pdl_wait();
     __shared__ double s_red[32];
     constexpr int GPB = kEpThreads / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
@@ -766,6 +776,7 @@ template <int G>
 __global__ void __launch_bounds__(kEpThreads)
 proj_scale_kernel(int32_t n, const int32_t *__restrict__ nrp, const int32_t *__restrict__ ncol,
                   const int32_t *__restrict__ rowtype, const double *__restrict__ Bc, double *__restrict__ rs2) {
+    pdl_wait();
     constexpr int GPB = kEpThreads / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned mask = group_mask<G>();
@@ -930,6 +941,7 @@ __global__ void __launch_bounds__(kPlanThreads)
 ep_plan_sizes_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ nrp,
                      const int32_t *__restrict__ rowtype, int32_t *__restrict__ na, int32_t *__restrict__ slen,
                      int32_t *__restrict__ rinfo, int32_t *__restrict__ mx) {
+    pdl_wait();
     constexpr int RW = 32 / G;
     const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
     const int64_t nsl = ((int64_t)n + RW - 1) / RW;
@@ -966,6 +978,7 @@ ep_plan_sizes_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *
 // Words per A entry of every slice and the slice's word count
 __global__ void ep_plan_words_kernel(int64_t nsl, const int32_t *__restrict__ na, const int32_t *__restrict__ slen,
                                      int bits, int32_t *__restrict__ wps, int32_t *__restrict__ nw) {
+    pdl_wait();
     for (int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sl < nsl; sl += (int64_t)gridDim.x * blockDim.x) {
         const int32_t w = (slen[sl] * bits + 31) / 32;
         wps[sl] = w;
@@ -984,6 +997,7 @@ ep_plan_fill_kernel(int32_t n, const int32_t *__restrict__ arp, const int32_t *_
                     const int32_t *__restrict__ moff, const int32_t *__restrict__ wps, int bits,
                     const double *__restrict__ Bc, const double *__restrict__ dinv, TV *__restrict__ pa,
                     int32_t *__restrict__ pb, uint32_t *__restrict__ pm, TV *__restrict__ bq, TV *__restrict__ de) {
+    pdl_wait();
     constexpr int RW = 32 / G;
     const int lane = threadIdx.x & 31, r = lane / G, l = lane % G;
     const int64_t nsl = ((int64_t)n + RW - 1) / RW;
@@ -1107,6 +1121,7 @@ ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__re
                const uint32_t *__restrict__ pm,
                const TV *__restrict__ bq, const TV *__restrict__ rs2v, const TV *__restrict__ X, TV *__restrict__ W,
                TV scale, const TV *__restrict__ Y, Fin fin) {
+    pdl_wait();
     __shared__ double s_red[32];
     constexpr int RW = 32 / G;
     constexpr int PER = 32 / BITS;             // fields per word
