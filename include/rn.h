@@ -203,6 +203,26 @@ rn_status rn_solve_multi(rn_hierarchy *h, const double *B, double *X, int s, int
  * problem alone. */
 rn_status rn_setup_batched(int count, const rn_csr *A, const double *const *B, const double *const *Bhat,
                            const rn_params *p, int threads, rn_hierarchy **out);
+/* Independent problems set up together (Alg. 3 on the block-diagonal union of
+ * the problems; the paper sets up one operator).  rn_setup_merged builds
+ * hierarchy i for (A[i], B[i]) (device data, one candidate each) in one pass:
+ * every setup step is one set of launches for all problems, so many small
+ * problems do not each pay the setup's launch and synchronisation latency.
+ * Per problem are the aggregation priorities (a node's index within its own
+ * problem), the energy minimisation's CG step lengths and stopping test
+ * (reductions over chunks of one problem's pattern entries, in a fixed
+ * order), and the end of coarsening (a problem leaves the merged operator at
+ * its coarsest level).  So out[i] is the hierarchy rn_setup builds for
+ * problem i: the same strength, aggregates, patterns and level sizes; values
+ * agree to rounding (the CG sums run in another order).  out[i] owns its
+ * memory and a stream of its own, and is used and freed like any hierarchy
+ * (rn_solve, rn_batch_merge, rn_free).  Restrictions: params.stream NULL,
+ * p->symmetric (R = P^T), energy_method RN_ENERGY_CG, block_size 1;
+ * otherwise RN_EINVAL.  On any error every hierarchy is freed, out[] is all
+ * NULL and the status is returned (the message names the problem where it
+ * can).  Device memory comes from p's hooks (or the stream-ordered pool). */
+rn_status rn_setup_merged(int count, const rn_csr *A, const double *const *B, const rn_params *p,
+                          rn_hierarchy **out);
 rn_status rn_solve_batched(int count, rn_hierarchy *const *h, const double *const *b, double *const *x, double rtol,
                            int maxit, int threads, rn_solve_info *info);
 

@@ -235,6 +235,71 @@ extern "C" rn_status rn_setup_batched(int count, const rn_csr *A, const double *
     return st;
 }
 
+extern "C" rn_status rn_setup_merged(int count, const rn_csr *A, const double *const *B, const rn_params *p,
+                                     rn_hierarchy **out) {
+    if (!out || count < 0) {
+        rn::set_last_error("null argument or negative count");
+        return RN_EINVAL;
+    }
+    for (int i = 0; i < count; i++) out[i] = nullptr;
+    if (count == 0) return RN_OK;
+    std::vector<rn_hierarchy *> hs;  // freed with rn_free unless handed out
+    struct Guard {
+        std::vector<rn_hierarchy *> &hs;
+        cudaStream_t ws = nullptr;
+        ~Guard() {
+            if (ws) {
+                cudaStreamSynchronize(ws);
+                cudaStreamDestroy(ws);
+            }
+            for (rn_hierarchy *h : hs) rn_free(h);
+        }
+    } guard{hs};
+    RN_API_BEGIN
+    using rn::fail;
+    if (!A || !B || !p) fail(RN_EINVAL, "null argument");
+    check_params(p);
+    if (p->stream) fail(RN_EINVAL, "merged setup: params.stream must be NULL (every problem gets its own stream)");
+    if (!p->symmetric) fail(RN_EINVAL, "merged setup: symmetric problems only (R = P^T)");
+    if (p->energy_method != RN_ENERGY_CG) fail(RN_EINVAL, "merged setup: CG energy minimisation only");
+    if (p->block_size != 1) fail(RN_EINVAL, "merged setup: scalar problems only (block_size 1)");
+    std::vector<rn::CsrView> views;
+    std::vector<const double *> bs;
+    for (int i = 0; i < count; i++) {
+        const rn_csr &a = A[i];
+        if (a.n_rows <= 0 || a.n_rows != a.n_cols) fail(RN_EINVAL, rn::fmt("problem %d: A must be square and non-empty", i));
+        if (a.nnz <= 0 || a.nnz > INT32_MAX - 1) fail(RN_EINVAL, rn::fmt("problem %d: nnz out of range", i));
+        if (!a.rowptr || !a.col || !a.val || !B[i]) fail(RN_EINVAL, rn::fmt("problem %d: null array", i));
+        views.push_back(rn::CsrView{a.n_rows, a.n_cols, a.nnz, a.rowptr, a.col, a.val});
+        bs.push_back(B[i]);
+    }
+    const rn::AllocScope alloc_scope(alloc_of(*p));
+    const double t0 = rn::now_ms();
+    RN_CUDA_CHECK(cudaStreamCreate(&guard.ws));
+    for (int i = 0; i < count; i++) {
+        cudaStream_t s = nullptr;
+        RN_CUDA_CHECK(cudaStreamCreate(&s));
+        rn_hierarchy *h = new rn_hierarchy();
+        h->p = *p;
+        h->k = 1;
+        h->mb = 1;
+        h->s = s;
+        h->own_stream = true;
+        hs.push_back(h);
+    }
+    rn::build_hierarchies_merged(hs, views, bs, guard.ws);
+    for (rn_hierarchy *h : hs) rn::prepare_solve(*h);
+    for (rn_hierarchy *h : hs) RN_CUDA_CHECK(cudaStreamSynchronize(h->s));
+    const double ms = rn::now_ms() - t0;
+    for (int i = 0; i < count; i++) {
+        hs[i]->setup_ms = ms;
+        out[i] = hs[i];
+    }
+    hs.clear();
+    return RN_OK;
+    RN_API_END
+}
+
 extern "C" rn_status rn_solve_batched(int count, rn_hierarchy *const *h, const double *const *b, double *const *x,
                                       double rtol, int maxit, int threads, rn_solve_info *info) {
     if (count < 0 || (count > 0 && (!h || !b || !x))) {

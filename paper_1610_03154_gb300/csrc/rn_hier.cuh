@@ -9,6 +9,10 @@
 
 #include "rn_internal.cuh"
 
+namespace rn {
+struct MergedSetup;  // independent problems set up together (rn_setup.cu)
+}
+
 struct rn_level {
     rn::DCsr A, P, R;                       // operator, interpolation, restriction
     rn::DCsr S, N, T;                       // kept only with keep_aux
@@ -64,6 +68,8 @@ struct rn_hierarchy {
     // statistics
     double setup_ms = 0.0;
     int agg_rounds = 0;
+    // set while this hierarchy is the working copy of a merged setup
+    rn::MergedSetup *merged = nullptr;
     ~rn_hierarchy();
 };
 
@@ -124,11 +130,22 @@ template <typename T>
 void launch_subcycle(rn_hierarchy &h, T *cur_k, const char *name);
 // setup (rn_setup.cu)
 void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const double *Bhat0);
+// Independent problems set up together: out[t] receives problem t's hierarchy
+// (each already holding params, stream and scratch as rn_setup makes them).
+void build_hierarchies_merged(std::vector<rn_hierarchy *> &out, const std::vector<CsrView> &A,
+                              const std::vector<const double *> &B, cudaStream_t s);
 
 struct Pattern {  // borrowed view of a fixed interpolation pattern
     int32_t n, nc;
     int64_t nnz;
     const int32_t *rp, *col;
+};
+// Independent problems set up together: at the current level problem t of
+// the merged matrix owns rows [ro[t], ro[t + 1]) (host and device copies).
+struct SegRows {
+    int np = 0;
+    std::vector<int32_t> ro;
+    const int32_t *ro_d = nullptr;
 };
 // Context of one energy minimisation: stream, reduction scratch, scalar block
 // (>= 8 doubles), flags (>= 2 ints), settings, and optional workspaces
@@ -151,6 +168,8 @@ struct EmCtx {
     // no gather map is built; with R, Dd, W, rs2 supplied, k = 1 and FP64
     // sweeps the minimisation then allocates nothing (same results)
     bool scan_only = false;
+    // independent problems set up together: per-problem CG scalars (CG, k = 1)
+    const SegRows *seg = nullptr;
 };
 // dinv: the inverted diagonal of A (CG's preconditioner D^{-1} when c.precond)
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,

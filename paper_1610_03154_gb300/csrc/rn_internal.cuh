@@ -217,6 +217,17 @@ void read_small(T *dst, const T *dptr, size_t n, cudaStream_t s) {
     RN_CUDA_CHECK(cudaStreamSynchronize(s));
     std::memcpy(dst, h, n * sizeof(T));
 }
+// Read n elements and wait (through the pinned scratch when they fit, else a
+// plain copy into dst).
+template <typename T>
+void read_vec(T *dst, const T *dptr, size_t n, cudaStream_t s) {
+    if (n * sizeof(T) <= kPinnedBytes) {
+        read_small(dst, dptr, n, s);
+        return;
+    }
+    RN_CUDA_CHECK(cudaMemcpyAsync(dst, dptr, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    RN_CUDA_CHECK(cudaStreamSynchronize(s));
+}
 template <typename T>
 T read_scalar(const T *dptr, cudaStream_t s) {
     T v;

@@ -160,8 +160,14 @@ __global__ void union_kernel(int32_t n, const int32_t *__restrict__ arp, const i
 }
 
 // ------------------------------------------------------------------ seeded MIS-2 aggregation (Sec. 3.3)
-// priority pi(i) = (splitmix64(seed ^ i), i), compared lexicographically
-__device__ __forceinline__ bool prio_gt(int32_t a, int32_t b, uint64_t seed) {
+// priority pi(i) = (splitmix64(seed ^ i), i), compared lexicographically; i
+// is the node's index within its own problem: off is the first row of the
+// problem both nodes belong to (0 for a single problem; independent problems
+// set up together pass each row's problem offset, so every problem gets the
+// aggregates it gets alone)
+__device__ __forceinline__ bool prio_gt(int32_t a, int32_t b, uint64_t seed, int32_t off = 0) {
+    a -= off;
+    b -= off;
     uint64_t ha = splitmix64(seed ^ (uint64_t)(uint32_t)a), hb = splitmix64(seed ^ (uint64_t)(uint32_t)b);
     return ha > hb || (ha == hb && a > b);
 }
@@ -174,13 +180,15 @@ __global__ void mis_init_kernel(int32_t n, const int32_t *__restrict__ grp, int3
 
 // m1[i] = best undecided node in the closed neighbourhood of i (or -1)
 __global__ void mis_m1_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
-                              const int32_t *__restrict__ state, uint64_t seed, int32_t *__restrict__ m1) {
+                              const int32_t *__restrict__ state, uint64_t seed, const int32_t *__restrict__ roff,
+                              int32_t *__restrict__ m1) {
     pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t off = roff ? roff[i] : 0;
         int32_t best = (state[i] == UNDECIDED) ? i : -1;
         for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
             int32_t j = gcol[e];
-            if (state[j] == UNDECIDED && (best < 0 || prio_gt(j, best, seed))) best = j;
+            if (state[j] == UNDECIDED && (best < 0 || prio_gt(j, best, seed, off))) best = j;
         }
         m1[i] = best;
     }
@@ -188,14 +196,16 @@ __global__ void mis_m1_kernel(int32_t n, const int32_t *__restrict__ grp, const 
 
 // an undecided node is taken when it is the best undecided node within distance 2
 __global__ void mis_take_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
-                                const int32_t *__restrict__ m1, uint64_t seed, int32_t *__restrict__ state) {
+                                const int32_t *__restrict__ m1, uint64_t seed, const int32_t *__restrict__ roff,
+                                int32_t *__restrict__ state) {
     pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (state[i] != UNDECIDED) continue;
+        const int32_t off = roff ? roff[i] : 0;
         int32_t best = m1[i];
         for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
             int32_t c = m1[gcol[e]];
-            if (c >= 0 && (best < 0 || prio_gt(c, best, seed))) best = c;
+            if (c >= 0 && (best < 0 || prio_gt(c, best, seed, off))) best = c;
         }
         if (best == i) state[i] = TAKEN;
     }
@@ -242,17 +252,18 @@ __global__ void roots_kernel(int32_t n, const int32_t *__restrict__ state, const
 // pass 1: join the neighbouring root of largest priority
 __global__ void agg_pass1_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
                                  const int32_t *__restrict__ state, const int32_t *__restrict__ cidx, uint64_t seed,
-                                 int32_t *__restrict__ pass1) {
+                                 const int32_t *__restrict__ roff, int32_t *__restrict__ pass1) {
     pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t a = -1;
         if (state[i] == TAKEN) {
             a = cidx[i];
         } else if (state[i] == REMOVED) {
+            const int32_t off = roff ? roff[i] : 0;
             int32_t best = -1;
             for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
                 int32_t j = gcol[e];
-                if (state[j] == TAKEN && (best < 0 || prio_gt(j, best, seed))) best = j;
+                if (state[j] == TAKEN && (best < 0 || prio_gt(j, best, seed, off))) best = j;
             }
             if (best >= 0) a = cidx[best];
         }
@@ -263,16 +274,17 @@ __global__ void agg_pass1_kernel(int32_t n, const int32_t *__restrict__ grp, con
 // pass 2: join the aggregate of the pass-1 neighbour whose root has the largest priority
 __global__ void agg_pass2_kernel(int32_t n, const int32_t *__restrict__ grp, const int32_t *__restrict__ gcol,
                                  const int32_t *__restrict__ state, const int32_t *__restrict__ pass1,
-                                 const int32_t *__restrict__ roots, uint64_t seed, int32_t *__restrict__ agg,
-                                 int32_t *__restrict__ bad) {
+                                 const int32_t *__restrict__ roots, uint64_t seed, const int32_t *__restrict__ roff,
+                                 int32_t *__restrict__ agg, int32_t *__restrict__ bad) {
     pdl_wait();
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t a = pass1[i];
         if (a < 0 && state[i] == REMOVED) {
+            const int32_t off = roff ? roff[i] : 0;
             for (int32_t e = grp[i]; e < grp[i + 1]; e++) {
                 int32_t c = pass1[gcol[e]];
                 if (c < 0 || state[gcol[e]] == TAKEN) continue;
-                if (a < 0 || prio_gt(roots[c], roots[a], seed)) a = c;
+                if (a < 0 || prio_gt(roots[c], roots[a], seed, off)) a = c;
             }
             if (a < 0) atomicMax(bad, i + 1);
         }
@@ -980,6 +992,165 @@ cg_update_flat_kernel(int64_t nz, TV *__restrict__ P, TV *__restrict__ R, const 
     grid_finish<kT, 1>(v, fin, sm);  // the finisher ignores the sum once done is set
 }
 
+// ------------------------------------------------------------------ per-problem energy CG (merged setup)
+// Independent problems set up together share the pattern's value arrays
+// (problem p's entries are one contiguous range), but each keeps its own CG
+// step lengths, as if set up alone.  Reductions go by chunks of at most
+// kSegChunk entries of one problem: a block sums a chunk's entries into
+// part[c]; the last block to arrive adds every problem's chunks in chunk
+// order and runs that problem's recurrence (the single-problem finisher's,
+// per problem).  sc: 8 doubles per problem ([0] rho, [1] rho0, [2] beta,
+// [3] <D,W>, [4] alpha); fl: one "done" flag per problem.
+constexpr int kSegChunk = 4096;
+
+struct SegCg {
+    const int32_t *lo = nullptr, *hi = nullptr, *pid = nullptr, *pc = nullptr;
+    int nch = 0, np = 0;
+    double *part = nullptr;
+    unsigned *counter = nullptr;
+    double *sc = nullptr;
+    int32_t *fl = nullptr;
+    double stop = 0.0;
+};
+
+__device__ void seg_finish(const SegCg &g, int mode, int it) {
+    for (int p = threadIdx.x; p < g.np; p += blockDim.x) {
+        double v = 0.0;
+        for (int c = g.pc[p]; c < g.pc[p + 1]; c++) v += __ldcg(&g.part[c]);
+        if (g.fl[p]) continue;
+        double *sc = g.sc + 8 * p;
+        if (mode == FIN_CG_RHO) {
+            if (it == 0) sc[1] = v;
+            if (v == 0.0 || v <= g.stop * sc[1]) {
+                g.fl[p] = 1;
+                continue;
+            }
+            sc[2] = (it == 0) ? 0.0 : v / sc[0];
+            sc[0] = v;
+        } else {  // FIN_CG_DW
+            sc[3] = v;
+            if (!(v > 0.0)) {
+                g.fl[p] = 1;
+                continue;
+            }
+            sc[4] = sc[0] / v;
+        }
+    }
+}
+
+// the block's chunk sum to part[c]
+__device__ __forceinline__ void seg_chunk_store(const SegCg &g, int c, double v, double *sm) {
+    const double t = block_sum<kT>(v, sm);
+    if (threadIdx.x == 0) g.part[c] = t;
+}
+
+__device__ __forceinline__ void seg_arrive(const SegCg &g, int mode, int it) {
+    __shared__ int am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(g.counter, 1u);
+        am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        seg_finish(g, mode, it);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *g.counter = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// rho = <R, D^{-1} R> per problem
+template <typename TV>
+__global__ void __launch_bounds__(kT) seg_rho_kernel(SegCg g, const TV *__restrict__ R, const TV *__restrict__ de,
+                                                     int it) {
+    pdl_wait();
+    __shared__ double sm[32];
+    for (int c = blockIdx.x; c < g.nch; c += gridDim.x) {
+        TV acc = TV(0);
+        if (!g.fl[g.pid[c]])
+            for (int32_t q = g.lo[c] + threadIdx.x; q < g.hi[c]; q += kT) acc = fma(R[q], R[q] * de[q], acc);
+        seg_chunk_store(g, c, (double)acc, sm);
+    }
+    seg_arrive(g, FIN_CG_RHO, it);
+}
+
+// Dd = D^{-1} R (+ beta_p Dd after the first sweep)
+template <typename TV>
+__global__ void __launch_bounds__(kT) seg_dd_kernel(SegCg g, const TV *__restrict__ R, const TV *__restrict__ de,
+                                                    int first, TV *__restrict__ Dd) {
+    pdl_wait();
+    for (int c = blockIdx.x; c < g.nch; c += gridDim.x) {
+        const int p = g.pid[c];
+        if (g.fl[p]) continue;
+        const TV beta = (TV)g.sc[8 * p + 2];
+        for (int32_t q = g.lo[c] + threadIdx.x; q < g.hi[c]; q += kT) {
+            const TV z = R[q] * de[q];
+            Dd[q] = first ? z : z + beta * Dd[q];
+        }
+    }
+}
+
+// <Dd, W> per problem and alpha
+template <typename TV>
+__global__ void __launch_bounds__(kT) seg_dw_kernel(SegCg g, const TV *__restrict__ Dd, const TV *__restrict__ W) {
+    pdl_wait();
+    __shared__ double sm[32];
+    for (int c = blockIdx.x; c < g.nch; c += gridDim.x) {
+        TV acc = TV(0);
+        if (!g.fl[g.pid[c]])
+            for (int32_t q = g.lo[c] + threadIdx.x; q < g.hi[c]; q += kT) acc = fma(Dd[q], W[q], acc);
+        seg_chunk_store(g, c, (double)acc, sm);
+    }
+    seg_arrive(g, FIN_CG_DW, 0);
+}
+
+// X += alpha_p Dd, R -= alpha_p W, rho and beta per problem
+template <typename TV>
+__global__ void __launch_bounds__(kT) seg_update_kernel(SegCg g, TV *__restrict__ P, TV *__restrict__ R,
+                                                        const TV *__restrict__ Dd, const TV *__restrict__ W,
+                                                        const TV *__restrict__ de, int it) {
+    pdl_wait();
+    __shared__ double sm[32];
+    for (int c = blockIdx.x; c < g.nch; c += gridDim.x) {
+        const int p = g.pid[c];
+        TV acc = TV(0);
+        if (!g.fl[p]) {
+            const TV alpha = (TV)g.sc[8 * p + 4];
+            for (int32_t q = g.lo[c] + threadIdx.x; q < g.hi[c]; q += kT) {
+                P[q] = P[q] + alpha * Dd[q];
+                const TV rr = R[q] - alpha * W[q];
+                R[q] = rr;
+                acc = fma(rr, rr * de[q], acc);
+            }
+        }
+        seg_chunk_store(g, c, (double)acc, sm);
+    }
+    seg_arrive(g, FIN_CG_RHO, it);
+}
+
+// D^{-1} per pattern entry from the per-row diagonal inverse (1 without the preconditioner)
+template <typename TV>
+__global__ void entry_dinv_kernel(int32_t n, const int32_t *__restrict__ rp, const double *__restrict__ dinv,
+                                  TV *__restrict__ de) {
+    pdl_wait();
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const TV d = dinv ? (TV)dinv[i] : TV(1);
+        for (int32_t q = rp[i]; q < rp[i + 1]; q++) de[q] = d;
+    }
+}
+
+// out[t] = src[idx[t]] (the values of a row-pointer array at given rows)
+__global__ void gather_i32_kernel(int32_t m, const int32_t *__restrict__ src, const int32_t *__restrict__ idx,
+                                  int32_t *__restrict__ out) {
+    pdl_wait();
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) out[t] = src[idx[t]];
+}
+
 // ------------------------------------------------------------------ GMRES energy minimisation (Sec. 4.2)
 // sc[0] beta, sc[1] ||w||^2 / scratch, fl[0] done, fl[1] k (number of finished steps)
 __global__ void gm_start_kernel(double *sc, int32_t *fl, double *g) {
@@ -1372,6 +1543,13 @@ struct CgSweep {
     Fin fin;
     int G = 4;
     double nzb = 0, rpb = 0, db = 0;
+    // independent problems set up together (c.seg): per-problem scalars
+    SegCg sg;
+    DVec<int32_t> sgi, sgf;
+    DVec<double> sgd;
+    DVec<unsigned> sgc;
+    DVec<TV> sgde;
+    const TV *de_s = nullptr;  // D^{-1} per pattern entry
 
     CgSweep(const EmCtx &c_, const CsrView &A_, const Pattern &N_, double *X64, const int32_t *rowtype_,
             const double *Bc_, const double *c_dinv)
@@ -1436,7 +1614,63 @@ struct CgSweep {
             auto al = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
             vec = al(X) && al(R) && al(Dd) && al(W) && al(plan.de.p);
         }
+        if (c.seg) seg_build(c_dinv);
     }
+    // chunks of at most kSegChunk pattern entries, none across two problems
+    void seg_build(const double *c_dinv) {
+        if (c.k != 1) fail(RN_EINTERNAL, "per-problem energy minimisation needs one candidate");
+        const int np = c.seg->np;
+        DVec<int32_t> eo((size_t)np + 1, s);
+        RN_LAUNCH("energy_seg", 8.0 * (np + 1), s, gather_i32_kernel, grid_for(np + 1, 256), 256, 0, np + 1, N.rp,
+                  c.seg->ro_d, eo.p);
+        std::vector<int32_t> eoh((size_t)np + 1);
+        read_vec(eoh.data(), eo.p, (size_t)np + 1, s);
+        std::vector<int32_t> lo, hi, pid, pc((size_t)np + 1, 0);
+        for (int p = 0; p < np; p++) {
+            pc[p] = (int32_t)lo.size();
+            for (int64_t e = eoh[p]; e < eoh[p + 1]; e += kSegChunk) {
+                lo.push_back((int32_t)e);
+                hi.push_back((int32_t)std::min<int64_t>(e + kSegChunk, eoh[p + 1]));
+                pid.push_back(p);
+            }
+        }
+        pc[np] = (int32_t)lo.size();
+        const int nch = (int)lo.size();
+        std::vector<int32_t> all;
+        all.reserve(3 * (size_t)nch + np + 1);
+        all.insert(all.end(), lo.begin(), lo.end());
+        all.insert(all.end(), hi.begin(), hi.end());
+        all.insert(all.end(), pid.begin(), pid.end());
+        all.insert(all.end(), pc.begin(), pc.end());
+        sgi.alloc(all.size(), s);
+        h2d(sgi.p, all.data(), all.size(), s);
+        sgd.alloc((size_t)std::max(nch, 1) + 8 * (size_t)np, s);
+        fill_f64(sgd.p, 0.0, (int64_t)sgd.n, s);
+        sgf.alloc((size_t)np, s);
+        fill_i32(sgf.p, 0, np, s);
+        sgc.alloc(1, s);
+        RN_CUDA_CHECK(cudaMemsetAsync(sgc.p, 0, sizeof(unsigned), s));
+        sg.lo = sgi.p;
+        sg.hi = sgi.p + nch;
+        sg.pid = sgi.p + 2 * nch;
+        sg.pc = sgi.p + 3 * nch;
+        sg.nch = nch;
+        sg.np = np;
+        sg.part = sgd.p;
+        sg.sc = sgd.p + std::max(nch, 1);
+        sg.fl = sgf.p;
+        sg.counter = sgc.p;
+        sg.stop = kCgStop;
+        if (plan.ok) {
+            de_s = plan.de.p;
+        } else {
+            sgde.alloc((size_t)std::max<int64_t>(N.nnz, 1), s);
+            RN_LAUNCH("energy_seg", 4.0 * N.n + 8.0 * N.n + (double)sizeof(TV) * N.nnz, s, entry_dinv_kernel<TV>,
+                      rows_grid(N.n), kT, 0, N.n, N.rp, c.precond ? c_dinv : nullptr, sgde.p);
+            de_s = sgde.p;
+        }
+    }
+    int seg_grid() const { return std::max(1, std::min(sg.nch, 8 * num_sms())); }
     void product(const TV *Xin, TV *Wout, double scale, const TV *Y, const Fin &f) {
         const bool k1 = c.k == 1;
         const Fin none0;
@@ -1469,6 +1703,10 @@ struct CgSweep {
     void start() {
         const Fin none;
         product(X, R, -1.0, nullptr, none);
+        if (c.seg) {
+            RN_LAUNCH("energy_cg_rho", 2 * nzb, s, seg_rho_kernel<TV>, seg_grid(), kT, 0, sg, R, de_s, 0);
+            return;
+        }
         fin.mode = FIN_CG_RHO;
         fin.it = 0;
         if (plan.ok) RN_FLAT("energy_cg_rho", 2 * nzb, cg_rho_flat_kernel, N.nnz, R, plan.de.p, fin);
@@ -1476,7 +1714,10 @@ struct CgSweep {
     }
     // Dd = D^{-1} R (+ beta Dd after the first sweep)
     void direction(int it) {
-        if (plan.ok)
+        if (c.seg)
+            RN_LAUNCH("energy_cg_direction", (it == 0 ? 3 : 4) * nzb, s, seg_dd_kernel<TV>, seg_grid(), kT, 0, sg, R,
+                      de_s, it == 0 ? 1 : 0, Dd);
+        else if (plan.ok)
             RN_FLAT("energy_cg_direction", (it == 0 ? 3 : 4) * nzb, cg_dd_flat_kernel, N.nnz, R, plan.de.p, c.sc,
                     c.fl, it == 0 ? 1 : 0, Dd);
         else
@@ -1485,11 +1726,21 @@ struct CgSweep {
     }
     // W = Proj(Mask_N(A Dd)), <Dd, W> and alpha
     void sweep_product() {
+        if (c.seg) {  // the product unreduced, then <Dd, W> per problem
+            product(Dd, W, 1.0, nullptr, Fin());
+            RN_LAUNCH("energy_cg_dw", 2 * nzb, s, seg_dw_kernel<TV>, seg_grid(), kT, 0, sg, Dd, W);
+            return;
+        }
         fin.mode = FIN_CG_DW;
         product(Dd, W, 1.0, Dd, fin);
     }
     // X += alpha Dd, R -= alpha W, rho and beta
     void update(int it) {
+        if (c.seg) {
+            RN_LAUNCH("energy_cg_update", 7 * nzb, s, seg_update_kernel<TV>, seg_grid(), kT, 0, sg, X, R, Dd, W, de_s,
+                      it + 1);
+            return;
+        }
         fin.mode = FIN_CG_RHO;
         fin.it = it + 1;
         if (plan.ok)
@@ -1642,6 +1893,8 @@ void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, c
     else energy_min_cg(c, A, N, X, rowtype, Bc, dinv, sweeps);
 }
 
+static const SegRows *seg_of(const rn_hierarchy &h);
+
 static EmCtx ctx_of(rn_hierarchy &h) {
     EmCtx c;
     c.s = h.s;
@@ -1656,8 +1909,326 @@ static EmCtx ctx_of(rn_hierarchy &h) {
     // conditioning of each row's fit, so the sweeps stay FP64
     c.fp32 = h.p.precision == RN_MIXED && h.k == 1;
     c.k = h.k;
+    c.seg = seg_of(h);
     return c;
 }
+
+static void coarsest_lu(rn_hierarchy &h);
+
+// ================================================================== independent problems set up together
+// The problems' level-l operators form one block-diagonal matrix (problem t of
+// the active list owns rows [ro[t], ro[t + 1]) and the same columns), so every
+// step of Alg. 3 runs once for all of them: strength, transfer patterns,
+// energy minimisation, R and the Galerkin product never couple two blocks.
+// What is per problem: the aggregation priorities (each node's index within
+// its problem), the energy CG's step lengths (SegRows), and the end of
+// coarsening; a problem whose level is its coarsest leaves the merged matrix,
+// and every level is split into the problems' own hierarchies as it is
+// finished.
+
+// One block of a CSR copy: source rows [r0, r0 + nr) (entries [e0, e0 + ne))
+// to destination rows from dr (entries from de), columns shifted by dc.
+struct BlockCsr {
+    int32_t r0, nr, e0, ne, dr, de, dc;
+    int32_t *rp, *col;
+    double *val;
+    const int32_t *srp = nullptr, *scol = nullptr;  // source (filled from the copied matrix when null)
+    const double *sval = nullptr;
+};
+__global__ void block_csr_kernel(const BlockCsr *__restrict__ blk) {
+    pdl_wait();
+    const BlockCsr b = blk[blockIdx.y];
+    const int32_t t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    for (int32_t i = t0; i <= b.nr; i += st) b.rp[b.dr + i] = b.srp[b.r0 + i] - b.e0 + b.de;
+    for (int32_t e = t0; e < b.ne; e += st) {
+        b.col[b.de + e] = b.scol[b.e0 + e] + b.dc;
+        b.val[b.de + e] = b.sval[b.e0 + e];
+    }
+}
+// One block of a vector copy; with shift, values >= 0 get delta added (indices)
+template <typename T>
+struct BlockVec {
+    int32_t s0, n, d0;
+    T delta;
+    T *dst;
+};
+template <typename T>
+__global__ void block_vec_kernel(const BlockVec<T> *__restrict__ blk, const T *__restrict__ src, int shift) {
+    pdl_wait();
+    const BlockVec<T> b = blk[blockIdx.y];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        T v = src[b.s0 + i];
+        if (shift && v >= T(0)) v += b.delta;
+        b.dst[b.d0 + i] = v;
+    }
+}
+// every row's problem offset: roff[i] = ro[t] for ro[t] <= i < ro[t + 1]
+__global__ void row_offset_kernel(int32_t n, int np, const int32_t *__restrict__ ro, int32_t *__restrict__ roff) {
+    pdl_wait();
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int lo = 0, hi = np - 1;
+        while (lo < hi) {  // last t with ro[t] <= i
+            const int mid = (lo + hi + 1) >> 1;
+            if (ro[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        roff[i] = ro[lo];
+    }
+}
+
+struct MergedSetup {
+    std::vector<rn_hierarchy *> out;  // problem p's hierarchy
+    std::vector<int> act;             // active problems, in merged order
+    SegRows seg;                      // their row offsets at the current level
+    DVec<int32_t> ro_d, roff;         // device: row offsets, every row's problem offset
+    std::vector<int32_t> co;          // coarse row offsets (after aggregation)
+    DVec<int32_t> co_d;
+    std::vector<cudaEvent_t> ev;      // per problem: its stream's allocations are done
+    cudaStream_t s = nullptr;
+
+    ~MergedSetup() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    int np() const { return (int)act.size(); }
+    void set_rows(std::vector<int32_t> ro, int32_t n) {
+        seg.np = np();
+        seg.ro = std::move(ro);
+        ro_d.alloc(seg.ro.size(), s);
+        h2d(ro_d.p, seg.ro.data(), seg.ro.size(), s);
+        seg.ro_d = ro_d.p;
+        roff.alloc(std::max<int32_t>(n, 1), s);
+        RN_LAUNCH("merge_setup", 4.0 * n, s, row_offset_kernel, rows_grid(n), kT, 0, n, np(), ro_d.p, roff.p);
+    }
+    // values of a row-pointer array at the given block boundaries (one read)
+    std::vector<int32_t> bounds(const int32_t *rp, const int32_t *rows_d, size_t m) {
+        DVec<int32_t> g(m, s);
+        RN_LAUNCH("merge_setup", 8.0 * m, s, gather_i32_kernel, grid_for((int64_t)m, 256), 256, 0, (int32_t)m, rp,
+                  rows_d, g.p);
+        std::vector<int32_t> v(m);
+        read_vec(v.data(), g.p, m, s);
+        return v;
+    }
+    rn_level &level_of(int p, int l) {
+        auto &lev = out[p]->lev;
+        while ((int)lev.size() <= l) lev.push_back(std::make_unique<rn_level>());
+        return *lev[l];
+    }
+    // the merged stream waits for every listed problem's allocations
+    void wait_allocs(const std::vector<int> &ps) {
+        for (int p : ps) {
+            RN_CUDA_CHECK(cudaEventRecord(ev[p], out[p]->s));
+            RN_CUDA_CHECK(cudaStreamWaitEvent(s, ev[p], 0));
+        }
+    }
+    void launch_csr(std::vector<BlockCsr> b, const CsrView &M) {
+        if (b.empty()) return;
+        int32_t most = 1;
+        for (BlockCsr &x : b) {
+            most = std::max(most, std::max(x.nr + 1, x.ne));
+            if (!x.srp) {
+                x.srp = M.rowptr;
+                x.scol = M.col;
+                x.sval = M.val;
+            }
+        }
+        DVec<BlockCsr> d(b.size(), s);
+        h2d(d.p, b.data(), b.size(), s);
+        const dim3 grid((unsigned)std::min<int64_t>((most + 255) / 256, 2048), (unsigned)b.size());
+        RN_LAUNCH("merge_setup", 12.0 * M.nnz, s, block_csr_kernel, grid, 256, 0, d.p);
+    }
+    template <typename T>
+    void launch_vec(const std::vector<BlockVec<T>> &b, const T *src, int shift) {
+        if (b.empty()) return;
+        int32_t most = 1;
+        for (const BlockVec<T> &x : b) most = std::max(most, x.n);
+        DVec<BlockVec<T>> d(b.size(), s);
+        h2d(d.p, b.data(), b.size(), s);
+        const dim3 grid((unsigned)std::min<int64_t>((most + 255) / 256, 2048), (unsigned)b.size());
+        RN_LAUNCH("merge_setup", 0.0, s, block_vec_kernel<T>, grid, 256, 0, d.p, src, shift);
+    }
+    // problem blocks (merged index t) of a CSR with rows at rof and columns at cof,
+    // each into level l of its problem's hierarchy (field f)
+    void split_csr(const DCsr &M, const std::vector<int32_t> &rof, const int32_t *rof_d,
+                   const std::vector<int32_t> &cof, const std::vector<int> &ts, int l, DCsr rn_level::*f,
+                   std::vector<BlockCsr> &blk) {
+        const std::vector<int32_t> eb = bounds(M.rowptr.p, rof_d, rof.size());
+        for (int t : ts) {
+            const int p = act[t];
+            DCsr &X = level_of(p, l).*f;
+            cudaStream_t ps = out[p]->s;
+            X.n = rof[t + 1] - rof[t];
+            X.m = cof[t + 1] - cof[t];
+            X.nnz = eb[t + 1] - eb[t];
+            X.rowptr.alloc((size_t)X.n + 1, ps);
+            X.col.alloc((size_t)X.nnz, ps);
+            X.val.alloc((size_t)X.nnz, ps);
+            blk.push_back(BlockCsr{rof[t], X.n, eb[t], (int32_t)X.nnz, 0, 0, -cof[t], X.rowptr.p, X.col.p, X.val.p});
+        }
+    }
+    template <typename T>
+    void split_vec(const std::vector<int32_t> &rof, const std::vector<int32_t> &dof, const std::vector<int> &ts,
+                   int l, DVec<T> rn_level::*f, std::vector<BlockVec<T>> &blk) {
+        for (int t : ts) {
+            const int p = act[t];
+            DVec<T> &X = level_of(p, l).*f;
+            const int32_t n = rof[t + 1] - rof[t];
+            X.alloc((size_t)n, out[p]->s);
+            blk.push_back(BlockVec<T>{rof[t], n, 0, (T)(dof.empty() ? 0 : -dof[t]), X.p});
+        }
+    }
+    // level l is the coarsest of the listed problems: A, diag, B
+    void split_coarsest(rn_level &L, const std::vector<int> &ts, int l) {
+        if (ts.empty()) return;
+        const std::vector<int32_t> &ro = seg.ro;
+        std::vector<BlockCsr> ba;
+        std::vector<BlockVec<double>> bd, bb;
+        split_csr(L.A, ro, ro_d.p, ro, ts, l, &rn_level::A, ba);
+        split_vec(ro, {}, ts, l, &rn_level::diag, bd);
+        split_vec(ro, {}, ts, l, &rn_level::B, bb);
+        std::vector<int> ps;
+        for (int t : ts) ps.push_back(act[t]);
+        wait_allocs(ps);
+        launch_csr(ba, view(L.A));
+        launch_vec(bd, L.diag.p, 0);
+        launch_vec(bb, L.B.p, 0);
+    }
+    // keep only the listed problems in the merged level (A, B; diag is recomputed by the caller)
+    void keep_only(rn_level &L, const std::vector<int> &ts) {
+        const std::vector<int32_t> &ro = seg.ro;
+        const std::vector<int32_t> eb = bounds(L.A.rowptr.p, ro_d.p, ro.size());
+        std::vector<int32_t> nro(1, 0);
+        int64_t nnz = 0;
+        for (int t : ts) {
+            nro.push_back(nro.back() + (ro[t + 1] - ro[t]));
+            nnz += eb[t + 1] - eb[t];
+        }
+        const int32_t n = nro.back();
+        DCsr A;
+        A.n = A.m = n;
+        A.nnz = nnz;
+        A.rowptr.alloc((size_t)n + 1, s);
+        A.col.alloc((size_t)nnz, s);
+        A.val.alloc((size_t)nnz, s);
+        DVec<double> B((size_t)n, s);
+        std::vector<BlockCsr> ba;
+        std::vector<BlockVec<double>> bb;
+        int32_t de = 0;
+        for (size_t u = 0; u < ts.size(); u++) {
+            const int t = ts[u];
+            const int32_t ne = eb[t + 1] - eb[t];
+            ba.push_back(BlockCsr{ro[t], ro[t + 1] - ro[t], eb[t], ne, nro[u], de, nro[u] - ro[t], A.rowptr.p,
+                                  A.col.p, A.val.p});
+            bb.push_back(BlockVec<double>{ro[t], ro[t + 1] - ro[t], nro[u], 0.0, B.p});
+            de += ne;
+        }
+        launch_csr(ba, view(L.A));
+        launch_vec(bb, L.B.p, 0);
+        std::vector<int> nact;
+        for (int t : ts) nact.push_back(act[t]);
+        act = std::move(nact);
+        L.A = std::move(A);
+        L.B = std::move(B);
+        set_rows(std::move(nro), n);
+    }
+    std::vector<int> all_but(const std::vector<int> &ts) const {
+        std::vector<char> drop((size_t)np(), 0);
+        for (int t : ts) drop[t] = 1;
+        std::vector<int> keep;
+        for (int t = 0; t < np(); t++)
+            if (!drop[t]) keep.push_back(t);
+        return keep;
+    }
+    // hook after the level's diagonal: problems small enough (or at the level
+    // limit) end here.  Returns true when no problem is left.
+    bool end_small(rn_hierarchy &W, int l, int maxlev) {
+        rn_level &L = *W.lev[l];
+        std::vector<int> ending;
+        for (int t = 0; t < np(); t++)
+            if (seg.ro[t + 1] - seg.ro[t] <= W.p.max_coarse || l >= maxlev - 1) ending.push_back(t);
+        if (ending.empty()) return false;
+        split_coarsest(L, ending, l);
+        if ((int)ending.size() == np()) return true;
+        keep_only(L, all_but(ending));
+        L.diag.alloc((size_t)L.A.n, s);
+        fill_i32(W.iflags.p + 4, 0, 1, s);
+        extract_diag(view(L.A), L.diag.p, W.iflags.p + 4, s);
+        return false;
+    }
+    // hook after aggregation: problems whose coarsening stalled (no aggregate,
+    // or as many aggregates as nodes) end at this level.  Returns 0 (go on:
+    // co holds the coarse offsets), 1 (redo the level without them) or 2 (no
+    // problem left).
+    int stalled(rn_hierarchy &W, int l, const int32_t *cidx) {
+        rn_level &L = *W.lev[l];
+        const std::vector<int32_t> cb = bounds(cidx, ro_d.p, seg.ro.size());
+        std::vector<int> st;
+        for (int t = 0; t < np(); t++) {
+            const int32_t nct = cb[t + 1] - cb[t];
+            if (nct == 0 || nct >= seg.ro[t + 1] - seg.ro[t]) st.push_back(t);
+        }
+        if (st.empty()) {
+            co.assign(cb.begin(), cb.end());
+            for (auto &v : co) v -= cb[0];
+            co_d.alloc(co.size(), s);
+            h2d(co_d.p, co.data(), co.size(), s);
+            return 0;
+        }
+        split_coarsest(L, st, l);
+        if ((int)st.size() == np()) return 2;
+        keep_only(L, all_but(st));
+        return 1;
+    }
+    // hook after the Galerkin product: level l of every active problem (A,
+    // diag, B, rowtype, Bc, P, R, and with keep_aux S, N, T, roots, agg); the
+    // next level's rows are the coarse offsets
+    void split_level(rn_hierarchy &W, int l) {
+        rn_level &L = *W.lev[l];
+        rn_level &Lc = *W.lev[l + 1];
+        const std::vector<int32_t> &ro = seg.ro;
+        std::vector<int> ts(np());
+        for (int t = 0; t < np(); t++) ts[t] = t;
+        std::vector<BlockCsr> ba, bp, br, bs, bn, bt;
+        std::vector<BlockVec<double>> bd, bb, bc;
+        std::vector<BlockVec<int32_t>> brt, bro, bag;
+        split_csr(L.A, ro, ro_d.p, ro, ts, l, &rn_level::A, ba);
+        split_csr(L.P, ro, ro_d.p, co, ts, l, &rn_level::P, bp);
+        split_csr(L.R, co, co_d.p, ro, ts, l, &rn_level::R, br);
+        split_vec(ro, {}, ts, l, &rn_level::diag, bd);
+        split_vec(ro, {}, ts, l, &rn_level::B, bb);
+        split_vec(co, {}, ts, l, &rn_level::Bc, bc);
+        split_vec(ro, {}, ts, l, &rn_level::rowtype, brt);
+        const bool aux = W.p.keep_aux != 0;
+        if (aux) {
+            split_csr(L.S, ro, ro_d.p, ro, ts, l, &rn_level::S, bs);
+            split_csr(L.N, ro, ro_d.p, co, ts, l, &rn_level::N, bn);
+            split_csr(L.T, ro, ro_d.p, co, ts, l, &rn_level::T, bt);
+            split_vec(co, ro, ts, l, &rn_level::roots, bro);
+            split_vec(ro, co, ts, l, &rn_level::agg, bag);
+        }
+        for (int t : ts) level_of(act[t], l).nc = co[t + 1] - co[t];
+        wait_allocs(act);
+        launch_csr(ba, view(L.A));
+        launch_csr(bp, view(L.P));
+        launch_csr(br, view(L.R));
+        launch_vec(bd, L.diag.p, 0);
+        launch_vec(bb, L.B.p, 0);
+        launch_vec(bc, L.Bc.p, 0);
+        launch_vec(brt, L.rowtype.p, 0);
+        if (aux) {
+            launch_csr(bs, view(L.S));
+            launch_csr(bn, view(L.N));
+            launch_csr(bt, view(L.T));
+            launch_vec(bro, L.roots.p, 1);
+            launch_vec(bag, L.agg.p, 1);
+        }
+        // the merged level is no longer needed once its copies have run (stream order)
+        W.lev[l] = std::make_unique<rn_level>();
+        set_rows(co, Lc.A.n);
+    }
+};
+
+static const SegRows *seg_of(const rn_hierarchy &h) { return h.merged ? &h.merged->seg : nullptr; }
 
 static void check_flag(const int32_t *flag, cudaStream_t s, rn_status st, const char *what) {
     int32_t v = read_scalar(flag, s);
@@ -1813,15 +2384,21 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         h.lev.push_back(std::move(L));
     }
     const int maxlev = std::max(1, std::min(p.max_levels, RN_MAX_LEVELS));
+    MergedSetup *ms = h.merged;
     for (int l = 0;; l++) {
         rn_level &L = *h.lev[l];
+        L.diag.alloc(L.A.n, s);
+        fill_i32(h.iflags.p + 4, 0, 1, s);
+        extract_diag(view(L.A), L.diag.p, h.iflags.p + 4, s);
+        if (ms) {
+            if (ms->end_small(h, l, maxlev)) break;  // every problem has reached its coarsest level
+        } else if (L.A.n <= p.max_coarse || l >= maxlev - 1) {
+            break;
+        }
         const int32_t n = L.A.n;
         CsrView A = view(L.A);
-        L.diag.alloc(n, s);
-        fill_i32(h.iflags.p + 4, 0, 1, s);
-        extract_diag(A, L.diag.p, h.iflags.p + 4, s);
-        if (n <= p.max_coarse || l >= maxlev - 1) break;
         check_flag(h.iflags.p + 4, s, RN_EINVAL, "missing or zero diagonal");
+        const int32_t *roff = ms ? ms->roff.p : nullptr;  // aggregation priorities within each problem
         // ---- strength (line 'strength')
         const double theta = (l > 0 && p.soc_theta_coarse >= 0.0) ? p.soc_theta_coarse : p.soc_theta;
         const double thr = theta * omg;
@@ -1884,9 +2461,9 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             if (rounds >= kMaxAggRounds) fail(RN_ETIMEOUT, fmt("aggregation did not finish in %d rounds", rounds));
             fill_i32(h.iflags.p + 5, 0, 1, s);
             RN_LAUNCH("mis2", gb + 8.0 * nn, s, mis_m1_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p, state.p,
-                      seed, m1.p);
+                      seed, roff, m1.p);
             RN_LAUNCH("mis2", gb + 8.0 * nn, s, mis_take_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p, m1.p,
-                      seed, state.p);
+                      seed, roff, state.p);
             RN_LAUNCH("mis2", gb + 8.0 * nn, s, mis_r1_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p, state.p,
                       r1.p);
             RN_LAUNCH("mis2", gb + 8.0 * nn, s, mis_remove_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p, r1.p,
@@ -1899,7 +2476,16 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         DVec<int32_t> cidx(nn + 1, s);
         RN_LAUNCH("aggregate", 8.0 * nn, s, flag_taken_kernel, rows_grid(nn), kT, 0, nn, state.p, m1.p);
         const int32_t ncn = (int32_t)scan_counts(m1.p, cidx.p, nn, s);  // node aggregates
-        if (ncn == 0 || ncn >= nn) break;  // stalled: this level is the coarsest
+        if (ms) {
+            const int st = ms->stalled(h, l, cidx.p);
+            if (st == 2) break;  // every remaining problem stalled here
+            if (st == 1) {       // the level again without the problems that stalled
+                l--;
+                continue;
+            }
+        } else if (ncn == 0 || ncn >= nn) {
+            break;  // stalled: this level is the coarsest
+        }
         const int32_t nc = mb * ncn;       // coarse unknowns: m per root node
         L.nc = nc;
         L.roots.alloc(nc, s);
@@ -1915,10 +2501,10 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         int32_t *rt_n = mb > 1 ? rtN.p : L.rowtype.p;
         RN_LAUNCH("aggregate", 12.0 * nn, s, roots_kernel, rows_grid(nn), kT, 0, nn, state.p, cidx.p, roots_n);
         RN_LAUNCH("aggregate", gb + 12.0 * nn, s, agg_pass1_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p,
-                  state.p, cidx.p, seed, r1.p);
+                  state.p, cidx.p, seed, roff, r1.p);
         fill_i32(h.iflags.p + 6, 0, 1, s);
         RN_LAUNCH("aggregate", gb + 16.0 * nn, s, agg_pass2_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p,
-                  state.p, r1.p, roots_n, seed, agg_n, h.iflags.p + 6);
+                  state.p, r1.p, roots_n, seed, roff, agg_n, h.iflags.p + 6);
         check_flag(h.iflags.p + 6, s, RN_EINTERNAL, "aggregation pass 2 left a node unassigned");
         RN_LAUNCH("aggregate", 12.0 * nn, s, rowtype_kernel, rows_grid(nn), kT, 0, nn, state.p, agg_n, rt_n);
         if (mb > 1) {  // unamalgamate: aggregates, row types and roots of the unknowns
@@ -2010,8 +2596,21 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             L.N = std::move(N);
         }
         h.lev.push_back(std::move(Lc));
+        if (ms) ms->split_level(h, l);  // releases the merged level l (L is not used past this point)
     }
-    // ---- coarsest level: dense LU with partial pivoting, kept as an explicit inverse
+    if (ms) return;  // every problem's coarsest level is factored by the caller
+    coarsest_lu(h);
+    if (!p.keep_aux) {
+        for (auto &Lp : h.lev) {
+            Lp->agg.release();
+            Lp->roots.release();
+        }
+    }
+}
+
+// The coarsest level: dense LU with partial pivoting, kept as an explicit inverse
+static void coarsest_lu(rn_hierarchy &h) {
+    cudaStream_t s = h.s;
     rn_level &C = *h.lev.back();
     const int32_t nL = C.A.n;
     if (nL > kMaxDense)
@@ -2043,12 +2642,91 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         RN_LAUNCH("coarse_lu", 24.0 * nL * nL, s, lu_inverse_kernel, grid_for(nL, 64, 4), 64, 0, nL, M.p, piv.p, h.Ainv.p,
                   work.p);
     }
-    if (!p.keep_aux) {
-        for (auto &Lp : h.lev) {
-            Lp->agg.release();
-            Lp->roots.release();
-        }
+}
+
+// Independent problems set up together (see MergedSetup): out[t] must hold
+// problem t's params (CG energy minimisation, one candidate, scalar problems,
+// R = P^T), stream and no levels; A[t] and B[t] are device data.
+void build_hierarchies_merged(std::vector<rn_hierarchy *> &out, const std::vector<CsrView> &A,
+                              const std::vector<const double *> &B, cudaStream_t s) {
+    const int np = (int)out.size();
+    if (np == 0) return;
+    rn_hierarchy W;  // the working hierarchy of the merged matrices
+    W.p = out[0]->p;
+    W.k = 1;
+    W.mb = 1;
+    W.s = s;
+    MergedSetup ms;
+    ms.out = out;
+    ms.s = s;
+    ms.act.resize(np);
+    ms.ev.assign(np, nullptr);
+    for (int t = 0; t < np; t++) {
+        ms.act[t] = t;
+        RN_CUDA_CHECK(cudaEventCreateWithFlags(&ms.ev[t], cudaEventDisableTiming));
     }
+    // every problem's scratch, as build_hierarchy allocates it
+    for (rn_hierarchy *h : out) {
+        h->partial.alloc(2 * kReduceBlocks, h->s);
+        h->counters.alloc(4, h->s);
+        RN_CUDA_CHECK(cudaMemsetAsync(h->counters.p, 0, 4 * sizeof(unsigned), h->s));
+        h->scal.alloc(64, h->s);
+        h->iflags.alloc(16, h->s);
+        fill_f64(h->scal.p, 0.0, 64, h->s);
+        fill_i32(h->iflags.p, 0, 16, h->s);
+    }
+    // each problem's CSR checked on its own (a column past its own size is an error)
+    {
+        DVec<int32_t> bad((size_t)np, s);
+        fill_i32(bad.p, 0, np, s);
+        for (int t = 0; t < np; t++)
+            RN_LAUNCH("validate", 12.0 * A[t].nnz + 4.0 * A[t].n, s, validate_kernel, rows_grid(A[t].n), kT, 0,
+                      A[t].n, A[t].nnz, A[t].rowptr, A[t].col, A[t].val, bad.p + t);
+        std::vector<int32_t> bh((size_t)np);
+        read_vec(bh.data(), bad.p, (size_t)np, s);
+        for (int t = 0; t < np; t++)
+            if (bh[t])
+                fail(RN_EINVAL, fmt("problem %d: CSR row %d malformed (bounds, unsorted/duplicate columns, no "
+                                    "diagonal, or non-finite value)", t, bh[t] - 1));
+    }
+    // the merged level-0 operator and candidates
+    std::vector<int32_t> ro(1, 0);
+    std::vector<int64_t> eo(1, 0);
+    for (int t = 0; t < np; t++) {
+        ro.push_back(ro.back() + A[t].n);
+        eo.push_back(eo.back() + A[t].nnz);
+    }
+    if (eo.back() > INT32_MAX - 1 || ro.back() > INT32_MAX - 1) fail(RN_EINVAL, "merged problems exceed int32 sizes");
+    DCsr M;
+    M.n = M.m = ro.back();
+    M.nnz = eo.back();
+    M.rowptr.alloc((size_t)M.n + 1, s);
+    M.col.alloc((size_t)M.nnz, s);
+    M.val.alloc((size_t)M.nnz, s);
+    DVec<double> Bm((size_t)M.n, s);
+    {
+        std::vector<BlockCsr> blk;
+        for (int t = 0; t < np; t++) {
+            BlockCsr b{0, A[t].n, 0, (int32_t)A[t].nnz, ro[t], (int32_t)eo[t], ro[t], M.rowptr.p, M.col.p, M.val.p};
+            b.srp = A[t].rowptr;
+            b.scol = A[t].col;
+            b.sval = A[t].val;
+            blk.push_back(b);
+            d2d(Bm.p + ro[t], B[t], (size_t)A[t].n, s);
+        }
+        ms.launch_csr(blk, view(M));
+    }
+    ms.set_rows(ro, M.n);
+    W.merged = &ms;
+    build_hierarchy(W, view(M), Bm.p, nullptr);
+    W.merged = nullptr;
+    cudaEvent_t done = ms.ev[0];
+    RN_CUDA_CHECK(cudaEventRecord(done, s));
+    for (rn_hierarchy *h : out) {
+        RN_CUDA_CHECK(cudaStreamWaitEvent(h->s, done, 0));
+        h->agg_rounds = W.agg_rounds;
+    }
+    for (rn_hierarchy *h : out) coarsest_lu(*h);
 }
 
 // ================================================================== measurement hook

@@ -81,6 +81,7 @@ def _load():
                                  P(rn_solve_info)]
     L.rn_setup_batched.argtypes = [C.c_int, P(rn_csr), P(C.c_void_p), P(C.c_void_p), P(rn_params), C.c_int,
                                    P(C.c_void_p)]
+    L.rn_setup_merged.argtypes = [C.c_int, P(rn_csr), P(C.c_void_p), P(rn_params), P(C.c_void_p)]
     L.rn_solve_batched.argtypes = [C.c_int, P(C.c_void_p), P(C.c_void_p), P(C.c_void_p), C.c_double, C.c_int,
                                    C.c_int, P(rn_solve_info)]
     L.rn_free.argtypes = [C.c_void_p]
@@ -124,6 +125,7 @@ rn_solve = lib.rn_solve
 rn_vcycle = lib.rn_vcycle
 rn_solve_multi = lib.rn_solve_multi
 rn_setup_batched = lib.rn_setup_batched
+rn_setup_merged = lib.rn_setup_merged
 rn_solve_batched = lib.rn_solve_batched
 rn_free = lib.rn_free
 rn_batch_merge = lib.rn_batch_merge
@@ -191,6 +193,33 @@ def setup_batched(problems, params=None, threads=0):
         Bh[i] = _ptr(pr[4]) if len(pr) > 4 and pr[4] is not None else None
     out = (C.c_void_p * k)()
     _check(rn_setup_batched(k, A, Bp, Bh, C.byref(params), threads, out), "rn_setup_batched")
+    hs = []
+    for i in range(k):
+        h = Hierarchy.__new__(Hierarchy)
+        h.n = int(problems[i][0].shape[0]) - 1
+        h.params = params
+        h._keep = None
+        h._h = C.c_void_p(out[i])
+        hs.append(h)
+    return hs
+
+
+def setup_merged(problems, params=None):
+    """Hierarchies for many problems built in one merged pass (rn_setup_merged).
+    problems: a list of (rowptr, col, val, B) device tensors (symmetric, one
+    candidate); returns a list of Hierarchy."""
+    if params is None:
+        params = default_params()
+    k = len(problems)
+    A = (rn_csr * k)()
+    Bp = (C.c_void_p * k)()
+    for i, pr in enumerate(problems):
+        rp, ci, va, B = pr[:4]
+        n = int(rp.shape[0]) - 1
+        A[i] = rn_csr(n, n, int(ci.shape[0]), _ptr(rp), _ptr(ci), _ptr(va))
+        Bp[i] = _ptr(B)
+    out = (C.c_void_p * k)()
+    _check(rn_setup_merged(k, A, Bp, C.byref(params), out), "rn_setup_merged")
     hs = []
     for i in range(k):
         h = Hierarchy.__new__(Hierarchy)
