@@ -380,7 +380,8 @@ def next_rows(rn, torch, dev, stream, flush, prec):
     """Records for the batched and differentiable forms, each one warm-up
     and one timed pass with device-resident inputs (CUDA events, L2 flushed):
     256 right-hand sides on the 64^2 Poisson operator (setup + rn_solve_multi),
-    64 uneven rotated-anisotropy problems (rn_setup_batched + rn_solve_batched)
+    64 uneven rotated-anisotropy problems (rn_setup_merged + rn_batch_merge +
+    rn_batch_solve, beside the per-problem setups and solves)
     and a gradient through the solve on 512^2 variable-coefficient cells
     (forward setup + solve, adjoint solve, dL/dA scatter, chain to theta)."""
     from paper_1610_03154_gb300 import adjoint
@@ -454,11 +455,11 @@ def next_rows(rn, torch, dev, stream, flush, prec):
 
     phases = {}
 
-    def batched_merged():
+    def batched_merged(setup=rn.setup_merged):
         for x in xs:
             x.zero_()
         t0 = time.perf_counter()
-        hs = rn.setup_batched(dp, params=bparams)
+        hs = setup(dp, params=bparams)
         t1 = time.perf_counter()
         batch = rn.Batch(hs)
         for h in hs:
@@ -471,6 +472,8 @@ def next_rows(rn, torch, dev, stream, flush, prec):
         return infos
 
     tbs, ibs = clock(batched_streams)
+    tbt, ibt = clock(lambda: batched_merged(rn.setup_batched))
+    phases_st = dict(phases)
     tb, ib = clock(batched_merged)
     phases_thr = dict(phases)
     bparams_thr = bparams
@@ -518,9 +521,14 @@ def next_rows(rn, torch, dev, stream, flush, prec):
                              "autotuned": {"step_s": tba, "max_iters": max(i["iters"] for i in iba), "phases_s": phases_at,
                                            "what": "the same with the merged hierarchy's SpMV schedules picked by "
                                                    "timed trials (params.autotune)"},
-                             "what": "rn_setup_batched + rn_batch_merge + rn_batch_solve (CG per problem, one "
-                                     "launch per step for all problems), sides U{32..512}, eps 10^U[-4,-1], "
-                                     "psi U[0,pi)",
+                             "what": "rn_setup_merged (one setup pass over the block-diagonal union, per-problem "
+                                     "aggregation keys, energy-CG scalars and coarsening stops) + rn_batch_merge + "
+                                     "rn_batch_solve (CG per problem, one launch per step for all problems), sides "
+                                     "U{32..512}, eps 10^U[-4,-1], psi U[0,pi)",
+                             "setup_per_problem": {"step_s": tbt, "max_iters": max(i["iters"] for i in ibt),
+                                                   "phases_s": phases_st,
+                                                   "what": "the same with rn_setup_batched (a setup per problem on "
+                                                           "its own stream, host threads)"},
                              "streams_step_s": tbs, "streams_max_iters": max(i["iters"] for i in ibs),
                              "streams_what": "rn_setup_batched + rn_solve_batched (a stream and host thread per "
                                              "problem)", "precision": prec},
