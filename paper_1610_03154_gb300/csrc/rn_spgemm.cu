@@ -31,6 +31,11 @@ namespace rn {
 // compaction produce C.
 constexpr int kFuThreads = 128;
 constexpr int kSmallProd = 64;
+// Products with at most this many rows (the coarse levels) are bound by the
+// latency of each row's chain of dependent loads, not by the machine's
+// throughput: they take more lanes per row (sorted lists for short rows,
+// warp-wide hash tables for long ones)
+constexpr int32_t kFewRows = 40000;
 
 // Product counts, and the row lists of the two bins: rows with at most
 // kSmallProd products fill bins from the front, the others from the back.
@@ -520,7 +525,11 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fu
     DVec<double> tval(total > 0 ? total : 1, s);
     const double bytes = 12.0 * A.nnz + 8.0 * n + 12.0 * B.nnz + 12.0 * total;
     const int32_t nsmall = fl[0], nlarge = fl[1];
-    if (nsmall) {
+    if (nsmall && n <= kFewRows) {  // few rows: G lanes per row list, sort and sum each row's products
+        const double avg = (double)A.nnz / std::max(1, n) * ((double)B.nnz / std::max(1, B.n));
+        if (avg <= 8.0) launch_small<8>(nsmall, nullptr, bins.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+        else launch_small<16>(nsmall, nullptr, bins.p, A, B, ubp.p, tcol.p, tval.p, count.p, bytes, s);
+    } else if (nsmall) {
         // merge rows of few entries; the bin's other rows (counted on the
         // device) go to the sort kernel, launched for at most nsmall rows
         if (fused)
@@ -549,7 +558,10 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fu
         // sums per column run in ascending k either way (same result), and rows
         // past a table go to the block kernel
         const double avgB = B.n ? (double)B.nnz / B.n : 0.0;
-        if (avgB <= 12.0)
+        if (n <= kFewRows)  // few rows: a warp per row spreads each row's products widest
+            launch_hash<32, 1024>(fused, nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
+                                  flags.p + 3, bytes, s);
+        else if (avgB <= 12.0)
             launch_hash<8, 128>(fused, nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
                                 flags.p + 3, bytes, s);
         else if (avgB <= 16.0)
@@ -1185,7 +1197,8 @@ ep_plan_kernel(int32_t n, const int32_t *__restrict__ rinfo, const int32_t *__re
 }
 
 // lanes per row from the average length of A's rows
-static int plan_group(double avg_a) {
+static int plan_group(double avg_a, int32_t n) {
+    if (n <= kFewRows) return 8;  // few rows: the shortest chain of gathers per lane
     if (avg_a <= 12.0) return 1;
     if (avg_a <= 24.0) return 2;
     if (avg_a <= 48.0) return 4;
@@ -1198,7 +1211,7 @@ bool ep_plan_build(EpPlan<TV> &p, const CsrView &A, const int32_t *nrowptr, cons
     p.ok = false;
     const int32_t n = A.n;
     if (n == 0 || nnzN == 0) return false;
-    const int G = plan_group((double)A.nnz / n);
+    const int G = plan_group((double)A.nnz / n, n);
     const int RW = 32 / G;
     const int64_t nsl = ((int64_t)n + RW - 1) / RW;
     DVec<int32_t> na((size_t)nsl, s), nw((size_t)nsl, s), mx(2, s);
