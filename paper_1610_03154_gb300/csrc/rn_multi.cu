@@ -41,17 +41,32 @@ spmm_kernel(int32_t n, int s, const int32_t *__restrict__ rp, const int32_t *__r
             T acc[kCPL];
 #pragma unroll
             for (int u = 0; u < kCPL; u++) acc[u] = T(0);
-            for (int32_t e = e0; e < e1; e++) {
-                const int32_t j = col[e];
-                const T a = val[e];
-                const T dj = OP == M_JZ_RESID ? d[j] : T(1);
+            // the row's entries 32 at a time: one coalesced load of columns and
+            // values across the lanes, then each entry broadcast by a shuffle, so
+            // the operand rows of several entries are gathered at once instead of
+            // each gather waiting for its entry's column index
+            for (int32_t eb = e0; eb < e1; eb += 32) {
+                const int cnt = min(32, e1 - eb);
+                int32_t jl = 0;
+                T al = T(0), dl = T(1);
+                if (lane < cnt) {
+                    jl = col[eb + lane];
+                    al = val[eb + lane];
+                    if (OP == M_JZ_RESID) dl = d[jl];
+                }
+#pragma unroll 4
+                for (int k = 0; k < cnt; k++) {
+                    const int32_t j = __shfl_sync(0xffffffffu, jl, k);
+                    const T a = __shfl_sync(0xffffffffu, al, k);
+                    const T dj = OP == M_JZ_RESID ? __shfl_sync(0xffffffffu, dl, k) : T(1);
 #pragma unroll
-                for (int u = 0; u < kCPL; u++) {
-                    const int c = c0 + lane + 32 * u;
-                    if (c < s) {
-                        const int64_t o = (int64_t)j * s + c;
-                        const T xv = OP == M_JZ_RESID ? dj * (T)B[o] : X[o];
-                        acc[u] = fma(a, xv, acc[u]);
+                    for (int u = 0; u < kCPL; u++) {
+                        const int c = c0 + lane + 32 * u;
+                        if (c < s) {
+                            const int64_t o = (int64_t)j * s + c;
+                            const T xv = OP == M_JZ_RESID ? dj * (T)B[o] : X[o];
+                            acc[u] = fma(a, xv, acc[u]);
+                        }
                     }
                 }
             }
@@ -127,17 +142,33 @@ __global__ void jz_multi_kernel(int32_t n, int s, const TB *__restrict__ B, cons
         Y[o] = d[o / s] * (T)B[o];
 }
 
-// coarsest level: Y = A_L^{-1} B in FP64 arithmetic; a warp per row, lanes over columns
+// coarsest level: Y = A_L^{-1} B in FP64 arithmetic; a warp per row, lanes
+// over columns, kCPL columns per lane summed side by side (each column's sum
+// in ascending j), so every step of j issues kCPL independent loads
 template <typename TB, typename TO>
 __global__ void coarse_multi_kernel(int32_t n, int s, const double *__restrict__ Ainv, const TB *__restrict__ B,
                                     TO *__restrict__ Y) {
     pdl_wait();
     const int lane = threadIdx.x & 31;
     for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5)
-        for (int c = lane; c < s; c += 32) {
-            double acc = 0.0;
-            for (int32_t j = 0; j < n; j++) acc = fma(Ainv[(int64_t)i * n + j], (double)B[(int64_t)j * s + c], acc);
-            Y[(int64_t)i * s + c] = (TO)acc;
+        for (int c0 = 0; c0 < s; c0 += 32 * kCPL) {
+            double acc[kCPL];
+#pragma unroll
+            for (int u = 0; u < kCPL; u++) acc[u] = 0.0;
+#pragma unroll 4
+            for (int32_t j = 0; j < n; j++) {
+                const double aij = Ainv[(int64_t)i * n + j];
+#pragma unroll
+                for (int u = 0; u < kCPL; u++) {
+                    const int c = c0 + lane + 32 * u;
+                    if (c < s) acc[u] = fma(aij, (double)B[(int64_t)j * s + c], acc[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kCPL; u++) {
+                const int c = c0 + lane + 32 * u;
+                if (c < s) Y[(int64_t)i * s + c] = (TO)acc[u];
+            }
         }
 }
 
@@ -198,8 +229,9 @@ static T *mcycle_level(rn_hierarchy &h, MultiBufs<T> &W, int l, int ns) {
     rn_level &L = *h.lev[l];
     const int32_t n = L.A.n;
     if (l == (int)h.lev.size() - 1) {
+        // a warp per block: the rows' FP64 multiply-adds spread over as many SMs as rows
         RN_LAUNCH("multi_coarse_solve", 8.0 * n * n + 2.0 * sizeof(T) * n * ns, s, (coarse_multi_kernel<T, T>),
-                  grid_for((int64_t)n * 32, 256, 4), 256, 0, n, ns, h.Ainv.p, W.b[l].p, W.x[l].p);
+                  grid_for((int64_t)n * 32, 32, 16), 32, 0, n, ns, h.Ainv.p, W.b[l].p, W.x[l].p);
         return W.x[l].p;
     }
     const T *d = mweights<T>(L);
@@ -236,7 +268,7 @@ static void mcycle_top(rn_hierarchy &h, MultiBufs<T> &W, const double *R, double
     const int64_t tot = (int64_t)n * ns;
     if (h.lev.size() == 1) {
         RN_LAUNCH("multi_coarse_solve", 8.0 * n * n + 16.0 * tot, s, (coarse_multi_kernel<double, double>),
-                  grid_for((int64_t)n * 32, 256, 4), 256, 0, n, ns, h.Ainv.p, R, Z);
+                  grid_for((int64_t)n * 32, 32, 16), 32, 0, n, ns, h.Ainv.p, R, Z);
         return;
     }
     const T *d = mweights<T>(L);
@@ -315,10 +347,48 @@ static rn_status solve_multi_t(rn_hierarchy &h, const double *B, double *X, int 
     const double w0 = worst();
     double w = w0;
     int it = 0;
-    while (w >= rtol && it < maxit) {
+    // one iteration: Z = M R, X += Z, R = B - A X and the column norms; with
+    // graphs it is captured once and replayed (one launch per iteration
+    // instead of one per kernel: the small levels' launches cost more than
+    // their work)
+    auto iteration = [&]() {
         mcycle_top<T>(h, W, R.p, Z.p, ns);
         RN_LAUNCH("multi_outer_update", 24.0 * tot, s, add_multi_kernel, grid_for(tot, 1024), 256, 0, tot, X, Z.p);
         residual(nr2.p);
+    };
+    struct Graph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        int64_t kernels = 0;
+        ~Graph() {
+            if (e) cudaGraphExecDestroy(e);
+            if (g) cudaGraphDestroy(g);
+        }
+    } graph;
+    const bool use_graph = h.p.use_graphs && !profiling_enabled();
+    while (w >= rtol && it < maxit) {
+        if (use_graph) {
+            if (!graph.e) {
+                const int64_t before = launches_so_far();
+                RN_CUDA_CHECK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                try {
+                    iteration();
+                } catch (...) {
+                    cudaGraph_t g = nullptr;
+                    cudaStreamEndCapture(s, &g);
+                    if (g) cudaGraphDestroy(g);
+                    throw;
+                }
+                RN_CUDA_CHECK(cudaStreamEndCapture(s, &graph.g));
+                RN_CUDA_CHECK(cudaGraphInstantiate(&graph.e, graph.g, 0));
+                graph.kernels = launches_so_far() - before;
+                add_launches(-graph.kernels);  // captured, not launched
+            }
+            RN_CUDA_CHECK(cudaGraphLaunch(graph.e, s));
+            add_launches(graph.kernels);
+        } else {
+            iteration();
+        }
         w = worst();
         it++;
     }
