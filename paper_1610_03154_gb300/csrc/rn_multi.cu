@@ -22,7 +22,9 @@ enum MOp { M_SPMM = 0, M_SPMM_ADD = 1, M_RESID = 2, M_JACOBI = 3, M_JZ_RESID = 4
 // Y = op(M, X, B) on s columns.  M_JZ_RESID: XZ = D B, Y = B - M (D B), with D
 // (omega / a_ii) applied to the gathered rows of B.  With nrm, the squares of
 // Y's entries (M_RESID) are summed per column into nrm[block * s + c].
-template <typename T, typename TB, typename TO, int OP>
+// A warp takes (row, column chunk) tasks: CPL columns per lane, 32 * CPL per
+// chunk; few rows take narrow chunks (CPL = 2) so that more warps share them.
+template <typename T, typename TB, typename TO, int OP, int CPL>
 __global__ void __launch_bounds__(kMT)
 spmm_kernel(int32_t n, int s, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
             const T *__restrict__ val, const T *__restrict__ X, const TB *__restrict__ B, const T *__restrict__ d,
@@ -34,13 +36,17 @@ spmm_kernel(int32_t n, int s, const int32_t *__restrict__ rp, const int32_t *__r
     if (nrm)
         for (int c = threadIdx.x; c < wpb * s; c += kMT) snrm[c] = 0.0;
     __syncthreads();
-    for (int32_t i = blockIdx.x * wpb + warp; i < n; i += gridDim.x * wpb) {
+    const int nck = (s + 32 * CPL - 1) / (32 * CPL);
+    const int64_t ntask = (int64_t)n * nck;
+    for (int64_t task = (int64_t)blockIdx.x * wpb + warp; task < ntask; task += (int64_t)gridDim.x * wpb) {
+        const int32_t i = (int32_t)(task / nck);
+        const int c0 = (int)(task % nck) * 32 * CPL;
         const int32_t e0 = rp[i], e1 = rp[i + 1];
         const T di = (OP == M_JACOBI || OP == M_JZ_RESID) ? d[i] : T(0);
-        for (int c0 = 0; c0 < s; c0 += 32 * kCPL) {
-            T acc[kCPL];
+        {
+            T acc[CPL];
 #pragma unroll
-            for (int u = 0; u < kCPL; u++) acc[u] = T(0);
+            for (int u = 0; u < CPL; u++) acc[u] = T(0);
             // the row's entries 32 at a time: one coalesced load of columns and
             // values across the lanes, then each entry broadcast by a shuffle, so
             // the operand rows of several entries are gathered at once instead of
@@ -60,7 +66,7 @@ spmm_kernel(int32_t n, int s, const int32_t *__restrict__ rp, const int32_t *__r
                     const T a = __shfl_sync(0xffffffffu, al, k);
                     const T dj = OP == M_JZ_RESID ? __shfl_sync(0xffffffffu, dl, k) : T(1);
 #pragma unroll
-                    for (int u = 0; u < kCPL; u++) {
+                    for (int u = 0; u < CPL; u++) {
                         const int c = c0 + lane + 32 * u;
                         if (c < s) {
                             const int64_t o = (int64_t)j * s + c;
@@ -71,7 +77,7 @@ spmm_kernel(int32_t n, int s, const int32_t *__restrict__ rp, const int32_t *__r
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kCPL; u++) {
+            for (int u = 0; u < CPL; u++) {
                 const int c = c0 + lane + 32 * u;
                 if (c >= s) continue;
                 const int64_t o = (int64_t)i * s + c;
@@ -199,20 +205,31 @@ static const T *mweights(rn_level &L) {
 
 static int multi_grid(int32_t n) { return std::max(1, std::min<int>((n + 7) / 8, num_sms() * 8)); }
 
-template <typename T, typename TB, typename TO, int OP>
-static void spmm(cudaStream_t s, const char *name, const DCsr &M, int ns, const T *X, const TB *B, const T *d, TO *Y,
-                 T *XZ = nullptr, double *nrm = nullptr, int grid = 0) {
-    if (M.n == 0) return;
-    if (!grid) grid = multi_grid(M.n);
+constexpr int32_t kMultiFewRows = 2048;  // below: 2 columns per lane, 4x the warps per row
+
+template <typename T, typename TB, typename TO, int OP, int CPL>
+static void spmm_t(cudaStream_t s, const char *name, const DCsr &M, int ns, const T *X, const TB *B, const T *d,
+                   TO *Y, T *XZ, double *nrm, int grid) {
+    const int nck = (ns + 32 * CPL - 1) / (32 * CPL);
+    if (!grid) grid = std::max(1, (int)std::min<int64_t>(((int64_t)M.n * nck + 7) / 8, (int64_t)num_sms() * 8));
     const double bytes =
         (4.0 + sizeof(T)) * M.nnz + 4.0 * (M.n + 1) + (double)ns * (sizeof(T) * M.m + sizeof(TO) * M.n);
     const size_t smem = nrm ? sizeof(double) * (kMT / 32) * ns : 0;
     if (smem > 48 * 1024) {
-        RN_CUDA_CHECK(cudaFuncSetAttribute(spmm_kernel<T, TB, TO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
+        RN_CUDA_CHECK(cudaFuncSetAttribute(spmm_kernel<T, TB, TO, OP, CPL>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    RN_LAUNCH(name, bytes, s, (spmm_kernel<T, TB, TO, OP>), grid, kMT, smem, M.n, ns, M.rowptr.p, M.col.p,
+    RN_LAUNCH(name, bytes, s, (spmm_kernel<T, TB, TO, OP, CPL>), grid, kMT, smem, M.n, ns, M.rowptr.p, M.col.p,
               mvals<T>(M), X, B, d, Y, XZ, nrm);
+}
+// grid: given only for the outer residual, whose per-block column partials
+// the caller sizes (it keeps 8 columns per lane)
+template <typename T, typename TB, typename TO, int OP>
+static void spmm(cudaStream_t s, const char *name, const DCsr &M, int ns, const T *X, const TB *B, const T *d, TO *Y,
+                 T *XZ = nullptr, double *nrm = nullptr, int grid = 0) {
+    if (M.n == 0) return;
+    if (grid || M.n >= kMultiFewRows) spmm_t<T, TB, TO, OP, kCPL>(s, name, M, ns, X, B, d, Y, XZ, nrm, grid);
+    else spmm_t<T, TB, TO, OP, 2>(s, name, M, ns, X, B, d, Y, XZ, nrm, grid);
 }
 
 // multivector workspaces of one cycle, per level: b, x, t, r (n_l x s each)
