@@ -944,7 +944,7 @@ static cudaGraph_t capture(rn_hierarchy &h, F &&work) {
 // converged and below the iteration limit), so the host only relaunches the
 // graph, and reads the loop state, once per kCgGraphIters iterations.  The
 // graph holds no loop: whatever the conditions, one launch ends.
-constexpr int kCgGraphIters = 16;
+constexpr int kCgGraphIters = 8;
 
 static void build_cg_graph(rn_hierarchy &h) {
     const bool flexible = h.p.precision == RN_MIXED;
