@@ -29,12 +29,26 @@ def env():
     return torch, torch.device("cuda:0"), rn
 
 
+def _diagonal_problem(n=100):
+    """A diagonal operator above max_coarse: no strong coupling, so no
+    aggregate, and its coarsening stalls on the first level (which becomes its
+    coarsest, solved by the dense LU)."""
+    import scipy.sparse as sp
+
+    A = PR.CSR.from_scipy(sp.diags(np.linspace(1.0, 3.0, n)).tocsr())
+    return PR.Problem("diagonal", A, np.ones((n, 1)), np.random.default_rng(12).uniform(-1.0, 1.0, n),
+                      dict(PR.PARAMS_ANISO))
+
+
 def _problems():
     """Uneven rotated-anisotropy problems of different depths, one that is its
-    own coarsest level (7 x 7 interior nodes) and one a level deeper."""
+    own coarsest level (7 x 7 interior nodes), one a level deeper, and one
+    whose coarsening stalls on its first level (the merged level is redone
+    without it)."""
     probs = PR.batch_aniso_problems(count=7, seed=11, side_lo=24, side_hi=180)
     probs.insert(1, PR.aniso_problem(8, seed=9))
     probs.insert(4, PR.aniso_problem(14, seed=10))
+    probs.insert(6, _diagonal_problem())
     return probs
 
 
@@ -130,6 +144,22 @@ def test_merged_setup_feeds_the_merged_solve(env):
         res = np.linalg.norm(p.b - p.A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(p.b)
         assert res < 1e-8, (i, res)
     batch.close()
+    _close(own)
+    _close(mer)
+
+
+def test_merged_setup_of_one_problem_is_its_setup(env):
+    """One problem through the merged path: the hierarchy rn_setup builds."""
+    probs = [PR.aniso_problem(96, seed=13)]
+    own, mer, _ = _both(env, probs, 0)
+    a, b = own[0], mer[0]
+    assert a.stats()["n"] == b.stats()["n"] and a.stats()["nnz_A"] == b.stats()["nnz_A"]
+    for lvl in range(a.stats()["levels"] - 1):
+        for which in (0, 4, 5):
+            ra, ca, va, _ = a.export_csr(lvl, which)
+            rb, cb, vb, _ = b.export_csr(lvl, which)
+            assert np.array_equal(ra, rb) and np.array_equal(ca, cb)
+            assert np.max(np.abs(va - vb)) <= 1e-12 * np.max(np.abs(va))
     _close(own)
     _close(mer)
 
