@@ -288,7 +288,8 @@ extern "C" rn_status rn_setup_merged(int count, const rn_csr *A, const double *c
         hs.push_back(h);
     }
     rn::build_hierarchies_merged(hs, views, bs, guard.ws);
-    for (rn_hierarchy *h : hs) rn::prepare_solve(*h);
+    for (rn_hierarchy *h : hs) rn::prepare_solve_begin(*h);  // every problem's launches before any read
+    for (rn_hierarchy *h : hs) rn::prepare_solve_end(*h);
     for (rn_hierarchy *h : hs) RN_CUDA_CHECK(cudaStreamSynchronize(h->s));
     const double ms = rn::now_ms() - t0;
     for (int i = 0; i < count; i++) {

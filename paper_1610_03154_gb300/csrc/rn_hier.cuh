@@ -70,6 +70,7 @@ struct rn_hierarchy {
     int agg_rounds = 0;
     // set while this hierarchy is the working copy of a merged setup
     rn::MergedSetup *merged = nullptr;
+    rn::DVec<int32_t> maxlen;  // longest rows per level and matrix, between prepare_solve_begin and _end
     ~rn_hierarchy();
 };
 
@@ -175,7 +176,9 @@ struct EmCtx {
 void energy_min(const EmCtx &c, const CsrView &A, const Pattern &N, double *X, const int32_t *rowtype,
                 const double *Bc, const double *dinv, int sweeps);
 // solve (rn_solve.cu)
-void prepare_solve(rn_hierarchy &h);
+void prepare_solve(rn_hierarchy &h);  // prepare_solve_begin then prepare_solve_end
+void prepare_solve_begin(rn_hierarchy &h);
+void prepare_solve_end(rn_hierarchy &h);
 rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int maxit, rn_solve_info *info);
 void apply_cycle(rn_hierarchy &h, const double *rhs, double *out);
 void cycle_launches(rn_hierarchy &h, const double *rhs, double *out);  // the cycle's launches, no graph

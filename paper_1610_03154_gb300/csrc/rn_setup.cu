@@ -1913,7 +1913,8 @@ static EmCtx ctx_of(rn_hierarchy &h) {
     return c;
 }
 
-static void coarsest_lu(rn_hierarchy &h);
+static void coarsest_lu(rn_hierarchy &h, bool check = true);
+static void coarsest_lu_check(rn_hierarchy &h);
 
 // ================================================================== independent problems set up together
 // The problems' level-l operators form one block-diagonal matrix (problem t of
@@ -2608,8 +2609,15 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
     }
 }
 
-// The coarsest level: dense LU with partial pivoting, kept as an explicit inverse
-static void coarsest_lu(rn_hierarchy &h) {
+// The coarsest level: dense LU with partial pivoting, kept as an explicit
+// inverse.  Without check, the one-launch factorisation of a small level is
+// only enqueued (a singular pivot leaves non-finite values, nothing out of
+// bounds) and coarsest_lu_check reads the singularity flag later, so many
+// problems' factorisations overlap.
+static void coarsest_lu_check(rn_hierarchy &h) {
+    check_flag(h.iflags.p + 7, h.s, RN_ESINGULAR, "coarsest-level LU pivot below 1e-14 max|A|");
+}
+static void coarsest_lu(rn_hierarchy &h, bool check) {
     cudaStream_t s = h.s;
     rn_level &C = *h.lev.back();
     const int32_t nL = C.A.n;
@@ -2628,7 +2636,7 @@ static void coarsest_lu(rn_hierarchy &h) {
         h.Ainv.alloc((size_t)nL * nL, s);
         RN_LAUNCH("coarse_lu", 12.0 * C.A.nnz + 8.0 * nL * nL, s, dense_lu_small_kernel, 1, 256, smem, nL,
                   C.A.rowptr.p, C.A.col.p, C.A.val.p, h.Ainv.p, h.iflags.p + 7);
-        check_flag(h.iflags.p + 7, s, RN_ESINGULAR, "coarsest-level LU pivot below 1e-14 max|A|");
+        if (check) coarsest_lu_check(h);
     } else {
         DVec<double> M((size_t)nL * nL, s), work((size_t)nL * nL, s);
         DVec<int32_t> piv(nL, s);
@@ -2637,7 +2645,9 @@ static void coarsest_lu(rn_hierarchy &h) {
                   C.A.val.p, M.p);
         fill_i32(h.iflags.p + 7, 0, 1, s);
         RN_LAUNCH("coarse_lu", 16.0 * nL * nL, s, dense_lu_kernel, 1, 1024, 0, nL, M.p, piv.p, h.iflags.p + 7);
-        check_flag(h.iflags.p + 7, s, RN_ESINGULAR, "coarsest-level LU pivot below 1e-14 max|A|");
+        // always checked here: a singular factorisation stops early and leaves
+        // later pivot indices unset, which the inverse must not read
+        coarsest_lu_check(h);
         h.Ainv.alloc((size_t)nL * nL, s);
         RN_LAUNCH("coarse_lu", 24.0 * nL * nL, s, lu_inverse_kernel, grid_for(nL, 64, 4), 64, 0, nL, M.p, piv.p, h.Ainv.p,
                   work.p);
@@ -2726,7 +2736,15 @@ void build_hierarchies_merged(std::vector<rn_hierarchy *> &out, const std::vecto
         RN_CUDA_CHECK(cudaStreamWaitEvent(h->s, done, 0));
         h->agg_rounds = W.agg_rounds;
     }
-    for (rn_hierarchy *h : out) coarsest_lu(*h);
+    // every problem's coarsest LU enqueued on its stream, then the flags read
+    for (rn_hierarchy *h : out) coarsest_lu(*h, false);
+    for (size_t t = 0; t < out.size(); t++) {
+        try {
+            coarsest_lu_check(*out[t]);
+        } catch (const Error &e) {
+            fail(e.status, fmt("problem %zu: %s", t, e.msg.c_str()));
+        }
+    }
 }
 
 // ================================================================== measurement hook

@@ -803,20 +803,34 @@ static void autotune_schedules(rn_hierarchy &h) {
     }
 }
 
+// The solve's preparation in two halves, so that many hierarchies can enqueue
+// the first before any of them waits for its read-back: the longest rows of
+// every level's A, P and R (begin), then their read and the rest (end).
+void prepare_solve_begin(rn_hierarchy &h) {
+    cudaStream_t s = h.s;
+    const size_t nmat = 3 * h.lev.size();
+    h.maxlen.alloc(nmat, s);
+    RN_CUDA_CHECK(cudaMemsetAsync(h.maxlen.p, 0, h.maxlen.bytes(), s));
+    for (size_t l = 0; l < h.lev.size(); l++) {
+        launch_maxlen(h, h.lev[l]->A, h.maxlen.p + 3 * l);
+        launch_maxlen(h, h.lev[l]->P, h.maxlen.p + 3 * l + 1);
+        launch_maxlen(h, h.lev[l]->R, h.maxlen.p + 3 * l + 2);
+    }
+}
+
 void prepare_solve(rn_hierarchy &h) {
+    prepare_solve_begin(h);
+    prepare_solve_end(h);
+}
+
+void prepare_solve_end(rn_hierarchy &h) {
     cudaStream_t s = h.s;
     const bool mixed = h.p.precision == RN_MIXED;
-    // longest rows of every level's A, P and R: one read-back for all
     const size_t nmat = 3 * h.lev.size();
-    DVec<int32_t> ml(nmat, s);
-    RN_CUDA_CHECK(cudaMemsetAsync(ml.p, 0, ml.bytes(), s));
-    for (size_t l = 0; l < h.lev.size(); l++) {
-        launch_maxlen(h, h.lev[l]->A, ml.p + 3 * l);
-        launch_maxlen(h, h.lev[l]->P, ml.p + 3 * l + 1);
-        launch_maxlen(h, h.lev[l]->R, ml.p + 3 * l + 2);
-    }
+    if (h.maxlen.n != nmat) fail(RN_EINTERNAL, "prepare_solve_end without prepare_solve_begin");
     std::vector<int32_t> mlh(nmat);
-    read_small(mlh.data(), ml.p, nmat, s);  // at most 3 x 32 levels
+    read_small(mlh.data(), h.maxlen.p, nmat, s);  // at most 3 x 32 levels: one read-back for all
+    h.maxlen.release();
     for (size_t l = 0; l < h.lev.size(); l++) {
         rn_level &L = *h.lev[l];
         const int32_t n = L.A.n;
