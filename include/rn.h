@@ -215,8 +215,11 @@ rn_status rn_setup_batched(int count, const rn_csr *A, const double *const *B, c
  * its coarsest level).  So out[i] is the hierarchy rn_setup builds for
  * problem i: the same strength, aggregates, patterns and level sizes; values
  * agree to rounding (the CG sums run in another order).  out[i] owns its
- * memory and a stream of its own, and is used and freed like any hierarchy
- * (rn_solve, rn_batch_merge, rn_free).  Restrictions: params.stream NULL,
+ * memory and is used and freed like any hierarchy (rn_solve, rn_batch_merge,
+ * rn_free); its stream is one of 64 streams the library keeps for the
+ * process (problems i and i + 64 share one), each with a device pool of its
+ * own, because a stream-ordered pool that holds blocks freed on many streams
+ * is slow to allocate from.  Restrictions: params.stream NULL,
  * p->symmetric (R = P^T), energy_method RN_ENERGY_CG, block_size 1;
  * otherwise RN_EINVAL.  On any error every hierarchy is freed, out[] is all
  * NULL and the status is returned (the message names the problem where it

@@ -98,6 +98,12 @@ static rn::Allocator alloc_of(const rn_params &p) {
     a.ctx = p.alloc_ctx;
     return a;
 }
+// a hierarchy's allocator: its params' hooks, else its device pool
+static rn::Allocator alloc_of(const rn_hierarchy &h) {
+    rn::Allocator a = alloc_of(h.p);
+    a.pool = h.pool;
+    return a;
+}
 
 extern "C" rn_status rn_setup(const rn_csr *A, const double *B, const double *Bhat, int k, int location,
                               const rn_params *p, rn_hierarchy **out) {
@@ -248,10 +254,7 @@ extern "C" rn_status rn_setup_merged(int count, const rn_csr *A, const double *c
         std::vector<rn_hierarchy *> &hs;
         cudaStream_t ws = nullptr;
         ~Guard() {
-            if (ws) {
-                cudaStreamSynchronize(ws);
-                cudaStreamDestroy(ws);
-            }
+            if (ws) cudaStreamSynchronize(ws);
             for (rn_hierarchy *h : hs) rn_free(h);
         }
     } guard{hs};
@@ -273,23 +276,34 @@ extern "C" rn_status rn_setup_merged(int count, const rn_csr *A, const double *c
         views.push_back(rn::CsrView{a.n_rows, a.n_cols, a.nnz, a.rowptr, a.col, a.val});
         bs.push_back(B[i]);
     }
-    const rn::AllocScope alloc_scope(alloc_of(*p));
+    // Streams and device pools kept for the process: problem i works on stream
+    // k = i mod kMergedStreams with pool kMergedPoolBase + k, the merged
+    // matrices on the next stream and pool, so no pool sees frees from more
+    // than one stream (rn_free leaves these streams alone)
+    rn::Allocator wa = alloc_of(*p);
+    wa.pool = rn::kMergedPoolBase + rn::kMergedStreams;
+    const rn::AllocScope alloc_scope(wa);
     const double t0 = rn::now_ms();
-    RN_CUDA_CHECK(cudaStreamCreate(&guard.ws));
+    guard.ws = rn::merged_stream(rn::kMergedStreams);
     for (int i = 0; i < count; i++) {
-        cudaStream_t s = nullptr;
-        RN_CUDA_CHECK(cudaStreamCreate(&s));
         rn_hierarchy *h = new rn_hierarchy();
         h->p = *p;
         h->k = 1;
         h->mb = 1;
-        h->s = s;
-        h->own_stream = true;
+        h->s = rn::merged_stream(i % rn::kMergedStreams);
+        h->own_stream = false;
+        h->pool = rn::kMergedPoolBase + i % rn::kMergedStreams;
         hs.push_back(h);
     }
     rn::build_hierarchies_merged(hs, views, bs, guard.ws);
-    for (rn_hierarchy *h : hs) rn::prepare_solve_begin(*h);  // every problem's launches before any read
-    for (rn_hierarchy *h : hs) rn::prepare_solve_end(*h);
+    for (rn_hierarchy *h : hs) {  // every problem's launches before any read
+        const rn::AllocScope scope(alloc_of(*h));
+        rn::prepare_solve_begin(*h);
+    }
+    for (rn_hierarchy *h : hs) {
+        const rn::AllocScope scope(alloc_of(*h));
+        rn::prepare_solve_end(*h);
+    }
     for (rn_hierarchy *h : hs) RN_CUDA_CHECK(cudaStreamSynchronize(h->s));
     const double ms = rn::now_ms() - t0;
     for (int i = 0; i < count; i++) {
@@ -387,7 +401,7 @@ extern "C" rn_status rn_solve(rn_hierarchy *h, const double *b, double *x, int l
     if (!h || !b || !x) fail(RN_EINVAL, "null argument");
     if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
     if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
-    const rn::AllocScope alloc_scope(alloc_of(h->p));
+    const rn::AllocScope alloc_scope(alloc_of(*h));
     cudaStream_t s = h->s;
     const int64_t n = h->lev[0]->A.n;
     const double t0 = rn::now_ms();
@@ -417,7 +431,7 @@ extern "C" rn_status rn_solve_multi(rn_hierarchy *h, const double *B, double *X,
     if (h->p.gamma != 1) fail(RN_EINVAL, "the many-right-hand-side cycle is a V-cycle (gamma 1)");
     if (location != RN_DEVICE && location != RN_HOST) fail(RN_EINVAL, "location");
     if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
-    const rn::AllocScope alloc_scope(alloc_of(h->p));
+    const rn::AllocScope alloc_scope(alloc_of(*h));
     cudaStream_t st = h->s;
     const int64_t tot = (int64_t)h->lev[0]->A.n * s;
     const double t0 = rn::now_ms();
@@ -441,7 +455,7 @@ extern "C" rn_status rn_solve_multi(rn_hierarchy *h, const double *B, double *X,
 extern "C" rn_status rn_vcycle(rn_hierarchy *h, const double *b, double *x) {
     RN_API_BEGIN
     if (!h || !b || !x) rn::fail(RN_EINVAL, "null argument");
-    const rn::AllocScope alloc_scope(alloc_of(h->p));
+    const rn::AllocScope alloc_scope(alloc_of(*h));
     rn::cycle_checked(*h, b, x);
     RN_CUDA_CHECK(cudaStreamSynchronize(h->s));
     return RN_OK;
@@ -452,7 +466,7 @@ extern "C" rn_status rn_time_op(rn_hierarchy *h, int op, int reps, int64_t flush
                                 char *name) {
     RN_API_BEGIN
     if (!h || !us || !bytes) rn::fail(RN_EINVAL, "null argument");
-    const rn::AllocScope alloc_scope(alloc_of(h->p));
+    const rn::AllocScope alloc_scope(alloc_of(*h));
     std::string nm;
     rn::time_op(*h, op, reps, flush_bytes, us, bytes, nm);
     if (name) {
@@ -467,7 +481,7 @@ extern "C" rn_status rn_time_setup_op(rn_hierarchy *h, int op, int reps, int64_t
                                       double *bytes, char *name) {
     RN_API_BEGIN
     if (!h || !us || !bytes) rn::fail(RN_EINVAL, "null argument");
-    const rn::AllocScope alloc_scope(alloc_of(h->p));
+    const rn::AllocScope alloc_scope(alloc_of(*h));
     std::string nm;
     rn::time_setup_op(*h, op, reps, flush_bytes, us, bytes, nm);
     if (name) {

@@ -71,6 +71,7 @@ struct rn_hierarchy {
     // set while this hierarchy is the working copy of a merged setup
     rn::MergedSetup *merged = nullptr;
     rn::DVec<int32_t> maxlen;  // longest rows per level and matrix, between prepare_solve_begin and _end
+    int pool = -1;             // the library device pool its buffers come from without hooks (-1: default)
     ~rn_hierarchy();
 };
 

@@ -43,11 +43,17 @@ struct Allocator {
     void *(*alloc)(size_t, void *, void *) = nullptr;
     void (*dealloc)(void *, size_t, void *, void *) = nullptr;
     void *ctx = nullptr;
+    int pool = -1;  // without hooks: the library's device pool of this slot (-1: the thread's)
 };
 // The allocator new buffers take on this thread; the API entry points set it
 // for the duration of a call (AllocScope) from the call's parameters.
 Allocator &current_allocator();
 void set_thread_pool(int slot);  // worker threads of batched calls: a device pool per worker (-1: default)
+// Merged setups: problem streams kMergedPoolBase + k .. with pools of the same
+// index (see merged_stream); the working stream is merged_stream(kMergedStreams).
+constexpr int kMergedStreams = 64;
+constexpr int kMergedPoolBase = 16;  // above the batched calls' worker slots
+cudaStream_t merged_stream(int k);
 struct AllocScope {
     Allocator saved;
     explicit AllocScope(const Allocator &a) : saved(current_allocator()) { current_allocator() = a; }

@@ -2010,6 +2010,12 @@ struct MergedSetup {
         read_vec(v.data(), g.p, m, s);
         return v;
     }
+    // problem p's buffers come from its hierarchy's pool (or the caller's hooks)
+    Allocator alloc_for(int p) const {
+        Allocator a = current_allocator();
+        a.pool = out[p]->pool;
+        return a;
+    }
     rn_level &level_of(int p, int l) {
         auto &lev = out[p]->lev;
         while ((int)lev.size() <= l) lev.push_back(std::make_unique<rn_level>());
@@ -2058,6 +2064,7 @@ struct MergedSetup {
             const int p = act[t];
             DCsr &X = level_of(p, l).*f;
             cudaStream_t ps = out[p]->s;
+            const AllocScope scope(alloc_for(p));
             X.n = rof[t + 1] - rof[t];
             X.m = cof[t + 1] - cof[t];
             X.nnz = eb[t + 1] - eb[t];
@@ -2074,6 +2081,7 @@ struct MergedSetup {
             const int p = act[t];
             DVec<T> &X = level_of(p, l).*f;
             const int32_t n = rof[t + 1] - rof[t];
+            const AllocScope scope(alloc_for(p));
             X.alloc((size_t)n, out[p]->s);
             blk.push_back(BlockVec<T>{rof[t], n, 0, (T)(dof.empty() ? 0 : -dof[t]), X.p});
         }
@@ -2676,7 +2684,9 @@ void build_hierarchies_merged(std::vector<rn_hierarchy *> &out, const std::vecto
         RN_CUDA_CHECK(cudaEventCreateWithFlags(&ms.ev[t], cudaEventDisableTiming));
     }
     // every problem's scratch, as build_hierarchy allocates it
-    for (rn_hierarchy *h : out) {
+    for (int t = 0; t < np; t++) {
+        rn_hierarchy *h = out[t];
+        const AllocScope scope(ms.alloc_for(t));
         h->partial.alloc(2 * kReduceBlocks, h->s);
         h->counters.alloc(4, h->s);
         RN_CUDA_CHECK(cudaMemsetAsync(h->counters.p, 0, 4 * sizeof(unsigned), h->s));
@@ -2737,7 +2747,10 @@ void build_hierarchies_merged(std::vector<rn_hierarchy *> &out, const std::vecto
         h->agg_rounds = W.agg_rounds;
     }
     // every problem's coarsest LU enqueued on its stream, then the flags read
-    for (rn_hierarchy *h : out) coarsest_lu(*h, false);
+    for (int t = 0; t < np; t++) {
+        const AllocScope scope(ms.alloc_for(t));
+        coarsest_lu(*out[t], false);
+    }
     for (size_t t = 0; t < out.size(); t++) {
         try {
             coarsest_lu_check(*out[t]);
