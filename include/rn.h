@@ -239,7 +239,8 @@ rn_status rn_solve_batched(int count, rn_hierarchy *const *h, const double *cons
  * So every cycle step, and every step of the outer CG (per-problem alpha,
  * beta and stopping, reduced over row chunks in a fixed order), is one launch
  * for all problems.  The h[i] are only read and may be freed afterwards.
- * stream: the batch's CUDA stream (NULL: a stream of its own); the
+ * stream: the batch's CUDA stream (NULL: a stream the library keeps for the
+ * process, with a device pool of its own); the
  * solve and cycle read b[i] and write x[i] on it, and return after it has
  * finished with them.  Errors:
  * RN_EINVAL for count < 1, null arguments or differing cycle settings.

@@ -333,25 +333,20 @@ extern "C" rn_status rn_batch_merge(int count, rn_hierarchy *const *h, void *str
     if (!out || !h || count < 1) fail(RN_EINVAL, "null argument or count < 1");
     for (int i = 0; i < count; i++)
         if (!h[i]) fail(RN_EINVAL, rn::fmt("hierarchy %d is NULL", i));
-    const rn::AllocScope alloc_scope(alloc_of(h[0]->p));
-    struct StreamGuard {
-        cudaStream_t s = nullptr;
-        ~StreamGuard() {
-            if (s) {
-                cudaStreamSynchronize(s);
-                cudaStreamDestroy(s);
-            }
-        }
-    } own;
+    // With no stream given, the batch works on a stream the library keeps for
+    // the process, with a device pool of its own (a stream-ordered pool that
+    // holds blocks freed on many streams is slow to allocate from).
+    rn::Allocator a = alloc_of(h[0]->p);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (!s) {
-        RN_CUDA_CHECK(cudaStreamCreate(&own.s));
-        s = own.s;
+        s = rn::merged_stream(rn::kMergedStreams + 1);
+        a.pool = rn::kMergedPoolBase + rn::kMergedStreams + 1;
     }
+    const rn::AllocScope alloc_scope(a);
     for (int i = 0; i < count; i++) RN_CUDA_CHECK(cudaStreamSynchronize(h[i]->s));
     rn_batch *b = rn::batch_merge(count, h, s);
-    b->own_stream = own.s != nullptr;
-    own.s = nullptr;
+    b->own_stream = false;
+    b->M->pool = a.pool;
     *out = b;
     return RN_OK;
     RN_API_END
@@ -365,7 +360,7 @@ extern "C" rn_status rn_batch_solve(rn_batch *b, const double *const *bvec, doub
     for (int i = 0; i < b->np; i++)
         if (!bvec[i] || !x[i]) fail(RN_EINVAL, rn::fmt("vector of problem %d is NULL", i));
     if (maxit < 0 || !(rtol >= 0.0)) fail(RN_EINVAL, "maxit/rtol");
-    const rn::AllocScope alloc_scope(alloc_of(b->M->p));
+    const rn::AllocScope alloc_scope(alloc_of(*b->M));
     const rn_status st = rn::batch_solve(*b, bvec, x, rtol, maxit, info);
     if (st == RN_ENOTCONV) rn::set_last_error("a problem did not reach the tolerance within maxit");
     return st;
@@ -376,7 +371,7 @@ extern "C" rn_status rn_batch_cycle(rn_batch *b, const double *const *bvec, doub
     RN_API_BEGIN
     using rn::fail;
     if (!b || !bvec || !x) fail(RN_EINVAL, "null argument");
-    const rn::AllocScope alloc_scope(alloc_of(b->M->p));
+    const rn::AllocScope alloc_scope(alloc_of(*b->M));
     rn::batch_cycle(*b, bvec, x);
     return RN_OK;
     RN_API_END
