@@ -962,6 +962,45 @@ def test_amalgamate_is_block_maximum(oracle, m):
                 assert got == 0.0 and not (Sm.indices[Sm.indptr[I]:Sm.indptr[I + 1]] == J).any()
 
 
+def test_unamalgamated_pattern_is_kronecker_of_node_pattern(oracle):
+    """Block systems (Sec. 3.4): on every level of the plane-strain workload
+    (two unknowns per node, no pre-filter) the unknown-level pattern N is the
+    node pattern S_m^d C_m expanded by the Kronecker product with an m x m
+    block of ones (scipy.sparse.kron of a scipy product chain: another route
+    than the oracle's loops), each entry carrying its node entry's value; a
+    root unknown's row is the identity row of its own unknown in its
+    aggregate's block."""
+    pr = PR.elasticity_problem(8)
+    m, d = pr.params["block_size"], pr.params["degree"]
+    h = oracle.Hierarchy(pr.A.to_scipy(), pr.B, **pr.params)
+    checked = 0
+    for L in h.levels[:-1]:
+        n = L.A.shape[0]
+        nn = n // m
+        Sm = oracle.amalgamate(L.S, m)
+        aggn = L.agg[::m]
+        ncn = L.N.shape[1] // m
+        rows = np.nonzero(aggn >= 0)[0]
+        Nm = sp.csr_matrix((np.ones(len(rows)), (rows, aggn[rows])), shape=(nn, ncn))
+        for _ in range(d):
+            Nm = (Sm @ Nm).tocsr()
+        K = sp.kron(Nm, sp.csr_matrix(np.ones((m, m)))).tocsr()
+        K.sort_indices()
+        N = L.N
+        for i in range(n):
+            cols = N.indices[N.indptr[i]:N.indptr[i + 1]]
+            vals = N.data[N.indptr[i]:N.indptr[i + 1]]
+            if L.rowtype[i] == 1:
+                assert list(cols) == [m * L.agg[i] + i % m]
+                continue
+            kc = K.indices[K.indptr[i]:K.indptr[i + 1]]
+            kv = K.data[K.indptr[i]:K.indptr[i + 1]]
+            assert np.array_equal(cols, kc), i
+            assert np.allclose(vals, kv, rtol=1e-13, atol=0.0), i
+            checked += 1
+    assert checked > 1000
+
+
 def test_elasticity_hierarchy_blocks_and_constraints(oracle):
     """2 x 2 blocks and the three rigid-body modes: aggregates and roots come
     in node pairs, root rows are identity rows over their aggregate's block,
