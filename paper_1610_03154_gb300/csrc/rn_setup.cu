@@ -2246,24 +2246,57 @@ static void check_flag(const int32_t *flag, cudaStream_t s, rn_status st, const 
 
 // Smooth candidates, build P (or R^T) on pattern N: Alg. 3 inject / improve /
 // filter / enforce / improve.  Pout receives the final pattern and values.
+// b_sweeps weighted-Jacobi sweeps on A B = 0 (exact) from B (read only),
+// alternating between buf0 and buf1 on stream s; returns the buffer holding
+// the smoothed candidates (B itself without sweeps)
+static const double *smooth_candidates(const rn_hierarchy &h, const CsrView &A, const double *B, double *buf0,
+                                       double *buf1, cudaStream_t s) {
+    const int32_t n = A.n;
+    const int k = h.k;
+    const double *src = B;
+    double *dst = buf0;
+    for (int sw = 0; sw < h.p.b_sweeps; sw++) {
+        if (k == 1)
+            RN_LAUNCH("candidates", 12.0 * A.nnz + 24.0 * n, s, cand_jacobi_kernel, rows_grid(n), kT, 0, n, A.rowptr,
+                      A.col, A.val, src, h.p.omega, dst);
+        else
+            RN_LAUNCH("candidates", 12.0 * A.nnz + 8.0 * k * (A.nnz + 2.0 * n), s, cand_jacobi_k_kernel, rows_grid(n),
+                      kT, 0, n, k, A.rowptr, A.col, A.val, src, h.p.omega, dst);
+        src = dst;
+        dst = (dst == buf0) ? buf1 : buf0;
+    }
+    return src;
+}
+
+// This thread's side stream and fork/join events (kept for the thread's life):
+// work of a level that needs only its operator (the candidate smoothing) runs
+// there while the main stream aggregates, filling the main stream's gaps
+// between its host synchronisations.  Nothing is allocated on it.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+static SideStream &side_stream() {
+    thread_local SideStream ss;
+    if (!ss.s) {
+        RN_CUDA_CHECK(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+        RN_CUDA_CHECK(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+        RN_CUDA_CHECK(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+    }
+    return ss;
+}
+
+// smoothed: Bsm already holds the smoothed candidates
 static void build_transfer(rn_hierarchy &h, const CsrView &A, const DCsr &N, const int32_t *agg,
                            const int32_t *roots, int32_t nc, const int32_t *rowtype, double *Bsm, const double *diag,
-                           double *Bc, DCsr &Pout, DCsr *Tkeep) {
+                           double *Bc, DCsr &Pout, DCsr *Tkeep, bool smoothed = false) {
     cudaStream_t s = h.s;
     const int32_t n = A.n;
     const int k = h.k;
-    // candidates: b_sweeps weighted-Jacobi sweeps on A B = 0 (exact)
-    {
-        DVec<double> tmp((size_t)n * k, s);
-        for (int sw = 0; sw < h.p.b_sweeps; sw++) {
-            if (k == 1)
-                RN_LAUNCH("candidates", 12.0 * A.nnz + 24.0 * n, s, cand_jacobi_kernel, rows_grid(n), kT, 0, n,
-                          A.rowptr, A.col, A.val, Bsm, h.p.omega, tmp.p);
-            else
-                RN_LAUNCH("candidates", 12.0 * A.nnz + 8.0 * k * (A.nnz + 2.0 * n), s, cand_jacobi_k_kernel,
-                          rows_grid(n), kT, 0, n, k, A.rowptr, A.col, A.val, Bsm, h.p.omega, tmp.p);
-            d2d(Bsm, tmp.p, (size_t)n * k, s);
-        }
+    // candidates (unless the caller smoothed them)
+    if (!smoothed && h.p.b_sweeps > 0) {
+        DVec<double> t0((size_t)n * k, s), t1((size_t)n * k, s);
+        d2d(Bsm, smooth_candidates(h, A, Bsm, t0.p, t1.p, s), (size_t)n * k, s);
     }
     fill_i32(h.iflags.p + 2, 0, 1, s);
     if (k == 1)
@@ -2407,6 +2440,31 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         const int32_t n = L.A.n;
         CsrView A = view(L.A);
         check_flag(h.iflags.p + 4, s, RN_EINVAL, "missing or zero diagonal");
+        // ---- candidates smoothed on the side stream (they need only A and B)
+        //      while this stream aggregates; joined after the aggregate count
+        SideStream &ss = side_stream();
+        DVec<double> cb0, cb1;
+        const double *Bsmooth = nullptr;
+        if (p.b_sweeps > 0) {
+            cb0.alloc((size_t)n * h.k, s);
+            cb1.alloc((size_t)n * h.k, s);
+            RN_CUDA_CHECK(cudaEventRecord(ss.fork, s));
+            RN_CUDA_CHECK(cudaStreamWaitEvent(ss.s, ss.fork, 0));
+            Bsmooth = smooth_candidates(h, A, L.B.p, cb0.p, cb1.p, ss.s);
+            RN_CUDA_CHECK(cudaEventRecord(ss.join, ss.s));
+        }
+        struct Join {  // the side stream's work is joined before this level's buffers can go
+            cudaStream_t s;
+            cudaEvent_t e;
+            bool on;
+            void operator()() {
+                if (on) RN_CUDA_CHECK(cudaStreamWaitEvent(s, e, 0));
+                on = false;
+            }
+            ~Join() {
+                if (on) cudaStreamWaitEvent(s, e, 0);
+            }
+        } join{s, ss.join, p.b_sweeps > 0};
         const int32_t *roff = ms ? ms->roff.p : nullptr;  // aggregation priorities within each problem
         // ---- strength (line 'strength')
         const double theta = (l > 0 && p.soc_theta_coarse >= 0.0) ? p.soc_theta_coarse : p.soc_theta;
@@ -2485,6 +2543,7 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         DVec<int32_t> cidx(nn + 1, s);
         RN_LAUNCH("aggregate", 8.0 * nn, s, flag_taken_kernel, rows_grid(nn), kT, 0, nn, state.p, m1.p);
         const int32_t ncn = (int32_t)scan_counts(m1.p, cidx.p, nn, s);  // node aggregates
+        join();  // before a stalled level's buffers are split off or replaced
         if (ms) {
             const int st = ms->stalled(h, l, cidx.p);
             if (st == 2) break;  // every remaining problem stalled here
@@ -2572,8 +2631,9 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         }
         // ---- candidates, T, energy minimisation, filtering -> P
         L.Bc.alloc((size_t)nc * h.k, s);
+        if (Bsmooth) d2d(L.B.p, Bsmooth, (size_t)n * h.k, s);
         build_transfer(h, A, N, L.agg.p, L.roots.p, nc, L.rowtype.p, L.B.p, L.diag.p, L.Bc.p, L.P,
-                       p.keep_aux ? &L.T : nullptr);
+                       p.keep_aux ? &L.T : nullptr, true);
         // ---- R
         if (p.symmetric) {
             transpose(view(L.P), true, L.R, s);
