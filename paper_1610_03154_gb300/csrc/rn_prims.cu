@@ -601,7 +601,8 @@ void transpose(const CsrView &A, bool with_val, DCsr &At, cudaStream_t s) {
     if (A.nnz)
         RN_LAUNCH("transpose", 4.0 * A.nnz, s, count_cols_kernel, grid_for(A.nnz, 1024), 256, 0, A.nnz, A.col, cnt.p);
     At.rowptr.alloc(A.m + 1, s);
-    scan_counts(cnt.p, At.rowptr.p, A.m, s);
+    DVec<int64_t> tot(1, s);  // the total is A.nnz: nothing to read back
+    scan_counts_dev(cnt.p, At.rowptr.p, A.m, tot.p, s);
     DVec<int32_t> next(A.m, s), tcol(A.nnz, s);
     DVec<double> tval;
     if (with_val) tval.alloc(A.nnz, s);

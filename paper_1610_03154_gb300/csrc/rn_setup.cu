@@ -2514,7 +2514,11 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
                       SG.rowptr.p, SG.col.p, St.rowptr.p, St.col.p, cnt.p, nullptr, nullptr);
             Gr.n = Gr.m = nn;
             Gr.rowptr.alloc(nn + 1, s);
-            Gr.nnz = scan_counts(cnt.p, Gr.rowptr.p, nn, s);
+            // only the row pointers are read from here on: the graph is allocated at
+            // its bound (S and S^T without the diagonal) and its size never read back
+            DVec<int64_t> tot(1, s);
+            scan_counts_dev(cnt.p, Gr.rowptr.p, nn, tot.p, s);
+            Gr.nnz = 2 * SG.nnz;
             Gr.col.alloc(Gr.nnz, s);
             RN_LAUNCH("agg_graph", 8.0 * SG.nnz + 8.0 * nn + 4.0 * Gr.nnz, s, union_kernel<true>, rows_grid(nn), kT, 0,
                       nn, SG.rowptr.p, SG.col.p, St.rowptr.p, St.col.p, nullptr, Gr.rowptr.p, Gr.col.p);
@@ -2589,7 +2593,11 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             cur.m = ncn;
             cur.rowptr.alloc(nn + 1, s);
             RN_LAUNCH("pattern", 8.0 * nn, s, aggflag_kernel, rows_grid(nn), kT, 0, nn, agg_n, m1.p);
-            cur.nnz = scan_counts(m1.p, cur.rowptr.p, nn, s);
+            // at most one entry per row, read through the row pointers only: allocated
+            // at that bound, its size never read back
+            DVec<int64_t> tot(1, s);
+            scan_counts_dev(m1.p, cur.rowptr.p, nn, tot.p, s);
+            cur.nnz = nn;
             cur.col.alloc(cur.nnz, s);
             cur.val.alloc(cur.nnz, s);
             RN_LAUNCH("pattern", 16.0 * nn, s, c_matrix_kernel, rows_grid(nn), kT, 0, nn, agg_n, cur.rowptr.p,
