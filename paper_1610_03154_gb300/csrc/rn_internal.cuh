@@ -277,7 +277,13 @@ void reciprocal(const double *x, double *y, int64_t n, cudaStream_t s);
 // instruction instead of two; the Galerkin products, held to 1e-12 rather
 // than bit-exactness), still in ascending k; rows of the sorting kernel keep
 // the separate operations.
-void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fused = false);
+// b_nnz_dev (optional): B's size on the device (B.nnz then need only bound it:
+// the exact value comes back with the first read); err_dev (optional): no
+// second read - C is allocated at its bound (C.nnz = the product count, the
+// exact size in C.rowptr[n]) and a row past the block kernel's table is
+// reported in *err_dev (row + 1, atomic max) for the caller to read later
+void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fused = false,
+            const int32_t *b_nnz_dev = nullptr, int32_t *err_dev = nullptr);
 
 // Energy-minimisation operator on the fixed pattern N shared by X and W:
 //   W = scale * Proj(Mask_N(A X)) with A's values aval (TV = double, or float

@@ -2239,6 +2239,18 @@ struct MergedSetup {
 
 static const SegRows *seg_of(const rn_hierarchy &h) { return h.merged ? &h.merged->seg : nullptr; }
 
+// A scan whose total comes back in the same read as the level's flags
+// (iflags[0..16), the total in iflags[14..15]), so checks deferred to it cost
+// no synchronisation of their own
+static int64_t scan_with_flags(rn_hierarchy &h, const int32_t *counts, int32_t *out, int64_t n, int32_t (&fl)[16]) {
+    scan_counts_dev(counts, out, n, reinterpret_cast<int64_t *>(h.iflags.p + 14), h.s);
+    read_small(fl, h.iflags.p, 16, h.s);
+    int64_t t;
+    std::memcpy(&t, fl + 14, sizeof t);
+    if (t > INT32_MAX) fail(RN_EINTERNAL, fmt("scan total %lld exceeds int32", (long long)t));
+    return t;
+}
+
 static void check_flag(const int32_t *flag, cudaStream_t s, rn_status st, const char *what) {
     int32_t v = read_scalar(flag, s);
     if (v) fail(st, fmt("%s (index %d)", what, v - 1));
@@ -2439,7 +2451,8 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         }
         const int32_t n = L.A.n;
         CsrView A = view(L.A);
-        check_flag(h.iflags.p + 4, s, RN_EINVAL, "missing or zero diagonal");
+        // the diagonal's flag is read with the strength pattern's size (a zero
+        // diagonal only makes strength values non-finite until then)
         // ---- candidates smoothed on the side stream (they need only A and B)
         //      while this stream aggregates; joined after the aggregate count
         SideStream &ss = side_stream();
@@ -2478,7 +2491,9 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
                       A.rowptr, A.col, A.val, L.diag.p, thr, cnt.p, vtmp.p, vmax.p, nullptr, nullptr, nullptr,
                       p.soc_kind == RN_SOC_CLASSICAL ? 1 : 0);
             S.rowptr.alloc(n + 1, s);
-            S.nnz = scan_counts(cnt.p, S.rowptr.p, n, s);
+            int32_t fl[16];
+            S.nnz = scan_with_flags(h, cnt.p, S.rowptr.p, n, fl);
+            if (fl[4]) fail(RN_EINVAL, fmt("missing or zero diagonal (index %d)", fl[4] - 1));
             S.col.alloc(S.nnz, s);
             S.val.alloc(S.nnz, s);
             RN_LAUNCH("strength", 12.0 * A.nnz + 12.0 * n + 12.0 * S.nnz, s, strength_kernel<true>, rows_grid(n), kT,
@@ -2577,7 +2592,9 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
         fill_i32(h.iflags.p + 6, 0, 1, s);
         RN_LAUNCH("aggregate", gb + 16.0 * nn, s, agg_pass2_kernel, rows_grid(nn), kT, 0, nn, Gr.rowptr.p, Gr.col.p,
                   state.p, r1.p, roots_n, seed, roff, agg_n, h.iflags.p + 6);
-        check_flag(h.iflags.p + 6, s, RN_EINTERNAL, "aggregation pass 2 left a node unassigned");
+        // scalar problems read this flag with the pre-filter's size (an unassigned
+        // node is only an unaggregated row until then); block systems at once
+        if (mb > 1) check_flag(h.iflags.p + 6, s, RN_EINTERNAL, "aggregation pass 2 left a node unassigned");
         RN_LAUNCH("aggregate", 12.0 * nn, s, rowtype_kernel, rows_grid(nn), kT, 0, nn, state.p, agg_n, rt_n);
         if (mb > 1) {  // unamalgamate: aggregates, row types and roots of the unknowns
             RN_LAUNCH("aggregate", 16.0 * n, s, unamalgamate_nodes_kernel, rows_grid(n), kT, 0, n, mb, agg_n, rt_n,
@@ -2602,9 +2619,13 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             cur.val.alloc(cur.nnz, s);
             RN_LAUNCH("pattern", 16.0 * nn, s, c_matrix_kernel, rows_grid(nn), kT, 0, nn, agg_n, cur.rowptr.p,
                       cur.col.p, cur.val.p);
+            // each product's exact size stays on the device and comes back with the
+            // next product's first read; a row past the block kernel's table is
+            // reported with the pre-filter's read
+            fill_i32(h.iflags.p + 12, 0, 1, s);
             for (int t = 0; t < p.degree; t++) {
                 DCsr nxt;
-                spgemm(view(SG), view(cur), nxt, s);
+                spgemm(view(SG), view(cur), nxt, s, false, cur.rowptr.p + cur.n, h.iflags.p + 12);
                 cur = std::move(nxt);
             }
             DVec<int32_t> cnt(nn + 1, s);
@@ -2615,7 +2636,11 @@ void build_hierarchy(rn_hierarchy &h, const CsrView &A0, const double *B0, const
             NN.n = nn;
             NN.m = ncn;
             NN.rowptr.alloc(nn + 1, s);
-            NN.nnz = scan_counts(cnt.p, NN.rowptr.p, nn, s);
+            int32_t fl[16];
+            NN.nnz = scan_with_flags(h, cnt.p, NN.rowptr.p, nn, fl);
+            if (mb == 1 && fl[6])
+                fail(RN_EINTERNAL, fmt("aggregation pass 2 left a node unassigned (index %d)", fl[6] - 1));
+            if (fl[12]) fail(RN_EINTERNAL, fmt("pattern product row %d has more than 4096 distinct columns", fl[12] - 1));
             NN.col.alloc(NN.nnz, s);
             NN.val.alloc(NN.nnz, s);
             RN_LAUNCH("prefilter", 12.0 * cur.nnz + 12.0 * nn + 12.0 * NN.nnz, s, prefilter_kernel<true>,

@@ -417,7 +417,10 @@ hash_product_block_kernel(const int32_t *__restrict__ nrows_dev, const int32_t *
         }
         __syncthreads();
         if (bad || cnt > kBigProd / 2) {
-            if (threadIdx.x == 0) atomicMax(err, i + 1);
+            if (threadIdx.x == 0) {
+                atomicMax(err, i + 1);
+                count[i] = 0;  // an empty row keeps the compaction in bounds until the error is read
+            }
             continue;
         }
         for (int q = threadIdx.x; q < kBigProd; q += blockDim.x)
@@ -501,16 +504,20 @@ static void launch_small(int32_t nrows_max, const int32_t *nrows_dev, const int3
               A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, ubp, tcol, tval, count);
 }
 
-void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fused) {
+void spgemm(const CsrView &A, const CsrView &Bin, DCsr &C, cudaStream_t s, bool fused, const int32_t *b_nnz_dev,
+            int32_t *err_dev) {
+    CsrView B = Bin;
     if (A.m != B.n) fail(RN_EINTERNAL, "spgemm: inner dimensions differ");
     C.n = A.n;
     C.m = B.m;
     const int32_t n = A.n;
     // flags: [0] small rows, [1] large rows, [2] count overflow, [3] rows past the hash tables, [4] past kBigProd,
-    // [5] small rows with too many entries to merge; then two int64 totals at flags + 8 (8-byte aligned)
+    // [5] small rows with too many entries to merge, [6] B's size (given on the device); then two int64 totals at
+    // flags + 8 (8-byte aligned)
     DVec<int32_t> ub(n + 1, s), ubp(n + 1, s), count(n + 1, s), flags(12, s), bins(n > 0 ? n : 1, s),
         ovf_list(n > 0 ? n : 1, s), ovf2(n > 0 ? n : 1, s);
     fill_i32(flags.p, 0, 12, s);
+    if (b_nnz_dev) d2d(flags.p + 6, b_nnz_dev, 1, s);  // comes back with the first read
     int64_t *tot = reinterpret_cast<int64_t *>(flags.p + 8);
     if (n)
         RN_LAUNCH("spgemm_bound", 8.0 * A.nnz + 16.0 * n, s, product_bound_kernel, grid_for(n, 256), 256, 0, n,
@@ -521,6 +528,7 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fu
     int64_t total = 0;
     std::memcpy(&total, fl + 8, sizeof total);
     if (fl[2] || total > INT32_MAX) fail(RN_EINTERNAL, "spgemm: a row's product count exceeds int32");
+    if (b_nnz_dev) B.nnz = fl[6];
     DVec<int32_t> tcol(total > 0 ? total : 1, s);
     DVec<double> tval(total > 0 ? total : 1, s);
     const double bytes = 12.0 * A.nnz + 8.0 * n + 12.0 * B.nnz + 12.0 * total;
@@ -571,15 +579,22 @@ void spgemm(const CsrView &A, const CsrView &B, DCsr &C, cudaStream_t s, bool fu
             launch_hash<32, 1024>(fused, nlarge, bins.p + (n - nlarge), A, B, ubp.p, tcol.p, tval.p, count.p, ovf2.p,
                                   flags.p + 3, bytes, s);
         // rows past the tables (counted on the device): a block per row, looping
-        if (fused) launch_block<true>(nlarge, flags.p + 3, ovf2.p, A, B, ubp.p, tcol.p, tval.p, count.p, flags.p + 4, s);
-        else launch_block<false>(nlarge, flags.p + 3, ovf2.p, A, B, ubp.p, tcol.p, tval.p, count.p, flags.p + 4, s);
+        int32_t *err = err_dev ? err_dev : flags.p + 4;
+        if (fused) launch_block<true>(nlarge, flags.p + 3, ovf2.p, A, B, ubp.p, tcol.p, tval.p, count.p, err, s);
+        else launch_block<false>(nlarge, flags.p + 3, ovf2.p, A, B, ubp.p, tcol.p, tval.p, count.p, err, s);
     }
     C.rowptr.alloc(n + 1, s);
     scan_counts_dev(count.p, C.rowptr.p, n, tot + 1, s);
-    read_small(fl, flags.p, 12, s);
-    if (fl[4]) fail(RN_EINTERNAL, fmt("product row has more than %d distinct columns", kBigProd / 2));
-    std::memcpy(&total, fl + 10, sizeof total);
-    C.nnz = total;
+    if (err_dev) {
+        // C's size stays on the device (its last row pointer); C is allocated at
+        // its bound, the product count, and the caller reads err_dev later
+        C.nnz = total;
+    } else {
+        read_small(fl, flags.p, 12, s);
+        if (fl[4]) fail(RN_EINTERNAL, fmt("product row has more than %d distinct columns", kBigProd / 2));
+        std::memcpy(&total, fl + 10, sizeof total);
+        C.nnz = total;
+    }
     C.col.alloc(C.nnz, s);
     C.val.alloc(C.nnz, s);
     if (n)
