@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <type_traits>
 
 #include "rn_internal.cuh"
 
@@ -274,6 +275,11 @@ merge_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int3
     }
 }
 
+// The compaction list's slot indices: a byte for tables of up to 256 slots,
+// else 16 bits (a smaller footprint per group fits more CTAs per SM).
+template <int SLOTS>
+using HashListT = typename std::conditional<(SLOTS <= 256), uint8_t, uint16_t>::type;
+
 // G lanes per row, SLOTS table entries per group, for the rows listed in
 // rows.  Rows whose distinct columns exceed SLOTS/2 go to ovf_list.
 template <int G, int SLOTS, bool FUSED>
@@ -289,13 +295,13 @@ hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32
     extern __shared__ __align__(16) unsigned char fu_smem[];
     double *vals_all = reinterpret_cast<double *>(fu_smem);
     int32_t *keys_all = reinterpret_cast<int32_t *>(fu_smem + (size_t)GPB * SLOTS * sizeof(double));
-    int32_t *list_all = keys_all + GPB * SLOTS;
+    HashListT<SLOTS> *list_all = reinterpret_cast<HashListT<SLOTS> *>(keys_all + GPB * SLOTS);
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned mask = group_mask<G>();
     const unsigned gbase = (threadIdx.x & 31) & ~(G - 1);
     double *vals = vals_all + g * SLOTS;
     int32_t *keys = keys_all + g * SLOTS;
-    int32_t *list = list_all + g * (SLOTS / 2);
+    HashListT<SLOTS> *list = list_all + g * (SLOTS / 2);
     for (int32_t r = blockIdx.x * GPB + g; r < nrows; r += gridDim.x * GPB) {
         const int32_t i = rows[r];
         const int32_t ub = ubp[i + 1] - ubp[i];
@@ -350,7 +356,7 @@ hash_product_kernel(int32_t nrows, const int32_t *__restrict__ rows, const int32
             const int q = q0 + lane;
             const bool occ = keys[q] >= 0;
             const unsigned bal = (__ballot_sync(mask, occ) >> gbase) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
-            if (occ) list[u + __popc(bal & ((1u << lane) - 1u))] = q;
+            if (occ) list[u + __popc(bal & ((1u << lane) - 1u))] = (HashListT<SLOTS>)q;
             u += __popc(bal);
         }
         __syncwarp(mask);
@@ -459,7 +465,8 @@ static void launch_hash_t(int32_t nrows, const int32_t *rows, const CsrView &A, 
                           int32_t *tcol, double *tval, int32_t *count, int32_t *ovf_list, int32_t *ovf_n,
                           double bytes, cudaStream_t s) {
     constexpr int GPB = kFuThreads / G;
-    const size_t smem = (size_t)GPB * SLOTS * (sizeof(double) + sizeof(int32_t)) + (size_t)GPB * (SLOTS / 2) * 4;
+    const size_t smem = (size_t)GPB * SLOTS * (sizeof(double) + sizeof(int32_t)) +
+                        (size_t)GPB * (SLOTS / 2) * sizeof(HashListT<SLOTS>);
     static const bool configured = [&] {  // once per instantiation (thread-safe static initialisation)
         RN_CUDA_CHECK(cudaFuncSetAttribute(hash_product_kernel<G, SLOTS, FUSED>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
