@@ -54,6 +54,22 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// An L2 policy that makes the lines it tags the first to be evicted: the
+// matrix streams (read once per launch, and a cycle streams several times L2's
+// capacity) then leave the vectors the gathers read resident in L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void bulk_g2s_stream(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                                uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -139,6 +155,7 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
     }
     __syncthreads();
     uint32_t pend = 0u;             // thread 0: bit s = copies into stage s issued, not yet waited for
+    const uint64_t pol = l2_evict_first_policy();
     int32_t be0 = 0, be1 = 0;       // thread 0: nnz bounds of the next tile to issue
     // the tiles to process: all, or (TL) the first *tcount entries of tlist
     // (which only change between launches, so they are read before pdl_wait)
@@ -164,8 +181,8 @@ spmv_tile_kernel(int32_t n, int32_t ntiles, const int32_t *__restrict__ rp, cons
         const uint32_t rb = (uint32_t)(((r1 - r0 + 1) + 3) & ~3) * 4u;  // r0 is a multiple of 8: aligned
         mbar_expect_tx(&bar[stage], cb + vb + rb);
         bulk_g2s(srp + stage * RL, rp + r0, rb, &bar[stage]);
-        if (cb) bulk_g2s(scol + stage * SL, col + c0, cb, &bar[stage]);
-        if (vb) bulk_g2s(sval + stage * SL, val + v0, vb, &bar[stage]);
+        if (cb) bulk_g2s_stream(scol + stage * SL, col + c0, cb, &bar[stage], pol);
+        if (vb) bulk_g2s_stream(sval + stage * SL, val + v0, vb, &bar[stage], pol);
         pend |= 1u << stage;
     };
     double red[NV] = {};
