@@ -294,12 +294,13 @@ rn_status rn_energy_min(const rn_csr *A, const rn_csr *N, const int32_t *rowtype
  *   Limits: A->n_rows <= 262144 and N->nnz <= 524288; larger inputs return
  *   RN_EINVAL with a message naming the limit.
  *   The first call on a device resolves the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   (cudaGetSymbolAddress).
  *   stream NULL means the legacy default stream.
  *   All calls share the array: calls whose GPU work overlaps (other streams,
  *   other threads) race on it and must be serialised by the caller.
  *   The call reads one flag back to the host and synchronises its stream
- *   before it returns.  rn_allocation_count() is unchanged across the call. */
+ *   before it returns, so it cannot be captured into a CUDA graph.
+ *   rn_allocation_count() is unchanged across the call. */
 rn_status rn_energy_min_noalloc(const rn_csr *A, const rn_csr *N, const int32_t *rowtype, const double *Bc,
                                 double *P, int sweeps, int precond, void *stream);
 
