@@ -254,6 +254,10 @@ void scan_counts_dev(const int32_t *counts, int32_t *out, int64_t n, int64_t *to
 constexpr int kReduceBlocks = 1216;   // partial-sum slots per value (8 x 152 SMs)
 struct Fin;
 // *result = <x, y>
+// y -= (*h) x, then *result = <y, xn> (xn null: <y, y>), bit-identical to the
+// axpy and dot() launched apart
+void axpy_dot(double *y, const double *x, const double *h, const double *xn, int64_t n, double *result,
+              cudaStream_t s, double *partial, unsigned *counter);
 void dot(const double *x, const double *y, int64_t n, double *result, cudaStream_t s, double *partial,
          unsigned *counter);
 void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);

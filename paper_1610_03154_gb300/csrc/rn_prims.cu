@@ -465,6 +465,36 @@ void dot(const double *x, const double *y, int64_t n, double *result, cudaStream
     RN_LAUNCH("dot", 16.0 * n, s, dot_kernel, nb, kRedThreads, 0, x, y, n, f);
 }
 
+// y -= (*h) x, then <y, xn> of the updated y (xn null: <y, y>): one step of
+// modified Gram-Schmidt fused with the next projection (or the norm).  The update is the same
+// expression as a separate axpy and the sum is formed as dot() forms it (same
+// grid, per-thread order and block-order finish), so the results are the
+// same bits as the two launches.
+__global__ void axpy_dot_kernel(double *__restrict__ y, const double *__restrict__ x, const double *__restrict__ h,
+                                const double *__restrict__ xn, int64_t n, Fin fin) {
+    pdl_wait();
+    __shared__ double sm[32];
+    const double c = *h;
+    double v[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double yi = y[i] - c * x[i];
+        y[i] = yi;
+        v[0] = fma(yi, xn ? xn[i] : yi, v[0]);
+    }
+    grid_finish<kRedThreads, 1>(v, fin, sm);
+}
+
+void axpy_dot(double *y, const double *x, const double *h, const double *xn, int64_t n, double *result,
+              cudaStream_t s, double *partial, unsigned *counter) {
+    const int nb = grid_resident((const void *)dot_kernel, kRedThreads, 0, n, kRedThreads * 4, kReduceBlocks);
+    Fin f;
+    f.mode = FIN_STORE;
+    f.partial = partial;
+    f.counter = counter;
+    f.out = result;
+    RN_LAUNCH("outer_gmres_vec", 32.0 * n, s, axpy_dot_kernel, nb, kRedThreads, 0, y, x, h, xn, n, f);
+}
+
 // --------------------------------------------------------------------- elementwise
 __global__ void fill_i32_kernel(int32_t *p, int32_t v, int64_t n) {
     pdl_wait();

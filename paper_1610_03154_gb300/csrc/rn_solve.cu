@@ -240,14 +240,6 @@ __global__ void scale_copy_kernel(int64_t n, const double *__restrict__ x, const
         y[i] = x[i] / d;
 }
 
-__global__ void axpy_dev_kernel(int64_t n, double *__restrict__ w, const double *__restrict__ v,
-                                const double *__restrict__ h) {
-    pdl_wait();
-    const double c = *h;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        w[i] = w[i] - c * v[i];
-}
-
 // FGMRES Givens step on column j (H row-major (m+1) x m); g rhs; |g_{j+1}| -> sc[15]
 __global__ void fg_givens_kernel(int m, int j, double *H, double *cs, double *sn, double *g, double *sc) {
     pdl_wait();
@@ -1120,13 +1112,18 @@ rn_status solve(rn_hierarchy &h, const double *b, double *x, double rtol, int ma
                 apply_cycle(h, vj, zj);
                 spmv<double, double, double, OP_SPMV>(h, "outer_spmv", L0.A, zj, (const double *)nullptr, nullptr,
                                                       0.0, h.w.p, none);
+                // modified Gram-Schmidt: each update w -= h_ij v_i is fused with
+                // the next projection <w, v_{i+1}> (the last with ||w||^2), the
+                // same operations in the same order as separate launches
+                dot(h.w.p, h.V.p, n, H + j, s, h.partial.p, h.counters.p);
                 for (int i = 0; i <= j; i++) {
-                    double *vi = h.V.p + (int64_t)i * n;
-                    dot(h.w.p, vi, n, H + i * m + j, s, h.partial.p, h.counters.p);
-                    RN_LAUNCH("outer_gmres_vec", 24.0 * n, s, axpy_dev_kernel, eg, 256, 0, n, h.w.p, vi,
-                              H + i * m + j);
+                    const double *vi = h.V.p + (int64_t)i * n;
+                    if (i < j)
+                        axpy_dot(h.w.p, vi, H + i * m + j, vi + n, n, H + (i + 1) * m + j, s, h.partial.p,
+                                 h.counters.p);
+                    else
+                        axpy_dot(h.w.p, vi, H + i * m + j, nullptr, n, sc + 8, s, h.partial.p, h.counters.p);
                 }
-                dot(h.w.p, h.w.p, n, sc + 8, s, h.partial.p, h.counters.p);
                 RN_LAUNCH("outer_gmres_scalar", 0, s, fg_givens_kernel, 1, 1, 0, m, j, H, cs, sn, g, sc);
                 it++;
                 k = j + 1;
